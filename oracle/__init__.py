@@ -1,0 +1,222 @@
+"""Plain FP64 CPU oracle for the DG wall-model operators (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package. It wraps ``dgw_oracle.c`` (plain C, OpenMP over cells, full 3-D tabulation of the
+basis at every quadrature point, no sum factorisation) through ctypes and shares nothing with the
+CUDA library.
+
+Paper: Krank, Kronbichler & Wall, arXiv 1705.08813. Each C function cites the section or
+equation it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dgw_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP). Returns the path of the shared library."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("k", ctypes.c_int), ("enrich_l", ctypes.c_int), ("q_wall", ctypes.c_int),
+        ("geometry", ctypes.c_int), ("wall_law", ctypes.c_int), ("n_layers", ctypes.c_int),
+        ("extra_q", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("nu", ctypes.c_double), ("tau_w", ctypes.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lp = ctypes.POINTER(ctypes.c_long)
+        vp = ctypes.c_void_p
+        lib.dgo_mesh_create.restype = vp
+        lib.dgo_mesh_create.argtypes = [ctypes.POINTER(Params)]
+        lib.dgo_mesh_destroy.argtypes = [vp]
+        lib.dgo_mesh_info.argtypes = [vp, lp, lp, lp]
+        lib.dgo_node_coords.argtypes = [vp, dp]
+        lib.dgo_cell_tau.argtypes = [vp, dp]
+        for name in ("dgo_laplace", "dgo_divergence", "dgo_convective", "dgo_laplace_diag"):
+            getattr(lib, name).argtypes = [vp, dp, dp] if name != "dgo_laplace_diag" else [vp, dp]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.dgo_viscous.argtypes = [vp, dp, dp, dp]
+        lib.dgo_mass.argtypes = [vp, dp, dp]
+        lib.dgo_solve_cg.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_int, ip, dp]
+        lib.dgo_eval_point.argtypes = [vp, dp, ctypes.c_int, dp, dp]
+        lib.dgo_nut_cell.argtypes = [vp, dp, ctypes.c_int, dp]
+        lib.dgo_nut_cell.restype = ctypes.c_int
+        lib.dgo_volume.argtypes = [vp]
+        lib.dgo_volume.restype = ctypes.c_double
+        lib.dgo_psi_spalding.argtypes = [ctypes.c_double, dp]
+        lib.dgo_psi_spalding.restype = ctypes.c_double
+        lib.dgo_psi_vandriest.argtypes = [ctypes.c_double, dp]
+        lib.dgo_psi_vandriest.restype = ctypes.c_double
+        lib.dgo_psi_vd_from.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.dgo_psi_vd_from.restype = ctypes.c_double
+        lib.dgo_gauss.argtypes = [ctypes.c_int, dp, dp]
+        lib.dgo_lobatto.argtypes = [ctypes.c_int, dp]
+        lib.dgo_num_threads.restype = ctypes.c_int
+        lib.dgo_set_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def gauss(n: int):
+    """n-point Gauss-Legendre rule on [0, 1] (nodes ascending, weights)."""
+    x = np.zeros(n); w = np.zeros(n)
+    _load().dgo_gauss(n, _ptr(x), _ptr(w))
+    return x, w
+
+
+def lobatto(n: int):
+    """n Gauss-Lobatto nodes on [0, 1]."""
+    x = np.zeros(n)
+    _load().dgo_lobatto(n, _ptr(x))
+    return x
+
+
+def psi_spalding(yp: float):
+    """Spalding wall law inverted for psi = u+(y+); returns (psi, dpsi/dy+)."""
+    d = ctypes.c_double()
+    v = _load().dgo_psi_spalding(float(yp), ctypes.byref(d))
+    return v, d.value
+
+
+def psi_vandriest(yp: float):
+    """van Driest wall law, eq. (psi), evaluated as in Appendix A; returns (psi, dpsi/dy+)."""
+    d = ctypes.c_double()
+    v = _load().dgo_psi_vandriest(float(yp), ctypes.byref(d))
+    return v, d.value
+
+
+def psi_vandriest_from(i: int, yp: float) -> float:
+    """psi_i + 9-point Gauss integral over [y_i+, y+] from Table A1 row i (eq. psinum)."""
+    return _load().dgo_psi_vd_from(int(i), float(yp))
+
+
+def set_threads(n: int) -> None:
+    _load().dgo_set_threads(int(n))
+
+
+def num_threads() -> int:
+    return _load().dgo_num_threads()
+
+
+class Mesh:
+    """Oracle mesh of a channel (geometry 0) or bump channel (geometry 1)."""
+
+    def __init__(self, nx, ny, nz, k, *, lx=2 * np.pi, ly=2.0, lz=np.pi, gamma=1.8, nu=1.0 / 3250,
+                 tau_w=1.0, enrich_l=1, q_wall=8, geometry=0, wall_law=0, n_layers=1, extra_q=0):
+        self.lib = _load()
+        self.params = Params(nx, ny, nz, k, enrich_l, q_wall, geometry, wall_law, n_layers, extra_q,
+                             lx, ly, lz, gamma, nu, tau_w)
+        h = self.lib.dgo_mesh_create(ctypes.byref(self.params))
+        if not h:
+            raise ValueError("oracle: invalid mesh parameters")
+        self.h = ctypes.c_void_p(h)
+        np_, nu_, ne_ = ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+        self.lib.dgo_mesh_info(self.h, ctypes.byref(np_), ctypes.byref(nu_), ctypes.byref(ne_))
+        self.n_p, self.n_u, self.n_e = np_.value, nu_.value, ne_.value
+        self.k = k
+        self.nc = nx * ny * nz
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.dgo_mesh_destroy(h)
+            self.h = None
+
+    def node_coords(self) -> np.ndarray:
+        out = np.zeros((self.n_p, 3))
+        self.lib.dgo_node_coords(self.h, _ptr(out))
+        return out
+
+    def cell_tau(self) -> np.ndarray:
+        out = np.zeros(self.nc)
+        self.lib.dgo_cell_tau(self.h, _ptr(out))
+        return out
+
+    def volume(self) -> float:
+        return self.lib.dgo_volume(self.h)
+
+    def laplace(self, p: np.ndarray) -> np.ndarray:
+        p = np.ascontiguousarray(p, dtype=np.float64); y = np.zeros(self.n_p)
+        self.lib.dgo_laplace(self.h, _ptr(p), _ptr(y))
+        return y
+
+    def mass(self, p: np.ndarray) -> np.ndarray:
+        p = np.ascontiguousarray(p, dtype=np.float64); y = np.zeros(self.n_p)
+        self.lib.dgo_mass(self.h, _ptr(p), _ptr(y))
+        return y
+
+    def laplace_diag(self) -> np.ndarray:
+        y = np.zeros(self.n_p)
+        self.lib.dgo_laplace_diag(self.h, _ptr(y))
+        return y
+
+    def divergence(self, u: np.ndarray) -> np.ndarray:
+        u = np.ascontiguousarray(u, dtype=np.float64); b = np.zeros(self.n_p)
+        self.lib.dgo_divergence(self.h, _ptr(u), _ptr(b))
+        return b
+
+    def convective(self, u: np.ndarray) -> np.ndarray:
+        u = np.ascontiguousarray(u, dtype=np.float64); y = np.zeros(self.n_u)
+        self.lib.dgo_convective(self.h, _ptr(u), _ptr(y))
+        return y
+
+    def viscous(self, u_frozen: np.ndarray, u: np.ndarray) -> np.ndarray:
+        uf = np.ascontiguousarray(u_frozen, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64); y = np.zeros(self.n_u)
+        self.lib.dgo_viscous(self.h, _ptr(uf), _ptr(u), _ptr(y))
+        return y
+
+    def solve(self, b: np.ndarray, rtol=1e-12, maxit=20000):
+        b = np.ascontiguousarray(b, dtype=np.float64); p = np.zeros(self.n_p)
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        self.lib.dgo_solve_cg(self.h, _ptr(b), _ptr(p), rtol, maxit, ctypes.byref(it), ctypes.byref(rr))
+        return p, it.value, rr.value
+
+    def eval_point(self, u: np.ndarray, cell: int, xi) -> dict:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        xi = np.ascontiguousarray(xi, dtype=np.float64); out = np.zeros(12)
+        self.lib.dgo_eval_point(self.h, _ptr(u), int(cell), _ptr(xi), _ptr(out))
+        return {"u": out[0:3], "ubar": out[3:6], "util": out[6:9], "psi": out[9],
+                "yplus": out[10], "nut": out[11]}
+
+    def nut_cell(self, u: np.ndarray, e: int) -> np.ndarray:
+        u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(4096)
+        n = self.lib.dgo_nut_cell(self.h, _ptr(u), int(e), _ptr(out))
+        return out[:n]

@@ -1,0 +1,355 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: values printed in the paper,
+textbook rules computed by other code (NumPy, SciPy), closed-form integrals, invariants of the
+weak forms, brute-force assembly on tiny meshes, and convergence rates.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1705_08813_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------------
+# 1-D rules
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 9, 12])
+def test_gauss_rule_matches_numpy(n):
+    x, w = O.gauss(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(x, 0.5 * (xr + 1.0), atol=1e-15, rtol=0)
+    assert np.allclose(w, 0.5 * wr, atol=1e-15, rtol=0)
+    # exact for degree 2n-1 monomials on [0, 1]
+    for p in range(2 * n):
+        assert abs(np.dot(w, x ** p) - 1.0 / (p + 1)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7])
+def test_lobatto_nodes_are_roots_of_legendre_derivative(n):
+    x = O.lobatto(n)
+    ref = np.sort(np.concatenate([[-1.0, 1.0], np.polynomial.legendre.Legendre.basis(n - 1).deriv().roots()]))
+    assert np.allclose(x, 0.5 * (ref + 1.0), atol=1e-14, rtol=0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Wall laws (Sec. 3.2, Appendix A)
+# ---------------------------------------------------------------------------------------------
+
+def _table_a1():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "psi_vandriest_tableA1.txt")) if l[0] != "#"]
+    return np.array([[float(r[1]), float(r[2])] for r in rows])
+
+
+def test_vandriest_table_chain_reproduces_printed_values():
+    """psi_i + 9-point Gauss integral over [y_i, y_{i+1}] must give the printed psi_{i+1} to the
+    stated 1e-12 accuracy (Appendix A, Table A1): pins the integrand, kappa, A+ and the rule."""
+    t = _table_a1()
+    for i in range(len(t) - 1):
+        v = O.psi_vandriest_from(i, t[i + 1, 0])
+        assert abs(v / t[i + 1, 1] - 1.0) <= 1e-12, (i, v, t[i + 1, 1])
+
+
+def test_vandriest_against_adaptive_quadrature():
+    """psi at arbitrary y+ up to 5000 against an adaptive integration (SciPy) of eq. (psi),
+    anchored at the printed Table A1 values."""
+    from scipy.integrate import quad
+    t = _table_a1()
+
+    def f(y):
+        a = 2 * 0.41 * y * (1 - math.exp(-y / 26.0))
+        return 2.0 / (1.0 + math.sqrt(1.0 + a * a))
+
+    for yp in [0.3, 3.0, 7.5, 17.0, 40.0, 100.0, 250.0, 700.0, 1800.0, 4000.0, 5000.0]:
+        i = int(np.searchsorted(t[:, 0], yp, side="right") - 1)
+        ref = t[i, 1] + quad(f, t[i, 0], yp, epsabs=1e-15, epsrel=1e-15, limit=200)[0]
+        v, d = O.psi_vandriest(yp)
+        assert abs(v / ref - 1.0) <= 1e-12
+        assert abs(d - f(yp)) <= 1e-15
+    # wall behaviour u+(0) = 0, du+/dy+(0) = 1 (Sec. 3.2)
+    assert O.psi_vandriest(0.0) == (0.0, 1.0)
+
+
+def test_spalding_inverse_boundary_and_log_law():
+    k, B = 0.41, 5.17
+    assert O.psi_spalding(0.0) == (0.0, 1.0)
+    v, d = O.psi_spalding(1e-6)
+    assert abs(v - 1e-6) < 1e-15 and abs(d - 1.0) < 1e-5
+    for yp in [1e-3, 0.5, 5.0, 11.0, 30.0, 100.0, 1e3, 5e3, 2e4]:
+        psi, dpsi = O.psi_spalding(yp)
+        kp = k * psi
+        fwd = psi + math.exp(-k * B) * (math.exp(kp) - 1 - kp - kp ** 2 / 2 - kp ** 3 / 6)
+        assert abs(fwd / yp - 1.0) < 1e-14
+        # derivative against a central difference of the inverse
+        h = 1e-5 * max(yp, 1.0)
+        fd = (O.psi_spalding(yp + h)[0] - O.psi_spalding(yp - h)[0]) / (2 * h)
+        assert abs(dpsi / fd - 1.0) < 1e-6
+    # log law for large y+: psi -> ln(y+)/kappa + B
+    for yp in [5e3, 2e4]:
+        assert abs(O.psi_spalding(yp)[0] - (math.log(yp) / k + B)) < 0.05
+
+
+# ---------------------------------------------------------------------------------------------
+# Geometry (Sec. 5.1 channel; bump channel of the curved workload)
+# ---------------------------------------------------------------------------------------------
+
+def test_channel_volume_exact():
+    m = O.Mesh(4, 5, 3, 3, gamma=1.8)
+    assert abs(m.volume() - 4 * math.pi ** 2) < 1e-12 * 4 * math.pi ** 2
+
+
+def test_bump_volume_closed_form():
+    # 9 x [yw(x), 3.036] x 4.5 with yw = 0.3 cos^2(pi (x-4.5)/2) on |x-4.5| < 1: the bump area is
+    # 0.3 * 1 (integral of cos^2 over one period); isoparametric Q4 mapping error is tiny.
+    m = O.Mesh(24, 4, 2, 4, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
+    ref = 9.0 * 3.036 * 4.5 - 4.5 * 0.3
+    assert abs(m.volume() - ref) < 1e-6 * ref
+
+
+# ---------------------------------------------------------------------------------------------
+# SIPG Laplacian, eq. (ipflux)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_laplace_constants_in_null_space(geometry):
+    kw = dict(lx=9.0, ly=3.036, lz=4.5, geometry=1) if geometry else {}
+    m = O.Mesh(4, 3, 2, 3, n_layers=0, **kw)
+    y = m.laplace(np.ones(m.n_p))
+    d = m.laplace_diag()
+    assert np.abs(y).max() < 1e-12 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("dims,k,geometry", [((1, 1, 1), 1, 0), ((2, 1, 1), 2, 0), ((2, 3, 2), 1, 0),
+                                               ((3, 2, 2), 2, 0), ((2, 2, 1), 3, 0), ((3, 2, 1), 2, 1)])
+def test_laplace_bruteforce_symmetric_psd(dims, k, geometry):
+    kw = dict(lx=9.0, ly=3.036, lz=4.5, geometry=1) if geometry else {}
+    m = O.Mesh(*dims, k, n_layers=0, **kw)
+    n = m.n_p
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n); e[j] = 1.0
+        A[:, j] = m.laplace(e)
+    scale = np.abs(A).max()
+    assert np.abs(A - A.T).max() <= 1e-13 * scale
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    assert ev[0] >= -1e-12 * ev[-1]
+    assert ev[1] > 1e-8 * ev[-1]            # exactly one (near-)zero eigenvalue: the constants
+    assert np.allclose(np.diag(A), m.laplace_diag(), rtol=0, atol=1e-13 * scale)
+
+
+def test_laplace_bilinear_form_of_smooth_fields_closed_form():
+    """For continuous fields the SIPG face terms vanish and q^T A p = int grad q . grad p."""
+    m = O.Mesh(3, 5, 2, 3, n_layers=0, gamma=1.8)
+    X = m.node_coords()
+    y = X[:, 1]
+    q = y ** 2
+    p = y ** 2 + y
+    val = q @ m.laplace(p)
+    ref = (2 * math.pi) * math.pi * (8.0 / 3.0)      # Lx Lz int_{-1}^{1} 2y (2y + 1) dy
+    assert abs(val - ref) < 1e-12 * ref
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k,n0,gamma", [(1, 8, 1e-3), (2, 4, 1.0), (3, 3, 1.0)])
+def test_laplace_manufactured_solution_converges_at_k_plus_1(k, n0, gamma):
+    """p* = cos(pi y) cos(x) cos(2z) (zero mean, homogeneous Neumann at y = +-1). k = 1 needs
+    finer meshes to leave the pre-asymptotic range, so it runs on a uniform mesh."""
+    errs = []
+    for n in (n0, 2 * n0):
+        m = O.Mesh(n, n, n, k, n_layers=0, gamma=gamma)
+        X = m.node_coords()
+        ps = np.cos(math.pi * X[:, 1]) * np.cos(X[:, 0]) * np.cos(2 * X[:, 2])
+        b = m.mass((math.pi ** 2 + 5.0) * ps)
+        p, it, rr = m.solve(b, rtol=1e-12)
+        assert rr <= 1e-11
+        e = p - ps
+        e -= np.sum(m.mass(e)) / m.volume()
+        errs.append(math.sqrt(e @ m.mass(e)))
+    rate = math.log2(errs[0] / errs[1])
+    assert rate >= k + 1 - 0.3, (errs, rate)
+
+
+# ---------------------------------------------------------------------------------------------
+# Velocity divergence (Sec. 4.2)
+# ---------------------------------------------------------------------------------------------
+
+def _std_field(m, fx, fy, fz):
+    X = m.node_coords()
+    n3 = (m.k + 1) ** 3
+    u = np.zeros(m.n_u)
+    std = u[: 3 * m.n_p].reshape(m.nc, 3, n3)
+    for a, f in enumerate((fx, fy, fz)):
+        std[:, a, :] = f(X[:, 0], X[:, 1], X[:, 2]).reshape(m.nc, n3)
+    return u
+
+
+def test_divergence_closed_form_with_wall_flux():
+    """For continuous u: sum_i q_i b_i = -int q div(u); the wall rule {{u}} = u^- matters since
+    u.n != 0 on the walls."""
+    m = O.Mesh(3, 4, 2, 2, n_layers=0)
+    u = _std_field(m, lambda x, y, z: y ** 2, lambda x, y, z: 1 + y ** 2, lambda x, y, z: y + 0 * x)
+    q = m.node_coords()[:, 1] + 1.0
+    val = q @ m.divergence(u)
+    ref = -(2 * math.pi * math.pi) * (4.0 / 3.0)      # -Lx Lz int 2y (y+1) dy
+    assert abs(val - ref) < 1e-12 * abs(ref)
+
+
+def test_divergence_enrichment_volume_term():
+    """u = psi(y+) e_y from enrichment only: with q = y the face terms cancel or vanish (psi(0)=0)
+    and sum_i q_i b_i = int_{wall cells} psi(y+) dV (compare with adaptive quadrature of psi)."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    u = np.zeros(m.n_u)
+    enr = u[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    enr[:, 1, :] = 1.0
+    q = m.node_coords()[:, 1]
+    val = q @ m.divergence(u)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    ref = 2 * (2 * math.pi * math.pi) * quad(lambda s: O.psi_spalding(s * w.u_tau / w.nu)[0], 0.0, dy,
+                                             epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    assert abs(val / ref - 1.0) < 1e-6, (val, ref)
+
+
+# ---------------------------------------------------------------------------------------------
+# Convective term (Sec. 4.2, local Lax-Friedrichs flux)
+# ---------------------------------------------------------------------------------------------
+
+def test_convective_vanishes_for_shear_flow_with_enrichment():
+    """u = (f(y), 0, 0) (standard part) + u_tau psi(y+) e_x (enrichment): div(u x u) = 0, u.n = 0
+    on y-faces, so F^c(v, u) = 0 for every standard and enriched test function."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    u = _std_field(m, lambda x, y, z: 1 - y ** 2, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = w.u_tau
+    y = m.convective(u)
+    assert np.abs(y).max() < 1e-14
+
+
+def test_convective_conservation_equals_wall_flux():
+    """sum over all standard test functions of component d = sum of wall fluxes (interior fluxes
+    cancel). For u = (0, 1 + y^2, 0) the mirrored LF flux on the walls gives 12 (top) + 4 (bottom)."""
+    m = O.Mesh(2, 3, 2, 2, n_layers=0)
+    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: 1 + y ** 2, lambda x, y, z: 0 * y)
+    y = m.convective(u)[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    sums = y.sum(axis=(0, 2))
+    area = 2 * math.pi * math.pi
+    assert abs(sums[1] - 16.0 * area) < 1e-12 * 16 * area
+    assert abs(sums[0]) < 1e-12 and abs(sums[2]) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# Viscous multiscale term, eq. (viscous_multiscale)
+# ---------------------------------------------------------------------------------------------
+
+def test_viscous_bilinear_form_of_smooth_fields_closed_form():
+    """No enrichment, continuous u and v vanishing on the walls: all face terms vanish and
+    -F^nu(v, u) = int 2 nu eps(v):eps(u) = nu Lx Lz int u_x' v_x' dy."""
+    nu = 1e-3
+    m = O.Mesh(2, 3, 2, 3, n_layers=0, nu=nu)
+    u = _std_field(m, lambda x, y, z: 1 - y ** 2, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    v = _std_field(m, lambda x, y, z: (1 - y ** 2) * (1 + y), lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    val = v @ m.viscous(np.zeros(m.n_u), u)
+    ref = nu * 2 * math.pi * math.pi * (8.0 / 3.0)
+    assert abs(val / ref - 1.0) < 1e-12
+
+
+def test_viscous_wall_penalty_on_constant_field():
+    """u = v = e_x: eps = 0, interior jumps 0; the mirror gives [[u]] = 2 e_x on both walls, so
+    -F^nu(v,u) = sum_walls int 10 tau nu * 2 (penalty x10 on Dirichlet faces, Sec. 4.2)."""
+    nu = 1e-3
+    m = O.Mesh(2, 3, 2, 2, n_layers=0, nu=nu)
+    one = lambda x, y, z: 1 + 0 * y
+    zero = lambda x, y, z: 0 * y
+    u = _std_field(m, one, zero, zero)
+    val = u @ m.viscous(np.zeros(m.n_u), u)
+    tau = m.cell_tau().reshape(2, 3, 2)      # [z][y][x]
+    area_cell = (2 * math.pi / 2) * (math.pi / 2)
+    ref = sum(10.0 * tau[:, j, :].sum() * nu * 2.0 * area_cell for j in (0, 2))
+    assert abs(val / ref - 1.0) < 1e-12
+
+
+def test_viscous_symmetric_part_is_volume_plus_penalty_and_psd():
+    """Skew-symmetric consistency/adjoint pairs (Sec. 4.2-4.3): the symmetric part of -F^nu
+    couples neighbouring cells only through penalty terms (standard functions not on the shared
+    face have zero coupling), and it is positive semi-definite with the clipped viscosity."""
+    nu = 1e-4
+    m = O.Mesh(2, 3, 2, 2, n_layers=1, nu=nu, tau_w=1e-2, gamma=1.8)
+    uf = np.zeros(m.n_u)
+    uf[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 0.1
+    uf[3 * m.n_p:] += 0.02 * I.uniform(5, m.n_e * 24, -1, 1)
+    n = m.n_u
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n); e[j] = 1.0
+        A[:, j] = m.viscous(uf, e)
+    S = 0.5 * (A + A.T)
+    ev = np.linalg.eigvalsh(S)
+    assert ev[0] >= -1e-11 * ev[-1]
+    # the clip must actually be active somewhere for this frozen field (nu_t > 3 nu)
+    assert max(m.nut_cell(uf, e).max() for e in range(m.n_e)) > 3 * nu
+    # structural zeros: x-neighbours (0,j,k) and (1,j,k); local nodes with lx = 0 of cell 0 lie on
+    # the face shared through the periodic boundary, lx = 2 on the interior face; lx = 1 is on
+    # neither, so its symmetric coupling to every standard function of cell 1 must vanish.
+    n1, n3 = 3, 27
+    lx = np.arange(n3) % n1
+    for comp in range(3):
+        rows = 0 * 3 * n3 + comp * n3 + np.where(lx == 1)[0]
+        cols = np.arange(1 * 3 * n3, 2 * 3 * n3)
+        assert np.abs(S[np.ix_(rows, cols)]).max() <= 1e-14 * np.abs(S).max()
+    # and the skew part does couple them (the consistency/adjoint terms are present)
+    K = 0.5 * (A - A.T)
+    rows = np.where(lx == 1)[0]
+    assert np.abs(K[np.ix_(rows, np.arange(3 * n3, 6 * n3))]).max() > 1e-6 * np.abs(S).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# Enrichment and eddy viscosity (Sec. 3, Sec. 2.2)
+# ---------------------------------------------------------------------------------------------
+
+def test_enrichment_reproduces_wall_law_profile():
+    """ubar = 0 and u~_B = u_tau e_x: the field in every wall cell is u_tau psi(y+) e_x with
+    y+ = (distance to the wall) u_tau / nu (Sec. 3.1, eq. enrichment)."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = w.u_tau
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    for c in [0, 5, 63, 7 * 8 + 3, 8 * 8 * 3 + 8 * 7 + 2]:
+        ys = X[c, :, 1]
+        for xi in ([0.1, 0.0, 0.7], [0.5, 0.37, 0.2], [0.9, 0.99, 0.4]):
+            r = m.eval_point(u, c, xi)
+            yphys = ys.min() + xi[1] * (ys.max() - ys.min())
+            yp = (1.0 - abs(yphys)) * w.u_tau / w.nu
+            assert abs(r["yplus"] - yp) < 1e-10 * max(yp, 1)
+            assert abs(r["u"][0] - w.u_tau * O.psi_spalding(yp)[0]) < 1e-14
+            assert abs(r["u"][1]) < 1e-300 and abs(r["u"][2]) < 1e-300
+
+
+def test_eddy_viscosity_log_layer_limit():
+    """Mixing length with the enriched log-law profile: in the log layer (y+ ~ 2000, damping ~ 1,
+    y << C_DES h) nu_t -> kappa u_tau y, the textbook Prandtl result."""
+    m = O.Mesh(1, 2, 1, 1, gamma=1e-3, nu=1e-5, tau_w=1.0, n_layers=1)
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 1.0
+    nut = m.nut_cell(u, 0)            # points x fastest, then 8 wall-normal, then z
+    gy, _ = O.gauss(8)
+    nq = 2
+    y0 = gy[0] * 1.0                   # bottom cell spans [-1, 0] (gamma -> 0 is uniform)
+    v = nut.reshape(nq, 8, nq)[0, 0, 0]
+    assert abs(v / (0.41 * y0) - 1.0) < 0.05
+    assert np.all(nut >= 0)
+
+
+def test_oracle_solve_reaches_tolerance_zero_mean():
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(3, 4, 3, 2, n_layers=0, nu=w.nu)
+    b = I.pressure_rhs(m.n_p, 7)
+    p, it, rr = m.solve(b, rtol=1e-12)
+    assert rr <= 1e-12 and abs(p.mean()) < 1e-14 and it > 0
