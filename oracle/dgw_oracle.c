@@ -621,7 +621,7 @@ static void face_points(const omesh *M, int c, int nb, int d, int op, int *t1, i
   int n = inplane_points(M, op);
   int enr = op != OP_LAPLACE && (M->enr[c] >= 0 || (nb >= 0 && M->enr[nb] >= 0));
   *n_t1 = (*t1 == 1 && enr) ? M->P.q_wall + M->P.extra_q : n;
-  *n_t2 = n;
+  *n_t2 = (*t2 == 1 && enr) ? M->P.q_wall + M->P.extra_q : n;
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -221,13 +221,18 @@ def test_divergence_enrichment_volume_term():
 # Convective term (Sec. 4.2, local Lax-Friedrichs flux)
 # ---------------------------------------------------------------------------------------------
 
-def test_convective_vanishes_for_shear_flow_with_enrichment():
-    """u = (f(y), 0, 0) (standard part) + u_tau psi(y+) e_x (enrichment): div(u x u) = 0, u.n = 0
-    on y-faces, so F^c(v, u) = 0 for every standard and enriched test function."""
+@pytest.mark.parametrize("comp", [0, 2])
+def test_convective_vanishes_for_shear_flow_with_enrichment(comp):
+    """u = f(y) e_c (standard part) + u_tau psi(y+) e_c (enrichment), c = x or z: div(u x u) = 0
+    and u.n = 0 on y-faces, so F^c(v, u) = 0 for every standard and enriched test function. The
+    discrete integration by parts along c holds only if the faces normal to c use the same
+    wall-normal rule as the volume (Sec. 4.4)."""
     w = I.WORKLOADS["channel_q2_8x8x8"]
     m = O.Mesh(**w.mesh_kwargs())
-    u = _std_field(m, lambda x, y, z: 1 - y ** 2, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
-    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = w.u_tau
+    f = [lambda x, y, z: 0 * y] * 3
+    f[comp] = lambda x, y, z: 1 - y ** 2
+    u = _std_field(m, *f)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, comp, :] = w.u_tau
     y = m.convective(u)
     assert np.abs(y).max() < 1e-14
 
