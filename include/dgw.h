@@ -1,0 +1,148 @@
+/*
+ * dgw.h -- C ABI of the GB300 (sm_103a) DG wall-model operator library (libdgw.so).
+ *
+ * The library evaluates, matrix-free and by sum factorisation, the spatial DG operators of the
+ * function-enrichment wall model of Krank, Kronbichler & Wall (arXiv 1705.08813) on hexahedral
+ * Q_k cells, and solves the pressure Poisson problem built on them:
+ *   - SIPG pressure Laplacian                 Sec. 4.2, pressure Laplace term, eq. (ipflux)
+ *   - velocity divergence (Poisson rhs)       Sec. 4.2, velocity divergence; eq. (poissonspat)
+ *   - Lax-Friedrichs convective term          Sec. 4.2, convective term
+ *   - multiscale interior-penalty viscous     Sec. 4.2, eq. (viscous_multiscale), (harmweights),
+ *     term with the clipped viscosity         Sec. 4.3, eq. (minvt)
+ *   - eddy viscosity of the enrichment        Sec. 2.2, eq. (mix), (lmix), (ydes)
+ *   - enrichment u~ = psi(y+) sum N_B u~_B     Sec. 3.1 eq. (enrichment), Sec. 3.2 eq. (psi)
+ *
+ * Conventions (all entry points):
+ *   - Vectors are CALLER-OWNED device buffers (e.g. torch tensors). Meshes, metric tables, wall
+ *     tables, multigrid hierarchies and solver workspaces are LIBRARY-OWNED.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Applies are
+ *     asynchronous on it; dgw_mesh_create, dgw_mesh_info and dgw_pressure_solve synchronise it.
+ *   - Every call returns a dgw_status; on error dgw_last_error() returns a thread-local message.
+ *     Errors of asynchronous work surface on a later synchronising call.
+ *   - Nothing falls back to the CPU: without a CUDA device every compute call fails with
+ *     DGW_ECUDA.
+ *
+ * Canonical layouts (ABI level):
+ *   - cells lexicographic: c = i + nx*(j + ny*kz) (x fastest, then y, then z); j = 0 is the
+ *     bottom wall row.
+ *   - pressure p[c][(k+1)^3], local index a + (k+1)*(b + (k+1)*c3) over the Gauss-Lobatto
+ *     nodes (x fastest).
+ *   - velocity: standard part u[c][3][(k+1)^3], followed by the enrichment coefficients
+ *     u~[e][3][8] (Q1 vertex v = vx + 2 vy + 4 vz) of the enriched cells; enriched cells are
+ *     numbered bottom layer(s) first, then top layer(s), lexicographic (x fastest, then z)
+ *     within a layer.
+ *   - prec: DGW_FP64 -> buffers are double*, DGW_FP32 -> float*.
+ */
+#ifndef DGW_H
+#define DGW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgw_mesh *dgw_mesh_t;
+typedef struct dgw_server *dgw_server_t;
+
+typedef enum {
+  DGW_OK = 0,
+  DGW_EINVAL = -1,    /* invalid argument (sizes, degree, null pointers, unsupported option) */
+  DGW_ENOMEM = -2,    /* device or host allocation failed / HBM budget exceeded */
+  DGW_ENOTCONV = -3,  /* solver reached max_iter before rtol */
+  DGW_ETIMEOUT = -4,  /* a bounded wait ran out (serving loop) */
+  DGW_EBUSY = -5,     /* job not finished yet (dgw_poll) */
+  DGW_ECUDA = -6,     /* CUDA runtime error (no device, launch failure, ...) */
+  DGW_EDEVICE = -7    /* a kernel set its device-side error word */
+} dgw_status;
+
+enum { DGW_FP64 = 0, DGW_FP32 = 1 };
+
+/* Mesh and discretisation parameters.
+ * Channel (geometry 0): [0,lx] x [-ly/2, ly/2] x [0,lz], periodic in x and z, no-slip walls at
+ * y = +-ly/2; vertex rows y_j = (ly/2) tanh(gamma (2j/ny - 1)) / tanh(gamma) (Sec. 5.1).
+ * Enriched cells: the n_layers cell rows next to each wall (Sec. 3.1, eq. enrichment).
+ * Wall distance y_B of each Q1 vertex = distance to the closest wall node; tau_w,B = tau_w
+ * (Sec. 3.2). psi: Spalding's law (wall_law 0, kappa 0.41, B 5.17) or van Driest's law
+ * (wall_law 1, eq. psi, evaluated as in Appendix A). */
+typedef struct {
+  int nx, ny, nz;      /* cells per direction (>= 1; ny >= 2*n_layers when enriched) */
+  int degree;          /* k in 1..5 */
+  int enrich_l;        /* 1: trilinear weights N^1 (24 coefficients per cell); 0 not supported */
+  int q_wall;          /* Gauss points in the wall-normal direction of enriched cells (1..10) */
+  int geometry;        /* 0: channel of boxes (1 reserved for the curved bump) */
+  int wall_law;        /* 0 Spalding, 1 van Driest */
+  int n_layers;        /* enriched layers per wall (0 = no enrichment) */
+  double lx, ly, lz;   /* domain lengths */
+  double stretch_gamma;/* tanh grading (> 0) */
+  double nu;           /* kinematic viscosity */
+  double tau_w;        /* wall shear stress (rho = 1) */
+  int precision_mask;  /* bit 0: FP64 tables, bit 1: FP32 tables (for DGW_FP32 applies) */
+} dgw_mesh_params;
+
+/* Build a mesh: geometry, penalty parameters tau_IP (Sec. 4.2: (k+1)^2 A(dK)/V(K), interior
+ * faces weighted 1/2, max over both sides; x10 on walls for the viscous term), wall tables
+ * (y_h, y+, psi, grad psi at every enriched quadrature point, Sec. 3.2 and Appendix A) and the
+ * operator diagonal. Synchronises `stream`. *out receives a library-owned handle. */
+dgw_status dgw_mesh_create(const dgw_mesh_params *params, void *stream, dgw_mesh_t *out);
+dgw_status dgw_mesh_destroy(dgw_mesh_t mesh);
+/* n_p = nc (k+1)^3, n_u = 3 n_p + 24 n_enriched; hbm_bytes = device memory the mesh holds. */
+dgw_status dgw_mesh_info(dgw_mesh_t mesh, long *n_p, long *n_u, long *n_enriched, size_t *hbm_bytes);
+/* Physical positions of the pressure/velocity nodes, host buffer of 3*n_p doubles,
+ * layout [c][(k+1)^3][xyz]. */
+dgw_status dgw_mesh_node_coords(dgw_mesh_t mesh, double *xyz_host);
+
+/* Evaluate nu_t = l_mix^2 |eps(u~)| (Sec. 2.2, eq. mix/lmix/ydes; kappa 0.41, A+ 26,
+ * C_DES 0.85, beta 6, h = dy_e/(k+1)) at every quadrature point of the enriched cells and faces
+ * from the enrichment part of u_dev (FP64, n_u doubles). The values stay frozen for all later
+ * viscous applies until the next call. Before the first call nu_t = 0. */
+dgw_status dgw_update_eddy_viscosity(dgw_mesh_t mesh, const double *u_dev, void *stream);
+
+/* y = -L(q, p) (Sec. 4.2, SIPG Laplace term with the flux of eq. ipflux on interior and
+ * periodic faces; homogeneous Neumann on walls). p, y: n_p values of type `prec`. */
+dgw_status dgw_apply_laplace(dgw_mesh_t mesh, int prec, const void *p, void *y, void *stream);
+
+/* b = -C(q, u) = (grad q, u) - (q, {{u}}.n) with {{u}} = u^- on walls (Sec. 4.2, velocity
+ * divergence; boundary rule below eq. poissonspat). u: n_u doubles, b: n_p doubles. */
+dgw_status dgw_apply_divergence(dgw_mesh_t mesh, const double *u, double *b, void *stream);
+
+/* y = F^c(v, u) = -(grad v, u x u) + (v, F^c*.n), local Lax-Friedrichs flux with
+ * Lambda = max(2|u^-.n|, 2|u^+.n|), mirror state u^+ = -u^- on walls (Sec. 4.2). Over-integrated
+ * with floor(3k/2)+1 Gauss points per direction, q_wall wall-normal points in enriched cells
+ * (Sec. 4.4). u, y: n_u values of type `prec`. */
+dgw_status dgw_apply_convective(dgw_mesh_t mesh, int prec, const void *u, void *y, void *stream);
+
+/* y = -F^nu(vbar, v~; ubar, u~), eq. (viscous_multiscale), with the frozen nu_t of the last
+ * dgw_update_eddy_viscosity, harmonic weights eq. (harmweights), clipped viscosity eq. (minvt),
+ * penalty with nu only, mirror state on walls. u, y: n_u values of type `prec`. */
+dgw_status dgw_apply_viscous(dgw_mesh_t mesh, int prec, const void *u, void *y, void *stream);
+
+typedef struct {
+  double rtol;        /* relative residual ||b - A p||_2 / ||b||_2 target (e.g. 1e-10) */
+  int max_iter;       /* outer CG iteration limit */
+  int mode;           /* 0: FP64 CG + FP64 multigrid, 1: FP64 CG + FP32 multigrid (mixed),
+                         2: FP64 CG + Jacobi */
+  int cheb_degree;    /* Chebyshev smoother degree (e.g. 5) */
+} dgw_solve_opts;
+
+typedef struct {
+  int iterations;
+  double rel_residual; /* true residual of the returned p, recomputed in FP64 */
+  float ms;            /* device time of the solve */
+} dgw_solve_info;
+
+/* Solve -L p = b (Sec. 4.1 eq. poisson, Sec. 4.2 eq. poissonspat) by preconditioned CG on the
+ * zero-mean subspace: b is projected to 1^T b = 0 internally (b itself is not modified), p is
+ * returned with 1^T p = 0. b, p: n_p doubles. Synchronises `stream`. Returns DGW_ENOTCONV (with
+ * p and info filled) when max_iter is reached first. */
+dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const dgw_solve_opts *opts,
+                              dgw_solve_info *info, void *stream);
+
+/* Thread-local description of the last error. */
+const char *dgw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGW_H */

@@ -69,6 +69,7 @@ def _load():
             getattr(lib, name).restype = ctypes.c_int
         lib.dgo_viscous.argtypes = [vp, dp, dp, dp]
         lib.dgo_mass.argtypes = [vp, dp, dp]
+        lib.dgo_set_active.argtypes = [vp, ctypes.c_void_p]
         lib.dgo_solve_cg.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_int, ip, dp]
         lib.dgo_eval_point.argtypes = [vp, dp, ctypes.c_int, dp, dp]
         lib.dgo_nut_cell.argtypes = [vp, dp, ctypes.c_int, dp]
@@ -158,6 +159,16 @@ class Mesh:
         if h:
             self.lib.dgo_mesh_destroy(h)
             self.h = None
+
+    def set_active(self, cells=None) -> None:
+        """Compute only the outputs of the given cells in later operator calls (None: all)."""
+        if cells is None:
+            self.lib.dgo_set_active(self.h, None)
+            return
+        mask = np.zeros(self.nc, dtype=np.uint8)
+        mask[np.asarray(cells, dtype=np.int64)] = 1
+        self._mask = mask
+        self.lib.dgo_set_active(self.h, mask.ctypes.data_as(ctypes.c_void_p))
 
     def node_coords(self) -> np.ndarray:
         out = np.zeros((self.n_p, 3))

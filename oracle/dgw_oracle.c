@@ -75,6 +75,7 @@ typedef struct {
   double *tauv;               /* per enriched cell: 8 vertex wall shear stresses */
   double *dye;                /* per cell wall-normal width */
   double *tau_cell;           /* per cell penalty tau_IP */
+  unsigned char *active;      /* optional: only these cells' outputs are computed (NULL = all) */
 } omesh;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -416,9 +417,21 @@ void *dgo_mesh_create(const dgo_params *P) {
   return M;
 }
 
+/* Restrict the operators to the outputs of the cells with mask[c] != 0 (mask == NULL: all). */
+void dgo_set_active(void *h, const unsigned char *mask) {
+  omesh *M = (omesh *)h;
+  free(M->active);
+  M->active = NULL;
+  if (mask) {
+    M->active = (unsigned char *)malloc(M->nc);
+    memcpy(M->active, mask, M->nc);
+  }
+}
+
 void dgo_mesh_destroy(void *h) {
   omesh *M = (omesh *)h;
   if (!M) return;
+  free(M->active);
   free(M->xv); free(M->yv); free(M->zv); free(M->X); free(M->enr); free(M->enr_cell);
   free(M->ywall); free(M->tauv); free(M->dye); free(M->tau_cell); free(M);
 }
@@ -639,6 +652,7 @@ int dgo_laplace(void *h, const double *p, double *y) {
     double gx[MAXP], gw[MAXP], gx2[MAXP], gw2[MAXP];
 #pragma omp for schedule(dynamic, 4)
     for (int c = 0; c < M->nc; ++c) {
+      if (M->active && !M->active[c]) continue;
       double *yc = y + (size_t)c * n3;
       const double *pc = p + (size_t)c * n3;
       int nq[3];
@@ -764,6 +778,7 @@ int dgo_divergence(void *h, const double *u, double *b) {
     double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP], gx2[MAXP], gw2[MAXP];
 #pragma omp for schedule(dynamic, 4)
     for (int c = 0; c < M->nc; ++c) {
+      if (M->active && !M->active[c]) continue;
       double *bc = b + (size_t)c * n3;
       int nq[3];
       cell_points(M, c, OP_LINEAR, nq);
@@ -829,6 +844,7 @@ int dgo_convective(void *h, const double *u, double *y) {
     double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP], gx2[MAXP], gw2[MAXP];
 #pragma omp for schedule(dynamic, 4)
     for (int c = 0; c < M->nc; ++c) {
+      if (M->active && !M->active[c]) continue;
       int enriched = M->enr[c] >= 0;
       int nq[3];
       cell_points(M, c, OP_CONVECTIVE, nq);
@@ -924,6 +940,7 @@ int dgo_viscous(void *h, const double *u_frz, const double *u, double *y) {
     double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP], gx2[MAXP], gw2[MAXP];
 #pragma omp for schedule(dynamic, 4)
     for (int c = 0; c < M->nc; ++c) {
+      if (M->active && !M->active[c]) continue;
       int enr_c = M->enr[c] >= 0;
       int nq[3];
       cell_points(M, c, OP_LINEAR, nq);

@@ -1,0 +1,365 @@
+// C ABI entry points: mesh construction, operator applies, eddy-viscosity update.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dgw_internal.h"
+
+namespace dgw {
+
+static thread_local std::string g_last_error;
+
+dgw_status set_error(dgw_status s, const std::string &msg) {
+  g_last_error = msg;
+  return s;
+}
+
+dgw_status cuda_check(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return DGW_OK;
+  return set_error(DGW_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename X>
+static X *dalloc(dgw_mesh *M, size_t count, cudaError_t *err) {
+  void *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(X));
+  if (e != cudaSuccess) { *err = e; return nullptr; }
+  M->allocs.push_back(p);
+  M->hbm_bytes += count * sizeof(X);
+  return static_cast<X *>(p);
+}
+
+template <typename X>
+static X *upload(dgw_mesh *M, const X *h, size_t count, cudaStream_t s, cudaError_t *err) {
+  X *d = dalloc<X>(M, count, err);
+  if (!d) return nullptr;
+  if (count) {
+    cudaError_t e = cudaMemcpyAsync(d, h, count * sizeof(X), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+  }
+  return d;
+}
+
+static void free_mesh(dgw_mesh *M);
+
+// Jacobi diagonal of the SIPG Laplacian on the channel of boxes, from the 1-D mass and
+// stiffness diagonals (exact Gauss integration of the tensor-product basis).
+static void laplace_diagonal(const dgw_mesh *M, std::vector<double> &dg) {
+  const int n = M->n1, nx = M->P.nx, ny = M->P.ny, nz = M->P.nz;
+  const Basis<double> &B = M->basis64;
+  const int q = B.q[QSET_LIN];
+  std::vector<double> m1(n, 0.0), k1(n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int t = 0; t < q; ++t) {
+      m1[a] += B.w[QSET_LIN][t] * B.S[QSET_LIN][t * n + a] * B.S[QSET_LIN][t * n + a];
+      k1[a] += B.w[QSET_LIN][t] * B.D[QSET_LIN][t * n + a] * B.D[QSET_LIN][t * n + a];
+    }
+  const double hx = M->P.lx / nx, hz = M->P.lz / nz;
+  dg.assign(M->np, 0.0);
+  for (int kz = 0; kz < nz; ++kz)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int c = i + nx * (j + ny * kz);
+        const double h[3] = {hx, M->hy[j], hz};
+        const double vol = h[0] * h[1] * h[2];
+        for (int i2 = 0; i2 < n; ++i2)
+          for (int i1 = 0; i1 < n; ++i1)
+            for (int i0 = 0; i0 < n; ++i0) {
+              const int id[3] = {i0, i1, i2};
+              double v = vol * (k1[i0] * m1[i1] * m1[i2] / (h[0] * h[0]) + m1[i0] * k1[i1] * m1[i2] / (h[1] * h[1]) +
+                                m1[i0] * m1[i1] * k1[i2] / (h[2] * h[2]));
+              for (int f = 0; f < 6; ++f) {
+                const int d = f >> 1, side = f & 1;
+                int nb;
+                {
+                  int ii = i, jj = j, kk = kz, s = side ? 1 : -1;
+                  if (d == 0) ii = (i + s + nx) % nx;
+                  else if (d == 2) kk = (kz + s + nz) % nz;
+                  else { jj = j + s; if (jj < 0 || jj >= ny) continue; }
+                  nb = ii + nx * (jj + ny * kk);
+                }
+                const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+                const double sgn = side ? 1.0 : -1.0;
+                const double tau = std::max(M->tau[c], M->tau[nb]);
+                const double area = h[t1] * h[t2] * m1[id[t1]] * m1[id[t2]];
+                const int Ls = side ? n - 1 : 0, Lo = side ? 0 : n - 1;
+                const double ps = id[d] == Ls ? 1.0 : 0.0;
+                const double dns = sgn / h[d] * B.dend[side][id[d]];
+                double po = 0.0, dno = 0.0;
+                if (nb == c) {   // a single cell across a periodic direction
+                  po = id[d] == Lo ? 1.0 : 0.0;
+                  dno = sgn / h[d] * B.dend[1 - side][id[d]];
+                }
+                const double jump = ps - po;
+                v -= area * (0.5 * dns * jump + ps * (0.5 * (dns + dno) - tau * jump));
+              }
+              dg[(size_t)c * n * n * n + i0 + n * (i1 + n * i2)] = v;
+            }
+      }
+}
+
+template <typename T>
+static void fill_view(dgw_mesh *M, MeshView<T> &v) {
+  v.nx = M->P.nx; v.ny = M->P.ny; v.nz = M->P.nz;
+  v.n1 = M->n1; v.nc = M->nc; v.ne = M->ne;
+  v.np = M->np; v.nu = M->nu;
+  v.hx = (T)(M->P.lx / M->P.nx);
+  v.hz = (T)(M->P.lz / M->P.nz);
+  v.visc = (T)M->P.nu;
+}
+
+}  // namespace dgw
+
+using namespace dgw;
+
+extern "C" {
+
+const char *dgw_last_error(void) { return g_last_error.c_str(); }
+
+dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *out) {
+  if (!P || !out) return set_error(DGW_EINVAL, "dgw_mesh_create: null argument");
+  *out = nullptr;
+  if (P->degree < 1 || P->degree > 5) return set_error(DGW_EINVAL, "dgw_mesh_create: degree must be in 1..5");
+  if (P->nx < 1 || P->ny < 1 || P->nz < 1) return set_error(DGW_EINVAL, "dgw_mesh_create: cell counts must be >= 1");
+  if (P->geometry != 0) return set_error(DGW_EINVAL, "dgw_mesh_create: only the channel geometry (0) is implemented");
+  if (P->n_layers < 0 || 2 * P->n_layers > P->ny)
+    return set_error(DGW_EINVAL, "dgw_mesh_create: need 0 <= n_layers and 2*n_layers <= ny");
+  if (P->n_layers > 0 && P->enrich_l != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: only enrich_l = 1 is implemented");
+  if (P->q_wall < 1 || P->q_wall > QW_MAX) return set_error(DGW_EINVAL, "dgw_mesh_create: q_wall must be in 1..10");
+  if (!(P->lx > 0 && P->ly > 0 && P->lz > 0 && P->stretch_gamma > 0 && P->nu > 0 && P->tau_w > 0))
+    return set_error(DGW_EINVAL, "dgw_mesh_create: lengths, gamma, nu and tau_w must be positive");
+  if (P->wall_law != 0 && P->wall_law != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: wall_law must be 0 or 1");
+  long long ncl = (long long)P->nx * P->ny * P->nz;
+  if (ncl > (1LL << 26)) return set_error(DGW_EINVAL, "dgw_mesh_create: too many cells");
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+    return set_error(DGW_ECUDA, "dgw_mesh_create: no CUDA device");
+  cudaStream_t s = (cudaStream_t)stream;
+  dgw_mesh *M = new dgw_mesh();
+  M->P = *P;
+  const int k = P->degree, n = k + 1;
+  M->n1 = n;
+  M->nc = (int)ncl;
+  M->np = (long)M->nc * n * n * n;
+  const int nx = P->nx, ny = P->ny, nz = P->nz;
+  // vertex rows of the tanh-graded channel (Sec. 5.1)
+  M->yv.resize(ny + 1);
+  for (int j = 0; j <= ny; ++j)
+    M->yv[j] = 0.5 * P->ly * std::tanh(P->stretch_gamma * (2.0 * j / ny - 1.0)) / std::tanh(P->stretch_gamma);
+  M->hy.resize(ny);
+  for (int j = 0; j < ny; ++j) M->hy[j] = M->yv[j + 1] - M->yv[j];
+  const double hx = P->lx / nx, hz = P->lz / nz;
+  // penalty tau_IP = (k+1)^2 A/V, interior faces weighted 1/2, wall faces 1
+  M->tau.resize(M->nc);
+  for (int kz = 0; kz < nz; ++kz)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const double hy = M->hy[j];
+        const double wb = j == 0 ? 1.0 : 0.5, wt = j == ny - 1 ? 1.0 : 0.5;
+        const double A = hy * hz + hx * hy + hx * hz * (wb + wt);
+        M->tau[i + nx * (j + ny * kz)] = (double)(n * n) * A / (hx * hy * hz);
+      }
+  // enriched cells: bottom rows then top rows, lexicographic (x fastest, then z)
+  M->enr.assign(M->nc, -1);
+  const int L = P->n_layers;
+  int ne = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int j = 0; j < ny; ++j) {
+      const bool rowb = j < L, rowt = j >= ny - L;
+      if (!(pass == 0 ? rowb : (rowt && !rowb))) continue;
+      for (int kz = 0; kz < nz; ++kz)
+        for (int i = 0; i < nx; ++i) M->enr[i + nx * (j + ny * kz)] = ne++;
+    }
+  M->ne = ne;
+  M->nu = 3 * M->np + 24L * ne;
+  M->enr_cell.resize(std::max(ne, 1));
+  for (int c = 0; c < M->nc; ++c)
+    if (M->enr[c] >= 0) M->enr_cell[M->enr[c]] = c;
+  M->ywall.resize(8 * std::max(ne, 1));
+  M->tauv.resize(8 * std::max(ne, 1));
+  M->dye.resize(std::max(ne, 1));
+  for (int e = 0; e < ne; ++e) {
+    const int c = M->enr_cell[e], j = (c / nx) % ny;
+    for (int v = 0; v < 8; ++v) {
+      const double y = M->yv[j + ((v >> 1) & 1)];
+      M->ywall[8 * e + v] = std::min(y - M->yv[0], M->yv[ny] - y);   // closest wall node
+      M->tauv[8 * e + v] = P->tau_w;
+    }
+    M->dye[e] = M->hy[j];
+  }
+  const int qc = (3 * k) / 2 + 1;
+  fill_basis<double>(k, qc, P->q_wall, &M->basis64);
+  fill_basis<float>(k, qc, P->q_wall, &M->basis32);
+  M->has32 = (P->precision_mask & 2) != 0;
+  cudaError_t err = cudaSuccess;
+  fill_view(M, M->v64);
+  fill_view(M, M->v32);
+  for (int sidx = 0; sidx < NQSET; ++sidx) { M->v64.q[sidx] = M->basis64.q[sidx]; M->v32.q[sidx] = M->basis32.q[sidx]; }
+  std::vector<float> hy32(M->hy.begin(), M->hy.end()), tau32(M->tau.begin(), M->tau.end());
+  M->hy_dev64 = upload(M, M->hy.data(), ny, s, &err);
+  M->v64.hy = M->hy_dev64;
+  M->v64.tau = upload(M, M->tau.data(), M->nc, s, &err);
+  M->v64.enr = upload(M, M->enr.data(), M->nc, s, &err);
+  M->v32.enr = M->v64.enr;
+  M->v64.basis = upload(M, &M->basis64, 1, s, &err);
+  if (M->has32) {
+    M->v32.hy = upload(M, hy32.data(), ny, s, &err);
+    M->v32.tau = upload(M, tau32.data(), M->nc, s, &err);
+    M->v32.basis = upload(M, &M->basis32, 1, s, &err);
+  }
+  M->enr_cell_dev = upload(M, M->enr_cell.data(), M->enr_cell.size(), s, &err);
+  M->wall_ywall_dev = upload(M, M->ywall.data(), M->ywall.size(), s, &err);
+  M->wall_tauv_dev = upload(M, M->tauv.data(), M->tauv.size(), s, &err);
+  M->dye_dev = upload(M, M->dye.data(), M->dye.size(), s, &err);
+  const int qw = P->q_wall;
+  for (int cls = 0; cls < 2; ++cls) {
+    const int qi = cls == 0 ? n : qc;
+    const int nvol = qi * qi * qw, fpmax = std::max(qw * qi, qi * qi);
+    M->v64.nvol[cls] = M->v32.nvol[cls] = nvol;
+    M->v64.fpmax[cls] = M->v32.fpmax[cls] = fpmax;
+    M->v64.wt_vol[cls] = dalloc<double>(M, (size_t)ne * nvol * WT, &err);
+    M->v64.wt_face[cls] = dalloc<double>(M, (size_t)ne * 6 * fpmax * WT, &err);
+    if (M->has32) {
+      M->v32.wt_vol[cls] = dalloc<float>(M, (size_t)ne * nvol * WT, &err);
+      M->v32.wt_face[cls] = dalloc<float>(M, (size_t)ne * 6 * fpmax * WT, &err);
+    }
+  }
+  const size_t nv0 = (size_t)ne * M->v64.nvol[0], nf0 = (size_t)ne * 6 * M->v64.fpmax[0];
+  M->aux_vol = dalloc<double>(M, nv0 * 2, &err);
+  M->aux_face = dalloc<double>(M, nf0 * 2, &err);
+  M->v64.nut_vol = dalloc<double>(M, nv0, &err);
+  M->v64.nut_face = dalloc<double>(M, nf0, &err);
+  if (M->has32) {
+    M->v32.nut_vol = dalloc<float>(M, nv0, &err);
+    M->v32.nut_face = dalloc<float>(M, nf0, &err);
+  }
+  if (err != cudaSuccess) {
+    free_mesh(M);
+    return set_error(err == cudaErrorMemoryAllocation ? DGW_ENOMEM : DGW_ECUDA,
+                     std::string("dgw_mesh_create: ") + cudaGetErrorString(err));
+  }
+  // nu_t = 0 until the first update
+  cudaMemsetAsync((void *)M->v64.nut_vol, 0, nv0 * sizeof(double), s);
+  cudaMemsetAsync((void *)M->v64.nut_face, 0, nf0 * sizeof(double), s);
+  if (M->has32) {
+    cudaMemsetAsync((void *)M->v32.nut_vol, 0, nv0 * sizeof(float), s);
+    cudaMemsetAsync((void *)M->v32.nut_face, 0, nf0 * sizeof(float), s);
+  }
+  err = launch_wall_tables(M, s);
+  if (err == cudaSuccess && M->has32)
+    for (int cls = 0; cls < 2 && err == cudaSuccess; ++cls) {
+      err = launch_to_float(M->v64.wt_vol[cls], const_cast<float *>(M->v32.wt_vol[cls]),
+                            (size_t)ne * M->v64.nvol[cls] * WT, s);
+      if (err == cudaSuccess)
+        err = launch_to_float(M->v64.wt_face[cls], const_cast<float *>(M->v32.wt_face[cls]),
+                              (size_t)ne * 6 * M->v64.fpmax[cls] * WT, s);
+    }
+  // Jacobi diagonal
+  std::vector<double> dg;
+  laplace_diagonal(M, dg);
+  std::vector<float> dg32(dg.begin(), dg.end());
+  if (err == cudaSuccess) M->diag64 = upload(M, dg.data(), dg.size(), s, &err);
+  if (err == cudaSuccess) M->diag32 = upload(M, dg32.data(), dg32.size(), s, &err);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) {
+    free_mesh(M);
+    return set_error(err == cudaErrorMemoryAllocation ? DGW_ENOMEM : DGW_ECUDA,
+                     std::string("dgw_mesh_create: ") + cudaGetErrorString(err));
+  }
+  *out = M;
+  return DGW_OK;
+}
+
+dgw_status dgw_mesh_info(dgw_mesh_t M, long *n_p, long *n_u, long *n_enriched, size_t *hbm_bytes) {
+  if (!M) return set_error(DGW_EINVAL, "dgw_mesh_info: null mesh");
+  if (n_p) *n_p = M->np;
+  if (n_u) *n_u = M->nu;
+  if (n_enriched) *n_enriched = M->ne;
+  if (hbm_bytes) *hbm_bytes = M->hbm_bytes;
+  return DGW_OK;
+}
+
+dgw_status dgw_mesh_node_coords(dgw_mesh_t M, double *xyz) {
+  if (!M || !xyz) return set_error(DGW_EINVAL, "dgw_mesh_node_coords: null argument");
+  double z[NMAX], w[NMAX];
+  lobatto_nodes(M->n1, z);
+  (void)w;
+  const int n = M->n1, nx = M->P.nx, ny = M->P.ny, nz = M->P.nz;
+  const double hx = M->P.lx / nx, hz = M->P.lz / nz;
+  for (int kz = 0; kz < nz; ++kz)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t c = i + (size_t)nx * (j + (size_t)ny * kz);
+        for (int c3 = 0; c3 < n; ++c3)
+          for (int b = 0; b < n; ++b)
+            for (int a = 0; a < n; ++a) {
+              double *X = xyz + 3 * (c * n * n * n + a + n * (b + n * c3));
+              X[0] = hx * (i + z[a]);
+              X[1] = M->yv[j] + M->hy[j] * z[b];
+              X[2] = hz * (kz + z[c3]);
+            }
+      }
+  return DGW_OK;
+}
+
+dgw_status dgw_update_eddy_viscosity(dgw_mesh_t M, const double *u, void *stream) {
+  if (!M || !u) return set_error(DGW_EINVAL, "dgw_update_eddy_viscosity: null argument");
+  return cuda_check(launch_eddy_viscosity(M, u, (cudaStream_t)stream), "dgw_update_eddy_viscosity");
+}
+
+dgw_status dgw_apply_laplace(dgw_mesh_t M, int prec, const void *p, void *y, void *stream) {
+  if (!M || !p || !y) return set_error(DGW_EINVAL, "dgw_apply_laplace: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == DGW_FP64)
+    return cuda_check(launch_laplace<double>(M->v64, (const double *)p, (double *)y, s), "dgw_apply_laplace");
+  if (prec == DGW_FP32) {
+    if (!M->has32) return set_error(DGW_EINVAL, "dgw_apply_laplace: mesh built without FP32 tables");
+    return cuda_check(launch_laplace<float>(M->v32, (const float *)p, (float *)y, s), "dgw_apply_laplace");
+  }
+  return set_error(DGW_EINVAL, "dgw_apply_laplace: prec must be DGW_FP64 or DGW_FP32");
+}
+
+static dgw_status apply_vec(dgw_mesh_t M, int op, int prec, const void *u, void *y, void *stream, const char *name) {
+  if (!M || !u || !y) return set_error(DGW_EINVAL, std::string(name) + ": null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == DGW_FP64) return cuda_check(launch_vector_op<double>(op, M->v64, (const double *)u, (double *)y, s), name);
+  if (prec == DGW_FP32) {
+    if (!M->has32) return set_error(DGW_EINVAL, std::string(name) + ": mesh built without FP32 tables");
+    return cuda_check(launch_vector_op<float>(op, M->v32, (const float *)u, (float *)y, s), name);
+  }
+  return set_error(DGW_EINVAL, std::string(name) + ": prec must be DGW_FP64 or DGW_FP32");
+}
+
+dgw_status dgw_apply_divergence(dgw_mesh_t M, const double *u, double *b, void *stream) {
+  return apply_vec(M, OP_DIV, DGW_FP64, u, b, stream, "dgw_apply_divergence");
+}
+
+dgw_status dgw_apply_convective(dgw_mesh_t M, int prec, const void *u, void *y, void *stream) {
+  return apply_vec(M, OP_CONV, prec, u, y, stream, "dgw_apply_convective");
+}
+
+dgw_status dgw_apply_viscous(dgw_mesh_t M, int prec, const void *u, void *y, void *stream) {
+  return apply_vec(M, OP_VISC, prec, u, y, stream, "dgw_apply_viscous");
+}
+
+}  // extern "C"
+
+void dgw_solver_free(dgw_mesh *M);
+
+namespace dgw {
+static void free_mesh(dgw_mesh *M) {
+  if (!M) return;
+  dgw_solver_free(M);
+  for (void *p : M->allocs) cudaFree(p);
+  delete M;
+}
+}  // namespace dgw
+
+extern "C" dgw_status dgw_mesh_destroy(dgw_mesh_t M) {
+  if (!M) return set_error(DGW_EINVAL, "dgw_mesh_destroy: null mesh");
+  dgw::free_mesh(M);
+  return DGW_OK;
+}

@@ -1,0 +1,121 @@
+// Internal data structures of libdgw (host and device). Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/dgw.h"
+
+namespace dgw {
+
+constexpr int NMAX = 6;    // max nodes per direction (k <= 5)
+constexpr int QMAX = 10;   // max quadrature points per direction
+constexpr int QW_MAX = 10; // max wall-normal points in enriched cells
+
+// Quadrature sets: 0 = k+1 Gauss points (linear terms), 1 = floor(3k/2)+1 (convective term),
+// 2 = q_wall points (wall-normal direction of enriched cells), Sec. 4.4.
+enum { QSET_LIN = 0, QSET_CONV = 1, QSET_WALL = 2, NQSET = 3 };
+
+// Gauss-Lobatto nodal basis tabulated at Gauss points, for one degree. S[s][q*n1+j] = l_j(x_q),
+// D[s][q*n1+j] = l_j'(x_q); dend[side][j] = l_j'(side); x, w: Gauss points/weights on [0,1].
+template <typename T>
+struct Basis {
+  int n1;
+  int q[NQSET];
+  T S[NQSET][QMAX * NMAX];
+  T D[NQSET][QMAX * NMAX];
+  T x[NQSET][QMAX];
+  T w[NQSET][QMAX];
+  T dend[2][NMAX];
+  // h-multigrid embedding: P[o][i*n1+j] = l_j((o + xhat_i)/2), child offset o in {0,1}
+  T P[2][NMAX * NMAX];
+};
+
+// Per-point wall-table record of an enriched cell: psi and its physical gradient.
+constexpr int WT = 4;
+
+// Device-side view of a mesh in precision T (geometry of the channel of boxes).
+template <typename T>
+struct MeshView {
+  int nx, ny, nz, n1, nc, ne;
+  int q[NQSET];       // point counts of the quadrature sets (host-visible copy)
+  long np, nu;
+  T hx, hz;
+  const T *hy;        // [ny] row heights
+  const T *tau;       // [nc] penalty tau_IP per cell
+  const int *enr;     // [nc] enriched index or -1
+  T visc;             // kinematic viscosity nu
+  const Basis<T> *basis;
+  // wall tables [qset lin/conv]: volume [ne][nvol][WT], faces [ne][6][fpmax][WT]
+  const T *wt_vol[2];
+  const T *wt_face[2];
+  int nvol[2], fpmax[2];
+  // frozen eddy viscosity (linear quadrature set): [ne][nvol[0]], [ne][6][fpmax[0]]
+  const T *nut_vol;
+  const T *nut_face;
+};
+
+// One multigrid level (a nested coarser channel mesh with the same degree).
+struct Level;
+
+struct MeshHost;
+
+}  // namespace dgw
+
+// Opaque handle behind dgw_mesh_t.
+struct dgw_mesh {
+  dgw_mesh_params P;
+  int n1, nc, ne;
+  long np, nu;
+  size_t hbm_bytes = 0;
+  std::vector<double> yv;       // vertex rows
+  std::vector<double> hy;       // row heights
+  std::vector<double> tau;      // per cell tau_IP
+  std::vector<int> enr;         // cell -> enriched index
+  std::vector<int> enr_cell;    // enriched index -> cell
+  std::vector<double> ywall;    // [ne][8] vertex wall distances
+  std::vector<double> tauv;     // [ne][8] vertex wall shear stresses
+  std::vector<double> dye;      // [ne] wall-normal width
+  dgw::Basis<double> basis64;   // host copies of the basis tables
+  dgw::Basis<float> basis32;
+  // device allocations (owned)
+  std::vector<void *> allocs;
+  dgw::MeshView<double> v64;
+  dgw::MeshView<float> v32;
+  bool has32 = false;
+  double *hy_dev64 = nullptr;
+  int *enr_cell_dev = nullptr;
+  double *wall_ywall_dev = nullptr, *wall_tauv_dev = nullptr;
+  double *aux_vol = nullptr, *aux_face = nullptr;   // (y_h, y+) at linear-set points
+  double *dye_dev = nullptr;
+  double *diag64 = nullptr;     // Jacobi diagonal of the Laplace operator
+  float *diag32 = nullptr;
+  struct dgw_solver *solver = nullptr;   // lazily built solver workspace and multigrid hierarchy
+};
+
+namespace dgw {
+
+// error reporting (thread-local message)
+dgw_status set_error(dgw_status s, const std::string &msg);
+dgw_status cuda_check(cudaError_t e, const char *what);
+
+// host-side 1-D rules (Gauss-Legendre, Gauss-Lobatto, barycentric Lagrange)
+void gauss_rule(int n, double *x, double *w);
+void lobatto_nodes(int n, double *x);
+template <typename T>
+void fill_basis(int k, int q_conv, int q_wall, Basis<T> *b);
+
+// kernels (launched by api.cu)
+template <typename T>
+cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s);
+cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
+cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
+cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
+
+enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2 };
+
+}  // namespace dgw

@@ -1,0 +1,236 @@
+// Pressure Poisson solve: preconditioned CG on -L p = b restricted to zero-mean vectors
+// (Sec. 4.1 eq. poisson, Sec. 4.2 eq. poissonspat; the null space of the pure-Neumann/periodic
+// SIPG operator is the constant vector). Deterministic two-stage reductions; FP64 vectors,
+// residuals and dot products.
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "dgw_internal.h"
+#include "solver.h"
+
+namespace dgw {
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+// Block-level sum for a fixed-order reduction.
+template <typename T>
+__device__ T block_sum(T v) {
+  __shared__ T warp_part[32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_part[w] = v;
+  __syncthreads();
+  T s = T(0);
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? warp_part[threadIdx.x] : T(0);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  }
+  __syncthreads();
+  return s;
+}
+
+// partial[blockIdx] = sum_i a_i b_i (b == nullptr: sum_i a_i)
+__global__ void dot_partial_kernel(const double *__restrict__ a, const double *__restrict__ b, long n,
+                                   double *__restrict__ partial) {
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += b ? a[i] * b[i] : a[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[slot] = sum of partials (one warp, fixed order)
+__global__ void dot_finish_kernel(const double *__restrict__ partial, int np, double *__restrict__ out, int slot) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += 32) s += partial[i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (threadIdx.x == 0) out[slot] = s;
+}
+
+// x = a - mean(a) where the sum of a is sc[slot]
+__global__ void sub_mean_kernel(const double *__restrict__ a, double *__restrict__ x, long n, const double *sc,
+                                int slot) {
+  const double m = sc[slot] / (double)n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) x[i] = a[i] - m;
+}
+
+// p += alpha d; r -= alpha q with alpha = sc[RZ] / sc[DQ]
+__global__ void cg_update_kernel(double *__restrict__ p, double *__restrict__ r, const double *__restrict__ d,
+                                 const double *__restrict__ q, long n, const double *sc) {
+  const double alpha = sc[SC_RZ] / sc[SC_DQ];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    p[i] += alpha * d[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// z = r / diag
+__global__ void jacobi_kernel(const double *__restrict__ r, const double *__restrict__ dg, double *__restrict__ z,
+                              long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    z[i] = r[i] / dg[i];
+}
+
+// d = z + beta d, beta = sc[RZNEW]/sc[RZ]; then sc[RZ] = sc[RZNEW] (one thread after the grid, by
+// a separate launch)
+__global__ void cg_direction_kernel(double *__restrict__ d, const double *__restrict__ z, long n, const double *sc,
+                                    int first) {
+  const double beta = first ? 0.0 : sc[SC_RZNEW] / sc[SC_RZ];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    d[i] = z[i] + beta * d[i];
+}
+
+__global__ void copy_scalar_kernel(double *sc, int dst, int src) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[dst] = sc[src];
+}
+
+__global__ void axpby_kernel(double *__restrict__ y, const double *__restrict__ x, double a, double b, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+static inline int grid_for(long n) {
+  long g = (n + 255) / 256;
+  return (int)std::min<long>(std::max<long>(g, 1), 152 * 16);
+}
+
+cudaError_t reduce_to(const double *a, const double *b, long n, double *partial, double *sc, int slot,
+                      cudaStream_t s) {
+  dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, partial);
+  dot_finish_kernel<<<1, 32, 0, s>>>(partial, RED_BLOCKS, sc, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t project_mean(const double *a, double *x, long n, double *partial, double *sc, int slot, cudaStream_t s) {
+  cudaError_t e = reduce_to(a, nullptr, n, partial, sc, slot, s);
+  if (e != cudaSuccess) return e;
+  sub_mean_kernel<<<grid_for(n), 256, 0, s>>>(a, x, n, sc, slot);
+  return cudaGetLastError();
+}
+
+static dgw_solver *get_solver(dgw_mesh *M) {
+  if (M->solver) return M->solver;
+  dgw_solver *S = new dgw_solver();
+  const long n = M->np;
+  cudaError_t e = cudaSuccess;
+  double **vecs[] = {&S->b, &S->r, &S->z, &S->d, &S->q, &S->partial, &S->sc};
+  const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)RED_BLOCKS, (size_t)SC_COUNT};
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaMalloc(vecs[i], sizes[i] * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->host_sc, SC_COUNT * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
+  if (e != cudaSuccess) {
+    M->solver = S;
+    dgw_solver_free(M);
+    return nullptr;
+  }
+  M->solver = S;
+  return S;
+}
+
+dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_solve_opts *o, dgw_solve_info *info,
+                          cudaStream_t s) {
+  dgw_solver *S = get_solver(M);
+  if (!S) return set_error(DGW_ENOMEM, "dgw_pressure_solve: workspace allocation failed");
+  const long n = M->np;
+  const int G = grid_for(n);
+  cudaError_t e;
+  cudaEventRecord(S->ev0, s);
+  // b <- b - mean(b); ||b||
+  project_mean(b_in, S->b, n, S->partial, S->sc, SC_TMP, s);
+  reduce_to(S->b, S->b, n, S->partial, S->sc, SC_BB, s);
+  cudaMemsetAsync(p, 0, n * sizeof(double), s);
+  cudaMemcpyAsync(S->r, S->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
+  const double bnorm = std::sqrt(S->host_sc[SC_BB]);
+  int it = 0;
+  double rel = 0.0;
+  dgw_status st = DGW_OK;
+  if (bnorm == 0.0) {
+    info->iterations = 0;
+    info->rel_residual = 0.0;
+    info->ms = 0.0f;
+    return DGW_OK;
+  }
+  auto precondition = [&](const double *r, double *z) -> cudaError_t {
+    if (o->mode == 2 || !S->mg_ready) {
+      jacobi_kernel<<<G, 256, 0, s>>>(r, M->diag64, z, n);
+    } else {
+      cudaError_t ee = mg_vcycle(M, S, o->mode, r, z, s);
+      if (ee != cudaSuccess) return ee;
+    }
+    return project_mean(z, z, n, S->partial, S->sc, SC_TMP, s);
+  };
+  if (o->mode != 2) {
+    e = mg_setup(M, S, o->mode, o->cheb_degree > 0 ? o->cheb_degree : 5, s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: multigrid setup");
+  }
+  e = precondition(S->r, S->z);
+  reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
+  cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 1);
+  copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
+  for (it = 1; it <= o->max_iter; ++it) {
+    e = launch_laplace<double>(M->v64, S->d, S->q, s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
+    reduce_to(S->d, S->q, n, S->partial, S->sc, SC_DQ, s);
+    cg_update_kernel<<<G, 256, 0, s>>>(p, S->r, S->d, S->q, n, S->sc);
+    reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RR, s);
+    cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
+    rel = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
+    if (rel <= o->rtol) break;
+    e = precondition(S->r, S->z);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
+    reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
+    cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 0);
+    copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
+  }
+  if (it > o->max_iter) { it = o->max_iter; st = DGW_ENOTCONV; }
+  // p <- p - mean(p); true residual in FP64
+  project_mean(p, p, n, S->partial, S->sc, SC_TMP, s);
+  launch_laplace<double>(M->v64, p, S->q, s);
+  cudaMemcpyAsync(S->r, S->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  axpby_kernel<<<G, 256, 0, s>>>(S->r, S->q, -1.0, 1.0, n);
+  reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RR, s);
+  cudaEventRecord(S->ev1, s);
+  cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+  info->iterations = it;
+  info->rel_residual = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
+  info->ms = ms;
+  if (st == DGW_ENOTCONV) return set_error(DGW_ENOTCONV, "dgw_pressure_solve: max_iter reached");
+  return DGW_OK;
+}
+
+}  // namespace dgw
+
+void dgw_solver_free(dgw_mesh *M) {
+  dgw_solver *S = M ? M->solver : nullptr;
+  if (!S) return;
+  dgw::mg_free(S);
+  cudaFree(S->b); cudaFree(S->r); cudaFree(S->z); cudaFree(S->d); cudaFree(S->q);
+  cudaFree(S->partial); cudaFree(S->sc);
+  if (S->host_sc) cudaFreeHost(S->host_sc);
+  if (S->ev0) cudaEventDestroy(S->ev0);
+  if (S->ev1) cudaEventDestroy(S->ev1);
+  delete S;
+  M->solver = nullptr;
+}
+
+extern "C" dgw_status dgw_pressure_solve(dgw_mesh_t M, const double *b, double *p, const dgw_solve_opts *opts,
+                                         dgw_solve_info *info, void *stream) {
+  if (!M || !b || !p || !opts || !info) return dgw::set_error(DGW_EINVAL, "dgw_pressure_solve: null argument");
+  if (!(opts->rtol > 0) || opts->max_iter < 1 || opts->mode < 0 || opts->mode > 2)
+    return dgw::set_error(DGW_EINVAL, "dgw_pressure_solve: rtol > 0, max_iter >= 1, mode in 0..2 required");
+  if (opts->mode == 1 && !M->has32)
+    return dgw::set_error(DGW_EINVAL, "dgw_pressure_solve: mixed mode needs a mesh with FP32 tables");
+  return dgw::pressure_solve(M, b, p, opts, info, (cudaStream_t)stream);
+}

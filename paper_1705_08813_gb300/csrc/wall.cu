@@ -1,0 +1,256 @@
+// Wall tables and eddy viscosity of the enriched cells.
+//
+// Sec. 3.2: the wall distance y_h and the wall shear stress tau_w,h are interpolated with the
+// linear C0 functions of the cell's vertices; y+ = y_h sqrt(tau_w,h)/nu (rho = 1); the
+// enrichment function psi(y+) is Spalding's law (inverted by safeguarded Newton) or van Driest's
+// law eq. (psi), evaluated as in Appendix A (Table A1 support points plus a 9-point Gauss rule,
+// eq. psinum); grad psi = psi'(y+) grad y+ by the chain rule. The tables hold psi and grad psi at
+// every quadrature point of the enriched cells and of their faces ("computed once ... and
+// stored", Appendix A).
+//
+// Sec. 2.2: nu_t = l_mix^2 |eps(u~)| (eq. mix), l_mix = kappa y_DES (1 - exp(-y+/A+)) (eq. lmix),
+// y_DES = (y^-beta + (C_DES h)^-beta)^(-1/beta) (eq. ydes) with h = dy_e/(k+1).
+#include "sumfac.cuh"
+
+namespace dgw {
+
+namespace {
+constexpr double kKappa = 0.41;
+constexpr double kAplus = 26.0;
+constexpr double kBSpalding = 5.17;
+constexpr double kCdes = 0.85;
+constexpr double kBetaDes = 6.0;
+
+__constant__ double c_vd_y[9] = {0.0, 5.0, 11.0, 24.0, 59.0, 144.0, 361.0, 946.0, 2517.0};
+__constant__ double c_vd_psi[9] = {0.0, 4.88298776233176, 8.91824406645381, 12.3978516813118, 15.1875389926298,
+                                   17.4177125619900, 19.6484300823042, 21.9930107788854, 24.3778307011372};
+__constant__ double c_g9x[9];
+__constant__ double c_g9w[9];
+}  // namespace
+
+__device__ double psi_spalding_dev(double yp, double *dpsi) {
+  if (yp <= 0.0) { *dpsi = 1.0; return 0.0; }
+  const double k = kKappa, eb = exp(-kKappa * kBSpalding);
+  double lo = 0.0, hi = yp;
+  double x = fmin(yp, kBSpalding + log1p(yp) / kKappa);
+  for (int it = 0; it < 200; ++it) {
+    const double kx = k * x;
+    if (kx > 700.0) { hi = x; x = 0.5 * (lo + hi); continue; }
+    const double e = exp(kx);
+    const double g = x + eb * (e - 1.0 - kx - 0.5 * kx * kx - kx * kx * kx / 6.0) - yp;
+    const double gp = 1.0 + eb * k * (e - 1.0 - kx - 0.5 * kx * kx);
+    if (g > 0.0) hi = x; else lo = x;
+    double xn = x - g / gp;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    const bool done = fabs(xn - x) <= 1e-16 * (1.0 + fabs(x));
+    x = xn;
+    if (done) break;
+  }
+  const double kx = k * x;
+  *dpsi = 1.0 / (1.0 + eb * k * (exp(kx) - 1.0 - kx - 0.5 * kx * kx));
+  return x;
+}
+
+__device__ __forceinline__ double vd_integrand(double y) {
+  const double a = 2.0 * kKappa * y * (1.0 - exp(-y / kAplus));
+  return 2.0 / (1.0 + sqrt(1.0 + a * a));
+}
+
+__device__ double psi_vandriest_dev(double yp, double *dpsi) {
+  if (yp <= 0.0) { *dpsi = 1.0; return 0.0; }
+  int i = 0;
+  while (i < 8 && c_vd_y[i + 1] <= yp) ++i;
+  const double a = c_vd_y[i], h = yp - a;
+  double s = 0.0;
+  for (int q = 0; q < 9; ++q) s += c_g9w[q] * vd_integrand(a + h * c_g9x[q]);
+  *dpsi = vd_integrand(yp);
+  return c_vd_psi[i] + h * s;
+}
+
+struct WallCellData {
+  const double *ywall;   // [ne][8]
+  const double *tauv;    // [ne][8]
+  const int *enr_cell;   // [ne]
+  const double *hy;      // [ny]
+  double hx, hz, nu;
+  int nx, ny, wall_law;
+};
+
+// Evaluate psi, grad psi, y_h and y+ at reference point xi of enriched cell e.
+__device__ void wall_point(const WallCellData &w, int e, const double xi[3], double out[WT], double aux[2]) {
+  const int c = w.enr_cell[e];
+  const double h[3] = {w.hx, w.hy[(c / w.nx) % w.ny], w.hz};
+  double N[8], dN[8][3];
+  q1_weights(xi, N, dN);
+  double yh = 0.0, th = 0.0, gy[3] = {0, 0, 0}, gt[3] = {0, 0, 0};
+  for (int v = 0; v < 8; ++v) {
+    const double yv = w.ywall[8 * e + v], tv = w.tauv[8 * e + v];
+    yh += N[v] * yv;
+    th += N[v] * tv;
+    for (int d = 0; d < 3; ++d) {
+      gy[d] += dN[v][d] / h[d] * yv;
+      gt[d] += dN[v][d] / h[d] * tv;
+    }
+  }
+  const double st = sqrt(th);
+  const double yp = yh * st / w.nu;
+  double dpsi;
+  const double psi = w.wall_law == 1 ? psi_vandriest_dev(yp, &dpsi) : psi_spalding_dev(yp, &dpsi);
+  out[0] = psi;
+  for (int d = 0; d < 3; ++d) out[1 + d] = dpsi * (st * gy[d] + yh * gt[d] / (2.0 * st)) / w.nu;
+  aux[0] = yh;
+  aux[1] = yp;
+}
+
+// Reference point of volume point t (x fastest; y uses the wall set) and of face point t.
+__device__ __forceinline__ void vol_xi(const Basis<double> &B, int qs, int t, double xi[3]) {
+  const int q0 = B.q[qs], q1 = B.q[QSET_WALL];
+  const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
+  xi[0] = B.x[qs][i0]; xi[1] = B.x[QSET_WALL][i1]; xi[2] = B.x[qs][i2];
+}
+__device__ __forceinline__ bool face_xi(const Basis<double> &B, int qs, int f, int t, double xi[3]) {
+  const int d = f >> 1, side = f & 1;
+  int t1, t2;
+  face_axes(d, t1, t2);
+  const int s1 = t1 == 1 ? QSET_WALL : qs, s2 = t2 == 1 ? QSET_WALL : qs;
+  const int p1 = B.q[s1], p2 = B.q[s2];
+  if (t >= p1 * p2) return false;
+  xi[d] = side; xi[t1] = B.x[s1][t % p1]; xi[t2] = B.x[s2][t / p1];
+  return true;
+}
+
+__global__ void wall_table_kernel(WallCellData w, const Basis<double> *Bg, int qs, int nvol, int fpmax,
+                                  double *vol, double *face, double *aux_vol, double *aux_face) {
+  const Basis<double> &B = *Bg;
+  const int e = blockIdx.x;
+  for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
+    double xi[3], out[WT], aux[2];
+    vol_xi(B, qs, t, xi);
+    wall_point(w, e, xi, out, aux);
+    for (int r = 0; r < WT; ++r) vol[((size_t)e * nvol + t) * WT + r] = out[r];
+    if (aux_vol) { aux_vol[((size_t)e * nvol + t) * 2] = aux[0]; aux_vol[((size_t)e * nvol + t) * 2 + 1] = aux[1]; }
+  }
+  for (int t = threadIdx.x; t < 6 * fpmax; t += blockDim.x) {
+    const int f = t / fpmax, pt = t % fpmax;
+    double xi[3], out[WT] = {0, 0, 0, 0}, aux[2] = {0, 0};
+    if (face_xi(B, qs, f, pt, xi)) wall_point(w, e, xi, out, aux);
+    for (int r = 0; r < WT; ++r) face[((size_t)e * 6 * fpmax + t) * WT + r] = out[r];
+    if (aux_face) { aux_face[((size_t)e * 6 * fpmax + t) * 2] = aux[0]; aux_face[((size_t)e * 6 * fpmax + t) * 2 + 1] = aux[1]; }
+  }
+}
+
+// nu_t at the linear-set volume and face points of enriched cell e from the enrichment
+// coefficients of u.
+__global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, int nvol, int fpmax, const double *wt_vol,
+                                      const double *wt_face, const double *aux_vol, const double *aux_face,
+                                      const double *dye, int k, const double *u_enr, double *nut_vol, double *nut_face,
+                                      float *nut_vol32, float *nut_face32) {
+  const Basis<double> &B = *Bg;
+  const int e = blockIdx.x;
+  const int c = w.enr_cell[e];
+  const double h[3] = {w.hx, w.hy[(c / w.nx) % w.ny], w.hz};
+  __shared__ double cu[24];
+  for (int t = threadIdx.x; t < 24; t += blockDim.x) cu[t] = u_enr[(size_t)e * 24 + t];
+  __syncthreads();
+  const double hdes = kCdes * dye[e] / (k + 1);
+  auto nut_at = [&](const double xi[3], const double *wt, const double *aux) -> double {
+    double N[8], dN[8][3];
+    q1_weights(xi, N, dN);
+    double G[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int v = 0; v < 8; ++v) s += cu[a * 8 + v] * (wt[0] * dN[v][d] / h[d] + N[v] * wt[1 + d]);
+        G[a][d] = s;
+      }
+    double e2 = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) {
+        const double eps = 0.5 * (G[a][d] + G[d][a]);
+        e2 += eps * eps;
+      }
+    const double yh = aux[0], yp = aux[1];
+    double ydes = 0.0;
+    if (yh > 0.0) ydes = pow(pow(yh, -kBetaDes) + pow(hdes, -kBetaDes), -1.0 / kBetaDes);
+    const double lmix = kKappa * ydes * (1.0 - exp(-yp / kAplus));
+    return lmix * lmix * sqrt(2.0 * e2);
+  };
+  for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
+    double xi[3];
+    vol_xi(B, QSET_LIN, t, xi);
+    const size_t i = (size_t)e * nvol + t;
+    const double v = nut_at(xi, wt_vol + i * WT, aux_vol + i * 2);
+    nut_vol[i] = v;
+    if (nut_vol32) nut_vol32[i] = (float)v;
+  }
+  for (int t = threadIdx.x; t < 6 * fpmax; t += blockDim.x) {
+    const int f = t / fpmax, pt = t % fpmax;
+    double xi[3];
+    const size_t i = (size_t)e * 6 * fpmax + t;
+    double v = 0.0;
+    if (face_xi(B, QSET_LIN, f, pt, xi)) v = nut_at(xi, wt_face + i * WT, aux_face + i * 2);
+    nut_face[i] = v;
+    if (nut_face32) nut_face32[i] = (float)v;
+  }
+}
+
+static WallCellData wall_data(dgw_mesh *M) {
+  WallCellData w;
+  w.ywall = M->wall_ywall_dev;
+  w.tauv = M->wall_tauv_dev;
+  w.enr_cell = M->enr_cell_dev;
+  w.hy = M->hy_dev64;
+  w.hx = M->P.lx / M->P.nx;
+  w.hz = M->P.lz / M->P.nz;
+  w.nu = M->P.nu;
+  w.nx = M->P.nx;
+  w.ny = M->P.ny;
+  w.wall_law = M->P.wall_law;
+  return w;
+}
+
+cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s) {
+  if (M->ne == 0) return cudaSuccess;
+  double gx[9], gw[9];
+  gauss_rule(9, gx, gw);
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_g9x, gx, sizeof(gx), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbolAsync(c_g9w, gw, sizeof(gw), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  WallCellData w = wall_data(M);
+  for (int cls = 0; cls < 2; ++cls) {
+    const int qs = cls == 0 ? QSET_LIN : QSET_CONV;
+    wall_table_kernel<<<M->ne, 128, 0, s>>>(w, M->v64.basis, qs, M->v64.nvol[cls], M->v64.fpmax[cls],
+                                            const_cast<double *>(M->v64.wt_vol[cls]),
+                                            const_cast<double *>(M->v64.wt_face[cls]), cls == 0 ? M->aux_vol : nullptr,
+                                            cls == 0 ? M->aux_face : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s) {
+  if (M->ne == 0) return cudaSuccess;
+  WallCellData w = wall_data(M);
+  eddy_viscosity_kernel<<<M->ne, 128, 0, s>>>(
+      w, M->v64.basis, M->v64.nvol[0], M->v64.fpmax[0], M->v64.wt_vol[0], M->v64.wt_face[0], M->aux_vol, M->aux_face,
+      M->dye_dev, M->P.degree, u + 3 * M->np, const_cast<double *>(M->v64.nut_vol),
+      const_cast<double *>(M->v64.nut_face), M->has32 ? const_cast<float *>(M->v32.nut_vol) : nullptr,
+      M->has32 ? const_cast<float *>(M->v32.nut_face) : nullptr);
+  return cudaGetLastError();
+}
+
+// float copies of the wall tables
+__global__ void to_float_kernel(const double *a, float *b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  to_float_kernel<<<1216, 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dgw

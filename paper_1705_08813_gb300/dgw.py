@@ -1,0 +1,180 @@
+"""Thin ctypes binding of libdgw.so (argument marshalling only; every step runs in the CUDA
+library). Device vectors are torch tensors; their data pointers and the current CUDA stream are
+passed through the C ABI declared in include/dgw.h."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdgw.so")
+
+DGW_FP64 = 0
+DGW_FP32 = 1
+STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -4: "DGW_ETIMEOUT",
+          -5: "DGW_EBUSY", -6: "DGW_ECUDA", -7: "DGW_EDEVICE"}
+
+# every symbol include/dgw.h declares
+EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
+           "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
+           "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error"]
+
+
+class DGWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("degree", ctypes.c_int), ("enrich_l", ctypes.c_int), ("q_wall", ctypes.c_int),
+                ("geometry", ctypes.c_int), ("wall_law", ctypes.c_int), ("n_layers", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("stretch_gamma", ctypes.c_double), ("nu", ctypes.c_double), ("tau_w", ctypes.c_double),
+                ("precision_mask", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdgw.so; raises if the CUDA extension has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdgw.so not found at {path}: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp, lp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)
+    lib.dgw_mesh_create.argtypes = [ctypes.POINTER(MeshParams), vp, ctypes.POINTER(vp)]
+    lib.dgw_mesh_destroy.argtypes = [vp]
+    lib.dgw_mesh_info.argtypes = [vp, lp, lp, lp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.dgw_mesh_node_coords.argtypes = [vp, dp]
+    lib.dgw_update_eddy_viscosity.argtypes = [vp, vp, vp]
+    lib.dgw_apply_laplace.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.dgw_apply_divergence.argtypes = [vp, vp, vp, vp]
+    lib.dgw_apply_convective.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.dgw_apply_viscous.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.dgw_pressure_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.dgw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "dgw_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise DGWError(status, (_lib.dgw_last_error() or b"").decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A device-resident mesh of the channel with its metric and wall tables."""
+
+    def __init__(self, nx, ny, nz, k, *, lx, ly=2.0, lz, gamma=1.8, nu, tau_w, n_layers=1, q_wall=8,
+                 wall_law=0, enrich_l=1, geometry=0, fp32=True, stream=None):
+        lib = load()
+        self.lib = lib
+        self.params = MeshParams(nx, ny, nz, k, enrich_l, q_wall, geometry, wall_law, n_layers,
+                                 lx, ly, lz, gamma, nu, tau_w, 3 if fp32 else 1)
+        h = ctypes.c_void_p()
+        _check(lib.dgw_mesh_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
+        self.h = h
+        a, b, c, d = ctypes.c_long(), ctypes.c_long(), ctypes.c_long(), ctypes.c_size_t()
+        _check(lib.dgw_mesh_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        self.n_p, self.n_u, self.n_e, self.hbm_bytes = a.value, b.value, c.value, d.value
+        self.k = k
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgw_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def node_coords(self):
+        import numpy as np
+        out = np.zeros((self.n_p, 3))
+        _check(self.lib.dgw_mesh_node_coords(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    @staticmethod
+    def _prec(t):
+        import torch
+        return DGW_FP64 if t.dtype == torch.float64 else DGW_FP32
+
+    def update_eddy_viscosity(self, u, stream=None):
+        import torch
+        _check(self.lib.dgw_update_eddy_viscosity(self.h, _ptr(u, torch.float64, self.n_u, "u"), _stream(stream)))
+
+    def laplace(self, p, y, stream=None):
+        _check(self.lib.dgw_apply_laplace(self.h, self._prec(p), _ptr(p, None, self.n_p, "p"),
+                                          _ptr(y, p.dtype, self.n_p, "y"), _stream(stream)))
+        return y
+
+    def divergence(self, u, b, stream=None):
+        import torch
+        _check(self.lib.dgw_apply_divergence(self.h, _ptr(u, torch.float64, self.n_u, "u"),
+                                             _ptr(b, torch.float64, self.n_p, "b"), _stream(stream)))
+        return b
+
+    def convective(self, u, y, stream=None):
+        _check(self.lib.dgw_apply_convective(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
+                                             _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
+        return y
+
+    def viscous(self, u, y, stream=None):
+        _check(self.lib.dgw_apply_viscous(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
+                                          _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
+        return y
+
+    def pressure_solve(self, b, p, rtol=1e-10, max_iter=1000, mode=1, cheb_degree=5, stream=None, check=True):
+        import torch
+        opts = SolveOpts(rtol, max_iter, mode, cheb_degree)
+        info = SolveInfo()
+        st = self.lib.dgw_pressure_solve(self.h, _ptr(b, torch.float64, self.n_p, "b"),
+                                         _ptr(p, torch.float64, self.n_p, "p"), ctypes.byref(opts),
+                                         ctypes.byref(info), _stream(stream))
+        if check:
+            _check(st)
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual, "ms": info.ms, "status": st}
+
+
+def mesh_for(workload, **kw) -> Mesh:
+    """Mesh of a channel workload preset (paper_1705_08813_gb300.inputs.Workload)."""
+    return Mesh(workload.nx, workload.ny, workload.nz, workload.k, lx=workload.lx, ly=workload.ly,
+                lz=workload.lz, gamma=workload.gamma, nu=workload.nu, tau_w=workload.tau_w, **kw)
