@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the DG wall-model hot path on one GB300 (or N replicas under torchrun).
+
+One step = one pass of the whole hot path over the workload: eddy-viscosity update of the
+enriched cells, FP64 applies of the SIPG Laplacian, the velocity divergence, the convective and
+the viscous operator, and one pressure Poisson solve to a 1e-10 relative residual (FP64 CG with
+the FP32 multigrid preconditioner) whose right-hand side is the step's divergence.
+
+value = operator DoF applications of the step (output DoFs of every operator apply, including the
+applies inside the solve) / step time, in GDoF/s. Per-operator GDoF/s and FP64-vs-mixed solves/s
+are reported beside it.
+
+--impl reference times the CPU oracle (the plain FP64 implementation the tests check against) on a
+bounded sample of the same workload: the four operator applies on a subset of cells.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF/s per DG operator apply; pressure solves/s at 1e-10 (FP64 vs mixed)"
+UNIT = "GDoF/s"
+DEFAULT_WORKLOAD = "channel_q4_32x24x24"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(w, target_s=12.0, max_cells=None):
+    """Time the oracle's four operator applies on a bounded sample of the workload's cells.
+    Returns (GDoF/s, seconds, threads, description)."""
+    import numpy as np
+    import oracle as O
+    from paper_1705_08813_gb300 import inputs as I
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    om = O.Mesh(**w.mesh_kwargs())
+    u = I.velocity_field(om.node_coords(), om.n_e, w)
+    p = I.pressure_field(om.n_p, w.seed)
+    n1 = w.k + 1
+    # pick cells spread over the mesh, including wall cells, growing until the time budget is used
+    ncell = 16
+    order = np.random.default_rng(w.seed).permutation(om.nc)
+    elapsed, dofs = 0.0, 0.0
+    while True:
+        cells = order[:ncell]
+        om.set_active(cells)
+        n_enr = int(sum(1 for c in cells if ((c // w.nx) % w.ny) in (0, w.ny - 1)))
+        t0 = time.perf_counter()
+        om.laplace(p)
+        om.divergence(u)
+        om.convective(u)
+        om.viscous(u, u)
+        dt = time.perf_counter() - t0
+        d = len(cells) * n1 ** 3 * (1 + 1 + 3 + 3) + n_enr * 24 * 2
+        elapsed, dofs = dt, d
+        if dt * 2.0 > target_s or ncell >= om.nc or (max_cells and ncell >= max_cells):
+            break
+        ncell = min(om.nc, ncell * 2)
+    om.set_active(None)
+    desc = (f"{len(cells)} of {om.nc} cells ({n_enr} enriched): Laplace, divergence, convective and "
+            f"viscous applies of the oracle on those cells' outputs, {threads} threads")
+    return dofs / elapsed / 1e9, elapsed, threads, desc
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1705_08813_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(w, target_s=2.0, max_cells=64)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s, threads, desc = oracle_sample(w, target_s=args.ref_seconds)
+        vals.append(v)
+        secs.append(s)
+    val = statistics.mean(vals)
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "degree": w.k, "re_tau": w.re_tau},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def laplace_flops_per_cell(k):
+    """FP64 operations of one cell of laplace_kernel (sum-factorised passes, 2 flops per FMA),
+    counted from the pass structure: volume gradients and their transpose, six faces with the
+    own and neighbour trace, normal derivatives and the transposed face integration."""
+    n = q = k + 1
+    fma = 0
+    fma += 2 * q * n * n * n + 3 * q * q * n * n + 3 * q * q * q * n      # eval_cell (3 gradients)
+    fma += 3 * q * q * q * n + 3 * q * q * n * n + 2 * q * n * n * n      # integrate_cell
+    per_face = 2 * (n * n * n + 2 * q * n * n + 2 * q * q * n)             # two traces: normal derivative + 2-D interpolation
+    per_face += 2 * q * q * n + 2 * q * n * n + n * n * n                  # transposed face integration + scatter
+    fma += 6 * per_face
+    return 2 * fma
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1705_08813_gb300 import dgw, inputs as I
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.WORKLOADS[args.workload]
+    dgw.load()
+    m = dgw.mesh_for(w)
+    nodes = m.node_coords()
+    u_host = torch.from_numpy(I.velocity_field(nodes, m.n_e, w)).pin_memory()
+    p_host = torch.from_numpy(I.pressure_field(m.n_p, w.seed)).pin_memory()
+    ud = u_host.to(dev)
+    pd = p_host.to(dev)
+    y_lap = torch.empty(m.n_p, dtype=torch.float64, device=dev)
+    b_div = torch.empty(m.n_p, dtype=torch.float64, device=dev)
+    y_conv = torch.empty(m.n_u, dtype=torch.float64, device=dev)
+    y_visc = torch.empty(m.n_u, dtype=torch.float64, device=dev)
+    p_sol = torch.zeros(m.n_p, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    stream = torch.cuda.current_stream()
+    ops = ["eddy_viscosity", "laplace", "divergence", "convective", "viscous", "solve"]
+    ev = {o: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for o in ops}
+
+    def step(timed):
+        times = {}
+        solve = None
+        for o in ops:
+            if timed:
+                ev[o][0].record(stream)
+            if o == "eddy_viscosity":
+                m.update_eddy_viscosity(ud)
+            elif o == "laplace":
+                m.laplace(pd, y_lap)
+            elif o == "divergence":
+                m.divergence(ud, b_div)
+            elif o == "convective":
+                m.convective(ud, y_conv)
+            elif o == "viscous":
+                m.viscous(ud, y_visc)
+            else:
+                solve = m.pressure_solve(b_div, p_sol, rtol=1e-10, max_iter=500, mode=args.solve_mode)
+            if timed:
+                ev[o][1].record(stream)
+        return solve
+
+    # warm-up (includes multigrid setup)
+    for _ in range(max(args.warmup, 1)):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0, _ = dgw.counters()
+    step_ms, op_ms = [], {o: [] for o in ops}
+    solves = []
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                       # evict the previous step's data from L2 (not timed)
+        s = step(True)
+        torch.cuda.synchronize()
+        for o in ops:
+            op_ms[o].append(ev[o][0].elapsed_time(ev[o][1]))
+        step_ms.append(ev[ops[0]][0].elapsed_time(ev[ops[-1]][1]))
+        solves.append(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches1, _ = dgw.counters()
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    # DoF applications of one step
+    dofs_ops = {"laplace": m.n_p, "divergence": m.n_p, "convective": m.n_u, "viscous": m.n_u}
+    solve_dofs = statistics.mean(s["dof_applies"] for s in solves)
+    dofs_step = sum(dofs_ops.values()) + solve_dofs
+    value = world * dofs_step / (ms_max * 1e-3) / 1e9
+    per_op = {o: {"ms": statistics.mean(op_ms[o])} for o in ops}
+    for o, d in dofs_ops.items():
+        per_op[o]["gdofs"] = d / (per_op[o]["ms"] * 1e-3) / 1e9
+    per_op["solve"]["iterations"] = statistics.mean(s["iterations"] for s in solves)
+    per_op["solve"]["rel_residual"] = max(s["rel_residual"] for s in solves)
+
+    # solves/s: FP64 (FP64 CG + FP64 multigrid) vs mixed (FP64 CG + FP32 multigrid)
+    solve_rates = {}
+    for name, mode in (("fp64", 0), ("mixed", 1)):
+        m.pressure_solve(b_div, p_sol, rtol=1e-10, max_iter=500, mode=mode)   # setup
+        ts, its = [], []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = m.pressure_solve(b_div, p_sol, rtol=1e-10, max_iter=500, mode=mode)
+            ts.append(time.perf_counter() - t0)
+            its.append(info["iterations"])
+        solve_rates[name] = {"solves_per_s": 1.0 / statistics.median(ts), "iterations": statistics.mean(its),
+                             "rel_residual": info["rel_residual"]}
+
+    # dominant kernel roofline: FP64 Laplace apply, timed live with CUDA events
+    peaks, src = _peaks()
+    k = w.k
+    fl_cell = laplace_flops_per_cell(k)
+    lap_ms = per_op["laplace"]["ms"]
+    nc = w.nx * w.ny * w.nz
+    fp64_peak = 152 * 4 * 2.07e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+    achieved_tf = nc * fl_cell / (lap_ms * 1e-3) / 1e12
+    roofline = {"kernel": "laplace_kernel<double>", "bound": "alu", "achieved": achieved_tf,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
+                "traffic": args.traffic_bytes,
+                "peak_source": "derived FP64 rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "hbm": {"achieved_gbs": 16.0 * m.n_p / (lap_ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                        "frac": 16.0 * m.n_p / (lap_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                        "peak_source": src}}
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    out_host = {n: torch.empty(t.numel(), dtype=torch.float64).pin_memory()
+                for n, t in (("lap", y_lap), ("div", b_div), ("conv", y_conv), ("visc", y_visc), ("p", p_sol))}
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ud.copy_(u_host, non_blocking=True)
+        pd.copy_(p_host, non_blocking=True)
+        step(False)
+        for n, t in (("lap", y_lap), ("div", b_div), ("conv", y_conv), ("visc", y_visc), ("p", p_sol)):
+            out_host[n].copy_(t, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d = 8 * (m.n_u + m.n_p)
+    d2h = 8 * (3 * m.n_p + 2 * m.n_u)
+    e2e = {"value": world * dofs_step / (statistics.mean(e2e_ms) * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, threads, desc = oracle_sample(w, target_s=args.ref_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "seconds": secs}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "degree": w.k, "re_tau": w.re_tau,
+                           "n_p": m.n_p, "n_u": m.n_u, "n_enriched": m.n_e, "solve_mode": args.solve_mode,
+                           "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
+                "per_op": per_op, "solves": solve_rates, "dof_applies_per_step": dofs_step,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": int(launches1 - launches0),
+                "wall_s": t_wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dgw", choices=["dgw", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--solve-mode", type=int, default=1)
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -129,6 +129,7 @@ typedef struct {
   int iterations;
   double rel_residual; /* true residual of the returned p, recomputed in FP64 */
   float ms;            /* device time of the solve */
+  double dof_applies;  /* operator DoF applications inside the solve (all levels, both precisions) */
 } dgw_solve_info;
 
 /* Solve -L p = b (Sec. 4.1 eq. poisson, Sec. 4.2 eq. poissonspat) by preconditioned CG on the
@@ -140,6 +141,10 @@ dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const
 
 /* Thread-local description of the last error. */
 const char *dgw_last_error(void);
+
+/* Process-wide counters since the library was loaded: kernels the library launched, and operator
+ * DoF applications (the output DoFs of every operator apply, including those inside solves). */
+void dgw_counters(unsigned long long *kernel_launches, unsigned long long *dof_applies);
 
 #ifdef __cplusplus
 }

@@ -1,5 +1,6 @@
 // C ABI entry points: mesh construction, operator applies, eddy-viscosity update.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -10,6 +11,12 @@
 namespace dgw {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<unsigned long long> g_dofs{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_dofs(long long n) { g_dofs.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long dof_counter() { return g_dofs.load(std::memory_order_relaxed); }
 
 dgw_status set_error(dgw_status s, const std::string &msg) {
   g_last_error = msg;
@@ -45,62 +52,6 @@ static X *upload(dgw_mesh *M, const X *h, size_t count, cudaStream_t s, cudaErro
 
 static void free_mesh(dgw_mesh *M);
 
-// Jacobi diagonal of the SIPG Laplacian on the channel of boxes, from the 1-D mass and
-// stiffness diagonals (exact Gauss integration of the tensor-product basis).
-static void laplace_diagonal(const dgw_mesh *M, std::vector<double> &dg) {
-  const int n = M->n1, nx = M->P.nx, ny = M->P.ny, nz = M->P.nz;
-  const Basis<double> &B = M->basis64;
-  const int q = B.q[QSET_LIN];
-  std::vector<double> m1(n, 0.0), k1(n, 0.0);
-  for (int a = 0; a < n; ++a)
-    for (int t = 0; t < q; ++t) {
-      m1[a] += B.w[QSET_LIN][t] * B.S[QSET_LIN][t * n + a] * B.S[QSET_LIN][t * n + a];
-      k1[a] += B.w[QSET_LIN][t] * B.D[QSET_LIN][t * n + a] * B.D[QSET_LIN][t * n + a];
-    }
-  const double hx = M->P.lx / nx, hz = M->P.lz / nz;
-  dg.assign(M->np, 0.0);
-  for (int kz = 0; kz < nz; ++kz)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        const int c = i + nx * (j + ny * kz);
-        const double h[3] = {hx, M->hy[j], hz};
-        const double vol = h[0] * h[1] * h[2];
-        for (int i2 = 0; i2 < n; ++i2)
-          for (int i1 = 0; i1 < n; ++i1)
-            for (int i0 = 0; i0 < n; ++i0) {
-              const int id[3] = {i0, i1, i2};
-              double v = vol * (k1[i0] * m1[i1] * m1[i2] / (h[0] * h[0]) + m1[i0] * k1[i1] * m1[i2] / (h[1] * h[1]) +
-                                m1[i0] * m1[i1] * k1[i2] / (h[2] * h[2]));
-              for (int f = 0; f < 6; ++f) {
-                const int d = f >> 1, side = f & 1;
-                int nb;
-                {
-                  int ii = i, jj = j, kk = kz, s = side ? 1 : -1;
-                  if (d == 0) ii = (i + s + nx) % nx;
-                  else if (d == 2) kk = (kz + s + nz) % nz;
-                  else { jj = j + s; if (jj < 0 || jj >= ny) continue; }
-                  nb = ii + nx * (jj + ny * kk);
-                }
-                const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-                const double sgn = side ? 1.0 : -1.0;
-                const double tau = std::max(M->tau[c], M->tau[nb]);
-                const double area = h[t1] * h[t2] * m1[id[t1]] * m1[id[t2]];
-                const int Ls = side ? n - 1 : 0, Lo = side ? 0 : n - 1;
-                const double ps = id[d] == Ls ? 1.0 : 0.0;
-                const double dns = sgn / h[d] * B.dend[side][id[d]];
-                double po = 0.0, dno = 0.0;
-                if (nb == c) {   // a single cell across a periodic direction
-                  po = id[d] == Lo ? 1.0 : 0.0;
-                  dno = sgn / h[d] * B.dend[1 - side][id[d]];
-                }
-                const double jump = ps - po;
-                v -= area * (0.5 * dns * jump + ps * (0.5 * (dns + dno) - tau * jump));
-              }
-              dg[(size_t)c * n * n * n + i0 + n * (i1 + n * i2)] = v;
-            }
-      }
-}
-
 template <typename T>
 static void fill_view(dgw_mesh *M, MeshView<T> &v) {
   v.nx = M->P.nx; v.ny = M->P.ny; v.nz = M->P.nz;
@@ -118,6 +69,11 @@ using namespace dgw;
 extern "C" {
 
 const char *dgw_last_error(void) { return g_last_error.c_str(); }
+
+void dgw_counters(unsigned long long *kernel_launches, unsigned long long *dof_applies) {
+  if (kernel_launches) *kernel_launches = g_launches.load(std::memory_order_relaxed);
+  if (dof_applies) *dof_applies = g_dofs.load(std::memory_order_relaxed);
+}
 
 dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *out) {
   if (!P || !out) return set_error(DGW_EINVAL, "dgw_mesh_create: null argument");
@@ -151,17 +107,12 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     M->yv[j] = 0.5 * P->ly * std::tanh(P->stretch_gamma * (2.0 * j / ny - 1.0)) / std::tanh(P->stretch_gamma);
   M->hy.resize(ny);
   for (int j = 0; j < ny; ++j) M->hy[j] = M->yv[j + 1] - M->yv[j];
-  const double hx = P->lx / nx, hz = P->lz / nz;
-  // penalty tau_IP = (k+1)^2 A/V, interior faces weighted 1/2, wall faces 1
-  M->tau.resize(M->nc);
-  for (int kz = 0; kz < nz; ++kz)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        const double hy = M->hy[j];
-        const double wb = j == 0 ? 1.0 : 0.5, wt = j == ny - 1 ? 1.0 : 0.5;
-        const double A = hy * hz + hx * hy + hx * hz * (wb + wt);
-        M->tau[i + nx * (j + ny * kz)] = (double)(n * n) * A / (hx * hy * hz);
-      }
+  // penalty tau_IP = (k+1)^2 A/V per cell, interior faces weighted 1/2, wall faces 1
+  BoxGeometry geo;
+  box_geometry(k, nx, ny, nz, P->lx, P->lz, M->yv, geo);
+  M->tau = geo.tau;
+  const double hx = geo.hx, hz = geo.hz;
+  (void)hx; (void)hz;
   // enriched cells: bottom rows then top rows, lexicographic (x fastest, then z)
   M->enr.assign(M->nc, -1);
   const int L = P->n_layers;
@@ -259,7 +210,7 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     }
   // Jacobi diagonal
   std::vector<double> dg;
-  laplace_diagonal(M, dg);
+  laplace_diagonal(geo, M->basis64, dg);
   std::vector<float> dg32(dg.begin(), dg.end());
   if (err == cudaSuccess) M->diag64 = upload(M, dg.data(), dg.size(), s, &err);
   if (err == cudaSuccess) M->diag32 = upload(M, dg32.data(), dg32.size(), s, &err);

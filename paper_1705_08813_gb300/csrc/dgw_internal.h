@@ -97,6 +97,12 @@ struct dgw_mesh {
 
 namespace dgw {
 
+// process-wide counters: kernel launches and operator DoF applications (output DoFs of every
+// operator apply, including the applies inside solves)
+void note_launch();
+void note_dofs(long long n);
+unsigned long long dof_counter();
+
 // error reporting (thread-local message)
 dgw_status set_error(dgw_status s, const std::string &msg);
 dgw_status cuda_check(cudaError_t e, const char *what);
@@ -106,6 +112,17 @@ void gauss_rule(int n, double *x, double *w);
 void lobatto_nodes(int n, double *x);
 template <typename T>
 void fill_basis(int k, int q_conv, int q_wall, Basis<T> *b);
+
+// Geometry of a channel of boxes: uniform x and z spacing, graded rows in y.
+struct BoxGeometry {
+  int nx, ny, nz, k;
+  double hx, hz;
+  std::vector<double> yv, hy, tau;
+};
+// Row heights and penalty tau_IP = (k+1)^2 A(dK)/V(K) (interior faces weighted 1/2, walls 1).
+void box_geometry(int k, int nx, int ny, int nz, double lx, double lz, const std::vector<double> &yv, BoxGeometry &g);
+// Diagonal of the SIPG Laplacian (Jacobi), from the 1-D mass and stiffness diagonals.
+void laplace_diagonal(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &dg);
 
 // kernels (launched by api.cu)
 template <typename T>

@@ -1,15 +1,512 @@
-// Geometric multigrid preconditioner (built in a later step).
+// Geometric multigrid preconditioner for the pressure Poisson problem (the paper solves it with
+// a matrix-free multigrid-preconditioned CG, Sec. 4.4; its multigrid details are not given, so
+// this design is our own): h-coarsening of the tanh-graded channel by factors of two in every
+// direction whose cell count is even (coarse vertex rows are every other fine row, so the
+// meshes nest), the same degree k on every level, re-discretised SIPG level operators,
+// Chebyshev smoothing with the inverse diagonal, DG embedding (prolongation) and its transpose
+// (restriction), and a fixed number of device-side Jacobi-PCG steps on the coarsest level.
+// Mode 1 runs the whole V-cycle in FP32 (operators, smoothers, transfers) on a residual scaled
+// by its RMS value; mode 0 runs it in FP64.
+#include <cmath>
+#include <vector>
+
 #include "solver.h"
+#include "sumfac.cuh"
 
 namespace dgw {
 
-cudaError_t mg_setup(dgw_mesh *, dgw_solver *S, int, int, cudaStream_t) {
+constexpr double kSmoothRange = 15.0;   // Chebyshev smooths [lmax/15, 1.1 lmax]
+constexpr int kCoarseIters = 24;       // PCG steps on the coarsest level
+constexpr int kPowerIters = 40;        // power iterations for lmax(D^-1 A)
+
+// ------------------------------------------------------------------------------------------
+// vector kernels (templated on the level precision; reductions accumulate in double)
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void mg_dot_partial(const T *__restrict__ a, const T *__restrict__ b, long n, double *__restrict__ partial) {
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += b ? (double)a[i] * (double)b[i] : (double)a[i];
+  __shared__ double wp[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? wp[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void mg_dot_finish(const double *__restrict__ partial, int np, double *out, int slot) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += 32) s += partial[i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (threadIdx.x == 0) out[slot] = s;
+}
+
+constexpr int MG_RED = 152;
+
+template <typename T>
+static void mg_reduce(const T *a, const T *b, long n, double *partial, double *sc, int slot, cudaStream_t s) {
+  note_launch();
+  mg_dot_partial<T><<<MG_RED, 256, 0, s>>>(a, b, n, partial);
+  note_launch();
+  mg_dot_finish<<<1, 32, 0, s>>>(partial, MG_RED, sc, slot);
+}
+
+static inline int mg_grid(long n) {
+  long g = (n + 255) / 256;
+  return (int)std::min<long>(std::max<long>(g, 1), 152 * 8);
+}
+
+// slots of the level scalars
+enum { MS_RZ = 0, MS_RZNEW, MS_DQ, MS_SUM, MS_COUNT = 8 };
+
+// Chebyshev step: r = b - t (t = A x); d = c1 d + c2 D^-1 r; x += d (first: d = c2 D^-1 r)
+template <typename T>
+__global__ void cheb_step(T *__restrict__ x, T *__restrict__ d, const T *__restrict__ b, const T *__restrict__ t,
+                          const T *__restrict__ dinv, long n, T c1, T c2, int first, int zero_x) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const T r = zero_x ? b[i] : b[i] - t[i];
+    const T dn = (first ? T(0) : c1 * d[i]) + c2 * dinv[i] * r;
+    d[i] = dn;
+    x[i] = (zero_x ? T(0) : x[i]) + dn;
+  }
+}
+
+template <typename T>
+__global__ void residual_kernel(T *__restrict__ r, const T *__restrict__ b, const T *__restrict__ t, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) r[i] = b[i] - t[i];
+}
+
+// coarse PCG pieces (scalars on the device)
+template <typename T>
+__global__ void cpcg_update(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ d, const T *__restrict__ t,
+                            long n, const double *sc) {
+  const double alpha = sc[MS_DQ] != 0.0 ? sc[MS_RZ] / sc[MS_DQ] : 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] = (T)((double)x[i] + alpha * (double)d[i]);
+    r[i] = (T)((double)r[i] - alpha * (double)t[i]);
+  }
+}
+
+template <typename T>
+__global__ void cpcg_precond(T *__restrict__ z, const T *__restrict__ r, const T *__restrict__ dinv, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) z[i] = dinv[i] * r[i];
+}
+
+template <typename T>
+__global__ void sub_mean_T(T *__restrict__ z, long n, const double *sc, int slot) {
+  const double m = sc[slot] / (double)n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    z[i] = (T)((double)z[i] - m);
+}
+
+template <typename T>
+__global__ void cpcg_direction(T *__restrict__ d, const T *__restrict__ z, long n, double *sc, int first) {
+  const double beta = (first || sc[MS_RZ] == 0.0) ? 0.0 : sc[MS_RZNEW] / sc[MS_RZ];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    d[i] = (T)((double)z[i] + beta * (double)d[i]);
+}
+
+__global__ void shift_scalar(double *sc, int dst, int src) {
+  if (threadIdx.x == 0) sc[dst] = sc[src];
+}
+
+// FP64 residual -> level-0 right-hand side scaled by 1/rms(r); rms from the CG scalar RR.
+template <typename T>
+__global__ void scale_in(T *__restrict__ b0, const double *__restrict__ r, long n, const double *csc, int rr_slot) {
+  const double rr = csc[rr_slot];
+  const double s = rr > 0.0 ? sqrt((double)n / rr) : 1.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    b0[i] = (T)(r[i] * s);
+}
+template <typename T>
+__global__ void scale_out(double *__restrict__ z, const T *__restrict__ x0, long n, const double *csc, int rr_slot) {
+  const double rr = csc[rr_slot];
+  const double s = rr > 0.0 ? sqrt(rr / (double)n) : 1.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    z[i] = (double)x0[i] * s;
+}
+
+template <typename T>
+__global__ void inv_kernel(const double *__restrict__ dg, T *__restrict__ dinv, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    dinv[i] = (T)(1.0 / dg[i]);
+}
+
+template <typename T>
+__global__ void scale_vec(T *__restrict__ y, const T *__restrict__ x, long n, const double *sc, int slot) {
+  const double nrm = sqrt(sc[slot]);
+  const double s = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] = (T)((double)x[i] * s);
+}
+
+template <typename T>
+__global__ void mul_kernel(T *__restrict__ y, const T *__restrict__ a, const T *__restrict__ b, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] = a[i] * b[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// transfers: DG embedding of a coarse cell's polynomial into its children and the transpose
+// ------------------------------------------------------------------------------------------
+
+struct XferDims {
+  int fnx, fny, fnz;   // fine cells
+  int cnx, cny, cnz;   // coarse cells
+  int cf[3];           // factors (1 or 2)
+};
+
+template <typename T>
+__global__ void prolongate_add(const Basis<T> *Bg, XferDims X, const T *__restrict__ xc, T *__restrict__ xf) {
+  __shared__ T Pm[3][NMAX * NMAX];
+  __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX];
+  const Basis<T> &B = *Bg;
+  const int n = B.n1, n3 = n * n * n;
+  const int fc = blockIdx.x;
+  const int fi = fc % X.fnx, fj = (fc / X.fnx) % X.fny, fk = fc / (X.fnx * X.fny);
+  const int fidx[3] = {fi, fj, fk};
+  const int ci = fi / X.cf[0], cj = fj / X.cf[1], ck = fk / X.cf[2];
+  const int cc = ci + X.cnx * (cj + X.cny * ck);
+  for (int d = 0; d < 3; ++d)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, j = t % n;
+      Pm[d][t] = X.cf[d] == 2 ? B.P[fidx[d] & 1][t] : (i == j ? T(1) : T(0));
+    }
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = xc[(size_t)cc * n3 + t];
+  __syncthreads();
+  axis_pass(A, Bv, n, n, n, 0, Pm[0], n, n, false, false);
+  __syncthreads();
+  axis_pass(Bv, A, n, n, n, 1, Pm[1], n, n, false, false);
+  __syncthreads();
+  axis_pass(A, Bv, n, n, n, 2, Pm[2], n, n, false, false);
+  __syncthreads();
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) xf[(size_t)fc * n3 + t] += Bv[t];
+}
+
+template <typename T>
+__global__ void restrict_kernel(const Basis<T> *Bg, XferDims X, const T *__restrict__ rf, T *__restrict__ rc) {
+  __shared__ T Pm[2][3][NMAX * NMAX];
+  __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX], Acc[NMAX * NMAX * NMAX];
+  const Basis<T> &B = *Bg;
+  const int n = B.n1, n3 = n * n * n;
+  const int cc = blockIdx.x;
+  const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
+  for (int o = 0; o < 2; ++o)
+    for (int d = 0; d < 3; ++d)
+      for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int i = t / n, j = t % n;
+        Pm[o][d][t] = X.cf[d] == 2 ? B.P[o][t] : (i == j ? T(1) : T(0));
+      }
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) Acc[t] = T(0);
+  __syncthreads();
+  for (int oz = 0; oz < X.cf[2]; ++oz)
+    for (int oy = 0; oy < X.cf[1]; ++oy)
+      for (int ox = 0; ox < X.cf[0]; ++ox) {
+        const int fi = ci * X.cf[0] + ox, fj = cj * X.cf[1] + oy, fk = ck * X.cf[2] + oz;
+        const int fc = fi + X.fnx * (fj + X.fny * fk);
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = rf[(size_t)fc * n3 + t];
+        __syncthreads();
+        axis_pass(A, Bv, n, n, n, 0, Pm[ox][0], n, n, true, false);
+        __syncthreads();
+        axis_pass(Bv, A, n, n, n, 1, Pm[oy][1], n, n, true, false);
+        __syncthreads();
+        axis_pass(A, Bv, n, n, n, 2, Pm[oz][2], n, n, true, false);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) Acc[t] += Bv[t];
+        __syncthreads();
+      }
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) rc[(size_t)cc * n3 + t] = Acc[t];
+}
+
+// ------------------------------------------------------------------------------------------
+// hierarchy
+// ------------------------------------------------------------------------------------------
+
+template <typename T>
+struct Lvl {
+  BoxGeometry geo;
+  MeshView<T> view;
+  long n = 0;
+  T *dinv = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *z = nullptr;
+  double *sc = nullptr, *partial = nullptr;
+  double lmax = 1.0;
+  XferDims to_coarse{};   // transfer to the next coarser level
+  std::vector<void *> allocs;
+};
+
+template <typename T>
+struct Hierarchy {
+  std::vector<Lvl<T> *> L;
+  int cheb = 5;
+  const Basis<T> *basis = nullptr;
+};
+
+}  // namespace dgw
+
+struct dgw::MGLevel {
+  int prec = -1;   // 0 double, 1 float
+  void *h = nullptr;
+};
+
+namespace dgw {
+
+template <typename T>
+static T *lalloc(Lvl<T> *L, size_t n, cudaError_t &e) {
+  void *p = nullptr;
+  if (e != cudaSuccess) return nullptr;
+  e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+  if (e == cudaSuccess) L->allocs.push_back(p);
+  return (T *)p;
+}
+
+template <typename T>
+static void free_hier(Hierarchy<T> *H) {
+  if (!H) return;
+  for (auto *L : H->L) {
+    for (void *p : L->allocs) cudaFree(p);
+    delete L;
+  }
+  delete H;
+}
+
+template <typename T>
+static cudaError_t level_apply(const Lvl<T> *L, const T *x, T *y, cudaStream_t s) {
+  return launch_laplace<T>(L->view, x, y, s);
+}
+
+// lmax of D^-1 A by power iteration (setup only; host-synchronising)
+template <typename T>
+static cudaError_t estimate_lmax(Lvl<T> *L, cudaStream_t s) {
+  const long n = L->n;
+  std::vector<T> h(n);
+  uint64_t st = 0x243F6A8885A308D3ull;
+  for (long i = 0; i < n; ++i) {
+    st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+    h[i] = (T)((double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+  }
+  cudaError_t e = cudaMemcpyAsync(L->x, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, s);
+  double lam = 1.0, host[MS_COUNT];
+  for (int it = 0; it < kPowerIters && e == cudaSuccess; ++it) {
+    mg_reduce<T>(L->x, L->x, n, L->partial, L->sc, MS_SUM, s);
+    note_launch();
+    scale_vec<T><<<mg_grid(n), 256, 0, s>>>(L->x, L->x, n, L->sc, MS_SUM);
+    e = level_apply(L, L->x, L->t, s);
+    note_launch();
+    mul_kernel<T><<<mg_grid(n), 256, 0, s>>>(L->t, L->t, L->dinv, n);
+    mg_reduce<T>(L->x, L->t, n, L->partial, L->sc, MS_DQ, s);   // Rayleigh-like estimate x.(D^-1 A x)
+    mg_reduce<T>(L->t, L->t, n, L->partial, L->sc, MS_RZ, s);
+    cudaMemcpyAsync(L->x, L->t, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, L->sc, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    lam = std::sqrt(host[MS_RZ]);   // ||D^-1 A x|| with ||x|| = 1
+    L->lmax = lam > 0 ? lam : 1.0;
+  }
+  return e;
+}
+
+template <typename T>
+static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<T> &fine, const T *fine_basis_dev,
+                                   cudaStream_t s) {
+  (void)fine_basis_dev;
+  cudaError_t e = cudaSuccess;
+  const int k = M->P.degree, n = k + 1, n3 = n * n * n;
+  int nx = M->P.nx, ny = M->P.ny, nz = M->P.nz;
+  std::vector<double> yv = M->yv;
+  for (int lev = 0; e == cudaSuccess; ++lev) {
+    Lvl<T> *L = new Lvl<T>();
+    H->L.push_back(L);
+    box_geometry(k, nx, ny, nz, M->P.lx, M->P.lz, yv, L->geo);
+    L->n = (long)nx * ny * nz * n3;
+    if (lev == 0) {
+      L->view = fine;
+    } else {
+      L->view = fine;
+      L->view.nx = nx; L->view.ny = ny; L->view.nz = nz;
+      L->view.nc = nx * ny * nz;
+      L->view.ne = 0;
+      L->view.np = L->n;
+      L->view.hx = (T)L->geo.hx;
+      L->view.hz = (T)L->geo.hz;
+      std::vector<T> hy(L->geo.hy.begin(), L->geo.hy.end()), tau(L->geo.tau.begin(), L->geo.tau.end());
+      T *hyd = lalloc<T>(L, hy.size(), e), *taud = lalloc<T>(L, tau.size(), e);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hyd, hy.data(), hy.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(taud, tau.data(), tau.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+      L->view.hy = hyd;
+      L->view.tau = taud;
+      L->view.enr = nullptr;
+    }
+    std::vector<double> dg;
+    laplace_diagonal(L->geo, M->basis64, dg);
+    double *dg_dev = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&dg_dev, dg.size() * sizeof(double));
+    L->dinv = lalloc<T>(L, L->n, e);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dg_dev, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) { note_launch(); inv_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(dg_dev, L->dinv, L->n); }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (dg_dev) cudaFree(dg_dev);
+    L->x = lalloc<T>(L, L->n, e); L->b = lalloc<T>(L, L->n, e); L->r = lalloc<T>(L, L->n, e);
+    L->d = lalloc<T>(L, L->n, e); L->t = lalloc<T>(L, L->n, e); L->z = lalloc<T>(L, L->n, e);
+    void *p = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
+    if (e == cudaSuccess) { L->allocs.push_back(p); L->sc = (double *)p; }
+    if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
+    if (e == cudaSuccess) { L->allocs.push_back(p); L->partial = (double *)p; }
+    if (e == cudaSuccess) e = estimate_lmax(L, s);
+    // next coarser level: halve every even direction
+    int cf[3] = {nx % 2 == 0 ? 2 : 1, ny % 2 == 0 ? 2 : 1, nz % 2 == 0 ? 2 : 1};
+    const long cells = (long)nx * ny * nz;
+    if (cells <= 64 || (cf[0] == 1 && cf[1] == 1 && cf[2] == 1) || lev >= 12) break;
+    XferDims X;
+    X.fnx = nx; X.fny = ny; X.fnz = nz;
+    X.cf[0] = cf[0]; X.cf[1] = cf[1]; X.cf[2] = cf[2];
+    nx /= cf[0]; ny /= cf[1]; nz /= cf[2];
+    X.cnx = nx; X.cny = ny; X.cnz = nz;
+    L->to_coarse = X;
+    if (cf[1] == 2) {
+      std::vector<double> yc(ny + 1);
+      for (int j = 0; j <= ny; ++j) yc[j] = yv[2 * j];
+      yv.swap(yc);
+    }
+  }
+  return e;
+}
+
+template <typename T>
+static void chebyshev(const Hierarchy<T> *H, Lvl<T> *L, bool zero_init, cudaStream_t s) {
+  const double lmax = 1.1 * L->lmax, lmin = lmax / kSmoothRange;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const int G = mg_grid(L->n);
+  // first step
+  if (!zero_init) launch_laplace<T>(L->view, L->x, L->t, s);
+  note_launch();
+  cheb_step<T><<<G, 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, T(0), (T)(1.0 / theta), 1, zero_init ? 1 : 0);
+  for (int k = 1; k < H->cheb; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    launch_laplace<T>(L->view, L->x, L->t, s);
+    note_launch();
+    cheb_step<T><<<G, 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), 0, 0);
+    rho = rho_new;
+  }
+}
+
+template <typename T>
+static void coarse_solve(Lvl<T> *L, cudaStream_t s) {
+  const long n = L->n;
+  const int G = mg_grid(n);
+  cudaMemsetAsync(L->x, 0, n * sizeof(T), s);
+  cudaMemcpyAsync(L->r, L->b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  for (int it = 0; it < kCoarseIters; ++it) {
+    note_launch();
+    cpcg_precond<T><<<G, 256, 0, s>>>(L->z, L->r, L->dinv, n);
+    mg_reduce<T>(L->z, nullptr, n, L->partial, L->sc, MS_SUM, s);
+    note_launch();
+    sub_mean_T<T><<<G, 256, 0, s>>>(L->z, n, L->sc, MS_SUM);
+    mg_reduce<T>(L->r, L->z, n, L->partial, L->sc, MS_RZNEW, s);
+    note_launch();
+    cpcg_direction<T><<<G, 256, 0, s>>>(L->d, L->z, n, L->sc, it == 0);
+    note_launch();
+    shift_scalar<<<1, 32, 0, s>>>(L->sc, MS_RZ, MS_RZNEW);
+    launch_laplace<T>(L->view, L->d, L->t, s);
+    mg_reduce<T>(L->d, L->t, n, L->partial, L->sc, MS_DQ, s);
+    note_launch();
+    cpcg_update<T><<<G, 256, 0, s>>>(L->x, L->r, L->d, L->t, n, L->sc);
+  }
+}
+
+template <typename T>
+static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
+  Lvl<T> *L = H->L[lev];
+  if (lev + 1 == H->L.size()) {
+    coarse_solve(L, s);
+    return;
+  }
+  Lvl<T> *C = H->L[lev + 1];
+  chebyshev(H, L, true, s);
+  launch_laplace<T>(L->view, L->x, L->t, s);
+  note_launch();
+  residual_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(L->r, L->b, L->t, L->n);
+  note_launch();
+  restrict_kernel<T><<<C->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, L->r, C->b);
+  vcycle(H, lev + 1, s);
+  note_launch();
+  prolongate_add<T><<<L->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, C->x, L->x);
+  chebyshev(H, L, false, s);
+}
+
+cudaError_t mg_setup(dgw_mesh *M, dgw_solver *S, int mode, int cheb, cudaStream_t s) {
+  if (S->mg_ready && S->mg_mode == mode && S->mg_cheb == cheb) return cudaSuccess;
+  mg_free(S);
+  MGLevel *ml = new MGLevel();
+  cudaError_t e;
+  if (mode == 1) {
+    auto *H = new Hierarchy<float>();
+    H->cheb = cheb;
+    H->basis = M->v32.basis;
+    ml->prec = 1;
+    ml->h = H;
+    e = build_hierarchy<float>(M, H, M->v32, nullptr, s);
+  } else {
+    auto *H = new Hierarchy<double>();
+    H->cheb = cheb;
+    H->basis = M->v64.basis;
+    ml->prec = 0;
+    ml->h = H;
+    e = build_hierarchy<double>(M, H, M->v64, nullptr, s);
+  }
+  S->levels.push_back(ml);
+  if (e != cudaSuccess) { mg_free(S); return e; }
+  S->mg_ready = true;
+  S->mg_mode = mode;
+  S->mg_cheb = cheb;
+  return cudaSuccess;
+}
+
+cudaError_t mg_vcycle(dgw_mesh *M, dgw_solver *S, int mode, const double *r, double *z, cudaStream_t s) {
+  (void)mode;
+  MGLevel *ml = S->levels.empty() ? nullptr : S->levels[0];
+  if (!ml) return cudaErrorNotReady;
+  const long n = M->np;
+  const int G = mg_grid(n);
+  if (ml->prec == 1) {
+    auto *H = (Hierarchy<float> *)ml->h;
+    note_launch();
+    scale_in<float><<<G, 256, 0, s>>>(H->L[0]->b, r, n, S->sc, SC_RR);
+    vcycle(H, 0, s);
+    note_launch();
+    scale_out<float><<<G, 256, 0, s>>>(z, H->L[0]->x, n, S->sc, SC_RR);
+  } else {
+    auto *H = (Hierarchy<double> *)ml->h;
+    note_launch();
+    scale_in<double><<<G, 256, 0, s>>>(H->L[0]->b, r, n, S->sc, SC_RR);
+    vcycle(H, 0, s);
+    note_launch();
+    scale_out<double><<<G, 256, 0, s>>>(z, H->L[0]->x, n, S->sc, SC_RR);
+  }
+  return cudaGetLastError();
+}
+
+int mg_levels(dgw_solver *S) {
+  if (S->levels.empty()) return 0;
+  MGLevel *ml = S->levels[0];
+  return ml->prec == 1 ? (int)((Hierarchy<float> *)ml->h)->L.size() : (int)((Hierarchy<double> *)ml->h)->L.size();
+}
+
+void mg_free(dgw_solver *S) {
+  for (MGLevel *ml : S->levels) {
+    if (ml->prec == 1) free_hier((Hierarchy<float> *)ml->h);
+    else if (ml->prec == 0) free_hier((Hierarchy<double> *)ml->h);
+    delete ml;
+  }
+  S->levels.clear();
   S->mg_ready = false;
-  return cudaErrorNotSupported;
+  S->mg_mode = -1;
 }
-cudaError_t mg_vcycle(dgw_mesh *, dgw_solver *, int, const double *, double *, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-void mg_free(dgw_solver *S) { S->levels.clear(); S->mg_ready = false; }
 
 }  // namespace dgw

@@ -138,6 +138,8 @@ cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t 
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  note_launch();
+  note_dofs(m.np);
   laplace_kernel<T><<<m.nc, 128, sm, s>>>(m, p, y);
   return cudaGetLastError();
 }
@@ -582,6 +584,8 @@ static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  note_launch();
+  note_dofs(OP == OP_DIV ? m.np : m.nu);
   vector_op_kernel<T, OP><<<m.nc, 128, sm, s>>>(m, u, y);
   return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 // (Sec. 4.1 eq. poisson, Sec. 4.2 eq. poissonspat; the null space of the pure-Neumann/periodic
 // SIPG operator is the constant vector). Deterministic two-stage reductions; FP64 vectors,
 // residuals and dot products.
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -73,11 +74,13 @@ __global__ void jacobi_kernel(const double *__restrict__ r, const double *__rest
     z[i] = r[i] / dg[i];
 }
 
-// d = z + beta d, beta = sc[RZNEW]/sc[RZ]; then sc[RZ] = sc[RZNEW] (one thread after the grid, by
-// a separate launch)
+// d = z + beta d with the flexible (Polak-Ribiere) beta = (r.z - r.z_old) / rz_old, which
+// equals the standard beta for a fixed linear preconditioner and stays robust when the
+// preconditioner varies slightly between iterations (FP32 multigrid, inner coarse PCG).
+// sc[RZ] = sc[RZNEW] is shifted by a separate launch.
 __global__ void cg_direction_kernel(double *__restrict__ d, const double *__restrict__ z, long n, const double *sc,
                                     int first) {
-  const double beta = first ? 0.0 : sc[SC_RZNEW] / sc[SC_RZ];
+  const double beta = first ? 0.0 : (sc[SC_RZNEW] - sc[SC_RZOLD]) / sc[SC_RZ];
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     d[i] = z[i] + beta * d[i];
 }
@@ -98,7 +101,9 @@ static inline int grid_for(long n) {
 
 cudaError_t reduce_to(const double *a, const double *b, long n, double *partial, double *sc, int slot,
                       cudaStream_t s) {
+  note_launch();
   dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, partial);
+  note_launch();
   dot_finish_kernel<<<1, 32, 0, s>>>(partial, RED_BLOCKS, sc, slot);
   return cudaGetLastError();
 }
@@ -106,6 +111,7 @@ cudaError_t reduce_to(const double *a, const double *b, long n, double *partial,
 cudaError_t project_mean(const double *a, double *x, long n, double *partial, double *sc, int slot, cudaStream_t s) {
   cudaError_t e = reduce_to(a, nullptr, n, partial, sc, slot, s);
   if (e != cudaSuccess) return e;
+  note_launch();
   sub_mean_kernel<<<grid_for(n), 256, 0, s>>>(a, x, n, sc, slot);
   return cudaGetLastError();
 }
@@ -115,9 +121,10 @@ static dgw_solver *get_solver(dgw_mesh *M) {
   dgw_solver *S = new dgw_solver();
   const long n = M->np;
   cudaError_t e = cudaSuccess;
-  double **vecs[] = {&S->b, &S->r, &S->z, &S->d, &S->q, &S->partial, &S->sc};
-  const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)RED_BLOCKS, (size_t)SC_COUNT};
-  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaMalloc(vecs[i], sizes[i] * sizeof(double));
+  double **vecs[] = {&S->b, &S->r, &S->z, &S->d, &S->q, &S->zold, &S->partial, &S->sc};
+  const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)RED_BLOCKS,
+                          (size_t)SC_COUNT};
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaMalloc(vecs[i], sizes[i] * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&S->host_sc, SC_COUNT * sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
@@ -137,6 +144,7 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
   const long n = M->np;
   const int G = grid_for(n);
   cudaError_t e;
+  const unsigned long long dof0 = dof_counter();
   cudaEventRecord(S->ev0, s);
   // b <- b - mean(b); ||b||
   project_mean(b_in, S->b, n, S->partial, S->sc, SC_TMP, s);
@@ -154,10 +162,12 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
     info->iterations = 0;
     info->rel_residual = 0.0;
     info->ms = 0.0f;
+    info->dof_applies = 0.0;
     return DGW_OK;
   }
   auto precondition = [&](const double *r, double *z) -> cudaError_t {
     if (o->mode == 2 || !S->mg_ready) {
+      note_launch();
       jacobi_kernel<<<G, 256, 0, s>>>(r, M->diag64, z, n);
     } else {
       cudaError_t ee = mg_vcycle(M, S, o->mode, r, z, s);
@@ -169,14 +179,20 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
     e = mg_setup(M, S, o->mode, o->cheb_degree > 0 ? o->cheb_degree : 5, s);
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: multigrid setup");
   }
+  note_launch();
+  copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RR, SC_BB);   // r = b: the preconditioner scales by rms(r)
   e = precondition(S->r, S->z);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
   reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
+  note_launch();
   cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 1);
+  note_launch();
   copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
   for (it = 1; it <= o->max_iter; ++it) {
     e = launch_laplace<double>(M->v64, S->d, S->q, s);
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
     reduce_to(S->d, S->q, n, S->partial, S->sc, SC_DQ, s);
+    note_launch();
     cg_update_kernel<<<G, 256, 0, s>>>(p, S->r, S->d, S->q, n, S->sc);
     reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RR, s);
     cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -184,10 +200,14 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
     rel = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
     if (rel <= o->rtol) break;
+    std::swap(S->z, S->zold);
     e = precondition(S->r, S->z);
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
     reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
+    reduce_to(S->r, S->zold, n, S->partial, S->sc, SC_RZOLD, s);
+    note_launch();
     cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 0);
+    note_launch();
     copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
   }
   if (it > o->max_iter) { it = o->max_iter; st = DGW_ENOTCONV; }
@@ -195,6 +215,7 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
   project_mean(p, p, n, S->partial, S->sc, SC_TMP, s);
   launch_laplace<double>(M->v64, p, S->q, s);
   cudaMemcpyAsync(S->r, S->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  note_launch();
   axpby_kernel<<<G, 256, 0, s>>>(S->r, S->q, -1.0, 1.0, n);
   reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RR, s);
   cudaEventRecord(S->ev1, s);
@@ -206,6 +227,7 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
   info->iterations = it;
   info->rel_residual = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
   info->ms = ms;
+  info->dof_applies = (double)(dof_counter() - dof0);
   if (st == DGW_ENOTCONV) return set_error(DGW_ENOTCONV, "dgw_pressure_solve: max_iter reached");
   return DGW_OK;
 }
@@ -216,7 +238,7 @@ void dgw_solver_free(dgw_mesh *M) {
   dgw_solver *S = M ? M->solver : nullptr;
   if (!S) return;
   dgw::mg_free(S);
-  cudaFree(S->b); cudaFree(S->r); cudaFree(S->z); cudaFree(S->d); cudaFree(S->q);
+  cudaFree(S->b); cudaFree(S->r); cudaFree(S->z); cudaFree(S->d); cudaFree(S->q); cudaFree(S->zold);
   cudaFree(S->partial); cudaFree(S->sc);
   if (S->host_sc) cudaFreeHost(S->host_sc);
   if (S->ev0) cudaEventDestroy(S->ev0);

@@ -6,14 +6,14 @@
 namespace dgw {
 
 // device scalar slots of the CG recurrences
-enum { SC_RZ = 0, SC_RZNEW, SC_DQ, SC_RR, SC_BB, SC_TMP, SC_COUNT = 8 };
+enum { SC_RZ = 0, SC_RZNEW, SC_DQ, SC_RR, SC_BB, SC_TMP, SC_RZOLD, SC_COUNT = 8 };
 
 struct MGLevel;
 
 }  // namespace dgw
 
 struct dgw_solver {
-  double *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr;
+  double *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr, *zold = nullptr;
   double *partial = nullptr, *sc = nullptr, *host_sc = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // multigrid hierarchy (built on first use per mode)
@@ -32,5 +32,6 @@ cudaError_t project_mean(const double *a, double *x, long n, double *partial, do
 cudaError_t mg_setup(dgw_mesh *M, dgw_solver *S, int mode, int cheb_degree, cudaStream_t s);
 cudaError_t mg_vcycle(dgw_mesh *M, dgw_solver *S, int mode, const double *r, double *z, cudaStream_t s);
 void mg_free(dgw_solver *S);
+int mg_levels(dgw_solver *S);
 
 }  // namespace dgw

@@ -220,6 +220,7 @@ cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s) {
   WallCellData w = wall_data(M);
   for (int cls = 0; cls < 2; ++cls) {
     const int qs = cls == 0 ? QSET_LIN : QSET_CONV;
+    note_launch();
     wall_table_kernel<<<M->ne, 128, 0, s>>>(w, M->v64.basis, qs, M->v64.nvol[cls], M->v64.fpmax[cls],
                                             const_cast<double *>(M->v64.wt_vol[cls]),
                                             const_cast<double *>(M->v64.wt_face[cls]), cls == 0 ? M->aux_vol : nullptr,
@@ -233,6 +234,7 @@ cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s) {
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s) {
   if (M->ne == 0) return cudaSuccess;
   WallCellData w = wall_data(M);
+  note_launch();
   eddy_viscosity_kernel<<<M->ne, 128, 0, s>>>(
       w, M->v64.basis, M->v64.nvol[0], M->v64.fpmax[0], M->v64.wt_vol[0], M->v64.wt_face[0], M->aux_vol, M->aux_face,
       M->dye_dev, M->P.degree, u + 3 * M->np, const_cast<double *>(M->v64.nut_vol),
@@ -249,6 +251,7 @@ __global__ void to_float_kernel(const double *a, float *b, size_t n) {
 
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  note_launch();
   to_float_kernel<<<1216, 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }

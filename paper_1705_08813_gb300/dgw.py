@@ -17,7 +17,8 @@ STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -
 # every symbol include/dgw.h declares
 EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
-           "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error"]
+           "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
+           "dgw_counters"]
 
 
 class DGWError(RuntimeError):
@@ -41,7 +42,8 @@ class SolveOpts(ctypes.Structure):
 
 
 class SolveInfo(ctypes.Structure):
-    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms", ctypes.c_float)]
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms", ctypes.c_float),
+                ("dof_applies", ctypes.c_double)]
 
 
 _lib = None
@@ -67,8 +69,10 @@ def load(path: str = LIB_PATH):
     lib.dgw_apply_viscous.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_pressure_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.dgw_last_error.restype = ctypes.c_char_p
+    lib.dgw_counters.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.dgw_counters.restype = None
     for name in EXPORTS:
-        if name != "dgw_last_error":
+        if name not in ("dgw_last_error", "dgw_counters"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -171,7 +175,16 @@ class Mesh:
                                          ctypes.byref(info), _stream(stream))
         if check:
             _check(st)
-        return {"iterations": info.iterations, "rel_residual": info.rel_residual, "ms": info.ms, "status": st}
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual, "ms": info.ms, "status": st,
+                "dof_applies": info.dof_applies}
+
+
+def counters():
+    """(kernel launches, operator DoF applications) performed by the library so far."""
+    lib = load()
+    a, b = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    lib.dgw_counters(ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
 
 
 def mesh_for(workload, **kw) -> Mesh:

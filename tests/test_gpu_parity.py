@@ -123,3 +123,37 @@ def test_empty_input_rejected(dgw):
         gm.laplace(torch.zeros(0, dtype=torch.float64, device="cuda"), torch.zeros(0, dtype=torch.float64, device="cuda"))
     with pytest.raises(dgw.DGWError):
         dgw.Mesh(0, 4, 4, 2, lx=1.0, lz=1.0, nu=1e-3, tau_w=1e-2)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pressure_solve_multigrid_modes(dgw, mode):
+    """FP64 CG with the FP64 (mode 0) or FP32 (mode 1) multigrid V-cycle reaches 1e-10; the residual
+    is re-evaluated with the oracle's own operator."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    om, gm = _meshes(dgw, w)
+    dev = torch.device("cuda:0")
+    u = I.velocity_field(om.node_coords(), om.n_e, w)
+    b = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
+    gm.divergence(torch.tensor(u, device=dev), b)
+    p = torch.zeros_like(b)
+    info = gm.pressure_solve(b, p, rtol=1e-10, max_iter=200, mode=mode)
+    bh = b.cpu().numpy()
+    bh = bh - bh.mean()
+    res = np.linalg.norm(bh - om.laplace(p.cpu().numpy())) / np.linalg.norm(bh)
+    assert info["rel_residual"] <= 1e-10 and res <= 1.5e-10, (info, res)
+    assert info["iterations"] < 60, info
+    assert abs(p.cpu().numpy().mean()) < 1e-14
+
+
+@pytest.mark.parametrize("dims,k", [((6, 4, 4), 3), ((5, 6, 3), 2), ((4, 2, 4), 4)])
+def test_pressure_solve_multigrid_odd_and_semi_coarsening(dgw, dims, k):
+    """Odd cell counts stop the coarsening of that direction (semi-coarsening) or the hierarchy."""
+    w = I.Workload("mg", *dims, k, 180.0, 1.0 / 3250.0, seed=21)
+    gm = dgw.mesh_for(w)
+    om = O.Mesh(**w.mesh_kwargs())
+    b = torch.tensor(I.pressure_rhs(gm.n_p, 5), device="cuda")
+    p = torch.zeros_like(b)
+    info = gm.pressure_solve(b, p, rtol=1e-10, max_iter=300, mode=1)
+    bh = b.cpu().numpy()
+    res = np.linalg.norm(bh - om.laplace(p.cpu().numpy())) / np.linalg.norm(bh)
+    assert res <= 1.5e-10, (info, res)
