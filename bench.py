@@ -345,7 +345,7 @@ def run_gpu(args):
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
                 "per_op": per_op, "solves": solve_rates, "dof_applies_per_step": dofs_step,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk, "gpu_launches": int(launches1 - launches0),
+                "clocks": clk, "gpu_launches": int(launches1 - launches0), "launches_before_timed": int(launches0),
                 "wall_s": t_wall}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -139,6 +139,13 @@ typedef struct {
 dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const dgw_solve_opts *opts,
                               dgw_solve_info *info, void *stream);
 
+/* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32): number of
+ * levels, the estimated largest eigenvalue of D^-1 A per level (the Chebyshev smoother works on
+ * [1.2 lmax / 15, 1.2 lmax]) and the cell count per level, finest first; at most max_levels
+ * entries are written. Synchronises the library's solver stream. */
+dgw_status dgw_solver_describe(dgw_mesh_t mesh, int mode, int *n_levels, double *lmax, int *cells, int max_levels,
+                               void *stream);
+
 /* Thread-local description of the last error. */
 const char *dgw_last_error(void);
 

@@ -15,6 +15,8 @@ static std::atomic<unsigned long long> g_launches{0};
 static std::atomic<unsigned long long> g_dofs{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launch_counter() { return g_launches.load(std::memory_order_relaxed); }
 void note_dofs(long long n) { g_dofs.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 unsigned long long dof_counter() { return g_dofs.load(std::memory_order_relaxed); }
 
@@ -156,6 +158,11 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->v64.enr = upload(M, M->enr.data(), M->nc, s, &err);
   M->v32.enr = M->v64.enr;
   M->v64.basis = upload(M, &M->basis64, 1, s, &err);
+  std::vector<double> rops;
+  box_rowops(geo, M->basis64, rops);
+  std::vector<float> rops32(rops.begin(), rops.end());
+  M->v64.rowops = upload(M, rops.data(), rops.size(), s, &err);
+  M->v32.rowops = upload(M, rops32.data(), rops32.size(), s, &err);
   if (M->has32) {
     M->v32.hy = upload(M, hy32.data(), ny, s, &err);
     M->v32.tau = upload(M, tau32.data(), M->nc, s, &err);

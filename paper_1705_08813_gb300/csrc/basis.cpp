@@ -112,12 +112,30 @@ void fill_basis(int k, int q_conv, int q_wall, Basis<T> *b) {
     lagrange_row(n, z, (double)side, v, d);
     for (int j = 0; j < n; ++j) b->dend[side][j] = (T)d[j];
   }
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) {
+      double s = 0.0;
+      for (int q = 0; q < b->q[QSET_LIN]; ++q) s += (double)b->w[QSET_LIN][q] * b->S[QSET_LIN][q * n + a] * b->S[QSET_LIN][q * n + c];
+      b->mass[a * n + c] = (T)s;
+    }
   for (int o = 0; o < 2; ++o)
     for (int i = 0; i < n; ++i) {
       double v[NMAX], d[NMAX];
       lagrange_row(n, z, 0.5 * (o + z[i]), v, d);
       for (int j = 0; j < n; ++j) b->P[o][i * n + j] = (T)v[j];
     }
+}
+
+// P[i*n + j] = l_j(a + b z_i): nodal embedding of the parent cell's basis into a child whose local
+// coordinate x maps to a + b x in the parent (z: Gauss-Lobatto nodes).
+void embed_matrix(int n, double a, double b, double *P) {
+  double z[NMAX];
+  lobatto_nodes(n, z);
+  for (int i = 0; i < n; ++i) {
+    double v[NMAX], d[NMAX];
+    lagrange_row(n, z, a + b * z[i], v, d);
+    for (int j = 0; j < n; ++j) P[i * n + j] = v[j];
+  }
 }
 
 template void fill_basis<double>(int, int, int, Basis<double> *);

@@ -29,6 +29,7 @@ struct Basis {
   T x[NQSET][QMAX];
   T w[NQSET][QMAX];
   T dend[2][NMAX];
+  T mass[NMAX * NMAX];   // 1-D reference mass matrix sum_q w_q l_a(x_q) l_b(x_q)
   // h-multigrid embedding: P[o][i*n1+j] = l_j((o + xhat_i)/2), child offset o in {0,1}
   T P[2][NMAX * NMAX];
 };
@@ -45,6 +46,7 @@ struct MeshView {
   T hx, hz;
   const T *hy;        // [ny] row heights
   const T *tau;       // [nc] penalty tau_IP per cell
+  const T *rowops;    // [ny][rowops_size] factorised 1-D Laplace operators per cell row
   const int *enr;     // [nc] enriched index or -1
   T visc;             // kinematic viscosity nu
   const Basis<T> *basis;
@@ -100,8 +102,10 @@ namespace dgw {
 // process-wide counters: kernel launches and operator DoF applications (output DoFs of every
 // operator apply, including the applies inside solves)
 void note_launch();
+void note_launches(unsigned long long n);
 void note_dofs(long long n);
 unsigned long long dof_counter();
+unsigned long long launch_counter();
 
 // error reporting (thread-local message)
 dgw_status set_error(dgw_status s, const std::string &msg);
@@ -112,6 +116,7 @@ void gauss_rule(int n, double *x, double *w);
 void lobatto_nodes(int n, double *x);
 template <typename T>
 void fill_basis(int k, int q_conv, int q_wall, Basis<T> *b);
+void embed_matrix(int n, double a, double b, double *P);
 
 // Geometry of a channel of boxes: uniform x and z spacing, graded rows in y.
 struct BoxGeometry {
@@ -123,6 +128,8 @@ struct BoxGeometry {
 void box_geometry(int k, int nx, int ny, int nz, double lx, double lz, const std::vector<double> &yv, BoxGeometry &g);
 // Diagonal of the SIPG Laplacian (Jacobi), from the 1-D mass and stiffness diagonals.
 void laplace_diagonal(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &dg);
+// Per-row 1-D operators of the factorised SIPG Laplacian on boxes.
+void box_rowops(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &R);
 
 // kernels (launched by api.cu)
 template <typename T>

@@ -7,6 +7,7 @@
 // (restriction), and a fixed number of device-side Jacobi-PCG steps on the coarsest level.
 // Mode 1 runs the whole V-cycle in FP32 (operators, smoothers, transfers) on a residual scaled
 // by its RMS value; mode 0 runs it in FP64.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -15,9 +16,9 @@
 
 namespace dgw {
 
-constexpr double kSmoothRange = 15.0;   // Chebyshev smooths [lmax/15, 1.1 lmax]
+constexpr double kSmoothRange = 15.0;   // Chebyshev smooths [1.2 lmax/15, 1.2 lmax]
 constexpr int kCoarseIters = 24;       // PCG steps on the coarsest level
-constexpr int kPowerIters = 40;        // power iterations for lmax(D^-1 A)
+constexpr int kLanczos = 24;           // CG-Lanczos steps for lmax(D^-1 A)
 
 // ------------------------------------------------------------------------------------------
 // vector kernels (templated on the level precision; reductions accumulate in double)
@@ -108,7 +109,7 @@ template <typename T>
 __global__ void cpcg_direction(T *__restrict__ d, const T *__restrict__ z, long n, double *sc, int first) {
   const double beta = (first || sc[MS_RZ] == 0.0) ? 0.0 : sc[MS_RZNEW] / sc[MS_RZ];
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    d[i] = (T)((double)z[i] + beta * (double)d[i]);
+    d[i] = first ? z[i] : (T)((double)z[i] + beta * (double)d[i]);   // d unread on the first step
 }
 
 __global__ void shift_scalar(double *sc, int dst, int src) {
@@ -158,6 +159,7 @@ struct XferDims {
   int fnx, fny, fnz;   // fine cells
   int cnx, cny, cnz;   // coarse cells
   int cf[3];           // factors (1 or 2)
+  const void *py;      // [cny][2][n*n] y-embeddings (graded rows split unevenly), when cf[1] == 2
 };
 
 template <typename T>
@@ -171,10 +173,13 @@ __global__ void prolongate_add(const Basis<T> *Bg, XferDims X, const T *__restri
   const int fidx[3] = {fi, fj, fk};
   const int ci = fi / X.cf[0], cj = fj / X.cf[1], ck = fk / X.cf[2];
   const int cc = ci + X.cnx * (cj + X.cny * ck);
+  const T *py = static_cast<const T *>(X.py);
   for (int d = 0; d < 3; ++d)
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
       const int i = t / n, j = t % n;
-      Pm[d][t] = X.cf[d] == 2 ? B.P[fidx[d] & 1][t] : (i == j ? T(1) : T(0));
+      T v = i == j ? T(1) : T(0);
+      if (X.cf[d] == 2) v = d == 1 ? py[((size_t)cj * 2 + (fidx[1] & 1)) * n * n + t] : B.P[fidx[d] & 1][t];
+      Pm[d][t] = v;
     }
   for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = xc[(size_t)cc * n3 + t];
   __syncthreads();
@@ -195,11 +200,14 @@ __global__ void restrict_kernel(const Basis<T> *Bg, XferDims X, const T *__restr
   const int n = B.n1, n3 = n * n * n;
   const int cc = blockIdx.x;
   const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
+  const T *py = static_cast<const T *>(X.py);
   for (int o = 0; o < 2; ++o)
     for (int d = 0; d < 3; ++d)
       for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
         const int i = t / n, j = t % n;
-        Pm[o][d][t] = X.cf[d] == 2 ? B.P[o][t] : (i == j ? T(1) : T(0));
+        T v = i == j ? T(1) : T(0);
+        if (X.cf[d] == 2) v = d == 1 ? py[((size_t)cj * 2 + o) * n * n + t] : B.P[o][t];
+        Pm[o][d][t] = v;
       }
   for (int t = threadIdx.x; t < n3; t += blockDim.x) Acc[t] = T(0);
   __syncthreads();
@@ -259,6 +267,7 @@ static T *lalloc(Lvl<T> *L, size_t n, cudaError_t &e) {
   void *p = nullptr;
   if (e != cudaSuccess) return nullptr;
   e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemset(p, 0, std::max<size_t>(n, 1) * sizeof(T));
   if (e == cudaSuccess) L->allocs.push_back(p);
   return (T *)p;
 }
@@ -278,36 +287,82 @@ static cudaError_t level_apply(const Lvl<T> *L, const T *x, T *y, cudaStream_t s
   return launch_laplace<T>(L->view, x, y, s);
 }
 
-// lmax of D^-1 A by power iteration (setup only; host-synchronising)
+// Largest eigenvalue of D^-1 A from the Lanczos tridiagonal of kLanczos Jacobi-PCG steps on a
+// random zero-mean right-hand side (setup only; host-synchronising). The Ritz value approaches
+// lmax from below; the smoother applies a 1.2 safety factor.
+static double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &b) {
+  // Sturm-sequence bisection for the largest eigenvalue of the symmetric tridiagonal (a, b)
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {   // eigenvalues < x
+    int c = 0;
+    double q = a[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = a[i] - x - b[i - 1] * b[i - 1] / q;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) < m) lo = mid; else hi = mid;
+  }
+  return hi;
+}
+
 template <typename T>
 static cudaError_t estimate_lmax(Lvl<T> *L, cudaStream_t s) {
   const long n = L->n;
+  const int G = mg_grid(n);
   std::vector<T> h(n);
   uint64_t st = 0x243F6A8885A308D3ull;
   for (long i = 0; i < n; ++i) {
     st ^= st << 13; st ^= st >> 7; st ^= st << 17;
     h[i] = (T)((double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
   }
-  cudaError_t e = cudaMemcpyAsync(L->x, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, s);
-  double lam = 1.0, host[MS_COUNT];
-  for (int it = 0; it < kPowerIters && e == cudaSuccess; ++it) {
-    mg_reduce<T>(L->x, L->x, n, L->partial, L->sc, MS_SUM, s);
-    note_launch();
-    scale_vec<T><<<mg_grid(n), 256, 0, s>>>(L->x, L->x, n, L->sc, MS_SUM);
-    e = level_apply(L, L->x, L->t, s);
-    note_launch();
-    mul_kernel<T><<<mg_grid(n), 256, 0, s>>>(L->t, L->t, L->dinv, n);
-    mg_reduce<T>(L->x, L->t, n, L->partial, L->sc, MS_DQ, s);   // Rayleigh-like estimate x.(D^-1 A x)
-    mg_reduce<T>(L->t, L->t, n, L->partial, L->sc, MS_RZ, s);
-    cudaMemcpyAsync(L->x, L->t, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(L->r, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, s);
+  // r zero-mean; z = D^-1 r (zero-mean); d = z
+  mg_reduce<T>(L->r, nullptr, n, L->partial, L->sc, MS_SUM, s);
+  sub_mean_T<T><<<G, 256, 0, s>>>(L->r, n, L->sc, MS_SUM);
+  std::vector<double> alpha, beta;
+  double host[MS_COUNT];
+  double rz_old = 0.0;
+  for (int it = 0; it < kLanczos && e == cudaSuccess; ++it) {
+    cpcg_precond<T><<<G, 256, 0, s>>>(L->z, L->r, L->dinv, n);
+    mg_reduce<T>(L->z, nullptr, n, L->partial, L->sc, MS_SUM, s);
+    sub_mean_T<T><<<G, 256, 0, s>>>(L->z, n, L->sc, MS_SUM);
+    mg_reduce<T>(L->r, L->z, n, L->partial, L->sc, MS_RZNEW, s);
+    cpcg_direction<T><<<G, 256, 0, s>>>(L->d, L->z, n, L->sc, it == 0);
+    shift_scalar<<<1, 32, 0, s>>>(L->sc, MS_RZ, MS_RZNEW);
+    e = level_apply(L, L->d, L->t, s);
+    mg_reduce<T>(L->d, L->t, n, L->partial, L->sc, MS_DQ, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, L->sc, sizeof(host), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    const double rz = host[MS_RZ], dq = host[MS_DQ];
+    if (!(rz > 0.0) || !(dq > 0.0)) break;
+    if (it > 0) beta.push_back(rz / rz_old);
+    alpha.push_back(rz / dq);
+    rz_old = rz;
+    cpcg_update<T><<<G, 256, 0, s>>>(L->x, L->r, L->d, L->t, n, L->sc);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host, L->sc, sizeof(host), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) {
-    lam = std::sqrt(host[MS_RZ]);   // ||D^-1 A x|| with ||x|| = 1
-    L->lmax = lam > 0 ? lam : 1.0;
+  if (e != cudaSuccess || alpha.empty()) return e;
+  // Lanczos tridiagonal from the CG coefficients
+  const int m = (int)alpha.size();
+  std::vector<double> ta(m), tb(std::max(m - 1, 0));
+  for (int i = 0; i < m; ++i) {
+    ta[i] = 1.0 / alpha[i] + (i > 0 ? beta[i - 1] / alpha[i - 1] : 0.0);
+    if (i + 1 < m) tb[i] = std::sqrt(beta[i]) / alpha[i];
   }
-  return e;
+  L->lmax = tridiag_max_eig(ta, tb);
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -340,6 +395,12 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       L->view.hy = hyd;
       L->view.tau = taud;
       L->view.enr = nullptr;
+      std::vector<double> rops;
+      box_rowops(L->geo, M->basis64, rops);
+      std::vector<T> ropsT(rops.begin(), rops.end());
+      T *rd = lalloc<T>(L, ropsT.size(), e);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(rd, ropsT.data(), ropsT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+      L->view.rowops = rd;
     }
     std::vector<double> dg;
     laplace_diagonal(L->geo, M->basis64, dg);
@@ -354,6 +415,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     L->d = lalloc<T>(L, L->n, e); L->t = lalloc<T>(L, L->n, e); L->z = lalloc<T>(L, L->n, e);
     void *p = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(p, 0, MS_COUNT * sizeof(double));
     if (e == cudaSuccess) { L->allocs.push_back(p); L->sc = (double *)p; }
     if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
     if (e == cudaSuccess) { L->allocs.push_back(p); L->partial = (double *)p; }
@@ -365,6 +427,22 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     XferDims X;
     X.fnx = nx; X.fny = ny; X.fnz = nz;
     X.cf[0] = cf[0]; X.cf[1] = cf[1]; X.cf[2] = cf[2];
+    X.py = nullptr;
+    if (cf[1] == 2) {
+      // child rows 2J and 2J+1 of coarse row J split it in the ratio of their heights
+      const int cny = ny / 2, nn = n * n;
+      std::vector<double> P((size_t)cny * 2 * nn);
+      for (int J = 0; J < cny; ++J) {
+        const double h0 = yv[2 * J + 1] - yv[2 * J], h1 = yv[2 * J + 2] - yv[2 * J + 1], r = h0 / (h0 + h1);
+        embed_matrix(n, 0.0, r, &P[((size_t)J * 2 + 0) * nn]);
+        embed_matrix(n, r, 1.0 - r, &P[((size_t)J * 2 + 1) * nn]);
+      }
+      std::vector<T> PT(P.begin(), P.end());
+      T *pyd = lalloc<T>(L, PT.size(), e);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(pyd, PT.data(), PT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      X.py = pyd;
+    }
     nx /= cf[0]; ny /= cf[1]; nz /= cf[2];
     X.cnx = nx; X.cny = ny; X.cnz = nz;
     L->to_coarse = X;
@@ -379,7 +457,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
 
 template <typename T>
 static void chebyshev(const Hierarchy<T> *H, Lvl<T> *L, bool zero_init, cudaStream_t s) {
-  const double lmax = 1.1 * L->lmax, lmin = lmax / kSmoothRange;
+  const double lmax = 1.2 * L->lmax, lmin = lmax / kSmoothRange;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
   const int G = mg_grid(L->n);
@@ -401,6 +479,10 @@ static void coarse_solve(Lvl<T> *L, cudaStream_t s) {
   const long n = L->n;
   const int G = mg_grid(n);
   cudaMemsetAsync(L->x, 0, n * sizeof(T), s);
+  // the coarse problem is singular (constants): make its right-hand side consistent
+  mg_reduce<T>(L->b, nullptr, n, L->partial, L->sc, MS_SUM, s);
+  note_launch();
+  sub_mean_T<T><<<G, 256, 0, s>>>(L->b, n, L->sc, MS_SUM);
   cudaMemcpyAsync(L->r, L->b, n * sizeof(T), cudaMemcpyDeviceToDevice, s);
   for (int it = 0; it < kCoarseIters; ++it) {
     note_launch();
@@ -443,6 +525,7 @@ static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
 cudaError_t mg_setup(dgw_mesh *M, dgw_solver *S, int mode, int cheb, cudaStream_t s) {
   if (S->mg_ready && S->mg_mode == mode && S->mg_cheb == cheb) return cudaSuccess;
   mg_free(S);
+  if (S->vgraph) { cudaGraphExecDestroy(S->vgraph); S->vgraph = nullptr; }
   MGLevel *ml = new MGLevel();
   cudaError_t e;
   if (mode == 1) {
@@ -490,6 +573,24 @@ cudaError_t mg_vcycle(dgw_mesh *M, dgw_solver *S, int mode, const double *r, dou
     scale_out<double><<<G, 256, 0, s>>>(z, H->L[0]->x, n, S->sc, SC_RR);
   }
   return cudaGetLastError();
+}
+
+int mg_describe(dgw_solver *S, double *lmax, int *cells, int max_levels) {
+  if (S->levels.empty()) return 0;
+  MGLevel *ml = S->levels[0];
+  int nl = 0;
+  auto fill = [&](auto *H) {
+    for (auto *L : H->L) {
+      if (nl < max_levels) {
+        if (lmax) lmax[nl] = L->lmax;
+        if (cells) cells[nl] = L->view.nc;
+      }
+      ++nl;
+    }
+  };
+  if (ml->prec == 1) fill((Hierarchy<float> *)ml->h);
+  else fill((Hierarchy<double> *)ml->h);
+  return nl;
 }
 
 int mg_levels(dgw_solver *S) {

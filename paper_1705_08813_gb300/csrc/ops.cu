@@ -3,7 +3,6 @@
 // integrals over its six faces for its own test functions, re-reading the neighbour's
 // coefficients (cell-centric face loop: no atomics, deterministic).
 //
-//   laplace_kernel   : y = -L(q,p), SIPG with the flux of eq. (ipflux), Neumann walls
 //   vector_op_kernel : OP_DIV  b = -C(q,u)                   (Sec. 4.2, velocity divergence)
 //                      OP_CONV y = F^c(v,u), LF flux          (Sec. 4.2, convective term)
 //                      OP_VISC y = -F^nu(vbar,v~;ubar,u~)     (eq. viscous_multiscale)
@@ -49,103 +48,6 @@ __device__ void load_basis(const Basis<T> *g, Basis<T> *s) {
   int *dst = reinterpret_cast<int *>(s);
   for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = src[t];
 }
-
-// ------------------------------------------------------------------------------------------
-// SIPG Laplacian
-// ------------------------------------------------------------------------------------------
-
-template <typename T>
-__global__ void __launch_bounds__(128) laplace_kernel(MeshView<T> m, const T *__restrict__ p, T *__restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Basis<T> &B = *reinterpret_cast<Basis<T> *>(smem_raw);
-  T *base = reinterpret_cast<T *>(smem_raw + ((sizeof(Basis<T>) + 15) / 16) * 16);
-  const int n = m.n1, n3 = n * n * n, q = n;
-  const int P = q * q * q;
-  const int FP = q * q;
-  const int tsz = 5 * max(max(q * n * n, q * q * n), n * max(n, q));
-  T *u = base, *un = u + n3, *r = un + n3;
-  T *g0 = r + n3, *g1 = g0 + P, *g2 = g1 + P;
-  T *vs = g2 + P, *ds = vs + FP, *vo = ds + FP, *dso = vo + FP, *fc = dso + FP, *hc = fc + FP;
-  T *tmp = hc + FP;
-  (void)tsz;
-  load_basis(m.basis, &B);
-  const int c = blockIdx.x;
-  const T *pc = p + (size_t)c * n3;
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) { u[t] = pc[t]; r[t] = T(0); }
-  __syncthreads();
-  const T h[3] = {m.hx, m.hy[(c / m.nx) % m.ny], m.hz};
-  AxisTabs<T> tabs;
-  for (int d = 0; d < 3; ++d) { tabs.S[d] = B.S[QSET_LIN]; tabs.D[d] = B.D[QSET_LIN]; tabs.q[d] = q; }
-  // volume: (grad phi_i, grad p)
-  eval_cell(u, n, tabs, (T *)nullptr, g0, g1, g2, tmp);
-  const T vol = h[0] * h[1] * h[2];
-  for (int t = threadIdx.x; t < P; t += blockDim.x) {
-    const int i0 = t % q, i1 = (t / q) % q, i2 = t / (q * q);
-    const T dV = vol * B.w[QSET_LIN][i0] * B.w[QSET_LIN][i1] * B.w[QSET_LIN][i2];
-    g0[t] *= dV / (h[0] * h[0]);
-    g1[t] *= dV / (h[1] * h[1]);
-    g2[t] *= dV / (h[2] * h[2]);
-  }
-  __syncthreads();
-  integrate_cell((const T *)nullptr, g0, g1, g2, n, tabs, r, tmp);
-  // faces
-  for (int f = 0; f < 6; ++f) {
-    const int nb = neighbour(m, c, f);
-    if (nb < 0) continue;   // homogeneous Neumann on walls
-    const int d = f >> 1, side = f & 1;
-    int t1, t2;
-    face_axes(d, t1, t2);
-    const T *pn = p + (size_t)nb * n3;
-    for (int t = threadIdx.x; t < n3; t += blockDim.x) un[t] = pn[t];
-    __syncthreads();
-    const T *S = B.S[QSET_LIN], *D = B.D[QSET_LIN];
-    eval_face(u, n, d, side, B.dend[side], S, D, q, S, D, q, vs, ds, (T *)nullptr, (T *)nullptr, tmp);
-    eval_face(un, n, d, 1 - side, B.dend[1 - side], S, D, q, S, D, q, vo, dso, (T *)nullptr, (T *)nullptr, tmp);
-    const T hd = h[d], hdo = cell_h(m, nb, d);
-    const T sgn = side ? T(1) : T(-1);
-    const T tau = max(m.tau[c], m.tau[nb]);
-    const T area = h[t1] * h[t2];
-    for (int t = threadIdx.x; t < FP; t += blockDim.x) {
-      const int a = t % q, b = t / q;
-      const T dA = area * B.w[QSET_LIN][a] * B.w[QSET_LIN][b];
-      const T dns = sgn * ds[t] / hd, dno = sgn * dso[t] / hdo;
-      const T jump = vs[t] - vo[t];
-      const T flux = T(0.5) * (dns + dno) - tau * jump;
-      fc[t] = -dA * flux;
-      hc[t] = -dA * T(0.5) * jump * sgn / hd;
-    }
-    __syncthreads();
-    integrate_face(fc, hc, (const T *)nullptr, (const T *)nullptr, n, d, side, B.dend[side], S, D, q, S, D, q, r, tmp);
-  }
-  T *yc = y + (size_t)c * n3;
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) yc[t] = r[t];
-}
-
-template <typename T>
-static size_t laplace_smem(int n) {
-  const int q = n, n3 = n * n * n, P = q * q * q, FP = q * q;
-  const int tsz = 5 * std::max(std::max(q * n * n, q * q * n), n * std::max(n, q));
-  const size_t words = 3 * n3 + 3 * P + 6 * FP + tsz;
-  return ((sizeof(Basis<T>) + 15) / 16) * 16 + words * sizeof(T);
-}
-
-template <typename T>
-cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s) {
-  const size_t sm = laplace_smem<T>(m.n1);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(laplace_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  note_launch();
-  note_dofs(m.np);
-  laplace_kernel<T><<<m.nc, 128, sm, s>>>(m, p, y);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_laplace<double>(const MeshView<double> &, const double *, double *, cudaStream_t);
-template cudaError_t launch_laplace<float>(const MeshView<float> &, const float *, float *, cudaStream_t);
 
 // ------------------------------------------------------------------------------------------
 // Vector operators (divergence, convective, viscous) with enriched wall cells

@@ -82,7 +82,7 @@ __global__ void cg_direction_kernel(double *__restrict__ d, const double *__rest
                                     int first) {
   const double beta = first ? 0.0 : (sc[SC_RZNEW] - sc[SC_RZOLD]) / sc[SC_RZ];
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    d[i] = z[i] + beta * d[i];
+    d[i] = first ? z[i] : z[i] + beta * d[i];   // d is not read on the first step (may be uninitialised)
 }
 
 __global__ void copy_scalar_kernel(double *sc, int dst, int src) {
@@ -116,7 +116,7 @@ cudaError_t project_mean(const double *a, double *x, long n, double *partial, do
   return cudaGetLastError();
 }
 
-static dgw_solver *get_solver(dgw_mesh *M) {
+dgw_solver *get_solver(dgw_mesh *M) {
   if (M->solver) return M->solver;
   dgw_solver *S = new dgw_solver();
   const long n = M->np;
@@ -124,10 +124,16 @@ static dgw_solver *get_solver(dgw_mesh *M) {
   double **vecs[] = {&S->b, &S->r, &S->z, &S->d, &S->q, &S->zold, &S->partial, &S->sc};
   const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)RED_BLOCKS,
                           (size_t)SC_COUNT};
-  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaMalloc(vecs[i], sizes[i] * sizeof(double));
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(vecs[i], sizes[i] * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(*vecs[i], 0, sizes[i] * sizeof(double));
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&S->host_sc, SC_COUNT * sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     M->solver = S;
     dgw_solver_free(M);
@@ -137,10 +143,36 @@ static dgw_solver *get_solver(dgw_mesh *M) {
   return S;
 }
 
+// The V-cycle r -> z as a CUDA graph: captured once per hierarchy on the internal stream and
+// replayed every CG iteration (about 300 small launches per cycle otherwise).
+static cudaError_t vcycle_graph(dgw_mesh *M, dgw_solver *S, int mode, cudaStream_t s) {
+  if (S->vgraph) return cudaGraphLaunch(S->vgraph, s) == cudaSuccess
+                             ? (note_launches(S->vgraph_launches), note_dofs((long long)S->vgraph_dofs), cudaSuccess)
+                             : cudaErrorLaunchFailure;
+  const unsigned long long l0 = launch_counter(), d0 = dof_counter();
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t ev = mg_vcycle(M, S, mode, S->r, S->z, s);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  if (ev != cudaSuccess) e = ev;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&S->vgraph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) { S->vgraph = nullptr; return e; }
+  S->vgraph_launches = launch_counter() - l0;
+  S->vgraph_dofs = dof_counter() - d0;
+  // the capture itself counted nothing that ran; the launch below runs and counts it
+  e = cudaGraphLaunch(S->vgraph, s);
+  return e;
+}
+
 dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_solve_opts *o, dgw_solve_info *info,
-                          cudaStream_t s) {
+                          cudaStream_t cs) {
   dgw_solver *S = get_solver(M);
   if (!S) return set_error(DGW_ENOMEM, "dgw_pressure_solve: workspace allocation failed");
+  cudaStream_t s = S->stream;
+  cudaEventRecord(S->ev_in, cs);
+  cudaStreamWaitEvent(s, S->ev_in, 0);
   const long n = M->np;
   const int G = grid_for(n);
   cudaError_t e;
@@ -200,7 +232,7 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
     rel = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
     if (rel <= o->rtol) break;
-    std::swap(S->z, S->zold);
+    cudaMemcpyAsync(S->zold, S->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     e = precondition(S->r, S->z);
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
     reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
@@ -224,6 +256,8 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
   if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, S->ev0, S->ev1);
+  cudaEventRecord(S->ev_out, s);
+  cudaStreamWaitEvent(cs, S->ev_out, 0);
   info->iterations = it;
   info->rel_residual = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
   info->ms = ms;
@@ -243,6 +277,10 @@ void dgw_solver_free(dgw_mesh *M) {
   if (S->host_sc) cudaFreeHost(S->host_sc);
   if (S->ev0) cudaEventDestroy(S->ev0);
   if (S->ev1) cudaEventDestroy(S->ev1);
+  if (S->ev_in) cudaEventDestroy(S->ev_in);
+  if (S->ev_out) cudaEventDestroy(S->ev_out);
+  if (S->vgraph) cudaGraphExecDestroy(S->vgraph);
+  if (S->stream) cudaStreamDestroy(S->stream);
   delete S;
   M->solver = nullptr;
 }
@@ -255,4 +293,18 @@ extern "C" dgw_status dgw_pressure_solve(dgw_mesh_t M, const double *b, double *
   if (opts->mode == 1 && !M->has32)
     return dgw::set_error(DGW_EINVAL, "dgw_pressure_solve: mixed mode needs a mesh with FP32 tables");
   return dgw::pressure_solve(M, b, p, opts, info, (cudaStream_t)stream);
+}
+
+extern "C" dgw_status dgw_solver_describe(dgw_mesh_t M, int mode, int *n_levels, double *lmax, int *cells,
+                                          int max_levels, void *stream) {
+  if (!M || !n_levels) return dgw::set_error(DGW_EINVAL, "dgw_solver_describe: null argument");
+  if (mode < 0 || mode > 1) return dgw::set_error(DGW_EINVAL, "dgw_solver_describe: mode must be 0 or 1");
+  if (mode == 1 && !M->has32) return dgw::set_error(DGW_EINVAL, "dgw_solver_describe: mesh has no FP32 tables");
+  dgw_solver *S = dgw::get_solver(M);
+  if (!S) return dgw::set_error(DGW_ENOMEM, "dgw_solver_describe: workspace allocation failed");
+  cudaError_t e = dgw::mg_setup(M, S, mode, S->mg_cheb > 0 ? S->mg_cheb : 5, S->stream);
+  if (e != cudaSuccess) return dgw::cuda_check(e, "dgw_solver_describe");
+  (void)stream;
+  *n_levels = dgw::mg_describe(S, lmax, cells, max_levels);
+  return DGW_OK;
 }

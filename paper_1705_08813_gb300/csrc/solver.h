@@ -15,7 +15,11 @@ struct MGLevel;
 struct dgw_solver {
   double *b = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *q = nullptr, *zold = nullptr;
   double *partial = nullptr, *sc = nullptr, *host_sc = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t stream = nullptr;   // internal stream (graph capture needs a non-legacy stream)
+  // captured V-cycle (fixed buffers r -> z) and the launches / DoF applications one replay adds
+  cudaGraphExec_t vgraph = nullptr;
+  unsigned long long vgraph_launches = 0, vgraph_dofs = 0;
   // multigrid hierarchy (built on first use per mode)
   bool mg_ready = false;
   int mg_mode = -1;
@@ -32,6 +36,8 @@ cudaError_t project_mean(const double *a, double *x, long n, double *partial, do
 cudaError_t mg_setup(dgw_mesh *M, dgw_solver *S, int mode, int cheb_degree, cudaStream_t s);
 cudaError_t mg_vcycle(dgw_mesh *M, dgw_solver *S, int mode, const double *r, double *z, cudaStream_t s);
 void mg_free(dgw_solver *S);
+dgw_solver *get_solver(dgw_mesh *M);
 int mg_levels(dgw_solver *S);
+int mg_describe(dgw_solver *S, double *lmax, int *cells, int max_levels);
 
 }  // namespace dgw

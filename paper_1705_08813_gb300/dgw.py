@@ -18,7 +18,7 @@ STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -
 EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
-           "dgw_counters"]
+           "dgw_counters", "dgw_solver_describe"]
 
 
 class DGWError(RuntimeError):
@@ -68,6 +68,8 @@ def load(path: str = LIB_PATH):
     lib.dgw_apply_convective.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_apply_viscous.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_pressure_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.dgw_solver_describe.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp]
     lib.dgw_last_error.restype = ctypes.c_char_p
     lib.dgw_counters.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.dgw_counters.restype = None
@@ -177,6 +179,16 @@ class Mesh:
             _check(st)
         return {"iterations": info.iterations, "rel_residual": info.rel_residual, "ms": info.ms, "status": st,
                 "dof_applies": info.dof_applies}
+
+
+def describe_solver(mesh, mode=1):
+    """Multigrid hierarchy of `mode`: list of (cells, lmax of D^-1 A) per level, finest first."""
+    lib = load()
+    nl = ctypes.c_int()
+    lm = (ctypes.c_double * 32)()
+    cells = (ctypes.c_int * 32)()
+    _check(lib.dgw_solver_describe(mesh.h, mode, ctypes.byref(nl), lm, cells, 32, None))
+    return [(cells[i], lm[i]) for i in range(min(nl.value, 32))]
 
 
 def counters():
