@@ -171,17 +171,11 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 
 def laplace_flops_per_cell(k):
-    """FP64 operations of one cell of laplace_kernel (sum-factorised passes, 2 flops per FMA),
-    counted from the pass structure: volume gradients and their transpose, six faces with the
-    own and neighbour trace, normal derivatives and the transposed face integration."""
-    n = q = k + 1
-    fma = 0
-    fma += 2 * q * n * n * n + 3 * q * q * n * n + 3 * q * q * q * n      # eval_cell (3 gradients)
-    fma += 3 * q * q * q * n + 3 * q * q * n * n + 2 * q * n * n * n      # integrate_cell
-    per_face = 2 * (n * n * n + 2 * q * n * n + 2 * q * q * n)             # two traces: normal derivative + 2-D interpolation
-    per_face += 2 * q * q * n + 2 * q * n * n + n * n * n                  # transposed face integration + scatter
-    fma += 6 * per_face
-    return 2 * fma
+    """FP64 operations of one cell of laplace_box_kernel (2 flops per FMA), counted from its
+    passes with n = k + 1: neighbour trace derivatives 6n^3; x-lines 2n^4 + 4n^3; M_x on the y- and
+    z-face traces 8n^3; y-lines 3n^4 + 4n^3; M_y on the z-face traces 4n^3; z-lines 2n^4 + 4n^3."""
+    n = k + 1
+    return 2 * (7 * n ** 4 + 30 * n ** 3)
 
 
 def run_gpu(args):
@@ -303,7 +297,7 @@ def run_gpu(args):
     nc = w.nx * w.ny * w.nz
     fp64_peak = 152 * 4 * 2.07e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
     achieved_tf = nc * fl_cell / (lap_ms * 1e-3) / 1e12
-    roofline = {"kernel": "laplace_kernel<double>", "bound": "alu", "achieved": achieved_tf,
+    roofline = {"kernel": "laplace_box_kernel<double,k>", "bound": "alu", "achieved": achieved_tf,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
                 "traffic": args.traffic_bytes,
                 "peak_source": "derived FP64 rate (152 SMs x 2 DFMA/clk x 2.07 GHz)",

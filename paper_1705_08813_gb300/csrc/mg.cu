@@ -262,12 +262,14 @@ struct dgw::MGLevel {
 
 namespace dgw {
 
+// Allocation zeroed on the solver stream (all multigrid work runs on that non-blocking stream; a
+// plain cudaMemset would run on the legacy stream and could race with it).
 template <typename T>
-static T *lalloc(Lvl<T> *L, size_t n, cudaError_t &e) {
+static T *lalloc(Lvl<T> *L, size_t n, cudaError_t &e, cudaStream_t s) {
   void *p = nullptr;
   if (e != cudaSuccess) return nullptr;
   e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
-  if (e == cudaSuccess) e = cudaMemset(p, 0, std::max<size_t>(n, 1) * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(T), s);
   if (e == cudaSuccess) L->allocs.push_back(p);
   return (T *)p;
 }
@@ -389,7 +391,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       L->view.hx = (T)L->geo.hx;
       L->view.hz = (T)L->geo.hz;
       std::vector<T> hy(L->geo.hy.begin(), L->geo.hy.end()), tau(L->geo.tau.begin(), L->geo.tau.end());
-      T *hyd = lalloc<T>(L, hy.size(), e), *taud = lalloc<T>(L, tau.size(), e);
+      T *hyd = lalloc<T>(L, hy.size(), e, s), *taud = lalloc<T>(L, tau.size(), e, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(hyd, hy.data(), hy.size() * sizeof(T), cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(taud, tau.data(), tau.size() * sizeof(T), cudaMemcpyHostToDevice, s);
       L->view.hy = hyd;
@@ -398,7 +400,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       std::vector<double> rops;
       box_rowops(L->geo, M->basis64, rops);
       std::vector<T> ropsT(rops.begin(), rops.end());
-      T *rd = lalloc<T>(L, ropsT.size(), e);
+      T *rd = lalloc<T>(L, ropsT.size(), e, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(rd, ropsT.data(), ropsT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
       L->view.rowops = rd;
     }
@@ -406,16 +408,16 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     laplace_diagonal(L->geo, M->basis64, dg);
     double *dg_dev = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&dg_dev, dg.size() * sizeof(double));
-    L->dinv = lalloc<T>(L, L->n, e);
+    L->dinv = lalloc<T>(L, L->n, e, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dg_dev, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) { note_launch(); inv_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(dg_dev, L->dinv, L->n); }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (dg_dev) cudaFree(dg_dev);
-    L->x = lalloc<T>(L, L->n, e); L->b = lalloc<T>(L, L->n, e); L->r = lalloc<T>(L, L->n, e);
-    L->d = lalloc<T>(L, L->n, e); L->t = lalloc<T>(L, L->n, e); L->z = lalloc<T>(L, L->n, e);
+    L->x = lalloc<T>(L, L->n, e, s); L->b = lalloc<T>(L, L->n, e, s); L->r = lalloc<T>(L, L->n, e, s);
+    L->d = lalloc<T>(L, L->n, e, s); L->t = lalloc<T>(L, L->n, e, s); L->z = lalloc<T>(L, L->n, e, s);
     void *p = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(p, 0, MS_COUNT * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * sizeof(double), s);
     if (e == cudaSuccess) { L->allocs.push_back(p); L->sc = (double *)p; }
     if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
     if (e == cudaSuccess) { L->allocs.push_back(p); L->partial = (double *)p; }
@@ -438,7 +440,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
         embed_matrix(n, r, 1.0 - r, &P[((size_t)J * 2 + 1) * nn]);
       }
       std::vector<T> PT(P.begin(), P.end());
-      T *pyd = lalloc<T>(L, PT.size(), e);
+      T *pyd = lalloc<T>(L, PT.size(), e, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(pyd, PT.data(), PT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       X.py = pyd;

@@ -124,16 +124,17 @@ dgw_solver *get_solver(dgw_mesh *M) {
   double **vecs[] = {&S->b, &S->r, &S->z, &S->d, &S->q, &S->zold, &S->partial, &S->sc};
   const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)RED_BLOCKS,
                           (size_t)SC_COUNT};
+  e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
     e = cudaMalloc(vecs[i], sizes[i] * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(*vecs[i], 0, sizes[i] * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(*vecs[i], 0, sizes[i] * sizeof(double), S->stream);
   }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&S->host_sc, SC_COUNT * sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&S->ev1);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     M->solver = S;
     dgw_solver_free(M);
