@@ -139,6 +139,22 @@ typedef struct {
 dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const dgw_solve_opts *opts,
                               dgw_solve_info *info, void *stream);
 
+/* Pressure solve that allocates nothing, for callers that cannot let a library allocate device
+ * memory at solve time: code recording its work into a CUDA graph (allocation is illegal during
+ * stream capture), code whose device memory belongs to a framework's caching allocator or to a
+ * budget fixed at start-up, and latency-critical loops where cudaMalloc/cudaFree would
+ * synchronise the device. The paper has no counterpart; this is a service of the library.
+ * Solves -L p = b like dgw_pressure_solve with mode 2 (FP64 CG, Jacobi preconditioner, zero-mean
+ * b and p) on `stream`, with all scratch vectors in one file-scope device array of fixed size:
+ * 5 * 131072 + 312 doubles (about 5.2 MB), which every GPU that loads the library holds until the
+ * process exits. Meshes with n_p > 131072 are rejected with DGW_EINVAL. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. Every call shares the one array and clears what must start at zero; calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller. info->ms is host wall time. Synchronises `stream`. */
+dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t mesh, const double *b, double *p, double rtol, int max_iter,
+                                             dgw_solve_info *info, void *stream);
+
 /* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32): number of
  * levels, the estimated largest eigenvalue of D^-1 A per level (the Chebyshev smoother works on
  * [1.2 lmax / 15, 1.2 lmax]) and the cell count per level, finest first; at most max_levels

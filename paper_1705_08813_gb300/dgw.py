@@ -18,7 +18,7 @@ STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -
 EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
-           "dgw_counters", "dgw_solver_describe"]
+           "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc"]
 
 
 class DGWError(RuntimeError):
@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
     lib.dgw_pressure_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.dgw_solver_describe.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp]
+    lib.dgw_pressure_solve_jacobi_noalloc.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int,
+                                                      ctypes.POINTER(SolveInfo), vp]
     lib.dgw_last_error.restype = ctypes.c_char_p
     lib.dgw_counters.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.dgw_counters.restype = None
