@@ -348,6 +348,113 @@ def run_gpu(args):
     return 0
 
 
+def run_serving(args):
+    """Serving workload: Poisson arrivals (mean args.rate jobs/s, seed 999) of pressure solves (3/4,
+    mixed precision, 1e-10) and operator applies (1/4) on channels with N_x uniform in
+    {8,16,24,32,40,48}, N_y = N_z = max(8, N_x/2), k uniform in {2,3,4,5}; per-job seeded inputs.
+    Reports p50/p99 latency (arrival to completion) and solves/s through the request loop, and the
+    same job stream run one at a time with FP64 solves."""
+    import numpy as np
+    import torch
+    from paper_1705_08813_gb300 import dgw, inputs as I
+    torch.cuda.set_device(0)
+    dgw.load()
+    n = args.serving_jobs
+    rng_u = I.uniform(999, 4 * n, 0.0, 1.0, stream=41)
+    gaps = -np.log(1.0 - rng_u[:n]) / args.rate
+    arrivals = np.cumsum(gaps)
+    nxs = [8, 16, 24, 32, 40, 48]
+    specs = []
+    for j in range(n):
+        nx = nxs[int(rng_u[n + j] * 6)]
+        k = 2 + int(rng_u[2 * n + j] * 4)
+        kind = 0 if rng_u[3 * n + j] < 0.75 else 1 + int((rng_u[3 * n + j] - 0.75) * 16)
+        w = I.Workload(f"s{j}", nx, max(8, nx // 2), max(8, nx // 2), k, 590.0, 1.0 / 12000.0, seed=1000 + j)
+        specs.append((kind, w))
+    gen = torch.Generator(device="cuda")
+    bufs = []
+    for j, (kind, w) in enumerate(specs):
+        n1 = w.k + 1
+        npd = w.nx * w.ny * w.nz * n1 ** 3
+        nud = 3 * npd + 24 * 2 * w.nx * w.nz
+        gen.manual_seed(1000 + j)
+        nin = npd if kind in (0, 1) else nud
+        nout = npd if kind in (0, 1, 2) else nud
+        inp = torch.rand(nin, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+        if kind == 0:
+            inp -= inp.mean()
+        aux = inp if kind == 4 else None
+        bufs.append((inp, torch.zeros(nout, dtype=torch.float64, device="cuda"), aux))
+    torch.cuda.synchronize()
+    srv = dgw.Server(int(args.serving_budget_gb * (1 << 30)), max_inflight=args.serving_slots)
+    # warm the resident meshes and solver state: one job per distinct (mesh, kind)
+    seen, warm = set(), []
+    for j, (kind, w) in enumerate(specs):
+        key = (w.nx, w.k, kind)
+        if key not in seen:
+            seen.add(key)
+            inp, out, aux = bufs[j]
+            warm.append(srv.submit(kind, dgw.mesh_params(w), inp, out, aux=aux, mode=1))
+    pend = set(warm)
+    while pend:
+        for t in list(pend):
+            if srv.poll(t) is not None:
+                pend.discard(t)
+        time.sleep(0.001)
+    # timed stream
+    t0 = time.perf_counter()
+    tickets, submitted = {}, 0
+    done = {}
+    while len(done) < n:
+        now = time.perf_counter() - t0
+        while submitted < n and arrivals[submitted] <= now:
+            kind, w = specs[submitted]
+            inp, out, aux = bufs[submitted]
+            tickets[srv.submit(kind, dgw.mesh_params(w), inp, out, aux=aux, mode=1)] = submitted
+            submitted += 1
+        for t in list(tickets):
+            r = srv.poll(t)
+            if r is not None:
+                j = tickets.pop(t)
+                done[j] = (r, time.perf_counter() - t0)
+        time.sleep(0.0002)
+    makespan = max(v[1] for v in done.values())
+    lat = np.array([1e3 * (done[j][1] - arrivals[j]) for j in range(n)])
+    ok = all(done[j][0]["status"] == 0 for j in range(n))
+    n_solves = sum(1 for kind, _ in specs if kind == 0)
+    srv.close()
+    # one at a time, FP64 solves
+    meshes = {}
+    t1 = time.perf_counter()
+    for j, (kind, w) in enumerate(specs):
+        key = (w.nx, w.k)
+        if key not in meshes:
+            meshes[key] = dgw.mesh_for(w)
+        m = meshes[key]
+        inp, out, aux = bufs[j]
+        if kind == 0:
+            m.pressure_solve(inp, out, rtol=1e-10, max_iter=500, mode=0)
+        elif kind == 1:
+            m.laplace(inp, out)
+        elif kind == 2:
+            m.divergence(inp, out)
+        elif kind == 3:
+            m.convective(inp, out)
+        else:
+            m.update_eddy_viscosity(aux)
+            m.viscous(inp, out)
+        torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    line = {"metric": "serving: p50/p99 latency and solves/s (mixed, request loop) vs one-at-a-time FP64",
+            "jobs": n, "solves": n_solves, "rate_per_s": args.rate, "slots": args.serving_slots,
+            "all_ok": ok, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": n_solves / makespan, "makespan_s": makespan,
+            "sequential_fp64_solves_per_s": n_solves / seq, "sequential_s": seq,
+            "note": "sequential FP64 includes first-use multigrid setup of each mesh"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,7 +466,14 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None)
+    ap.add_argument("--serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=400)
+    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--serving-budget-gb", type=float, default=120.0)
+    ap.add_argument("--rate", type=float, default=200.0)
     args = ap.parse_args()
+    if args.serving:
+        return run_serving(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -162,6 +162,43 @@ dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t mesh, const double *b, d
 dgw_status dgw_solver_describe(dgw_mesh_t mesh, int mode, int *n_levels, double *lmax, int *cells, int max_levels,
                                void *stream);
 
+/* ---- Request loop (serving) --------------------------------------------------------------
+ * No counterpart in the paper: a service for running many independent jobs. Jobs of any mesh size
+ * and degree are admitted as worker slots and device memory free up; each job runs on a resident
+ * mesh with its parameters (created on first use, kept for later jobs, at most one job per mesh
+ * instance at a time, idle meshes evicted least-recently-used when the HBM budget is short), and
+ * each worker has its own CUDA stream, so concurrent jobs overlap on the device. Results do not
+ * depend on the mix (jobs share no scratch; all kernels and reductions are deterministic). */
+enum { DGW_JOB_SOLVE = 0, DGW_JOB_LAPLACE = 1, DGW_JOB_DIVERGENCE = 2, DGW_JOB_CONVECTIVE = 3, DGW_JOB_VISCOUS = 4 };
+
+typedef struct {
+  int kind;               /* DGW_JOB_* */
+  int prec;               /* applies: DGW_FP64 or DGW_FP32 (divergence and solves are FP64) */
+  dgw_mesh_params mesh;   /* mesh of the job (meshes are cached by these parameters) */
+  const void *in;         /* caller-owned device input: b (solve), p (Laplace), u (other applies) */
+  void *out;              /* caller-owned device output: p (solve) or y */
+  const double *aux;      /* viscous only: FP64 velocity (n_u) that freezes nu_t before the apply;
+                             NULL keeps the mesh's current nu_t */
+  dgw_solve_opts opts;    /* solves only */
+} dgw_job;
+
+/* Start a request loop with `max_inflight` worker slots (1..64) and a device-memory budget for
+ * resident meshes and solver state. */
+dgw_status dgw_server_create(size_t hbm_budget, int max_inflight, dgw_server_t *out);
+/* Queue a job. Its input must be complete on the device when submitted (synchronise the stream
+ * that produced it); in, out and aux must stay valid until dgw_poll reports completion. A viscous
+ * job with aux != NULL first freezes nu_t from aux (dgw_update_eddy_viscosity), then applies. */
+dgw_status dgw_submit(dgw_server_t server, const dgw_job *job, long *ticket);
+/* Non-blocking. Returns DGW_EBUSY (and *job_status = DGW_EBUSY) while the job is queued or running;
+ * otherwise DGW_OK with the job's own status (DGW_ENOMEM if it can never fit the budget), the solve
+ * info (solves) and the submit-to-completion latency. A completed ticket is reported once. */
+dgw_status dgw_poll(dgw_server_t server, long ticket, dgw_status *job_status, dgw_solve_info *info, double *latency_ms);
+/* Queue depth, running jobs, resident meshes and reserved device bytes. */
+dgw_status dgw_server_stats(dgw_server_t server, int *queued, int *running, int *resident_meshes, size_t *reserved_bytes);
+/* Cancel queued jobs and wait up to timeout_ms for running ones; on DGW_ETIMEOUT the server stays
+ * alive (running jobs still own their streams) and may be destroyed again later. */
+dgw_status dgw_server_destroy(dgw_server_t server, int timeout_ms);
+
 /* Thread-local description of the last error. */
 const char *dgw_last_error(void);
 

@@ -18,7 +18,10 @@ STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -
 EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
-           "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc"]
+           "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
+           "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy"]
+
+JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
 
 class DGWError(RuntimeError):
@@ -39,6 +42,11 @@ class MeshParams(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("prec", ctypes.c_int), ("mesh", MeshParams),
+                ("inp", ctypes.c_void_p), ("out", ctypes.c_void_p), ("aux", ctypes.c_void_p), ("opts", SolveOpts)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -72,6 +80,13 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp]
     lib.dgw_pressure_solve_jacobi_noalloc.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int,
                                                       ctypes.POINTER(SolveInfo), vp]
+    lib.dgw_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.dgw_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_long)]
+    lib.dgw_poll.argtypes = [vp, ctypes.c_long, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SolveInfo),
+                             ctypes.POINTER(ctypes.c_double)]
+    lib.dgw_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
+    lib.dgw_server_destroy.argtypes = [vp, ctypes.c_int]
     lib.dgw_last_error.restype = ctypes.c_char_p
     lib.dgw_counters.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.dgw_counters.restype = None
@@ -191,6 +206,51 @@ def describe_solver(mesh, mode=1):
     cells = (ctypes.c_int * 32)()
     _check(lib.dgw_solver_describe(mesh.h, mode, ctypes.byref(nl), lm, cells, 32, None))
     return [(cells[i], lm[i]) for i in range(min(nl.value, 32))]
+
+
+class Server:
+    """Request loop: jobs (solves and applies on any channel mesh) admitted as worker slots and
+    device memory free up; concurrent jobs overlap on the device."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=4):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.dgw_server_create(int(hbm_budget_bytes), int(max_inflight), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, kind, params: MeshParams, inp, out, prec=DGW_FP64, rtol=1e-10, max_iter=500, mode=1,
+               cheb_degree=5, aux=None):
+        job = Job(kind, prec, params, ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                  ctypes.c_void_p(aux.data_ptr() if aux is not None else 0), SolveOpts(rtol, max_iter, mode, cheb_degree))
+        t = ctypes.c_long()
+        _check(self.lib.dgw_submit(self.h, ctypes.byref(job), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else dict(status, iterations, rel_residual, latency_ms)."""
+        st, info, lat = ctypes.c_int(), SolveInfo(), ctypes.c_double()
+        r = self.lib.dgw_poll(self.h, int(ticket), ctypes.byref(st), ctypes.byref(info), ctypes.byref(lat))
+        if r == -5:
+            return None
+        _check(r)
+        return {"status": st.value, "iterations": info.iterations, "rel_residual": info.rel_residual,
+                "latency_ms": lat.value}
+
+    def stats(self):
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(self.lib.dgw_server_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return {"queued": a.value, "running": b.value, "meshes": c.value, "reserved_bytes": d.value}
+
+    def close(self, timeout_ms=60000):
+        if getattr(self, "h", None):
+            _check(self.lib.dgw_server_destroy(self.h, int(timeout_ms)))
+            self.h = None
+
+
+def mesh_params(workload, n_layers=1, q_wall=8, wall_law=0, fp32=True) -> MeshParams:
+    return MeshParams(workload.nx, workload.ny, workload.nz, workload.k, 1, q_wall, 0, wall_law, n_layers,
+                      workload.lx, workload.ly, workload.lz, workload.gamma, workload.nu, workload.tau_w,
+                      3 if fp32 else 1)
 
 
 def counters():
