@@ -130,6 +130,9 @@ void box_geometry(int k, int nx, int ny, int nz, double lx, double lz, const std
 void laplace_diagonal(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &dg);
 // Per-row 1-D operators of the factorised SIPG Laplacian on boxes.
 void box_rowops(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &R);
+// Host evaluation of the same factorised operator (small coarse-level matrices).
+void host_box_apply(const BoxGeometry &g, const Basis<double> &B, const std::vector<double> &R, const double *x,
+                    double *y);
 
 // kernels (launched by api.cu)
 template <typename T>

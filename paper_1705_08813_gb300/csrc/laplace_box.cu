@@ -20,9 +20,16 @@ namespace dgw {
 // Per-row operator layout: Lx, Ly, Lz (n*n each), then for d in {x,y,z}, s in {0,1}: c1[n], c2[n].
 __host__ __device__ constexpr int rowops_size(int n) { return 3 * n * n + 12 * n; }
 
+// FP32: up to 3 CTAs of <= 256 threads per SM for k <= 4 (register budget ~85/thread), 2 for k = 5;
+// FP64 is FP64-pipe bound and keeps the default budget.
 template <typename T, int K>
-__global__ void __launch_bounds__(256) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p, T *__restrict__ y,
-                                                          int cpb) {
+struct BoxOcc { static constexpr int min_blocks = 1; };
+template <int K>
+struct BoxOcc<float, K> { static constexpr int min_blocks = K <= 4 ? 3 : 2; };
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p,
+                                                                                T *__restrict__ y, int cpb) {
   constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
   constexpr int ROW = rowops_size(n);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -221,6 +228,8 @@ static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, cudaStre
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(laplace_box_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e == cudaSuccess)   // the whole unified L1/shared array as shared memory: more CTAs per SM
+      e = cudaFuncSetAttribute(laplace_box_kernel<T, K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -295,6 +304,69 @@ void box_rowops(const BoxGeometry &g, const Basis<double> &B, std::vector<double
       }
     }
   }
+}
+
+// Host reference of the same factorised operator (assembles small coarse-level matrices).
+void host_box_apply(const BoxGeometry &g, const Basis<double> &B, const std::vector<double> &R, const double *x,
+                    double *y) {
+  const int n = g.k + 1, n2 = n * n, n3 = n2 * n, ROW = rowops_size(n);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  std::vector<double> v(n3), w(n3);
+  auto idx = [&](int d, int a, int t1, int t2) {   // local index with coordinate a along d
+    int c[3];
+    const int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
+    c[d] = a; c[o1] = t1; c[o2] = t2;
+    return c[0] + n * (c[1] + n * c[2]);
+  };
+  for (int kz = 0; kz < nz; ++kz)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const size_t c = i + (size_t)nx * (j + (size_t)ny * kz);
+        const double *u = x + c * n3;
+        const double *Rj = R.data() + (size_t)j * ROW;
+        double *yc = y + c * n3;
+        for (int t = 0; t < n3; ++t) yc[t] = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double *L = Rj + d * n2;
+          for (int t2 = 0; t2 < n; ++t2)
+            for (int t1 = 0; t1 < n; ++t1)
+              for (int a = 0; a < n; ++a) {
+                double sum = 0.0;
+                for (int b = 0; b < n; ++b) sum += L[a * n + b] * u[idx(d, b, t1, t2)];
+                v[idx(d, a, t1, t2)] = sum;
+              }
+          for (int sd = 0; sd < 2; ++sd) {
+            int ii = i, jj = j, kk = kz;
+            const int sg = sd ? 1 : -1;
+            if (d == 0) ii = (i + sg + nx) % nx;
+            else if (d == 2) kk = (kz + sg + nz) % nz;
+            else { jj = j + sg; if (jj < 0 || jj >= ny) continue; }
+            const double *un = x + (ii + (size_t)nx * (jj + (size_t)ny * kk)) * n3;
+            const double *c1 = Rj + 3 * n2 + (d * 2 + sd) * 2 * n, *c2 = c1 + n;
+            const int ep = sd ? 0 : 1, lay = ep ? n - 1 : 0;
+            for (int t2 = 0; t2 < n; ++t2)
+              for (int t1 = 0; t1 < n; ++t1) {
+                const double tv = un[idx(d, lay, t1, t2)];
+                double td = 0.0;
+                for (int b = 0; b < n; ++b) td += B.dend[ep][b] * un[idx(d, b, t1, t2)];
+                for (int a = 0; a < n; ++a) v[idx(d, a, t1, t2)] += c1[a] * tv + c2[a] * td;
+              }
+          }
+          // M along the two other directions
+          for (int e = 0; e < 3; ++e) {
+            if (e == d) continue;
+            for (int t2 = 0; t2 < n; ++t2)
+              for (int t1 = 0; t1 < n; ++t1)
+                for (int a = 0; a < n; ++a) {
+                  double sum = 0.0;
+                  for (int b = 0; b < n; ++b) sum += B.mass[a * n + b] * v[idx(e, b, t1, t2)];
+                  w[idx(e, a, t1, t2)] = sum;
+                }
+            v.swap(w);
+          }
+          for (int t = 0; t < n3; ++t) yc[t] += v[t];
+        }
+      }
 }
 
 }  // namespace dgw

@@ -19,6 +19,7 @@ namespace dgw {
 constexpr double kSmoothRange = 15.0;   // Chebyshev smooths [1.2 lmax/15, 1.2 lmax]
 constexpr int kCoarseIters = 24;       // PCG steps on the coarsest level
 constexpr int kLanczos = 24;           // CG-Lanczos steps for lmax(D^-1 A)
+constexpr long kDenseMax = 1000;       // coarsest systems up to this size are solved densely
 
 // ------------------------------------------------------------------------------------------
 // vector kernels (templated on the level precision; reductions accumulate in double)
@@ -230,6 +231,90 @@ __global__ void restrict_kernel(const Basis<T> *Bg, XferDims X, const T *__restr
   for (int t = threadIdx.x; t < n3; t += blockDim.x) rc[(size_t)cc * n3 + t] = Acc[t];
 }
 
+// p-transfer between Q_k and Q_1 on the same cells: P1[i*2 + j] = linear Lagrange j at the
+// Gauss-Lobatto node z_i of degree k (prolongation: nodal interpolation, restriction: transpose).
+template <typename T>
+__global__ void p_prolongate_add(const T *__restrict__ P1, int n, const T *__restrict__ x1, T *__restrict__ xk) {
+  __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX], Pm[NMAX * 2];
+  const int c = blockIdx.x, n3 = n * n * n;
+  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) Pm[t] = P1[t];
+  for (int t = threadIdx.x; t < 8; t += blockDim.x) A[t] = x1[(size_t)c * 8 + t];
+  __syncthreads();
+  axis_pass(A, Bv, 2, 2, 2, 0, Pm, 2, n, false, false);
+  __syncthreads();
+  axis_pass(Bv, A, n, 2, 2, 1, Pm, 2, n, false, false);
+  __syncthreads();
+  axis_pass(A, Bv, n, n, 2, 2, Pm, 2, n, false, false);
+  __syncthreads();
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) xk[(size_t)c * n3 + t] += Bv[t];
+}
+
+template <typename T>
+__global__ void p_restrict(const T *__restrict__ P1, int n, const T *__restrict__ rk, T *__restrict__ r1) {
+  __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX], Pm[NMAX * 2];
+  const int c = blockIdx.x, n3 = n * n * n;
+  for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) Pm[t] = P1[t];
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = rk[(size_t)c * n3 + t];
+  __syncthreads();
+  axis_pass(A, Bv, n, n, n, 0, Pm, 2, n, true, false);
+  __syncthreads();
+  axis_pass(Bv, A, 2, n, n, 1, Pm, 2, n, true, false);
+  __syncthreads();
+  axis_pass(A, Bv, 2, 2, n, 2, Pm, 2, n, true, false);
+  __syncthreads();
+  for (int t = threadIdx.x; t < 8; t += blockDim.x) r1[(size_t)c * 8 + t] = Bv[t];
+}
+
+// x = Ainv b (one warp per row, lanes stride the row)
+template <typename T>
+__global__ void dense_gemv(const T *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x, int N) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  const T *row = Ainv + (size_t)warp * N;
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32) s += (double)row[j] * (double)b[j];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) x[warp] = (T)s;
+}
+
+// Inverse of A + c 1 1^T (SPD when the null space of A is the constants; on zero-mean right-hand
+// sides it acts as the pseudo-inverse of A and returns zero-mean solutions). Cholesky, in place.
+static bool dense_regularised_inverse(std::vector<double> &A, int N) {
+  double tr = 0.0;
+  for (int i = 0; i < N; ++i) tr += A[(size_t)i * N + i];
+  const double c = tr / N;
+  for (size_t i = 0; i < (size_t)N * N; ++i) A[i] += c / N;
+  std::vector<double> Lf(A);
+  for (int j = 0; j < N; ++j) {
+    double d = Lf[(size_t)j * N + j];
+    for (int k = 0; k < j; ++k) d -= Lf[(size_t)j * N + k] * Lf[(size_t)j * N + k];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    Lf[(size_t)j * N + j] = d;
+    for (int i = j + 1; i < N; ++i) {
+      double v = Lf[(size_t)i * N + j];
+      for (int k = 0; k < j; ++k) v -= Lf[(size_t)i * N + k] * Lf[(size_t)j * N + k];
+      Lf[(size_t)i * N + j] = v / d;
+    }
+  }
+  // inverse column by column: L L^T x = e_col
+  std::vector<double> col(N);
+  for (int cidx = 0; cidx < N; ++cidx) {
+    for (int i = 0; i < N; ++i) {
+      double v = i == cidx ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= Lf[(size_t)i * N + k] * col[k];
+      col[i] = v / Lf[(size_t)i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      double v = col[i];
+      for (int k = i + 1; k < N; ++k) v -= Lf[(size_t)k * N + i] * col[k];
+      col[i] = v / Lf[(size_t)i * N + i];
+    }
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + cidx] = col[i];
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------------------------------
 // hierarchy
 // ------------------------------------------------------------------------------------------
@@ -243,6 +328,8 @@ struct Lvl {
   double *sc = nullptr, *partial = nullptr;
   double lmax = 1.0;
   XferDims to_coarse{};   // transfer to the next coarser level
+  const T *p1 = nullptr;  // when set: the next level is Q_1 on the same cells (p-transfer table)
+  const T *ainv = nullptr; // coarsest level solved densely with this inverse (N = n)
   std::vector<void *> allocs;
 };
 
@@ -454,6 +541,65 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       yv.swap(yc);
     }
   }
+  if (e != cudaSuccess) return e;
+  // coarsest level: dense solve at degree k, or one more level with Q_1 on the same cells solved
+  // densely, or (too large for either) the iterative coarse PCG
+  Lvl<T> *C = H->L.back();
+  const long cells = (long)C->geo.nx * C->geo.ny * C->geo.nz;
+  int kd = -1;
+  if (C->n <= kDenseMax) kd = k;
+  else if (k > 1 && cells * 8 <= kDenseMax) kd = 1;
+  if (kd < 0) return e;
+  Lvl<T> *D = C;
+  Basis<double> b1d;
+  const Basis<double> *Bd = &M->basis64;
+  if (kd == 1) {
+    D = new Lvl<T>();
+    H->L.push_back(D);
+    box_geometry(1, C->geo.nx, C->geo.ny, C->geo.nz, M->P.lx, M->P.lz, C->geo.yv, D->geo);
+    D->n = cells * 8;
+    fill_basis<double>(1, 2, M->P.q_wall, &b1d);
+    Bd = &b1d;
+    // transfer table P1 (n x 2): linear functions at the degree-k Gauss-Lobatto nodes
+    std::vector<double> P1(2 * n);
+    {
+      double z[NMAX], w[NMAX];
+      lobatto_nodes(n, z);
+      (void)w;
+      for (int i = 0; i < n; ++i) { P1[2 * i] = 1.0 - z[i]; P1[2 * i + 1] = z[i]; }
+    }
+    std::vector<T> P1T(P1.begin(), P1.end());
+    T *p1d = lalloc<T>(C, P1T.size(), e, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p1d, P1T.data(), P1T.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    C->p1 = p1d;
+    D->view = C->view;
+    D->view.n1 = 2;
+    D->view.np = D->n;
+    D->x = lalloc<T>(D, D->n, e, s); D->b = lalloc<T>(D, D->n, e, s);
+    void *p = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * sizeof(double), s);
+    if (e == cudaSuccess) { D->allocs.push_back(p); D->sc = (double *)p; }
+    if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
+    if (e == cudaSuccess) { D->allocs.push_back(p); D->partial = (double *)p; }
+  }
+  // assemble the level operator on the host column by column, invert A + c 1 1^T
+  const int N = (int)D->n;
+  std::vector<double> rops;
+  box_rowops(D->geo, *Bd, rops);
+  std::vector<double> A((size_t)N * N), ej(N, 0.0), col(N);
+  for (int jc = 0; jc < N; ++jc) {
+    ej[jc] = 1.0;
+    host_box_apply(D->geo, *Bd, rops, ej.data(), col.data());
+    ej[jc] = 0.0;
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + jc] = col[i];
+  }
+  if (!dense_regularised_inverse(A, N)) return e;   // keep the iterative coarse solve
+  std::vector<T> AT(A.begin(), A.end());
+  T *ad = lalloc<T>(D, AT.size(), e, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ad, AT.data(), AT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  D->ainv = ad;
   return e;
 }
 
@@ -480,6 +626,14 @@ template <typename T>
 static void coarse_solve(Lvl<T> *L, cudaStream_t s) {
   const long n = L->n;
   const int G = mg_grid(n);
+  if (L->ainv) {
+    // consistent right-hand side, then the exact (pseudo-)inverse
+    mg_reduce<T>(L->b, nullptr, n, L->partial, L->sc, MS_SUM, s);
+    note_launches(2);
+    sub_mean_T<T><<<G, 256, 0, s>>>(L->b, n, L->sc, MS_SUM);
+    dense_gemv<T><<<(int)((n * 32 + 255) / 256), 256, 0, s>>>(L->ainv, L->b, L->x, (int)n);
+    return;
+  }
   cudaMemsetAsync(L->x, 0, n * sizeof(T), s);
   // the coarse problem is singular (constants): make its right-hand side consistent
   mg_reduce<T>(L->b, nullptr, n, L->partial, L->sc, MS_SUM, s);
@@ -517,10 +671,12 @@ static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
   note_launch();
   residual_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(L->r, L->b, L->t, L->n);
   note_launch();
-  restrict_kernel<T><<<C->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, L->r, C->b);
+  if (L->p1) p_restrict<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, L->r, C->b);
+  else restrict_kernel<T><<<C->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, L->r, C->b);
   vcycle(H, lev + 1, s);
   note_launch();
-  prolongate_add<T><<<L->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, C->x, L->x);
+  if (L->p1) p_prolongate_add<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, C->x, L->x);
+  else prolongate_add<T><<<L->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, C->x, L->x);
   chebyshev(H, L, false, s);
 }
 
