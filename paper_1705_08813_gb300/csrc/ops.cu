@@ -1,13 +1,18 @@
-// Matrix-free DG operator kernels on the channel of boxes (one CTA per cell, shared-memory
-// sum factorisation; Sec. 4.4). Every CTA evaluates the volume integral of its cell and the
-// integrals over its six faces for its own test functions, re-reading the neighbour's
-// coefficients (cell-centric face loop: no atomics, deterministic).
+// Matrix-free DG vector operators on the channel of boxes, with enriched wall cells (Sec. 4.2,
+// Sec. 4.4): one CTA per cell evaluates the volume integral of its cell and the integrals over its
+// six faces for its own test functions, re-reading the neighbours' coefficients (cell-centric face
+// loop: no atomics, deterministic).
 //
-//   vector_op_kernel : OP_DIV  b = -C(q,u)                   (Sec. 4.2, velocity divergence)
-//                      OP_CONV y = F^c(v,u), LF flux          (Sec. 4.2, convective term)
-//                      OP_VISC y = -F^nu(vbar,v~;ubar,u~)     (eq. viscous_multiscale)
+//   OP_DIV  b = -C(q,u)                   (Sec. 4.2, velocity divergence; {{u}} = u^- on walls)
+//   OP_CONV y = F^c(v,u), LF flux         (Sec. 4.2, convective term; mirror state on walls)
+//   OP_VISC y = -F^nu(vbar,v~;ubar,u~)    (eq. viscous_multiscale, harmweights, minvt)
+//
 // Wall-layer cells add the enrichment u~ = psi sum_B N_B u~_B (eq. enrichment) at q_wall
 // wall-normal Gauss points, with psi and grad psi read from the wall tables.
+//
+// Every sum-factorisation phase is batched over the three velocity components, over both faces
+// normal to one direction and over both sides of those faces, so one barrier separates phases
+// that each carry enough independent outputs to occupy the CTA (about 35 barriers per cell).
 #include "sumfac.cuh"
 
 namespace dgw {
@@ -49,43 +54,108 @@ __device__ void load_basis(const Basis<T> *g, Basis<T> *s) {
   for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = src[t];
 }
 
-// ------------------------------------------------------------------------------------------
-// Vector operators (divergence, convective, viscous) with enriched wall cells
-// ------------------------------------------------------------------------------------------
-
-struct VecLayout {
-  int n, n3, P, FP, tsz;
-  // offsets in T words
-  int uo, un, r, eo, en, re, vol, face, tmp, total;
+// One term or the sum of two terms (same output shape) of a 1-D pass.
+template <typename T>
+struct Pass {
+  const T *in;
+  const T *M;
+  const T *in2;
+  const T *M2;
+  T *out;
 };
 
-__host__ __device__ inline VecLayout vec_layout(int op, int n, int qin, int qw) {
-  VecLayout L;
-  L.n = n;
-  L.n3 = n * n * n;
-  const int qy = qw > qin ? qw : qin;
-  L.P = qin * qy * qin;
-  L.FP = qin * qy;
-  const int qm = qy > n ? qy : n;
-  int a = qin * n * n, b = qin * qy * n, c = n * (n > qm ? n : qm);
-  L.tsz = 5 * (a > b ? (a > c ? a : c) : (b > c ? b : c));
+// nb independent passes along axis ax over arrays of input dims (s0, s1, s2); desc(b) returns the
+// b-th pass. Matrices are stored q x n (points x nodes): forward maps nodes -> points, trans maps
+// points -> nodes. acc adds into the output. Ends with a barrier.
+template <typename T, typename F>
+__device__ void pass_batch(F desc, int nb, int s0, int s1, int s2, int ax, int n, int q, bool trans, bool acc) {
+  const int mi = trans ? q : n, mo = trans ? n : q;
+  const int o0 = ax == 0 ? mo : s0, o1 = ax == 1 ? mo : s1, o2 = ax == 2 ? mo : s2;
+  const int size = o0 * o1 * o2;
+  const int stride = ax == 0 ? 1 : (ax == 1 ? s0 : s0 * s1);
+  for (int t = threadIdx.x; t < nb * size; t += blockDim.x) {
+    const int b = t / size, e = t - b * size;
+    const int i0 = e % o0, i1 = (e / o0) % o1, i2 = e / (o0 * o1);
+    const int r = ax == 0 ? i0 : (ax == 1 ? i1 : i2);
+    const int base = (ax == 0 ? 0 : i0) + s0 * ((ax == 1 ? 0 : i1) + s1 * (ax == 2 ? 0 : i2));
+    const Pass<T> d = desc(b);
+    T sum = T(0);
+    if (!trans) {
+      const T *row = d.M + r * n;
+      for (int c = 0; c < mi; ++c) sum += row[c] * d.in[base + c * stride];
+      if (d.in2) {
+        const T *row2 = d.M2 + r * n;
+        for (int c = 0; c < mi; ++c) sum += row2[c] * d.in2[base + c * stride];
+      }
+    } else {
+      for (int c = 0; c < mi; ++c) sum += d.M[c * n + r] * d.in[base + c * stride];
+      if (d.in2)
+        for (int c = 0; c < mi; ++c) sum += d.M2[c * n + r] * d.in2[base + c * stride];
+    }
+    d.out[e] = acc ? d.out[e] + sum : sum;
+  }
+  __syncthreads();
+}
+
+// Shared-memory plan (in T words) for one cell. The volume and face phases share one work
+// region; inside the face region the neighbour coefficients share room with the arrays written
+// after the layer traces are taken, and the integration arrays with the trace arrays.
+struct VecPlan {
+  int n, n3, qi, qy, P, FP, pn;   // pn = largest (face points along t1) x n
+  int uo, r, eo, re, en, work, total;
+  int vA, vB, vV, vG, vGt, vol_end;                                               // volume regions
+  int fV2, fN2, fA0, fA1, fB0, fTr, fC, fE, fUn, fI0, fI1, fI2, fF2, fG2, face_end;  // face regions
+};
+
+__host__ __device__ inline VecPlan vec_plan(int op, int n, int qin, int qw) {
+  VecPlan p;
+  p.n = n;
+  p.n3 = n * n * n;
+  p.qi = qin;
+  p.qy = qw > qin ? qw : qin;
+  p.P = qin * p.qy * qin;
+  p.FP = qin * p.qy;
+  p.pn = p.qy * n;
+  const int nn = n * n;
+  const int SX = qin * nn, SZ = qin * p.qy * n;
   int o = 0;
-  L.uo = o; o += 3 * L.n3;
-  L.un = o; o += 3 * L.n3;
-  L.r = o; o += 3 * L.n3;
-  L.eo = o; o += 24;
-  L.en = o; o += 24;
-  L.re = o; o += 24;
-  L.vol = o;
-  // volume arrays: DIV 3 (U) + 3 (H); CONV 3 (U) + 9 (H); VISC 9 (Gb/H) + 9 (Gt)
-  o += (op == OP_DIV ? 6 : (op == OP_CONV ? 12 : 18)) * L.P;
-  L.face = o;
-  // face arrays: per side 3 values + 9 gradients (VISC) or 3 values; coefficients 12 + enriched 12
-  o += (op == OP_VISC ? (2 * 12 + 12 + 12) : (2 * 3 + 4 + 3)) * L.FP;
-  L.tmp = o;
-  o += L.tsz;
-  L.total = o;
-  return L;
+  p.uo = o; o += 3 * p.n3;
+  p.r = o; o += 3 * p.n3;
+  p.eo = o; o += 24;
+  p.re = o; o += 24;
+  p.en = o; o += 48;   // enrichment coefficients of the two neighbours of one direction
+  p.work = o;
+  int v = o;
+  p.vA = v; v += 6 * SX;
+  p.vB = v; v += 9 * SZ;
+  p.vV = v; v += (op == 2 ? 0 : 3 * p.P);
+  p.vG = v; v += 9 * p.P;
+  p.vGt = v; v += (op == 2 ? 9 * p.P : 0);
+  p.vol_end = v;
+  int f = o;   // 12 trace slots: 2 faces x 2 sides x 3 components
+  p.fV2 = f; f += 12 * nn;
+  p.fN2 = f; f += 12 * nn;
+  p.fA0 = f; f += 12 * p.pn;
+  p.fA1 = f; f += 12 * p.pn;
+  p.fB0 = f; f += 12 * p.pn;
+  p.fTr = f; f += 12 * 4 * p.FP;     // value, d/dxi_d, d/dxi_t1, d/dxi_t2
+  p.fC = f; f += 2 * 3 * 4 * p.FP;   // coefficients of the standard test functions (face, component)
+  p.fE = f; f += 2 * 3 * 4 * p.FP;   // coefficients of the enriched test functions
+  p.face_end = f;
+  // both neighbours' coefficients: dead once the layers are taken (only en must survive)
+  p.fUn = p.fA0;
+  if (p.fUn + 6 * p.n3 > p.face_end) p.face_end = p.fUn + 6 * p.n3;
+  // integration arrays: written after the traces are consumed, must not reach the coefficients C
+  const int isz = 18 * p.pn + 12 * nn;
+  int g = p.fV2 + isz <= p.fC ? p.fV2 : p.face_end;
+  p.fI0 = g; g += 6 * p.pn;
+  p.fI1 = g; g += 6 * p.pn;
+  p.fI2 = g; g += 6 * p.pn;
+  p.fF2 = g; g += 6 * nn;
+  p.fG2 = g; g += 6 * nn;
+  if (g > p.face_end) p.face_end = g;
+  p.total = p.vol_end > p.face_end ? p.vol_end : p.face_end;
+  return p;
 }
 
 template <typename T, int OP>
@@ -94,279 +164,291 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   Basis<T> &B = *reinterpret_cast<Basis<T> *>(smem_raw);
   T *S0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Basis<T>) + 15) / 16) * 16);
   load_basis(m.basis, &B);
-  __syncthreads();
-  const int n = m.n1;
+  const int n = m.n1, nn = n * n;
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const int opc = OP == OP_CONV ? 1 : 0;   // wall-table class
-  const int qin = B.q[qset], qw = B.q[QSET_WALL];
-  const VecLayout L = vec_layout(OP, n, qin, qw);
+  const VecPlan L = vec_plan(OP, n, m.q[qset], m.q[QSET_WALL]);
   const int n3 = L.n3;
-  T *uo = S0 + L.uo, *un = S0 + L.un, *r = S0 + L.r, *eo = S0 + L.eo, *en = S0 + L.en, *re = S0 + L.re;
-  T *tmp = S0 + L.tmp;
+  const int ncomp = OP == OP_DIV ? 1 : 3;
+  constexpr bool GRAD = OP == OP_VISC;
+  T *uo = S0 + L.uo, *r = S0 + L.r, *eo = S0 + L.eo, *re = S0 + L.re, *un = S0 + L.fUn, *en = S0 + L.en;
   const int c = blockIdx.x;
   const int ec = m.enr[c];
   const bool enr_c = ec >= 0;
-  const int ncomp_out = OP == OP_DIV ? 1 : 3;
   const T nu = m.visc;
-  // load own coefficients
   for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) {
     uo[t] = u[(size_t)c * 3 * n3 + t];
     r[t] = T(0);
   }
-  if (enr_c)
-    for (int t = threadIdx.x; t < 24; t += blockDim.x) { eo[t] = u[3 * m.np + (size_t)ec * 24 + t]; re[t] = T(0); }
+  for (int t = threadIdx.x; t < 24; t += blockDim.x) {
+    eo[t] = enr_c ? u[3 * m.np + (size_t)ec * 24 + t] : T(0);
+    re[t] = T(0);
+  }
   __syncthreads();
   const T h[3] = {m.hx, m.hy[(c / m.nx) % m.ny], m.hz};
   const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
-  const int ys = enr_c ? QSET_WALL : qset;
-  AxisTabs<T> tabs;
-  const int sets[3] = {qset, ys, qset};
-  for (int d = 0; d < 3; ++d) { tabs.S[d] = B.S[sets[d]]; tabs.D[d] = B.D[sets[d]]; tabs.q[d] = B.q[sets[d]]; }
-  const int q0 = tabs.q[0], q1 = tabs.q[1], q2 = tabs.q[2];
+  const int sets[3] = {qset, enr_c ? QSET_WALL : qset, qset};
+  const int q0 = B.q[sets[0]], q1 = B.q[sets[1]], q2 = B.q[sets[2]];
   const int P = q0 * q1 * q2;
   const T vol = h[0] * h[1] * h[2];
   const T *wtv = enr_c ? m.wt_vol[opc] + (size_t)ec * m.nvol[opc] * WT : nullptr;
+  const T *S_[3] = {B.S[sets[0]], B.S[sets[1]], B.S[sets[2]]};
+  const T *D_[3] = {B.D[sets[0]], B.D[sets[1]], B.D[sets[2]]};
 
-  // ---------------- volume ----------------
-  T *V = S0 + L.vol;
-  if (OP == OP_DIV || OP == OP_CONV) {
-    T *U = V;            // 3 x P values
-    T *H = V + 3 * L.P;  // DIV: 3 x P ; CONV: 9 x P
-    for (int a = 0; a < 3; ++a) eval_cell(uo + a * n3, n, tabs, U + a * L.P, (T *)nullptr, (T *)nullptr, (T *)nullptr, tmp);
+  // ================= volume =================
+  {
+    T *A = S0 + L.vA, *Bv = S0 + L.vB, *V = S0 + L.vV, *G = S0 + L.vG, *Gt = S0 + L.vGt;
+    const int SX = q0 * nn, SZ = q0 * q1 * n;
+    // P1: X0_a = S_x u_a (and X1_a = D_x u_a for gradients)
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int a = b % 3, k = b / 3;
+      return {uo + a * n3, k ? D_[0] : S_[0], nullptr, nullptr, A + b * SX};
+    }, GRAD ? 6 : 3, n, n, n, 0, n, q0, false, false);
+    // P2: Y00_a = S_y X0_a (Y01_a = D_y X0_a, Y10_a = S_y X1_a)
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int a = b % 3, k = b / 3;   // k: 0 Y00, 1 Y01, 2 Y10
+      return {A + (k == 2 ? 3 + a : a) * SX, k == 1 ? D_[1] : S_[1], nullptr, nullptr, Bv + b * SZ};
+    }, GRAD ? 9 : 3, q0, n, n, 1, n, q1, false, false);
+    // P3: values (DIV, CONV) or reference gradients (VISC) at the points
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int a = b % 3, k = b / 3;
+      if (!GRAD) return {Bv + a * SZ, S_[2], nullptr, nullptr, V + a * P};
+      // k = 0: d/dz from Y00; 1: d/dy from Y01; 2: d/dx from Y10
+      return {Bv + b * SZ, k == 0 ? D_[2] : S_[2], nullptr, nullptr, G + (a * 3 + 2 - k) * P};
+    }, GRAD ? 9 : 3, q0, q1, n, 2, n, q2, false, false);
+    // P4: pointwise test-function coefficients (H_{a,d} multiplies d phi / d xi_d)
+    const T *nutv = (OP == OP_VISC && enr_c) ? m.nut_vol + (size_t)ec * m.nvol[0] : nullptr;
     for (int t = threadIdx.x; t < P; t += blockDim.x) {
       const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-      T uu[3] = {U[t], U[L.P + t], U[2 * L.P + t]};
-      if (enr_c) {
-        const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
-        T N[8], dN[8][3];
-        q1_weights(xi, N, dN);
-        const T psi = wtv[t * WT];
-        for (int a = 0; a < 3; ++a) {
-          T s = T(0);
-          for (int v = 0; v < 8; ++v) s += N[v] * eo[a * 8 + v];
-          uu[a] += psi * s;
-          U[a * L.P + t] = uu[a];
-        }
-      }
       const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
-      if (OP == OP_DIV) {
-        for (int d = 0; d < 3; ++d) H[d * L.P + t] = dV * uu[d] * hinv[d];
-      } else {
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) H[(a * 3 + d) * L.P + t] = -dV * uu[a] * uu[d] * hinv[d];
-      }
-    }
-    __syncthreads();
-    if (OP == OP_DIV) {
-      integrate_cell((const T *)nullptr, H, H + L.P, H + 2 * L.P, n, tabs, r, tmp);
-    } else {
-      for (int a = 0; a < 3; ++a)
-        integrate_cell((const T *)nullptr, H + (a * 3) * L.P, H + (a * 3 + 1) * L.P, H + (a * 3 + 2) * L.P, n, tabs,
-                       r + a * n3, tmp);
-      if (enr_c) {
-        // enriched tests: -(grad(psi N_v) e_a, u x u)
-        auto val = [&](int o, int t) -> T {
-          const int a = o >> 3, v = o & 7;
-          const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-          const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
-          T N[8], dN[8][3];
-          q1_weights(xi, N, dN);
-          const T *w = wtv + t * WT;
-          T ug = T(0);
-          for (int d = 0; d < 3; ++d) ug += U[d * L.P + t] * (w[0] * dN[v][d] * hinv[d] + N[v] * w[1 + d]);
-          const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
-          return -dV * U[a * L.P + t] * ug;
-        };
-        reduce_outputs(24, P, val, re);
-      }
-    }
-  } else {  // OP_VISC
-    T *G = V;             // 9 x P: grad ubar (then test coefficients)
-    T *Gt = V + 9 * L.P;  // 9 x P: grad u~ (physical)
-    for (int a = 0; a < 3; ++a)
-      eval_cell(uo + a * n3, n, tabs, (T *)nullptr, G + (a * 3) * L.P, G + (a * 3 + 1) * L.P, G + (a * 3 + 2) * L.P, tmp);
-    const T *nutv = enr_c ? m.nut_vol + (size_t)ec * m.nvol[0] : nullptr;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) {
-      const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-      T gb[3][3], tb[3][3];
-      for (int a = 0; a < 3; ++a)
-        for (int d = 0; d < 3; ++d) gb[a][d] = G[(a * 3 + d) * L.P + t] * hinv[d];
-      for (int a = 0; a < 3; ++a)
-        for (int d = 0; d < 3; ++d) tb[a][d] = nu * (gb[a][d] + gb[d][a]);
+      T Nv[8], dN[8][3];
+      const T *w = nullptr;
       if (enr_c) {
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
-        T N[8], dN[8][3];
-        q1_weights(xi, N, dN);
-        const T *w = wtv + t * WT;
-        T gt[3][3];
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) {
+        q1_weights(xi, Nv, dN);
+        w = wtv + t * WT;
+      }
+      if (OP == OP_DIV || OP == OP_CONV) {
+        T uu[3] = {V[t], V[P + t], V[2 * P + t]};
+        if (enr_c)
+          for (int a = 0; a < 3; ++a) {
             T s = T(0);
-            for (int v = 0; v < 8; ++v) s += eo[a * 8 + v] * (w[0] * dN[v][d] * hinv[d] + N[v] * w[1 + d]);
-            gt[a][d] = s;
-            Gt[(a * 3 + d) * L.P + t] = s;
+            for (int v = 0; v < 8; ++v) s += Nv[v] * eo[a * 8 + v];
+            uu[a] += w[0] * s;
+            V[a * P + t] = uu[a];
           }
-        const T nut = nutv[t];
-        const T nuh = min(nu + nut, T(2) * sqrt(nu * (nu + nut)));   // eq. (minvt)
+        if (OP == OP_DIV) {
+          for (int d = 0; d < 3; ++d) G[d * P + t] = dV * uu[d] * hinv[d];
+        } else {
+          for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = -dV * uu[a] * uu[d] * hinv[d];
+        }
+      } else {
+        T gb[3][3], tb[3][3];
         for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) tb[a][d] += nuh * (gt[a][d] + gt[d][a]);
+          for (int d = 0; d < 3; ++d) gb[a][d] = G[(a * 3 + d) * P + t] * hinv[d];
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) tb[a][d] = nu * (gb[a][d] + gb[d][a]);
+        if (enr_c) {
+          T gt[3][3];
+          for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) {
+              T s = T(0);
+              for (int v = 0; v < 8; ++v) s += eo[a * 8 + v] * (w[0] * dN[v][d] * hinv[d] + Nv[v] * w[1 + d]);
+              gt[a][d] = s;
+              Gt[(a * 3 + d) * P + t] = s;
+            }
+          const T nut = nutv[t];
+          const T nuh = min(nu + nut, T(2) * sqrt(nu * (nu + nut)));   // eq. (minvt)
+          for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) tb[a][d] += nuh * (gt[a][d] + gt[d][a]);
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = dV * tb[a][d] * hinv[d];
       }
-      const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
-      for (int a = 0; a < 3; ++a)
-        for (int d = 0; d < 3; ++d) G[(a * 3 + d) * L.P + t] = dV * tb[a][d] * hinv[d];
     }
     __syncthreads();
-    for (int a = 0; a < 3; ++a)
-      integrate_cell((const T *)nullptr, G + (a * 3) * L.P, G + (a * 3 + 1) * L.P, G + (a * 3 + 2) * L.P, n, tabs,
-                     r + a * n3, tmp);
-    if (enr_c) {
-      // enriched tests: (eps(psi N_v e_a), 2(nu+nu_t) eps(u~))
+    // enriched test functions: -(grad(psi N_v) e_a, u x u) or (eps(psi N_v e_a), 2(nu+nu_t) eps(u~))
+    if (enr_c && OP != OP_DIV) {
       auto val = [&](int o, int t) -> T {
         const int a = o >> 3, v = o & 7;
         const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
-        T N[8], dN[8][3];
-        q1_weights(xi, N, dN);
+        T Nv[8], dN[8][3];
+        q1_weights(xi, Nv, dN);
         const T *w = wtv + t * WT;
-        const T nut = nutv[t];
-        T s = T(0);
-        for (int d = 0; d < 3; ++d) {
-          const T gv = w[0] * dN[v][d] * hinv[d] + N[v] * w[1 + d];
-          s += gv * (nu + nut) * (Gt[(a * 3 + d) * L.P + t] + Gt[(d * 3 + a) * L.P + t]);
-        }
         const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
-        return dV * s;
+        T s = T(0);
+        if (OP == OP_CONV) {
+          T ug = T(0);
+          for (int d = 0; d < 3; ++d) ug += V[d * P + t] * (w[0] * dN[v][d] * hinv[d] + Nv[v] * w[1 + d]);
+          s = -dV * V[a * P + t] * ug;
+        } else {
+          const T nut = nutv[t];
+          for (int d = 0; d < 3; ++d) {
+            const T gv = w[0] * dN[v][d] * hinv[d] + Nv[v] * w[1 + d];
+            s += gv * (nu + nut) * (Gt[(a * 3 + d) * P + t] + Gt[(d * 3 + a) * P + t]);
+          }
+          s *= dV;
+        }
+        return s;
       };
       reduce_outputs(24, P, val, re);
     }
+    // P5-P7: integrate the gradient coefficients back to the nodes (z, y, x)
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int a = b % ncomp, k = b / ncomp;   // k: 0 Z0 = D_z^T H_z, 1 Z1 = S_z^T H_y, 2 Z2 = S_z^T H_x
+      return {G + (a * 3 + 2 - k) * P, k == 0 ? D_[2] : S_[2], nullptr, nullptr, Bv + b * SZ};
+    }, 3 * ncomp, q0, q1, q2, 2, n, q2, true, false);
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int a = b % ncomp, k = b / ncomp;   // k: 0 Y0 = S_y^T Z0 + D_y^T Z1, 1 Y1 = S_y^T Z2
+      if (k == 0) return {Bv + a * SZ, S_[1], Bv + (ncomp + a) * SZ, D_[1], A + b * SX};
+      return {Bv + (2 * ncomp + a) * SZ, S_[1], nullptr, nullptr, A + b * SX};
+    }, 2 * ncomp, q0, q1, n, 1, n, q1, true, false);
+    pass_batch<T>([&](int a) -> Pass<T> {
+      return {A + a * SX, S_[0], A + (ncomp + a) * SX, D_[0], r + a * n3};
+    }, ncomp, q0, n, n, 0, n, q0, true, true);
   }
 
-  // ---------------- faces ----------------
-  T *F = S0 + L.face;
-  for (int f = 0; f < 6; ++f) {
-    const int nb = neighbour(m, c, f);
-    const int d = f >> 1, side = f & 1;
+  // ================= faces, one direction (two faces) at a time =================
+  for (int d = 0; d < 3; ++d) {
     int t1, t2;
     face_axes(d, t1, t2);
-    const int eb = nb >= 0 ? m.enr[nb] : -1;
-    const bool enr_o = nb >= 0 ? eb >= 0 : enr_c;
-    const bool both = enr_c && enr_o, iface = enr_c != enr_o;
-    const int s1 = (t1 == 1 && (enr_c || enr_o)) ? QSET_WALL : qset;
-    const int s2 = (t2 == 1 && (enr_c || enr_o)) ? QSET_WALL : qset;
+    int nbr[2], enb[2];
+    bool enr_o[2];
+    for (int s = 0; s < 2; ++s) {
+      nbr[s] = neighbour(m, c, 2 * d + s);
+      enb[s] = nbr[s] >= 0 ? m.enr[nbr[s]] : -1;
+      enr_o[s] = nbr[s] >= 0 ? enb[s] >= 0 : enr_c;   // the mirror side carries c's class
+    }
+    // point sets of the faces normal to d: the same for both faces (x/z neighbours share the row,
+    // y-faces have only in-plane tangential axes)
+    const bool enr_any = enr_c || enr_o[0] || enr_o[1];
+    const int s1 = (t1 == 1 && enr_any) ? QSET_WALL : qset;
+    const int s2 = (t2 == 1 && enr_any) ? QSET_WALL : qset;
     const int p1 = B.q[s1], p2 = B.q[s2], FP = p1 * p2;
-    if (nb >= 0) {
-      for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) un[t] = u[(size_t)nb * 3 * n3 + t];
-      if (eb >= 0)
-        for (int t = threadIdx.x; t < 24; t += blockDim.x) en[t] = u[3 * m.np + (size_t)eb * 24 + t];
-      __syncthreads();
+    for (int t = threadIdx.x; t < 2 * 3 * n3; t += blockDim.x) {
+      const int s = t / (3 * n3), e = t - s * 3 * n3;
+      un[t] = nbr[s] >= 0 ? u[(size_t)nbr[s] * 3 * n3 + e] : T(0);
     }
-    const T sgn = side ? T(1) : T(-1);
-    const T hd = h[d];
-    const T hdo = nb >= 0 ? cell_h(m, nb, d) : hd;
-    const T area = h[t1] * h[t2];
-    const T *wts = enr_c ? m.wt_face[opc] + (((size_t)ec * 6 + f) * m.fpmax[opc]) * WT : nullptr;
-    const T *wto = (nb >= 0 && eb >= 0) ? m.wt_face[opc] + (((size_t)eb * 6 + (f ^ 1)) * m.fpmax[opc]) * WT : nullptr;
-    // traces: own values Vs[3], neighbour Vo[3]; VISC: gradients (reference d, t1, t2)
-    T *Vs = F, *Vo = F + 3 * L.FP;
-    T *Gs = nullptr, *Go = nullptr, *C = nullptr, *E = nullptr;
-    if (OP == OP_VISC) {
-      Gs = F + 6 * L.FP;       // 9: [a][dir d,t1,t2]
-      Go = F + 15 * L.FP;      // 9
-      C = F + 24 * L.FP;       // 12: per component f, hd, ht1, ht2
-      E = F + 36 * L.FP;       // 12: per component value coeff + 3 physical gradient coeffs (enriched tests)
-    } else {
-      C = F + 6 * L.FP;        // DIV: 1 (f) ; CONV: 3 (f per component)
-      E = F + 10 * L.FP;       // CONV enriched value coeffs (3)
+    for (int t = threadIdx.x; t < 48; t += blockDim.x) {
+      const int s = t / 24;
+      en[t] = enb[s] >= 0 ? u[3 * m.np + (size_t)enb[s] * 24 + (t - 24 * s)] : T(0);
     }
-    const T *S1 = B.S[s1], *D1 = B.D[s1], *Sb2 = B.S[s2], *D2 = B.D[s2];
-    for (int a = 0; a < 3; ++a) {
-      if (OP == OP_VISC)
-        eval_face(uo + a * n3, n, d, side, B.dend[side], S1, D1, p1, Sb2, D2, p2, Vs + a * L.FP, Gs + (a * 3) * L.FP,
-                  Gs + (a * 3 + 1) * L.FP, Gs + (a * 3 + 2) * L.FP, tmp);
-      else
-        eval_face(uo + a * n3, n, d, side, B.dend[side], S1, D1, p1, Sb2, D2, p2, Vs + a * L.FP, (T *)nullptr,
-                  (T *)nullptr, (T *)nullptr, tmp);
-      if (nb >= 0) {
-        if (OP == OP_VISC)
-          eval_face(un + a * n3, n, d, 1 - side, B.dend[1 - side], S1, D1, p1, Sb2, D2, p2, Vo + a * L.FP,
-                    Go + (a * 3) * L.FP, Go + (a * 3 + 1) * L.FP, Go + (a * 3 + 2) * L.FP, tmp);
-        else
-          eval_face(un + a * n3, n, d, 1 - side, B.dend[1 - side], S1, D1, p1, Sb2, D2, p2, Vo + a * L.FP,
-                    (T *)nullptr, (T *)nullptr, (T *)nullptr, tmp);
+    __syncthreads();
+    T *V2 = S0 + L.fV2, *N2 = S0 + L.fN2, *A0 = S0 + L.fA0, *A1 = S0 + L.fA1, *B0 = S0 + L.fB0, *Tr = S0 + L.fTr;
+    // slot k = (s * 2 + side) * 3 + a; side 0 = own cell at xi_d = s, side 1 = neighbour at xi_d = 1 - s
+    // T1: face-layer values and reference normal derivatives
+    for (int t = threadIdx.x; t < 12 * nn; t += blockDim.x) {
+      const int k = t / nn, node = t - k * nn;
+      const int a = k % 3, side = (k / 3) % 2, s = k / 6;
+      const T *src = side ? un + (s * 3 + a) * n3 : uo + a * n3;
+      const int ep = side ? 1 - s : s;
+      const int i1 = node % n, i2 = node / n;
+      V2[t] = src[node_index(d, t1, t2, ep ? n - 1 : 0, i1, i2, n)];
+      if (GRAD) {
+        T sum = T(0);
+        for (int j = 0; j < n; ++j) sum += B.dend[ep][j] * src[node_index(d, t1, t2, j, i1, i2, n)];
+        N2[t] = sum;
       }
     }
-    const T tau = nb >= 0 ? max(m.tau[c], m.tau[nb]) : T(10) * m.tau[c];
-    const T *nuts = (OP == OP_VISC && enr_c) ? m.nut_face + ((size_t)ec * 6 + f) * m.fpmax[0] : nullptr;
-    const T *nuto = (OP == OP_VISC && nb >= 0 && eb >= 0) ? m.nut_face + ((size_t)eb * 6 + (f ^ 1)) * m.fpmax[0] : nullptr;
-    for (int t = threadIdx.x; t < FP; t += blockDim.x) {
-      const int a1 = t % p1, a2 = t / p1;
-      const T dA = area * B.w[s1][a1] * B.w[s2][a2];
-      // physical point coordinates on both sides
+    __syncthreads();
+    // T2: along t1 (n -> p1)
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int k = b % 12, j = b / 12;   // j: 0 A0 = S1 V2, 1 A1 = D1 V2, 2 B0 = S1 N2
+      const T *in = (j == 2 ? N2 : V2) + k * nn;
+      T *out = (j == 0 ? A0 : (j == 1 ? A1 : B0)) + k * L.pn;
+      return {in, j == 1 ? B.D[s1] : B.S[s1], nullptr, nullptr, out};
+    }, GRAD ? 36 : 12, n, n, 1, 0, n, p1, false, false);
+    // T3: along t2 (n -> p2): value, d/dxi_d, d/dxi_t1, d/dxi_t2 at the face points
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int k = b % 12, j = b / 12;   // j: 0 val = S2 A0, 1 gd = S2 B0, 2 gt1 = S2 A1, 3 gt2 = D2 A0
+      const T *in = (j == 1 ? B0 : (j == 2 ? A1 : A0)) + k * L.pn;
+      return {in, j == 3 ? B.D[s2] : B.S[s2], nullptr, nullptr, Tr + (k * 4 + j) * L.FP};
+    }, GRAD ? 48 : 12, p1, n, 1, 1, n, p2, false, false);
+    // pointwise fluxes -> coefficients of the own test functions
+    T *C = S0 + L.fC, *E = S0 + L.fE;
+    for (int t = threadIdx.x; t < 2 * FP; t += blockDim.x) {
+      const int s = t / FP, pt = t - s * FP;
+      const int f = 2 * d + s, side = s;
+      const int nb = nbr[s], eb = enb[s];
+      const int a1 = pt % p1, a2 = pt / p1;
+      const T dA = h[t1] * h[t2] * B.w[s1][a1] * B.w[s2][a2];
+      const T sgn = side ? T(1) : T(-1);
+      const T hdo = nb >= 0 ? cell_h(m, nb, d) : h[d];
+      const bool both = enr_c && enr_o[s], iface = enr_c != enr_o[s];
+      const T tau = nb >= 0 ? max(m.tau[c], m.tau[nb]) : T(10) * m.tau[c];
+      const T *wts = enr_c ? m.wt_face[opc] + (((size_t)ec * 6 + f) * m.fpmax[opc]) * WT : nullptr;
+      const T *wto = (nb >= 0 && eb >= 0) ? m.wt_face[opc] + (((size_t)eb * 6 + (f ^ 1)) * m.fpmax[opc]) * WT : nullptr;
       T xs[3], xo[3];
       xs[d] = T(side); xs[t1] = B.x[s1][a1]; xs[t2] = B.x[s2][a2];
       xo[d] = T(1 - side); xo[t1] = xs[t1]; xo[t2] = xs[t2];
-      T ub_s[3], ub_o[3], ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
-      T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
       T Ns[8], dNs[8][3], No[8], dNo[8][3];
       if (enr_c) q1_weights(xs, Ns, dNs);
-      if (nb >= 0 && eb >= 0) q1_weights(xo, No, dNo);
+      if (wto) q1_weights(xo, No, dNo);
+      T ub_s[3], ub_o[3], ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
+      T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
+      const T hob1 = nb >= 0 ? cell_h(m, nb, 1) : h[1];
       for (int a = 0; a < 3; ++a) {
-        ub_s[a] = Vs[a * L.FP + t];
-        if (OP == OP_VISC) {
-          T gref[3] = {Gs[(a * 3) * L.FP + t], Gs[(a * 3 + 1) * L.FP + t], Gs[(a * 3 + 2) * L.FP + t]};
-          gbs[a][d] = gref[0] * hinv[d]; gbs[a][t1] = gref[1] * hinv[t1]; gbs[a][t2] = gref[2] * hinv[t2];
+        const T *tr_s = Tr + (((s * 2 + 0) * 3 + a) * 4) * L.FP;
+        const T *tr_o = Tr + (((s * 2 + 1) * 3 + a) * 4) * L.FP;
+        ub_s[a] = tr_s[pt];
+        if (GRAD) {
+          gbs[a][d] = tr_s[L.FP + pt] * hinv[d];
+          gbs[a][t1] = tr_s[2 * L.FP + pt] * hinv[t1];
+          gbs[a][t2] = tr_s[3 * L.FP + pt] * hinv[t2];
         }
         if (enr_c) {
-          const T *w = wts + t * WT;
-          T s = T(0);
-          for (int v = 0; v < 8; ++v) s += Ns[v] * eo[a * 8 + v];
-          ut_s[a] = w[0] * s;
-          if (OP == OP_VISC)
+          const T *w = wts + pt * WT;
+          T sum = T(0);
+          for (int v = 0; v < 8; ++v) sum += Ns[v] * eo[a * 8 + v];
+          ut_s[a] = w[0] * sum;
+          if (GRAD)
             for (int e = 0; e < 3; ++e) {
               T g = T(0);
               for (int v = 0; v < 8; ++v) g += eo[a * 8 + v] * (w[0] * dNs[v][e] * hinv[e] + Ns[v] * w[1 + e]);
               gts[a][e] = g;
             }
-        } else if (OP == OP_VISC) {
+        } else if (GRAD) {
           gts[a][0] = gts[a][1] = gts[a][2] = T(0);
         }
         if (nb >= 0) {
-          ub_o[a] = Vo[a * L.FP + t];
-          if (OP == OP_VISC) {
-            T gref[3] = {Go[(a * 3) * L.FP + t], Go[(a * 3 + 1) * L.FP + t], Go[(a * 3 + 2) * L.FP + t]};
-            const T hto1 = (t1 == 1) ? cell_h(m, nb, 1) : h[t1];
-            const T hto2 = (t2 == 1) ? cell_h(m, nb, 1) : h[t2];
-            gbo[a][d] = gref[0] / hdo; gbo[a][t1] = gref[1] / hto1; gbo[a][t2] = gref[2] / hto2;
+          ub_o[a] = tr_o[pt];
+          if (GRAD) {
+            const T ht1 = t1 == 1 ? hob1 : h[t1], ht2 = t2 == 1 ? hob1 : h[t2];
+            gbo[a][d] = tr_o[L.FP + pt] / hdo;
+            gbo[a][t1] = tr_o[2 * L.FP + pt] / ht1;
+            gbo[a][t2] = tr_o[3 * L.FP + pt] / ht2;
           }
-          if (eb >= 0) {
-            const T *w = wto + t * WT;
-            T s = T(0);
-            for (int v = 0; v < 8; ++v) s += No[v] * en[a * 8 + v];
-            ut_o[a] = w[0] * s;
-            if (OP == OP_VISC) {
-              const T hob[3] = {m.hx, cell_h(m, nb, 1), m.hz};
+          if (wto) {
+            const T *w = wto + pt * WT;
+            T sum = T(0);
+            for (int v = 0; v < 8; ++v) sum += No[v] * en[s * 24 + a * 8 + v];
+            ut_o[a] = w[0] * sum;
+            if (GRAD) {
+              const T hob[3] = {m.hx, hob1, m.hz};
               for (int e = 0; e < 3; ++e) {
                 T g = T(0);
-                for (int v = 0; v < 8; ++v) g += en[a * 8 + v] * (w[0] * dNo[v][e] / hob[e] + No[v] * w[1 + e]);
+                for (int v = 0; v < 8; ++v) g += en[s * 24 + a * 8 + v] * (w[0] * dNo[v][e] / hob[e] + No[v] * w[1 + e]);
                 gto[a][e] = g;
               }
             }
-          } else if (OP == OP_VISC) {
+          } else if (GRAD) {
             gto[a][0] = gto[a][1] = gto[a][2] = T(0);
           }
         } else {
           // mirror principle on no-slip walls: u+ = -u-, grad u+ = grad u-
           ub_o[a] = -ub_s[a];
           ut_o[a] = -ut_s[a];
-          if (OP == OP_VISC)
+          if (GRAD)
             for (int e = 0; e < 3; ++e) { gbo[a][e] = gbs[a][e]; gto[a][e] = gts[a][e]; }
         }
       }
+      T *Cs = C + s * 3 * 4 * L.FP, *Es = E + s * 3 * 4 * L.FP;
       if (OP == OP_DIV) {
-        // -(q, {{u}}.n), wall: u^-
         const T us = ub_s[d] + ut_s[d], uo_ = ub_o[d] + ut_o[d];
         const T avg = nb >= 0 ? T(0.5) * (us + uo_) : us;
-        C[t] = -dA * sgn * avg;
+        Cs[pt] = -dA * sgn * avg;
       } else if (OP == OP_CONV) {
         T um[3], up[3];
         for (int a = 0; a < 3; ++a) { um[a] = ub_s[a] + ut_s[a]; up[a] = ub_o[a] + ut_o[a]; }
@@ -374,18 +456,19 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         const T lam = max(T(2) * fabs(unm), T(2) * fabs(unp));
         for (int a = 0; a < 3; ++a) {
           const T Fa = T(0.5) * (um[a] * unm + up[a] * unp) + T(0.5) * lam * (um[a] - up[a]);
-          C[a * L.FP + t] = dA * Fa;
-          E[a * L.FP + t] = dA * Fa;
+          Cs[(a * 4) * L.FP + pt] = dA * Fa;
+          Es[(a * 4) * L.FP + pt] = dA * Fa;
         }
       } else {  // VISC
-        const T nut_s = nuts ? nuts[t] : T(0);
-        const T nut_o = nb >= 0 ? (nuto ? nuto[t] : T(0)) : nut_s;
+        const T *nuts = enr_c ? m.nut_face + ((size_t)ec * 6 + f) * m.fpmax[0] : nullptr;
+        const T *nuto = (nb >= 0 && eb >= 0) ? m.nut_face + ((size_t)eb * 6 + (f ^ 1)) * m.fpmax[0] : nullptr;
+        const T nut_s = nuts ? nuts[pt] : T(0);
+        const T nut_o = nb >= 0 ? (nuto ? nuto[pt] : T(0)) : nut_s;
         T jb[3], jt[3], jtot[3], avgb_n[3], avgt_n[3] = {0, 0, 0};
         for (int a = 0; a < 3; ++a) {
           jb[a] = ub_s[a] - ub_o[a];
           jt[a] = ut_s[a] - ut_o[a];
           jtot[a] = jb[a] + jt[a];
-          // {{F^nu(ubar)}}.n with n = sgn e_d
           avgb_n[a] = T(0.5) * nu * sgn * ((gbs[a][d] + gbs[d][a]) + (gbo[a][d] + gbo[d][a]));
         }
         T wt_s = T(0.5);
@@ -401,67 +484,77 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         for (int a = 0; a < 3; ++a) {
           T cv = -avgb_n[a] + tau * nu * jtot[a];
           if (both) cv -= avgt_n[a];
-          // coefficient of phi: dA cv; of dphi/dxi_b: dA nu/2 sgn (jadj_a delta_bd + delta_ad jadj_b)/h_b
-          C[(a * 4 + 0) * L.FP + t] = dA * cv;
-          C[(a * 4 + 1) * L.FP + t] = dA * T(0.5) * nu * sgn * (jadj[a] + (a == d ? jadj[d] : T(0))) * hinv[d];
-          C[(a * 4 + 2) * L.FP + t] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t1] : T(0)) * hinv[t1];
-          C[(a * 4 + 3) * L.FP + t] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t2] : T(0)) * hinv[t2];
+          // coefficient of phi: dA cv; of dphi/dxi_b: dA nu/2 sgn (jadj_a delta_bd + delta_ad jadj_b) / h_b
+          Cs[(a * 4 + 0) * L.FP + pt] = dA * cv;
+          Cs[(a * 4 + 1) * L.FP + pt] = dA * T(0.5) * nu * sgn * (jadj[a] + (a == d ? jadj[d] : T(0))) * hinv[d];
+          Cs[(a * 4 + 2) * L.FP + pt] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t1] : T(0)) * hinv[t1];
+          Cs[(a * 4 + 3) * L.FP + pt] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t2] : T(0)) * hinv[t2];
           if (enr_c) {
             T cve = tau * nu * jtot[a];
             if (both) cve -= avgt_n[a];
             if (iface) cve -= avgb_n[a];
-            E[(a * 4 + 0) * L.FP + t] = dA * cve;
+            Es[(a * 4 + 0) * L.FP + pt] = dA * cve;
             for (int b = 0; b < 3; ++b) {
               // (w F^{nu+nut}(v~), [[u~]] + [[ubar]]) on d Omega~_e: physical-gradient coefficient
               const T coef = both ? wt_s * (nu + nut_s) * sgn * ((b == d ? jtot[a] : T(0)) + (a == d ? jtot[b] : T(0))) : T(0);
-              E[(a * 4 + 1 + b) * L.FP + t] = dA * coef;
+              Es[(a * 4 + 1 + b) * L.FP + pt] = dA * coef;
             }
           }
         }
       }
     }
     __syncthreads();
-    if (OP == OP_DIV) {
-      integrate_face(C, (const T *)nullptr, (const T *)nullptr, (const T *)nullptr, n, d, side, B.dend[side], S1, D1,
-                     p1, Sb2, D2, p2, r, tmp);
-    } else if (OP == OP_CONV) {
-      for (int a = 0; a < 3; ++a)
-        integrate_face(C + a * L.FP, (const T *)nullptr, (const T *)nullptr, (const T *)nullptr, n, d, side,
-                       B.dend[side], S1, D1, p1, Sb2, D2, p2, r + a * n3, tmp);
-      if (enr_c) {
-        auto val = [&](int o, int t) -> T {
-          const int a = o >> 3, v = o & 7;
-          const int a1 = t % p1, a2 = t / p1;
-          T xs[3];
-          xs[d] = T(side); xs[t1] = B.x[s1][a1]; xs[t2] = B.x[s2][a2];
-          T N[8], dN[8][3];
-          q1_weights(xs, N, dN);
-          return E[a * L.FP + t] * wts[t * WT] * N[v];
-        };
-        reduce_outputs(24, FP, val, re);
-      }
-    } else {
-      for (int a = 0; a < 3; ++a)
-        integrate_face(C + (a * 4) * L.FP, C + (a * 4 + 1) * L.FP, C + (a * 4 + 2) * L.FP, C + (a * 4 + 3) * L.FP, n, d,
-                       side, B.dend[side], S1, D1, p1, Sb2, D2, p2, r + a * n3, tmp);
-      if (enr_c) {
-        auto val = [&](int o, int t) -> T {
-          const int a = o >> 3, v = o & 7;
-          const int a1 = t % p1, a2 = t / p1;
-          T xs[3];
-          xs[d] = T(side); xs[t1] = B.x[s1][a1]; xs[t2] = B.x[s2][a2];
-          T N[8], dN[8][3];
-          q1_weights(xs, N, dN);
-          const T *w = wts + t * WT;
-          T s = E[(a * 4) * L.FP + t] * w[0] * N[v];
-          for (int b = 0; b < 3; ++b) s += E[(a * 4 + 1 + b) * L.FP + t] * (w[0] * dN[v][b] * hinv[b] + N[v] * w[1 + b]);
-          return s;
-        };
-        reduce_outputs(24, FP, val, re);
-      }
+    // enriched tests on these two faces
+    if (enr_c && OP != OP_DIV) {
+      auto val = [&](int o, int t) -> T {
+        const int a = o >> 3, v = o & 7;
+        const int s = t / FP, pt = t - s * FP;
+        const int a1 = pt % p1, a2 = pt / p1;
+        T xs[3];
+        xs[d] = T(s); xs[t1] = B.x[s1][a1]; xs[t2] = B.x[s2][a2];
+        T Nv[8], dN[8][3];
+        q1_weights(xs, Nv, dN);
+        const T *w = m.wt_face[opc] + (((size_t)ec * 6 + 2 * d + s) * m.fpmax[opc]) * WT + pt * WT;
+        const T *Es = E + s * 3 * 4 * L.FP;
+        T sum = Es[(a * 4) * L.FP + pt] * w[0] * Nv[v];
+        if (OP == OP_VISC)
+          for (int b = 0; b < 3; ++b) sum += Es[(a * 4 + 1 + b) * L.FP + pt] * (w[0] * dN[v][b] * hinv[b] + Nv[v] * w[1 + b]);
+        return sum;
+      };
+      reduce_outputs(24, 2 * FP, val, re);
     }
+    // I1: along t2 (p2 -> n); I2: along t1 (p1 -> n); item k = (face s, component a)
+    T *I0 = S0 + L.fI0, *I1 = S0 + L.fI1, *I2 = S0 + L.fI2, *F2 = S0 + L.fF2, *G2 = S0 + L.fG2;
+    const int ni = 2 * ncomp;
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int k = b % ni, j = b / ni;   // j: 0 I0 = S2^T f + D2^T ht2, 1 I1 = S2^T ht1, 2 I2 = S2^T hd
+      const int s = k / ncomp, a = k % ncomp;
+      const T *Ck = C + (s * 3 + a) * 4 * L.FP;
+      if (j == 0) return {Ck, B.S[s2], GRAD ? Ck + 3 * L.FP : nullptr, B.D[s2], I0 + k * L.pn};
+      if (j == 1) return {Ck + 2 * L.FP, B.S[s2], nullptr, nullptr, I1 + k * L.pn};
+      return {Ck + 1 * L.FP, B.S[s2], nullptr, nullptr, I2 + k * L.pn};
+    }, GRAD ? 3 * ni : ni, p1, p2, 1, 1, n, p2, true, false);
+    pass_batch<T>([&](int b) -> Pass<T> {
+      const int k = b % ni, j = b / ni;   // j: 0 F2 = S1^T I0 + D1^T I1, 1 G2 = S1^T I2
+      if (j == 0) return {I0 + k * L.pn, B.S[s1], GRAD ? I1 + k * L.pn : nullptr, B.D[s1], F2 + k * nn};
+      return {I2 + k * L.pn, B.S[s1], nullptr, nullptr, G2 + k * nn};
+    }, GRAD ? 2 * ni : ni, p1, n, 1, 0, n, p1, true, false);
+    // scatter the face-layer values and the normal-derivative coefficients into the cell nodes
+    for (int t = threadIdx.x; t < ncomp * n3; t += blockDim.x) {
+      const int a = t / n3, node = t - a * n3;
+      const int id[3] = {node % n, (node / n) % n, node / nn};
+      const int fi = id[t1] + n * id[t2];
+      T add = T(0);
+      for (int s = 0; s < 2; ++s) {
+        const int k = s * ncomp + a;
+        if (id[d] == (s ? n - 1 : 0)) add += F2[k * nn + fi];
+        if (GRAD) add += B.dend[s][id[d]] * G2[k * nn + fi];
+      }
+      r[t] += add;
+    }
+    __syncthreads();
   }
-  // ---------------- store ----------------
+  // ================= store =================
   if (OP == OP_DIV) {
     T *yc = y + (size_t)c * n3;
     for (int t = threadIdx.x; t < n3; t += blockDim.x) yc[t] = r[t];
@@ -471,18 +564,19 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     if (enr_c)
       for (int t = threadIdx.x; t < 24; t += blockDim.x) y[3 * m.np + (size_t)ec * 24 + t] = re[t];
   }
-  (void)ncomp_out;
 }
 
 template <typename T, int OP>
 static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s) {
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
-  const VecLayout L = vec_layout(OP, m.n1, m.q[qset], m.q[QSET_WALL]);
+  const VecPlan L = vec_plan(OP, m.n1, m.q[qset], m.q[QSET_WALL]);
   const size_t sm = ((sizeof(Basis<T>) + 15) / 16) * 16 + (size_t)L.total * sizeof(T);
   if (sm > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(vector_op_kernel<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e == cudaSuccess)   // the whole unified L1/shared array as shared memory: more CTAs per SM
+      e = cudaFuncSetAttribute(vector_op_kernel<T, OP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
