@@ -97,12 +97,80 @@ __device__ void pass_batch(F desc, int nb, int s0, int s1, int s2, int ax, int n
   __syncthreads();
 }
 
+// Trilinear weight N_v and its reference gradient at a point from the 1-D factors
+// f[d][0] = 1 - xi_d, f[d][1] = xi_d.
+template <typename T>
+__device__ __forceinline__ void q1_vertex(const T f[3][2], int v, T &N, T dN[3]) {
+  const int b0 = v & 1, b1 = (v >> 1) & 1, b2 = (v >> 2) & 1;
+  const T s0 = b0 ? T(1) : T(-1), s1 = b1 ? T(1) : T(-1), s2 = b2 ? T(1) : T(-1);
+  const T f12 = f[1][b1] * f[2][b2];
+  N = f[0][b0] * f12;
+  dN[0] = s0 * f12;
+  dN[1] = s1 * f[0][b0] * f[2][b2];
+  dN[2] = s2 * f[0][b0] * f[1][b1];
+}
+
+// Adds to out[24] the sum over npts points of 24 per-point contributions (the enriched test
+// functions e_a psi N_v, output a * 8 + v). Each thread accumulates its points in registers; a
+// butterfly reduce-scatter halves the set a lane holds at each of three steps (27 shuffles per warp
+// instead of 24 x 5), and one pass adds the warps' partial sums in a fixed order. part holds
+// 24 T per warp. Ends with a barrier.
+template <typename T, typename F>
+__device__ void reduce24(int npts, F contrib, T *out, T *part) {
+  T acc[24];
+#pragma unroll
+  for (int o = 0; o < 24; ++o) acc[o] = T(0);
+  for (int p = threadIdx.x; p < npts; p += blockDim.x) contrib(p, acc);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const T send = up ? acc[i] : acc[i + 12], keep = up ? acc[i + 12] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(full, send, 16);
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const T send = up ? acc[i] : acc[i + 6], keep = up ? acc[i + 6] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(full, send, 8);
+    }
+  }
+  {
+    const bool up = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T send = up ? acc[i] : acc[i + 3], keep = up ? acc[i + 3] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(full, send, 4);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc[i] += __shfl_xor_sync(full, acc[i], 2);
+    acc[i] += __shfl_xor_sync(full, acc[i], 1);
+  }
+  if ((lane & 3) == 0) {
+    const int base = ((lane & 16) ? 12 : 0) + ((lane & 8) ? 6 : 0) + ((lane & 4) ? 3 : 0);
+    for (int i = 0; i < 3; ++i) part[warp * 24 + base + i] = acc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < 24) {
+    T sum = T(0);
+    for (int w = 0; w < nw; ++w) sum += part[w * 24 + threadIdx.x];
+    out[threadIdx.x] += sum;
+  }
+  __syncthreads();
+}
+
 // Shared-memory plan (in T words) for one cell. The volume and face phases share one work
 // region; inside the face region the neighbour coefficients share room with the arrays written
 // after the layer traces are taken, and the integration arrays with the trace arrays.
 struct VecPlan {
   int n, n3, qi, qy, P, FP, pn;   // pn = largest (face points along t1) x n
-  int uo, r, eo, re, en, work, total;
+  int uo, r, eo, re, en, part, work, total;
   int vA, vB, vV, vG, vGt, vol_end;                                               // volume regions
   int fV2, fN2, fA0, fA1, fB0, fTr, fC, fE, fUn, fI0, fI1, fI2, fF2, fG2, face_end;  // face regions
 };
@@ -124,6 +192,7 @@ __host__ __device__ inline VecPlan vec_plan(int op, int n, int qin, int qw) {
   p.eo = o; o += 24;
   p.re = o; o += 24;
   p.en = o; o += 48;   // enrichment coefficients of the two neighbours of one direction
+  p.part = o; o += 4 * 24;   // per-warp partial sums of the enriched reductions (128 threads)
   p.work = o;
   int v = o;
   p.vA = v; v += 6 * SX;
@@ -221,20 +290,31 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     for (int t = threadIdx.x; t < P; t += blockDim.x) {
       const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
       const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
-      T Nv[8], dN[8][3];
+      // enrichment at the point: sN_a = sum_v N_v e_av, sD_ad = sum_v dN_v/dxi_d e_av
+      T sN[3] = {0, 0, 0}, sD[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       const T *w = nullptr;
       if (enr_c) {
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
-        q1_weights(xi, Nv, dN);
+        const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          T Nv, dN[3];
+          q1_vertex(f, v, Nv, dN);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            sN[a] += Nv * eo[a * 8 + v];
+            if (GRAD)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) sD[a][d] += dN[d] * eo[a * 8 + v];
+          }
+        }
         w = wtv + t * WT;
       }
       if (OP == OP_DIV || OP == OP_CONV) {
         T uu[3] = {V[t], V[P + t], V[2 * P + t]};
         if (enr_c)
           for (int a = 0; a < 3; ++a) {
-            T s = T(0);
-            for (int v = 0; v < 8; ++v) s += Nv[v] * eo[a * 8 + v];
-            uu[a] += w[0] * s;
+            uu[a] += w[0] * sN[a];
             V[a * P + t] = uu[a];
           }
         if (OP == OP_DIV) {
@@ -253,10 +333,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           T gt[3][3];
           for (int a = 0; a < 3; ++a)
             for (int d = 0; d < 3; ++d) {
-              T s = T(0);
-              for (int v = 0; v < 8; ++v) s += eo[a * 8 + v] * (w[0] * dN[v][d] * hinv[d] + Nv[v] * w[1 + d]);
-              gt[a][d] = s;
-              Gt[(a * 3 + d) * P + t] = s;
+              gt[a][d] = w[0] * sD[a][d] * hinv[d] + sN[a] * w[1 + d];
+              Gt[(a * 3 + d) * P + t] = gt[a][d];
             }
           const T nut = nutv[t];
           const T nuh = min(nu + nut, T(2) * sqrt(nu * (nu + nut)));   // eq. (minvt)
@@ -270,30 +348,38 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     __syncthreads();
     // enriched test functions: -(grad(psi N_v) e_a, u x u) or (eps(psi N_v e_a), 2(nu+nu_t) eps(u~))
     if (enr_c && OP != OP_DIV) {
-      auto val = [&](int o, int t) -> T {
-        const int a = o >> 3, v = o & 7;
+      auto contrib = [&](int t, T *acc) {
         const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
-        T Nv[8], dN[8][3];
-        q1_weights(xi, Nv, dN);
+        const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
         const T *w = wtv + t * WT;
         const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
-        T s = T(0);
+        T cf[3][3];   // coefficient of d(psi N_v)/dx_d in output (a, v)
         if (OP == OP_CONV) {
-          T ug = T(0);
-          for (int d = 0; d < 3; ++d) ug += V[d * P + t] * (w[0] * dN[v][d] * hinv[d] + Nv[v] * w[1 + d]);
-          s = -dV * V[a * P + t] * ug;
+          const T uu[3] = {V[t], V[P + t], V[2 * P + t]};
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cf[a][d] = -dV * uu[a] * uu[d];
         } else {
-          const T nut = nutv[t];
-          for (int d = 0; d < 3; ++d) {
-            const T gv = w[0] * dN[v][d] * hinv[d] + Nv[v] * w[1 + d];
-            s += gv * (nu + nut) * (Gt[(a * 3 + d) * P + t] + Gt[(d * 3 + a) * P + t]);
-          }
-          s *= dV;
+          const T nd = dV * (nu + nutv[t]);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cf[a][d] = nd * (Gt[(a * 3 + d) * P + t] + Gt[(d * 3 + a) * P + t]);
         }
-        return s;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          T Nv, dN[3];
+          q1_vertex(f, v, Nv, dN);
+          T g[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) g[d] = w[0] * dN[d] * hinv[d] + Nv * w[1 + d];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cf[a][0] * g[0] + cf[a][1] * g[1] + cf[a][2] * g[2];
+        }
       };
-      reduce_outputs(24, P, val, re);
+      reduce24<T>(P, contrib, re, S0 + L.part);
     }
     // P5-P7: integrate the gradient coefficients back to the nodes (z, y, x)
     pass_batch<T>([&](int b) -> Pass<T> {
@@ -311,6 +397,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   }
 
   // ================= faces, one direction (two faces) at a time =================
+  // trace slots per direction: (face s, side, component); the divergence needs one component
+  constexpr int NCA = OP == OP_DIV ? 1 : 3;
+  constexpr int NS = 4 * NCA;
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
     int t1, t2;
     face_axes(d, t1, t2);
@@ -337,11 +427,11 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
     __syncthreads();
     T *V2 = S0 + L.fV2, *N2 = S0 + L.fN2, *A0 = S0 + L.fA0, *A1 = S0 + L.fA1, *B0 = S0 + L.fB0, *Tr = S0 + L.fTr;
-    // slot k = (s * 2 + side) * 3 + a; side 0 = own cell at xi_d = s, side 1 = neighbour at xi_d = 1 - s
+    // slot k = (s * 2 + side) * NCA + a; side 0 = own cell at xi_d = s, side 1 = neighbour at xi_d = 1 - s
     // T1: face-layer values and reference normal derivatives
-    for (int t = threadIdx.x; t < 12 * nn; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NS * nn; t += blockDim.x) {
       const int k = t / nn, node = t - k * nn;
-      const int a = k % 3, side = (k / 3) % 2, s = k / 6;
+      const int a = NCA == 1 ? d : k % NCA, side = (k / NCA) % 2, s = k / (2 * NCA);
       const T *src = side ? un + (s * 3 + a) * n3 : uo + a * n3;
       const int ep = side ? 1 - s : s;
       const int i1 = node % n, i2 = node / n;
@@ -355,17 +445,17 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     __syncthreads();
     // T2: along t1 (n -> p1)
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int k = b % 12, j = b / 12;   // j: 0 A0 = S1 V2, 1 A1 = D1 V2, 2 B0 = S1 N2
+      const int k = b % NS, j = b / NS;   // j: 0 A0 = S1 V2, 1 A1 = D1 V2, 2 B0 = S1 N2
       const T *in = (j == 2 ? N2 : V2) + k * nn;
       T *out = (j == 0 ? A0 : (j == 1 ? A1 : B0)) + k * L.pn;
       return {in, j == 1 ? B.D[s1] : B.S[s1], nullptr, nullptr, out};
-    }, GRAD ? 36 : 12, n, n, 1, 0, n, p1, false, false);
+    }, GRAD ? 3 * NS : NS, n, n, 1, 0, n, p1, false, false);
     // T3: along t2 (n -> p2): value, d/dxi_d, d/dxi_t1, d/dxi_t2 at the face points
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int k = b % 12, j = b / 12;   // j: 0 val = S2 A0, 1 gd = S2 B0, 2 gt1 = S2 A1, 3 gt2 = D2 A0
+      const int k = b % NS, j = b / NS;   // j: 0 val = S2 A0, 1 gd = S2 B0, 2 gt1 = S2 A1, 3 gt2 = D2 A0
       const T *in = (j == 1 ? B0 : (j == 2 ? A1 : A0)) + k * L.pn;
       return {in, j == 3 ? B.D[s2] : B.S[s2], nullptr, nullptr, Tr + (k * 4 + j) * L.FP};
-    }, GRAD ? 48 : 12, p1, n, 1, 1, n, p2, false, false);
+    }, GRAD ? 4 * NS : NS, p1, n, 1, 1, n, p2, false, false);
     // pointwise fluxes -> coefficients of the own test functions
     T *C = S0 + L.fC, *E = S0 + L.fE;
     for (int t = threadIdx.x; t < 2 * FP; t += blockDim.x) {
@@ -380,35 +470,47 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       const T tau = nb >= 0 ? max(m.tau[c], m.tau[nb]) : T(10) * m.tau[c];
       const T *wts = enr_c ? m.wt_face[opc] + (((size_t)ec * 6 + f) * m.fpmax[opc]) * WT : nullptr;
       const T *wto = (nb >= 0 && eb >= 0) ? m.wt_face[opc] + (((size_t)eb * 6 + (f ^ 1)) * m.fpmax[opc]) * WT : nullptr;
-      T xs[3], xo[3];
-      xs[d] = T(side); xs[t1] = B.x[s1][a1]; xs[t2] = B.x[s2][a2];
-      xo[d] = T(1 - side); xo[t1] = xs[t1]; xo[t2] = xs[t2];
-      T Ns[8], dNs[8][3], No[8], dNo[8][3];
-      if (enr_c) q1_weights(xs, Ns, dNs);
-      if (wto) q1_weights(xo, No, dNo);
-      T ub_s[3], ub_o[3], ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
+      T fs[3][2], fo[3][2];   // 1-D factors of the trilinear weights on both sides
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const T xe = e == d ? T(side) : (e == t1 ? B.x[s1][a1] : B.x[s2][a2]);
+        const T xoe = e == d ? T(1 - side) : xe;
+        fs[e][0] = T(1) - xe; fs[e][1] = xe;
+        fo[e][0] = T(1) - xoe; fo[e][1] = xoe;
+      }
+      T ub_s[3] = {0, 0, 0}, ub_o[3] = {0, 0, 0}, ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
       T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
       const T hob1 = nb >= 0 ? cell_h(m, nb, 1) : h[1];
+      const T hob[3] = {m.hx, hob1, m.hz};
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const T *tr_s = Tr + (((s * 2 + 0) * 3 + a) * 4) * L.FP;
-        const T *tr_o = Tr + (((s * 2 + 1) * 3 + a) * 4) * L.FP;
+        if (OP == OP_DIV && a != d) continue;   // the divergence needs the normal component only
+        const int ka = NCA == 1 ? 0 : a;
+        const T *tr_s = Tr + (((s * 2 + 0) * NCA + ka) * 4) * L.FP;
+        const T *tr_o = Tr + (((s * 2 + 1) * NCA + ka) * 4) * L.FP;
         ub_s[a] = tr_s[pt];
         if (GRAD) {
           gbs[a][d] = tr_s[L.FP + pt] * hinv[d];
           gbs[a][t1] = tr_s[2 * L.FP + pt] * hinv[t1];
           gbs[a][t2] = tr_s[3 * L.FP + pt] * hinv[t2];
         }
+        // enrichment u~_a = psi sum_v N_v e_av and its physical gradient
         if (enr_c) {
           const T *w = wts + pt * WT;
-          T sum = T(0);
-          for (int v = 0; v < 8; ++v) sum += Ns[v] * eo[a * 8 + v];
-          ut_s[a] = w[0] * sum;
+          T sN = T(0), sD[3] = {0, 0, 0};
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            T Nv, dN[3];
+            q1_vertex(fs, v, Nv, dN);
+            sN += Nv * eo[a * 8 + v];
+            if (GRAD)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eo[a * 8 + v];
+          }
+          ut_s[a] = w[0] * sN;
           if (GRAD)
-            for (int e = 0; e < 3; ++e) {
-              T g = T(0);
-              for (int v = 0; v < 8; ++v) g += eo[a * 8 + v] * (w[0] * dNs[v][e] * hinv[e] + Ns[v] * w[1 + e]);
-              gts[a][e] = g;
-            }
+#pragma unroll
+            for (int e = 0; e < 3; ++e) gts[a][e] = w[0] * sD[e] * hinv[e] + sN * w[1 + e];
         } else if (GRAD) {
           gts[a][0] = gts[a][1] = gts[a][2] = T(0);
         }
@@ -422,17 +524,21 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           }
           if (wto) {
             const T *w = wto + pt * WT;
-            T sum = T(0);
-            for (int v = 0; v < 8; ++v) sum += No[v] * en[s * 24 + a * 8 + v];
-            ut_o[a] = w[0] * sum;
-            if (GRAD) {
-              const T hob[3] = {m.hx, hob1, m.hz};
-              for (int e = 0; e < 3; ++e) {
-                T g = T(0);
-                for (int v = 0; v < 8; ++v) g += en[s * 24 + a * 8 + v] * (w[0] * dNo[v][e] / hob[e] + No[v] * w[1 + e]);
-                gto[a][e] = g;
-              }
+            const T *eb_a = en + s * 24 + a * 8;
+            T sN = T(0), sD[3] = {0, 0, 0};
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              T Nv, dN[3];
+              q1_vertex(fo, v, Nv, dN);
+              sN += Nv * eb_a[v];
+              if (GRAD)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eb_a[v];
             }
+            ut_o[a] = w[0] * sN;
+            if (GRAD)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) gto[a][e] = w[0] * sD[e] / hob[e] + sN * w[1 + e];
           } else if (GRAD) {
             gto[a][0] = gto[a][1] = gto[a][2] = T(0);
           }
@@ -441,6 +547,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           ub_o[a] = -ub_s[a];
           ut_o[a] = -ut_s[a];
           if (GRAD)
+#pragma unroll
             for (int e = 0; e < 3; ++e) { gbo[a][e] = gbs[a][e]; gto[a][e] = gts[a][e]; }
         }
       }
@@ -506,22 +613,39 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     __syncthreads();
     // enriched tests on these two faces
     if (enr_c && OP != OP_DIV) {
-      auto val = [&](int o, int t) -> T {
-        const int a = o >> 3, v = o & 7;
+      auto contrib = [&](int t, T *acc) {
         const int s = t / FP, pt = t - s * FP;
         const int a1 = pt % p1, a2 = pt / p1;
         T xs[3];
-        xs[d] = T(s); xs[t1] = B.x[s1][a1]; xs[t2] = B.x[s2][a2];
-        T Nv[8], dN[8][3];
-        q1_weights(xs, Nv, dN);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) xs[e] = e == d ? T(s) : (e == t1 ? B.x[s1][a1] : B.x[s2][a2]);
+        const T f[3][2] = {{T(1) - xs[0], xs[0]}, {T(1) - xs[1], xs[1]}, {T(1) - xs[2], xs[2]}};
         const T *w = m.wt_face[opc] + (((size_t)ec * 6 + 2 * d + s) * m.fpmax[opc]) * WT + pt * WT;
         const T *Es = E + s * 3 * 4 * L.FP;
-        T sum = Es[(a * 4) * L.FP + pt] * w[0] * Nv[v];
-        if (OP == OP_VISC)
-          for (int b = 0; b < 3; ++b) sum += Es[(a * 4 + 1 + b) * L.FP + pt] * (w[0] * dN[v][b] * hinv[b] + Nv[v] * w[1 + b]);
-        return sum;
+        T cv[3], cg[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          cv[a] = Es[(a * 4) * L.FP + pt] * w[0];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) cg[a][b] = OP == OP_VISC ? Es[(a * 4 + 1 + b) * L.FP + pt] : T(0);
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          T Nv, dN[3];
+          q1_vertex(f, v, Nv, dN);
+          if (OP == OP_VISC) {
+            T g[3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) g[b] = w[0] * dN[b] * hinv[b] + Nv * w[1 + b];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cv[a] * Nv + cg[a][0] * g[0] + cg[a][1] * g[1] + cg[a][2] * g[2];
+          } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cv[a] * Nv;
+          }
+        }
       };
-      reduce_outputs(24, 2 * FP, val, re);
+      reduce24<T>(2 * FP, contrib, re, S0 + L.part);
     }
     // I1: along t2 (p2 -> n); I2: along t1 (p1 -> n); item k = (face s, component a)
     T *I0 = S0 + L.fI0, *I1 = S0 + L.fI1, *I2 = S0 + L.fI2, *F2 = S0 + L.fF2, *G2 = S0 + L.fG2;
