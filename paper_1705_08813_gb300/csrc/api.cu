@@ -82,7 +82,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   *out = nullptr;
   if (P->degree < 1 || P->degree > 5) return set_error(DGW_EINVAL, "dgw_mesh_create: degree must be in 1..5");
   if (P->nx < 1 || P->ny < 1 || P->nz < 1) return set_error(DGW_EINVAL, "dgw_mesh_create: cell counts must be >= 1");
-  if (P->geometry != 0) return set_error(DGW_EINVAL, "dgw_mesh_create: only the channel geometry (0) is implemented");
+  if (P->geometry != 0 && P->geometry != 1)
+    return set_error(DGW_EINVAL, "dgw_mesh_create: geometry must be 0 (channel) or 1 (bump)");
   if (P->n_layers < 0 || 2 * P->n_layers > P->ny)
     return set_error(DGW_EINVAL, "dgw_mesh_create: need 0 <= n_layers and 2*n_layers <= ny");
   if (P->n_layers > 0 && P->enrich_l != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: only enrich_l = 1 is implemented");
@@ -103,6 +104,10 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->nc = (int)ncl;
   M->np = (long)M->nc * n * n * n;
   const int nx = P->nx, ny = P->ny, nz = P->nz;
+  const bool curved = P->geometry == 1;
+  const int qc = (3 * k) / 2 + 1;
+  fill_basis<double>(k, qc, P->q_wall, &M->basis64);
+  fill_basis<float>(k, qc, P->q_wall, &M->basis32);
   // vertex rows of the tanh-graded channel (Sec. 5.1)
   M->yv.resize(ny + 1);
   for (int j = 0; j <= ny; ++j)
@@ -111,10 +116,17 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   for (int j = 0; j < ny; ++j) M->hy[j] = M->yv[j + 1] - M->yv[j];
   // penalty tau_IP = (k+1)^2 A/V per cell, interior faces weighted 1/2, wall faces 1
   BoxGeometry geo;
-  box_geometry(k, nx, ny, nz, P->lx, P->lz, M->yv, geo);
-  M->tau = geo.tau;
-  const double hx = geo.hx, hz = geo.hz;
-  (void)hx; (void)hz;
+  CurvedHost cg;
+  if (curved) {
+    curved_geometry(*P, nx, ny, nz, k, M->basis64, cg);
+    M->tau.resize(M->nc);
+    for (int c = 0; c < M->nc; ++c) M->tau[c] = cg.tau[c % (nx * ny)];
+    M->cxn = cg.xn;
+    M->cyn = cg.yn;
+  } else {
+    box_geometry(k, nx, ny, nz, P->lx, P->lz, M->yv, geo);
+    M->tau = geo.tau;
+  }
   // enriched cells: bottom rows then top rows, lexicographic (x fastest, then z)
   M->enr.assign(M->nc, -1);
   const int L = P->n_layers;
@@ -135,17 +147,41 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->tauv.resize(8 * std::max(ne, 1));
   M->dye.resize(std::max(ne, 1));
   for (int e = 0; e < ne; ++e) {
-    const int c = M->enr_cell[e], j = (c / nx) % ny;
+    const int c = M->enr_cell[e], i = c % nx, j = (c / nx) % ny;
+    if (!curved) {
+      for (int v = 0; v < 8; ++v) {
+        const double y = M->yv[j + ((v >> 1) & 1)];
+        M->ywall[8 * e + v] = std::min(y - M->yv[0], M->yv[ny] - y);   // closest wall node
+        M->tauv[8 * e + v] = P->tau_w;
+      }
+      M->dye[e] = M->hy[j];
+      continue;
+    }
+    // curved: distance to the closest vertex of either wall (the map does not depend on z, so the
+    // closest wall vertex lies in the vertex's own z plane), and the mean of the four edges
+    // crossing the cell in the wall-normal direction
     for (int v = 0; v < 8; ++v) {
-      const double y = M->yv[j + ((v >> 1) & 1)];
-      M->ywall[8 * e + v] = std::min(y - M->yv[0], M->yv[ny] - y);   // closest wall node
+      double xv, yv;
+      bump_point(*P, nx, ny, i + (v & 1), j + ((v >> 1) & 1), &xv, &yv);
+      double best = 1e300;
+      for (int wj = 0; wj <= ny; wj += ny)
+        for (int wi = 0; wi <= nx; ++wi) {
+          double xw, yw;
+          bump_point(*P, nx, ny, wi, wj, &xw, &yw);
+          best = std::min(best, (xw - xv) * (xw - xv) + (yw - yv) * (yw - yv));
+        }
+      M->ywall[8 * e + v] = std::sqrt(best);
       M->tauv[8 * e + v] = P->tau_w;
     }
-    M->dye[e] = M->hy[j];
+    double len = 0.0;
+    for (int o = 0; o < 2; ++o) {
+      double x0, y0, x1, y1;
+      bump_point(*P, nx, ny, i + o, j, &x0, &y0);
+      bump_point(*P, nx, ny, i + o, j + 1, &x1, &y1);
+      len += std::sqrt((x1 - x0) * (x1 - x0) + (y1 - y0) * (y1 - y0));
+    }
+    M->dye[e] = 0.5 * len;
   }
-  const int qc = (3 * k) / 2 + 1;
-  fill_basis<double>(k, qc, P->q_wall, &M->basis64);
-  fill_basis<float>(k, qc, P->q_wall, &M->basis32);
   M->has32 = (P->precision_mask & 2) != 0;
   cudaError_t err = cudaSuccess;
   fill_view(M, M->v64);
@@ -158,11 +194,25 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->v64.enr = upload(M, M->enr.data(), M->nc, s, &err);
   M->v32.enr = M->v64.enr;
   M->v64.basis = upload(M, &M->basis64, 1, s, &err);
-  std::vector<double> rops;
-  box_rowops(geo, M->basis64, rops);
-  std::vector<float> rops32(rops.begin(), rops.end());
-  M->v64.rowops = upload(M, rops.data(), rops.size(), s, &err);
-  M->v32.rowops = upload(M, rops32.data(), rops32.size(), s, &err);
+  M->v64.geo = M->v32.geo = curved ? GEO_CURVED : GEO_BOX;
+  if (curved) {
+    auto up2 = [&](const std::vector<double> &h, const double **d64, const float **d32) {
+      *d64 = upload(M, h.data(), h.size(), s, &err);
+      if (M->has32) {
+        std::vector<float> f(h.begin(), h.end());
+        *d32 = upload(M, f.data(), f.size(), s, &err);
+      }
+    };
+    for (int t = 0; t < NMVOL; ++t) up2(cg.mvol[t], &M->v64.mvol[t], &M->v32.mvol[t]);
+    for (int t = 0; t < NQSET; ++t) up2(cg.mxf[t], &M->v64.mxf[t], &M->v32.mxf[t]);
+    for (int t = 0; t < 2; ++t) up2(cg.myf[t], &M->v64.myf[t], &M->v32.myf[t]);
+  } else {
+    std::vector<double> rops;
+    box_rowops(geo, M->basis64, rops);
+    std::vector<float> rops32(rops.begin(), rops.end());
+    M->v64.rowops = upload(M, rops.data(), rops.size(), s, &err);
+    M->v32.rowops = upload(M, rops32.data(), rops32.size(), s, &err);
+  }
   if (M->has32) {
     M->v32.hy = upload(M, hy32.data(), ny, s, &err);
     M->v32.tau = upload(M, tau32.data(), M->nc, s, &err);
@@ -216,11 +266,18 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
                               (size_t)ne * 6 * M->v64.fpmax[cls] * WT, s);
     }
   // Jacobi diagonal
-  std::vector<double> dg;
-  laplace_diagonal(geo, M->basis64, dg);
-  std::vector<float> dg32(dg.begin(), dg.end());
-  if (err == cudaSuccess) M->diag64 = upload(M, dg.data(), dg.size(), s, &err);
-  if (err == cudaSuccess) M->diag32 = upload(M, dg32.data(), dg32.size(), s, &err);
+  if (curved) {
+    if (err == cudaSuccess) M->diag64 = dalloc<double>(M, M->np, &err);
+    if (err == cudaSuccess) M->diag32 = dalloc<float>(M, M->np, &err);
+    if (err == cudaSuccess) err = launch_curved_diagonal(M->v64, M->diag64, s);
+    if (err == cudaSuccess) err = launch_to_float(M->diag64, M->diag32, M->np, s);
+  } else {
+    std::vector<double> dg;
+    laplace_diagonal(geo, M->basis64, dg);
+    std::vector<float> dg32(dg.begin(), dg.end());
+    if (err == cudaSuccess) M->diag64 = upload(M, dg.data(), dg.size(), s, &err);
+    if (err == cudaSuccess) M->diag32 = upload(M, dg32.data(), dg32.size(), s, &err);
+  }
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) {
     free_mesh(M);
@@ -247,16 +304,18 @@ dgw_status dgw_mesh_node_coords(dgw_mesh_t M, double *xyz) {
   (void)w;
   const int n = M->n1, nx = M->P.nx, ny = M->P.ny, nz = M->P.nz;
   const double hx = M->P.lx / nx, hz = M->P.lz / nz;
+  const bool curved = M->P.geometry == 1;
   for (int kz = 0; kz < nz; ++kz)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         const size_t c = i + (size_t)nx * (j + (size_t)ny * kz);
+        const size_t col = (size_t)(i + nx * j) * n * n;
         for (int c3 = 0; c3 < n; ++c3)
           for (int b = 0; b < n; ++b)
             for (int a = 0; a < n; ++a) {
               double *X = xyz + 3 * (c * n * n * n + a + n * (b + n * c3));
-              X[0] = hx * (i + z[a]);
-              X[1] = M->yv[j] + M->hy[j] * z[b];
+              X[0] = curved ? M->cxn[col + a + n * b] : hx * (i + z[a]);
+              X[1] = curved ? M->cyn[col + a + n * b] : M->yv[j] + M->hy[j] * z[b];
               X[2] = hz * (kz + z[c3]);
             }
       }

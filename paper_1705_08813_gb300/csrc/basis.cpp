@@ -62,7 +62,7 @@ void lobatto_nodes(int n, double *x) {
 }
 
 // Barycentric Lagrange basis on nodes z[0..n-1]: values l_j(s) and derivatives l_j'(s).
-static void lagrange_row(int n, const double *z, double s, double *val, double *der) {
+void lagrange_row(int n, const double *z, double s, double *val, double *der) {
   double bw[NMAX];
   for (int j = 0; j < n; ++j) {
     double p = 1.0;

@@ -37,16 +37,31 @@ struct Basis {
 // Per-point wall-table record of an enriched cell: psi and its physical gradient.
 constexpr int WT = 4;
 
-// Device-side view of a mesh in precision T (geometry of the channel of boxes).
+// Cell geometry: axis-aligned boxes (channel) or isoparametric curved cells (bump).
+enum { GEO_BOX = 0, GEO_CURVED = 1 };
+
+// Metric record of a curved cell at one point: J^-1 row-major ([r*3+c] = d xi_r / d x_c), det J.
+constexpr int MREC = 10;
+// Volume metric tables by (x-set, y-set): (lin, lin), (conv, conv), (lin, wall), (conv, wall).
+constexpr int NMVOL = 4;
+
+// Device-side view of a mesh in precision T.
 template <typename T>
 struct MeshView {
   int nx, ny, nz, n1, nc, ne;
   int q[NQSET];       // point counts of the quadrature sets (host-visible copy)
   long np, nu;
+  int geo;            // GEO_BOX or GEO_CURVED
   T hx, hz;
-  const T *hy;        // [ny] row heights
+  const T *hy;        // [ny] row heights (boxes)
   const T *tau;       // [nc] penalty tau_IP per cell
-  const T *rowops;    // [ny][rowops_size] factorised 1-D Laplace operators per cell row
+  const T *rowops;    // [ny][rowops_size] factorised 1-D Laplace operators per cell row (boxes)
+  // curved metric tables per metric column m = i + nx*j (the map is an extrusion along z):
+  // mvol[pair]: [m][a1][a0][MREC]; mxf[y-set]: [m][side][a1][MREC] (faces xi_0 = side);
+  // myf[x-set]: [m][side][a0][MREC] (faces xi_1 = side); faces xi_2 = side use mvol
+  const T *mvol[NMVOL];
+  const T *mxf[NQSET];
+  const T *myf[2];
   const int *enr;     // [nc] enriched index or -1
   T visc;             // kinematic viscosity nu
   const Basis<T> *basis;
@@ -80,6 +95,7 @@ struct dgw_mesh {
   std::vector<double> ywall;    // [ne][8] vertex wall distances
   std::vector<double> tauv;     // [ne][8] vertex wall shear stresses
   std::vector<double> dye;      // [ne] wall-normal width
+  std::vector<double> cxn, cyn; // curved: nodal (x, y) per metric column [nx*ny][n*n]
   dgw::Basis<double> basis64;   // host copies of the basis tables
   dgw::Basis<float> basis32;
   // device allocations (owned)
@@ -117,6 +133,8 @@ void lobatto_nodes(int n, double *x);
 template <typename T>
 void fill_basis(int k, int q_conv, int q_wall, Basis<T> *b);
 void embed_matrix(int n, double a, double b, double *P);
+// Lagrange basis on the nodes z[0..n-1] at s: values l_j(s) and derivatives l_j'(s).
+void lagrange_row(int n, const double *z, double s, double *val, double *der);
 
 // Geometry of a channel of boxes: uniform x and z spacing, graded rows in y.
 struct BoxGeometry {
@@ -134,15 +152,29 @@ void box_rowops(const BoxGeometry &g, const Basis<double> &B, std::vector<double
 void host_box_apply(const BoxGeometry &g, const Basis<double> &B, const std::vector<double> &R, const double *x,
                     double *y);
 
+// Curved bump channel (geometry 1), host side: metric tables, penalty and wall data of a mesh
+// with nx x ny x nz cells of degree k over the bump map of the parameters.
+struct CurvedHost {
+  int nx, ny, nz, k;
+  std::vector<double> mvol[NMVOL], mxf[NQSET], myf[2];   // layouts as in MeshView
+  std::vector<double> tau;                               // [nx*ny] per metric column
+  std::vector<double> xn, yn;                            // [nx*ny][n*n] nodal (x, y), x-node fastest
+};
+void curved_geometry(const dgw_mesh_params &P, int nx, int ny, int nz, int k, const Basis<double> &B, CurvedHost &G);
+// Physical (x, y) of the logical coordinates (a0, a1) of the bump map (z is lz a2 / nz).
+void bump_point(const dgw_mesh_params &P, int nx, int ny, double a0, double a1, double *x, double *y);
+
 // kernels (launched by api.cu)
 template <typename T>
 cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s);
+// Jacobi diagonal of the SIPG Laplacian of a curved mesh (FP64, one thread per DoF)
+cudaError_t launch_curved_diagonal(const MeshView<double> &m, double *dg, cudaStream_t s);
 template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s);
 cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 
-enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2 };
+enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3 };
 
 }  // namespace dgw

@@ -242,6 +242,7 @@ static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, cudaStre
 
 template <typename T>
 cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s) {
+  if (m.geo == GEO_CURVED) return launch_vector_op<T>(OP_LAP, m, p, y, s);   // per-point metrics
   switch (m.n1) {
     case 2: return launch_box_k<T, 1>(m, p, y, s);
     case 3: return launch_box_k<T, 2>(m, p, y, s);

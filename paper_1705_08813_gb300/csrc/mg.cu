@@ -454,14 +454,58 @@ static cudaError_t estimate_lmax(Lvl<T> *L, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// Curved levels: metric tables of a coarser mesh over the same map, uploaded in precision X.
+template <typename X>
+static void upload_curved(Lvl<X> *L, const CurvedHost &g, MeshView<X> &v, cudaError_t &e, cudaStream_t s) {
+  auto up = [&](const std::vector<double> &h) -> const X * {
+    std::vector<X> hx(h.begin(), h.end());
+    X *d = lalloc<X>(L, hx.size(), e, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, hx.data(), hx.size() * sizeof(X), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the staging vector dies here
+    return d;
+  };
+  v.geo = GEO_CURVED;
+  for (int t = 0; t < NMVOL; ++t) v.mvol[t] = up(g.mvol[t]);
+  for (int t = 0; t < NQSET; ++t) v.mxf[t] = up(g.mxf[t]);
+  for (int t = 0; t < 2; ++t) v.myf[t] = up(g.myf[t]);
+  std::vector<double> tau((size_t)g.nx * g.ny * g.nz);
+  for (size_t c = 0; c < tau.size(); ++c) tau[c] = g.tau[c % ((size_t)g.nx * g.ny)];
+  v.tau = up(tau);
+  v.hy = nullptr;
+  v.rowops = nullptr;
+}
+
+// Dense matrix of a level operator, assembled on the device column by column from the FP64
+// operator of the level (curved meshes have no host-side operator).
+static cudaError_t assemble_device(const MeshView<double> &v, int N, std::vector<double> &A, cudaStream_t s) {
+  double *I = nullptr, *Y = nullptr;
+  cudaError_t e = cudaMalloc(&I, (size_t)N * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)N * N * sizeof(double));
+  std::vector<double> eye((size_t)N * N, 0.0);
+  for (int j = 0; j < N; ++j) eye[(size_t)j * N + j] = 1.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(I, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  for (int j = 0; j < N && e == cudaSuccess; ++j) e = launch_laplace<double>(v, I + (size_t)j * N, Y + (size_t)j * N, s);
+  std::vector<double> cols((size_t)N * N);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cols.data(), Y, cols.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (I) cudaFree(I);
+  if (Y) cudaFree(Y);
+  A.assign((size_t)N * N, 0.0);
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + j] = cols[(size_t)j * N + i];
+  return e;
+}
+
 template <typename T>
 static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<T> &fine, const T *fine_basis_dev,
                                    cudaStream_t s) {
   (void)fine_basis_dev;
   cudaError_t e = cudaSuccess;
+  const bool curved = M->P.geometry == 1;
   const int k = M->P.degree, n = k + 1, n3 = n * n * n;
   int nx = M->P.nx, ny = M->P.ny, nz = M->P.nz;
   std::vector<double> yv = M->yv;
+  MeshView<double> v64 = M->v64;   // FP64 view of the current level (curved: diagonal, dense assembly)
   for (int lev = 0; e == cudaSuccess; ++lev) {
     Lvl<T> *L = new Lvl<T>();
     H->L.push_back(L);
@@ -477,26 +521,46 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       L->view.np = L->n;
       L->view.hx = (T)L->geo.hx;
       L->view.hz = (T)L->geo.hz;
-      std::vector<T> hy(L->geo.hy.begin(), L->geo.hy.end()), tau(L->geo.tau.begin(), L->geo.tau.end());
-      T *hyd = lalloc<T>(L, hy.size(), e, s), *taud = lalloc<T>(L, tau.size(), e, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(hyd, hy.data(), hy.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(taud, tau.data(), tau.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-      L->view.hy = hyd;
-      L->view.tau = taud;
       L->view.enr = nullptr;
-      std::vector<double> rops;
-      box_rowops(L->geo, M->basis64, rops);
-      std::vector<T> ropsT(rops.begin(), rops.end());
-      T *rd = lalloc<T>(L, ropsT.size(), e, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(rd, ropsT.data(), ropsT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-      L->view.rowops = rd;
+      if (curved) {
+        CurvedHost cg;
+        curved_geometry(M->P, nx, ny, nz, k, M->basis64, cg);
+        upload_curved<T>(L, cg, L->view, e, s);
+        v64 = M->v64;
+        v64.nx = nx; v64.ny = ny; v64.nz = nz;
+        v64.nc = nx * ny * nz;
+        v64.ne = 0;
+        v64.np = L->n;
+        v64.enr = nullptr;
+        Lvl<double> tmp;   // owns nothing: the FP64 tables live with the level
+        upload_curved<double>(&tmp, cg, v64, e, s);
+        L->allocs.insert(L->allocs.end(), tmp.allocs.begin(), tmp.allocs.end());
+      } else {
+        std::vector<T> hy(L->geo.hy.begin(), L->geo.hy.end()), tau(L->geo.tau.begin(), L->geo.tau.end());
+        T *hyd = lalloc<T>(L, hy.size(), e, s), *taud = lalloc<T>(L, tau.size(), e, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hyd, hy.data(), hy.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(taud, tau.data(), tau.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        L->view.hy = hyd;
+        L->view.tau = taud;
+        std::vector<double> rops;
+        box_rowops(L->geo, M->basis64, rops);
+        std::vector<T> ropsT(rops.begin(), rops.end());
+        T *rd = lalloc<T>(L, ropsT.size(), e, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rd, ropsT.data(), ropsT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        L->view.rowops = rd;
+      }
     }
-    std::vector<double> dg;
-    laplace_diagonal(L->geo, M->basis64, dg);
     double *dg_dev = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&dg_dev, dg.size() * sizeof(double));
     L->dinv = lalloc<T>(L, L->n, e, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dg_dev, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&dg_dev, L->n * sizeof(double));
+    if (curved) {
+      if (e == cudaSuccess) e = launch_curved_diagonal(v64, dg_dev, s);
+    } else {
+      std::vector<double> dg;
+      laplace_diagonal(L->geo, M->basis64, dg);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dg_dev, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     if (e == cudaSuccess) { note_launch(); inv_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(dg_dev, L->dinv, L->n); }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (dg_dev) cudaFree(dg_dev);
@@ -518,11 +582,16 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     X.cf[0] = cf[0]; X.cf[1] = cf[1]; X.cf[2] = cf[2];
     X.py = nullptr;
     if (cf[1] == 2) {
-      // child rows 2J and 2J+1 of coarse row J split it in the ratio of their heights
+      // child rows 2J and 2J+1 of coarse row J split it in the ratio of their heights (boxes) or
+      // at the middle of the logical coordinate (curved cells are images of the logical grid)
       const int cny = ny / 2, nn = n * n;
       std::vector<double> P((size_t)cny * 2 * nn);
       for (int J = 0; J < cny; ++J) {
-        const double h0 = yv[2 * J + 1] - yv[2 * J], h1 = yv[2 * J + 2] - yv[2 * J + 1], r = h0 / (h0 + h1);
+        double r = 0.5;
+        if (!curved) {
+          const double h0 = yv[2 * J + 1] - yv[2 * J], h1 = yv[2 * J + 2] - yv[2 * J + 1];
+          r = h0 / (h0 + h1);
+        }
         embed_matrix(n, 0.0, r, &P[((size_t)J * 2 + 0) * nn]);
         embed_matrix(n, r, 1.0 - r, &P[((size_t)J * 2 + 1) * nn]);
       }
@@ -553,6 +622,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
   Lvl<T> *D = C;
   Basis<double> b1d;
   const Basis<double> *Bd = &M->basis64;
+  MeshView<double> d64 = v64;   // FP64 view of the dense level (curved)
   if (kd == 1) {
     D = new Lvl<T>();
     H->L.push_back(D);
@@ -582,17 +652,40 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     if (e == cudaSuccess) { D->allocs.push_back(p); D->sc = (double *)p; }
     if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
     if (e == cudaSuccess) { D->allocs.push_back(p); D->partial = (double *)p; }
+    if (curved) {
+      // degree-1 tables and basis of the coarsest cells for the dense assembly
+      CurvedHost cg;
+      curved_geometry(M->P, C->geo.nx, C->geo.ny, C->geo.nz, 1, b1d, cg);
+      Lvl<double> tmp;
+      d64.n1 = 2;
+      d64.np = D->n;
+      for (int t = 0; t < NQSET; ++t) d64.q[t] = b1d.q[t];
+      double *bmem = lalloc<double>(&tmp, (sizeof(b1d) + sizeof(double) - 1) / sizeof(double), e, s);
+      Basis<double> *bdev = reinterpret_cast<Basis<double> *>(bmem);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(bdev, &b1d, sizeof(b1d), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      d64.basis = bdev;
+      upload_curved<double>(&tmp, cg, d64, e, s);
+      D->allocs.insert(D->allocs.end(), tmp.allocs.begin(), tmp.allocs.end());
+    }
   }
-  // assemble the level operator on the host column by column, invert A + c 1 1^T
+  if (e != cudaSuccess) return e;
+  // assemble the level operator column by column, invert A + c 1 1^T
   const int N = (int)D->n;
-  std::vector<double> rops;
-  box_rowops(D->geo, *Bd, rops);
-  std::vector<double> A((size_t)N * N), ej(N, 0.0), col(N);
-  for (int jc = 0; jc < N; ++jc) {
-    ej[jc] = 1.0;
-    host_box_apply(D->geo, *Bd, rops, ej.data(), col.data());
-    ej[jc] = 0.0;
-    for (int i = 0; i < N; ++i) A[(size_t)i * N + jc] = col[i];
+  std::vector<double> A((size_t)N * N);
+  if (curved) {
+    e = assemble_device(d64, N, A, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    std::vector<double> rops;
+    box_rowops(D->geo, *Bd, rops);
+    std::vector<double> ej(N, 0.0), col(N);
+    for (int jc = 0; jc < N; ++jc) {
+      ej[jc] = 1.0;
+      host_box_apply(D->geo, *Bd, rops, ej.data(), col.data());
+      ej[jc] = 0.0;
+      for (int i = 0; i < N; ++i) A[(size_t)i * N + jc] = col[i];
+    }
   }
   if (!dense_regularised_inverse(A, N)) return e;   // keep the iterative coarse solve
   std::vector<T> AT(A.begin(), A.end());

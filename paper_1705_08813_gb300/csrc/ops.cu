@@ -1,43 +1,27 @@
-// Matrix-free DG vector operators on the channel of boxes, with enriched wall cells (Sec. 4.2,
-// Sec. 4.4): one CTA per cell evaluates the volume integral of its cell and the integrals over its
-// six faces for its own test functions, re-reading the neighbours' coefficients (cell-centric face
-// loop: no atomics, deterministic).
+// Matrix-free DG operators with one CTA per cell: the volume integral of the cell and the integrals
+// over its six faces for its own test functions, re-reading the neighbours' coefficients
+// (cell-centric face loop: no atomics, deterministic).
 //
 //   OP_DIV  b = -C(q,u)                   (Sec. 4.2, velocity divergence; {{u}} = u^- on walls)
 //   OP_CONV y = F^c(v,u), LF flux         (Sec. 4.2, convective term; mirror state on walls)
 //   OP_VISC y = -F^nu(vbar,v~;ubar,u~)    (eq. viscous_multiscale, harmweights, minvt)
+//   OP_LAP  y = A_L p, SIPG               (eq. ipflux; curved cells only, boxes use laplace_box.cu)
 //
 // Wall-layer cells add the enrichment u~ = psi sum_B N_B u~_B (eq. enrichment) at q_wall
 // wall-normal Gauss points, with psi and grad psi read from the wall tables.
 //
-// Every sum-factorisation phase is batched over the three velocity components, over both faces
-// normal to one direction and over both sides of those faces, so one barrier separates phases
-// that each carry enough independent outputs to occupy the CTA (about 35 barriers per cell).
+// Geometry: GEO_BOX cells are axis-aligned boxes (diagonal Jacobian from the row spacing);
+// GEO_CURVED cells are isoparametric Q_k images of the reference cube (the periodic-hill setting of
+// Sec. 5.2, the mesh "mapped onto the exact ... geometry using the same polynomial ansatz"), with
+// J^-1 and det J read per quadrature point from the metric tables.
+//
+// Every sum-factorisation phase is batched over the velocity components, over both faces normal
+// to one direction and over both sides of those faces, so one barrier separates phases that each
+// carry enough independent outputs to occupy the CTA (about 35 barriers per cell).
+#include "metric.cuh"
 #include "sumfac.cuh"
 
 namespace dgw {
-
-template <typename T>
-__device__ __forceinline__ void cell_ijk(const MeshView<T> &m, int c, int &i, int &j, int &kz) {
-  i = c % m.nx;
-  j = (c / m.nx) % m.ny;
-  kz = c / (m.nx * m.ny);
-}
-
-// neighbour across face f = 2d + side, -1 on a wall
-template <typename T>
-__device__ __forceinline__ int neighbour(const MeshView<T> &m, int c, int f) {
-  int i, j, kz;
-  cell_ijk(m, c, i, j, kz);
-  const int d = f >> 1, s = (f & 1) ? 1 : -1;
-  if (d == 0) i = (i + s + m.nx) % m.nx;
-  else if (d == 2) kz = (kz + s + m.nz) % m.nz;
-  else {
-    j += s;
-    if (j < 0 || j >= m.ny) return -1;
-  }
-  return i + m.nx * (j + m.ny * kz);
-}
 
 template <typename T>
 __device__ __forceinline__ T cell_h(const MeshView<T> &m, int c, int d) {
@@ -175,8 +159,13 @@ struct VecPlan {
   int fV2, fN2, fA0, fA1, fB0, fTr, fC, fE, fUn, fI0, fI1, fI2, fF2, fG2, face_end;  // face regions
 };
 
-__host__ __device__ inline VecPlan vec_plan(int op, int n, int qin, int qw) {
+__host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin, int qw) {
   VecPlan p;
+  if (op == OP_LAP) qw = qin;   // the Laplacian has no enriched point sets
+  const bool grad = op == OP_VISC || op == OP_LAP;
+  const int nin = op == OP_LAP ? 1 : 3, nout = (op == OP_DIV || op == OP_LAP) ? 1 : 3;
+  const int nca = op == OP_LAP ? 1 : ((op == OP_DIV && !curved) ? 1 : 3);
+  const int ns = 4 * nca;
   p.n = n;
   p.n3 = n * n * n;
   p.qi = qin;
@@ -186,75 +175,79 @@ __host__ __device__ inline VecPlan vec_plan(int op, int n, int qin, int qw) {
   p.pn = p.qy * n;
   const int nn = n * n;
   const int SX = qin * nn, SZ = qin * p.qy * n;
+  const int ka = (grad ? 2 : 1) * nin > 2 * nout ? (grad ? 2 : 1) * nin : 2 * nout;
+  const int kb = (grad ? 3 : 1) * nin > 3 * nout ? (grad ? 3 : 1) * nin : 3 * nout;
   int o = 0;
-  p.uo = o; o += 3 * p.n3;
-  p.r = o; o += 3 * p.n3;
+  p.uo = o; o += nin * p.n3;
+  p.r = o; o += nout * p.n3;
   p.eo = o; o += 24;
   p.re = o; o += 24;
   p.en = o; o += 48;   // enrichment coefficients of the two neighbours of one direction
   p.part = o; o += 4 * 24;   // per-warp partial sums of the enriched reductions (128 threads)
   p.work = o;
   int v = o;
-  p.vA = v; v += 6 * SX;
-  p.vB = v; v += 9 * SZ;
-  p.vV = v; v += (op == 2 ? 0 : 3 * p.P);
-  p.vG = v; v += 9 * p.P;
-  p.vGt = v; v += (op == 2 ? 9 * p.P : 0);
+  p.vA = v; v += ka * SX;
+  p.vB = v; v += kb * SZ;
+  p.vV = v; v += (op == OP_DIV || op == OP_CONV) ? 3 * p.P : 0;
+  p.vG = v; v += (op == OP_CONV || op == OP_VISC ? 9 : 3) * p.P;
+  p.vGt = v; v += op == OP_VISC ? 9 * p.P : 0;
   p.vol_end = v;
-  int f = o;   // 12 trace slots: 2 faces x 2 sides x 3 components
-  p.fV2 = f; f += 12 * nn;
-  p.fN2 = f; f += 12 * nn;
-  p.fA0 = f; f += 12 * p.pn;
-  p.fA1 = f; f += 12 * p.pn;
-  p.fB0 = f; f += 12 * p.pn;
-  p.fTr = f; f += 12 * 4 * p.FP;     // value, d/dxi_d, d/dxi_t1, d/dxi_t2
+  int f = o;   // trace slots: 2 faces x 2 sides x nca components
+  p.fV2 = f; f += ns * nn;
+  p.fN2 = f; f += grad ? ns * nn : 0;
+  p.fA0 = f; f += ns * p.pn;
+  p.fA1 = f; f += grad ? ns * p.pn : 0;
+  p.fB0 = f; f += grad ? ns * p.pn : 0;
+  p.fTr = f; f += ns * 4 * p.FP;     // value, d/dxi_d, d/dxi_t1, d/dxi_t2
   p.fC = f; f += 2 * 3 * 4 * p.FP;   // coefficients of the standard test functions (face, component)
-  p.fE = f; f += 2 * 3 * 4 * p.FP;   // coefficients of the enriched test functions
+  p.fE = f; f += (op == OP_CONV || op == OP_VISC) ? 2 * 3 * 4 * p.FP : 0;   // enriched test functions
   p.face_end = f;
   // both neighbours' coefficients: dead once the layers are taken (only en must survive)
   p.fUn = p.fA0;
-  if (p.fUn + 6 * p.n3 > p.face_end) p.face_end = p.fUn + 6 * p.n3;
+  if (p.fUn + 2 * nin * p.n3 > p.face_end) p.face_end = p.fUn + 2 * nin * p.n3;
   // integration arrays: written after the traces are consumed, must not reach the coefficients C
-  const int isz = 18 * p.pn + 12 * nn;
+  const int isz = 2 * nout * (3 * p.pn + 2 * nn);
   int g = p.fV2 + isz <= p.fC ? p.fV2 : p.face_end;
-  p.fI0 = g; g += 6 * p.pn;
-  p.fI1 = g; g += 6 * p.pn;
-  p.fI2 = g; g += 6 * p.pn;
-  p.fF2 = g; g += 6 * nn;
-  p.fG2 = g; g += 6 * nn;
+  p.fI0 = g; g += 2 * nout * p.pn;
+  p.fI1 = g; g += 2 * nout * p.pn;
+  p.fI2 = g; g += 2 * nout * p.pn;
+  p.fF2 = g; g += 2 * nout * nn;
+  p.fG2 = g; g += 2 * nout * nn;
   if (g > p.face_end) p.face_end = g;
   p.total = p.vol_end > p.face_end ? p.vol_end : p.face_end;
   return p;
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int GEO>
 __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Basis<T> &B = *reinterpret_cast<Basis<T> *>(smem_raw);
   T *S0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Basis<T>) + 15) / 16) * 16);
   load_basis(m.basis, &B);
+  constexpr bool CURVED = GEO == GEO_CURVED;
+  constexpr bool GRAD = OP == OP_VISC || OP == OP_LAP;
+  constexpr int NIN = OP == OP_LAP ? 1 : 3;                             // input components
+  constexpr int NOUT = (OP == OP_DIV || OP == OP_LAP) ? 1 : 3;          // output components
   const int n = m.n1, nn = n * n;
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const int opc = OP == OP_CONV ? 1 : 0;   // wall-table class
-  const VecPlan L = vec_plan(OP, n, m.q[qset], m.q[QSET_WALL]);
+  const VecPlan L = vec_plan(OP, CURVED, n, m.q[qset], m.q[QSET_WALL]);
   const int n3 = L.n3;
-  const int ncomp = OP == OP_DIV ? 1 : 3;
-  constexpr bool GRAD = OP == OP_VISC;
   T *uo = S0 + L.uo, *r = S0 + L.r, *eo = S0 + L.eo, *re = S0 + L.re, *un = S0 + L.fUn, *en = S0 + L.en;
   const int c = blockIdx.x;
-  const int ec = m.enr[c];
+  const int ec = OP == OP_LAP ? -1 : m.enr[c];
   const bool enr_c = ec >= 0;
   const T nu = m.visc;
-  for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) {
-    uo[t] = u[(size_t)c * 3 * n3 + t];
-    r[t] = T(0);
-  }
+  const int col = CURVED ? metric_col(m, c) : 0;
+  for (int t = threadIdx.x; t < NIN * n3; t += blockDim.x) uo[t] = u[(size_t)c * NIN * n3 + t];
+  for (int t = threadIdx.x; t < NOUT * n3; t += blockDim.x) r[t] = T(0);
   for (int t = threadIdx.x; t < 24; t += blockDim.x) {
     eo[t] = enr_c ? u[3 * m.np + (size_t)ec * 24 + t] : T(0);
     re[t] = T(0);
   }
   __syncthreads();
-  const T h[3] = {m.hx, m.hy[(c / m.nx) % m.ny], m.hz};
+  T h[3] = {T(1), T(1), T(1)};
+  if (!CURVED) { h[0] = m.hx; h[1] = m.hy[(c / m.nx) % m.ny]; h[2] = m.hz; }
   const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
   const int sets[3] = {qset, enr_c ? QSET_WALL : qset, qset};
   const int q0 = B.q[sets[0]], q1 = B.q[sets[1]], q2 = B.q[sets[2]];
@@ -263,6 +256,21 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   const T *wtv = enr_c ? m.wt_vol[opc] + (size_t)ec * m.nvol[opc] * WT : nullptr;
   const T *S_[3] = {B.S[sets[0]], B.S[sets[1]], B.S[sets[2]]};
   const T *D_[3] = {B.D[sets[0]], B.D[sets[1]], B.D[sets[2]]};
+  // metric at volume point (i0, i1): J^-1 and the volume weight dV
+  auto vol_metric = [&](int i0, int i1, int i2, T Ji[3][3], T &dV) {
+    const T w3 = B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
+    if (CURVED) {
+      T det;
+      load_rec(vol_rec(m, B, col, sets[0], sets[1], i0, i1), Ji, det);
+      dV = fabs(det) * w3;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Ji[a][b] = a == b ? hinv[a] : T(0);
+      dV = vol * w3;
+    }
+  };
 
   // ================= volume =================
   {
@@ -270,26 +278,31 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     const int SX = q0 * nn, SZ = q0 * q1 * n;
     // P1: X0_a = S_x u_a (and X1_a = D_x u_a for gradients)
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int a = b % 3, k = b / 3;
+      const int a = b % NIN, k = b / NIN;
       return {uo + a * n3, k ? D_[0] : S_[0], nullptr, nullptr, A + b * SX};
-    }, GRAD ? 6 : 3, n, n, n, 0, n, q0, false, false);
+    }, (GRAD ? 2 : 1) * NIN, n, n, n, 0, n, q0, false, false);
     // P2: Y00_a = S_y X0_a (Y01_a = D_y X0_a, Y10_a = S_y X1_a)
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int a = b % 3, k = b / 3;   // k: 0 Y00, 1 Y01, 2 Y10
-      return {A + (k == 2 ? 3 + a : a) * SX, k == 1 ? D_[1] : S_[1], nullptr, nullptr, Bv + b * SZ};
-    }, GRAD ? 9 : 3, q0, n, n, 1, n, q1, false, false);
-    // P3: values (DIV, CONV) or reference gradients (VISC) at the points
+      const int a = b % NIN, k = b / NIN;   // k: 0 Y00, 1 Y01, 2 Y10
+      return {A + (k == 2 ? NIN + a : a) * SX, k == 1 ? D_[1] : S_[1], nullptr, nullptr, Bv + b * SZ};
+    }, (GRAD ? 3 : 1) * NIN, q0, n, n, 1, n, q1, false, false);
+    // P3: values (DIV, CONV) or reference gradients (VISC, LAP) at the points
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int a = b % 3, k = b / 3;
+      const int a = b % NIN, k = b / NIN;
       if (!GRAD) return {Bv + a * SZ, S_[2], nullptr, nullptr, V + a * P};
       // k = 0: d/dz from Y00; 1: d/dy from Y01; 2: d/dx from Y10
       return {Bv + b * SZ, k == 0 ? D_[2] : S_[2], nullptr, nullptr, G + (a * 3 + 2 - k) * P};
-    }, GRAD ? 9 : 3, q0, q1, n, 2, n, q2, false, false);
+    }, (GRAD ? 3 : 1) * NIN, q0, q1, n, 2, n, q2, false, false);
     // P4: pointwise test-function coefficients (H_{a,d} multiplies d phi / d xi_d)
     const T *nutv = (OP == OP_VISC && enr_c) ? m.nut_vol + (size_t)ec * m.nvol[0] : nullptr;
     for (int t = threadIdx.x; t < P; t += blockDim.x) {
       const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-      const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
+      T dV, Ji[3][3];
+      if (CURVED) {
+        vol_metric(i0, i1, i2, Ji, dV);
+      } else {
+        dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
+      }
       // enrichment at the point: sN_a = sum_v N_v e_av, sD_ad = sum_v dN_v/dxi_d e_av
       T sN[3] = {0, 0, 0}, sD[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       const T *w = nullptr;
@@ -317,43 +330,76 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
             uu[a] += w[0] * sN[a];
             V[a * P + t] = uu[a];
           }
-        if (OP == OP_DIV) {
+        if (CURVED) {
+          T cf[3];
+          if (OP == OP_DIV) {
+            phys_to_ref(Ji, uu, cf);
+            for (int d = 0; d < 3; ++d) G[d * P + t] = dV * cf[d];
+          } else {
+            phys_to_ref(Ji, uu, cf);   // J^-1 u: the convective coefficient is -dV u_a (J^-1 u)_d
+            for (int a = 0; a < 3; ++a)
+              for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = -dV * uu[a] * cf[d];
+          }
+        } else if (OP == OP_DIV) {
           for (int d = 0; d < 3; ++d) G[d * P + t] = dV * uu[d] * hinv[d];
         } else {
           for (int a = 0; a < 3; ++a)
             for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = -dV * uu[a] * uu[d] * hinv[d];
         }
+      } else if (OP == OP_LAP) {
+        const T gr[3] = {G[t], G[P + t], G[2 * P + t]};
+        T g[3], cf[3];
+        ref_to_phys(Ji, gr, g);
+        phys_to_ref(Ji, g, cf);
+        for (int d = 0; d < 3; ++d) G[d * P + t] = dV * cf[d];
       } else {
         T gb[3][3], tb[3][3];
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) gb[a][d] = G[(a * 3 + d) * P + t] * hinv[d];
+        for (int a = 0; a < 3; ++a) {
+          if (CURVED) {
+            const T gr[3] = {G[(a * 3) * P + t], G[(a * 3 + 1) * P + t], G[(a * 3 + 2) * P + t]};
+            ref_to_phys(Ji, gr, gb[a]);
+          } else {
+            for (int d = 0; d < 3; ++d) gb[a][d] = G[(a * 3 + d) * P + t] * hinv[d];
+          }
+        }
         for (int a = 0; a < 3; ++a)
           for (int d = 0; d < 3; ++d) tb[a][d] = nu * (gb[a][d] + gb[d][a]);
         if (enr_c) {
           T gt[3][3];
-          for (int a = 0; a < 3; ++a)
+          for (int a = 0; a < 3; ++a) {
+            if (CURVED) ref_to_phys(Ji, sD[a], gt[a]);
             for (int d = 0; d < 3; ++d) {
-              gt[a][d] = w[0] * sD[a][d] * hinv[d] + sN[a] * w[1 + d];
+              gt[a][d] = w[0] * (CURVED ? gt[a][d] : sD[a][d] * hinv[d]) + sN[a] * w[1 + d];
               Gt[(a * 3 + d) * P + t] = gt[a][d];
             }
+          }
           const T nut = nutv[t];
           const T nuh = min(nu + nut, T(2) * sqrt(nu * (nu + nut)));   // eq. (minvt)
           for (int a = 0; a < 3; ++a)
             for (int d = 0; d < 3; ++d) tb[a][d] += nuh * (gt[a][d] + gt[d][a]);
         }
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = dV * tb[a][d] * hinv[d];
+        for (int a = 0; a < 3; ++a) {
+          if (CURVED) {
+            T cf[3];
+            phys_to_ref(Ji, tb[a], cf);
+            for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = dV * cf[d];
+          } else {
+            for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = dV * tb[a][d] * hinv[d];
+          }
+        }
       }
     }
     __syncthreads();
     // enriched test functions: -(grad(psi N_v) e_a, u x u) or (eps(psi N_v e_a), 2(nu+nu_t) eps(u~))
-    if (enr_c && OP != OP_DIV) {
+    if (enr_c && (OP == OP_CONV || OP == OP_VISC)) {
       auto contrib = [&](int t, T *acc) {
         const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
         const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
         const T *w = wtv + t * WT;
-        const T dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
+        T dV, Ji[3][3];
+        if (CURVED) vol_metric(i0, i1, i2, Ji, dV);
+        else dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
         T cf[3][3];   // coefficient of d(psi N_v)/dx_d in output (a, v)
         if (OP == OP_CONV) {
           const T uu[3] = {V[t], V[P + t], V[2 * P + t]};
@@ -373,8 +419,15 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           T Nv, dN[3];
           q1_vertex(f, v, Nv, dN);
           T g[3];
+          if (CURVED) {
+            T gp[3];
+            ref_to_phys(Ji, dN, gp);
 #pragma unroll
-          for (int d = 0; d < 3; ++d) g[d] = w[0] * dN[d] * hinv[d] + Nv * w[1 + d];
+            for (int d = 0; d < 3; ++d) g[d] = w[0] * gp[d] + Nv * w[1 + d];
+          } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[d] = w[0] * dN[d] * hinv[d] + Nv * w[1 + d];
+          }
 #pragma unroll
           for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cf[a][0] * g[0] + cf[a][1] * g[1] + cf[a][2] * g[2];
         }
@@ -383,22 +436,23 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
     // P5-P7: integrate the gradient coefficients back to the nodes (z, y, x)
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int a = b % ncomp, k = b / ncomp;   // k: 0 Z0 = D_z^T H_z, 1 Z1 = S_z^T H_y, 2 Z2 = S_z^T H_x
+      const int a = b % NOUT, k = b / NOUT;   // k: 0 Z0 = D_z^T H_z, 1 Z1 = S_z^T H_y, 2 Z2 = S_z^T H_x
       return {G + (a * 3 + 2 - k) * P, k == 0 ? D_[2] : S_[2], nullptr, nullptr, Bv + b * SZ};
-    }, 3 * ncomp, q0, q1, q2, 2, n, q2, true, false);
+    }, 3 * NOUT, q0, q1, q2, 2, n, q2, true, false);
     pass_batch<T>([&](int b) -> Pass<T> {
-      const int a = b % ncomp, k = b / ncomp;   // k: 0 Y0 = S_y^T Z0 + D_y^T Z1, 1 Y1 = S_y^T Z2
-      if (k == 0) return {Bv + a * SZ, S_[1], Bv + (ncomp + a) * SZ, D_[1], A + b * SX};
-      return {Bv + (2 * ncomp + a) * SZ, S_[1], nullptr, nullptr, A + b * SX};
-    }, 2 * ncomp, q0, q1, n, 1, n, q1, true, false);
+      const int a = b % NOUT, k = b / NOUT;   // k: 0 Y0 = S_y^T Z0 + D_y^T Z1, 1 Y1 = S_y^T Z2
+      if (k == 0) return {Bv + a * SZ, S_[1], Bv + (NOUT + a) * SZ, D_[1], A + b * SX};
+      return {Bv + (2 * NOUT + a) * SZ, S_[1], nullptr, nullptr, A + b * SX};
+    }, 2 * NOUT, q0, q1, n, 1, n, q1, true, false);
     pass_batch<T>([&](int a) -> Pass<T> {
-      return {A + a * SX, S_[0], A + (ncomp + a) * SX, D_[0], r + a * n3};
-    }, ncomp, q0, n, n, 0, n, q0, true, true);
+      return {A + a * SX, S_[0], A + (NOUT + a) * SX, D_[0], r + a * n3};
+    }, NOUT, q0, n, n, 0, n, q0, true, true);
   }
 
   // ================= faces, one direction (two faces) at a time =================
-  // trace slots per direction: (face s, side, component); the divergence needs one component
-  constexpr int NCA = OP == OP_DIV ? 1 : 3;
+  // trace slots per direction: (face s, side, component); on boxes the divergence needs the normal
+  // component only
+  constexpr int NCA = OP == OP_LAP ? 1 : ((OP == OP_DIV && !CURVED) ? 1 : 3);
   constexpr int NS = 4 * NCA;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -408,7 +462,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     bool enr_o[2];
     for (int s = 0; s < 2; ++s) {
       nbr[s] = neighbour(m, c, 2 * d + s);
-      enb[s] = nbr[s] >= 0 ? m.enr[nbr[s]] : -1;
+      enb[s] = (OP != OP_LAP && nbr[s] >= 0) ? m.enr[nbr[s]] : -1;
       enr_o[s] = nbr[s] >= 0 ? enb[s] >= 0 : enr_c;   // the mirror side carries c's class
     }
     // point sets of the faces normal to d: the same for both faces (x/z neighbours share the row,
@@ -417,9 +471,9 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     const int s1 = (t1 == 1 && enr_any) ? QSET_WALL : qset;
     const int s2 = (t2 == 1 && enr_any) ? QSET_WALL : qset;
     const int p1 = B.q[s1], p2 = B.q[s2], FP = p1 * p2;
-    for (int t = threadIdx.x; t < 2 * 3 * n3; t += blockDim.x) {
-      const int s = t / (3 * n3), e = t - s * 3 * n3;
-      un[t] = nbr[s] >= 0 ? u[(size_t)nbr[s] * 3 * n3 + e] : T(0);
+    for (int t = threadIdx.x; t < 2 * NIN * n3; t += blockDim.x) {
+      const int s = t / (NIN * n3), e = t - s * NIN * n3;
+      un[t] = nbr[s] >= 0 ? u[(size_t)nbr[s] * NIN * n3 + e] : T(0);
     }
     for (int t = threadIdx.x; t < 48; t += blockDim.x) {
       const int s = t / 24;
@@ -431,8 +485,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     // T1: face-layer values and reference normal derivatives
     for (int t = threadIdx.x; t < NS * nn; t += blockDim.x) {
       const int k = t / nn, node = t - k * nn;
-      const int a = NCA == 1 ? d : k % NCA, side = (k / NCA) % 2, s = k / (2 * NCA);
-      const T *src = side ? un + (s * 3 + a) * n3 : uo + a * n3;
+      const int a = NCA == 1 ? (OP == OP_DIV ? d : 0) : k % NCA, side = (k / NCA) % 2, s = k / (2 * NCA);
+      const T *src = side ? un + (s * NIN + a) * n3 : uo + a * n3;
       const int ep = side ? 1 - s : s;
       const int i1 = node % n, i2 = node / n;
       V2[t] = src[node_index(d, t1, t2, ep ? n - 1 : 0, i1, i2, n)];
@@ -463,9 +517,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       const int f = 2 * d + s, side = s;
       const int nb = nbr[s], eb = enb[s];
       const int a1 = pt % p1, a2 = pt / p1;
-      const T dA = h[t1] * h[t2] * B.w[s1][a1] * B.w[s2][a2];
       const T sgn = side ? T(1) : T(-1);
-      const T hdo = nb >= 0 ? cell_h(m, nb, d) : h[d];
       const bool both = enr_c && enr_o[s], iface = enr_c != enr_o[s];
       const T tau = nb >= 0 ? max(m.tau[c], m.tau[nb]) : T(10) * m.tau[c];
       const T *wts = enr_c ? m.wt_face[opc] + (((size_t)ec * 6 + f) * m.fpmax[opc]) * WT : nullptr;
@@ -478,133 +530,301 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         fs[e][0] = T(1) - xe; fs[e][1] = xe;
         fo[e][0] = T(1) - xoe; fo[e][1] = xoe;
       }
-      T ub_s[3] = {0, 0, 0}, ub_o[3] = {0, 0, 0}, ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
-      T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
-      const T hob1 = nb >= 0 ? cell_h(m, nb, 1) : h[1];
-      const T hob[3] = {m.hx, hob1, m.hz};
+      T *Cs = C + s * 3 * 4 * L.FP, *Es = E + s * 3 * 4 * L.FP;
+      if constexpr (!CURVED) {
+        const T dA = h[t1] * h[t2] * B.w[s1][a1] * B.w[s2][a2];
+        const T hdo = nb >= 0 ? cell_h(m, nb, d) : h[d];
+        T ub_s[3] = {0, 0, 0}, ub_o[3] = {0, 0, 0}, ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
+        T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
+        const T hob1 = nb >= 0 ? cell_h(m, nb, 1) : h[1];
+        const T hob[3] = {m.hx, hob1, m.hz};
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (OP == OP_DIV && a != d) continue;   // the divergence needs the normal component only
-        const int ka = NCA == 1 ? 0 : a;
-        const T *tr_s = Tr + (((s * 2 + 0) * NCA + ka) * 4) * L.FP;
-        const T *tr_o = Tr + (((s * 2 + 1) * NCA + ka) * 4) * L.FP;
-        ub_s[a] = tr_s[pt];
-        if (GRAD) {
-          gbs[a][d] = tr_s[L.FP + pt] * hinv[d];
-          gbs[a][t1] = tr_s[2 * L.FP + pt] * hinv[t1];
-          gbs[a][t2] = tr_s[3 * L.FP + pt] * hinv[t2];
-        }
-        // enrichment u~_a = psi sum_v N_v e_av and its physical gradient
-        if (enr_c) {
-          const T *w = wts + pt * WT;
-          T sN = T(0), sD[3] = {0, 0, 0};
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            T Nv, dN[3];
-            q1_vertex(fs, v, Nv, dN);
-            sN += Nv * eo[a * 8 + v];
-            if (GRAD)
-#pragma unroll
-              for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eo[a * 8 + v];
-          }
-          ut_s[a] = w[0] * sN;
-          if (GRAD)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) gts[a][e] = w[0] * sD[e] * hinv[e] + sN * w[1 + e];
-        } else if (GRAD) {
-          gts[a][0] = gts[a][1] = gts[a][2] = T(0);
-        }
-        if (nb >= 0) {
-          ub_o[a] = tr_o[pt];
+        for (int a = 0; a < 3; ++a) {
+          if (OP == OP_DIV && a != d) continue;   // the divergence needs the normal component only
+          const int ka = NCA == 1 ? 0 : a;
+          const T *tr_s = Tr + (((s * 2 + 0) * NCA + ka) * 4) * L.FP;
+          const T *tr_o = Tr + (((s * 2 + 1) * NCA + ka) * 4) * L.FP;
+          ub_s[a] = tr_s[pt];
           if (GRAD) {
-            const T ht1 = t1 == 1 ? hob1 : h[t1], ht2 = t2 == 1 ? hob1 : h[t2];
-            gbo[a][d] = tr_o[L.FP + pt] / hdo;
-            gbo[a][t1] = tr_o[2 * L.FP + pt] / ht1;
-            gbo[a][t2] = tr_o[3 * L.FP + pt] / ht2;
+            gbs[a][d] = tr_s[L.FP + pt] * hinv[d];
+            gbs[a][t1] = tr_s[2 * L.FP + pt] * hinv[t1];
+            gbs[a][t2] = tr_s[3 * L.FP + pt] * hinv[t2];
           }
-          if (wto) {
-            const T *w = wto + pt * WT;
-            const T *eb_a = en + s * 24 + a * 8;
+          // enrichment u~_a = psi sum_v N_v e_av and its physical gradient
+          if (enr_c) {
+            const T *w = wts + pt * WT;
             T sN = T(0), sD[3] = {0, 0, 0};
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
               T Nv, dN[3];
-              q1_vertex(fo, v, Nv, dN);
-              sN += Nv * eb_a[v];
+              q1_vertex(fs, v, Nv, dN);
+              sN += Nv * eo[a * 8 + v];
               if (GRAD)
 #pragma unroll
-                for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eb_a[v];
+                for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eo[a * 8 + v];
             }
-            ut_o[a] = w[0] * sN;
+            ut_s[a] = w[0] * sN;
             if (GRAD)
 #pragma unroll
-              for (int e = 0; e < 3; ++e) gto[a][e] = w[0] * sD[e] / hob[e] + sN * w[1 + e];
+              for (int e = 0; e < 3; ++e) gts[a][e] = w[0] * sD[e] * hinv[e] + sN * w[1 + e];
           } else if (GRAD) {
-            gto[a][0] = gto[a][1] = gto[a][2] = T(0);
+            gts[a][0] = gts[a][1] = gts[a][2] = T(0);
           }
-        } else {
-          // mirror principle on no-slip walls: u+ = -u-, grad u+ = grad u-
-          ub_o[a] = -ub_s[a];
-          ut_o[a] = -ut_s[a];
-          if (GRAD)
+          if (nb >= 0) {
+            ub_o[a] = tr_o[pt];
+            if (GRAD) {
+              const T ht1 = t1 == 1 ? hob1 : h[t1], ht2 = t2 == 1 ? hob1 : h[t2];
+              gbo[a][d] = tr_o[L.FP + pt] / hdo;
+              gbo[a][t1] = tr_o[2 * L.FP + pt] / ht1;
+              gbo[a][t2] = tr_o[3 * L.FP + pt] / ht2;
+            }
+            if (wto) {
+              const T *w = wto + pt * WT;
+              const T *eb_a = en + s * 24 + a * 8;
+              T sN = T(0), sD[3] = {0, 0, 0};
 #pragma unroll
-            for (int e = 0; e < 3; ++e) { gbo[a][e] = gbs[a][e]; gto[a][e] = gts[a][e]; }
+              for (int v = 0; v < 8; ++v) {
+                T Nv, dN[3];
+                q1_vertex(fo, v, Nv, dN);
+                sN += Nv * eb_a[v];
+                if (GRAD)
+#pragma unroll
+                  for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eb_a[v];
+              }
+              ut_o[a] = w[0] * sN;
+              if (GRAD)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) gto[a][e] = w[0] * sD[e] / hob[e] + sN * w[1 + e];
+            } else if (GRAD) {
+              gto[a][0] = gto[a][1] = gto[a][2] = T(0);
+            }
+          } else {
+            // mirror principle on no-slip walls: u+ = -u-, grad u+ = grad u-
+            ub_o[a] = -ub_s[a];
+            ut_o[a] = -ut_s[a];
+            if (GRAD)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) { gbo[a][e] = gbs[a][e]; gto[a][e] = gts[a][e]; }
+          }
         }
-      }
-      T *Cs = C + s * 3 * 4 * L.FP, *Es = E + s * 3 * 4 * L.FP;
-      if (OP == OP_DIV) {
-        const T us = ub_s[d] + ut_s[d], uo_ = ub_o[d] + ut_o[d];
-        const T avg = nb >= 0 ? T(0.5) * (us + uo_) : us;
-        Cs[pt] = -dA * sgn * avg;
-      } else if (OP == OP_CONV) {
-        T um[3], up[3];
-        for (int a = 0; a < 3; ++a) { um[a] = ub_s[a] + ut_s[a]; up[a] = ub_o[a] + ut_o[a]; }
-        const T unm = sgn * um[d], unp = sgn * up[d];
-        const T lam = max(T(2) * fabs(unm), T(2) * fabs(unp));
-        for (int a = 0; a < 3; ++a) {
-          const T Fa = T(0.5) * (um[a] * unm + up[a] * unp) + T(0.5) * lam * (um[a] - up[a]);
-          Cs[(a * 4) * L.FP + pt] = dA * Fa;
-          Es[(a * 4) * L.FP + pt] = dA * Fa;
+        if (OP == OP_DIV) {
+          const T us = ub_s[d] + ut_s[d], uo_ = ub_o[d] + ut_o[d];
+          const T avg = nb >= 0 ? T(0.5) * (us + uo_) : us;
+          Cs[pt] = -dA * sgn * avg;
+        } else if (OP == OP_CONV) {
+          T um[3], up[3];
+          for (int a = 0; a < 3; ++a) { um[a] = ub_s[a] + ut_s[a]; up[a] = ub_o[a] + ut_o[a]; }
+          const T unm = sgn * um[d], unp = sgn * up[d];
+          const T lam = max(T(2) * fabs(unm), T(2) * fabs(unp));
+          for (int a = 0; a < 3; ++a) {
+            const T Fa = T(0.5) * (um[a] * unm + up[a] * unp) + T(0.5) * lam * (um[a] - up[a]);
+            Cs[(a * 4) * L.FP + pt] = dA * Fa;
+            Es[(a * 4) * L.FP + pt] = dA * Fa;
+          }
+        } else if (OP == OP_VISC) {
+          const T *nuts = enr_c ? m.nut_face + ((size_t)ec * 6 + f) * m.fpmax[0] : nullptr;
+          const T *nuto = (nb >= 0 && eb >= 0) ? m.nut_face + ((size_t)eb * 6 + (f ^ 1)) * m.fpmax[0] : nullptr;
+          const T nut_s = nuts ? nuts[pt] : T(0);
+          const T nut_o = nb >= 0 ? (nuto ? nuto[pt] : T(0)) : nut_s;
+          T jb[3], jt[3], jtot[3], avgb_n[3], avgt_n[3] = {0, 0, 0};
+          for (int a = 0; a < 3; ++a) {
+            jb[a] = ub_s[a] - ub_o[a];
+            jt[a] = ut_s[a] - ut_o[a];
+            jtot[a] = jb[a] + jt[a];
+            avgb_n[a] = T(0.5) * nu * sgn * ((gbs[a][d] + gbs[d][a]) + (gbo[a][d] + gbo[d][a]));
+          }
+          T wt_s = T(0.5);
+          if (both) {
+            const T den = T(2) * nu + nut_s + nut_o;
+            wt_s = (nu + nut_o) / den;
+            const T wt_o = (nu + nut_s) / den;
+            for (int a = 0; a < 3; ++a)
+              avgt_n[a] = sgn * (wt_s * (nu + nut_s) * (gts[a][d] + gts[d][a]) + wt_o * (nu + nut_o) * (gto[a][d] + gto[d][a]));
+          }
+          T jadj[3];
+          for (int a = 0; a < 3; ++a) jadj[a] = jb[a] + (iface ? jt[a] : T(0));
+          for (int a = 0; a < 3; ++a) {
+            T cv = -avgb_n[a] + tau * nu * jtot[a];
+            if (both) cv -= avgt_n[a];
+            // coefficient of phi: dA cv; of dphi/dxi_b: dA nu/2 sgn (jadj_a delta_bd + delta_ad jadj_b) / h_b
+            Cs[(a * 4 + 0) * L.FP + pt] = dA * cv;
+            Cs[(a * 4 + 1) * L.FP + pt] = dA * T(0.5) * nu * sgn * (jadj[a] + (a == d ? jadj[d] : T(0))) * hinv[d];
+            Cs[(a * 4 + 2) * L.FP + pt] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t1] : T(0)) * hinv[t1];
+            Cs[(a * 4 + 3) * L.FP + pt] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t2] : T(0)) * hinv[t2];
+            if (enr_c) {
+              T cve = tau * nu * jtot[a];
+              if (both) cve -= avgt_n[a];
+              if (iface) cve -= avgb_n[a];
+              Es[(a * 4 + 0) * L.FP + pt] = dA * cve;
+              for (int b = 0; b < 3; ++b) {
+                // (w F^{nu+nut}(v~), [[u~]] + [[ubar]]) on d Omega~_e: physical-gradient coefficient
+                const T coef = both ? wt_s * (nu + nut_s) * sgn * ((b == d ? jtot[a] : T(0)) + (a == d ? jtot[b] : T(0))) : T(0);
+                Es[(a * 4 + 1 + b) * L.FP + pt] = dA * coef;
+              }
+            }
+          }
         }
-      } else {  // VISC
-        const T *nuts = enr_c ? m.nut_face + ((size_t)ec * 6 + f) * m.fpmax[0] : nullptr;
-        const T *nuto = (nb >= 0 && eb >= 0) ? m.nut_face + ((size_t)eb * 6 + (f ^ 1)) * m.fpmax[0] : nullptr;
-        const T nut_s = nuts ? nuts[pt] : T(0);
-        const T nut_o = nb >= 0 ? (nuto ? nuto[pt] : T(0)) : nut_s;
-        T jb[3], jt[3], jtot[3], avgb_n[3], avgt_n[3] = {0, 0, 0};
-        for (int a = 0; a < 3; ++a) {
-          jb[a] = ub_s[a] - ub_o[a];
-          jt[a] = ut_s[a] - ut_o[a];
-          jtot[a] = jb[a] + jt[a];
-          avgb_n[a] = T(0.5) * nu * sgn * ((gbs[a][d] + gbs[d][a]) + (gbo[a][d] + gbo[d][a]));
+      } else {
+        // ---- curved cells: metric of both sides at the shared point, outward normal, area weight
+        T Js[3][3], Jo[3][3], dets, deto;
+        load_rec(face_rec(m, B, col, d, s, s1, s2, a1, a2), Js, dets);
+        if (nb >= 0) load_rec(face_rec(m, B, metric_col(m, nb), d, 1 - s, s1, s2, a1, a2), Jo, deto);
+        const T nrm = sqrt(Js[d][0] * Js[d][0] + Js[d][1] * Js[d][1] + Js[d][2] * Js[d][2]);
+        const T nv[3] = {sgn * Js[d][0] / nrm, sgn * Js[d][1] / nrm, sgn * Js[d][2] / nrm};
+        const T dA = fabs(dets) * nrm * B.w[s1][a1] * B.w[s2][a2];
+        T vJ[3];   // J^-1 n: the normal derivative is grad_xi . (J^-1 n)
+        phys_to_ref(Js, nv, vJ);
+        T ub_s[3] = {0, 0, 0}, ub_o[3] = {0, 0, 0}, ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
+        T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
+#pragma unroll
+        for (int a = 0; a < NIN; ++a) {
+          const int ka = NCA == 1 ? 0 : a;
+          const T *tr_s = Tr + (((s * 2 + 0) * NCA + ka) * 4) * L.FP;
+          const T *tr_o = Tr + (((s * 2 + 1) * NCA + ka) * 4) * L.FP;
+          ub_s[a] = tr_s[pt];
+          if (GRAD) {
+            T gr[3];
+            gr[d] = tr_s[L.FP + pt]; gr[t1] = tr_s[2 * L.FP + pt]; gr[t2] = tr_s[3 * L.FP + pt];
+            ref_to_phys(Js, gr, gbs[a]);
+          }
+          if (OP != OP_LAP && enr_c) {
+            const T *w = wts + pt * WT;
+            T sN = T(0), sD[3] = {0, 0, 0};
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              T Nv, dN[3];
+              q1_vertex(fs, v, Nv, dN);
+              sN += Nv * eo[a * 8 + v];
+              if (GRAD)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eo[a * 8 + v];
+            }
+            ut_s[a] = w[0] * sN;
+            if (GRAD) {
+              T gp[3];
+              ref_to_phys(Js, sD, gp);
+#pragma unroll
+              for (int e = 0; e < 3; ++e) gts[a][e] = w[0] * gp[e] + sN * w[1 + e];
+            }
+          } else if (GRAD) {
+            gts[a][0] = gts[a][1] = gts[a][2] = T(0);
+          }
+          if (nb >= 0) {
+            ub_o[a] = tr_o[pt];
+            if (GRAD) {
+              T gr[3];
+              gr[d] = tr_o[L.FP + pt]; gr[t1] = tr_o[2 * L.FP + pt]; gr[t2] = tr_o[3 * L.FP + pt];
+              ref_to_phys(Jo, gr, gbo[a]);
+            }
+            if (OP != OP_LAP && wto) {
+              const T *w = wto + pt * WT;
+              const T *eb_a = en + s * 24 + a * 8;
+              T sN = T(0), sD[3] = {0, 0, 0};
+#pragma unroll
+              for (int v = 0; v < 8; ++v) {
+                T Nv, dN[3];
+                q1_vertex(fo, v, Nv, dN);
+                sN += Nv * eb_a[v];
+                if (GRAD)
+#pragma unroll
+                  for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eb_a[v];
+              }
+              ut_o[a] = w[0] * sN;
+              if (GRAD) {
+                T gp[3];
+                ref_to_phys(Jo, sD, gp);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) gto[a][e] = w[0] * gp[e] + sN * w[1 + e];
+              }
+            } else if (GRAD) {
+              gto[a][0] = gto[a][1] = gto[a][2] = T(0);
+            }
+          } else {
+            // mirror principle on no-slip walls: u+ = -u-, grad u+ = grad u-
+            ub_o[a] = -ub_s[a];
+            ut_o[a] = -ut_s[a];
+            if (GRAD)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) { gbo[a][e] = gbs[a][e]; gto[a][e] = gts[a][e]; }
+          }
         }
-        T wt_s = T(0.5);
-        if (both) {
-          const T den = T(2) * nu + nut_s + nut_o;
-          wt_s = (nu + nut_o) / den;
-          const T wt_o = (nu + nut_s) / den;
-          for (int a = 0; a < 3; ++a)
-            avgt_n[a] = sgn * (wt_s * (nu + nut_s) * (gts[a][d] + gts[d][a]) + wt_o * (nu + nut_o) * (gto[a][d] + gto[d][a]));
-        }
-        T jadj[3];
-        for (int a = 0; a < 3; ++a) jadj[a] = jb[a] + (iface ? jt[a] : T(0));
-        for (int a = 0; a < 3; ++a) {
-          T cv = -avgb_n[a] + tau * nu * jtot[a];
-          if (both) cv -= avgt_n[a];
-          // coefficient of phi: dA cv; of dphi/dxi_b: dA nu/2 sgn (jadj_a delta_bd + delta_ad jadj_b) / h_b
-          Cs[(a * 4 + 0) * L.FP + pt] = dA * cv;
-          Cs[(a * 4 + 1) * L.FP + pt] = dA * T(0.5) * nu * sgn * (jadj[a] + (a == d ? jadj[d] : T(0))) * hinv[d];
-          Cs[(a * 4 + 2) * L.FP + pt] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t1] : T(0)) * hinv[t1];
-          Cs[(a * 4 + 3) * L.FP + pt] = dA * T(0.5) * nu * sgn * (a == d ? jadj[t2] : T(0)) * hinv[t2];
-          if (enr_c) {
-            T cve = tau * nu * jtot[a];
-            if (both) cve -= avgt_n[a];
-            if (iface) cve -= avgb_n[a];
-            Es[(a * 4 + 0) * L.FP + pt] = dA * cve;
-            for (int b = 0; b < 3; ++b) {
-              // (w F^{nu+nut}(v~), [[u~]] + [[ubar]]) on d Omega~_e: physical-gradient coefficient
-              const T coef = both ? wt_s * (nu + nut_s) * sgn * ((b == d ? jtot[a] : T(0)) + (a == d ? jtot[b] : T(0))) : T(0);
-              Es[(a * 4 + 1 + b) * L.FP + pt] = dA * coef;
+        const int ax[3] = {d, t1, t2};   // reference axis of trace slots 1..3
+        if (OP == OP_LAP) {
+          // SIPG (eq. ipflux); homogeneous Neumann walls carry no face terms
+          T c0 = T(0), cj = T(0);
+          if (nb >= 0) {
+            const T gn = (gbs[0][0] + gbo[0][0]) * nv[0] + (gbs[0][1] + gbo[0][1]) * nv[1] + (gbs[0][2] + gbo[0][2]) * nv[2];
+            const T jump = ub_s[0] - ub_o[0];
+            c0 = dA * (T(-0.5) * gn + tau * jump);
+            cj = dA * T(-0.5) * jump;
+          }
+          Cs[pt] = c0;
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) Cs[(1 + jj) * L.FP + pt] = cj * vJ[ax[jj]];
+        } else if (OP == OP_DIV) {
+          T us = T(0), uo_ = T(0);
+#pragma unroll
+          for (int e = 0; e < 3; ++e) { us += (ub_s[e] + ut_s[e]) * nv[e]; uo_ += (ub_o[e] + ut_o[e]) * nv[e]; }
+          const T avg = nb >= 0 ? T(0.5) * (us + uo_) : us;
+          Cs[pt] = -dA * avg;
+        } else if (OP == OP_CONV) {
+          T um[3], up[3];
+          for (int a = 0; a < 3; ++a) { um[a] = ub_s[a] + ut_s[a]; up[a] = ub_o[a] + ut_o[a]; }
+          const T unm = um[0] * nv[0] + um[1] * nv[1] + um[2] * nv[2];
+          const T unp = up[0] * nv[0] + up[1] * nv[1] + up[2] * nv[2];
+          const T lam = max(T(2) * fabs(unm), T(2) * fabs(unp));
+          for (int a = 0; a < 3; ++a) {
+            const T Fa = T(0.5) * (um[a] * unm + up[a] * unp) + T(0.5) * lam * (um[a] - up[a]);
+            Cs[(a * 4) * L.FP + pt] = dA * Fa;
+            Es[(a * 4) * L.FP + pt] = dA * Fa;
+          }
+        } else {  // VISC
+          const T *nuts = enr_c ? m.nut_face + ((size_t)ec * 6 + f) * m.fpmax[0] : nullptr;
+          const T *nuto = (nb >= 0 && eb >= 0) ? m.nut_face + ((size_t)eb * 6 + (f ^ 1)) * m.fpmax[0] : nullptr;
+          const T nut_s = nuts ? nuts[pt] : T(0);
+          const T nut_o = nb >= 0 ? (nuto ? nuto[pt] : T(0)) : nut_s;
+          T jb[3], jt[3], jtot[3], avgb_n[3], avgt_n[3] = {0, 0, 0};
+          for (int a = 0; a < 3; ++a) {
+            jb[a] = ub_s[a] - ub_o[a];
+            jt[a] = ut_s[a] - ut_o[a];
+            jtot[a] = jb[a] + jt[a];
+            T sn = T(0);
+            for (int e = 0; e < 3; ++e) sn += ((gbs[a][e] + gbs[e][a]) + (gbo[a][e] + gbo[e][a])) * nv[e];
+            avgb_n[a] = T(0.5) * nu * sn;
+          }
+          T wt_s = T(0.5);
+          if (both) {
+            const T den = T(2) * nu + nut_s + nut_o;
+            wt_s = (nu + nut_o) / den;
+            const T wt_o = (nu + nut_s) / den;
+            for (int a = 0; a < 3; ++a) {
+              T sn = T(0);
+              for (int e = 0; e < 3; ++e)
+                sn += (wt_s * (nu + nut_s) * (gts[a][e] + gts[e][a]) + wt_o * (nu + nut_o) * (gto[a][e] + gto[e][a])) * nv[e];
+              avgt_n[a] = sn;
+            }
+          }
+          T jadj[3];
+          for (int a = 0; a < 3; ++a) jadj[a] = jb[a] + (iface ? jt[a] : T(0));
+          for (int a = 0; a < 3; ++a) {
+            T cv = -avgb_n[a] + tau * nu * jtot[a];
+            if (both) cv -= avgt_n[a];
+            Cs[(a * 4 + 0) * L.FP + pt] = dA * cv;
+            // physical coefficient of grad v_a: nu/2 (jadj_a n + n_a jadj), mapped to reference derivatives
+            T pv[3], cf[3];
+            for (int e = 0; e < 3; ++e) pv[e] = T(0.5) * nu * (jadj[a] * nv[e] + nv[a] * jadj[e]);
+            phys_to_ref(Js, pv, cf);
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) Cs[(a * 4 + 1 + jj) * L.FP + pt] = dA * cf[ax[jj]];
+            if (enr_c) {
+              T cve = tau * nu * jtot[a];
+              if (both) cve -= avgt_n[a];
+              if (iface) cve -= avgb_n[a];
+              Es[(a * 4 + 0) * L.FP + pt] = dA * cve;
+              for (int b = 0; b < 3; ++b) {
+                const T coef = both ? wt_s * (nu + nut_s) * (jtot[a] * nv[b] + nv[a] * jtot[b]) : T(0);
+                Es[(a * 4 + 1 + b) * L.FP + pt] = dA * coef;
+              }
             }
           }
         }
@@ -612,7 +832,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
     __syncthreads();
     // enriched tests on these two faces
-    if (enr_c && OP != OP_DIV) {
+    if (enr_c && (OP == OP_CONV || OP == OP_VISC)) {
       auto contrib = [&](int t, T *acc) {
         const int s = t / FP, pt = t - s * FP;
         const int a1 = pt % p1, a2 = pt / p1;
@@ -622,6 +842,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         const T f[3][2] = {{T(1) - xs[0], xs[0]}, {T(1) - xs[1], xs[1]}, {T(1) - xs[2], xs[2]}};
         const T *w = m.wt_face[opc] + (((size_t)ec * 6 + 2 * d + s) * m.fpmax[opc]) * WT + pt * WT;
         const T *Es = E + s * 3 * 4 * L.FP;
+        T Js[3][3], dets;
+        if (CURVED && OP == OP_VISC) load_rec(face_rec(m, B, col, d, s, s1, s2, a1, a2), Js, dets);
         T cv[3], cg[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -635,8 +857,15 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           q1_vertex(f, v, Nv, dN);
           if (OP == OP_VISC) {
             T g[3];
+            if (CURVED) {
+              T gp[3];
+              ref_to_phys(Js, dN, gp);
 #pragma unroll
-            for (int b = 0; b < 3; ++b) g[b] = w[0] * dN[b] * hinv[b] + Nv * w[1 + b];
+              for (int b = 0; b < 3; ++b) g[b] = w[0] * gp[b] + Nv * w[1 + b];
+            } else {
+#pragma unroll
+              for (int b = 0; b < 3; ++b) g[b] = w[0] * dN[b] * hinv[b] + Nv * w[1 + b];
+            }
 #pragma unroll
             for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cv[a] * Nv + cg[a][0] * g[0] + cg[a][1] * g[1] + cg[a][2] * g[2];
           } else {
@@ -649,10 +878,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
     // I1: along t2 (p2 -> n); I2: along t1 (p1 -> n); item k = (face s, component a)
     T *I0 = S0 + L.fI0, *I1 = S0 + L.fI1, *I2 = S0 + L.fI2, *F2 = S0 + L.fF2, *G2 = S0 + L.fG2;
-    const int ni = 2 * ncomp;
+    const int ni = 2 * NOUT;
     pass_batch<T>([&](int b) -> Pass<T> {
       const int k = b % ni, j = b / ni;   // j: 0 I0 = S2^T f + D2^T ht2, 1 I1 = S2^T ht1, 2 I2 = S2^T hd
-      const int s = k / ncomp, a = k % ncomp;
+      const int s = k / NOUT, a = k % NOUT;
       const T *Ck = C + (s * 3 + a) * 4 * L.FP;
       if (j == 0) return {Ck, B.S[s2], GRAD ? Ck + 3 * L.FP : nullptr, B.D[s2], I0 + k * L.pn};
       if (j == 1) return {Ck + 2 * L.FP, B.S[s2], nullptr, nullptr, I1 + k * L.pn};
@@ -664,13 +893,13 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       return {I2 + k * L.pn, B.S[s1], nullptr, nullptr, G2 + k * nn};
     }, GRAD ? 2 * ni : ni, p1, n, 1, 0, n, p1, true, false);
     // scatter the face-layer values and the normal-derivative coefficients into the cell nodes
-    for (int t = threadIdx.x; t < ncomp * n3; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NOUT * n3; t += blockDim.x) {
       const int a = t / n3, node = t - a * n3;
       const int id[3] = {node % n, (node / n) % n, node / nn};
       const int fi = id[t1] + n * id[t2];
       T add = T(0);
       for (int s = 0; s < 2; ++s) {
-        const int k = s * ncomp + a;
+        const int k = s * NOUT + a;
         if (id[d] == (s ? n - 1 : 0)) add += F2[k * nn + fi];
         if (GRAD) add += B.dend[s][id[d]] * G2[k * nn + fi];
       }
@@ -679,7 +908,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     __syncthreads();
   }
   // ================= store =================
-  if (OP == OP_DIV) {
+  if (NOUT == 1) {
     T *yc = y + (size_t)c * n3;
     for (int t = threadIdx.x; t < n3; t += blockDim.x) yc[t] = r[t];
   } else {
@@ -690,32 +919,42 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int GEO>
 static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s) {
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
-  const VecPlan L = vec_plan(OP, m.n1, m.q[qset], m.q[QSET_WALL]);
+  const VecPlan L = vec_plan(OP, GEO == GEO_CURVED, m.n1, m.q[qset], m.q[QSET_WALL]);
   const size_t sm = ((sizeof(Basis<T>) + 15) / 16) * 16 + (size_t)L.total * sizeof(T);
   if (sm > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(vector_op_kernel<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(vector_op_kernel<T, OP, GEO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         220 * 1024);
     if (e == cudaSuccess)   // the whole unified L1/shared array as shared memory: more CTAs per SM
-      e = cudaFuncSetAttribute(vector_op_kernel<T, OP>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      e = cudaFuncSetAttribute(vector_op_kernel<T, OP, GEO>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   note_launch();
-  note_dofs(OP == OP_DIV ? m.np : m.nu);
-  vector_op_kernel<T, OP><<<m.nc, 128, sm, s>>>(m, u, y);
+  note_dofs((OP == OP_DIV || OP == OP_LAP) ? m.np : m.nu);
+  vector_op_kernel<T, OP, GEO><<<m.nc, 128, sm, s>>>(m, u, y);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s) {
+  if (m.geo == GEO_CURVED) {
+    switch (op) {
+      case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s);
+      case OP_CONV: return launch_vec<T, OP_CONV, GEO_CURVED>(m, u, y, s);
+      case OP_VISC: return launch_vec<T, OP_VISC, GEO_CURVED>(m, u, y, s);
+      case OP_LAP: return launch_vec<T, OP_LAP, GEO_CURVED>(m, u, y, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (op) {
-    case OP_DIV: return launch_vec<T, OP_DIV>(m, u, y, s);
-    case OP_CONV: return launch_vec<T, OP_CONV>(m, u, y, s);
-    case OP_VISC: return launch_vec<T, OP_VISC>(m, u, y, s);
+    case OP_DIV: return launch_vec<T, OP_DIV, GEO_BOX>(m, u, y, s);
+    case OP_CONV: return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s);
+    case OP_VISC: return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s);
   }
   return cudaErrorInvalidValue;
 }

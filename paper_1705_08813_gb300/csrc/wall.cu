@@ -10,6 +10,7 @@
 //
 // Sec. 2.2: nu_t = l_mix^2 |eps(u~)| (eq. mix), l_mix = kappa y_DES (1 - exp(-y+/A+)) (eq. lmix),
 // y_DES = (y^-beta + (C_DES h)^-beta)^(-1/beta) (eq. ydes) with h = dy_e/(k+1).
+#include "metric.cuh"
 #include "sumfac.cuh"
 
 namespace dgw {
@@ -71,25 +72,43 @@ struct WallCellData {
   const double *ywall;   // [ne][8]
   const double *tauv;    // [ne][8]
   const int *enr_cell;   // [ne]
-  const double *hy;      // [ny]
-  double hx, hz, nu;
-  int nx, ny, wall_law;
+  MeshView<double> mv;   // geometry (boxes: row spacing; curved: metric tables)
+  double nu;
+  int wall_law;
 };
 
-// Evaluate psi, grad psi, y_h and y+ at reference point xi of enriched cell e.
-__device__ void wall_point(const WallCellData &w, int e, const double xi[3], double out[WT], double aux[2]) {
-  const int c = w.enr_cell[e];
-  const double h[3] = {w.hx, w.hy[(c / w.nx) % w.ny], w.hz};
+// J^-1 at a point of cell c: boxes are diagonal; curved cells read the metric record (volume point
+// (a0 of set sx, a1 of set sy), or face point (a1, a2) of face f with sets s1, s2 when f >= 0).
+__device__ void point_metric(const WallCellData &w, const Basis<double> &B, int c, int f, int sx, int sy, int a0,
+                             int a1, double Ji[3][3]) {
+  const MeshView<double> &m = w.mv;
+  if (m.geo == GEO_CURVED) {
+    const int col = metric_col(m, c);
+    const double *rec = f < 0 ? vol_rec(m, B, col, sx, sy, a0, a1) : face_rec(m, B, col, f >> 1, f & 1, sx, sy, a0, a1);
+    double det;
+    load_rec(rec, Ji, det);
+    return;
+  }
+  const double h[3] = {m.hx, m.hy[(c / m.nx) % m.ny], m.hz};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Ji[a][b] = a == b ? 1.0 / h[a] : 0.0;
+}
+
+// Evaluate psi, grad psi, y_h and y+ at reference point xi of enriched cell e (J^-1 at the point).
+__device__ void wall_point(const WallCellData &w, int e, const double xi[3], const double Ji[3][3], double out[WT],
+                           double aux[2]) {
   double N[8], dN[8][3];
   q1_weights(xi, N, dN);
   double yh = 0.0, th = 0.0, gy[3] = {0, 0, 0}, gt[3] = {0, 0, 0};
   for (int v = 0; v < 8; ++v) {
     const double yv = w.ywall[8 * e + v], tv = w.tauv[8 * e + v];
+    double g[3];
+    ref_to_phys(Ji, dN[v], g);
     yh += N[v] * yv;
     th += N[v] * tv;
     for (int d = 0; d < 3; ++d) {
-      gy[d] += dN[v][d] / h[d] * yv;
-      gt[d] += dN[v][d] / h[d] * tv;
+      gy[d] += g[d] * yv;
+      gt[d] += g[d] * tv;
     }
   }
   const double st = sqrt(th);
@@ -102,13 +121,17 @@ __device__ void wall_point(const WallCellData &w, int e, const double xi[3], dou
   aux[1] = yp;
 }
 
-// Reference point of volume point t (x fastest; y uses the wall set) and of face point t.
-__device__ __forceinline__ void vol_xi(const Basis<double> &B, int qs, int t, double xi[3]) {
+// Reference point of volume point t (x fastest; y uses the wall set) and of face point t, with the
+// point's metric.
+__device__ __forceinline__ void vol_xi(const WallCellData &w, const Basis<double> &B, int c, int qs, int t, double xi[3],
+                                       double Ji[3][3]) {
   const int q0 = B.q[qs], q1 = B.q[QSET_WALL];
   const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
   xi[0] = B.x[qs][i0]; xi[1] = B.x[QSET_WALL][i1]; xi[2] = B.x[qs][i2];
+  point_metric(w, B, c, -1, qs, QSET_WALL, i0, i1, Ji);
 }
-__device__ __forceinline__ bool face_xi(const Basis<double> &B, int qs, int f, int t, double xi[3]) {
+__device__ __forceinline__ bool face_xi(const WallCellData &w, const Basis<double> &B, int c, int qs, int f, int t,
+                                        double xi[3], double Ji[3][3]) {
   const int d = f >> 1, side = f & 1;
   int t1, t2;
   face_axes(d, t1, t2);
@@ -116,6 +139,7 @@ __device__ __forceinline__ bool face_xi(const Basis<double> &B, int qs, int f, i
   const int p1 = B.q[s1], p2 = B.q[s2];
   if (t >= p1 * p2) return false;
   xi[d] = side; xi[t1] = B.x[s1][t % p1]; xi[t2] = B.x[s2][t / p1];
+  point_metric(w, B, c, f, s1, s2, t % p1, t / p1, Ji);
   return true;
 }
 
@@ -123,17 +147,18 @@ __global__ void wall_table_kernel(WallCellData w, const Basis<double> *Bg, int q
                                   double *vol, double *face, double *aux_vol, double *aux_face) {
   const Basis<double> &B = *Bg;
   const int e = blockIdx.x;
+  const int c = w.enr_cell[e];
   for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
-    double xi[3], out[WT], aux[2];
-    vol_xi(B, qs, t, xi);
-    wall_point(w, e, xi, out, aux);
+    double xi[3], Ji[3][3], out[WT], aux[2];
+    vol_xi(w, B, c, qs, t, xi, Ji);
+    wall_point(w, e, xi, Ji, out, aux);
     for (int r = 0; r < WT; ++r) vol[((size_t)e * nvol + t) * WT + r] = out[r];
     if (aux_vol) { aux_vol[((size_t)e * nvol + t) * 2] = aux[0]; aux_vol[((size_t)e * nvol + t) * 2 + 1] = aux[1]; }
   }
   for (int t = threadIdx.x; t < 6 * fpmax; t += blockDim.x) {
     const int f = t / fpmax, pt = t % fpmax;
-    double xi[3], out[WT] = {0, 0, 0, 0}, aux[2] = {0, 0};
-    if (face_xi(B, qs, f, pt, xi)) wall_point(w, e, xi, out, aux);
+    double xi[3], Ji[3][3], out[WT] = {0, 0, 0, 0}, aux[2] = {0, 0};
+    if (face_xi(w, B, c, qs, f, pt, xi, Ji)) wall_point(w, e, xi, Ji, out, aux);
     for (int r = 0; r < WT; ++r) face[((size_t)e * 6 * fpmax + t) * WT + r] = out[r];
     if (aux_face) { aux_face[((size_t)e * 6 * fpmax + t) * 2] = aux[0]; aux_face[((size_t)e * 6 * fpmax + t) * 2 + 1] = aux[1]; }
   }
@@ -148,19 +173,20 @@ __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, i
   const Basis<double> &B = *Bg;
   const int e = blockIdx.x;
   const int c = w.enr_cell[e];
-  const double h[3] = {w.hx, w.hy[(c / w.nx) % w.ny], w.hz};
   __shared__ double cu[24];
   for (int t = threadIdx.x; t < 24; t += blockDim.x) cu[t] = u_enr[(size_t)e * 24 + t];
   __syncthreads();
   const double hdes = kCdes * dye[e] / (k + 1);
-  auto nut_at = [&](const double xi[3], const double *wt, const double *aux) -> double {
+  auto nut_at = [&](const double xi[3], const double Ji[3][3], const double *wt, const double *aux) -> double {
     double N[8], dN[8][3];
     q1_weights(xi, N, dN);
+    double gN[8][3];
+    for (int v = 0; v < 8; ++v) ref_to_phys(Ji, dN[v], gN[v]);
     double G[3][3];
     for (int a = 0; a < 3; ++a)
       for (int d = 0; d < 3; ++d) {
         double s = 0.0;
-        for (int v = 0; v < 8; ++v) s += cu[a * 8 + v] * (wt[0] * dN[v][d] / h[d] + N[v] * wt[1 + d]);
+        for (int v = 0; v < 8; ++v) s += cu[a * 8 + v] * (wt[0] * gN[v][d] + N[v] * wt[1 + d]);
         G[a][d] = s;
       }
     double e2 = 0.0;
@@ -176,19 +202,19 @@ __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, i
     return lmix * lmix * sqrt(2.0 * e2);
   };
   for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
-    double xi[3];
-    vol_xi(B, QSET_LIN, t, xi);
+    double xi[3], Ji[3][3];
+    vol_xi(w, B, c, QSET_LIN, t, xi, Ji);
     const size_t i = (size_t)e * nvol + t;
-    const double v = nut_at(xi, wt_vol + i * WT, aux_vol + i * 2);
+    const double v = nut_at(xi, Ji, wt_vol + i * WT, aux_vol + i * 2);
     nut_vol[i] = v;
     if (nut_vol32) nut_vol32[i] = (float)v;
   }
   for (int t = threadIdx.x; t < 6 * fpmax; t += blockDim.x) {
     const int f = t / fpmax, pt = t % fpmax;
-    double xi[3];
+    double xi[3], Ji[3][3];
     const size_t i = (size_t)e * 6 * fpmax + t;
     double v = 0.0;
-    if (face_xi(B, QSET_LIN, f, pt, xi)) v = nut_at(xi, wt_face + i * WT, aux_face + i * 2);
+    if (face_xi(w, B, c, QSET_LIN, f, pt, xi, Ji)) v = nut_at(xi, Ji, wt_face + i * WT, aux_face + i * 2);
     nut_face[i] = v;
     if (nut_face32) nut_face32[i] = (float)v;
   }
@@ -199,12 +225,8 @@ static WallCellData wall_data(dgw_mesh *M) {
   w.ywall = M->wall_ywall_dev;
   w.tauv = M->wall_tauv_dev;
   w.enr_cell = M->enr_cell_dev;
-  w.hy = M->hy_dev64;
-  w.hx = M->P.lx / M->P.nx;
-  w.hz = M->P.lz / M->P.nz;
+  w.mv = M->v64;
   w.nu = M->P.nu;
-  w.nx = M->P.nx;
-  w.ny = M->P.ny;
   w.wall_law = M->P.wall_law;
   return w;
 }

@@ -248,7 +248,7 @@ class Server:
 
 
 def mesh_params(workload, n_layers=1, q_wall=8, wall_law=0, fp32=True) -> MeshParams:
-    return MeshParams(workload.nx, workload.ny, workload.nz, workload.k, 1, q_wall, 0, wall_law, n_layers,
+    return MeshParams(workload.nx, workload.ny, workload.nz, workload.k, 1, q_wall, workload.geometry, wall_law, n_layers,
                       workload.lx, workload.ly, workload.lz, workload.gamma, workload.nu, workload.tau_w,
                       3 if fp32 else 1)
 
@@ -262,6 +262,7 @@ def counters():
 
 
 def mesh_for(workload, **kw) -> Mesh:
-    """Mesh of a channel workload preset (paper_1705_08813_gb300.inputs.Workload)."""
+    """Mesh of a workload preset (paper_1705_08813_gb300.inputs.Workload), channel or bump."""
+    kw.setdefault("geometry", workload.geometry)
     return Mesh(workload.nx, workload.ny, workload.nz, workload.k, lx=workload.lx, ly=workload.ly,
                 lz=workload.lz, gamma=workload.gamma, nu=workload.nu, tau_w=workload.tau_w, **kw)

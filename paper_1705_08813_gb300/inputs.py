@@ -89,11 +89,23 @@ def nu_for_unit_centreline(re_tau: float) -> float:
     return 1.0 / (float(_reichardt(np.float64(re_tau))) * re_tau)
 
 
+# Bump channel (stand-in for the periodic hill of Sec. 5.2): box 9 x 3.036 x 4.5 with a cos^2 bump of
+# height 0.3 on the lower wall; Re_tau = 395 on the half height delta = 1.518 with centreline
+# velocity 1, so nu = delta u_tau / Re_tau.
+BUMP_DELTA = 0.5 * 3.036
+
+
+def bump_workload(name: str, nx: int, ny: int, nz: int, k: int, seed: int, re_tau: float = 395.0) -> Workload:
+    return Workload(name, nx, ny, nz, k, re_tau, BUMP_DELTA * nu_for_unit_centreline(re_tau),
+                    lx=9.0, ly=3.036, lz=4.5, geometry=1, seed=seed)
+
+
 WORKLOADS = {
     "channel_q2_8x8x8": Workload("channel_q2_8x8x8", 8, 8, 8, 2, 180.0, 1.0 / 3250.0, seed=1),
     "channel_q4_32x24x24": Workload("channel_q4_32x24x24", 32, 24, 24, 4, 590.0, 1.0 / 12000.0, seed=2),
     "channel_q3_64x32x32": Workload("channel_q3_64x32x32", 64, 32, 32, 3, 950.0,
                                     nu_for_unit_centreline(950.0), seed=3),
+    "bump_q4_48x32x24": bump_workload("bump_q4_48x32x24", 48, 32, 24, 4, seed=4),
 }
 
 
@@ -202,6 +214,46 @@ def velocity_field(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1,
     enr[:, 0, :] = w.u_tau
     u[std.size:] = enr.reshape(-1)
     return u
+
+
+def _bump_wall(x: np.ndarray, lx: float) -> np.ndarray:
+    s = x - 0.5 * lx
+    return np.where(np.abs(s) < 1.0, 0.3 * np.cos(0.5 * math.pi * s) ** 2, 0.0)
+
+
+def bump_velocity_field(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1,
+                        amplitude: float = 0.1) -> np.ndarray:
+    """Velocity DoF vector for a bump workload: the mean profile along x in the vertical distance to
+    the nearer wall, plus a seeded perturbation uniform in [-1, 1] * amplitude * U_c (U_c the
+    largest mean nodal value) in every component of every node; wall cells carry the perturbation
+    only, with enrichment coefficients u_tau e_x."""
+    nx, ny, nz, k = w.nx, w.ny, w.nz, w.k
+    n3 = (k + 1) ** 3
+    X = nodes.reshape(nz, ny, nx, n3, 3)
+    yd = np.maximum(np.minimum(X[..., 1] - _bump_wall(X[..., 0], w.lx), w.ly - X[..., 1]), 0.0)
+    U = w.u_tau * _reichardt(yd * w.u_tau / w.nu)                 # (nz, ny, nx, n3)
+    wall_row = np.zeros(ny, dtype=bool)
+    if n_layers > 0:
+        wall_row[:n_layers] = True
+        wall_row[ny - n_layers:] = True
+    U = np.where(wall_row[None, :, None, None], 0.0, U)
+    uc = max(float(U.max()), w.u_tau)
+    pert = uniform(w.seed, 3 * U.size, -1.0, 1.0, stream=31).reshape(nz, ny, nx, 3, n3) * amplitude * uc
+    std = pert.copy()
+    std[:, :, :, 0, :] += U
+    u = np.zeros(std.size + 3 * 8 * n_e)
+    u[: std.size] = std.reshape(-1)
+    enr = np.zeros((n_e, 3, 8))
+    enr[:, 0, :] = w.u_tau
+    u[std.size:] = enr.reshape(-1)
+    return u
+
+
+def workload_velocity(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1) -> np.ndarray:
+    """Velocity input of a workload of either geometry."""
+    if w.geometry == 1:
+        return bump_velocity_field(nodes, n_e, w, n_layers=n_layers)
+    return velocity_field(nodes, n_e, w, n_layers=n_layers)
 
 
 def pressure_rhs(n_p: int, seed: int) -> np.ndarray:
