@@ -111,7 +111,7 @@ def oracle_sample(w, target_s=12.0, max_cells=None):
     threads = os.cpu_count() or 1
     O.set_threads(threads)
     om = O.Mesh(**w.mesh_kwargs())
-    u = I.velocity_field(om.node_coords(), om.n_e, w)
+    u = I.workload_velocity(om.node_coords(), om.n_e, w)
     p = I.pressure_field(om.n_p, w.seed)
     n1 = w.k + 1
     # pick cells spread over the mesh, including wall cells, growing until the time budget is used
@@ -170,11 +170,18 @@ def run_reference(args):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
-def laplace_flops_per_cell(k):
-    """FP64 operations of one cell of laplace_box_kernel (2 flops per FMA), counted from its
-    passes with n = k + 1: neighbour trace derivatives 6n^3; x-lines 2n^4 + 4n^3; M_x on the y- and
-    z-face traces 8n^3; y-lines 3n^4 + 4n^3; M_y on the z-face traces 4n^3; z-lines 2n^4 + 4n^3."""
+def laplace_flops_per_cell(k, curved=False):
+    """Floating-point operations of one cell of the Laplace kernel (2 flops per FMA), counted from
+    its passes with n = k + 1.
+    Boxes (laplace_box_kernel): neighbour trace derivatives 6n^3; x-lines 2n^4 + 4n^3; M_x on the
+    y- and z-face traces 8n^3; y-lines 3n^4 + 4n^3; M_y on the z-face traces 4n^3; z-lines
+    2n^4 + 4n^3.
+    Curved cells (vector_op_kernel, OP_LAP): reference gradient at the points and back 16n^4; metric
+    products 21n^3; per face direction (both faces, both sides) normal derivatives 4n^3, tangential
+    passes 28n^3, integration 14n^3, scatter 2n^3 and about 40 per face point (2n^2 points)."""
     n = k + 1
+    if curved:
+        return 2 * (16 * n ** 4 + 21 * n ** 3 + 3 * (48 * n ** 3 + 80 * n ** 2))
     return 2 * (7 * n ** 4 + 30 * n ** 3)
 
 
@@ -193,7 +200,7 @@ def run_gpu(args):
     dgw.load()
     m = dgw.mesh_for(w)
     nodes = m.node_coords()
-    u_host = torch.from_numpy(I.velocity_field(nodes, m.n_e, w)).pin_memory()
+    u_host = torch.from_numpy(I.workload_velocity(nodes, m.n_e, w)).pin_memory()
     p_host = torch.from_numpy(I.pressure_field(m.n_p, w.seed)).pin_memory()
     ud = u_host.to(dev)
     pd = p_host.to(dev)
@@ -301,18 +308,23 @@ def run_gpu(args):
     peaks, src = _peaks()
     k = w.k
     nc = w.nx * w.ny * w.nz
+    curved = w.geometry == 1
     lap32_ms = per_op["laplace32"]["ms"]
     achieved32 = 8.0 * m.n_p / (lap32_ms * 1e-3) / 1e9
-    fl_cell = laplace_flops_per_cell(k)
+    fl_cell = laplace_flops_per_cell(k, curved)
     lap_ms = per_op["laplace"]["ms"]
     fp64_peak = 152 * 4 * 2.07e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
     achieved_tf = nc * fl_cell / (lap_ms * 1e-3) / 1e12
-    roofline = {"kernel": f"laplace_box_kernel<float,{k}>", "bound": "hbm", "achieved": achieved32,
+    kname32 = "vector_op_kernel<float,OP_LAP,GEO_CURVED>" if curved else f"laplace_box_kernel<float,{k}>"
+    kname64 = "vector_op_kernel<double,OP_LAP,GEO_CURVED>" if curved else f"laplace_box_kernel<double,{k}>"
+    if curved:
+        args.traffic_bytes = None   # the ncu capture of record covers the box kernel
+    roofline = {"kernel": kname32, "bound": "hbm", "achieved": achieved32,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved32 / peaks["hbm_gbs"],
                 "traffic": args.traffic_bytes, "algorithmic_bytes_per_launch": 8.0 * m.n_p,
                 "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" if src == "measured" else "fallback 6800 GB/s",
                 "fp32_flop_frac": nc * fl_cell / (lap32_ms * 1e-3) / 1e12 / (152 * 256 * 2.07e9 / 1e12),
-                "fp64_apply": {"kernel": f"laplace_box_kernel<double,{k}>", "bound": "alu", "achieved": achieved_tf,
+                "fp64_apply": {"kernel": kname64, "bound": "alu", "achieved": achieved_tf,
                                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
                                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz (probe measured 1.19)",
                                "hbm_frac": 16.0 * m.n_p / (lap_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
@@ -473,7 +485,10 @@ def run_profile_kernel(args):
     import torch
     from paper_1705_08813_gb300 import dgw, inputs as I
     nx, ny, nz, k = args.profile_cells
-    w = I.Workload("profile", nx, ny, nz, k, 590.0, 1.0 / 12000.0, seed=7)
+    if args.profile_geometry == 1:
+        w = I.bump_workload("profile", nx, ny, nz, k, seed=7)
+    else:
+        w = I.Workload("profile", nx, ny, nz, k, 590.0, 1.0 / 12000.0, seed=7)
     m = dgw.mesh_for(w)
     kind = args.profile_kernel
     dt = torch.float32 if kind.endswith("32") else torch.float64
@@ -501,8 +516,8 @@ def run_profile_kernel(args):
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.profile_reps
-    print(json.dumps({"kernel": kind, "cells": [nx, ny, nz], "degree": k, "n_p": m.n_p, "n_u": m.n_u,
-                      "ms_per_launch": ms}), flush=True)
+    print(json.dumps({"kernel": kind, "geometry": args.profile_geometry, "cells": [nx, ny, nz], "degree": k,
+                      "n_p": m.n_p, "n_u": m.n_u, "ms_per_launch": ms}), flush=True)
     return 0
 
 
@@ -529,6 +544,7 @@ def main():
                              "viscous32"])
     ap.add_argument("--profile-cells", type=int, nargs=4, default=[64, 48, 48, 4], metavar=("NX", "NY", "NZ", "K"))
     ap.add_argument("--profile-reps", type=int, default=3)
+    ap.add_argument("--profile-geometry", type=int, default=0, choices=[0, 1], help="0 channel, 1 bump")
     args = ap.parse_args()
     if args.profile_kernel:
         return run_profile_kernel(args)

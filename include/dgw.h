@@ -61,16 +61,21 @@ enum { DGW_FP64 = 0, DGW_FP32 = 1 };
 /* Mesh and discretisation parameters.
  * Channel (geometry 0): [0,lx] x [-ly/2, ly/2] x [0,lz], periodic in x and z, no-slip walls at
  * y = +-ly/2; vertex rows y_j = (ly/2) tanh(gamma (2j/ny - 1)) / tanh(gamma) (Sec. 5.1).
+ * Bump (geometry 1; the periodic-hill setting of Sec. 5.2): x in [0,lx], lower wall
+ * y_w(x) = 0.3 cos^2(pi (x - lx/2)/2) for |x - lx/2| < 1 (else 0), upper wall y = ly, z in [0,lz],
+ * periodic in x and z; the logical point (a0, a1, a2) maps to x = lx a0/nx, z = lz a2/nz,
+ * y = y_w + (ly - y_w)(1 + f(a1/ny))/2 with f the tanh grading above, and every cell is the
+ * isoparametric Q_k image of its Gauss-Lobatto nodes (J^-1 and det J stored per quadrature point).
  * Enriched cells: the n_layers cell rows next to each wall (Sec. 3.1, eq. enrichment).
- * Wall distance y_B of each Q1 vertex = distance to the closest wall node; tau_w,B = tau_w
- * (Sec. 3.2). psi: Spalding's law (wall_law 0, kappa 0.41, B 5.17) or van Driest's law
+ * Wall distance y_B of each Q1 vertex = distance to the closest wall node (vertex for the bump);
+ * tau_w,B = tau_w (Sec. 3.2). psi: Spalding's law (wall_law 0, kappa 0.41, B 5.17) or van Driest's law
  * (wall_law 1, eq. psi, evaluated as in Appendix A). */
 typedef struct {
   int nx, ny, nz;      /* cells per direction (>= 1; ny >= 2*n_layers when enriched) */
   int degree;          /* k in 1..5 */
   int enrich_l;        /* 1: trilinear weights N^1 (24 coefficients per cell); 0 not supported */
   int q_wall;          /* Gauss points in the wall-normal direction of enriched cells (1..10) */
-  int geometry;        /* 0: channel of boxes (1 reserved for the curved bump) */
+  int geometry;        /* 0: channel of boxes, 1: curved bump channel */
   int wall_law;        /* 0 Spalding, 1 van Driest */
   int n_layers;        /* enriched layers per wall (0 = no enrichment) */
   double lx, ly, lz;   /* domain lengths */
@@ -81,7 +86,8 @@ typedef struct {
 } dgw_mesh_params;
 
 /* Build a mesh: geometry, penalty parameters tau_IP (Sec. 4.2: (k+1)^2 A(dK)/V(K), interior
- * faces weighted 1/2, max over both sides; x10 on walls for the viscous term), wall tables
+ * faces weighted 1/2, max over both sides; x10 on walls for the viscous term; curved cells
+ * integrate A and V with k+2 Gauss points), wall tables
  * (y_h, y+, psi, grad psi at every enriched quadrature point, Sec. 3.2 and Appendix A) and the
  * operator diagonal. Synchronises `stream`. *out receives a library-owned handle. */
 dgw_status dgw_mesh_create(const dgw_mesh_params *params, void *stream, dgw_mesh_t *out);
