@@ -97,6 +97,7 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
     return set_error(DGW_ECUDA, "dgw_mesh_create: no CUDA device");
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaError_t ce = box_constants_init(); ce != cudaSuccess) return cuda_check(ce, "dgw_mesh_create");
   dgw_mesh *M = new dgw_mesh();
   M->P = *P;
   const int k = P->degree, n = k + 1;
@@ -208,7 +209,7 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     for (int t = 0; t < 2; ++t) up2(cg.myf[t], &M->v64.myf[t], &M->v32.myf[t]);
   } else {
     std::vector<double> rops;
-    box_rowops(geo, M->basis64, rops);
+    box_rowscal(geo, rops);
     std::vector<float> rops32(rops.begin(), rops.end());
     M->v64.rowops = upload(M, rops.data(), rops.size(), s, &err);
     M->v32.rowops = upload(M, rops32.data(), rops32.size(), s, &err);

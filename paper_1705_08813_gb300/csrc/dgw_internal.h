@@ -55,7 +55,7 @@ struct MeshView {
   T hx, hz;
   const T *hy;        // [ny] row heights (boxes)
   const T *tau;       // [nc] penalty tau_IP per cell
-  const T *rowops;    // [ny][rowops_size] factorised 1-D Laplace operators per cell row (boxes)
+  const T *rowops;    // [ny][24] per-row scalars of the factorised Laplace operator (boxes)
   // curved metric tables per metric column m = i + nx*j (the map is an extrusion along z):
   // mvol[pair]: [m][a1][a0][MREC]; mxf[y-set]: [m][side][a1][MREC] (faces xi_0 = side);
   // myf[x-set]: [m][side][a0][MREC] (faces xi_1 = side); faces xi_2 = side use mvol
@@ -146,8 +146,12 @@ struct BoxGeometry {
 void box_geometry(int k, int nx, int ny, int nz, double lx, double lz, const std::vector<double> &yv, BoxGeometry &g);
 // Diagonal of the SIPG Laplacian (Jacobi), from the 1-D mass and stiffness diagonals.
 void laplace_diagonal(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &dg);
-// Per-row 1-D operators of the factorised SIPG Laplacian on boxes.
+// Per-row 1-D operators of the factorised SIPG Laplacian on boxes (full matrices, host use).
 void box_rowops(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &R);
+// Per-row scalars of the same operator for the device kernel ([ny][24]).
+void box_rowscal(const BoxGeometry &g, std::vector<double> &R);
+// Degree tables of the box kernel in constant memory (once per device; host-synchronous).
+cudaError_t box_constants_init();
 // Host evaluation of the same factorised operator (small coarse-level matrices).
 void host_box_apply(const BoxGeometry &g, const Basis<double> &B, const std::vector<double> &R, const double *x,
                     double *y);
@@ -164,13 +168,32 @@ void curved_geometry(const dgw_mesh_params &P, int nx, int ny, int nz, int k, co
 // Physical (x, y) of the logical coordinates (a0, a1) of the bump map (z is lz a2 / nz).
 void bump_point(const dgw_mesh_params &P, int nx, int ny, double a0, double a1, double *x, double *y);
 
+// Elementwise epilogue of a Laplace apply t = A x, fused into the operator kernel:
+//   LAP_PLAIN y = t; LAP_RESIDUAL y = b - t;
+//   LAP_CHEB  Chebyshev step d = (first ? 0 : c1 d) + c2 D^-1 (b - t), xout = x + d (xout != x:
+//             neighbouring cells still read x; y is not written).
+enum { LAP_PLAIN = 0, LAP_RESIDUAL = 1, LAP_CHEB = 2 };
+template <typename T>
+struct LapEpi {
+  int mode;
+  const T *b;
+  T *d;
+  const T *dinv;
+  T *xout;
+  T c1, c2;
+  int first;
+};
+
 // kernels (launched by api.cu)
 template <typename T>
 cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s);
 // Jacobi diagonal of the SIPG Laplacian of a curved mesh (FP64, one thread per DoF)
 cudaError_t launch_curved_diagonal(const MeshView<double> &m, double *dg, cudaStream_t s);
 template <typename T>
-cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s);
+cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s,
+                             const LapEpi<T> *epi = nullptr);
 cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);

@@ -6,19 +6,45 @@
 //   y_c = sum_d (L_d (x)_d M (x) M) u_c + sum_{d,s} (N_{d,s} (x)_d M (x) M) u_{nb(d,s)},
 // where L_d (n x n) holds the stiffness along d plus the own-side face terms of both faces
 // normal to d, and N_{d,s} is the rank-2 coupling to the neighbour across face s, which only
-// needs the neighbour's trace value and reference normal derivative on the shared face. L_d and
-// the coupling vectors depend only on the cell row j (graded spacing, penalty), so they are
-// tabulated per row on the host (box_rowops) and staged in shared memory.
+// needs the neighbour's trace value tv and reference normal derivative td on the shared face.
+// With the 1-D stiffness K and the end derivatives D_s = l'(s), one line of L_d u + N u_nb is
+//   out_a = a_d (K u)_a + sum_s [ p_s D_s,a (tv_s - u_e(s)) + delta_{a,e(s)} (-p_s D_s.u
+//           + t_s (u_e(s) - tv_s) - e_s td_s) ],
+// e(0) = 0, e(1) = k: the row of the cell (graded spacing, penalty) enters through seven scalars
+// per direction (a_d = |K|/h_d^2, p_s = a_d sigma_s/2, t_s = |K| tau_s/h_d, e_s = |K| sigma_s/(2 h_d h'_d),
+// zero for wall faces), while K, M and D_s depend only on the degree and sit in constant memory,
+// so the fully unrolled line passes read them as instruction operands.
 //
 // Evaluation: y = M_z [ M_y (L_x u + nbr_x) + L_y (M_x u) + nbr_y' ] + L_z (M_x M_y u) + nbr_z'',
 // three line passes (one thread owns a whole 1-D line in registers), with the y-face traces
 // transformed by M_x and the z-face traces by M_x M_y. A CTA holds cpb consecutive cells along x.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
 #include "sumfac.cuh"
 
 namespace dgw {
 
-// Per-row operator layout: Lx, Ly, Lz (n*n each), then for d in {x,y,z}, s in {0,1}: c1[n], c2[n].
-__host__ __device__ constexpr int rowops_size(int n) { return 3 * n * n + 12 * n; }
+// Per-row scalars: for d in {x, y, z}: a_d, p_0, p_1, t_0, t_1, e_0, e_1, (pad).
+constexpr int kRowScal = 24;
+
+// Degree tables: 1-D stiffness K, mass M (n x n, row-major), end derivatives D_0, D_1.
+template <typename T>
+struct BoxConst {
+  T K[NMAX * NMAX];
+  T M[NMAX * NMAX];
+  T D[2][NMAX];
+};
+__constant__ BoxConst<float> c_box32[5];
+__constant__ BoxConst<double> c_box64[5];
+
+template <typename T>
+__device__ __forceinline__ const BoxConst<T> &box_const(int k);
+template <>
+__device__ __forceinline__ const BoxConst<float> &box_const<float>(int k) { return c_box32[k - 1]; }
+template <>
+__device__ __forceinline__ const BoxConst<double> &box_const<double>(int k) { return c_box64[k - 1]; }
 
 // FP32: up to 3 CTAs of <= 256 threads per SM for k <= 4 (register budget ~85/thread), 2 for k = 5;
 // FP64 is FP64-pipe bound and keeps the default budget.
@@ -27,190 +53,195 @@ struct BoxOcc { static constexpr int min_blocks = 1; };
 template <int K>
 struct BoxOcc<float, K> { static constexpr int min_blocks = K <= 4 ? 3 : 2; };
 
+// One line of L_d u + N_d (tv, td) (see the file comment); R = the 8 scalars of direction d.
+template <typename T, int K>
+__device__ __forceinline__ void line_op(const T (&u)[K + 1], const T *R, T tv0, T td0, T tv1, T td1, T (&out)[K + 1]) {
+  constexpr int n = K + 1;
+  const BoxConst<T> &C = box_const<T>(K);
+  const T a = R[0], p0 = R[1], p1 = R[2], t0 = R[3], t1 = R[4], e0 = R[5], e1 = R[6];
+  const T j0 = tv0 - u[0], j1 = tv1 - u[n - 1];
+  T d0 = T(0), d1 = T(0);
+#pragma unroll
+  for (int b = 0; b < n; ++b) {
+    d0 += C.D[0][b] * u[b];
+    d1 += C.D[1][b] * u[b];
+  }
+#pragma unroll
+  for (int r = 0; r < n; ++r) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < n; ++b) s += C.K[r * n + b] * u[b];
+    out[r] = a * s + p0 * C.D[0][r] * j0 + p1 * C.D[1][r] * j1;
+  }
+  out[0] += -p0 * d0 - t0 * j0 - e0 * td0;
+  out[n - 1] += -p1 * d1 - t1 * j1 - e1 * td1;
+}
+
+// v <- M v along a line of n values
+template <typename T, int K>
+__device__ __forceinline__ void mass_line(const T (&v)[K + 1], T (&out)[K + 1]) {
+  constexpr int n = K + 1;
+  const BoxConst<T> &C = box_const<T>(K);
+#pragma unroll
+  for (int r = 0; r < n; ++r) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < n; ++b) s += C.M[r * n + b] * v[b];
+    out[r] = s;
+  }
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p,
-                                                                                T *__restrict__ y, int cpb) {
+                                                                                T *__restrict__ y, int cpb,
+                                                                                LapEpi<T> epi) {
   constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
-  constexpr int ROW = rowops_size(n);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Ms = reinterpret_cast<T *>(smem_raw);   // n2
-  T *Dd = Ms + n2;                             // 2n: l_j'(0), l_j'(1)
-  T *R = Dd + 2 * n;                           // ROW
-  T *U = R + ROW;                              // cpb n3 (input, then output)
-  T *A = U + cpb * n3;                         // cpb n3 (T1 -> W)
-  T *B = A + cpb * n3;                         // cpb n3 (T2 -> T3)
-  T *TR = B + cpb * n3;                        // cpb * 6 faces * 2 (val, der) * n2
-  T *TY = TR + cpb * 24 * n2;                  // cpb * 2 faces * 2 * n2 : y-face traces after M_x
-  T *TZ = TY + cpb * 8 * n2;                   // cpb * 2 * 2 * n2 : z-face traces after M_x
+  T *Rs = reinterpret_cast<T *>(smem_raw);     // kRowScal
+  T *U = Rs + kRowScal;                         // cpb n3 (input, then output)
+  T *A = U + cpb * n3;                          // cpb n3 (T1 -> W)
+  T *B = A + cpb * n3;                          // cpb n3 (T2 -> T3)
+  T *TR = B + cpb * n3;                         // cpb * 6 faces * 2 (val, der) * n2
+  T *TY = TR + cpb * 24 * n2;                   // cpb * 2 faces * 2 * n2 : y-face traces after M_x
+  T *TZ = TY + cpb * 8 * n2;                    // cpb * 2 * 2 * n2 : z-face traces after M_x
+  const BoxConst<T> &C = box_const<T>(K);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int c0 = blockIdx.x * cpb;
   const int i0 = c0 % m.nx, j = (c0 / m.nx) % m.ny, kz = c0 / (m.nx * m.ny);
-  const Basis<T> *Bg = m.basis;
-  for (int t = tid; t < n2; t += nt) Ms[t] = Bg->mass[t];
-  for (int t = tid; t < n; t += nt) { Dd[t] = Bg->dend[0][t]; Dd[n + t] = Bg->dend[1][t]; }
-  const T *Rg = m.rowops + (size_t)j * ROW;
-  for (int t = tid; t < ROW; t += nt) R[t] = Rg[t];
+  const T *Rg = m.rowops + (size_t)j * kRowScal;
+  for (int t = tid; t < kRowScal; t += nt) Rs[t] = Rg[t];
   const T *pc = p + (size_t)c0 * n3;
   for (int t = tid; t < cpb * n3; t += nt) U[t] = pc[t];
-  __syncthreads();   // Dd, Ms and R are read by every thread below
-  // neighbour traces: value and reference normal derivative on the shared face
-  for (int t = tid; t < cpb * 6 * n2; t += nt) {
-    const int cl = t / (6 * n2), f = (t / n2) % 6, node = t % n2;
-    const int d = f >> 1, side = f & 1;
-    int ii = i0 + cl, jj = j, kk = kz;
-    const int sg = side ? 1 : -1;
-    bool wall = false;
+  // Every thread owns line l of cell cl in all three passes (x-, y- then z-lines; l indexes the
+  // face nodes of the same two tangential axes), so the index arithmetic is done once here.
+  const bool line = tid < cpb * n2;
+  const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
+  const int lq = l / n, lr = l - lq * n;   // l = lr + n * lq
+  int *nbr = reinterpret_cast<int *>(TZ + cpb * 8 * n2);   // [cpb][6] neighbour cells (-1: wall)
+  if (tid < cpb * 6) {
+    const int c = tid / 6, f = tid - c * 6, d = f >> 1, sg = (f & 1) ? 1 : -1;
+    int ii = i0 + c, jj = j, kk = kz;
     if (d == 0) ii = (ii + sg + m.nx) % m.nx;
     else if (d == 2) kk = (kk + sg + m.nz) % m.nz;
-    else { jj += sg; wall = jj < 0 || jj >= m.ny; }
-    T val = T(0), der = T(0);
-    if (!wall) {
-      const T *pn = p + ((size_t)ii + (size_t)m.nx * (jj + (size_t)m.ny * kk)) * n3;
-      const int t1 = node % n, t2 = node / n;
-      // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
-      const int ep = side ? 0 : 1;
-      const T *dv = Dd + ep * n;
-      int stride, base;
-      if (d == 0) { stride = 1; base = n * (t1 + n * t2); }
-      else if (d == 1) { stride = n; base = t1 + n2 * t2; }
-      else { stride = n2; base = t1 + n * t2; }
-      const int lay = ep ? n - 1 : 0;
-      val = pn[base + lay * stride];
-#pragma unroll
-      for (int b = 0; b < n; ++b) der += dv[b] * pn[base + b * stride];
-    }
-    TR[((cl * 6 + f) * 2 + 0) * n2 + node] = val;
-    TR[((cl * 6 + f) * 2 + 1) * n2 + node] = der;
+    else jj += sg;
+    nbr[tid] = (jj < 0 || jj >= m.ny) ? -1 : ii + m.nx * (jj + m.ny * kk);
   }
   __syncthreads();
-  const T *Lx = R, *Ly = R + n2, *Lz = R + 2 * n2;
-  auto c1 = [&](int d, int s) -> const T * { return R + 3 * n2 + (d * 2 + s) * 2 * n; };
-  auto c2 = [&](int d, int s) -> const T * { return R + 3 * n2 + (d * 2 + s) * 2 * n + n; };
-  // ---- phase A: x-lines (T1 = Lx u + nbr_x, T2 = M_x u); y-traces <- M_x; z-traces <- M_x
-  {
-    const int nlines = cpb * n2, nty = cpb * 4 * n, total = nlines + 2 * nty;
-    for (int t = tid; t < total; t += nt) {
-      if (t < nlines) {
-        const int cl = t / n2, l = t % n2;
-        const int base = cl * n3 + n * l;
-        T u[n], o1[n], o2[n];
+  // neighbour traces at face node l of the six faces: value and reference normal derivative
+  if (line) {
 #pragma unroll
-        for (int b = 0; b < n; ++b) u[b] = U[base + b];
-        const T v0 = TR[((cl * 6 + 0) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 0) * 2 + 1) * n2 + l];
-        const T v1 = TR[((cl * 6 + 1) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 1) * 2 + 1) * n2 + l];
-        const T *a0 = c1(0, 0), *b0 = c2(0, 0), *a1 = c1(0, 1), *b1 = c2(0, 1);
-#pragma unroll
-        for (int a = 0; a < n; ++a) {
-          T s1 = a0[a] * v0 + b0[a] * d0 + a1[a] * v1 + b1[a] * d1, s2 = T(0);
-#pragma unroll
-          for (int b = 0; b < n; ++b) {
-            s1 += Lx[a * n + b] * u[b];
-            s2 += Ms[a * n + b] * u[b];
-          }
-          o1[a] = s1;
-          o2[a] = s2;
-        }
-#pragma unroll
-        for (int a = 0; a < n; ++a) { A[base + a] = o1[a]; B[base + a] = o2[a]; }
-      } else {
-        // trace transform along x (t1 axis of y- and z-faces): item = (cl, face, arr, t2)
-        const int r = t - nlines;
-        const bool isz = r >= nty;
-        const int q = isz ? r - nty : r;
-        const int cl = q / (4 * n), fa = (q / n) % 4, t2 = q % n;   // fa = 2*face + (val|der)
-        const int fl = fa >> 1, arr = fa & 1;
-        const int f = (isz ? 4 : 2) + fl;
-        const T *src = TR + ((cl * 6 + f) * 2 + arr) * n2 + n * t2;
-        T *dst = (isz ? TZ : TY) + ((cl * 2 + fl) * 2 + arr) * n2 + n * t2;
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, side = f & 1, nb = nbr[cl * 6 + f];
+      T val = T(0), der = T(0);
+      if (nb >= 0) {
+        const T *pn = p + (size_t)nb * n3;
+        // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
+        const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
+        const int base = d == 0 ? n * l : (d == 1 ? lr + n2 * lq : l);
         T v[n];
+#pragma unroll
+        for (int b = 0; b < n; ++b) v[b] = pn[base + b * stride];
+        val = side ? v[0] : v[n - 1];
+#pragma unroll
+        for (int b = 0; b < n; ++b) der += (side ? C.D[0][b] : C.D[1][b]) * v[b];
+      }
+      TR[((cl * 6 + f) * 2 + 0) * n2 + l] = val;
+      TR[((cl * 6 + f) * 2 + 1) * n2 + l] = der;
+    }
+  }
+  __syncthreads();
+  // ---- phase A: x-lines (T1 = Lx u + nbr_x, T2 = M_x u); y- and z-traces <- M_x (items
+  // it = l, l + n^2, ... < 4n: face (it / n) >> 1, array (it / n) & 1, t2 = it % n)
+  if (line) {
+    const int base = cl * n3 + n * l;
+    T u[n], o1[n], o2[n];
+#pragma unroll
+    for (int b = 0; b < n; ++b) u[b] = U[base + b];
+    const T v0 = TR[((cl * 6 + 0) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 0) * 2 + 1) * n2 + l];
+    const T v1 = TR[((cl * 6 + 1) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 1) * 2 + 1) * n2 + l];
+    line_op<T, K>(u, Rs, v0, d0, v1, d1, o1);
+    mass_line<T, K>(u, o2);
+#pragma unroll
+    for (int a = 0; a < n; ++a) { A[base + a] = o1[a]; B[base + a] = o2[a]; }
+    for (int it = l; it < 4 * n; it += n2) {   // one item per thread for k >= 3
+      const int iq = it / n, ir = it - iq * n;
+      const int fl = iq >> 1, arr = iq & 1;
+#pragma unroll
+      for (int isz = 0; isz < 2; ++isz) {
+        const T *src = TR + ((cl * 6 + (isz ? 4 : 2) + fl) * 2 + arr) * n2 + n * ir;
+        T *dst = (isz ? TZ : TY) + ((cl * 2 + fl) * 2 + arr) * n2 + n * ir;
+        T v[n], o[n];
 #pragma unroll
         for (int b = 0; b < n; ++b) v[b] = src[b];
+        mass_line<T, K>(v, o);
 #pragma unroll
-        for (int a = 0; a < n; ++a) {
-          T s = T(0);
-#pragma unroll
-          for (int b = 0; b < n; ++b) s += Ms[a * n + b] * v[b];
-          dst[a] = s;
-        }
+        for (int a = 0; a < n; ++a) dst[a] = o[a];
       }
     }
   }
   __syncthreads();
-  // ---- phase B: y-lines (W = M_y T1 + Ly T2 + nbr_y', T3 = M_y T2); z-traces <- M_y (into TR z slots)
-  {
-    const int nlines = cpb * n2, ntz = cpb * 4 * n, total = nlines + ntz;
-    for (int t = tid; t < total; t += nt) {
-      if (t < nlines) {
-        const int cl = t / n2, x = t % n, z = (t / n) % n;
-        const int base = cl * n3 + x + n2 * z;
-        T a1[n], a2[n], w[n], t3[n];
+  // ---- phase B: y-lines at (x, z) = (lr, lq): W = M_y T1 + Ly T2 + nbr_y', T3 = M_y T2; z-face
+  // traces (indexed x + n*y) <- M_y (items it as in phase A, x = it % n)
+  if (line) {
+    const int base = cl * n3 + lr + n2 * lq;
+    T a1[n], a2[n], w[n], t3[n], ly[n];
 #pragma unroll
-        for (int c = 0; c < n; ++c) { a1[c] = A[base + n * c]; a2[c] = B[base + n * c]; }
-        const int fi = x + n * z;
-        const T v0 = TY[((cl * 2 + 0) * 2 + 0) * n2 + fi], d0 = TY[((cl * 2 + 0) * 2 + 1) * n2 + fi];
-        const T v1 = TY[((cl * 2 + 1) * 2 + 0) * n2 + fi], d1 = TY[((cl * 2 + 1) * 2 + 1) * n2 + fi];
-        const T *e0 = c1(1, 0), *g0 = c2(1, 0), *e1 = c1(1, 1), *g1 = c2(1, 1);
+    for (int c = 0; c < n; ++c) { a1[c] = A[base + n * c]; a2[c] = B[base + n * c]; }
+    const T v0 = TY[((cl * 2 + 0) * 2 + 0) * n2 + l], d0 = TY[((cl * 2 + 0) * 2 + 1) * n2 + l];
+    const T v1 = TY[((cl * 2 + 1) * 2 + 0) * n2 + l], d1 = TY[((cl * 2 + 1) * 2 + 1) * n2 + l];
+    line_op<T, K>(a2, Rs + 8, v0, d0, v1, d1, ly);
+    mass_line<T, K>(a1, w);
+    mass_line<T, K>(a2, t3);
 #pragma unroll
-        for (int b = 0; b < n; ++b) {
-          T s = e0[b] * v0 + g0[b] * d0 + e1[b] * v1 + g1[b] * d1, s3 = T(0);
+    for (int b = 0; b < n; ++b) { A[base + n * b] = w[b] + ly[b]; B[base + n * b] = t3[b]; }
+    for (int it = l; it < 4 * n; it += n2) {
+      const int iq = it / n, ir = it - iq * n;
+      const int fl = iq >> 1, arr = iq & 1;
+      const T *src = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + ir;
+      T *dst = TR + ((cl * 6 + 4 + fl) * 2 + arr) * n2 + ir;
+      T v[n], o[n];
 #pragma unroll
-          for (int c = 0; c < n; ++c) {
-            s += Ms[b * n + c] * a1[c] + Ly[b * n + c] * a2[c];
-            s3 += Ms[b * n + c] * a2[c];
-          }
-          w[b] = s;
-          t3[b] = s3;
-        }
+      for (int b = 0; b < n; ++b) v[b] = src[n * b];
+      mass_line<T, K>(v, o);
 #pragma unroll
-        for (int b = 0; b < n; ++b) { A[base + n * b] = w[b]; B[base + n * b] = t3[b]; }
-      } else {
-        // z-face traces (indexed x + n*y) after M_x: apply M_y along t2 = y; item = (cl, fl, arr, x)
-        const int q = t - nlines;
-        const int cl = q / (4 * n), pr = (q / n) % 4, x = q % n;
-        const int fl = pr >> 1, arr = pr & 1;
-        const T *src = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + x;
-        T *dst = TR + ((cl * 6 + 4 + fl) * 2 + arr) * n2 + x;
-        T v[n];
-#pragma unroll
-        for (int b = 0; b < n; ++b) v[b] = src[n * b];
-#pragma unroll
-        for (int a = 0; a < n; ++a) {
-          T s = T(0);
-#pragma unroll
-          for (int b = 0; b < n; ++b) s += Ms[a * n + b] * v[b];
-          dst[n * a] = s;
-        }
-      }
+      for (int a = 0; a < n; ++a) dst[n * a] = o[a];
     }
   }
   __syncthreads();
-  // ---- phase C: z-lines (y = M_z W + Lz T3 + nbr_z'')
-  for (int t = tid; t < cpb * n2; t += nt) {
-    const int cl = t / n2, l = t % n2;   // l = x + n*y
+  // ---- phase C: z-lines at l = x + n*y (y = M_z W + Lz T3 + nbr_z'')
+  if (line) {
     const int base = cl * n3 + l;
-    T a1[n], a2[n];
+    T a1[n], a2[n], w[n], lz[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) { a1[e] = A[base + n2 * e]; a2[e] = B[base + n2 * e]; }
     const T v0 = TR[((cl * 6 + 4) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 4) * 2 + 1) * n2 + l];
     const T v1 = TR[((cl * 6 + 5) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 5) * 2 + 1) * n2 + l];
-    const T *e0 = c1(2, 0), *g0 = c2(2, 0), *e1 = c1(2, 1), *g1 = c2(2, 1);
+    line_op<T, K>(a2, Rs + 16, v0, d0, v1, d1, lz);
+    mass_line<T, K>(a1, w);
 #pragma unroll
-    for (int c = 0; c < n; ++c) {
-      T s = e0[c] * v0 + g0[c] * d0 + e1[c] * v1 + g1[c] * d1;
-#pragma unroll
-      for (int e = 0; e < n; ++e) s += Ms[c * n + e] * a1[e] + Lz[c * n + e] * a2[e];
-      U[base + n2 * c] = s;
-    }
+    for (int c = 0; c < n; ++c) U[base + n2 * c] = w[c] + lz[c];
   }
   __syncthreads();
-  T *yc = y + (size_t)c0 * n3;
-  for (int t = tid; t < cpb * n3; t += nt) yc[t] = U[t];
+  const size_t o = (size_t)c0 * n3;
+  if (epi.mode == LAP_PLAIN) {
+    for (int t = tid; t < cpb * n3; t += nt) y[o + t] = U[t];
+  } else if (epi.mode == LAP_RESIDUAL) {
+    for (int t = tid; t < cpb * n3; t += nt) y[o + t] = epi.b[o + t] - U[t];
+  } else {
+    for (int t = tid; t < cpb * n3; t += nt) {
+      const size_t i = o + t;
+      const T dn = (epi.first ? T(0) : epi.c1 * epi.d[i]) + epi.c2 * epi.dinv[i] * (epi.b[i] - U[t]);
+      epi.d[i] = dn;
+      epi.xout[i] = p[i] + dn;
+    }
+  }
 }
 
 template <typename T>
 static size_t box_smem(int n, int cpb) {
   const int n2 = n * n, n3 = n2 * n;
-  return sizeof(T) * ((size_t)n2 + 2 * n + rowops_size(n) + 3 * (size_t)cpb * n3 + (size_t)cpb * (24 + 8 + 8) * n2);
+  return sizeof(T) * ((size_t)kRowScal + 3 * (size_t)cpb * n3 + (size_t)cpb * (24 + 8 + 8) * n2) +
+         sizeof(int) * (size_t)cpb * 6;
 }
 
 // cells per CTA: the largest power of two dividing nx with cpb*(k+1)^2 <= 256 and cpb <= 8
@@ -220,8 +251,52 @@ static int box_cpb(int nx, int n) {
   return c;
 }
 
+// Degree tables in constant memory, written once per device before the first box kernel runs.
+cudaError_t box_constants_init() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  BoxConst<double> h64[5];
+  BoxConst<float> h32[5];
+  std::memset(h64, 0, sizeof(h64));
+  std::memset(h32, 0, sizeof(h32));
+  for (int k = 1; k <= 5; ++k) {
+    Basis<double> B;
+    fill_basis<double>(k, k + 1, k + 1, &B);
+    const int n = k + 1, q = B.q[QSET_LIN];
+    for (int a = 0; a < n; ++a) {
+      for (int b = 0; b < n; ++b) {
+        double mv = 0.0, kv = 0.0;
+        for (int t = 0; t < q; ++t) {
+          mv += B.w[QSET_LIN][t] * B.S[QSET_LIN][t * n + a] * B.S[QSET_LIN][t * n + b];
+          kv += B.w[QSET_LIN][t] * B.D[QSET_LIN][t * n + a] * B.D[QSET_LIN][t * n + b];
+        }
+        h64[k - 1].M[a * n + b] = mv;
+        h64[k - 1].K[a * n + b] = kv;
+      }
+      h64[k - 1].D[0][a] = B.dend[0][a];
+      h64[k - 1].D[1][a] = B.dend[1][a];
+    }
+    for (int i = 0; i < NMAX * NMAX; ++i) {
+      h32[k - 1].M[i] = (float)h64[k - 1].M[i];
+      h32[k - 1].K[i] = (float)h64[k - 1].K[i];
+    }
+    for (int sd = 0; sd < 2; ++sd)
+      for (int i = 0; i < NMAX; ++i) h32[k - 1].D[sd][i] = (float)h64[k - 1].D[sd][i];
+  }
+  e = cudaMemcpyToSymbol(c_box64, h64, sizeof(h64));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_box32, h32, sizeof(h32));
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
 template <typename T, int K>
-static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, cudaStream_t s) {
+static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
   constexpr int n = K + 1;
   const int cpb = box_cpb(m.nx, n);
   const size_t sm = box_smem<T>(n, cpb);
@@ -236,25 +311,73 @@ static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, cudaStre
   const int threads = ((cpb * n * n + 31) / 32) * 32;
   note_launch();
   note_dofs(m.np);
-  laplace_box_kernel<T, K><<<m.nc / cpb, threads, sm, s>>>(m, p, y, cpb);
+  laplace_box_kernel<T, K><<<m.nc / cpb, threads, sm, s>>>(m, p, y, cpb, epi);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s) {
-  if (m.geo == GEO_CURVED) return launch_vector_op<T>(OP_LAP, m, p, y, s);   // per-point metrics
+cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
+  if (epi.mode == LAP_CHEB && epi.xout == p) return cudaErrorInvalidValue;   // neighbours read p
+  if (m.geo == GEO_CURVED) return launch_vector_op<T>(OP_LAP, m, p, y, s, &epi);   // per-point metrics
   switch (m.n1) {
-    case 2: return launch_box_k<T, 1>(m, p, y, s);
-    case 3: return launch_box_k<T, 2>(m, p, y, s);
-    case 4: return launch_box_k<T, 3>(m, p, y, s);
-    case 5: return launch_box_k<T, 4>(m, p, y, s);
-    case 6: return launch_box_k<T, 5>(m, p, y, s);
+    case 2: return launch_box_k<T, 1>(m, p, y, epi, s);
+    case 3: return launch_box_k<T, 2>(m, p, y, epi, s);
+    case 4: return launch_box_k<T, 3>(m, p, y, epi, s);
+    case 5: return launch_box_k<T, 4>(m, p, y, epi, s);
+    case 6: return launch_box_k<T, 5>(m, p, y, epi, s);
   }
   return cudaErrorInvalidValue;
 }
 
+template <typename T>
+cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s) {
+  LapEpi<T> epi{};
+  epi.mode = LAP_PLAIN;
+  return launch_laplace_epi<T>(m, p, y, epi, s);
+}
+
 template cudaError_t launch_laplace<double>(const MeshView<double> &, const double *, double *, cudaStream_t);
 template cudaError_t launch_laplace<float>(const MeshView<float> &, const float *, float *, cudaStream_t);
+template cudaError_t launch_laplace_epi<double>(const MeshView<double> &, const double *, double *,
+                                                const LapEpi<double> &, cudaStream_t);
+template cudaError_t launch_laplace_epi<float>(const MeshView<float> &, const float *, float *, const LapEpi<float> &,
+                                               cudaStream_t);
+
+// Per-row scalars of the factorised operator (see the file comment): with h = (hx, hy_j, hz),
+// |K| = hx hy hz, for direction d and face s present (g_s = 1; y-faces at the walls are absent):
+// a_d = |K|/h_d^2, p_s = a_d sigma_s/2, t_s = |K| tau_s/h_d (tau_s: max over the two cells),
+// e_s = |K| sigma_s/(2 h_d h'_d) (h'_d: the neighbour's spacing), sigma_0 = -1, sigma_1 = +1.
+void box_rowscal(const BoxGeometry &g, std::vector<double> &R) {
+  R.assign((size_t)g.ny * kRowScal, 0.0);
+  for (int j = 0; j < g.ny; ++j) {
+    double *Rj = R.data() + (size_t)j * kRowScal;
+    const double h[3] = {g.hx, g.hy[j], g.hz};
+    const double hV = h[0] * h[1] * h[2];
+    const double tauc = g.tau[(size_t)j * g.nx];
+    for (int d = 0; d < 3; ++d) {
+      double *r = Rj + 8 * d;
+      const double hd = h[d], sc = hV / hd;
+      r[0] = sc / hd;
+      for (int s = 0; s < 2; ++s) {
+        double tau = tauc, hdo = hd;
+        if (d == 1) {
+          const int jn = j + (s ? 1 : -1);
+          if (jn < 0 || jn >= g.ny) continue;   // homogeneous Neumann on walls: no face terms
+          tau = std::max(tauc, g.tau[(size_t)jn * g.nx]);
+          hdo = g.hy[jn];
+        }
+        const double sig = s ? 1.0 : -1.0;
+        r[1 + s] = 0.5 * sig * sc / hd;
+        r[3 + s] = sc * tau;
+        r[5 + s] = 0.5 * sig * sc / hdo;
+      }
+    }
+  }
+}
+
+// Full per-row 1-D operators of the same factorisation (host assembly of small coarse-level
+// matrices): Lx, Ly, Lz (n*n each), then for d in {x,y,z}, s in {0,1}: c1[n], c2[n].
+static constexpr int rowops_size(int n) { return 3 * n * n + 12 * n; }
 
 // Per-row 1-D operators of the factorised SIPG Laplacian (see the file comment).
 void box_rowops(const BoxGeometry &g, const Basis<double> &B, std::vector<double> &R) {

@@ -325,6 +325,7 @@ struct Lvl {
   MeshView<T> view;
   long n = 0;
   T *dinv = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr, *z = nullptr;
+  T *x2 = nullptr;   // second iterate buffer of the fused Chebyshev steps
   double *sc = nullptr, *partial = nullptr;
   double lmax = 1.0;
   XferDims to_coarse{};   // transfer to the next coarser level
@@ -543,7 +544,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
         L->view.hy = hyd;
         L->view.tau = taud;
         std::vector<double> rops;
-        box_rowops(L->geo, M->basis64, rops);
+        box_rowscal(L->geo, rops);
         std::vector<T> ropsT(rops.begin(), rops.end());
         T *rd = lalloc<T>(L, ropsT.size(), e, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(rd, ropsT.data(), ropsT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
@@ -566,6 +567,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     if (dg_dev) cudaFree(dg_dev);
     L->x = lalloc<T>(L, L->n, e, s); L->b = lalloc<T>(L, L->n, e, s); L->r = lalloc<T>(L, L->n, e, s);
     L->d = lalloc<T>(L, L->n, e, s); L->t = lalloc<T>(L, L->n, e, s); L->z = lalloc<T>(L, L->n, e, s);
+    L->x2 = lalloc<T>(L, L->n, e, s);
     void *p = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
     if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * sizeof(double), s);
@@ -696,23 +698,45 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
   return e;
 }
 
+// Chebyshev smoothing with the point-Jacobi diagonal. Every step after a zero initial guess is one
+// fused launch: the operator kernel applies A to the current iterate and, in its epilogue, updates
+// the direction d and writes the next iterate into the other buffer (neighbouring cells still read
+// the current one); the result ends in L->x.
 template <typename T>
 static void chebyshev(const Hierarchy<T> *H, Lvl<T> *L, bool zero_init, cudaStream_t s) {
   const double lmax = 1.2 * L->lmax, lmin = lmax / kSmoothRange;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
   const int G = mg_grid(L->n);
-  // first step
-  if (!zero_init) launch_laplace<T>(L->view, L->x, L->t, s);
-  note_launch();
-  cheb_step<T><<<G, 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, T(0), (T)(1.0 / theta), 1, zero_init ? 1 : 0);
-  for (int k = 1; k < H->cheb; ++k) {
-    const double rho_new = 1.0 / (2.0 * sigma - rho);
-    launch_laplace<T>(L->view, L->x, L->t, s);
+  T *cur = L->x;
+  int k = 0;
+  if (zero_init) {   // x = 0: the first step needs no operator apply
     note_launch();
-    cheb_step<T><<<G, 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), 0, 0);
-    rho = rho_new;
+    cheb_step<T><<<G, 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, T(0), (T)(1.0 / theta), 1, 1);
+    k = 1;
   }
+  for (; k < H->cheb; ++k) {
+    LapEpi<T> epi{};
+    epi.mode = LAP_CHEB;
+    epi.b = L->b;
+    epi.d = L->d;
+    epi.dinv = L->dinv;
+    epi.xout = cur == L->x ? L->x2 : L->x;
+    if (k == 0) {
+      epi.c1 = T(0);
+      epi.c2 = (T)(1.0 / theta);
+      epi.first = 1;
+    } else {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      epi.c1 = (T)(rho_new * rho);
+      epi.c2 = (T)(2.0 * rho_new / delta);
+      epi.first = 0;
+      rho = rho_new;
+    }
+    launch_laplace_epi<T>(L->view, cur, nullptr, epi, s);
+    cur = epi.xout;
+  }
+  if (cur != L->x) cudaMemcpyAsync(L->x, cur, L->n * sizeof(T), cudaMemcpyDeviceToDevice, s);
 }
 
 template <typename T>
@@ -760,9 +784,10 @@ static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
   }
   Lvl<T> *C = H->L[lev + 1];
   chebyshev(H, L, true, s);
-  launch_laplace<T>(L->view, L->x, L->t, s);
-  note_launch();
-  residual_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(L->r, L->b, L->t, L->n);
+  LapEpi<T> res{};
+  res.mode = LAP_RESIDUAL;
+  res.b = L->b;
+  launch_laplace_epi<T>(L->view, L->x, L->r, res, s);   // r = b - A x
   note_launch();
   if (L->p1) p_restrict<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, L->r, C->b);
   else restrict_kernel<T><<<C->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, L->r, C->b);

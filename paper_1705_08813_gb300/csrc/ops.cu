@@ -219,7 +219,8 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
 }
 
 template <typename T, int OP, int GEO>
-__global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y) {
+__global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y,
+                                                        LapEpi<T> epi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Basis<T> &B = *reinterpret_cast<Basis<T> *>(smem_raw);
   T *S0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Basis<T>) + 15) / 16) * 16);
@@ -908,7 +909,19 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     __syncthreads();
   }
   // ================= store =================
-  if (NOUT == 1) {
+  if (OP == OP_LAP && epi.mode != LAP_PLAIN) {
+    const size_t o = (size_t)c * n3;
+    for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+      const size_t i = o + t;
+      if (epi.mode == LAP_RESIDUAL) {
+        y[i] = epi.b[i] - r[t];
+      } else {
+        const T dn = (epi.first ? T(0) : epi.c1 * epi.d[i]) + epi.c2 * epi.dinv[i] * (epi.b[i] - r[t]);
+        epi.d[i] = dn;
+        epi.xout[i] = u[i] + dn;
+      }
+    }
+  } else if (NOUT == 1) {
     T *yc = y + (size_t)c * n3;
     for (int t = threadIdx.x; t < n3; t += blockDim.x) yc[t] = r[t];
   } else {
@@ -920,7 +933,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
 }
 
 template <typename T, int OP, int GEO>
-static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s) {
+static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const VecPlan L = vec_plan(OP, GEO == GEO_CURVED, m.n1, m.q[qset], m.q[QSET_WALL]);
   const size_t sm = ((sizeof(Basis<T>) + 15) / 16) * 16 + (size_t)L.total * sizeof(T);
@@ -936,30 +949,35 @@ static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream
   }
   note_launch();
   note_dofs((OP == OP_DIV || OP == OP_LAP) ? m.np : m.nu);
-  vector_op_kernel<T, OP, GEO><<<m.nc, 128, sm, s>>>(m, u, y);
+  LapEpi<T> e{};
+  e.mode = LAP_PLAIN;
+  if (epi) e = *epi;
+  vector_op_kernel<T, OP, GEO><<<m.nc, 128, sm, s>>>(m, u, y, e);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s) {
+cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
   if (m.geo == GEO_CURVED) {
     switch (op) {
-      case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s);
-      case OP_CONV: return launch_vec<T, OP_CONV, GEO_CURVED>(m, u, y, s);
-      case OP_VISC: return launch_vec<T, OP_VISC, GEO_CURVED>(m, u, y, s);
-      case OP_LAP: return launch_vec<T, OP_LAP, GEO_CURVED>(m, u, y, s);
+      case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s, nullptr);
+      case OP_CONV: return launch_vec<T, OP_CONV, GEO_CURVED>(m, u, y, s, nullptr);
+      case OP_VISC: return launch_vec<T, OP_VISC, GEO_CURVED>(m, u, y, s, nullptr);
+      case OP_LAP: return launch_vec<T, OP_LAP, GEO_CURVED>(m, u, y, s, epi);
     }
     return cudaErrorInvalidValue;
   }
   switch (op) {
-    case OP_DIV: return launch_vec<T, OP_DIV, GEO_BOX>(m, u, y, s);
-    case OP_CONV: return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s);
-    case OP_VISC: return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s);
+    case OP_DIV: return launch_vec<T, OP_DIV, GEO_BOX>(m, u, y, s, nullptr);
+    case OP_CONV: return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s, nullptr);
+    case OP_VISC: return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s, nullptr);
   }
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_vector_op<double>(int, const MeshView<double> &, const double *, double *, cudaStream_t);
-template cudaError_t launch_vector_op<float>(int, const MeshView<float> &, const float *, float *, cudaStream_t);
+template cudaError_t launch_vector_op<double>(int, const MeshView<double> &, const double *, double *, cudaStream_t,
+                                              const LapEpi<double> *);
+template cudaError_t launch_vector_op<float>(int, const MeshView<float> &, const float *, float *, cudaStream_t,
+                                             const LapEpi<float> *);
 
 }  // namespace dgw
