@@ -163,72 +163,175 @@ struct XferDims {
   const void *py;      // [cny][2][n*n] y-embeddings (graded rows split unevenly), when cf[1] == 2
 };
 
-template <typename T>
-__global__ void prolongate_add(const Basis<T> *Bg, XferDims X, const T *__restrict__ xc, T *__restrict__ xf) {
-  __shared__ T Pm[3][NMAX * NMAX];
-  __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX];
-  const Basis<T> &B = *Bg;
-  const int n = B.n1, n3 = n * n * n;
-  const int fc = blockIdx.x;
-  const int fi = fc % X.fnx, fj = (fc / X.fnx) % X.fny, fk = fc / (X.fnx * X.fny);
-  const int fidx[3] = {fi, fj, fk};
-  const int ci = fi / X.cf[0], cj = fj / X.cf[1], ck = fk / X.cf[2];
-  const int cc = ci + X.cnx * (cj + X.cny * ck);
+// Transfers with one CTA per coarse cell and all its children: the 1-D passes are shared
+// between the children (2n^4 + 4n^4 + 8n^4 FMAs for 8 children instead of 24n^4), every thread owns
+// whole lines, and n is a compile-time constant. Directions that are not coarsened (cf = 1) use the
+// identity.
+template <typename T, int K>
+__device__ __forceinline__ void load_xfer_matrices(const Basis<T> &B, const XferDims &X, int cj, T (*Pm)[2][(K + 1) * (K + 1)]) {
+  constexpr int n = K + 1, n2 = n * n;
   const T *py = static_cast<const T *>(X.py);
-  for (int d = 0; d < 3; ++d)
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const int i = t / n, j = t % n;
-      T v = i == j ? T(1) : T(0);
-      if (X.cf[d] == 2) v = d == 1 ? py[((size_t)cj * 2 + (fidx[1] & 1)) * n * n + t] : B.P[fidx[d] & 1][t];
-      Pm[d][t] = v;
+  for (int t = threadIdx.x; t < 3 * 2 * n2; t += blockDim.x) {
+    const int d = t / (2 * n2), o = (t / n2) % 2, e = t % n2;
+    T v = (e / n == e % n) ? T(1) : T(0);
+    if (X.cf[d] == 2) v = d == 1 ? py[((size_t)cj * 2 + o) * n2 + e] : B.P[o][e];
+    Pm[d][o][e] = v;
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) prolong_cell_kernel(const Basis<T> *Bg, XferDims X, const T *__restrict__ xc,
+                                                           T *__restrict__ xf) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  __shared__ T Pm[3][2][n2];
+  __shared__ T Xc[n3], A[2 * n3], Bm[4 * n3];
+  const int cc = blockIdx.x;
+  const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
+  const int c0 = X.cf[0], c1 = X.cf[1], c2 = X.cf[2];
+  load_xfer_matrices<T, K>(*Bg, X, cj, Pm);
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) Xc[t] = xc[(size_t)cc * n3 + t];
+  __syncthreads();
+  for (int it = threadIdx.x; it < c0 * n2; it += blockDim.x) {   // x: (ox, line y,z)
+    const int ox = it / n2, l = it - ox * n2;
+    T v[n];
+#pragma unroll
+    for (int b = 0; b < n; ++b) v[b] = Xc[n * l + b];
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < n; ++b) s += Pm[0][ox][a * n + b] * v[b];
+      A[ox * n3 + n * l + a] = s;
     }
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = xc[(size_t)cc * n3 + t];
+  }
   __syncthreads();
-  axis_pass(A, Bv, n, n, n, 0, Pm[0], n, n, false, false);
+  for (int it = threadIdx.x; it < c0 * c1 * n2; it += blockDim.x) {   // y: (ox, oy, line x,z)
+    const int o = it / n2, l = it - o * n2, ox = o % c0, oy = o / c0;
+    const int x = l % n, z = l / n;
+    T v[n];
+#pragma unroll
+    for (int b = 0; b < n; ++b) v[b] = A[ox * n3 + x + n * b + n2 * z];
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < n; ++b) s += Pm[1][oy][a * n + b] * v[b];
+      Bm[(ox * 2 + oy) * n3 + x + n * a + n2 * z] = s;
+    }
+  }
   __syncthreads();
-  axis_pass(Bv, A, n, n, n, 1, Pm[1], n, n, false, false);
+  for (int it = threadIdx.x; it < c0 * c1 * c2 * n2; it += blockDim.x) {   // z: (ox, oy, oz, line x,y)
+    const int o = it / n2, l = it - o * n2, ox = o % c0, oy = (o / c0) % c1, oz = o / (c0 * c1);
+    const int fc = (ci * c0 + ox) + X.fnx * ((cj * c1 + oy) + X.fny * (ck * c2 + oz));
+    T v[n];
+#pragma unroll
+    for (int b = 0; b < n; ++b) v[b] = Bm[(ox * 2 + oy) * n3 + l + n2 * b];
+    T *out = xf + (size_t)fc * n3 + l;
+#pragma unroll
+    for (int a = 0; a < n; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < n; ++b) s += Pm[2][oz][a * n + b] * v[b];
+      out[n2 * a] += s;
+    }
+  }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) restrict_cell_kernel(const Basis<T> *Bg, XferDims X, const T *__restrict__ rf,
+                                                            T *__restrict__ rc) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  __shared__ T Pm[3][2][n2];
+  __shared__ T Rf[8 * n3], Zs[4 * n3], Ys[2 * n3];
+  const int cc = blockIdx.x;
+  const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
+  const int c0 = X.cf[0], c1 = X.cf[1], c2 = X.cf[2];
+  load_xfer_matrices<T, K>(*Bg, X, cj, Pm);
+  const int nch = c0 * c1 * c2;
+  for (int t = threadIdx.x; t < nch * n3; t += blockDim.x) {
+    const int o = t / n3, e = t - o * n3, ox = o % c0, oy = (o / c0) % c1, oz = o / (c0 * c1);
+    const int fc = (ci * c0 + ox) + X.fnx * ((cj * c1 + oy) + X.fny * (ck * c2 + oz));
+    Rf[((ox * 2 + oy) * 2 + oz) * n3 + e] = rf[(size_t)fc * n3 + e];
+  }
   __syncthreads();
-  axis_pass(A, Bv, n, n, n, 2, Pm[2], n, n, false, false);
+  for (int it = threadIdx.x; it < c0 * c1 * n2; it += blockDim.x) {   // z (summed over oz): (ox, oy, line x,y)
+    const int o = it / n2, l = it - o * n2, ox = o % c0, oy = o / c0;
+    T acc[n];
+#pragma unroll
+    for (int a = 0; a < n; ++a) acc[a] = T(0);
+    for (int oz = 0; oz < c2; ++oz) {
+      T v[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) v[b] = Rf[((ox * 2 + oy) * 2 + oz) * n3 + l + n2 * b];
+#pragma unroll
+      for (int a = 0; a < n; ++a)
+#pragma unroll
+        for (int b = 0; b < n; ++b) acc[a] += Pm[2][oz][b * n + a] * v[b];
+    }
+#pragma unroll
+    for (int a = 0; a < n; ++a) Zs[(ox * 2 + oy) * n3 + l + n2 * a] = acc[a];
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) xf[(size_t)fc * n3 + t] += Bv[t];
+  for (int it = threadIdx.x; it < c0 * n2; it += blockDim.x) {   // y (summed over oy): (ox, line x,z)
+    const int ox = it / n2, l = it - ox * n2, x = l % n, z = l / n;
+    T acc[n];
+#pragma unroll
+    for (int a = 0; a < n; ++a) acc[a] = T(0);
+    for (int oy = 0; oy < c1; ++oy) {
+      T v[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) v[b] = Zs[(ox * 2 + oy) * n3 + x + n * b + n2 * z];
+#pragma unroll
+      for (int a = 0; a < n; ++a)
+#pragma unroll
+        for (int b = 0; b < n; ++b) acc[a] += Pm[1][oy][b * n + a] * v[b];
+    }
+#pragma unroll
+    for (int a = 0; a < n; ++a) Ys[ox * n3 + x + n * a + n2 * z] = acc[a];
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < n2; l += blockDim.x) {   // x (summed over ox): line y,z
+    T acc[n];
+#pragma unroll
+    for (int a = 0; a < n; ++a) acc[a] = T(0);
+    for (int ox = 0; ox < c0; ++ox) {
+      T v[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) v[b] = Ys[ox * n3 + n * l + b];
+#pragma unroll
+      for (int a = 0; a < n; ++a)
+#pragma unroll
+        for (int b = 0; b < n; ++b) acc[a] += Pm[0][ox][b * n + a] * v[b];
+    }
+#pragma unroll
+    for (int a = 0; a < n; ++a) rc[(size_t)cc * n3 + n * l + a] = acc[a];
+  }
 }
 
 template <typename T>
-__global__ void restrict_kernel(const Basis<T> *Bg, XferDims X, const T *__restrict__ rf, T *__restrict__ rc) {
-  __shared__ T Pm[2][3][NMAX * NMAX];
-  __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX], Acc[NMAX * NMAX * NMAX];
-  const Basis<T> &B = *Bg;
-  const int n = B.n1, n3 = n * n * n;
-  const int cc = blockIdx.x;
-  const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
-  const T *py = static_cast<const T *>(X.py);
-  for (int o = 0; o < 2; ++o)
-    for (int d = 0; d < 3; ++d)
-      for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-        const int i = t / n, j = t % n;
-        T v = i == j ? T(1) : T(0);
-        if (X.cf[d] == 2) v = d == 1 ? py[((size_t)cj * 2 + o) * n * n + t] : B.P[o][t];
-        Pm[o][d][t] = v;
-      }
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) Acc[t] = T(0);
-  __syncthreads();
-  for (int oz = 0; oz < X.cf[2]; ++oz)
-    for (int oy = 0; oy < X.cf[1]; ++oy)
-      for (int ox = 0; ox < X.cf[0]; ++ox) {
-        const int fi = ci * X.cf[0] + ox, fj = cj * X.cf[1] + oy, fk = ck * X.cf[2] + oz;
-        const int fc = fi + X.fnx * (fj + X.fny * fk);
-        for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = rf[(size_t)fc * n3 + t];
-        __syncthreads();
-        axis_pass(A, Bv, n, n, n, 0, Pm[ox][0], n, n, true, false);
-        __syncthreads();
-        axis_pass(Bv, A, n, n, n, 1, Pm[oy][1], n, n, true, false);
-        __syncthreads();
-        axis_pass(A, Bv, n, n, n, 2, Pm[oz][2], n, n, true, false);
-        __syncthreads();
-        for (int t = threadIdx.x; t < n3; t += blockDim.x) Acc[t] += Bv[t];
-        __syncthreads();
-      }
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) rc[(size_t)cc * n3 + t] = Acc[t];
+static void launch_restrict(const Basis<T> *B, const XferDims &X, int n, const T *rf, T *rc, int ncoarse,
+                            cudaStream_t s) {
+  note_launch();
+  switch (n) {
+    case 2: restrict_cell_kernel<T, 1><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
+    case 3: restrict_cell_kernel<T, 2><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
+    case 4: restrict_cell_kernel<T, 3><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
+    case 5: restrict_cell_kernel<T, 4><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
+    default: restrict_cell_kernel<T, 5><<<ncoarse, 160, 0, s>>>(B, X, rf, rc); break;
+  }
+}
+
+template <typename T>
+static void launch_prolong(const Basis<T> *B, const XferDims &X, int n, const T *xc, T *xf, int ncoarse,
+                           cudaStream_t s) {
+  note_launch();
+  switch (n) {
+    case 2: prolong_cell_kernel<T, 1><<<ncoarse, 64, 0, s>>>(B, X, xc, xf); break;
+    case 3: prolong_cell_kernel<T, 2><<<ncoarse, 96, 0, s>>>(B, X, xc, xf); break;
+    case 4: prolong_cell_kernel<T, 3><<<ncoarse, 128, 0, s>>>(B, X, xc, xf); break;
+    case 5: prolong_cell_kernel<T, 4><<<ncoarse, 224, 0, s>>>(B, X, xc, xf); break;
+    default: prolong_cell_kernel<T, 5><<<ncoarse, 256, 0, s>>>(B, X, xc, xf); break;
+  }
 }
 
 // p-transfer between Q_k and Q_1 on the same cells: P1[i*2 + j] = linear Lagrange j at the
@@ -790,11 +893,11 @@ static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
   launch_laplace_epi<T>(L->view, L->x, L->r, res, s);   // r = b - A x
   note_launch();
   if (L->p1) p_restrict<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, L->r, C->b);
-  else restrict_kernel<T><<<C->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, L->r, C->b);
+  else launch_restrict<T>(H->basis, L->to_coarse, L->view.n1, L->r, C->b, C->view.nc, s);
   vcycle(H, lev + 1, s);
   note_launch();
   if (L->p1) p_prolongate_add<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, C->x, L->x);
-  else prolongate_add<T><<<L->view.nc, 64, 0, s>>>(H->basis, L->to_coarse, C->x, L->x);
+  else launch_prolong<T>(H->basis, L->to_coarse, L->view.n1, C->x, L->x, C->view.nc, s);
   chebyshev(H, L, false, s);
 }
 
@@ -802,6 +905,7 @@ cudaError_t mg_setup(dgw_mesh *M, dgw_solver *S, int mode, int cheb, cudaStream_
   if (S->mg_ready && S->mg_mode == mode && S->mg_cheb == cheb) return cudaSuccess;
   mg_free(S);
   if (S->vgraph) { cudaGraphExecDestroy(S->vgraph); S->vgraph = nullptr; }
+  if (S->vgraph32) { cudaGraphExecDestroy(S->vgraph32); S->vgraph32 = nullptr; }
   MGLevel *ml = new MGLevel();
   cudaError_t e;
   if (mode == 1) {
@@ -848,6 +952,22 @@ cudaError_t mg_vcycle(dgw_mesh *M, dgw_solver *S, int mode, const double *r, dou
     note_launch();
     scale_out<double><<<G, 256, 0, s>>>(z, H->L[0]->x, n, S->sc, SC_RR);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t mg_level0_f32(dgw_solver *S, float **b0, float **x0) {
+  MGLevel *ml = S->levels.empty() ? nullptr : S->levels[0];
+  if (!ml || ml->prec != 1) return cudaErrorNotReady;
+  auto *H = (Hierarchy<float> *)ml->h;
+  *b0 = H->L[0]->b;
+  *x0 = H->L[0]->x;
+  return cudaSuccess;
+}
+
+cudaError_t mg_vcycle_f32(dgw_solver *S, cudaStream_t s) {
+  MGLevel *ml = S->levels.empty() ? nullptr : S->levels[0];
+  if (!ml || ml->prec != 1) return cudaErrorNotReady;
+  vcycle((Hierarchy<float> *)ml->h, 0, s);
   return cudaGetLastError();
 }
 

@@ -94,6 +94,58 @@ __global__ void axpby_kernel(double *__restrict__ y, const double *__restrict__ 
     y[i] = a * x[i] + b * y[i];
 }
 
+// ---- FP32 vectors of the mixed-precision inner solve (reductions accumulate in FP64)
+
+// partial[blockIdx] = sum_i a_i b_i (b == nullptr: sum_i a_i), FP32 inputs
+__global__ void dot32_partial_kernel(const float *__restrict__ a, const float *__restrict__ b, long n,
+                                     double *__restrict__ partial) {
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += b ? (double)a[i] * (double)b[i] : (double)a[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// r32 = r / sqrt(sc[slot]) (the outer residual normalised to unit 2-norm)
+__global__ void to_unit32_kernel(float *__restrict__ r32, const double *__restrict__ r, long n, const double *sc,
+                                 int slot) {
+  const double s = 1.0 / sqrt(sc[slot]);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    r32[i] = (float)(r[i] * s);
+}
+
+// e += alpha d; r -= alpha q with alpha = sc[RZ] / sc[DQ]
+__global__ void pcg32_update_kernel(float *__restrict__ e, float *__restrict__ r, const float *__restrict__ d,
+                                    const float *__restrict__ q, long n, const double *sc) {
+  const float alpha = (float)(sc[SC_RZ] / sc[SC_DQ]);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    e[i] += alpha * d[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// d = z (first) or z + beta d, flexible beta = (r.z - r.z_old) / rz_old
+__global__ void pcg32_direction_kernel(float *__restrict__ d, const float *__restrict__ z, long n, const double *sc,
+                                       int first) {
+  const float beta = first ? 0.0f : (float)((sc[SC_RZNEW] - sc[SC_RZOLD]) / sc[SC_RZ]);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    d[i] = first ? z[i] : z[i] + beta * d[i];
+}
+
+// x -= mean(x), the sum of x in sc[slot]
+__global__ void sub_mean32_kernel(float *__restrict__ x, long n, const double *sc, int slot) {
+  const float m = (float)(sc[slot] / (double)n);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) x[i] -= m;
+}
+
+// p += sqrt(sc[slot]) e: the correction of the unit right-hand side scaled back
+__global__ void accumulate64_kernel(double *__restrict__ p, const float *__restrict__ e, long n, const double *sc,
+                                    int slot) {
+  const double s = sqrt(sc[slot]);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] += s * (double)e[i];
+}
+
 static inline int grid_for(long n) {
   long g = (n + 255) / 256;
   return (int)std::min<long>(std::max<long>(g, 1), 152 * 16);
@@ -103,6 +155,15 @@ cudaError_t reduce_to(const double *a, const double *b, long n, double *partial,
                       cudaStream_t s) {
   note_launch();
   dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, partial);
+  note_launch();
+  dot_finish_kernel<<<1, 32, 0, s>>>(partial, RED_BLOCKS, sc, slot);
+  return cudaGetLastError();
+}
+
+static cudaError_t reduce32_to(const float *a, const float *b, long n, double *partial, double *sc, int slot,
+                               cudaStream_t s) {
+  note_launch();
+  dot32_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, partial);
   note_launch();
   dot_finish_kernel<<<1, 32, 0, s>>>(partial, RED_BLOCKS, sc, slot);
   return cudaGetLastError();
@@ -167,6 +228,116 @@ static cudaError_t vcycle_graph(dgw_mesh *M, dgw_solver *S, int mode, cudaStream
   return e;
 }
 
+// One FP32 V-cycle on the finest level's buffers (r32 -> z32) followed by the projection of z32 onto
+// zero mean, as a CUDA graph captured on first use per hierarchy and replayed every inner iteration.
+static cudaError_t vcycle32_graph(dgw_mesh *M, dgw_solver *S, float *z32, cudaStream_t s) {
+  const long n = M->np;
+  const int G = grid_for(n);
+  if (!S->vgraph32) {
+    const unsigned long long l0 = launch_counter(), d0 = dof_counter();
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t ev = mg_vcycle_f32(S, s);
+    if (ev == cudaSuccess) ev = reduce32_to(z32, nullptr, n, S->partial, S->sc, SC_TMP, s);
+    if (ev == cudaSuccess) {
+      note_launch();
+      sub_mean32_kernel<<<G, 256, 0, s>>>(z32, n, S->sc, SC_TMP);
+      ev = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (ev != cudaSuccess) e = ev;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->vgraph32, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) { S->vgraph32 = nullptr; return e; }
+    // the capture counted the launches and DoFs of one replay: they stand for the launch below, and
+    // every later replay adds them again
+    S->vgraph32_launches = launch_counter() - l0;
+    S->vgraph32_dofs = dof_counter() - d0;
+    return cudaGraphLaunch(S->vgraph32, s);
+  }
+  note_launches(S->vgraph32_launches);
+  note_dofs((long long)S->vgraph32_dofs);
+  return cudaGraphLaunch(S->vgraph32, s);
+}
+
+// Mixed precision (mode 1): FP64 iterative refinement around an FP32 preconditioned CG. The outer
+// loop keeps p, the residual r = b - A p and its norm in FP64 (one FP64 operator apply per outer
+// step); each inner solve takes the residual scaled to unit norm, runs flexible CG with the FP32
+// operator and the FP32 multigrid V-cycle (dot products accumulated in FP64) until the unit
+// residual drops below max(1e-4, rtol ||b|| / (2 ||r||)), and the scaled correction is added to p.
+static dgw_status pressure_solve_mixed(dgw_mesh *M, dgw_solver *S, const dgw_solve_opts *o, double *p, double bnorm,
+                                       int *iterations, cudaStream_t s) {
+  const long n = M->np;
+  const int G = grid_for(n);
+  float *r32 = nullptr, *z32 = nullptr;
+  cudaError_t e = mg_level0_f32(S, &r32, &z32);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: mixed hierarchy");
+  if (!S->d32) {
+    float **v32[] = {&S->d32, &S->q32, &S->e32, &S->zold32};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+      e = cudaMalloc(v32[i], n * sizeof(float));
+      if (e == cudaSuccess) e = cudaMemsetAsync(*v32[i], 0, n * sizeof(float), s);
+    }
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: mixed workspace");
+  }
+  constexpr double kInnerTol = 1e-4;   // reduction per inner solve; FP32 rounding allows about 1e-6
+  int it = 0;
+  for (;;) {
+    // S->r holds the FP64 residual of p; its squared norm goes to SC_RN
+    reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RN, s);
+    cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
+    const double rn = std::sqrt(std::max(S->host_sc[SC_RN], 0.0));
+    if (rn <= o->rtol * bnorm) break;
+    if (it >= o->max_iter) { *iterations = it; return DGW_ENOTCONV; }
+    const double tol_in = std::max(kInnerTol, 0.5 * o->rtol * bnorm / rn);
+    note_launch();
+    to_unit32_kernel<<<G, 256, 0, s>>>(r32, S->r, n, S->sc, SC_RN);
+    cudaMemsetAsync(S->e32, 0, n * sizeof(float), s);
+    e = vcycle32_graph(M, S, z32, s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
+    reduce32_to(r32, z32, n, S->partial, S->sc, SC_RZNEW, s);
+    note_launch();
+    pcg32_direction_kernel<<<G, 256, 0, s>>>(S->d32, z32, n, S->sc, 1);
+    note_launch();
+    copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
+    for (;;) {
+      e = launch_laplace<float>(M->v32, S->d32, S->q32, s);
+      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
+      reduce32_to(S->d32, S->q32, n, S->partial, S->sc, SC_DQ, s);
+      note_launch();
+      pcg32_update_kernel<<<G, 256, 0, s>>>(S->e32, r32, S->d32, S->q32, n, S->sc);
+      reduce32_to(r32, r32, n, S->partial, S->sc, SC_RR, s);
+      cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
+      ++it;
+      if (std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) <= tol_in || it >= o->max_iter) break;
+      cudaMemcpyAsync(S->zold32, z32, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+      e = vcycle32_graph(M, S, z32, s);
+      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
+      reduce32_to(r32, z32, n, S->partial, S->sc, SC_RZNEW, s);
+      reduce32_to(r32, S->zold32, n, S->partial, S->sc, SC_RZOLD, s);
+      note_launch();
+      pcg32_direction_kernel<<<G, 256, 0, s>>>(S->d32, z32, n, S->sc, 0);
+      note_launch();
+      copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
+    }
+    // p += ||r|| e; r = b - A p in FP64
+    note_launch();
+    accumulate64_kernel<<<G, 256, 0, s>>>(p, S->e32, n, S->sc, SC_RN);
+    e = launch_laplace<double>(M->v64, p, S->q, s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
+    cudaMemcpyAsync(S->r, S->b, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    note_launch();
+    axpby_kernel<<<G, 256, 0, s>>>(S->r, S->q, -1.0, 1.0, n);
+  }
+  *iterations = it;
+  return DGW_OK;
+}
+
 dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_solve_opts *o, dgw_solve_info *info,
                           cudaStream_t cs) {
   dgw_solver *S = get_solver(M);
@@ -198,52 +369,61 @@ dgw_status pressure_solve(dgw_mesh *M, const double *b_in, double *p, const dgw_
     info->dof_applies = 0.0;
     return DGW_OK;
   }
+  if (o->mode == 1) {
+    e = mg_setup(M, S, 1, o->cheb_degree > 0 ? o->cheb_degree : 5, s);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: multigrid setup");
+    st = pressure_solve_mixed(M, S, o, p, bnorm, &it, s);
+    if (st != DGW_OK && st != DGW_ENOTCONV) return st;
+  }
   auto precondition = [&](const double *r, double *z) -> cudaError_t {
     if (o->mode == 2 || !S->mg_ready) {
       note_launch();
       jacobi_kernel<<<G, 256, 0, s>>>(r, M->diag64, z, n);
     } else {
-      cudaError_t ee = mg_vcycle(M, S, o->mode, r, z, s);
+      // the CG always preconditions S->r into S->z: the captured V-cycle reads and writes exactly those
+      cudaError_t ee = (r == S->r && z == S->z) ? vcycle_graph(M, S, o->mode, s) : mg_vcycle(M, S, o->mode, r, z, s);
       if (ee != cudaSuccess) return ee;
     }
     return project_mean(z, z, n, S->partial, S->sc, SC_TMP, s);
   };
-  if (o->mode != 2) {
+  if (o->mode == 0) {
     e = mg_setup(M, S, o->mode, o->cheb_degree > 0 ? o->cheb_degree : 5, s);
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: multigrid setup");
   }
-  note_launch();
-  copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RR, SC_BB);   // r = b: the preconditioner scales by rms(r)
-  e = precondition(S->r, S->z);
-  if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
-  reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
-  note_launch();
-  cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 1);
-  note_launch();
-  copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
-  for (it = 1; it <= o->max_iter; ++it) {
-    e = launch_laplace<double>(M->v64, S->d, S->q, s);
-    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
-    reduce_to(S->d, S->q, n, S->partial, S->sc, SC_DQ, s);
+  if (o->mode != 1) {
     note_launch();
-    cg_update_kernel<<<G, 256, 0, s>>>(p, S->r, S->d, S->q, n, S->sc);
-    reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RR, s);
-    cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
-    rel = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
-    if (rel <= o->rtol) break;
-    cudaMemcpyAsync(S->zold, S->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RR, SC_BB);   // r = b: the preconditioner scales by rms(r)
     e = precondition(S->r, S->z);
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
     reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
-    reduce_to(S->r, S->zold, n, S->partial, S->sc, SC_RZOLD, s);
     note_launch();
-    cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 0);
+    cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 1);
     note_launch();
     copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
+    for (it = 1; it <= o->max_iter; ++it) {
+      e = launch_laplace<double>(M->v64, S->d, S->q, s);
+      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
+      reduce_to(S->d, S->q, n, S->partial, S->sc, SC_DQ, s);
+      note_launch();
+      cg_update_kernel<<<G, 256, 0, s>>>(p, S->r, S->d, S->q, n, S->sc);
+      reduce_to(S->r, S->r, n, S->partial, S->sc, SC_RR, s);
+      cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
+      rel = std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) / bnorm;
+      if (rel <= o->rtol) break;
+      cudaMemcpyAsync(S->zold, S->z, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      e = precondition(S->r, S->z);
+      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
+      reduce_to(S->r, S->z, n, S->partial, S->sc, SC_RZNEW, s);
+      reduce_to(S->r, S->zold, n, S->partial, S->sc, SC_RZOLD, s);
+      note_launch();
+      cg_direction_kernel<<<G, 256, 0, s>>>(S->d, S->z, n, S->sc, 0);
+      note_launch();
+      copy_scalar_kernel<<<1, 1, 0, s>>>(S->sc, SC_RZ, SC_RZNEW);
+    }
+    if (it > o->max_iter) { it = o->max_iter; st = DGW_ENOTCONV; }
   }
-  if (it > o->max_iter) { it = o->max_iter; st = DGW_ENOTCONV; }
   // p <- p - mean(p); true residual in FP64
   project_mean(p, p, n, S->partial, S->sc, SC_TMP, s);
   launch_laplace<double>(M->v64, p, S->q, s);
@@ -275,6 +455,8 @@ void dgw_solver_free(dgw_mesh *M) {
   dgw::mg_free(S);
   cudaFree(S->b); cudaFree(S->r); cudaFree(S->z); cudaFree(S->d); cudaFree(S->q); cudaFree(S->zold);
   cudaFree(S->partial); cudaFree(S->sc);
+  cudaFree(S->d32); cudaFree(S->q32); cudaFree(S->e32); cudaFree(S->zold32);
+  if (S->vgraph32) cudaGraphExecDestroy(S->vgraph32);
   if (S->host_sc) cudaFreeHost(S->host_sc);
   if (S->ev0) cudaEventDestroy(S->ev0);
   if (S->ev1) cudaEventDestroy(S->ev1);
