@@ -3,8 +3,9 @@
 
 One step = one pass of the whole hot path over the workload: eddy-viscosity update of the
 enriched cells, FP64 applies of the SIPG Laplacian, the velocity divergence, the convective and
-the viscous operator, and one pressure Poisson solve to a 1e-10 relative residual (FP64 CG with
-the FP32 multigrid preconditioner) whose right-hand side is the step's divergence.
+the viscous operator, and one pressure Poisson solve to a 1e-10 relative residual (mixed precision:
+FP64 iterative refinement around FP32 CG with the FP32 multigrid preconditioner) whose right-hand
+side is the step's divergence.
 
 value = operator DoF applications of the step (output DoFs of every operator apply, including the
 applies inside the solve) / step time, in GDoF/s. Per-operator GDoF/s and FP64-vs-mixed solves/s

@@ -125,14 +125,16 @@ dgw_status dgw_apply_viscous(dgw_mesh_t mesh, int prec, const void *u, void *y, 
 
 typedef struct {
   double rtol;        /* relative residual ||b - A p||_2 / ||b||_2 target (e.g. 1e-10) */
-  int max_iter;       /* outer CG iteration limit */
-  int mode;           /* 0: FP64 CG + FP64 multigrid, 1: FP64 CG + FP32 multigrid (mixed),
-                         2: FP64 CG + Jacobi */
+  int max_iter;       /* limit on CG iterations (mode 1: inner iterations summed over refinement steps) */
+  int mode;           /* 0: FP64 CG + FP64 multigrid; 1 (mixed): FP64 iterative refinement (p, b - A p
+                         and its norm in FP64) around FP32 CG + FP32 multigrid, each inner solve
+                         reducing the unit-scaled residual by 1e-4 or to what the target still needs,
+                         dot products accumulated in FP64; 2: FP64 CG + Jacobi */
   int cheb_degree;    /* Chebyshev smoother degree (e.g. 5) */
 } dgw_solve_opts;
 
 typedef struct {
-  int iterations;
+  int iterations;      /* CG iterations (mode 1: inner FP32 iterations, all refinement steps) */
   double rel_residual; /* true residual of the returned p, recomputed in FP64 */
   float ms;            /* device time of the solve */
   double dof_applies;  /* operator DoF applications inside the solve (all levels, both precisions) */
