@@ -218,7 +218,9 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   return p;
 }
 
-template <typename T, int OP, int GEO>
+// NC > 0: the node count per direction as a compile-time constant (the curved Laplacian, whose point
+// sets are all k+1 Gauss points, is instantiated per degree so the pass index arithmetic folds).
+template <typename T, int OP, int GEO, int NC = 0>
 __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y,
                                                         LapEpi<T> epi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -229,10 +231,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   constexpr bool GRAD = OP == OP_VISC || OP == OP_LAP;
   constexpr int NIN = OP == OP_LAP ? 1 : 3;                             // input components
   constexpr int NOUT = (OP == OP_DIV || OP == OP_LAP) ? 1 : 3;          // output components
-  const int n = m.n1, nn = n * n;
+  const int n = NC > 0 ? NC : m.n1, nn = n * n;
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const int opc = OP == OP_CONV ? 1 : 0;   // wall-table class
-  const VecPlan L = vec_plan(OP, CURVED, n, m.q[qset], m.q[QSET_WALL]);
+  const VecPlan L = vec_plan(OP, CURVED, n, NC > 0 ? NC : m.q[qset], NC > 0 ? NC : m.q[QSET_WALL]);
   const int n3 = L.n3;
   T *uo = S0 + L.uo, *r = S0 + L.r, *eo = S0 + L.eo, *re = S0 + L.re, *un = S0 + L.fUn, *en = S0 + L.en;
   const int c = blockIdx.x;
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   if (!CURVED) { h[0] = m.hx; h[1] = m.hy[(c / m.nx) % m.ny]; h[2] = m.hz; }
   const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
   const int sets[3] = {qset, enr_c ? QSET_WALL : qset, qset};
-  const int q0 = B.q[sets[0]], q1 = B.q[sets[1]], q2 = B.q[sets[2]];
+  const int q0 = NC > 0 ? NC : B.q[sets[0]], q1 = NC > 0 ? NC : B.q[sets[1]], q2 = NC > 0 ? NC : B.q[sets[2]];
   const int P = q0 * q1 * q2;
   const T vol = h[0] * h[1] * h[2];
   const T *wtv = enr_c ? m.wt_vol[opc] + (size_t)ec * m.nvol[opc] * WT : nullptr;
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     const bool enr_any = enr_c || enr_o[0] || enr_o[1];
     const int s1 = (t1 == 1 && enr_any) ? QSET_WALL : qset;
     const int s2 = (t2 == 1 && enr_any) ? QSET_WALL : qset;
-    const int p1 = B.q[s1], p2 = B.q[s2], FP = p1 * p2;
+    const int p1 = NC > 0 ? NC : B.q[s1], p2 = NC > 0 ? NC : B.q[s2], FP = p1 * p2;
     for (int t = threadIdx.x; t < 2 * NIN * n3; t += blockDim.x) {
       const int s = t / (NIN * n3), e = t - s * NIN * n3;
       un[t] = nbr[s] >= 0 ? u[(size_t)nbr[s] * NIN * n3 + e] : T(0);
@@ -932,7 +934,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   }
 }
 
-template <typename T, int OP, int GEO>
+template <typename T, int OP, int GEO, int NC = 0>
 static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const VecPlan L = vec_plan(OP, GEO == GEO_CURVED, m.n1, m.q[qset], m.q[QSET_WALL]);
@@ -940,10 +942,10 @@ static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream
   if (sm > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(vector_op_kernel<T, OP, GEO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(vector_op_kernel<T, OP, GEO, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          220 * 1024);
     if (e == cudaSuccess)   // the whole unified L1/shared array as shared memory: more CTAs per SM
-      e = cudaFuncSetAttribute(vector_op_kernel<T, OP, GEO>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      e = cudaFuncSetAttribute(vector_op_kernel<T, OP, GEO, NC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -952,7 +954,7 @@ static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream
   LapEpi<T> e{};
   e.mode = LAP_PLAIN;
   if (epi) e = *epi;
-  vector_op_kernel<T, OP, GEO><<<m.nc, 128, sm, s>>>(m, u, y, e);
+  vector_op_kernel<T, OP, GEO, NC><<<m.nc, 128, sm, s>>>(m, u, y, e);
   return cudaGetLastError();
 }
 
@@ -963,7 +965,15 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
       case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_CONV: return launch_vec<T, OP_CONV, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_VISC: return launch_vec<T, OP_VISC, GEO_CURVED>(m, u, y, s, nullptr);
-      case OP_LAP: return launch_vec<T, OP_LAP, GEO_CURVED>(m, u, y, s, epi);
+      case OP_LAP:
+        switch (m.n1) {
+          case 2: return launch_vec<T, OP_LAP, GEO_CURVED, 2>(m, u, y, s, epi);
+          case 3: return launch_vec<T, OP_LAP, GEO_CURVED, 3>(m, u, y, s, epi);
+          case 4: return launch_vec<T, OP_LAP, GEO_CURVED, 4>(m, u, y, s, epi);
+          case 5: return launch_vec<T, OP_LAP, GEO_CURVED, 5>(m, u, y, s, epi);
+          case 6: return launch_vec<T, OP_LAP, GEO_CURVED, 6>(m, u, y, s, epi);
+        }
+        return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
   }
