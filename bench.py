@@ -318,8 +318,8 @@ def run_gpu(args):
     achieved_tf = nc * fl_cell / (lap_ms * 1e-3) / 1e12
     kname32 = "vector_op_kernel<float,OP_LAP,GEO_CURVED>" if curved else f"laplace_box_kernel<float,{k}>"
     kname64 = "vector_op_kernel<double,OP_LAP,GEO_CURVED>" if curved else f"laplace_box_kernel<double,{k}>"
-    if curved:
-        args.traffic_bytes = None   # the ncu capture of record covers the box kernel
+    if w.name != DEFAULT_WORKLOAD:
+        args.traffic_bytes = None   # the ncu capture of record covers the Q4 box kernel of the default workload
     roofline = {"kernel": kname32, "bound": "hbm", "achieved": achieved32,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved32 / peaks["hbm_gbs"],
                 "traffic": args.traffic_bytes, "algorithmic_bytes_per_launch": 8.0 * m.n_p,

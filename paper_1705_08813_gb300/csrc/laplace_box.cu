@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_k
       const int d = f >> 1, side = f & 1, nb = nbr[cl * 6 + f];
       T val = T(0), der = T(0);
       if (nb >= 0) {
-        const T *pn = p + (size_t)nb * n3;
+        // x-neighbours inside this CTA's row segment are already in shared memory
+        const T *pn = (nb >= c0 && nb < c0 + cpb) ? U + (nb - c0) * n3 : p + (size_t)nb * n3;
         // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
         const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
         const int base = d == 0 ? n * l : (d == 1 ? lr + n2 * lq : l);

@@ -19,7 +19,8 @@ namespace dgw {
 constexpr double kSmoothRange = 15.0;   // Chebyshev smooths [1.2 lmax/15, 1.2 lmax]
 constexpr int kCoarseIters = 24;       // PCG steps on the coarsest level
 constexpr int kLanczos = 24;           // CG-Lanczos steps for lmax(D^-1 A)
-constexpr long kDenseMax = 1000;       // coarsest systems up to this size are solved densely
+constexpr long kDenseMax = 2400;       // coarsest systems up to this size are solved densely (the
+                                       // hierarchy stops coarsening once Q_1 on its cells fits)
 
 // ------------------------------------------------------------------------------------------
 // vector kernels (templated on the level precision; reductions accumulate in double)
@@ -380,43 +381,6 @@ __global__ void dense_gemv(const T *__restrict__ Ainv, const T *__restrict__ b, 
   if (lane == 0) x[warp] = (T)s;
 }
 
-// Inverse of A + c 1 1^T (SPD when the null space of A is the constants; on zero-mean right-hand
-// sides it acts as the pseudo-inverse of A and returns zero-mean solutions). Cholesky, in place.
-static bool dense_regularised_inverse(std::vector<double> &A, int N) {
-  double tr = 0.0;
-  for (int i = 0; i < N; ++i) tr += A[(size_t)i * N + i];
-  const double c = tr / N;
-  for (size_t i = 0; i < (size_t)N * N; ++i) A[i] += c / N;
-  std::vector<double> Lf(A);
-  for (int j = 0; j < N; ++j) {
-    double d = Lf[(size_t)j * N + j];
-    for (int k = 0; k < j; ++k) d -= Lf[(size_t)j * N + k] * Lf[(size_t)j * N + k];
-    if (!(d > 0.0)) return false;
-    d = std::sqrt(d);
-    Lf[(size_t)j * N + j] = d;
-    for (int i = j + 1; i < N; ++i) {
-      double v = Lf[(size_t)i * N + j];
-      for (int k = 0; k < j; ++k) v -= Lf[(size_t)i * N + k] * Lf[(size_t)j * N + k];
-      Lf[(size_t)i * N + j] = v / d;
-    }
-  }
-  // inverse column by column: L L^T x = e_col
-  std::vector<double> col(N);
-  for (int cidx = 0; cidx < N; ++cidx) {
-    for (int i = 0; i < N; ++i) {
-      double v = i == cidx ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) v -= Lf[(size_t)i * N + k] * col[k];
-      col[i] = v / Lf[(size_t)i * N + i];
-    }
-    for (int i = N - 1; i >= 0; --i) {
-      double v = col[i];
-      for (int k = i + 1; k < N; ++k) v -= Lf[(size_t)k * N + i] * col[k];
-      col[i] = v / Lf[(size_t)i * N + i];
-    }
-    for (int i = 0; i < N; ++i) A[(size_t)i * N + cidx] = col[i];
-  }
-  return true;
-}
 
 // ------------------------------------------------------------------------------------------
 // hierarchy
@@ -463,6 +427,82 @@ static T *lalloc(Lvl<T> *L, size_t n, cudaError_t &e, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(T), s);
   if (e == cudaSuccess) L->allocs.push_back(p);
   return (T *)p;
+}
+
+// Gauss-Jordan inversion in place on the device (FP64, no pivoting: the matrices inverted here are
+// symmetric positive definite, whose pivots stay positive). Step k saves the scaled pivot row R and
+// the pivot column C, then updates every entry: A_ij -= C_i R_j (A_ik -> -C_i / p, row k -> R).
+__global__ void gj_pivot_kernel(const double *__restrict__ A, int N, int k, double *__restrict__ R,
+                                double *__restrict__ Cc) {
+  const double p = A[(size_t)k * N + k];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+    R[j] = j == k ? 1.0 / p : A[(size_t)k * N + j] / p;
+    Cc[j] = A[(size_t)j * N + k];
+  }
+}
+
+__global__ void gj_update_kernel(double *__restrict__ A, int N, int k, const double *__restrict__ R,
+                                 const double *__restrict__ Cc) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double *a = A + (size_t)i * N + j;
+  if (i == k) *a = R[j];
+  else *a = (j == k ? 0.0 : *a) - Cc[i] * R[j];
+}
+
+template <typename T>
+__global__ void narrow_kernel(const double *__restrict__ a, T *__restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+
+// Inverse of A + c 1 1^T (SPD when the null space of A is the constants; on zero-mean right-hand
+// sides it acts as the pseudo-inverse of A and returns zero-mean solutions), c 1 1^T adding
+// trace(A)/N^2 to every entry. Computed on the device into out (N x N, type T, allocated on the
+// level). Returns false, leaving out unset, if the inverse has a non-positive or non-finite
+// diagonal entry (the caller keeps the iterative coarse solve).
+template <typename T>
+static bool dense_inverse_device(Lvl<T> *D, std::vector<double> A, int N, T **out, cudaError_t &e, cudaStream_t s) {
+  double tr = 0.0;
+  for (int i = 0; i < N; ++i) tr += A[(size_t)i * N + i];
+  const double c = tr / N;
+  for (size_t i = 0; i < (size_t)N * N; ++i) A[i] += c / N;
+  double *Ad = nullptr, *R = nullptr, *Cc = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&Ad, (size_t)N * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&R, (size_t)N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Cc, (size_t)N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Ad, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // A's staging copy may go now
+  const dim3 ug((N + 255) / 256, N);
+  for (int k = 0; k < N && e == cudaSuccess; ++k) {
+    gj_pivot_kernel<<<(N + 255) / 256, 256, 0, s>>>(Ad, N, k, R, Cc);
+    gj_update_kernel<<<ug, 256, 0, s>>>(Ad, N, k, R, Cc);
+    if ((k & 255) == 255) e = cudaGetLastError();
+  }
+  note_launches(2ull * N);
+  bool ok = false;
+  if (e == cudaSuccess) {
+    std::vector<double> diag(N);
+    for (int i = 0; i < N && e == cudaSuccess; ++i)   // the inverse's diagonal must be positive and finite
+      e = cudaMemcpyAsync(&diag[i], Ad + (size_t)i * N + i, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    ok = e == cudaSuccess;
+    for (int i = 0; i < N && ok; ++i) ok = std::isfinite(diag[i]) && diag[i] > 0.0;
+  }
+  if (ok) {
+    T *o = lalloc<T>(D, (size_t)N * N, e, s);
+    if (e == cudaSuccess) {
+      note_launch();
+      narrow_kernel<T><<<1216, 256, 0, s>>>(Ad, o, (size_t)N * N);
+      e = cudaStreamSynchronize(s);
+    }
+    if (e == cudaSuccess) *out = o;
+    else ok = false;
+  }
+  if (Ad) cudaFree(Ad);
+  if (R) cudaFree(R);
+  if (Cc) cudaFree(Cc);
+  return ok;
 }
 
 template <typename T>
@@ -681,7 +721,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     // next coarser level: halve every even direction
     int cf[3] = {nx % 2 == 0 ? 2 : 1, ny % 2 == 0 ? 2 : 1, nz % 2 == 0 ? 2 : 1};
     const long cells = (long)nx * ny * nz;
-    if (cells <= 64 || (cf[0] == 1 && cf[1] == 1 && cf[2] == 1) || lev >= 12) break;
+    if (cells * 8 <= kDenseMax || cells <= 64 || (cf[0] == 1 && cf[1] == 1 && cf[2] == 1) || lev >= 12) break;
     XferDims X;
     X.fnx = nx; X.fny = ny; X.fnz = nz;
     X.cf[0] = cf[0]; X.cf[1] = cf[1]; X.cf[2] = cf[2];
@@ -792,11 +832,8 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       for (int i = 0; i < N; ++i) A[(size_t)i * N + jc] = col[i];
     }
   }
-  if (!dense_regularised_inverse(A, N)) return e;   // keep the iterative coarse solve
-  std::vector<T> AT(A.begin(), A.end());
-  T *ad = lalloc<T>(D, AT.size(), e, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ad, AT.data(), AT.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  T *ad = nullptr;
+  if (!dense_inverse_device<T>(D, std::move(A), N, &ad, e, s)) return e;   // keep the iterative coarse solve
   D->ainv = ad;
   return e;
 }
