@@ -98,6 +98,7 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     return set_error(DGW_ECUDA, "dgw_mesh_create: no CUDA device");
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaError_t ce = box_constants_init(); ce != cudaSuccess) return cuda_check(ce, "dgw_mesh_create");
+  if (cudaError_t ce = curved_constants_init(); ce != cudaSuccess) return cuda_check(ce, "dgw_mesh_create");
   dgw_mesh *M = new dgw_mesh();
   M->P = *P;
   const int k = P->degree, n = k + 1;
@@ -207,6 +208,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     for (int t = 0; t < NMVOL; ++t) up2(cg.mvol[t], &M->v64.mvol[t], &M->v32.mvol[t]);
     for (int t = 0; t < NQSET; ++t) up2(cg.mxf[t], &M->v64.mxf[t], &M->v32.mxf[t]);
     for (int t = 0; t < 2; ++t) up2(cg.myf[t], &M->v64.myf[t], &M->v32.myf[t]);
+    up2(cg.lvol, &M->v64.lvol, &M->v32.lvol);
+    up2(cg.lface, &M->v64.lface, &M->v32.lface);
   } else {
     std::vector<double> rops;
     box_rowscal(geo, rops);

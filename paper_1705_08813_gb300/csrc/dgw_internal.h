@@ -62,6 +62,11 @@ struct MeshView {
   const T *mvol[NMVOL];
   const T *mxf[NQSET];
   const T *myf[2];
+  // curved SIPG Laplacian tables per metric column (k+1 Gauss points): lvol [m][(k+1)^3][6] =
+  // |det J| w J^-1 J^-T (xx yy zz xy xz yz); lface [m][6][(k+1)^2][7] = dA, dA J^-1 n of the own
+  // side, dA J^-1 n of the neighbour at the shared point (n the own outward normal; zero on walls)
+  const T *lvol;
+  const T *lface;
   const int *enr;     // [nc] enriched index or -1
   T visc;             // kinematic viscosity nu
   const Basis<T> *basis;
@@ -162,6 +167,7 @@ struct CurvedHost {
   int nx, ny, nz, k;
   std::vector<double> mvol[NMVOL], mxf[NQSET], myf[2];   // layouts as in MeshView
   std::vector<double> tau;                               // [nx*ny] per metric column
+  std::vector<double> lvol, lface;                       // Laplace tables (layout as in MeshView)
   std::vector<double> xn, yn;                            // [nx*ny][n*n] nodal (x, y), x-node fastest
 };
 void curved_geometry(const dgw_mesh_params &P, int nx, int ny, int nz, int k, const Basis<double> &B, CurvedHost &G);
@@ -191,6 +197,11 @@ template <typename T>
 cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s);
 // Jacobi diagonal of the SIPG Laplacian of a curved mesh (FP64, one thread per DoF)
 cudaError_t launch_curved_diagonal(const MeshView<double> &m, double *dg, cudaStream_t s);
+// SIPG Laplacian on curved cells from the lvol/lface tables (degree-specialised line passes)
+template <typename T>
+cudaError_t launch_curved_laplace(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s);
+// Degree tables of the curved Laplace kernel in constant memory (once per device; host-synchronous)
+cudaError_t curved_constants_init();
 template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s,
                              const LapEpi<T> *epi = nullptr);

@@ -213,6 +213,58 @@ void curved_geometry(const dgw_mesh_params &P, int nx, int ny, int nz, int k, co
         }
       G.tau[m] = (double)(n * n) * A / V;
     }
+  // SIPG Laplacian tables at the k+1 Gauss points (QSET_LIN)
+  const int q = B.q[QSET_LIN];
+  const double *w = B.w[QSET_LIN];
+  G.lvol.assign((size_t)ncol * q * q * q * 6, 0.0);
+  G.lface.assign((size_t)ncol * 6 * q * q * 7, 0.0);
+  for (int m = 0; m < ncol; ++m)
+    for (int a2 = 0; a2 < q; ++a2)
+      for (int a1 = 0; a1 < q; ++a1)
+        for (int a0 = 0; a0 < q; ++a0) {
+          const double *r = &G.mvol[0][((size_t)m * q * q + a0 + q * a1) * MREC];
+          const double dv = std::fabs(r[9]) * w[a0] * w[a1] * w[a2];
+          auto jj = [&](int x, int y) { return dv * (r[x * 3] * r[y * 3] + r[x * 3 + 1] * r[y * 3 + 1] + r[x * 3 + 2] * r[y * 3 + 2]); };
+          double *o = &G.lvol[((size_t)m * q * q * q + a0 + q * (a1 + q * a2)) * 6];
+          o[0] = jj(0, 0); o[1] = jj(1, 1); o[2] = jj(2, 2); o[3] = jj(0, 1); o[4] = jj(0, 2); o[5] = jj(1, 2);
+        }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const int m = i + nx * j;
+      for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1, s = f & 1;
+        int mo = m;
+        if (d == 0) mo = ((i + (s ? 1 : -1) + nx) % nx) + nx * j;
+        if (d == 1) {
+          const int jn = j + (s ? 1 : -1);
+          if (jn < 0 || jn >= ny) continue;   // homogeneous Neumann wall: no face terms
+          mo = i + nx * jn;
+        }
+        for (int a2 = 0; a2 < q; ++a2)
+          for (int a1 = 0; a1 < q; ++a1) {
+            const double *rs, *ro;
+            if (d == 0) {
+              rs = &G.mxf[QSET_LIN][(((size_t)m * 2 + s) * q + a1) * MREC];
+              ro = &G.mxf[QSET_LIN][(((size_t)mo * 2 + 1 - s) * q + a1) * MREC];
+            } else if (d == 1) {
+              rs = &G.myf[QSET_LIN][(((size_t)m * 2 + s) * q + a1) * MREC];
+              ro = &G.myf[QSET_LIN][(((size_t)mo * 2 + 1 - s) * q + a1) * MREC];
+            } else {
+              rs = ro = &G.mvol[0][((size_t)m * q * q + a1 + q * a2) * MREC];
+            }
+            const double sg = s ? 1.0 : -1.0;
+            const double nrm = std::sqrt(rs[d * 3] * rs[d * 3] + rs[d * 3 + 1] * rs[d * 3 + 1] + rs[d * 3 + 2] * rs[d * 3 + 2]);
+            const double nv[3] = {sg * rs[d * 3] / nrm, sg * rs[d * 3 + 1] / nrm, sg * rs[d * 3 + 2] / nrm};
+            const double dA = std::fabs(rs[9]) * nrm * w[a1] * w[a2];
+            double *o = &G.lface[(((size_t)m * 6 + f) * q * q + a1 + q * a2) * 7];
+            o[0] = dA;
+            for (int r = 0; r < 3; ++r) {
+              o[1 + r] = dA * (rs[r * 3] * nv[0] + rs[r * 3 + 1] * nv[1] + rs[r * 3 + 2] * nv[2]);
+              o[4 + r] = dA * (ro[r * 3] * nv[0] + ro[r * 3 + 1] * nv[1] + ro[r * 3 + 2] * nv[2]);
+            }
+          }
+      }
+    }
 }
 
 }  // namespace dgw

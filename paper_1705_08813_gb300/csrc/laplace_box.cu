@@ -319,7 +319,10 @@ static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, const La
 template <typename T>
 cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
   if (epi.mode == LAP_CHEB && epi.xout == p) return cudaErrorInvalidValue;   // neighbours read p
-  if (m.geo == GEO_CURVED) return launch_vector_op<T>(OP_LAP, m, p, y, s, &epi);   // per-point metrics
+  if (m.geo == GEO_CURVED) {   // per-point metrics: the table-driven kernel, else the general one
+    if (m.lvol && m.lface) return launch_curved_laplace<T>(m, p, y, epi, s);
+    return launch_vector_op<T>(OP_LAP, m, p, y, s, &epi);
+  }
   switch (m.n1) {
     case 2: return launch_box_k<T, 1>(m, p, y, epi, s);
     case 3: return launch_box_k<T, 2>(m, p, y, epi, s);

@@ -612,6 +612,8 @@ static void upload_curved(Lvl<X> *L, const CurvedHost &g, MeshView<X> &v, cudaEr
   for (int t = 0; t < NMVOL; ++t) v.mvol[t] = up(g.mvol[t]);
   for (int t = 0; t < NQSET; ++t) v.mxf[t] = up(g.mxf[t]);
   for (int t = 0; t < 2; ++t) v.myf[t] = up(g.myf[t]);
+  v.lvol = up(g.lvol);
+  v.lface = up(g.lface);
   std::vector<double> tau((size_t)g.nx * g.ny * g.nz);
   for (size_t c = 0; c < tau.size(); ++c) tau[c] = g.tau[c % ((size_t)g.nx * g.ny)];
   v.tau = up(tau);

@@ -186,9 +186,12 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   p.part = o; o += 4 * 24;   // per-warp partial sums of the enriched reductions (128 threads)
   p.work = o;
   int v = o;
-  p.vA = v; v += ka * SX;
+  // the point values V (written by the last forward pass, read until the enriched reduction) share
+  // room with A, which is dead between the second forward pass and the second integration pass
+  const bool has_v = op == OP_DIV || op == OP_CONV;
+  p.vA = v; v += (has_v && 3 * p.P > ka * SX) ? 3 * p.P : ka * SX;
+  p.vV = p.vA;
   p.vB = v; v += kb * SZ;
-  p.vV = v; v += (op == OP_DIV || op == OP_CONV) ? 3 * p.P : 0;
   p.vG = v; v += (op == OP_CONV || op == OP_VISC ? 9 : 3) * p.P;
   p.vGt = v; v += op == OP_VISC ? 9 * p.P : 0;
   p.vol_end = v;
