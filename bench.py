@@ -534,7 +534,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # DRAM bytes per launch of laplace_box_kernel<float,4> at the bench workload, scaled by DoFs from the
     # ncu capture summarised in profiles/laplace_box_fp32_q4_64x48x48.md (same kernel build)
-    ap.add_argument("--traffic-bytes", type=float, default=(76.820480e6 + 40.347136e6) * 2304000 / 18432000)
+    ap.add_argument("--traffic-bytes", type=float, default=(76.903424e6 + 40.288256e6) * 2304000 / 18432000)
     ap.add_argument("--serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=400)
     ap.add_argument("--serving-slots", type=int, default=8)
