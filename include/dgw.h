@@ -128,7 +128,7 @@ typedef struct {
   int max_iter;       /* limit on CG iterations (mode 1: inner iterations summed over refinement steps) */
   int mode;           /* 0: FP64 CG + FP64 multigrid; 1 (mixed): FP64 iterative refinement (p, b - A p
                          and its norm in FP64) around FP32 CG + FP32 multigrid, each inner solve
-                         reducing the unit-scaled residual by 1e-4 or to what the target still needs,
+                         reducing the unit-scaled residual by 1e-5 or to what the target still needs,
                          dot products accumulated in FP64; 2: FP64 CG + Jacobi */
   int cheb_degree;    /* Chebyshev smoother degree (e.g. 5) */
 } dgw_solve_opts;

@@ -265,7 +265,7 @@ static cudaError_t vcycle32_graph(dgw_mesh *M, dgw_solver *S, float *z32, cudaSt
 // loop keeps p, the residual r = b - A p and its norm in FP64 (one FP64 operator apply per outer
 // step); each inner solve takes the residual scaled to unit norm, runs flexible CG with the FP32
 // operator and the FP32 multigrid V-cycle (dot products accumulated in FP64) until the unit
-// residual drops below max(1e-4, rtol ||b|| / (2 ||r||)), and the scaled correction is added to p.
+// residual drops below max(1e-5, rtol ||b|| / (2 ||r||)), and the scaled correction is added to p.
 static dgw_status pressure_solve_mixed(dgw_mesh *M, dgw_solver *S, const dgw_solve_opts *o, double *p, double bnorm,
                                        int *iterations, cudaStream_t s) {
   const long n = M->np;
@@ -281,7 +281,7 @@ static dgw_status pressure_solve_mixed(dgw_mesh *M, dgw_solver *S, const dgw_sol
     }
     if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: mixed workspace");
   }
-  constexpr double kInnerTol = 1e-4;   // reduction per inner solve; FP32 rounding allows about 1e-6
+  constexpr double kInnerTol = 1e-5;   // reduction per inner solve; FP32 rounding allows about 1e-6
   int it = 0;
   for (;;) {
     // S->r holds the FP64 residual of p; its squared norm goes to SC_RN
