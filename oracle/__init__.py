@@ -69,6 +69,7 @@ def _load():
             getattr(lib, name).restype = ctypes.c_int
         lib.dgo_viscous.argtypes = [vp, dp, dp, dp]
         lib.dgo_mass.argtypes = [vp, dp, dp]
+        lib.dgo_vmass.argtypes = [vp, dp, dp]
         lib.dgo_set_active.argtypes = [vp, ctypes.c_void_p]
         lib.dgo_solve_cg.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_int, ip, dp]
         lib.dgo_eval_point.argtypes = [vp, dp, ctypes.c_int, dp, dp]
@@ -191,6 +192,12 @@ class Mesh:
     def mass(self, p: np.ndarray) -> np.ndarray:
         p = np.ascontiguousarray(p, dtype=np.float64); y = np.zeros(self.n_p)
         self.lib.dgo_mass(self.h, _ptr(p), _ptr(y))
+        return y
+
+    def vmass(self, u: np.ndarray) -> np.ndarray:
+        """Velocity mass operator on standard and enriched DoFs (n_u values in, n_u out)."""
+        u = np.ascontiguousarray(u, dtype=np.float64); y = np.zeros(self.n_u)
+        self.lib.dgo_vmass(self.h, _ptr(u), _ptr(y))
         return y
 
     def laplace_diag(self) -> np.ndarray:

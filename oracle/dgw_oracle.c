@@ -1197,6 +1197,47 @@ void dgo_set_threads(int n) {
 #endif
 }
 
+/* y = M_e(v, u) = (v, u) over every cell (Sec. 4.2 mass term) for the velocity space: standard test
+ * functions and, in enriched cells, the enriched ones psi N_B e_a; u = ubar + util; linear-term points
+ * (q_wall wall-normal points in enriched cells). No face terms. */
+int dgo_vmass(void *h, const double *u, double *y) {
+  omesh *M = (omesh *)h;
+  int n3 = M->n1 * M->n1 * M->n1;
+  memset(y, 0, sizeof(double) * M->nu);
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < M->nc; ++c) {
+      if (M->active && !M->active[c]) continue;
+      int nq[3];
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      int en = M->enr[c];
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            vstate s; eval_vel(M, u, c, &t, &s);
+            for (int a = 0; a < 3; ++a) {
+              double va = dV * (s.ub[a] + s.ut[a]);
+              double *yc = y + ((size_t)c * 3 + a) * n3;
+              for (int i = 0; i < n3; ++i) yc[i] += t.phi[i] * va;
+              if (en >= 0) {
+                double *ye = y + 3L * M->np + ((size_t)en * 3 + a) * M->nef;
+                for (int v = 0; v < M->nef; ++v) ye[v] += t.ephi[v] * va;
+              }
+            }
+          }
+    }
+    ptab_free(&t);
+  }
+  return 0;
+}
+
 /* y = M p, the pressure-space mass matrix (Sec. 4.2 mass term, scalar), k+1 Gauss points. */
 int dgo_mass(void *h, const double *p, double *y) {
   omesh *M = (omesh *)h;

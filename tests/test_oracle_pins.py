@@ -218,6 +218,54 @@ def test_divergence_enrichment_volume_term():
 
 
 # ---------------------------------------------------------------------------------------------
+# Velocity mass term (Sec. 4.2, M_e(v, u) = (v, u) per cell)
+# ---------------------------------------------------------------------------------------------
+def test_vmass_standard_part_integrates_polynomials():
+    """Sum_i phi_i = 1: summing M u over the standard test functions of component a gives int u_a,
+    exact for a polynomial field (the channel volume factor 2 pi^2 times the y-integral)."""
+    m = O.Mesh(3, 4, 2, 2, n_layers=0)
+    u = _std_field(m, lambda x, y, z: y ** 2, lambda x, y, z: 1 + 0 * y, lambda x, y, z: y + 0 * x)
+    y = m.vmass(u)[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    ref = [(2 * math.pi * math.pi) * (2.0 / 3.0), (2 * math.pi * math.pi) * 2.0, 0.0]
+    for a in range(3):
+        assert abs(y[:, a, :].sum() - ref[a]) < 1e-12 * 2 * math.pi * math.pi * 2
+
+
+def test_vmass_enrichment_integrates_psi():
+    """u = psi(y+) e_x from enrichment only (all 8 weights 1): the standard test functions of component
+    x sum to int_{wall cells} psi dV and the enriched ones psi N_B (sum_B N_B = 1) to int psi^2 dV -
+    both compared with adaptive quadrature of Spalding's law; the other components stay zero."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    u = np.zeros(m.n_u)
+    enr = u[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    enr[:, 0, :] = 1.0
+    y = m.vmass(u)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    ref = 2 * (2 * math.pi * math.pi) * quad(lambda s: O.psi_spalding(s * w.u_tau / w.nu)[0], 0.0, dy,
+                                             epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    std = y[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    ye = y[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    assert abs(std[:, 0, :].sum() / ref - 1.0) < 1e-6
+    ref2 = 2 * (2 * math.pi * math.pi) * quad(lambda s: O.psi_spalding(s * w.u_tau / w.nu)[0] ** 2, 0.0, dy,
+                                              epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    assert abs(ye[:, 0, :].sum() / ref2 - 1.0) < 1e-6
+    assert np.abs(std[:, 1:, :]).max() == 0.0 and np.abs(ye[:, 1:, :]).max() == 0.0
+
+
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_vmass_symmetric_positive_definite(geometry):
+    """(v, u) is a symmetric positive definite bilinear form on standard plus enriched DoFs:
+    brute-force assembly on a tiny mesh."""
+    kw = dict(lx=9.0, ly=3.036, lz=4.5, geometry=1) if geometry else {}
+    m = O.Mesh(2, 2, 1, 1, nu=1e-3, tau_w=1e-2, **kw)
+    A = np.column_stack([m.vmass(e) for e in np.eye(m.n_u)])
+    assert np.abs(A - A.T).max() < 1e-14 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0.0
+
+
+# ---------------------------------------------------------------------------------------------
 # Convective term (Sec. 4.2, local Lax-Friedrichs flux)
 # ---------------------------------------------------------------------------------------------
 
