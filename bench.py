@@ -480,6 +480,56 @@ def run_serving(args):
     return 0
 
 
+def run_helmholtz(args):
+    """Viscous step of the dual-splitting scheme on the workload: velocity mass apply (FP64, FP32) and the
+    Helmholtz solve gamma M u - F^nu(u) = gamma M u^ (gamma = 1.5 / dt, BDF2, dt = args.dt) to 1e-10 with
+    restarted GMRES, nu_t frozen from the workload's velocity field, initial guess u^."""
+    import torch
+    from paper_1705_08813_gb300 import dgw, inputs as I
+    torch.cuda.set_device(0)
+    w = I.WORKLOADS[args.workload]
+    m = dgw.mesh_for(w)
+    u_hat = torch.from_numpy(I.workload_velocity(m.node_coords(), m.n_e, w)).cuda()
+    m.update_eddy_viscosity(u_hat)
+    gamma = 1.5 / args.dt
+    rhs = torch.empty_like(u_hat)
+    m.mass(u_hat, rhs)
+    rhs *= gamma
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y = torch.empty_like(u_hat)
+    y32 = torch.empty(m.n_u, dtype=torch.float32, device="cuda")
+    u32 = u_hat.float()
+    times = {}
+    for name, fn in (("mass64", lambda: m.mass(u_hat, y)), ("mass32", lambda: m.mass(u32, y32))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(10):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        times[name] = ev0.elapsed_time(ev1) / 10
+    u = u_hat.clone()
+    m.helmholtz_solve(gamma, rhs, u, rtol=1e-10, max_iter=5000, restart=args.restart)   # setup and warm-up
+    ts, infos = [], []
+    for _ in range(max(1, args.steps)):
+        u.copy_(u_hat)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos.append(m.helmholtz_solve(gamma, rhs, u, rtol=1e-10, max_iter=5000, restart=args.restart))
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.median(ts)
+    print(json.dumps({"metric": "viscous Helmholtz step: mass apply GDoF/s and GMRES solves/s at 1e-10",
+                      "workload": w.name, "n_u": m.n_u, "gamma": gamma, "dt": args.dt, "restart": args.restart,
+                      "mass_fp64_ms": times["mass64"], "mass_fp64_gdofs": m.n_u / (times["mass64"] * 1e-3) / 1e9,
+                      "mass_fp32_ms": times["mass32"], "mass_fp32_gdofs": m.n_u / (times["mass32"] * 1e-3) / 1e9,
+                      "solve_ms": ms, "solves_per_s": 1e3 / ms, "iterations": infos[-1]["iterations"],
+                      "rel_residual": infos[-1]["rel_residual"]}), flush=True)
+    return 0
+
+
 def run_profile_kernel(args):
     """A few launches of one operator kernel on a channel of the given size (used for ncu captures:
     a small number of launches, inputs larger than L2 when the mesh is large enough)."""
@@ -540,6 +590,9 @@ def main():
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--serving-budget-gb", type=float, default=120.0)
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--helmholtz", action="store_true", help="time the mass apply and the Helmholtz solve")
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--profile-kernel", default=None,
                     choices=["laplace64", "laplace32", "divergence", "convective", "convective32", "viscous",
                              "viscous32"])
@@ -551,6 +604,8 @@ def main():
         return run_profile_kernel(args)
     if args.serving:
         return run_serving(args)
+    if args.helmholtz:
+        return run_helmholtz(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

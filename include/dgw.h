@@ -163,6 +163,33 @@ dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const
 dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t mesh, const double *b, double *p, double rtol, int max_iter,
                                              dgw_solve_info *info, void *stream);
 
+/* ---- Viscous step of the dual-splitting scheme ------------------------------------------- */
+
+/* y = M(v, u) = (v, u) over every cell (Sec. 4.2 mass term) for the velocity space: standard test
+ * functions and, in enriched cells, the enriched ones psi N_B e_a, with the linear-term points
+ * (q_wall wall-normal in enriched cells). No face terms. u, y: n_u values of type `prec`. */
+dgw_status dgw_apply_mass(dgw_mesh_t mesh, int prec, const void *u, void *y, void *stream);
+
+typedef struct {
+  double rtol;        /* relative residual ||rhs - H u||_2 / ||rhs||_2 target */
+  int max_iter;       /* limit on GMRES iterations (Krylov vectors built, all restarts) */
+  int restart;        /* Krylov vectors per restart cycle (1..64; 0: 30) */
+} dgw_helmholtz_opts;
+
+/* Solve the viscous Helmholtz problem of the dual-splitting step (eq. helmholtzspat),
+ *   H u = gamma M u - F^nu(vbar, v~; ubar, u~) = rhs,   gamma = gamma_0 / dt > 0,
+ * with the nu_t frozen by the last dgw_update_eddy_viscosity (the paper's right-hand side is
+ * gamma M u^^ of the projected velocity). u: on entry the initial guess, on exit the solution
+ * (n_u doubles, device); rhs: n_u doubles. Restarted GMRES with right preconditioning by the
+ * inverse of gamma times the block-diagonal mass (exact on the standard DoFs of box cells, the
+ * volume-scaled reference inverse on curved cells, the 8 x 8 enriched blocks inverted), FP64;
+ * the workspace ((restart + 1) + restart vectors of n_u doubles) is allocated on first use and kept
+ * with the mesh. info->iterations = Krylov vectors built, rel_residual = the true relative residual
+ * of the returned u, ms = host wall time. Synchronises `stream`. Returns DGW_ENOTCONV (u and info
+ * filled) when max_iter is reached first. */
+dgw_status dgw_helmholtz_solve(dgw_mesh_t mesh, double gamma, const double *rhs, double *u,
+                               const dgw_helmholtz_opts *opts, dgw_solve_info *info, void *stream);
+
 /* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32): number of
  * levels, the estimated largest eigenvalue of D^-1 A per level (the Chebyshev smoother works on
  * [1.2 lmax / 15, 1.2 lmax]) and the cell count per level, finest first; at most max_levels

@@ -116,6 +116,7 @@ struct dgw_mesh {
   double *diag64 = nullptr;     // Jacobi diagonal of the Laplace operator
   float *diag32 = nullptr;
   struct dgw_solver *solver = nullptr;   // lazily built solver workspace and multigrid hierarchy
+  struct dgw_helm *helm = nullptr;       // lazily built Helmholtz (GMRES) workspace
 };
 
 namespace dgw {
@@ -209,6 +210,6 @@ cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 
-enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3 };
+enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3, OP_MASS = 4 };
 
 }  // namespace dgw

@@ -6,6 +6,7 @@
 //   OP_CONV y = F^c(v,u), LF flux         (Sec. 4.2, convective term; mirror state on walls)
 //   OP_VISC y = -F^nu(vbar,v~;ubar,u~)    (eq. viscous_multiscale, harmweights, minvt)
 //   OP_LAP  y = A_L p, SIPG               (eq. ipflux; curved cells only, boxes use laplace_box.cu)
+//   OP_MASS y = M(v,u) = (v,u)            (Sec. 4.2 mass term; volume only, enriched DoFs included)
 //
 // Wall-layer cells add the enrichment u~ = psi sum_B N_B u~_B (eq. enrichment) at q_wall
 // wall-normal Gauss points, with psi and grad psi read from the wall tables.
@@ -188,7 +189,7 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   int v = o;
   // the point values V (written by the last forward pass, read until the enriched reduction) share
   // room with A, which is dead between the second forward pass and the second integration pass
-  const bool has_v = op == OP_DIV || op == OP_CONV;
+  const bool has_v = op == OP_DIV || op == OP_CONV || op == OP_MASS;
   p.vA = v; v += (has_v && 3 * p.P > ka * SX) ? 3 * p.P : ka * SX;
   p.vV = p.vA;
   p.vB = v; v += kb * SZ;
@@ -217,6 +218,7 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   p.fF2 = g; g += 2 * nout * nn;
   p.fG2 = g; g += 2 * nout * nn;
   if (g > p.face_end) p.face_end = g;
+  if (op == OP_MASS) p.face_end = p.work;   // no face terms
   p.total = p.vol_end > p.face_end ? p.vol_end : p.face_end;
   return p;
 }
@@ -329,14 +331,16 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         }
         w = wtv + t * WT;
       }
-      if (OP == OP_DIV || OP == OP_CONV) {
+      if (OP == OP_DIV || OP == OP_CONV || OP == OP_MASS) {
         T uu[3] = {V[t], V[P + t], V[2 * P + t]};
         if (enr_c)
           for (int a = 0; a < 3; ++a) {
             uu[a] += w[0] * sN[a];
             V[a * P + t] = uu[a];
           }
-        if (CURVED) {
+        if (OP == OP_MASS) {   // value coefficients of the test functions
+          for (int a = 0; a < 3; ++a) G[a * P + t] = dV * uu[a];
+        } else if (CURVED) {
           T cf[3];
           if (OP == OP_DIV) {
             phys_to_ref(Ji, uu, cf);
@@ -440,6 +444,36 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       };
       reduce24<T>(P, contrib, re, S0 + L.part);
     }
+    if (OP == OP_MASS) {
+      // enriched test functions: (psi N_v e_a, u)
+      if (enr_c) {
+        auto contrib = [&](int t, T *acc) {
+          const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
+          const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
+          const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
+          const T psi = wtv[t * WT];
+          const T pv[3] = {psi * G[t], psi * G[P + t], psi * G[2 * P + t]};   // dV psi u_a
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            T Nv, dN[3];
+            q1_vertex(f, v, Nv, dN);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[a * 8 + v] += Nv * pv[a];
+          }
+        };
+        reduce24<T>(P, contrib, re, S0 + L.part);
+      }
+      // integrate the value coefficients back to the nodes: S_z^T, S_y^T, S_x^T
+      pass_batch<T>([&](int a) -> Pass<T> {
+        return {G + a * P, S_[2], nullptr, nullptr, Bv + a * SZ};
+      }, 3, q0, q1, q2, 2, n, q2, true, false);
+      pass_batch<T>([&](int a) -> Pass<T> {
+        return {Bv + a * SZ, S_[1], nullptr, nullptr, A + a * SX};
+      }, 3, q0, q1, n, 1, n, q1, true, false);
+      pass_batch<T>([&](int a) -> Pass<T> {
+        return {A + a * SX, S_[0], nullptr, nullptr, r + a * n3};
+      }, 3, q0, n, n, 0, n, q0, true, true);
+    } else {
     // P5-P7: integrate the gradient coefficients back to the nodes (z, y, x)
     pass_batch<T>([&](int b) -> Pass<T> {
       const int a = b % NOUT, k = b / NOUT;   // k: 0 Z0 = D_z^T H_z, 1 Z1 = S_z^T H_y, 2 Z2 = S_z^T H_x
@@ -453,8 +487,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     pass_batch<T>([&](int a) -> Pass<T> {
       return {A + a * SX, S_[0], A + (NOUT + a) * SX, D_[0], r + a * n3};
     }, NOUT, q0, n, n, 0, n, q0, true, true);
+    }
   }
 
+  if constexpr (OP != OP_MASS) {
   // ================= faces, one direction (two faces) at a time =================
   // trace slots per direction: (face s, side, component); on boxes the divergence needs the normal
   // component only
@@ -913,6 +949,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
     __syncthreads();
   }
+  }
   // ================= store =================
   if (OP == OP_LAP && epi.mode != LAP_PLAIN) {
     const size_t o = (size_t)c * n3;
@@ -968,6 +1005,7 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
       case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_CONV: return launch_vec<T, OP_CONV, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_VISC: return launch_vec<T, OP_VISC, GEO_CURVED>(m, u, y, s, nullptr);
+      case OP_MASS: return launch_vec<T, OP_MASS, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_LAP:
         switch (m.n1) {
           case 2: return launch_vec<T, OP_LAP, GEO_CURVED, 2>(m, u, y, s, epi);
@@ -984,6 +1022,7 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
     case OP_DIV: return launch_vec<T, OP_DIV, GEO_BOX>(m, u, y, s, nullptr);
     case OP_CONV: return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s, nullptr);
     case OP_VISC: return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s, nullptr);
+    case OP_MASS: return launch_vec<T, OP_MASS, GEO_BOX>(m, u, y, s, nullptr);
   }
   return cudaErrorInvalidValue;
 }

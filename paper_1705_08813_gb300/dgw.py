@@ -19,7 +19,8 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
            "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
-           "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy"]
+           "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
+           "dgw_apply_mass", "dgw_helmholtz_solve"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -42,6 +43,10 @@ class MeshParams(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int)]
+
+
+class HelmholtzOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int)]
 
 
 class Job(ctypes.Structure):
@@ -80,6 +85,9 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp]
     lib.dgw_pressure_solve_jacobi_noalloc.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int,
                                                       ctypes.POINTER(SolveInfo), vp]
+    lib.dgw_apply_mass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.dgw_helmholtz_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.POINTER(HelmholtzOpts),
+                                        ctypes.POINTER(SolveInfo), vp]
     lib.dgw_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
     lib.dgw_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_long)]
     lib.dgw_poll.argtypes = [vp, ctypes.c_long, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(SolveInfo),
@@ -184,6 +192,24 @@ class Mesh:
         _check(self.lib.dgw_apply_viscous(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
                                           _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
         return y
+
+    def mass(self, u, y, stream=None):
+        _check(self.lib.dgw_apply_mass(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
+                                       _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
+        return y
+
+    def helmholtz_solve(self, gamma, rhs, u, rtol=1e-10, max_iter=1000, restart=30, stream=None, check=True):
+        """Solve gamma M u - F^nu(u) = rhs (u: initial guess in, solution out)."""
+        import torch
+        opts = HelmholtzOpts(rtol, max_iter, restart)
+        info = SolveInfo()
+        st = self.lib.dgw_helmholtz_solve(self.h, ctypes.c_double(gamma), _ptr(rhs, torch.float64, self.n_u, "rhs"),
+                                          _ptr(u, torch.float64, self.n_u, "u"), ctypes.byref(opts),
+                                          ctypes.byref(info), _stream(stream))
+        if check:
+            _check(st)
+        return {"iterations": info.iterations, "rel_residual": info.rel_residual, "ms": info.ms, "status": st,
+                "dof_applies": info.dof_applies}
 
     def pressure_solve(self, b, p, rtol=1e-10, max_iter=1000, mode=1, cheb_degree=5, stream=None, check=True):
         import torch
