@@ -181,10 +181,11 @@ def _perturbation_grid(xs, ys, zs, w: Workload):
 
 
 def velocity_field(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1,
-                   amplitude: float = 0.1) -> np.ndarray:
-    """Velocity DoF vector [cell][3][(k+1)^3] followed by [enriched cell][3][8] for a channel
+                   amplitude: float = 0.1, nef: int = 8) -> np.ndarray:
+    """Velocity DoF vector [cell][3][(k+1)^3] followed by [enriched cell][3][nef] for a channel
     workload: mean profile + perturbation in non-wall cells, perturbation only in wall cells
-    plus enrichment coefficients u_tau e_x. Perturbation scaled to amplitude * U_bulk."""
+    plus enrichment coefficients u_tau e_x (nef = 8 trilinear weights, 1 a constant weight).
+    Perturbation scaled to amplitude * U_bulk."""
     nx, ny, nz, k = w.nx, w.ny, w.nz, w.k
     n1 = k + 1
     xs, ys, zs = _unique_axes(nodes, nx, ny, nz, k)
@@ -208,9 +209,9 @@ def velocity_field(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1,
         wall_row[ny - n_layers:] = True
     mean = np.where(wall_row[:, None], 0.0, Ucell)                 # cy, ly
     std[:, :, :, 0, :, :, :] += mean[None, :, None, None, :, None]
-    u = np.zeros(3 * nx * ny * nz * n1 ** 3 + 3 * 8 * n_e)
+    u = np.zeros(3 * nx * ny * nz * n1 ** 3 + 3 * nef * n_e)
     u[: std.size] = std.reshape(-1)
-    enr = np.zeros((n_e, 3, 8))
+    enr = np.zeros((n_e, 3, nef))
     enr[:, 0, :] = w.u_tau
     u[std.size:] = enr.reshape(-1)
     return u
@@ -222,7 +223,7 @@ def _bump_wall(x: np.ndarray, lx: float) -> np.ndarray:
 
 
 def bump_velocity_field(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1,
-                        amplitude: float = 0.1) -> np.ndarray:
+                        amplitude: float = 0.1, nef: int = 8) -> np.ndarray:
     """Velocity DoF vector for a bump workload: the mean profile along x in the vertical distance to
     the nearer wall, plus a seeded perturbation uniform in [-1, 1] * amplitude * U_c (U_c the
     largest mean nodal value) in every component of every node; wall cells carry the perturbation
@@ -241,19 +242,19 @@ def bump_velocity_field(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int 
     pert = uniform(w.seed, 3 * U.size, -1.0, 1.0, stream=31).reshape(nz, ny, nx, 3, n3) * amplitude * uc
     std = pert.copy()
     std[:, :, :, 0, :] += U
-    u = np.zeros(std.size + 3 * 8 * n_e)
+    u = np.zeros(std.size + 3 * nef * n_e)
     u[: std.size] = std.reshape(-1)
-    enr = np.zeros((n_e, 3, 8))
+    enr = np.zeros((n_e, 3, nef))
     enr[:, 0, :] = w.u_tau
     u[std.size:] = enr.reshape(-1)
     return u
 
 
-def workload_velocity(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1) -> np.ndarray:
-    """Velocity input of a workload of either geometry."""
+def workload_velocity(nodes: np.ndarray, n_e: int, w: Workload, n_layers: int = 1, nef: int = 8) -> np.ndarray:
+    """Velocity input of a workload of either geometry (nef enrichment coefficients per component)."""
     if w.geometry == 1:
-        return bump_velocity_field(nodes, n_e, w, n_layers=n_layers)
-    return velocity_field(nodes, n_e, w, n_layers=n_layers)
+        return bump_velocity_field(nodes, n_e, w, n_layers=n_layers, nef=nef)
+    return velocity_field(nodes, n_e, w, n_layers=n_layers, nef=nef)
 
 
 def pressure_rhs(n_p: int, seed: int) -> np.ndarray:

@@ -406,3 +406,129 @@ def test_oracle_solve_reaches_tolerance_zero_mean():
     b = I.pressure_rhs(m.n_p, 7)
     p, it, rr = m.solve(b, rtol=1e-12)
     assert rr <= 1e-12 and abs(p.mean()) < 1e-14 and it > 0
+
+
+# ---------------------------------------------------------------------------------------------
+# Constant enrichment weights, l = 0 (Sec. 3.1 with N^0 = 1; the setting of every simulation of
+# Sec. 5 except the one comparison of Sec. 5.1): one coefficient per component and wall cell
+# ---------------------------------------------------------------------------------------------
+
+def _l0_mesh(w, **kw):
+    return O.Mesh(**w.mesh_kwargs(), enrich_l=0, **kw)
+
+
+def test_l0_layout_has_one_coefficient_per_component():
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m0, m1 = _l0_mesh(w), O.Mesh(**w.mesh_kwargs())
+    assert m0.n_e == m1.n_e > 0 and m0.n_p == m1.n_p
+    assert m0.n_u == 3 * m0.n_p + 3 * m0.n_e and m1.n_u == 3 * m1.n_p + 24 * m1.n_e
+
+
+def test_l0_enrichment_reproduces_wall_law_profile():
+    """ubar = 0 and u~ = u_tau e_x: the field in every wall cell is u_tau psi(y+) e_x (eq. enrichment
+    with a constant weight)."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = _l0_mesh(w)
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3)[:, 0] = w.u_tau
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    for c in [0, 5, 63, 8 * 8 * 3 + 8 * 7 + 2]:
+        ys = X[c, :, 1]
+        for xi in ([0.1, 0.0, 0.7], [0.5, 0.37, 0.2], [0.9, 0.99, 0.4]):
+            r = m.eval_point(u, c, xi)
+            yphys = ys.min() + xi[1] * (ys.max() - ys.min())
+            yp = (1.0 - abs(yphys)) * w.u_tau / w.nu
+            assert abs(r["u"][0] - w.u_tau * O.psi_spalding(yp)[0]) < 1e-14
+            assert abs(r["u"][1]) < 1e-300 and abs(r["u"][2]) < 1e-300
+
+
+def test_l0_mass_and_divergence_integrate_psi():
+    """u~ = e_x (then e_y), ubar = 0: the enriched mass output of component x is int psi^2 over the
+    wall cells, the standard outputs sum to int psi, and with q = y the divergence gives int psi
+    (face terms vanish or cancel as for l = 1) - all against adaptive quadrature of Spalding's law."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = _l0_mesh(w)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    area = 2 * (2 * math.pi * math.pi)
+
+    def integral(f):
+        return area * quad(lambda s: f(O.psi_spalding(s * w.u_tau / w.nu)[0]), 0.0, dy,
+                           epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3)[:, 0] = 1.0
+    y = m.vmass(u)
+    std = y[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    ye = y[3 * m.n_p:].reshape(m.n_e, 3)
+    assert abs(std[:, 0, :].sum() / integral(lambda p: p) - 1.0) < 1e-6
+    assert abs(ye[:, 0].sum() / integral(lambda p: p * p) - 1.0) < 1e-6
+    assert np.abs(ye[:, 1:]).max() == 0.0
+    u[:] = 0.0
+    u[3 * m.n_p:].reshape(m.n_e, 3)[:, 1] = 1.0
+    val = m.node_coords()[:, 1] @ m.divergence(u)
+    assert abs(val / integral(lambda p: p) - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("comp", [0, 2])
+def test_l0_convective_vanishes_for_shear_flow(comp):
+    """The shear-flow invariant of the convective term (div(u x u) = 0, u.n = 0 on y-faces) with the
+    constant-weight enrichment."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = _l0_mesh(w)
+    f = [lambda x, y, z: 0 * y] * 3
+    f[comp] = lambda x, y, z: 1 - y ** 2
+    u = _std_field(m, *f)
+    u[3 * m.n_p:].reshape(m.n_e, 3)[:, comp] = w.u_tau
+    assert np.abs(m.convective(u)).max() < 1e-14
+
+
+def test_l0_viscous_symmetric_part_psd_and_mass_spd():
+    """Brute-force assembly on a tiny enriched mesh with l = 0: the symmetric part of -F^nu is
+    positive semi-definite (clipped viscosity active) and the mass matrix is SPD."""
+    nu = 1e-4
+    m = O.Mesh(2, 3, 2, 2, n_layers=1, nu=nu, tau_w=1e-2, gamma=1.8, enrich_l=0)
+    uf = np.zeros(m.n_u)
+    uf[3 * m.n_p:].reshape(m.n_e, 3)[:, 0] = 0.1
+    uf[3 * m.n_p:] += 0.02 * I.uniform(6, m.n_e * 3, -1, 1)
+    E = np.eye(m.n_u)
+    A = np.column_stack([m.viscous(uf, e) for e in E])
+    S = 0.5 * (A + A.T)
+    ev = np.linalg.eigvalsh(S)
+    assert ev[0] >= -1e-11 * ev[-1]
+    assert max(m.nut_cell(uf, e).max() for e in range(m.n_e)) > 3 * nu
+    Mm = np.column_stack([m.vmass(e) for e in E])
+    assert np.abs(Mm - Mm.T).max() < 1e-14 * np.abs(Mm).max()
+    assert np.linalg.eigvalsh(Mm).min() > 0.0
+
+
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_l0_equals_l1_with_equal_weights(geometry):
+    """sum_B N_B = 1: an l = 1 field whose 8 weights of a component are equal is the l = 0 field with
+    that coefficient, and the l = 0 test function psi e_a is the sum of the 8 l = 1 test functions.
+    So every operator (and nu_t) of l = 0 equals the l = 1 operator with replicated inputs and
+    summed enriched outputs - the oracle's two basis branches checked against each other."""
+    if geometry:
+        w = I.bump_workload("b0", 6, 4, 2, 2, seed=23)
+    else:
+        w = I.Workload("l0", 3, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=24)
+    m0, m1 = _l0_mesh(w), O.Mesh(**w.mesh_kwargs())
+    ne, np3 = m0.n_e, 3 * m0.n_p
+    u0 = I.workload_velocity(m0.node_coords(), ne, w, nef=1)
+    u0[np3:] += 0.1 * w.u_tau * I.uniform(w.seed, 3 * ne, -1, 1, stream=51)
+    u1 = np.concatenate([u0[:np3], np.repeat(u0[np3:], 8)])
+    r = I.uniform(w.seed, m0.n_u, -1, 1, stream=52)
+    r1 = np.concatenate([r[:np3], np.repeat(r[np3:], 8)])
+
+    def fold(y1):
+        return np.concatenate([y1[:np3], y1[np3:].reshape(-1, 8).sum(axis=1)])
+
+    pairs = [(m0.vmass(r), fold(m1.vmass(r1))), (m0.convective(u0), fold(m1.convective(u1))),
+             (m0.viscous(u0, r), fold(m1.viscous(u1, r1)))]
+    for y0, y1 in pairs:
+        assert np.abs(y0 - y1).max() <= 1e-13 * np.abs(y1).max()
+    d0, d1 = m0.divergence(u0), m1.divergence(u1)
+    assert np.abs(d0 - d1).max() <= 1e-13 * np.abs(d1).max()
+    for e in range(0, ne, max(ne // 4, 1)):
+        n0, n1 = m0.nut_cell(u0, e), m1.nut_cell(u1, e)
+        assert np.abs(n0 - n1).max() <= 1e-13 * max(np.abs(n1).max(), 1e-300)
