@@ -28,7 +28,8 @@
  *   - pressure p[c][(k+1)^3], local index a + (k+1)*(b + (k+1)*c3) over the Gauss-Lobatto
  *     nodes (x fastest).
  *   - velocity: standard part u[c][3][(k+1)^3], followed by the enrichment coefficients
- *     u~[e][3][8] (Q1 vertex v = vx + 2 vy + 4 vz) of the enriched cells; enriched cells are
+ *     u~[e][3][8] (enrich_l = 1, Q1 vertex v = vx + 2 vy + 4 vz) or u~[e][3] (enrich_l = 0,
+ *     a constant weight, Sec. 5.1) of the enriched cells; enriched cells are
  *     numbered bottom layer(s) first, then top layer(s), lexicographic (x fastest, then z)
  *     within a layer.
  *   - prec: DGW_FP64 -> buffers are double*, DGW_FP32 -> float*.
@@ -73,7 +74,7 @@ enum { DGW_FP64 = 0, DGW_FP32 = 1 };
 typedef struct {
   int nx, ny, nz;      /* cells per direction (>= 1; ny >= 2*n_layers when enriched) */
   int degree;          /* k in 1..5 */
-  int enrich_l;        /* 1: trilinear weights N^1 (24 coefficients per cell); 0 not supported */
+  int enrich_l;        /* 1: trilinear weights N^1 (24 coefficients per cell); 0: constant weight (3) */
   int q_wall;          /* Gauss points in the wall-normal direction of enriched cells (1..10) */
   int geometry;        /* 0: channel of boxes, 1: curved bump channel */
   int wall_law;        /* 0 Spalding, 1 van Driest */

@@ -58,7 +58,7 @@ template <typename T>
 static void fill_view(dgw_mesh *M, MeshView<T> &v) {
   v.nx = M->P.nx; v.ny = M->P.ny; v.nz = M->P.nz;
   v.n1 = M->n1; v.nc = M->nc; v.ne = M->ne;
-  v.np = M->np; v.nu = M->nu;
+  v.np = M->np; v.nu = M->nu; v.nef = M->nef;
   v.hx = (T)(M->P.lx / M->P.nx);
   v.hz = (T)(M->P.lz / M->P.nz);
   v.visc = (T)M->P.nu;
@@ -86,7 +86,7 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     return set_error(DGW_EINVAL, "dgw_mesh_create: geometry must be 0 (channel) or 1 (bump)");
   if (P->n_layers < 0 || 2 * P->n_layers > P->ny)
     return set_error(DGW_EINVAL, "dgw_mesh_create: need 0 <= n_layers and 2*n_layers <= ny");
-  if (P->n_layers > 0 && P->enrich_l != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: only enrich_l = 1 is implemented");
+  if (P->enrich_l != 0 && P->enrich_l != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: enrich_l must be 0 or 1");
   if (P->q_wall < 1 || P->q_wall > QW_MAX) return set_error(DGW_EINVAL, "dgw_mesh_create: q_wall must be in 1..10");
   if (!(P->lx > 0 && P->ly > 0 && P->lz > 0 && P->stretch_gamma > 0 && P->nu > 0 && P->tau_w > 0))
     return set_error(DGW_EINVAL, "dgw_mesh_create: lengths, gamma, nu and tau_w must be positive");
@@ -141,7 +141,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
         for (int i = 0; i < nx; ++i) M->enr[i + nx * (j + ny * kz)] = ne++;
     }
   M->ne = ne;
-  M->nu = 3 * M->np + 24L * ne;
+  M->nef = P->enrich_l == 0 ? 1 : 8;
+  M->nu = 3 * M->np + 3L * M->nef * ne;
   M->enr_cell.resize(std::max(ne, 1));
   for (int c = 0; c < M->nc; ++c)
     if (M->enr[c] >= 0) M->enr_cell[M->enr[c]] = c;

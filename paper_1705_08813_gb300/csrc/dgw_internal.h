@@ -51,6 +51,7 @@ struct MeshView {
   int nx, ny, nz, n1, nc, ne;
   int q[NQSET];       // point counts of the quadrature sets (host-visible copy)
   long np, nu;
+  int nef;            // enrichment coefficients per component and wall cell: 8 (l = 1) or 1 (l = 0)
   int geo;            // GEO_BOX or GEO_CURVED
   T hx, hz;
   const T *hy;        // [ny] row heights (boxes)
@@ -90,6 +91,7 @@ struct MeshHost;
 struct dgw_mesh {
   dgw_mesh_params P;
   int n1, nc, ne;
+  int nef = 8;                  // 8 (l = 1) or 1 (l = 0)
   long np, nu;
   size_t hbm_bytes = 0;
   std::vector<double> yv;       // vertex rows

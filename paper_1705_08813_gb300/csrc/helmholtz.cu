@@ -10,12 +10,12 @@
 // node-to-point interpolation, W the diagonal of |det J| w at the points), so its inverse is
 // S^-1 W^-1 S^-T: six 1-D passes of S_1^-1 and a pointwise division, exact on boxes and on curved
 // cells off the wall (wall cells integrate with q_w points across the wall; there it is exact only
-// where det J is constant). The enriched DoFs of a wall cell (8 per component) take the inverse of their own 8 x 8
-// block, computed once from the mass operator. The coupling between standard and enriched DoFs is
-// left to GMRES: an exact block inverse through the Schur complement Mee - Mes Mss^-1 Mse gained
-// nothing on the flat channel and, where Mss^-1 is only approximate (wall cells of curved geometry,
-// q_w points across the wall and a non-constant det J), turned the nearly singular complement
-// indefinite and stalled GMRES.
+// where det J is constant). The enriched DoFs of a wall cell (8 per component with l = 1, one with
+// l = 0) take the inverse of their own block, computed once from the mass operator. The coupling
+// between standard and enriched DoFs is left to GMRES: an exact block inverse through the Schur
+// complement Mee - Mes Mss^-1 Mse gained nothing on the flat channel and, where Mss^-1 is only
+// approximate (wall cells of curved geometry, q_w points across the wall and a non-constant det J),
+// turned the nearly singular complement indefinite and stalled GMRES.
 //
 // Orthogonalisation: classical Gram-Schmidt applied twice, so each Krylov step needs two batched
 // reductions (all inner products at once) and one norm, deterministic two-stage sums.
@@ -144,11 +144,11 @@ __device__ void mss_inverse(const double *in, double *out, const double *Si, con
   __syncthreads();
 }
 
-// z = (gamma M_blocks)^-1 r, one CTA per cell: Mss^-1 per component, and the 8 x 8 enriched block
-// inverse of each component in wall cells.
+// z = (gamma M_blocks)^-1 r, one CTA per cell: Mss^-1 per component, and the nef x nef enriched
+// block inverse of each component in wall cells.
 __global__ void inverse_mass_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ sinv,
                                     const double *__restrict__ detw, const int *__restrict__ enr,
-                                    const double *__restrict__ meeinv, int n, long np, double inv_gamma) {
+                                    const double *__restrict__ meeinv, int n, int nef, long np, double inv_gamma) {
   __shared__ double A[NMAX * NMAX * NMAX], Bs[NMAX * NMAX * NMAX], Si[NMAX * NMAX];
   const int c = blockIdx.x, n3 = n * n * n;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) Si[t] = sinv[t];
@@ -157,12 +157,12 @@ __global__ void inverse_mass_kernel(const double *__restrict__ r, double *__rest
     mss_inverse(r + ((size_t)c * 3 + a) * n3, z + ((size_t)c * 3 + a) * n3, Si, detw + (size_t)c * n3, inv_gamma, n,
                 A, Bs);
   const int e = enr ? enr[c] : -1;
-  if (e < 0 || threadIdx.x >= 24) return;
-  const int a = threadIdx.x / 8, v = threadIdx.x % 8;
-  const double *rin = r + 3 * np + ((size_t)e * 3 + a) * 8;
+  if (e < 0 || threadIdx.x >= 3 * nef) return;
+  const int a = threadIdx.x / nef, v = threadIdx.x % nef;
+  const double *rin = r + 3 * np + ((size_t)e * 3 + a) * nef;
   double acc = 0.0;
-  for (int w = 0; w < 8; ++w) acc += meeinv[(size_t)e * 64 + v * 8 + w] * rin[w];
-  z[3 * np + ((size_t)e * 3 + a) * 8 + v] = inv_gamma * acc;
+  for (int w = 0; w < nef; ++w) acc += meeinv[(size_t)e * 64 + v * nef + w] * rin[w];
+  z[3 * np + ((size_t)e * 3 + a) * nef + v] = inv_gamma * acc;
 }
 
 // detw[c][q] = |det J| w_q at the Gauss points: boxes vol_c w0 w1 w2, curved cells from the metric
@@ -190,9 +190,10 @@ __global__ void cell_sum_kernel(const double *__restrict__ y, int n3, double *__
   if (threadIdx.x == 0) vol[c] = s;
 }
 
-// u[3 np + (e*3 + 0)*8 + v] = 1 for every enriched cell e (component x, weight v)
-__global__ void enriched_unit_kernel(double *__restrict__ u, long np, int ne, int v) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) u[3 * np + (size_t)e * 24 + v] = 1.0;
+// u[3 np + (e*3 + 0)*nef + v] = 1 for every enriched cell e (component x, weight v)
+__global__ void enriched_unit_kernel(double *__restrict__ u, long np, int ne, int nef, int v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+    u[3 * np + (size_t)e * 3 * nef + v] = 1.0;
 }
 
 inline int grid_for(long n) {
@@ -200,23 +201,24 @@ inline int grid_for(long n) {
   return (int)std::min<long>(std::max<long>(g, 1), 152 * 16);
 }
 
-// 8 x 8 SPD inverse by Gauss-Jordan (host); false if a pivot is not positive
-bool invert8(const double *A, double *inv) {
+// inverse of an SPD q x q matrix (q <= 8, row-major) by Gauss-Jordan elimination without pivoting
+// (host); false if a pivot is not positive
+bool invert_spd(const double *A, double *inv, int q) {
   double a[8][16];
-  for (int i = 0; i < 8; ++i)
-    for (int j = 0; j < 16; ++j) a[i][j] = j < 8 ? A[i * 8 + j] : (j - 8 == i ? 1.0 : 0.0);
-  for (int k = 0; k < 8; ++k) {
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < 2 * q; ++j) a[i][j] = j < q ? A[i * q + j] : (j - q == i ? 1.0 : 0.0);
+  for (int k = 0; k < q; ++k) {
     const double p = a[k][k];
     if (!(p > 0.0)) return false;
-    for (int j = 0; j < 16; ++j) a[k][j] /= p;
-    for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 2 * q; ++j) a[k][j] /= p;
+    for (int i = 0; i < q; ++i)
       if (i != k) {
         const double f = a[i][k];
-        for (int j = 0; j < 16; ++j) a[i][j] -= f * a[k][j];
+        for (int j = 0; j < 2 * q; ++j) a[i][j] -= f * a[k][j];
       }
   }
-  for (int i = 0; i < 8; ++i)
-    for (int j = 0; j < 8; ++j) inv[i * 8 + j] = a[i][8 + j];
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) inv[i * q + j] = a[i][q + j];
   return true;
 }
 
@@ -234,7 +236,7 @@ static void helm_free(dgw_helm *H) {
   delete H;
 }
 
-// Workspace, cell volumes, 1-D inverse mass and the enriched 8 x 8 inverse blocks (first use, and
+// Workspace, cell volumes, 1-D inverse mass and the enriched inverse blocks (first use, and
 // again when a larger restart length is asked for).
 static cudaError_t helm_setup(dgw_mesh *M, int restart) {
   dgw_helm *H = M->helm;
@@ -312,25 +314,26 @@ static cudaError_t helm_setup(dgw_mesh *M, int restart) {
       e = cudaGetLastError();
     }
   }
-  // enriched blocks: M applied to the enrichment unit vectors of component x; the 8 x 8 blocks are
-  // inverted on the host
+  // enriched blocks: M applied to the enrichment unit vectors of component x; the nef x nef blocks
+  // are inverted on the host (stored with a stride of 64 per wall cell)
   if (e == cudaSuccess && M->ne > 0) {
-    std::vector<double> mee((size_t)M->ne * 64), inv((size_t)M->ne * 64), out(24 * (size_t)M->ne);
-    for (int v = 0; v < 8 && e == cudaSuccess; ++v) {
+    const int q = M->nef;
+    std::vector<double> mee((size_t)M->ne * 64), inv((size_t)M->ne * 64), out(3 * (size_t)q * M->ne);
+    for (int v = 0; v < q && e == cudaSuccess; ++v) {
       e = cudaMemsetAsync(H->w, 0, nu * sizeof(double), s);
       if (e == cudaSuccess) {
         note_launch();
-        enriched_unit_kernel<<<(M->ne + 255) / 256, 256, 0, s>>>(H->w, np, M->ne, v);
+        enriched_unit_kernel<<<(M->ne + 255) / 256, 256, 0, s>>>(H->w, np, M->ne, q, v);
         e = launch_vector_op<double>(OP_MASS, M->v64, H->w, H->t, s);
       }
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(out.data(), H->t + 3 * np, out.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       for (int c = 0; c < M->ne && e == cudaSuccess; ++c)
-        for (int wv = 0; wv < 8; ++wv) mee[(size_t)c * 64 + wv * 8 + v] = out[(size_t)c * 24 + wv];
+        for (int wv = 0; wv < q; ++wv) mee[(size_t)c * 64 + wv * q + v] = out[(size_t)c * 3 * q + wv];
     }
     for (int c = 0; c < M->ne && e == cudaSuccess; ++c)
-      if (!invert8(&mee[(size_t)c * 64], &inv[(size_t)c * 64])) e = cudaErrorInvalidValue;
+      if (!invert_spd(&mee[(size_t)c * 64], &inv[(size_t)c * 64], q)) e = cudaErrorInvalidValue;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(H->meeinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -413,8 +416,8 @@ dgw_status helmholtz_solve(dgw_mesh *M, double gamma, const double *rhs, double 
     for (; j < m && it < o->max_iter; ++j) {
       double *Vj = H->V + (size_t)j * nu, *Zj = H->Z + (size_t)j * nu, *Vn = H->V + (size_t)(j + 1) * nu;
       note_launch();
-      inverse_mass_kernel<<<M->nc, 128, 0, s>>>(Vj, Zj, H->m1inv, H->detw, M->v64.enr, H->meeinv, M->n1, M->np,
-                                                1.0 / gamma);
+      inverse_mass_kernel<<<M->nc, 128, 0, s>>>(Vj, Zj, H->m1inv, H->detw, M->v64.enr, H->meeinv, M->n1, M->nef,
+                                                M->np, 1.0 / gamma);
       e = helm_apply(M, gamma, Zj, H->w, H->t, s);
       if (e != cudaSuccess) return cuda_check(e, "dgw_helmholtz_solve: operator");
       // classical Gram-Schmidt, twice

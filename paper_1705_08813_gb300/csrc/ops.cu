@@ -249,8 +249,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   const int col = CURVED ? metric_col(m, c) : 0;
   for (int t = threadIdx.x; t < NIN * n3; t += blockDim.x) uo[t] = u[(size_t)c * NIN * n3 + t];
   for (int t = threadIdx.x; t < NOUT * n3; t += blockDim.x) r[t] = T(0);
+  // enrichment coefficients as 8 trilinear weights per component; with l = 0 the single coefficient
+  // is replicated (sum_B N_B = 1 makes that the same field)
   for (int t = threadIdx.x; t < 24; t += blockDim.x) {
-    eo[t] = enr_c ? u[3 * m.np + (size_t)ec * 24 + t] : T(0);
+    eo[t] = enr_c ? u[3 * m.np + (size_t)ec * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : T(0);
     re[t] = T(0);
   }
   __syncthreads();
@@ -519,7 +521,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
     for (int t = threadIdx.x; t < 48; t += blockDim.x) {
       const int s = t / 24;
-      en[t] = enb[s] >= 0 ? u[3 * m.np + (size_t)enb[s] * 24 + (t - 24 * s)] : T(0);
+      const int o = t - 24 * s;
+      en[t] = enb[s] >= 0 ? u[3 * m.np + (size_t)enb[s] * 3 * m.nef + (m.nef == 8 ? o : o >> 3)] : T(0);
     }
     __syncthreads();
     T *V2 = S0 + L.fV2, *N2 = S0 + L.fN2, *A0 = S0 + L.fA0, *A1 = S0 + L.fA1, *B0 = S0 + L.fB0, *Tr = S0 + L.fTr;
@@ -969,8 +972,14 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   } else {
     T *yc = y + (size_t)c * 3 * n3;
     for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) yc[t] = r[t];
-    if (enr_c)
+    if (enr_c && m.nef == 8)
       for (int t = threadIdx.x; t < 24; t += blockDim.x) y[3 * m.np + (size_t)ec * 24 + t] = re[t];
+    else if (enr_c && threadIdx.x < 3) {
+      // l = 0: the test function psi e_a is the sum of the 8 weighted ones
+      T acc = T(0);
+      for (int v = 0; v < 8; ++v) acc += re[threadIdx.x * 8 + v];
+      y[3 * m.np + (size_t)ec * 3 + threadIdx.x] = acc;
+    }
   }
 }
 

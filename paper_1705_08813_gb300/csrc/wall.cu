@@ -168,13 +168,13 @@ __global__ void wall_table_kernel(WallCellData w, const Basis<double> *Bg, int q
 // coefficients of u.
 __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, int nvol, int fpmax, const double *wt_vol,
                                       const double *wt_face, const double *aux_vol, const double *aux_face,
-                                      const double *dye, int k, const double *u_enr, double *nut_vol, double *nut_face,
+                                      const double *dye, int k, int nef, const double *u_enr, double *nut_vol, double *nut_face,
                                       float *nut_vol32, float *nut_face32) {
   const Basis<double> &B = *Bg;
   const int e = blockIdx.x;
   const int c = w.enr_cell[e];
   __shared__ double cu[24];
-  for (int t = threadIdx.x; t < 24; t += blockDim.x) cu[t] = u_enr[(size_t)e * 24 + t];
+  for (int t = threadIdx.x; t < 24; t += blockDim.x) cu[t] = u_enr[(size_t)e * 3 * nef + (nef == 8 ? t : t >> 3)];
   __syncthreads();
   const double hdes = kCdes * dye[e] / (k + 1);
   auto nut_at = [&](const double xi[3], const double Ji[3][3], const double *wt, const double *aux) -> double {
@@ -259,7 +259,7 @@ cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s) 
   note_launch();
   eddy_viscosity_kernel<<<M->ne, 128, 0, s>>>(
       w, M->v64.basis, M->v64.nvol[0], M->v64.fpmax[0], M->v64.wt_vol[0], M->v64.wt_face[0], M->aux_vol, M->aux_face,
-      M->dye_dev, M->P.degree, u + 3 * M->np, const_cast<double *>(M->v64.nut_vol),
+      M->dye_dev, M->P.degree, M->nef, u + 3 * M->np, const_cast<double *>(M->v64.nut_vol),
       const_cast<double *>(M->v64.nut_face), M->has32 ? const_cast<float *>(M->v32.nut_vol) : nullptr,
       M->has32 ? const_cast<float *>(M->v32.nut_face) : nullptr);
   return cudaGetLastError();
