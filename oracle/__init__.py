@@ -75,6 +75,11 @@ def _load():
         lib.dgo_eval_point.argtypes = [vp, dp, ctypes.c_int, dp, dp]
         lib.dgo_nut_cell.argtypes = [vp, dp, ctypes.c_int, dp]
         lib.dgo_nut_cell.restype = ctypes.c_int
+        lib.dgo_wall_nodes.argtypes = [vp]
+        lib.dgo_wall_nodes.restype = ctypes.c_int
+        lib.dgo_set_tau_nodes.argtypes = [vp, dp]
+        lib.dgo_wall_shear.argtypes = [vp, dp, dp]
+        lib.dgo_wall_shear.restype = ctypes.c_int
         lib.dgo_volume.argtypes = [vp]
         lib.dgo_volume.restype = ctypes.c_double
         lib.dgo_psi_spalding.argtypes = [ctypes.c_double, dp]
@@ -233,6 +238,24 @@ class Mesh:
         self.lib.dgo_eval_point(self.h, _ptr(u), int(cell), _ptr(xi), _ptr(out))
         return {"u": out[0:3], "ubar": out[3:6], "util": out[6:9], "psi": out[9],
                 "yplus": out[10], "nut": out[11]}
+
+    @property
+    def n_wall_nodes(self) -> int:
+        """Linear wall nodes: 2 walls x nx x nz (periodic), index wall * nx * nz + i + nx * k."""
+        return self.lib.dgo_wall_nodes(self.h)
+
+    def wall_shear(self, u: np.ndarray) -> np.ndarray:
+        """Nodal wall shear stress tau_w,B = |int N_B nu (grad u) n dA| / int N_B dA (Sec. 3.2)."""
+        u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(self.n_wall_nodes)
+        self.lib.dgo_wall_shear(self.h, _ptr(u), _ptr(out))
+        return out
+
+    def set_tau_nodes(self, tau_nodes: np.ndarray) -> None:
+        """Set the wall shear stress of every wall node (enriched-cell vertices off the wall take the
+        value of the wall node that defines their wall distance); changes the enrichment space."""
+        tn = np.ascontiguousarray(tau_nodes, dtype=np.float64)
+        assert tn.size == self.n_wall_nodes
+        self.lib.dgo_set_tau_nodes(self.h, _ptr(tn))
 
     def nut_cell(self, u: np.ndarray, e: int) -> np.ndarray:
         u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(4096)

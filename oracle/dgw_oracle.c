@@ -73,6 +73,7 @@ typedef struct {
   int *enr, *enr_cell;        /* cell -> enriched index (-1) ; enriched index -> cell */
   double *ywall;              /* per enriched cell: 8 vertex wall distances */
   double *tauv;               /* per enriched cell: 8 vertex wall shear stresses */
+  int *tsrc;                  /* per enriched cell: 8 wall-node indices (the node that defines y_B) */
   double *dye;                /* per cell wall-normal width */
   double *tau_cell;           /* per cell penalty tau_IP */
   unsigned char *active;      /* optional: only these cells' outputs are computed (NULL = all) */
@@ -389,15 +390,20 @@ void *dgo_mesh_create(const dgo_params *P) {
   /* vertex wall distances (closest wall node) and wall shear stresses of enriched cells */
   M->ywall = (double *)malloc(sizeof(double) * 8 * (ne > 0 ? ne : 1));
   M->tauv = (double *)malloc(sizeof(double) * 8 * (ne > 0 ? ne : 1));
+  M->tsrc = (int *)malloc(sizeof(int) * 8 * (ne > 0 ? ne : 1));
   for (int e = 0; e < ne; ++e) {
     int c = M->enr_cell[e], i = c % P->nx, j = (c / P->nx) % P->ny, kz = c / (P->nx * P->ny);
     for (int v = 0; v < 8; ++v) {
       int vi = i + (v & 1), vj = j + ((v >> 1) & 1), vk = kz + (v >> 2);
       double xv[3];
       vertex_pos(M, vi, vj, vk, xv);
+      /* closest wall node B (index wall * nx * nz + i + nx * k, periodic indices) */
       double best = 1e300;
+      int src = 0;
       if (P->geometry == 0) {
-        best = fmin(xv[1] - M->yv[0], M->yv[P->ny] - xv[1]);
+        double db = xv[1] - M->yv[0], dt = M->yv[P->ny] - xv[1];
+        best = fmin(db, dt);
+        src = (db <= dt ? 0 : P->nx * P->nz) + vi % P->nx + P->nx * (vk % P->nz);
       } else {
         for (int wk = 0; wk <= P->nz; ++wk)
           for (int wi = 0; wi <= P->nx; ++wi)
@@ -406,12 +412,16 @@ void *dgo_mesh_create(const dgo_params *P) {
               vertex_pos(M, wi, wj, wk, w);
               double d2 = (w[0] - xv[0]) * (w[0] - xv[0]) + (w[1] - xv[1]) * (w[1] - xv[1]) +
                           (w[2] - xv[2]) * (w[2] - xv[2]);
-              if (d2 < best) best = d2;
+              if (d2 < best) {
+                best = d2;
+                src = (wj ? P->nx * P->nz : 0) + wi % P->nx + P->nx * (wk % P->nz);
+              }
             }
         best = sqrt(best);
       }
       M->ywall[8 * e + v] = best;
       M->tauv[8 * e + v] = P->tau_w;
+      M->tsrc[8 * e + v] = src;
     }
   }
   return M;
@@ -433,7 +443,7 @@ void dgo_mesh_destroy(void *h) {
   if (!M) return;
   free(M->active);
   free(M->xv); free(M->yv); free(M->zv); free(M->X); free(M->enr); free(M->enr_cell);
-  free(M->ywall); free(M->tauv); free(M->dye); free(M->tau_cell); free(M);
+  free(M->ywall); free(M->tauv); free(M->tsrc); free(M->dye); free(M->tau_cell); free(M);
 }
 
 void dgo_mesh_info(void *h, long *np, long *nu, long *ne) {
@@ -1267,4 +1277,64 @@ int dgo_mass(void *h, const double *p, double *y) {
     ptab_free(&t);
   }
   return 0;
+}
+
+
+/* ----------------------------------------------------------------------------------------------
+ * Wall shear stress on the linear wall nodes (Sec. 3.2): for wall node B,
+ *   tau_w,B = || int_wall N_B tau_w dA || / int_wall N_B dA,   tau_w = rho nu (grad u_h) . n,
+ * the numerator integrated per component before the norm. N_B are the continuous bilinear
+ * functions of the wall vertices (periodic in x and z), u_h = ubar + utilde with the current
+ * enrichment, k+1 Gauss points per tangential direction on each wall face, rho = 1.
+ * Wall nodes: index wall * nx * nz + i + nx * k (wall 0 bottom, 1 top).
+ * Off-wall vertices of enriched cells carry the value of the wall node that defines their y_B.
+ * ---------------------------------------------------------------------------------------------- */
+int dgo_wall_nodes(void *h) {
+  omesh *M = (omesh *)h;
+  return 2 * M->P.nx * M->P.nz;
+}
+
+void dgo_set_tau_nodes(void *h, const double *tn) {
+  omesh *M = (omesh *)h;
+  for (int i = 0; i < 8 * M->ne; ++i) M->tauv[i] = tn[M->tsrc[i]];
+}
+
+int dgo_wall_shear(void *h, const double *u, double *tn) {
+  omesh *M = (omesh *)h;
+  const int nx = M->P.nx, ny = M->P.ny, nz = M->P.nz, nn = 2 * nx * nz, n1 = M->n1;
+  double *num = (double *)calloc((size_t)3 * nn, sizeof(double));
+  double *den = (double *)calloc((size_t)nn, sizeof(double));
+  double gx[MAXP], gw[MAXP];
+  dgo_gauss(n1, gx, gw);
+  ptab t; ptab_alloc(&t, M);
+  for (int wall = 0; wall < 2; ++wall)
+    for (int kz = 0; kz < nz; ++kz)
+      for (int i = 0; i < nx; ++i) {
+        const int j = wall ? ny - 1 : 0, c = cell_id(M, i, j, kz);
+        for (int q2 = 0; q2 < n1; ++q2)
+          for (int q0 = 0; q0 < n1; ++q0) {
+            double xi[3] = {gx[q0], wall ? 1.0 : 0.0, gx[q2]}, nrm[3];
+            tabulate(M, c, xi, &t);
+            double dA = face_geom(t.Ji, t.detJ, 1, wall, nrm) * gw[q0] * gw[q2];
+            vstate st; eval_vel(M, u, c, &t, &st);
+            double tw[3];
+            for (int a = 0; a < 3; ++a) {
+              tw[a] = 0.0;
+              for (int d = 0; d < 3; ++d) tw[a] += M->P.nu * (st.gb[a][d] + st.gt[a][d]) * nrm[d];
+            }
+            /* the four wall vertices of the face and their bilinear functions */
+            for (int b = 0; b < 4; ++b) {
+              int bi = b & 1, bk = b >> 1;
+              double Nb = (bi ? xi[0] : 1.0 - xi[0]) * (bk ? xi[2] : 1.0 - xi[2]);
+              int node = wall * nx * nz + (i + bi) % nx + nx * ((kz + bk) % nz);
+              for (int a = 0; a < 3; ++a) num[3 * node + a] += Nb * tw[a] * dA;
+              den[node] += Nb * dA;
+            }
+          }
+      }
+  ptab_free(&t);
+  for (int b = 0; b < nn; ++b)
+    tn[b] = sqrt(num[3 * b] * num[3 * b] + num[3 * b + 1] * num[3 * b + 1] + num[3 * b + 2] * num[3 * b + 2]) / den[b];
+  free(num); free(den);
+  return nn;
 }

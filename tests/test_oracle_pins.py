@@ -532,3 +532,75 @@ def test_l0_equals_l1_with_equal_weights(geometry):
     for e in range(0, ne, max(ne // 4, 1)):
         n0, n1 = m0.nut_cell(u0, e), m1.nut_cell(u1, e)
         assert np.abs(n0 - n1).max() <= 1e-13 * max(np.abs(n1).max(), 1e-300)
+
+
+# ---------------------------------------------------------------------------------------------
+# Wall shear stress on the linear wall nodes (Sec. 3.2): tau_w,B = |int N_B tau_w dA| / int N_B dA
+# ---------------------------------------------------------------------------------------------
+
+def test_wall_shear_of_parabolic_profile_is_exact():
+    """u = (1 - y^2) e_x (no enrichment): nu |du/dy| = 2 nu on both walls, so every node gets 2 nu
+    (a polynomial the Q_k space and the face rule hold exactly)."""
+    nu = 1e-3
+    m = O.Mesh(5, 4, 3, 2, n_layers=0, nu=nu)
+    assert m.n_wall_nodes == 2 * 5 * 3
+    u = _std_field(m, lambda x, y, z: 1 - y ** 2, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    tn = m.wall_shear(u)
+    assert np.abs(tn / (2 * nu) - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("enrich_l", [1, 0])
+def test_wall_shear_reproduces_the_enrichment_tau(enrich_l):
+    """ubar = 0, u~ = u_tau e_x with the prescribed tau_w = u_tau^2: at the wall psi = 0, psi'(0) = 1
+    and dy+/dy = u_tau / nu, so nu du/dy = u_tau^2 = tau_w at every wall point and node."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs(), enrich_l=enrich_l)
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, -1)[:, 0, :] = w.u_tau
+    tn = m.wall_shear(u)
+    assert np.abs(tn / w.tau_w - 1.0).max() < 1e-12
+
+
+def test_wall_shear_weights_nodes_with_the_hat_functions():
+    """u = (1 - y^2)(1 + a sin(2 pi x / L_x)) e_x: the traction 2 nu (1 + a sin) integrated against the
+    periodic hat of node x_i on a uniform grid of spacing h gives
+    2 nu (1 + a sin(kappa x_i) * 2 (1 - cos kappa h) / (kappa h)^2); the discrete field is the
+    degree-5 interpolant of the sine, hence the tolerance."""
+    nu, a, nx = 1e-3, 0.5, 16
+    m = O.Mesh(nx, 2, 2, 5, n_layers=0, nu=nu)
+    lx = 2 * math.pi
+    kap = 2 * math.pi / lx
+    u = _std_field(m, lambda x, y, z: (1 - y ** 2) * (1 + a * np.sin(kap * x)), lambda x, y, z: 0 * y,
+                   lambda x, y, z: 0 * y)
+    tn = m.wall_shear(u).reshape(2, 2, nx)            # [wall][k][i]
+    h = lx / nx
+    xi = np.arange(nx) * h
+    ref = 2 * nu * (1 + a * np.sin(kap * xi) * 2 * (1 - math.cos(kap * h)) / (kap * h) ** 2)
+    for wall in range(2):
+        for kz in range(2):
+            assert np.abs(tn[wall, kz] / ref - 1.0).max() < 1e-6
+
+
+def test_set_tau_nodes_interpolates_bilinearly_along_the_wall():
+    """Nodal tau_w: y+ at a point of a wall cell is y_h sqrt(tau_h) / nu with tau_h the bilinear
+    interpolant of the four wall nodes below it (off-wall vertices carry the value of the wall node
+    that defines their wall distance, the node of the same column on the channel)."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    tn = w.tau_w * (1.0 + 0.5 * I.uniform(3, m.n_wall_nodes, -1.0, 1.0))
+    m.set_tau_nodes(tn)
+    u = np.zeros(m.n_u)
+    nx, nz = 8, 8
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    for (i, j, kz) in [(0, 0, 0), (7, 0, 7), (3, 7, 5), (6, 7, 0)]:
+        c = i + nx * (j + 8 * kz)
+        wall = 0 if j == 0 else 1
+        T = tn.reshape(2, nz, nx)[wall]
+        ys = X[c, :, 1]
+        for xi in ([0.2, 0.3, 0.7], [0.9, 0.05, 0.4]):
+            r = m.eval_point(u, c, xi)
+            th = ((1 - xi[0]) * (1 - xi[2]) * T[kz, i] + xi[0] * (1 - xi[2]) * T[kz, (i + 1) % nx]
+                  + (1 - xi[0]) * xi[2] * T[(kz + 1) % nz, i] + xi[0] * xi[2] * T[(kz + 1) % nz, (i + 1) % nx])
+            yphys = ys.min() + xi[1] * (ys.max() - ys.min())
+            yp = (1.0 - abs(yphys)) * math.sqrt(th) / w.nu
+            assert abs(r["yplus"] / yp - 1.0) < 1e-12
