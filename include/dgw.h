@@ -93,7 +93,8 @@ typedef struct {
  * operator diagonal. Synchronises `stream`. *out receives a library-owned handle. */
 dgw_status dgw_mesh_create(const dgw_mesh_params *params, void *stream, dgw_mesh_t *out);
 dgw_status dgw_mesh_destroy(dgw_mesh_t mesh);
-/* n_p = nc (k+1)^3, n_u = 3 n_p + 24 n_enriched; hbm_bytes = device memory the mesh holds. */
+/* n_p = nc (k+1)^3, n_u = 3 n_p + 24 n_enriched (enrich_l = 1) or 3 n_p + 3 n_enriched
+ * (enrich_l = 0); hbm_bytes = device memory the mesh holds. */
 dgw_status dgw_mesh_info(dgw_mesh_t mesh, long *n_p, long *n_u, long *n_enriched, size_t *hbm_bytes);
 /* Physical positions of the pressure/velocity nodes, host buffer of 3*n_p doubles,
  * layout [c][(k+1)^3][xyz]. */
@@ -104,6 +105,23 @@ dgw_status dgw_mesh_node_coords(dgw_mesh_t mesh, double *xyz_host);
  * from the enrichment part of u_dev (FP64, n_u doubles). The values stay frozen for all later
  * viscous applies until the next call. Before the first call nu_t = 0. */
 dgw_status dgw_update_eddy_viscosity(dgw_mesh_t mesh, const double *u_dev, void *stream);
+
+/* Wall shear stress on the linear wall nodes (Sec. 3.2):
+ *   tau_w,B = | int_wall N_B rho nu (grad u_h) n dA | / int_wall N_B dA,  rho = 1,
+ * the numerator integrated per component before the norm; N_B are the continuous bilinear
+ * functions of the wall vertices (periodic in x and z) and u_h = ubar + utilde with the mesh's
+ * current enrichment; k+1 Gauss points per tangential direction on each wall face.
+ * u_dev: n_u doubles (device). tau_nodes_dev: 2 nx nz doubles (device, caller-owned), node
+ * index wall * nx * nz + i + nx * k (wall 0 = bottom). Does not change the mesh. Asynchronous. */
+dgw_status dgw_wall_shear_stress(dgw_mesh_t mesh, const double *u_dev, double *tau_nodes_dev, void *stream);
+
+/* Set the nodal wall shear stress (same layout, device buffer) and rebuild the wall tables: the
+ * enriched-cell vertices on a wall take their node's value, vertices off the wall the value of
+ * the wall node that defines their wall distance y_B; tau_w,h, y+, psi and grad psi follow at every
+ * enriched point (Sec. 3.2; the enrichment space changes). nu_t keeps its values until the next
+ * dgw_update_eddy_viscosity. Every value must be finite and > 0 (DGW_EINVAL otherwise); the
+ * check reads the buffer back, so the call synchronises `stream`. */
+dgw_status dgw_set_wall_shear_stress(dgw_mesh_t mesh, const double *tau_nodes_dev, void *stream);
 
 /* y = -L(q, p) (Sec. 4.2, SIPG Laplace term with the flux of eq. ipflux on interior and
  * periodic faces; homogeneous Neumann on walls). p, y: n_p values of type `prec`. */

@@ -68,6 +68,8 @@ static void fill_view(dgw_mesh *M, MeshView<T> &v) {
 
 using namespace dgw;
 
+void dgw_helm_free(dgw_mesh *M);
+
 extern "C" {
 
 const char *dgw_last_error(void) { return g_last_error.c_str(); }
@@ -148,14 +150,19 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     if (M->enr[c] >= 0) M->enr_cell[M->enr[c]] = c;
   M->ywall.resize(8 * std::max(ne, 1));
   M->tauv.resize(8 * std::max(ne, 1));
+  M->tsrc.resize(8 * std::max(ne, 1));
   M->dye.resize(std::max(ne, 1));
+  // each vertex also records the wall node (index wall * nx * nz + i + nx * k) that defines its
+  // distance; a nodal wall shear stress reaches the vertex from that node
   for (int e = 0; e < ne; ++e) {
-    const int c = M->enr_cell[e], i = c % nx, j = (c / nx) % ny;
+    const int c = M->enr_cell[e], i = c % nx, j = (c / nx) % ny, kz = c / (nx * ny);
     if (!curved) {
       for (int v = 0; v < 8; ++v) {
         const double y = M->yv[j + ((v >> 1) & 1)];
-        M->ywall[8 * e + v] = std::min(y - M->yv[0], M->yv[ny] - y);   // closest wall node
+        const double db = y - M->yv[0], dt = M->yv[ny] - y;
+        M->ywall[8 * e + v] = std::min(db, dt);   // closest wall node
         M->tauv[8 * e + v] = P->tau_w;
+        M->tsrc[8 * e + v] = (db <= dt ? 0 : nx * nz) + (i + (v & 1)) % nx + nx * ((kz + (v >> 2)) % nz);
       }
       M->dye[e] = M->hy[j];
       continue;
@@ -167,14 +174,20 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
       double xv, yv;
       bump_point(*P, nx, ny, i + (v & 1), j + ((v >> 1) & 1), &xv, &yv);
       double best = 1e300;
-      for (int wj = 0; wj <= ny; wj += ny)
-        for (int wi = 0; wi <= nx; ++wi) {
+      int src = 0;
+      for (int wi = 0; wi <= nx; ++wi)
+        for (int wj = 0; wj <= ny; wj += ny) {
           double xw, yw;
           bump_point(*P, nx, ny, wi, wj, &xw, &yw);
-          best = std::min(best, (xw - xv) * (xw - xv) + (yw - yv) * (yw - yv));
+          const double d2 = (xw - xv) * (xw - xv) + (yw - yv) * (yw - yv);
+          if (d2 < best) {
+            best = d2;
+            src = (wj ? nx * nz : 0) + wi % nx + nx * ((kz + (v >> 2)) % nz);
+          }
         }
       M->ywall[8 * e + v] = std::sqrt(best);
       M->tauv[8 * e + v] = P->tau_w;
+      M->tsrc[8 * e + v] = src;
     }
     double len = 0.0;
     for (int o = 0; o < 2; ++o) {
@@ -226,6 +239,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->enr_cell_dev = upload(M, M->enr_cell.data(), M->enr_cell.size(), s, &err);
   M->wall_ywall_dev = upload(M, M->ywall.data(), M->ywall.size(), s, &err);
   M->wall_tauv_dev = upload(M, M->tauv.data(), M->tauv.size(), s, &err);
+  M->tsrc_dev = upload(M, M->tsrc.data(), M->tsrc.size(), s, &err);
+  M->wall_mom_dev = dalloc<double>(M, (size_t)2 * nx * nz * 16, &err);
   M->dye_dev = upload(M, M->dye.data(), M->dye.size(), s, &err);
   const int qw = P->q_wall;
   for (int cls = 0; cls < 2; ++cls) {
@@ -332,6 +347,26 @@ dgw_status dgw_update_eddy_viscosity(dgw_mesh_t M, const double *u, void *stream
   return cuda_check(launch_eddy_viscosity(M, u, (cudaStream_t)stream), "dgw_update_eddy_viscosity");
 }
 
+
+dgw_status dgw_wall_shear_stress(dgw_mesh_t M, const double *u, double *tau_nodes, void *stream) {
+  if (!M || !u || !tau_nodes) return set_error(DGW_EINVAL, "dgw_wall_shear_stress: null argument");
+  return cuda_check(launch_wall_shear(M, u, tau_nodes, (cudaStream_t)stream), "dgw_wall_shear_stress");
+}
+
+dgw_status dgw_set_wall_shear_stress(dgw_mesh_t M, const double *tau_nodes, void *stream) {
+  if (!M || !tau_nodes) return set_error(DGW_EINVAL, "dgw_set_wall_shear_stress: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> h((size_t)2 * M->P.nx * M->P.nz);
+  cudaError_t e = cudaMemcpyAsync(h.data(), tau_nodes, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_set_wall_shear_stress");
+  for (double v : h)
+    if (!(v > 0.0) || !std::isfinite(v))
+      return set_error(DGW_EINVAL, "dgw_set_wall_shear_stress: every nodal value must be finite and > 0");
+  dgw_helm_free(M);   // the enriched mass blocks of the Helmholtz preconditioner change with tau_w
+  return cuda_check(launch_set_tau_nodes(M, tau_nodes, s), "dgw_set_wall_shear_stress");
+}
+
 dgw_status dgw_apply_laplace(dgw_mesh_t M, int prec, const void *p, void *y, void *stream) {
   if (!M || !p || !y) return set_error(DGW_EINVAL, "dgw_apply_laplace: null argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -370,7 +405,6 @@ dgw_status dgw_apply_viscous(dgw_mesh_t M, int prec, const void *u, void *y, voi
 }  // extern "C"
 
 void dgw_solver_free(dgw_mesh *M);
-void dgw_helm_free(dgw_mesh *M);
 
 namespace dgw {
 static void free_mesh(dgw_mesh *M) {

@@ -101,6 +101,7 @@ struct dgw_mesh {
   std::vector<int> enr_cell;    // enriched index -> cell
   std::vector<double> ywall;    // [ne][8] vertex wall distances
   std::vector<double> tauv;     // [ne][8] vertex wall shear stresses
+  std::vector<int> tsrc;        // [ne][8] wall node that defines the vertex's wall distance
   std::vector<double> dye;      // [ne] wall-normal width
   std::vector<double> cxn, cyn; // curved: nodal (x, y) per metric column [nx*ny][n*n]
   dgw::Basis<double> basis64;   // host copies of the basis tables
@@ -113,6 +114,8 @@ struct dgw_mesh {
   double *hy_dev64 = nullptr;
   int *enr_cell_dev = nullptr;
   double *wall_ywall_dev = nullptr, *wall_tauv_dev = nullptr;
+  int *tsrc_dev = nullptr;
+  double *wall_mom_dev = nullptr;   // [2 nx nz][16] per-wall-face moments of the tau_w update
   double *aux_vol = nullptr, *aux_face = nullptr;   // (y_h, y+) at linear-set points
   double *dye_dev = nullptr;
   double *diag64 = nullptr;     // Jacobi diagonal of the Laplace operator
@@ -209,6 +212,8 @@ template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s,
                              const LapEpi<T> *epi = nullptr);
 cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
+cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, cudaStream_t s);
+cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 

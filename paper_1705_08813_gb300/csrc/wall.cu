@@ -265,6 +265,134 @@ cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// Nodal wall shear stress (Sec. 3.2): tau_w,B = |int N_B nu (grad u_h) n dA| / int N_B dA over the
+// wall faces, N_B the continuous bilinear functions of the wall vertices (periodic in x and z),
+// k+1 Gauss points per tangential direction. One CTA per wall face (wall, i, k): every thread
+// takes one face point and its traction; the 16 moments of the face (numerator and denominator of
+// its four vertices) are summed over the points in a fixed order.
+__global__ void wall_shear_face_kernel(MeshView<double> m, const double *__restrict__ u, const double *__restrict__ wt_face,
+                                       int fpmax, double nu, double *__restrict__ out) {
+  const Basis<double> &B = *m.basis;
+  const int n = m.n1, n3 = n * n * n, np2 = n * n;
+  const int b = blockIdx.x, wall = b / (m.nx * m.nz), r = b % (m.nx * m.nz), i = r % m.nx, kz = r / m.nx;
+  const int j = wall ? m.ny - 1 : 0, c = i + m.nx * (j + m.ny * kz), side = wall;
+  __shared__ double su[3 * NMAX * NMAX * NMAX], ce[24], mom[NMAX * NMAX][16];
+  for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) su[t] = u[(size_t)c * 3 * n3 + t];
+  const int e = m.enr ? m.enr[c] : -1;
+  for (int t = threadIdx.x; t < 24; t += blockDim.x)
+    ce[t] = e >= 0 ? u[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : 0.0;
+  __syncthreads();
+  const double *S = B.S[QSET_LIN], *D = B.D[QSET_LIN], *de = B.dend[side];
+  const int jend = side ? n - 1 : 0;
+  for (int t = threadIdx.x; t < np2; t += blockDim.x) {
+    const int a1 = t % n, a2 = t / n;
+    const double xi[3] = {B.x[QSET_LIN][a1], (double)side, B.x[QSET_LIN][a2]};
+    double Ji[3][3], det;
+    if (m.geo == GEO_CURVED) {
+      load_rec(face_rec(m, B, metric_col(m, c), 1, side, QSET_LIN, QSET_LIN, a1, a2), Ji, det);
+    } else {
+      const double h[3] = {m.hx, m.hy[j], m.hz};
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) Ji[p][q] = p == q ? 1.0 / h[p] : 0.0;
+      det = h[0] * h[1] * h[2];
+    }
+    // reference gradient of the standard part (Gauss-Lobatto nodes: the face layer is node row jend)
+    double G[3][3];
+    for (int a = 0; a < 3; ++a) {
+      const double *ua = su + a * n3;
+      double g[3] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < n; ++l)
+        for (int ii = 0; ii < n; ++ii) {
+          const double ul = ua[ii + n * (jend + n * l)];
+          g[0] += D[a1 * n + ii] * S[a2 * n + l] * ul;
+          g[2] += S[a1 * n + ii] * D[a2 * n + l] * ul;
+          double s1 = 0.0;
+          for (int jj = 0; jj < n; ++jj) s1 += de[jj] * ua[ii + n * (jj + n * l)];
+          g[1] += S[a1 * n + ii] * S[a2 * n + l] * s1;
+        }
+      ref_to_phys(Ji, g, G[a]);
+    }
+    // enrichment: grad(psi N_v) = psi grad N_v + N_v grad psi, psi and grad psi from the wall table
+    if (e >= 0) {
+      const double *wt = wt_face + (((size_t)e * 6 + 2 + side) * fpmax + t) * WT;
+      double N[8], dN[8][3];
+      q1_weights(xi, N, dN);
+      for (int v = 0; v < 8; ++v) {
+        double gN[3];
+        ref_to_phys(Ji, dN[v], gN);
+        for (int a = 0; a < 3; ++a)
+          for (int d = 0; d < 3; ++d) G[a][d] += ce[a * 8 + v] * (wt[0] * gN[d] + N[v] * wt[1 + d]);
+      }
+    }
+    // outward unit normal and area weight of the face xi_1 = side (Nanson)
+    const double gl = sqrt(Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1] + Ji[1][2] * Ji[1][2]);
+    const double sg = side ? 1.0 : -1.0;
+    const double nrm[3] = {sg * Ji[1][0] / gl, sg * Ji[1][1] / gl, sg * Ji[1][2] / gl};
+    const double dA = fabs(det) * gl * B.w[QSET_LIN][a1] * B.w[QSET_LIN][a2];
+    double tw[3];
+    for (int a = 0; a < 3; ++a) tw[a] = nu * (G[a][0] * nrm[0] + G[a][1] * nrm[1] + G[a][2] * nrm[2]);
+    for (int v = 0; v < 4; ++v) {
+      const double Nb = ((v & 1) ? xi[0] : 1.0 - xi[0]) * ((v & 2) ? xi[2] : 1.0 - xi[2]);
+      for (int a = 0; a < 3; ++a) mom[t][v * 4 + a] = Nb * tw[a] * dA;
+      mom[t][v * 4 + 3] = Nb * dA;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    double acc = 0.0;
+    for (int t = 0; t < np2; ++t) acc += mom[t][threadIdx.x];
+    out[(size_t)b * 16 + threadIdx.x] = acc;
+  }
+}
+
+// tau_w,B per wall node from the moments of its (up to) four faces, in a fixed order
+__global__ void wall_shear_node_kernel(const double *__restrict__ mom, int nx, int nz, double *__restrict__ tau) {
+  const int nn = 2 * nx * nz;
+  for (int bnode = blockIdx.x * blockDim.x + threadIdx.x; bnode < nn; bnode += gridDim.x * blockDim.x) {
+    const int wall = bnode / (nx * nz), r = bnode % (nx * nz), i = r % nx, k = r / nx;
+    double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+      for (int da = 0; da < 2; ++da) {
+        const int fi = (i - da + nx) % nx, fk = (k - dk + nz) % nz;
+        const double *f = mom + ((size_t)wall * nx * nz + fi + nx * fk) * 16 + (da + 2 * dk) * 4;
+        for (int a = 0; a < 3; ++a) num[a] += f[a];
+        den += f[3];
+      }
+    tau[bnode] = sqrt(num[0] * num[0] + num[1] * num[1] + num[2] * num[2]) / den;
+  }
+}
+
+// vertex values of the enriched cells from the wall nodes that define their wall distances
+__global__ void tau_fill_kernel(const double *__restrict__ tau_nodes, const int *__restrict__ tsrc, int n,
+                                double *__restrict__ tauv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) tauv[i] = tau_nodes[tsrc[i]];
+}
+
+cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, cudaStream_t s) {
+  const int nf = 2 * M->P.nx * M->P.nz;
+  note_launches(2);
+  wall_shear_face_kernel<<<nf, 64, 0, s>>>(M->v64, u, M->v64.wt_face[0], M->v64.fpmax[0], M->P.nu, M->wall_mom_dev);
+  wall_shear_node_kernel<<<(nf + 255) / 256, 256, 0, s>>>(M->wall_mom_dev, M->P.nx, M->P.nz, tau_nodes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s) {
+  if (M->ne == 0) return cudaSuccess;
+  note_launch();
+  tau_fill_kernel<<<(8 * M->ne + 255) / 256, 256, 0, s>>>(tau_nodes, M->tsrc_dev, 8 * M->ne, M->wall_tauv_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_wall_tables(M, s);
+  if (e == cudaSuccess && M->has32)
+    for (int cls = 0; cls < 2 && e == cudaSuccess; ++cls) {
+      e = launch_to_float(M->v64.wt_vol[cls], const_cast<float *>(M->v32.wt_vol[cls]),
+                          (size_t)M->ne * M->v64.nvol[cls] * WT, s);
+      if (e == cudaSuccess)
+        e = launch_to_float(M->v64.wt_face[cls], const_cast<float *>(M->v32.wt_face[cls]),
+                            (size_t)M->ne * 6 * M->v64.fpmax[cls] * WT, s);
+    }
+  return e;
+}
+
 // float copies of the wall tables
 __global__ void to_float_kernel(const double *a, float *b, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)

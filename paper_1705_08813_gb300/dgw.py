@@ -20,7 +20,7 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
            "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
-           "dgw_apply_mass", "dgw_helmholtz_solve"]
+           "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     lib.dgw_pressure_solve_jacobi_noalloc.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int,
                                                       ctypes.POINTER(SolveInfo), vp]
     lib.dgw_apply_mass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.dgw_wall_shear_stress.argtypes = [vp, vp, vp, vp]
+    lib.dgw_set_wall_shear_stress.argtypes = [vp, vp, vp]
     lib.dgw_helmholtz_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.POINTER(HelmholtzOpts),
                                         ctypes.POINTER(SolveInfo), vp]
     lib.dgw_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
@@ -192,6 +194,25 @@ class Mesh:
         _check(self.lib.dgw_apply_viscous(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
                                           _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
         return y
+
+    @property
+    def n_wall_nodes(self) -> int:
+        """Linear wall nodes: 2 walls x nx x nz, index wall * nx * nz + i + nx * k."""
+        return 2 * self.params.nx * self.params.nz
+
+    def wall_shear_stress(self, u, tau_nodes, stream=None):
+        """Nodal wall shear stress tau_w,B of the velocity u (FP64) into tau_nodes (FP64 device)."""
+        import torch
+        _check(self.lib.dgw_wall_shear_stress(self.h, _ptr(u, torch.float64, self.n_u, "u"),
+                                              _ptr(tau_nodes, torch.float64, self.n_wall_nodes, "tau_nodes"),
+                                              _stream(stream)))
+        return tau_nodes
+
+    def set_wall_shear_stress(self, tau_nodes, stream=None):
+        """New nodal wall shear stress: rebuilds the enrichment's wall tables (synchronising)."""
+        import torch
+        _check(self.lib.dgw_set_wall_shear_stress(self.h, _ptr(tau_nodes, torch.float64, self.n_wall_nodes,
+                                                               "tau_nodes"), _stream(stream)))
 
     def mass(self, u, y, stream=None):
         _check(self.lib.dgw_apply_mass(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),

@@ -1,0 +1,123 @@
+"""GPU parity for the wall-shear-stress update (Sec. 3.2): the nodal tau_w,B computed from a velocity
+field against the FP64 oracle, every operator after a spatially varying nodal tau_w has been set
+(this exercises the grad tau_w,h terms of grad y+), and one full update cycle (tau_w from u, new
+wall tables, new nu_t, viscous apply) on channel and bump meshes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1705_08813_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def dgw():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1705_08813_gb300 import dgw as d
+    assert torch.cuda.is_available()
+    return d
+
+
+def _cmp(y, ref, tol, what):
+    y = np.asarray(y, dtype=np.float64)
+    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    ele = np.abs(y - ref).max() / np.abs(ref).max()
+    assert rel <= tol and ele <= tol, f"{what}: rel {rel:.3e} elem {ele:.3e}"
+
+
+KEYS = ("n_layers", "q_wall", "wall_law", "enrich_l")
+
+
+def _meshes(dgw, w, **kw):
+    om = O.Mesh(**w.mesh_kwargs(), **{k: v for k, v in kw.items() if k in KEYS})
+    gm = dgw.mesh_for(w, **kw)
+    assert (gm.n_p, gm.n_u, gm.n_e) == (om.n_p, om.n_u, om.n_e)
+    assert gm.n_wall_nodes == om.n_wall_nodes
+    return om, gm
+
+
+def _velocity(om, w, kw):
+    nef = 1 if kw.get("enrich_l", 1) == 0 else 8
+    u = I.workload_velocity(om.node_coords(), om.n_e, w, n_layers=kw.get("n_layers", 1), nef=nef)
+    u[3 * om.n_p:] += 0.2 * w.u_tau * I.uniform(w.seed, u.size - 3 * om.n_p, -1.0, 1.0, stream=71)
+    return u
+
+
+CASES = [
+    ("c1_q2_8x8x8", I.WORKLOADS["channel_q2_8x8x8"], {}),
+    ("ragged_q3_5x3x2_vandriest", I.Workload("r3", 5, 3, 2, 3, 395.0, 1.0 / 6000.0, seed=12), {"wall_law": 1}),
+    ("q4_two_layers_l0", I.Workload("r8", 3, 4, 3, 4, 590.0, 1.0 / 12000.0, seed=17), {"n_layers": 2, "enrich_l": 0}),
+    ("q2_single_cells_1x2x1", I.Workload("r6", 1, 2, 1, 2, 180.0, 1.0 / 3250.0, seed=15), {}),
+    ("q3_no_enrichment", I.Workload("r7", 4, 3, 3, 3, 180.0, 1.0 / 3250.0, seed=16), {"n_layers": 0}),
+    ("bump_q3_6x4x3", I.bump_workload("b2", 6, 4, 3, 3, seed=22), {}),
+    ("bump_q2_5x4x2_l0", I.bump_workload("b5", 5, 4, 2, 2, seed=25), {"enrich_l": 0}),
+]
+
+
+@pytest.mark.parametrize("name,w,kw", CASES, ids=[c[0] for c in CASES])
+def test_nodal_wall_shear_matches_oracle(dgw, name, w, kw):
+    om, gm = _meshes(dgw, w, **kw)
+    u = _velocity(om, w, kw)
+    ref = om.wall_shear(u)
+    tau = torch.empty(gm.n_wall_nodes, dtype=torch.float64, device="cuda")
+    _cmp(gm.wall_shear_stress(torch.tensor(u, device="cuda"), tau).cpu().numpy(), ref, TOL64, "tau_w,B")
+
+
+@pytest.mark.parametrize("name,w,kw", [c for c in CASES if c[2].get("n_layers", 1) > 0],
+                         ids=[c[0] for c in CASES if c[2].get("n_layers", 1) > 0])
+def test_operators_after_varying_nodal_tau(dgw, name, w, kw):
+    """A seeded nodal tau_w in [0.5, 1.5] tau_w: the enrichment space, y+ and nu_t all vary along the
+    wall; every operator must still match the oracle given the same nodal values."""
+    om, gm = _meshes(dgw, w, **kw)
+    dev = torch.device("cuda:0")
+    tn = w.tau_w * (1.0 + 0.5 * I.uniform(w.seed, om.n_wall_nodes, -1.0, 1.0, stream=72))
+    om.set_tau_nodes(tn)
+    gm.set_wall_shear_stress(torch.tensor(tn, device=dev))
+    u = _velocity(om, w, kw)
+    ud = torch.tensor(u, device=dev)
+    b = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
+    _cmp(gm.divergence(ud, b).cpu().numpy(), om.divergence(u), TOL64, "divergence")
+    y = torch.empty(gm.n_u, dtype=torch.float64, device=dev)
+    _cmp(gm.convective(ud, y).cpu().numpy(), om.convective(u), TOL64, "convective")
+    _cmp(gm.mass(ud, y).cpu().numpy(), om.vmass(u), TOL64, "mass")
+    gm.update_eddy_viscosity(ud)
+    v = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=73)
+    _cmp(gm.viscous(torch.tensor(v, device=dev), y).cpu().numpy(), om.viscous(u, v), TOL64, "viscous")
+    y32 = torch.empty(gm.n_u, dtype=torch.float32, device=dev)
+    _cmp(gm.viscous(torch.tensor(v, device=dev).float(), y32).cpu().numpy(), om.viscous(u, v), 2e-5, "viscous fp32")
+
+
+@pytest.mark.parametrize("wname", ["channel_q2_8x8x8", "bump_q3"])
+def test_update_cycle_matches_oracle(dgw, wname):
+    """tau_w,B from u, set as the new nodal tau_w, nu_t from u in the new space, then the wall shear
+    of the same u in the new space and a viscous apply - both sides run the same cycle."""
+    w = I.WORKLOADS["channel_q2_8x8x8"] if wname.startswith("channel") else I.bump_workload("b3", 6, 4, 2, 3, seed=26)
+    om, gm = _meshes(dgw, w)
+    dev = torch.device("cuda:0")
+    u = _velocity(om, w, {})
+    ud = torch.tensor(u, device=dev)
+    tau = torch.empty(gm.n_wall_nodes, dtype=torch.float64, device=dev)
+    gm.wall_shear_stress(ud, tau)
+    om.set_tau_nodes(om.wall_shear(u))
+    gm.set_wall_shear_stress(tau)
+    gm.update_eddy_viscosity(ud)
+    _cmp(gm.wall_shear_stress(ud, tau).cpu().numpy(), om.wall_shear(u), TOL64, "tau after update")
+    y = torch.empty(gm.n_u, dtype=torch.float64, device=dev)
+    _cmp(gm.viscous(ud, y).cpu().numpy(), om.viscous(u, u), TOL64, "viscous after update")
+
+
+def test_set_wall_shear_rejects_non_positive(dgw):
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    gm = dgw.mesh_for(w)
+    tn = torch.full((gm.n_wall_nodes,), w.tau_w, dtype=torch.float64, device="cuda")
+    tn[3] = 0.0
+    with pytest.raises(dgw.DGWError):
+        gm.set_wall_shear_stress(tn)
+    tn[3] = float("nan")
+    with pytest.raises(dgw.DGWError):
+        gm.set_wall_shear_stress(tn)
