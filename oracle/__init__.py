@@ -80,6 +80,8 @@ def _load():
         lib.dgo_set_tau_nodes.argtypes = [vp, dp]
         lib.dgo_wall_shear.argtypes = [vp, dp, dp]
         lib.dgo_wall_shear.restype = ctypes.c_int
+        lib.dgo_project.argtypes = [vp, dp, dp, dp]
+        lib.dgo_project.restype = ctypes.c_int
         lib.dgo_volume.argtypes = [vp]
         lib.dgo_volume.restype = ctypes.c_double
         lib.dgo_psi_spalding.argtypes = [ctypes.c_double, dp]
@@ -256,6 +258,16 @@ class Mesh:
         tn = np.ascontiguousarray(tau_nodes, dtype=np.float64)
         assert tn.size == self.n_wall_nodes
         self.lib.dgo_set_tau_nodes(self.h, _ptr(tn))
+
+    def project(self, tau_new: np.ndarray, u_old: np.ndarray) -> np.ndarray:
+        """Cell-wise L2 projection of u_old (current space) onto the space of the nodal wall shear
+        stress tau_new (eq. l2); the mesh keeps tau_new afterwards."""
+        tn = np.ascontiguousarray(tau_new, dtype=np.float64)
+        u = np.ascontiguousarray(u_old, dtype=np.float64); out = np.zeros(self.n_u)
+        assert tn.size == self.n_wall_nodes
+        if self.lib.dgo_project(self.h, _ptr(tn), _ptr(u), _ptr(out)) != 0:
+            raise RuntimeError("singular cell system in the L2 projection")
+        return out
 
     def nut_cell(self, u: np.ndarray, e: int) -> np.ndarray:
         u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(4096)

@@ -1338,3 +1338,117 @@ int dgo_wall_shear(void *h, const double *u, double *tn) {
   free(num); free(den);
   return nn;
 }
+
+/* ----------------------------------------------------------------------------------------------
+ * Cell-wise L2 projection onto the space of a new nodal wall shear stress (Sec. 3.2, eq. l2):
+ * in every enriched cell, u_new in V_new with int v . u_new = int v . u_old for all v in V_new
+ * (per component; V_new = standard Q_k plus psi_new N^l), integrated with the cell's velocity
+ * point set (k+1 points in-plane, q_w wall-normal). The other cells' spaces do not change and
+ * their coefficients are copied. The cell system is solved by Gaussian elimination with partial
+ * pivoting. The mesh keeps tau_new afterwards.
+ * ---------------------------------------------------------------------------------------------- */
+static int solve_dense(int N, double *A, double *B, int nrhs) {
+  /* A: N x N row-major, B: N x nrhs row-major; overwritten with the solution */
+  for (int k = 0; k < N; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < N; ++i)
+      if (fabs(A[(size_t)i * N + k]) > fabs(A[(size_t)piv * N + k])) piv = i;
+    if (A[(size_t)piv * N + k] == 0.0) return -1;
+    if (piv != k) {
+      for (int j = 0; j < N; ++j) {
+        double t = A[(size_t)k * N + j]; A[(size_t)k * N + j] = A[(size_t)piv * N + j]; A[(size_t)piv * N + j] = t;
+      }
+      for (int r = 0; r < nrhs; ++r) {
+        double t = B[(size_t)k * nrhs + r]; B[(size_t)k * nrhs + r] = B[(size_t)piv * nrhs + r]; B[(size_t)piv * nrhs + r] = t;
+      }
+    }
+    for (int i = k + 1; i < N; ++i) {
+      double f = A[(size_t)i * N + k] / A[(size_t)k * N + k];
+      if (f == 0.0) continue;
+      for (int j = k; j < N; ++j) A[(size_t)i * N + j] -= f * A[(size_t)k * N + j];
+      for (int r = 0; r < nrhs; ++r) B[(size_t)i * nrhs + r] -= f * B[(size_t)k * nrhs + r];
+    }
+  }
+  for (int k = N - 1; k >= 0; --k)
+    for (int r = 0; r < nrhs; ++r) {
+      double s = B[(size_t)k * nrhs + r];
+      for (int j = k + 1; j < N; ++j) s -= A[(size_t)k * N + j] * B[(size_t)j * nrhs + r];
+      B[(size_t)k * nrhs + r] = s / A[(size_t)k * N + k];
+    }
+  return 0;
+}
+
+int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_new) {
+  omesh *M = (omesh *)h;
+  const int n3 = M->n1 * M->n1 * M->n1, nef = M->nef, N = n3 + nef;
+  memcpy(u_new, u_old, sizeof(double) * M->nu);
+  if (M->ne == 0) { dgo_set_tau_nodes(h, tau_new); return 0; }
+  /* old field at the points of every enriched cell */
+  int nq[3];
+  cell_points(M, M->enr_cell[0], OP_LINEAR, nq);
+  const int npts = nq[0] * nq[1] * nq[2];
+  double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+  dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+  double *uold = (double *)malloc(sizeof(double) * (size_t)M->ne * npts * 3);
+  int status = 0;
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+#pragma omp for schedule(dynamic, 1)
+    for (int e = 0; e < M->ne; ++e) {
+      int c = M->enr_cell[e], q = 0;
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0, ++q) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            vstate s; eval_vel(M, u_old, c, &t, &s);
+            for (int a = 0; a < 3; ++a) uold[((size_t)e * npts + q) * 3 + a] = s.ub[a] + s.ut[a];
+          }
+    }
+    ptab_free(&t);
+  }
+  dgo_set_tau_nodes(h, tau_new);
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double *A = (double *)malloc(sizeof(double) * (size_t)N * N);
+    double *B = (double *)malloc(sizeof(double) * (size_t)N * 3);
+    double *phi = (double *)malloc(sizeof(double) * N);
+#pragma omp for schedule(dynamic, 1)
+    for (int e = 0; e < M->ne; ++e) {
+      int c = M->enr_cell[e], q = 0;
+      memset(A, 0, sizeof(double) * (size_t)N * N);
+      memset(B, 0, sizeof(double) * (size_t)N * 3);
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0, ++q) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            for (int i = 0; i < n3; ++i) phi[i] = t.phi[i];
+            for (int v = 0; v < nef; ++v) phi[n3 + v] = t.ephi[v];
+            for (int i = 0; i < N; ++i) {
+              double wi = dV * phi[i];
+              for (int j = 0; j < N; ++j) A[(size_t)i * N + j] += wi * phi[j];
+              for (int a = 0; a < 3; ++a) B[(size_t)i * 3 + a] += wi * uold[((size_t)e * npts + q) * 3 + a];
+            }
+          }
+      if (solve_dense(N, A, B, 3) != 0) {
+#pragma omp atomic write
+        status = -1;
+        continue;
+      }
+      for (int a = 0; a < 3; ++a) {
+        double *uc = u_new + ((size_t)c * 3 + a) * n3;
+        for (int i = 0; i < n3; ++i) uc[i] = B[(size_t)i * 3 + a];
+        double *ue = u_new + 3L * M->np + ((size_t)e * 3 + a) * nef;
+        for (int v = 0; v < nef; ++v) ue[v] = B[(size_t)(n3 + v) * 3 + a];
+      }
+    }
+    free(A); free(B); free(phi);
+    ptab_free(&t);
+  }
+  free(uold);
+  return status;
+}

@@ -604,3 +604,65 @@ def test_set_tau_nodes_interpolates_bilinearly_along_the_wall():
             yphys = ys.min() + xi[1] * (ys.max() - ys.min())
             yp = (1.0 - abs(yphys)) * math.sqrt(th) / w.nu
             assert abs(r["yplus"] / yp - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# Cell-wise L2 projection onto the space of a new wall shear stress (Sec. 3.2, eq. l2). The cell
+# systems are ill-conditioned (psi N_B is close to the polynomials where the cell spans few wall
+# units), so the pins compare functions in the L2 norm, not coefficients.
+# ---------------------------------------------------------------------------------------------
+
+def _l2_rel(m, a, b):
+    d = a - b
+    return math.sqrt(abs(d @ m.vmass(d)) / (b @ m.vmass(b)))
+
+
+def test_projection_onto_the_same_space_is_the_identity():
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    u = I.workload_velocity(m.node_coords(), m.n_e, w)
+    u[3 * m.n_p:] += 0.2 * w.u_tau * I.uniform(4, 24 * m.n_e, -1, 1)
+    un = m.project(np.full(m.n_wall_nodes, w.tau_w), u)
+    assert _l2_rel(m, un, u) < 1e-12
+    nw = [c for c in range(m.nc) if (c // 8) % 8 not in (0, 7)]     # cells off the wall: copied
+    std = lambda v: v[: 3 * m.n_p].reshape(m.nc, -1)[nw]
+    assert np.array_equal(std(un), std(u))
+
+
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_projection_keeps_a_polynomial_field(geometry):
+    """A standard Q_k field (no enrichment part) lies in every enriched space: projecting it onto the
+    space of a varying nodal tau_w leaves the function unchanged."""
+    if geometry:
+        w = I.bump_workload("bp", 6, 4, 2, 3, seed=31)
+    else:
+        w = I.Workload("pp", 4, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=32)
+    m = O.Mesh(**w.mesh_kwargs())
+    u = _std_field(m, lambda x, y, z: 1 + y ** 3 - 0.5 * x * y, lambda x, y, z: y * z, lambda x, y, z: x ** 2)
+    tn = w.tau_w * (1.0 + 0.6 * I.uniform(5, m.n_wall_nodes, -1, 1))
+    un = m.project(tn, u)          # the mesh now holds tn, so vmass measures in the new space
+    assert _l2_rel(m, un, u) < 1e-11
+
+
+def test_projection_matches_the_integrals_of_the_old_wall_law():
+    """u_old = psi_old(y+) e_x (ubar = 0, all weights 1) with tau_old, projected onto tau_new = 2 tau_old:
+    the Galerkin conditions for v = 1 and v = psi_new give int u_new = int psi_old and
+    int u_new psi_new = int psi_old psi_new over the wall cells, against adaptive quadrature."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 1.0
+    un = m.project(np.full(m.n_wall_nodes, 2.0 * w.tau_w), u)
+    y = m.vmass(un)
+    ut_old, ut_new = w.u_tau, math.sqrt(2.0) * w.u_tau
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    area = 2 * (2 * math.pi * math.pi)
+    ps = lambda s, ut: O.psi_spalding(s * ut / w.nu)[0]
+    r1 = area * quad(lambda s: ps(s, ut_old), 0.0, dy, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    r2 = area * quad(lambda s: ps(s, ut_old) * ps(s, ut_new), 0.0, dy, epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    std = y[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    ye = y[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    assert abs(std[:, 0, :].sum() / r1 - 1.0) < 1e-6
+    assert abs(ye[:, 0, :].sum() / r2 - 1.0) < 1e-6
+    assert np.abs(un[: 3 * m.n_p].reshape(m.nc, 3, -1)[:, 1:, :]).max() == 0.0
