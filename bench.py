@@ -532,6 +532,47 @@ def run_helmholtz(args):
     return 0
 
 
+def run_wall_update(args):
+    """Adaptive part of the wall model at the start of a time step (Sec. 3.2): nodal tau_w,B from the
+    velocity, the cell-wise L2 projection of the velocity onto the new enrichment space, and nu_t in
+    the new space; each timed with CUDA events on the workload (median of --steps runs)."""
+    import torch
+    from paper_1705_08813_gb300 import dgw, inputs as I
+    torch.cuda.set_device(0)
+    w = I.WORKLOADS[args.workload]
+    m = dgw.mesh_for(w, enrich_l=args.enrich_l)
+    nef = 8 if args.enrich_l == 1 else 1
+    u = torch.from_numpy(I.workload_velocity(m.node_coords(), m.n_e, w, nef=nef)).cuda()
+    tau = torch.empty(m.n_wall_nodes, dtype=torch.float64, device="cuda")
+    u2 = torch.empty_like(u)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    rec = {"tau_ms": [], "project_ms": [], "nut_ms": []}
+    for it in range(args.warmup + max(1, args.steps)):
+        torch.cuda.synchronize()
+        ev[0].record()
+        m.wall_shear_stress(u, tau)
+        ev[1].record()
+        m.project_velocity(tau, u, u2)
+        ev[2].record()
+        m.update_eddy_viscosity(u2)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            rec["tau_ms"].append(ev[0].elapsed_time(ev[1]))
+            rec["project_ms"].append(ev[1].elapsed_time(ev[2]))
+            rec["nut_ms"].append(ev[2].elapsed_time(ev[3]))
+        u, u2 = u2, u
+    tn = tau.cpu().numpy()
+    out = {"metric": "wall-model update: tau_w,B, L2 projection onto the new space, nu_t (ms)",
+           "workload": w.name, "enrich_l": args.enrich_l, "n_u": m.n_u, "n_enriched": m.n_e,
+           "tau_w_range": [float(tn.min()), float(tn.max())]}
+    for k, v in rec.items():
+        out[k] = statistics.median(v)
+    out["total_ms"] = out["tau_ms"] + out["project_ms"] + out["nut_ms"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_profile_kernel(args):
     """A few launches of one operator kernel on a channel of the given size (used for ncu captures:
     a small number of launches, inputs larger than L2 when the mesh is large enough)."""
@@ -595,7 +636,9 @@ def main():
     ap.add_argument("--helmholtz", action="store_true", help="time the mass apply and the Helmholtz solve")
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--restart", type=int, default=30)
-    ap.add_argument("--enrich-l", type=int, default=1, choices=[0, 1], help="enrichment weight degree (--helmholtz)")
+    ap.add_argument("--enrich-l", type=int, default=1, choices=[0, 1],
+                    help="enrichment weight degree (--helmholtz, --wall-update)")
+    ap.add_argument("--wall-update", action="store_true", help="time the tau_w update and the L2 projection")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["laplace64", "laplace32", "divergence", "convective", "convective32", "viscous",
                              "viscous32"])
@@ -609,6 +652,8 @@ def main():
         return run_serving(args)
     if args.helmholtz:
         return run_helmholtz(args)
+    if args.wall_update:
+        return run_wall_update(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -123,6 +123,21 @@ dgw_status dgw_wall_shear_stress(dgw_mesh_t mesh, const double *u_dev, double *t
  * check reads the buffer back, so the call synchronises `stream`. */
 dgw_status dgw_set_wall_shear_stress(dgw_mesh_t mesh, const double *tau_nodes_dev, void *stream);
 
+/* Move the velocity into the space of a new nodal wall shear stress (Sec. 3.2, eq. l2): sets
+ * tau_nodes_dev as dgw_set_wall_shear_stress does and writes the cell-wise L2 projection of u_old
+ * (a vector of the space before the call) onto the new space into u_new: in every enriched cell
+ * (v, u_new) = (v, u_old) for all v of the new space, per component, with the velocity point set
+ * (k+1 Gauss points in-plane, q_w wall-normal); other cells are copied. The cell systems are
+ * solved by Cholesky factorisation in FP64. u_old, u_new: n_u doubles (device, caller-owned; they
+ * may be the same buffer). The first call allocates scratch of n_enriched ((k+1)^3 + nef)^2
+ * doubles. Synchronises `stream`. DGW_EINVAL for a non-positive or non-finite nodal value or for
+ * q_wall < k+3 (l = 1) / k+2 (l = 0), where the wall-normal factor of a wall cell's space has more
+ * functions than points and the cell mass matrix is singular;
+ * DGW_EDEVICE if a cell matrix is not numerically positive definite (the enrichment and the
+ * polynomials are too close to independent there: switch the enrichment off). */
+dgw_status dgw_project_velocity(dgw_mesh_t mesh, const double *tau_nodes_dev, const double *u_old_dev,
+                                double *u_new_dev, void *stream);
+
 /* y = -L(q, p) (Sec. 4.2, SIPG Laplace term with the flux of eq. ipflux on interior and
  * periodic faces; homogeneous Neumann on walls). p, y: n_p values of type `prec`. */
 dgw_status dgw_apply_laplace(dgw_mesh_t mesh, int prec, const void *p, void *y, void *stream);

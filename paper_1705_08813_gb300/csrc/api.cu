@@ -353,18 +353,45 @@ dgw_status dgw_wall_shear_stress(dgw_mesh_t M, const double *u, double *tau_node
   return cuda_check(launch_wall_shear(M, u, tau_nodes, (cudaStream_t)stream), "dgw_wall_shear_stress");
 }
 
-dgw_status dgw_set_wall_shear_stress(dgw_mesh_t M, const double *tau_nodes, void *stream) {
-  if (!M || !tau_nodes) return set_error(DGW_EINVAL, "dgw_set_wall_shear_stress: null argument");
-  cudaStream_t s = (cudaStream_t)stream;
+// reads the nodal values back and checks that each is finite and > 0 (synchronises s)
+static dgw_status check_tau_nodes(dgw_mesh_t M, const double *tau_nodes, cudaStream_t s, const char *name) {
   std::vector<double> h((size_t)2 * M->P.nx * M->P.nz);
   cudaError_t e = cudaMemcpyAsync(h.data(), tau_nodes, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_check(e, "dgw_set_wall_shear_stress");
+  if (e != cudaSuccess) return cuda_check(e, name);
   for (double v : h)
     if (!(v > 0.0) || !std::isfinite(v))
-      return set_error(DGW_EINVAL, "dgw_set_wall_shear_stress: every nodal value must be finite and > 0");
+      return set_error(DGW_EINVAL, std::string(name) + ": every nodal value must be finite and > 0");
+  return DGW_OK;
+}
+
+dgw_status dgw_set_wall_shear_stress(dgw_mesh_t M, const double *tau_nodes, void *stream) {
+  if (!M || !tau_nodes) return set_error(DGW_EINVAL, "dgw_set_wall_shear_stress: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  dgw_status st = check_tau_nodes(M, tau_nodes, s, "dgw_set_wall_shear_stress");
+  if (st != DGW_OK) return st;
   dgw_helm_free(M);   // the enriched mass blocks of the Helmholtz preconditioner change with tau_w
   return cuda_check(launch_set_tau_nodes(M, tau_nodes, s), "dgw_set_wall_shear_stress");
+}
+
+dgw_status dgw_project_velocity(dgw_mesh_t M, const double *tau_nodes, const double *u_old, double *u_new,
+                                void *stream) {
+  if (!M || !tau_nodes || !u_old || !u_new) return set_error(DGW_EINVAL, "dgw_project_velocity: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the wall-normal factor of a wall cell's space has k+1 polynomials and 2 (l = 1) or 1 (l = 0)
+  // enriched functions; with fewer wall-normal points the discrete cell mass matrix is singular
+  if (M->ne > 0 && M->P.q_wall < M->n1 + (M->nef == 8 ? 2 : 1))
+    return set_error(DGW_EINVAL, "dgw_project_velocity: q_wall must be at least k+3 (l = 1) or k+2 (l = 0) for "
+                                 "the cell mass matrices to be regular");
+  dgw_status st = check_tau_nodes(M, tau_nodes, s, "dgw_project_velocity");
+  if (st != DGW_OK) return st;
+  dgw_helm_free(M);
+  int bad = -1;
+  st = cuda_check(launch_projection(M, tau_nodes, u_old, u_new, s, &bad), "dgw_project_velocity");
+  if (st == DGW_OK && bad >= 0)
+    return set_error(DGW_EDEVICE, "dgw_project_velocity: the mass matrix of cell " + std::to_string(bad) +
+                                      " is not numerically positive definite in the new space");
+  return st;
 }
 
 dgw_status dgw_apply_laplace(dgw_mesh_t M, int prec, const void *p, void *y, void *stream) {

@@ -116,6 +116,9 @@ struct dgw_mesh {
   double *wall_ywall_dev = nullptr, *wall_tauv_dev = nullptr;
   int *tsrc_dev = nullptr;
   double *wall_mom_dev = nullptr;   // [2 nx nz][16] per-wall-face moments of the tau_w update
+  double *proj_A = nullptr;         // L2 projection scratch: [ne][N][N] cell matrices (lazily allocated)
+  double *proj_P = nullptr;         // [ne][points][3] old field at the points
+  int *proj_err = nullptr;
   double *aux_vol = nullptr, *aux_face = nullptr;   // (y_h, y+) at linear-set points
   double *dye_dev = nullptr;
   double *diag64 = nullptr;     // Jacobi diagonal of the Laplace operator
@@ -214,6 +217,8 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
 cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, cudaStream_t s);
 cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s);
+cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, const double *u_old, double *u_new, cudaStream_t s,
+                              int *bad_cell);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 

@@ -20,7 +20,8 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
            "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
-           "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress"]
+           "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
+           "dgw_project_velocity"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
     lib.dgw_apply_mass.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_wall_shear_stress.argtypes = [vp, vp, vp, vp]
     lib.dgw_set_wall_shear_stress.argtypes = [vp, vp, vp]
+    lib.dgw_project_velocity.argtypes = [vp, vp, vp, vp, vp]
     lib.dgw_helmholtz_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.POINTER(HelmholtzOpts),
                                         ctypes.POINTER(SolveInfo), vp]
     lib.dgw_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
@@ -213,6 +215,14 @@ class Mesh:
         import torch
         _check(self.lib.dgw_set_wall_shear_stress(self.h, _ptr(tau_nodes, torch.float64, self.n_wall_nodes,
                                                                "tau_nodes"), _stream(stream)))
+
+    def project_velocity(self, tau_nodes, u_old, u_new, stream=None):
+        """Set a new nodal wall shear stress and L2-project u_old (old space) into u_new (new space)."""
+        import torch
+        _check(self.lib.dgw_project_velocity(self.h, _ptr(tau_nodes, torch.float64, self.n_wall_nodes, "tau_nodes"),
+                                             _ptr(u_old, torch.float64, self.n_u, "u_old"),
+                                             _ptr(u_new, torch.float64, self.n_u, "u_new"), _stream(stream)))
+        return u_new
 
     def mass(self, u, y, stream=None):
         _check(self.lib.dgw_apply_mass(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),

@@ -121,3 +121,80 @@ def test_set_wall_shear_rejects_non_positive(dgw):
     tn[3] = float("nan")
     with pytest.raises(dgw.DGWError):
         gm.set_wall_shear_stress(tn)
+
+
+def _l2(om, d, ref):
+    """relative L2 norm of d against ref in the mesh's current (new) space"""
+    return float(np.sqrt(abs(d @ om.vmass(d)) / (ref @ om.vmass(ref))))
+
+
+PROJ_CASES = [
+    ("c1_q2_8x8x8", I.WORKLOADS["channel_q2_8x8x8"], {}),
+    ("q4_two_layers_l0", I.Workload("r8", 3, 4, 3, 4, 590.0, 1.0 / 12000.0, seed=17), {"n_layers": 2, "enrich_l": 0}),
+    ("ragged_q3_vandriest_qwall6", I.Workload("r3", 5, 3, 2, 3, 395.0, 1.0 / 6000.0, seed=12),
+     {"wall_law": 1, "q_wall": 6}),
+    ("bump_q3_6x4x3", I.bump_workload("b2", 6, 4, 3, 3, seed=22), {}),
+]
+
+
+@pytest.mark.parametrize("name,w,kw", PROJ_CASES, ids=[c[0] for c in PROJ_CASES])
+def test_projection_matches_oracle(dgw, name, w, kw):
+    """Cell-wise L2 projection onto a varying new nodal tau_w (eq. l2): the cells off the wall are
+    copied bit for bit; in the wall cells the projected functions agree in the L2 norm (the cell
+    systems are ill-conditioned, so coefficients are not compared), and so do their Galerkin
+    moments M_new u_new."""
+    om, gm = _meshes(dgw, w, **kw)
+    dev = torch.device("cuda:0")
+    u = _velocity(om, w, kw)
+    tn = w.tau_w * (1.0 + 0.5 * I.uniform(w.seed, om.n_wall_nodes, -1.0, 1.0, stream=74))
+    ref = om.project(tn, u)
+    un = torch.empty(gm.n_u, dtype=torch.float64, device=dev)
+    gm.project_velocity(torch.tensor(tn, device=dev), torch.tensor(u, device=dev), un)
+    got = un.cpu().numpy()
+    wall = np.zeros(om.nc, dtype=bool)
+    L = kw.get("n_layers", 1)
+    for c in range(om.nc):
+        j = (c // w.nx) % w.ny
+        wall[c] = j < L or j >= w.ny - L
+    std = lambda v: v[: 3 * om.n_p].reshape(om.nc, -1)
+    assert np.array_equal(std(got)[~wall], std(u)[~wall])
+    # two backward-stable FP64 solves (Cholesky here, pivoted LU in the oracle) of a cell system with
+    # condition number kappa differ by about N eps sqrt(kappa) in the energy norm; the wall cells of
+    # these meshes reach kappa ~ 1e10 (N <= 133 unknowns), hence 1e-9 for the functions
+    l2 = _l2(om, got - ref, ref)
+    mg, mr = om.vmass(got), om.vmass(ref)
+    mom = np.linalg.norm(mg - mr) / np.linalg.norm(mr)
+    assert l2 < 1e-9 and mom < 1e-10, (l2, mom)
+    # the GPU mesh now holds the new space: the mass operators of both sides agree on the result
+    y = torch.empty_like(un)
+    _cmp(gm.mass(un, y).cpu().numpy(), mg, 1e-12, "mass in the new space")
+
+
+def test_projection_in_place_equals_out_of_place(dgw):
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    dev = torch.device("cuda:0")
+    g1, g2 = dgw.mesh_for(w), dgw.mesh_for(w)
+    om = O.Mesh(**w.mesh_kwargs())
+    u = torch.tensor(_velocity(om, w, {}), device=dev)
+    tn = torch.tensor(w.tau_w * (1.0 + 0.3 * I.uniform(9, g1.n_wall_nodes, -1.0, 1.0)), device=dev)
+    out = torch.empty_like(u)
+    g1.project_velocity(tn, u, out)
+    v = u.clone()
+    g2.project_velocity(tn, v, v)
+    assert torch.equal(out, v)
+
+
+def test_projection_rejects_non_positive_tau_and_singular_cell_spaces(dgw):
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    gm = dgw.mesh_for(w)
+    u = torch.zeros(gm.n_u, dtype=torch.float64, device="cuda")
+    tn = torch.full((gm.n_wall_nodes,), -1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgw.DGWError):
+        gm.project_velocity(tn, u, u)
+    # k = 3 with l = 1 has 6 wall-normal functions: 5 points cannot separate them
+    w3 = I.Workload("r3", 5, 3, 2, 3, 395.0, 1.0 / 6000.0, seed=12)
+    g3 = dgw.mesh_for(w3, q_wall=5)
+    u3 = torch.zeros(g3.n_u, dtype=torch.float64, device="cuda")
+    t3 = torch.full((g3.n_wall_nodes,), w3.tau_w, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgw.DGWError):
+        g3.project_velocity(t3, u3, u3)
