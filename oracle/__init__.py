@@ -81,6 +81,9 @@ def _load():
         lib.dgo_wall_shear.argtypes = [vp, dp, dp]
         lib.dgo_wall_shear.restype = ctypes.c_int
         lib.dgo_project.argtypes = [vp, dp, dp, dp]
+        lib.dgo_set_switch.argtypes = [vp, ctypes.c_double]
+        lib.dgo_active.argtypes = [vp, ip]
+        lib.dgo_active.restype = ctypes.c_int
         lib.dgo_project.restype = ctypes.c_int
         lib.dgo_volume.argtypes = [vp]
         lib.dgo_volume.restype = ctypes.c_double
@@ -268,6 +271,17 @@ class Mesh:
         if self.lib.dgo_project(self.h, _ptr(tn), _ptr(u), _ptr(out)) != 0:
             raise RuntimeError("singular cell system in the L2 projection")
         return out
+
+    def set_switch(self, yplus_off: float) -> None:
+        """Switch the wall model off in every wall column whose wall-nearest cell has y+ < yplus_off at
+        all of its points (0: never); re-evaluated whenever tau_w changes."""
+        self.lib.dgo_set_switch(self.h, float(yplus_off))
+
+    def active(self) -> np.ndarray:
+        """Per enriched index: 1 if the enrichment is switched on."""
+        out = np.zeros(max(self.n_e, 1), dtype=np.int32)
+        self.lib.dgo_active(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return out[: self.n_e]
 
     def nut_cell(self, u: np.ndarray, e: int) -> np.ndarray:
         u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(4096)

@@ -74,6 +74,8 @@ typedef struct {
   double *ywall;              /* per enriched cell: 8 vertex wall distances */
   double *tauv;               /* per enriched cell: 8 vertex wall shear stresses */
   int *tsrc;                  /* per enriched cell: 8 wall-node indices (the node that defines y_B) */
+  int *slot;                  /* cell -> enriched index whether switched on or off (-1: not a wall cell) */
+  double yp_off;              /* switch-off threshold: a wall column is off if all points have y+ < yp_off */
   double *dye;                /* per cell wall-normal width */
   double *tau_cell;           /* per cell penalty tau_IP */
   unsigned char *active;      /* optional: only these cells' outputs are computed (NULL = all) */
@@ -325,6 +327,10 @@ void *dgo_mesh_create(const dgo_params *P) {
   M->ne = ne;
   M->enr_cell = (int *)malloc(sizeof(int) * (ne > 0 ? ne : 1));
   for (int c = 0; c < M->nc; ++c) if (M->enr[c] >= 0) M->enr_cell[M->enr[c]] = c;
+  /* enr[] is the switched-on view used by every operator; slot[] keeps the DoF layout */
+  M->slot = (int *)malloc(sizeof(int) * M->nc);
+  memcpy(M->slot, M->enr, sizeof(int) * M->nc);
+  M->yp_off = 0.0;
   M->np = (long)M->nc * n3;
   M->nu = 3L * M->np + 3L * M->nef * ne;
   /* nodal positions */
@@ -442,7 +448,7 @@ void dgo_mesh_destroy(void *h) {
   omesh *M = (omesh *)h;
   if (!M) return;
   free(M->active);
-  free(M->xv); free(M->yv); free(M->zv); free(M->X); free(M->enr); free(M->enr_cell);
+  free(M->xv); free(M->yv); free(M->zv); free(M->X); free(M->enr); free(M->enr_cell); free(M->slot);
   free(M->ywall); free(M->tauv); free(M->tsrc); free(M->dye); free(M->tau_cell); free(M);
 }
 
@@ -1294,9 +1300,57 @@ int dgo_wall_nodes(void *h) {
   return 2 * M->P.nx * M->P.nz;
 }
 
+/* Switch-off of the wall model (Sec. 3.2): a wall-nearest enriched cell is switched off when every
+ * point of its velocity point set (k+1 in-plane, q_w wall-normal) has y+ < yp_off, with y+ from the
+ * linear y_h and tau_w,h of its vertices; enriched cells further from the wall follow the
+ * wall-nearest cell of their column. A switched-off cell is a standard cell for every operator
+ * (point sets and face classes included); its enrichment coefficients are kept at zero. */
+static void apply_switch(omesh *M) {
+  const int nx = M->P.nx, ny = M->P.ny, L = M->P.n_layers, n1 = M->n1, qw = M->P.q_wall + M->P.extra_q;
+  double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+  dgo_gauss(n1 + M->P.extra_q, gx, gw);
+  dgo_gauss(qw, gy, gwy);
+  const int nin = n1 + M->P.extra_q;
+  for (int c = 0; c < M->nc; ++c) {
+    int e = M->slot[c];
+    if (e < 0) continue;
+    int i = c % nx, j = (c / nx) % ny, kz = c / (nx * ny);
+    int jw = (j < L) ? 0 : ny - 1;                 /* wall-nearest row of this column */
+    int ew = M->slot[cell_id(M, i, jw, kz)];
+    double ymax = 0.0;
+    for (int q2 = 0; q2 < nin; ++q2)
+      for (int q1 = 0; q1 < qw; ++q1)
+        for (int q0 = 0; q0 < nin; ++q0) {
+          double xi[3] = {gx[q0], gy[q1], gx[q2]}, N8[8], g8[8][3], yh = 0.0, th = 0.0;
+          q1_basis(8, xi, N8, g8);
+          for (int v = 0; v < 8; ++v) { yh += N8[v] * M->ywall[8 * ew + v]; th += N8[v] * M->tauv[8 * ew + v]; }
+          double yp = yh * sqrt(th) / M->P.nu;
+          if (yp > ymax) ymax = yp;
+        }
+    M->enr[c] = ymax < M->yp_off ? -1 : e;
+  }
+}
+
 void dgo_set_tau_nodes(void *h, const double *tn) {
   omesh *M = (omesh *)h;
   for (int i = 0; i < 8 * M->ne; ++i) M->tauv[i] = tn[M->tsrc[i]];
+  apply_switch(M);
+}
+
+void dgo_set_switch(void *h, double yp_off) {
+  omesh *M = (omesh *)h;
+  M->yp_off = yp_off;
+  apply_switch(M);
+}
+
+int dgo_active(void *h, int *on) {
+  omesh *M = (omesh *)h;
+  int n = 0;
+  for (int e = 0; e < M->ne; ++e) {
+    on[e] = M->enr[M->enr_cell[e]] >= 0;
+    n += on[e];
+  }
+  return n;
 }
 
 int dgo_wall_shear(void *h, const double *u, double *tn) {
@@ -1384,8 +1438,8 @@ int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_n
   memcpy(u_new, u_old, sizeof(double) * M->nu);
   if (M->ne == 0) { dgo_set_tau_nodes(h, tau_new); return 0; }
   /* old field at the points of every enriched cell */
-  int nq[3];
-  cell_points(M, M->enr_cell[0], OP_LINEAR, nq);
+  /* the wall cells' velocity point set, whether switched on or off */
+  const int nq[3] = {M->n1 + M->P.extra_q, M->P.q_wall + M->P.extra_q, M->n1 + M->P.extra_q};
   const int npts = nq[0] * nq[1] * nq[2];
   double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
   dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
@@ -1418,6 +1472,7 @@ int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_n
 #pragma omp for schedule(dynamic, 1)
     for (int e = 0; e < M->ne; ++e) {
       int c = M->enr_cell[e], q = 0;
+      const int Nc = M->enr[c] >= 0 ? N : n3;   /* switched off: standard functions only */
       memset(A, 0, sizeof(double) * (size_t)N * N);
       memset(B, 0, sizeof(double) * (size_t)N * 3);
       for (int q2 = 0; q2 < nq[2]; ++q2)
@@ -1427,14 +1482,14 @@ int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_n
             tabulate(M, c, xi, &t);
             double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
             for (int i = 0; i < n3; ++i) phi[i] = t.phi[i];
-            for (int v = 0; v < nef; ++v) phi[n3 + v] = t.ephi[v];
-            for (int i = 0; i < N; ++i) {
+            for (int v = 0; v < nef; ++v) phi[n3 + v] = t.enriched ? t.ephi[v] : 0.0;
+            for (int i = 0; i < Nc; ++i) {
               double wi = dV * phi[i];
-              for (int j = 0; j < N; ++j) A[(size_t)i * N + j] += wi * phi[j];
+              for (int j = 0; j < Nc; ++j) A[(size_t)i * Nc + j] += wi * phi[j];
               for (int a = 0; a < 3; ++a) B[(size_t)i * 3 + a] += wi * uold[((size_t)e * npts + q) * 3 + a];
             }
           }
-      if (solve_dense(N, A, B, 3) != 0) {
+      if (solve_dense(Nc, A, B, 3) != 0) {
 #pragma omp atomic write
         status = -1;
         continue;
@@ -1443,7 +1498,7 @@ int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_n
         double *uc = u_new + ((size_t)c * 3 + a) * n3;
         for (int i = 0; i < n3; ++i) uc[i] = B[(size_t)i * 3 + a];
         double *ue = u_new + 3L * M->np + ((size_t)e * 3 + a) * nef;
-        for (int v = 0; v < nef; ++v) ue[v] = B[(size_t)(n3 + v) * 3 + a];
+        for (int v = 0; v < nef; ++v) ue[v] = Nc == N ? B[(size_t)(n3 + v) * 3 + a] : 0.0;
       }
     }
     free(A); free(B); free(phi);

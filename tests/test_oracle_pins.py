@@ -666,3 +666,74 @@ def test_projection_matches_the_integrals_of_the_old_wall_law():
     assert abs(std[:, 0, :].sum() / r1 - 1.0) < 1e-6
     assert abs(ye[:, 0, :].sum() / r2 - 1.0) < 1e-6
     assert np.abs(un[: 3 * m.n_p].reshape(m.nc, 3, -1)[:, 1:, :]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------------------------
+# Switch-off of the wall model where the wall-nearest cell lies below a y+ threshold (Sec. 3.2)
+# ---------------------------------------------------------------------------------------------
+
+def test_switched_off_mesh_equals_the_mesh_without_enrichment():
+    """With every wall column switched off the operators on the standard DoFs are those of the same
+    mesh built without enrichment, and the enrichment outputs are zero; switching back on restores
+    the enriched operators exactly."""
+    w = I.Workload("so", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=33)
+    m, m0 = O.Mesh(**w.mesh_kwargs()), O.Mesh(**w.mesh_kwargs(), n_layers=0)
+    u = I.workload_velocity(m.node_coords(), m.n_e, w)
+    u[3 * m.n_p:] += 0.1 * I.uniform(7, 24 * m.n_e, -1, 1)
+    np3 = 3 * m.n_p
+    before = [m.convective(u), m.viscous(u, u), m.vmass(u)]
+    m.set_switch(1e30)
+    assert m.active().sum() == 0
+    for f, f0 in ((m.convective, m0.convective), (m.vmass, m0.vmass)):
+        y, y0 = f(u), f0(u[:np3])
+        assert np.array_equal(y[:np3], y0) and not np.any(y[np3:])
+    y, y0 = m.viscous(u, u), m0.viscous(u[:np3], u[:np3])
+    assert np.array_equal(y[:np3], y0) and not np.any(y[np3:])
+    assert np.array_equal(m.divergence(u), m0.divergence(u[:np3]))
+    m.set_switch(0.0)
+    assert m.active().sum() == m.n_e
+    for y, f in zip(before, (m.convective, lambda v: m.viscous(v, v), m.vmass)):
+        assert np.array_equal(f(u), y)
+
+
+def test_switch_off_criterion_on_the_channel():
+    """Channel: y_h = xi_1 dy in a bottom wall cell, tau_h is bilinear in (xi_0, xi_2) and constant in
+    xi_1, so the largest y+ over the points is at the largest wall-normal Gauss point and the largest
+    in-plane value of tau_h; a column is on iff that maximum reaches the threshold."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    nx, nz = 8, 8
+    tn = w.tau_w * 10.0 ** I.uniform(8, m.n_wall_nodes, -1.0, 1.0)
+    m.set_tau_nodes(tn)
+    thr = 25.0
+    m.set_switch(thr)
+    gx, _ = O.gauss(3)
+    gq, _ = O.gauss(8)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    on = m.active()
+    T = tn.reshape(2, nz, nx)
+    for e in range(m.n_e):
+        wall, r = divmod(e, nx * nz)
+        kz, i = divmod(r, nx)
+        t4 = [T[wall, kz, i], T[wall, kz, (i + 1) % nx], T[wall, (kz + 1) % nz, i], T[wall, (kz + 1) % nz, (i + 1) % nx]]
+        th = max((1 - a) * (1 - b) * t4[0] + a * (1 - b) * t4[1] + (1 - a) * b * t4[2] + a * b * t4[3]
+                 for a in gx for b in gx)
+        ymax = (gq[-1] if wall == 0 else 1.0 - gq[0]) * dy * math.sqrt(th) / w.nu
+        assert on[e] == (ymax >= thr), (e, ymax)
+    assert 0 < on.sum() < m.n_e
+
+
+def test_projection_into_switched_off_cells_keeps_polynomials():
+    """Projecting onto a space whose wall columns are partly switched off: a polynomial field is
+    unchanged and the enrichment coefficients of the switched-off cells are zero."""
+    w = I.Workload("sp", 4, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=34)
+    m = O.Mesh(**w.mesh_kwargs())
+    m.set_switch(60.0)
+    u = _std_field(m, lambda x, y, z: 1 + y ** 3 - 0.5 * x * y, lambda x, y, z: y * z, lambda x, y, z: x ** 2)
+    tn = w.tau_w * 10.0 ** I.uniform(9, m.n_wall_nodes, -2.0, 0.3)
+    un = m.project(tn, u)
+    on = m.active()
+    assert 0 < on.sum() < m.n_e
+    assert _l2_rel(m, un, u) < 1e-11
+    ue = un[3 * m.n_p:].reshape(m.n_e, -1)
+    assert not np.any(ue[on == 0])
