@@ -138,6 +138,20 @@ dgw_status dgw_set_wall_shear_stress(dgw_mesh_t mesh, const double *tau_nodes_de
 dgw_status dgw_project_velocity(dgw_mesh_t mesh, const double *tau_nodes_dev, const double *u_old_dev,
                                 double *u_new_dev, void *stream);
 
+/* Switch-off of the wall model (Sec. 3.2): from now on, and again after every change of tau_w, a
+ * wall column is switched off when every point of the velocity point set of its wall-nearest
+ * enriched cell has y+ < yplus_off (y+ from the linear y_h and tau_w,h); the paper takes 30 and
+ * reports 20 to 30 as equivalent; 0 (the default) never switches off. A switched-off cell is a
+ * standard cell for every operator (point sets and face classes included) and its enrichment
+ * coefficients keep their slots in the vector: applies and solves write zeros there, and inputs
+ * there are ignored. To move a velocity between spaces with different switched-off cells use
+ * dgw_project_velocity (whose new space follows the threshold). Asynchronous. */
+dgw_status dgw_set_enrichment_switch(dgw_mesh_t mesh, double yplus_off, void *stream);
+
+/* Which enriched cells have the wall model switched on: active_host[e] (n_enriched ints, may be
+ * NULL) and their count *n_active (may be NULL). Synchronises `stream`. */
+dgw_status dgw_enrichment_active(dgw_mesh_t mesh, int *active_host, int *n_active, void *stream);
+
 /* y = -L(q, p) (Sec. 4.2, SIPG Laplace term with the flux of eq. ipflux on interior and
  * periodic faces; homogeneous Neumann on walls). p, y: n_p values of type `prec`. */
 dgw_status dgw_apply_laplace(dgw_mesh_t mesh, int prec, const void *p, void *y, void *stream);

@@ -209,6 +209,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->v64.tau = upload(M, M->tau.data(), M->nc, s, &err);
   M->v64.enr = upload(M, M->enr.data(), M->nc, s, &err);
   M->v32.enr = M->v64.enr;
+  M->slot_dev = upload(M, M->enr.data(), M->nc, s, &err);
+  M->v64.slot = M->v32.slot = M->slot_dev;
   M->v64.basis = upload(M, &M->basis64, 1, s, &err);
   M->v64.geo = M->v32.geo = curved ? GEO_CURVED : GEO_BOX;
   if (curved) {
@@ -240,6 +242,16 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   M->wall_ywall_dev = upload(M, M->ywall.data(), M->ywall.size(), s, &err);
   M->wall_tauv_dev = upload(M, M->tauv.data(), M->tauv.size(), s, &err);
   M->tsrc_dev = upload(M, M->tsrc.data(), M->tsrc.size(), s, &err);
+  {
+    // wall-nearest enriched cell of every enriched cell's column (the switch-off decides per column)
+    std::vector<int> ws(std::max(ne, 1), 0);
+    const int L = P->n_layers;
+    for (int e = 0; e < ne; ++e) {
+      const int c = M->enr_cell[e], i = c % nx, j = (c / nx) % ny, kz = c / (nx * ny);
+      ws[e] = M->enr[i + nx * ((j < L ? 0 : ny - 1) + ny * kz)];
+    }
+    M->wslot_dev = upload(M, ws.data(), ws.size(), s, &err);
+  }
   M->wall_mom_dev = dalloc<double>(M, (size_t)2 * nx * nz * 16, &err);
   M->dye_dev = upload(M, M->dye.data(), M->dye.size(), s, &err);
   const int qw = P->q_wall;
@@ -372,6 +384,32 @@ dgw_status dgw_set_wall_shear_stress(dgw_mesh_t M, const double *tau_nodes, void
   if (st != DGW_OK) return st;
   dgw_helm_free(M);   // the enriched mass blocks of the Helmholtz preconditioner change with tau_w
   return cuda_check(launch_set_tau_nodes(M, tau_nodes, s), "dgw_set_wall_shear_stress");
+}
+
+dgw_status dgw_set_enrichment_switch(dgw_mesh_t M, double yplus_off, void *stream) {
+  if (!M) return set_error(DGW_EINVAL, "dgw_set_enrichment_switch: null mesh");
+  if (!(yplus_off >= 0.0) || !std::isfinite(yplus_off))
+    return set_error(DGW_EINVAL, "dgw_set_enrichment_switch: yplus_off must be finite and >= 0");
+  M->yp_off = yplus_off;
+  dgw_helm_free(M);
+  return cuda_check(launch_switch(M, (cudaStream_t)stream), "dgw_set_enrichment_switch");
+}
+
+dgw_status dgw_enrichment_active(dgw_mesh_t M, int *active_host, int *n_active, void *stream) {
+  if (!M) return set_error(DGW_EINVAL, "dgw_enrichment_active: null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> enr(M->nc);
+  cudaError_t e = cudaMemcpyAsync(enr.data(), M->v64.enr, M->nc * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_enrichment_active");
+  int cnt = 0;
+  for (int i = 0; i < M->ne; ++i) {
+    const int on = enr[M->enr_cell[i]] >= 0;
+    cnt += on;
+    if (active_host) active_host[i] = on;
+  }
+  if (n_active) *n_active = cnt;
+  return DGW_OK;
 }
 
 dgw_status dgw_project_velocity(dgw_mesh_t M, const double *tau_nodes, const double *u_old, double *u_new,

@@ -68,7 +68,8 @@ struct MeshView {
   // side, dA J^-1 n of the neighbour at the shared point (n the own outward normal; zero on walls)
   const T *lvol;
   const T *lface;
-  const int *enr;     // [nc] enriched index or -1
+  const int *enr;     // [nc] enriched index or -1 (-1 also where the wall model is switched off)
+  const int *slot;    // [nc] enriched index whether switched on or off, -1 off the wall layers
   T visc;             // kinematic viscosity nu
   const Basis<T> *basis;
   // wall tables [qset lin/conv]: volume [ne][nvol][WT], faces [ne][6][fpmax][WT]
@@ -115,6 +116,9 @@ struct dgw_mesh {
   int *enr_cell_dev = nullptr;
   double *wall_ywall_dev = nullptr, *wall_tauv_dev = nullptr;
   int *tsrc_dev = nullptr;
+  int *slot_dev = nullptr;          // [nc] enriched index (layout), constant
+  int *wslot_dev = nullptr;         // [ne] enriched index of the wall-nearest cell of the column
+  double yp_off = 0.0;              // switch-off threshold on y+ (0: never)
   double *wall_mom_dev = nullptr;   // [2 nx nz][16] per-wall-face moments of the tau_w update
   double *proj_A = nullptr;         // L2 projection scratch: [ne][N][N] cell matrices (lazily allocated)
   double *proj_P = nullptr;         // [ne][points][3] old field at the points
@@ -217,6 +221,7 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
 cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, cudaStream_t s);
 cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s);
+cudaError_t launch_switch(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, const double *u_old, double *u_new, cudaStream_t s,
                               int *bad_cell);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);

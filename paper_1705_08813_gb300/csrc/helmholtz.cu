@@ -148,7 +148,8 @@ __device__ void mss_inverse(const double *in, double *out, const double *Si, con
 // block inverse of each component in wall cells.
 __global__ void inverse_mass_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ sinv,
                                     const double *__restrict__ detw, const int *__restrict__ enr,
-                                    const double *__restrict__ meeinv, int n, int nef, long np, double inv_gamma) {
+                                    const int *__restrict__ slot, const double *__restrict__ meeinv, int n, int nef,
+                                    long np, double inv_gamma) {
   __shared__ double A[NMAX * NMAX * NMAX], Bs[NMAX * NMAX * NMAX], Si[NMAX * NMAX];
   const int c = blockIdx.x, n3 = n * n * n;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) Si[t] = sinv[t];
@@ -157,6 +158,10 @@ __global__ void inverse_mass_kernel(const double *__restrict__ r, double *__rest
     mss_inverse(r + ((size_t)c * 3 + a) * n3, z + ((size_t)c * 3 + a) * n3, Si, detw + (size_t)c * n3, inv_gamma, n,
                 A, Bs);
   const int e = enr ? enr[c] : -1;
+  if (e < 0 && slot && slot[c] >= 0) {   // wall model switched off here: zero coefficients
+    for (int t = threadIdx.x; t < 3 * nef; t += blockDim.x) z[3 * np + (size_t)slot[c] * 3 * nef + t] = 0.0;
+    return;
+  }
   if (e < 0 || threadIdx.x >= 3 * nef) return;
   const int a = threadIdx.x / nef, v = threadIdx.x % nef;
   const double *rin = r + 3 * np + ((size_t)e * 3 + a) * nef;
@@ -332,8 +337,12 @@ static cudaError_t helm_setup(dgw_mesh *M, int restart) {
       for (int c = 0; c < M->ne && e == cudaSuccess; ++c)
         for (int wv = 0; wv < q; ++wv) mee[(size_t)c * 64 + wv * q + v] = out[(size_t)c * 3 * q + wv];
     }
-    for (int c = 0; c < M->ne && e == cudaSuccess; ++c)
+    for (int c = 0; c < M->ne && e == cudaSuccess; ++c) {
+      bool zero = true;   // a switched-off cell has no enrichment functions: its block is zero
+      for (int i = 0; i < q * q; ++i) zero = zero && mee[(size_t)c * 64 + i] == 0.0;
+      if (zero) continue;
       if (!invert_spd(&mee[(size_t)c * 64], &inv[(size_t)c * 64], q)) e = cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(H->meeinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -416,8 +425,8 @@ dgw_status helmholtz_solve(dgw_mesh *M, double gamma, const double *rhs, double 
     for (; j < m && it < o->max_iter; ++j) {
       double *Vj = H->V + (size_t)j * nu, *Zj = H->Z + (size_t)j * nu, *Vn = H->V + (size_t)(j + 1) * nu;
       note_launch();
-      inverse_mass_kernel<<<M->nc, 128, 0, s>>>(Vj, Zj, H->m1inv, H->detw, M->v64.enr, H->meeinv, M->n1, M->nef,
-                                                M->np, 1.0 / gamma);
+      inverse_mass_kernel<<<M->nc, 128, 0, s>>>(Vj, Zj, H->m1inv, H->detw, M->v64.enr, M->v64.slot, H->meeinv, M->n1,
+                                                M->nef, M->np, 1.0 / gamma);
       e = helm_apply(M, gamma, Zj, H->w, H->t, s);
       if (e != cudaSuccess) return cuda_check(e, "dgw_helmholtz_solve: operator");
       // classical Gram-Schmidt, twice

@@ -668,6 +668,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       L->view.hx = (T)L->geo.hx;
       L->view.hz = (T)L->geo.hz;
       L->view.enr = nullptr;
+      L->view.slot = nullptr;
       if (curved) {
         CurvedHost cg;
         curved_geometry(M->P, nx, ny, nz, k, M->basis64, cg);
@@ -678,6 +679,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
         v64.ne = 0;
         v64.np = L->n;
         v64.enr = nullptr;
+        v64.slot = nullptr;
         Lvl<double> tmp;   // owns nothing: the FP64 tables live with the level
         upload_curved<double>(&tmp, cg, v64, e, s);
         L->allocs.insert(L->allocs.end(), tmp.allocs.begin(), tmp.allocs.end());

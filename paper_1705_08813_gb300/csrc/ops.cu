@@ -972,7 +972,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   } else {
     T *yc = y + (size_t)c * 3 * n3;
     for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) yc[t] = r[t];
-    if (enr_c && m.nef == 8)
+    if (!enr_c && m.slot && m.slot[c] >= 0) {
+      // wall model switched off in this cell: its enrichment coefficients have no function
+      for (int t = threadIdx.x; t < 3 * m.nef; t += blockDim.x) y[3 * m.np + (size_t)m.slot[c] * 3 * m.nef + t] = T(0);
+    } else if (enr_c && m.nef == 8)
       for (int t = threadIdx.x; t < 24; t += blockDim.x) y[3 * m.np + (size_t)ec * 24 + t] = re[t];
     else if (enr_c && threadIdx.x < 3) {
       // l = 0: the test function psi e_a is the sum of the 8 weighted ones

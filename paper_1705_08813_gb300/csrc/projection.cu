@@ -12,7 +12,9 @@
 //      axes, the right-hand sides from the stored point values, then factorised by Cholesky in a
 //      global scratch block and solved for the three components.
 // The cell systems are ill-conditioned where a wall cell spans few wall units (psi N_B close to the
-// polynomials); a non-positive pivot sets the error word and the cell is left unsolved.
+// polynomials); a non-positive pivot sets the error word and the cell is left unsolved. A cell
+// whose wall model is switched off in the new space solves its standard block only (enrichment
+// coefficients zero); every wall cell integrates with the enriched point set either way.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -32,8 +34,9 @@ __global__ void project_eval_kernel(MeshView<double> m, const int *__restrict__ 
   const int n = m.n1, n3 = n * n * n, e = blockIdx.x, cell = enr_cell[e];
   __shared__ double su[3 * NMAX * NMAX * NMAX], ce[24];
   for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) su[t] = u[(size_t)cell * 3 * n3 + t];
+  const bool on = m.enr[cell] >= 0;   // switched off: the old space has no enrichment here
   for (int t = threadIdx.x; t < 24; t += blockDim.x)
-    ce[t] = u[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)];
+    ce[t] = on ? u[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : 0.0;
   __syncthreads();
   const int q0 = B.q[QSET_LIN], q1 = B.q[QSET_WALL];
   const double *S0 = B.S[QSET_LIN], *Sw = B.S[QSET_WALL];
@@ -89,11 +92,13 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
                                      double *__restrict__ Ag, double *__restrict__ u_new, int *__restrict__ err) {
   extern __shared__ double sm[];
   const Basis<double> &B = *m.basis;
-  const int n = m.n1, n2 = n * n, n3 = n2 * n, nef = m.nef, N = n3 + nef;
+  const int n = m.n1, n2 = n * n, n3 = n2 * n, N = n3 + m.nef;
   const int q0 = B.q[QSET_LIN], q1 = B.q[QSET_WALL], npts = q0 * q1 * q0;
-  const ProjLayout L = proj_layout(n, q0, q1, nef);
+  const ProjLayout L = proj_layout(n, q0, q1, m.nef);
   double *W = sm + L.W, *PSI = sm + L.PSI, *T1 = sm + L.T1, *T2 = sm + L.T2, *R = sm + L.RHS, *col = sm + L.COL;
   const int e = blockIdx.x, c = enr_cell[e], tid = threadIdx.x, nt = blockDim.x;
+  // switched off in the new space: the standard block alone (stride N kept), zero enrichment
+  const int nef = m.enr[c] >= 0 ? m.nef : 0, Nc = n3 + nef;
   double *A = Ag + (size_t)e * N * N;
   const double *S0 = B.S[QSET_LIN], *Sw = B.S[QSET_WALL];
   const double *w0 = B.w[QSET_LIN], *w1 = B.w[QSET_WALL];
@@ -173,38 +178,38 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
   __syncthreads();
   // 6. Cholesky A = L L^T (lower triangle, right-looking); one warp per trailing row
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int j = 0; j < N; ++j) {
+  for (int j = 0; j < Nc; ++j) {
     const double d = A[(size_t)j * N + j];
     if (!(d > 0.0)) {
       if (tid == 0) atomicCAS(err, 0, c + 1);
       return;   // uniform: every thread read the same pivot after the barrier
     }
     const double ljj = sqrt(d);
-    for (int i = j + 1 + tid; i < N; i += nt) {
+    for (int i = j + 1 + tid; i < Nc; i += nt) {
       const double l = A[(size_t)i * N + j] / ljj;
       col[i] = l;
       A[(size_t)i * N + j] = l;
     }
     __syncthreads();
     if (tid == 0) A[(size_t)j * N + j] = ljj;
-    for (int i = j + 1 + warp; i < N; i += nw) {
+    for (int i = j + 1 + warp; i < Nc; i += nw) {
       const double li = col[i];
       for (int k = j + 1 + lane; k <= i; k += 32) A[(size_t)i * N + k] -= li * col[k];
     }
     __syncthreads();
   }
   // 7. L y = r, then L^T x = y, for the three components
-  for (int j = 0; j < N; ++j) {
+  for (int j = 0; j < Nc; ++j) {
     const double ljj = A[(size_t)j * N + j];
     if (tid < 3) R[tid * N + j] /= ljj;
     __syncthreads();
-    for (int p = tid; p < 3 * (N - j - 1); p += nt) {
-      const int a = p / (N - j - 1), i = j + 1 + p % (N - j - 1);
+    for (int p = tid; p < 3 * (Nc - j - 1); p += nt) {
+      const int a = p / (Nc - j - 1), i = j + 1 + p % (Nc - j - 1);
       R[a * N + i] -= A[(size_t)i * N + j] * R[a * N + j];
     }
     __syncthreads();
   }
-  for (int j = N - 1; j >= 0; --j) {
+  for (int j = Nc - 1; j >= 0; --j) {
     const double ljj = A[(size_t)j * N + j];
     if (tid < 3) R[tid * N + j] /= ljj;
     __syncthreads();
@@ -219,9 +224,9 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
     const int a = p / n3, i = p % n3;
     u_new[((size_t)c * 3 + a) * n3 + i] = R[a * N + i];
   }
-  for (int p = tid; p < 3 * nef; p += nt) {
-    const int a = p / nef, v = p % nef;
-    u_new[3 * m.np + ((size_t)e * 3 + a) * nef + v] = R[a * N + n3 + v];
+  for (int p = tid; p < 3 * m.nef; p += nt) {
+    const int a = p / m.nef, v = p % m.nef;
+    u_new[3 * m.np + ((size_t)e * 3 + a) * m.nef + v] = nef ? R[a * N + n3 + v] : 0.0;
   }
 }
 

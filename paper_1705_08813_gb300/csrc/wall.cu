@@ -376,12 +376,34 @@ cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, c
   return cudaGetLastError();
 }
 
+// Switch-off of the wall model (Sec. 3.2): enriched cell e is on iff some point of the velocity point
+// set of the wall-nearest cell of its column has y+ >= yp_off (aux_vol holds (y_h, y+) per point of
+// every enriched cell, switched on or not). Writes the operators' view enr[c].
+__global__ void switch_kernel(const double *__restrict__ aux_vol, int nvol, const int *__restrict__ wslot,
+                              const int *__restrict__ enr_cell, int ne, double yp_off, int *__restrict__ enr) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+    const double *a = aux_vol + (size_t)wslot[e] * nvol * 2;
+    double ymax = 0.0;
+    for (int t = 0; t < nvol; ++t) ymax = fmax(ymax, a[2 * t + 1]);
+    enr[enr_cell[e]] = ymax < yp_off ? -1 : e;
+  }
+}
+
+cudaError_t launch_switch(dgw_mesh *M, cudaStream_t s) {
+  if (M->ne == 0) return cudaSuccess;
+  note_launch();
+  switch_kernel<<<(M->ne + 127) / 128, 128, 0, s>>>(M->aux_vol, M->v64.nvol[0], M->wslot_dev, M->enr_cell_dev, M->ne,
+                                                    M->yp_off, const_cast<int *>(M->v64.enr));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s) {
   if (M->ne == 0) return cudaSuccess;
   note_launch();
   tau_fill_kernel<<<(8 * M->ne + 255) / 256, 256, 0, s>>>(tau_nodes, M->tsrc_dev, 8 * M->ne, M->wall_tauv_dev);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_wall_tables(M, s);
+  if (e == cudaSuccess) e = launch_switch(M, s);
   if (e == cudaSuccess && M->has32)
     for (int cls = 0; cls < 2 && e == cudaSuccess; ++cls) {
       e = launch_to_float(M->v64.wt_vol[cls], const_cast<float *>(M->v32.wt_vol[cls]),

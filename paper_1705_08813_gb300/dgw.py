@@ -21,7 +21,7 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
            "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
-           "dgw_project_velocity"]
+           "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
     lib.dgw_wall_shear_stress.argtypes = [vp, vp, vp, vp]
     lib.dgw_set_wall_shear_stress.argtypes = [vp, vp, vp]
     lib.dgw_project_velocity.argtypes = [vp, vp, vp, vp, vp]
+    lib.dgw_set_enrichment_switch.argtypes = [vp, ctypes.c_double, vp]
+    lib.dgw_enrichment_active.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]
     lib.dgw_helmholtz_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.POINTER(HelmholtzOpts),
                                         ctypes.POINTER(SolveInfo), vp]
     lib.dgw_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
@@ -223,6 +225,19 @@ class Mesh:
                                              _ptr(u_old, torch.float64, self.n_u, "u_old"),
                                              _ptr(u_new, torch.float64, self.n_u, "u_new"), _stream(stream)))
         return u_new
+
+    def set_enrichment_switch(self, yplus_off: float, stream=None):
+        """Switch the wall model off in wall columns whose wall-nearest cell has y+ < yplus_off."""
+        _check(self.lib.dgw_set_enrichment_switch(self.h, ctypes.c_double(yplus_off), _stream(stream)))
+
+    def enrichment_active(self, stream=None):
+        """Per enriched cell: 1 if the wall model is switched on (numpy int32 array)."""
+        import numpy as np
+        out = np.zeros(max(self.n_e, 1), dtype=np.int32)
+        cnt = ctypes.c_int()
+        _check(self.lib.dgw_enrichment_active(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                              ctypes.byref(cnt), _stream(stream)))
+        return out[: self.n_e]
 
     def mass(self, u, y, stream=None):
         _check(self.lib.dgw_apply_mass(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),

@@ -198,3 +198,104 @@ def test_projection_rejects_non_positive_tau_and_singular_cell_spaces(dgw):
     t3 = torch.full((g3.n_wall_nodes,), w3.tau_w, dtype=torch.float64, device="cuda")
     with pytest.raises(dgw.DGWError):
         g3.project_velocity(t3, u3, u3)
+
+
+SWITCH_CASES = [
+    ("c1_q2_8x8x8", I.WORKLOADS["channel_q2_8x8x8"], {}),
+    ("q3_two_layers_l0", I.Workload("s3", 4, 6, 2, 3, 395.0, 1.0 / 6000.0, seed=35), {"n_layers": 2, "enrich_l": 0}),
+    ("bump_q3_6x4x3", I.bump_workload("b2", 6, 4, 3, 3, seed=22), {}),
+]
+
+
+def _switched(dgw, w, kw, thr=None):
+    """Seeded nodal tau_w over two decades; the threshold (if not given) is the first of a ladder that
+    leaves part of the wall columns on and part off in the oracle."""
+    om, gm = _meshes(dgw, w, **kw)
+    dev = torch.device("cuda:0")
+    tn = w.tau_w * 10.0 ** I.uniform(w.seed, om.n_wall_nodes, -1.0, 1.0, stream=75)
+    om.set_tau_nodes(tn)
+    for t in ([thr] if thr is not None else list(10.0 * 1.25 ** np.arange(25))):
+        om.set_switch(t)
+        if 0 < om.active().sum() < om.n_e:
+            thr = float(t)
+            break
+    assert thr is not None
+    gm.set_wall_shear_stress(torch.tensor(tn, device=dev))
+    gm.set_enrichment_switch(thr)
+    return om, gm, tn
+
+
+@pytest.mark.parametrize("name,w,kw", SWITCH_CASES, ids=[c[0] for c in SWITCH_CASES])
+def test_switch_off_operators_match_oracle(dgw, name, w, kw):
+    """Part of the wall columns switched off (y+ threshold between the smallest and largest column
+    maxima): the same columns on both sides, and every operator equal to the oracle's; outputs of the
+    switched-off enrichment slots are written as zeros (buffers start as NaN)."""
+    om, gm, _ = _switched(dgw, w, kw)
+    on = om.active()
+    assert 0 < on.sum() < om.n_e, on.sum()
+    assert np.array_equal(gm.enrichment_active(), on)
+    dev = torch.device("cuda:0")
+    u = _velocity(om, w, kw)
+    ud = torch.tensor(u, device=dev)
+    y = torch.full((gm.n_u,), float("nan"), dtype=torch.float64, device=dev)
+    _cmp(gm.convective(ud, y).cpu().numpy(), om.convective(u), TOL64, "convective")
+    y.fill_(float("nan"))
+    _cmp(gm.mass(ud, y).cpu().numpy(), om.vmass(u), TOL64, "mass")
+    b = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
+    _cmp(gm.divergence(ud, b).cpu().numpy(), om.divergence(u), TOL64, "divergence")
+    gm.update_eddy_viscosity(ud)
+    v = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=76)
+    y.fill_(float("nan"))
+    _cmp(gm.viscous(torch.tensor(v, device=dev), y).cpu().numpy(), om.viscous(u, v), TOL64, "viscous")
+    tau = torch.empty(gm.n_wall_nodes, dtype=torch.float64, device=dev)
+    _cmp(gm.wall_shear_stress(ud, tau).cpu().numpy(), om.wall_shear(u), TOL64, "tau_w,B")
+
+
+def test_switch_off_everywhere_equals_mesh_without_enrichment(dgw):
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    dev = torch.device("cuda:0")
+    gm, g0 = dgw.mesh_for(w), dgw.mesh_for(w, n_layers=0)
+    gm.set_enrichment_switch(1e30)
+    assert gm.enrichment_active().sum() == 0
+    om = O.Mesh(**w.mesh_kwargs())
+    u = torch.tensor(_velocity(om, w, {}), device=dev)
+    np3 = 3 * gm.n_p
+    for op in ("convective", "mass"):
+        y = torch.full((gm.n_u,), float("nan"), dtype=torch.float64, device=dev)
+        y0 = torch.empty(g0.n_u, dtype=torch.float64, device=dev)
+        getattr(gm, op)(u, y)
+        getattr(g0, op)(u[:np3].contiguous(), y0)
+        assert torch.equal(y[:np3], y0) and not torch.any(y[np3:] != 0)
+    gm.set_enrichment_switch(0.0)
+    assert gm.enrichment_active().sum() == gm.n_e
+
+
+def test_switch_off_helmholtz_and_projection(dgw):
+    """Helmholtz solve and L2 projection with part of the wall columns switched off, checked with the
+    oracle's operators (residual) and projection (L2 norm and Galerkin moments)."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    om, gm, tn = _switched(dgw, w, {}, 25.0)
+    dev = torch.device("cuda:0")
+    u = _velocity(om, w, {})
+    ud = torch.tensor(u, device=dev)
+    # projection onto a new space with a different switched-off pattern
+    tn2 = w.tau_w * 10.0 ** I.uniform(w.seed, om.n_wall_nodes, -1.0, 1.0, stream=77)
+    ref = om.project(tn2, u)
+    un = torch.empty_like(ud)
+    gm.project_velocity(torch.tensor(tn2, device=dev), ud, un)
+    assert np.array_equal(gm.enrichment_active(), om.active())
+    got = un.cpu().numpy()
+    l2 = _l2(om, got - ref, ref)
+    mom = np.linalg.norm(om.vmass(got) - om.vmass(ref)) / np.linalg.norm(om.vmass(ref))
+    assert l2 < 1e-9 and mom < 1e-10, (l2, mom)
+    # Helmholtz in the new space
+    gamma = 1.5e3
+    gm.update_eddy_viscosity(un)
+    rhs = gamma * om.vmass(ref)
+    x = un.clone()
+    info = gm.helmholtz_solve(gamma, torch.tensor(rhs, device=dev), x, rtol=1e-10, max_iter=2000, restart=30)
+    xh = x.cpu().numpy()
+    res = rhs - (gamma * om.vmass(xh) + om.viscous(got, xh))
+    assert info["rel_residual"] <= 1e-10 and np.linalg.norm(res) <= 1.5e-10 * np.linalg.norm(rhs)
+    off = np.repeat(om.active() == 0, 24)
+    assert not np.any(xh[3 * om.n_p:][off])
