@@ -82,6 +82,11 @@ def _load():
         lib.dgo_wall_shear.restype = ctypes.c_int
         lib.dgo_project.argtypes = [vp, dp, dp, dp]
         lib.dgo_set_switch.argtypes = [vp, ctypes.c_double]
+        lib.dgo_gradient.argtypes = [vp, dp, dp]
+        lib.dgo_divdiv.argtypes = [vp, dp, dp, dp]
+        lib.dgo_tau_divdiv.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp]
+        lib.dgo_inverse_mass.argtypes = [vp, dp, dp]
+        lib.dgo_inverse_mass.restype = ctypes.c_int
         lib.dgo_active.argtypes = [vp, ip]
         lib.dgo_active.restype = ctypes.c_int
         lib.dgo_project.restype = ctypes.c_int
@@ -271,6 +276,32 @@ class Mesh:
         if self.lib.dgo_project(self.h, _ptr(tn), _ptr(u), _ptr(out)) != 0:
             raise RuntimeError("singular cell system in the L2 projection")
         return out
+
+    def gradient(self, p: np.ndarray) -> np.ndarray:
+        """Pressure gradient P(v, p) = -(div v, p) + (v, {{p}} n), {{p}} = p^- on walls (n_p in, n_u out)."""
+        p = np.ascontiguousarray(p, dtype=np.float64); y = np.zeros(self.n_u)
+        self.lib.dgo_gradient(self.h, _ptr(p), _ptr(y))
+        return y
+
+    def tau_divdiv(self, u: np.ndarray, dt: float, cr: float) -> np.ndarray:
+        """Per-cell tau_D = |u|_K h dt / Cr (volume-averaged |u|, h = cube root of the cell volume)."""
+        u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(self.nc)
+        self.lib.dgo_tau_divdiv(self.h, _ptr(u), float(dt), float(cr), _ptr(out))
+        return out
+
+    def divdiv(self, tau_d: np.ndarray, u: np.ndarray) -> np.ndarray:
+        """Div-div penalty D(v, u) = (div v, tau_D div u) per cell."""
+        t = np.ascontiguousarray(tau_d, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64); y = np.zeros(self.n_u)
+        self.lib.dgo_divdiv(self.h, _ptr(t), _ptr(u), _ptr(y))
+        return y
+
+    def inverse_mass(self, r: np.ndarray) -> np.ndarray:
+        """x = M^-1 r, cell by cell (dense cell systems)."""
+        r = np.ascontiguousarray(r, dtype=np.float64); x = np.zeros(self.n_u)
+        if self.lib.dgo_inverse_mass(self.h, _ptr(r), _ptr(x)) != 0:
+            raise RuntimeError("singular cell mass matrix")
+        return x
 
     def set_switch(self, yplus_off: float) -> None:
         """Switch the wall model off in every wall column whose wall-nearest cell has y+ < yplus_off at

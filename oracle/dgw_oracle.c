@@ -1507,3 +1507,206 @@ int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_n
   free(uold);
   return status;
 }
+
+/* ----------------------------------------------------------------------------------------------
+ * Pressure gradient (Sec. 4.2): y = P(v, p) = -(div v, p)_K + (v, {{p}} n)_dK for every velocity
+ * test function (standard and enriched), {{p}} = p^- on walls (projection step, eq.
+ * projectionspat). Point sets as the divergence.
+ * ---------------------------------------------------------------------------------------------- */
+static double eval_p(const omesh *M, const double *p, int c, const ptab *t) {
+  const double *pc = p + (size_t)c * t->n3;
+  double v = 0.0;
+  for (int i = 0; i < t->n3; ++i) v += t->phi[i] * pc[i];
+  return v;
+}
+
+int dgo_gradient(void *h, const double *p, double *y) {
+  omesh *M = (omesh *)h;
+  int n3 = M->n1 * M->n1 * M->n1;
+  memset(y, 0, sizeof(double) * M->nu);
+#pragma omp parallel
+  {
+    ptab t, tn; ptab_alloc(&t, M); ptab_alloc(&tn, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP], gx2[MAXP], gw2[MAXP];
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < M->nc; ++c) {
+      int nq[3];
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            double pv = eval_p(M, p, c, &t);
+            for (int a = 0; a < 3; ++a) {
+              double *yc = y + ((size_t)c * 3 + a) * n3;
+              for (int i = 0; i < n3; ++i) yc[i] -= dV * t.gphi[3 * i + a] * pv;
+              if (t.enriched) {
+                double *ye = y + 3L * M->np + ((size_t)M->enr[c] * 3 + a) * M->nef;
+                for (int v = 0; v < M->nef; ++v) ye[v] -= dV * t.egphi[v][a] * pv;
+              }
+            }
+          }
+      for (int f = 0; f < 6; ++f) {
+        int nb = neighbour(M, c, f);
+        int d = f / 2, side = f % 2, t1, t2, m1, m2;
+        face_points(M, c, nb, d, OP_LINEAR, &t1, &t2, &m1, &m2);
+        dgo_gauss(m1, gx, gw); dgo_gauss(m2, gx2, gw2);
+        for (int bq = 0; bq < m2; ++bq)
+          for (int a1 = 0; a1 < m1; ++a1) {
+            double xi[3], xn[3], n[3];
+            xi[d] = side; xi[t1] = gx[a1]; xi[t2] = gx2[bq];
+            tabulate(M, c, xi, &t);
+            double dA = face_geom(t.Ji, t.detJ, d, side, n) * gw[a1] * gw2[bq];
+            double pm = eval_p(M, p, c, &t), avg = pm;
+            if (nb >= 0) {
+              xn[d] = 1 - side; xn[t1] = gx[a1]; xn[t2] = gx2[bq];
+              tabulate(M, nb, xn, &tn);
+              avg = 0.5 * (pm + eval_p(M, p, nb, &tn));
+            }
+            for (int a = 0; a < 3; ++a) {
+              double *yc = y + ((size_t)c * 3 + a) * n3, fa = dA * avg * n[a];
+              for (int i = 0; i < n3; ++i) yc[i] += t.phi[i] * fa;
+              if (t.enriched) {
+                double *ye = y + 3L * M->np + ((size_t)M->enr[c] * 3 + a) * M->nef;
+                for (int v = 0; v < M->nef; ++v) ye[v] += t.ephi[v] * fa;
+              }
+            }
+          }
+      }
+    }
+    ptab_free(&t); ptab_free(&tn);
+  }
+  return 0;
+}
+
+/* ----------------------------------------------------------------------------------------------
+ * Div-div penalty (Sec. 4.2, eq. div-div): y = D(v, u) = (div v, tau_D div u)_K with a constant
+ * tau_D per cell (eq. tauD: |u^n|_K h dt / Cr, computed by dgo_tau_divdiv). Cell-local.
+ * ---------------------------------------------------------------------------------------------- */
+int dgo_divdiv(void *h, const double *tau_d, const double *u, double *y) {
+  omesh *M = (omesh *)h;
+  int n3 = M->n1 * M->n1 * M->n1;
+  memset(y, 0, sizeof(double) * M->nu);
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < M->nc; ++c) {
+      int nq[3];
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            vstate s; eval_vel(M, u, c, &t, &s);
+            double dv = 0.0;
+            for (int a = 0; a < 3; ++a) dv += s.gb[a][a] + s.gt[a][a];
+            double f = dV * tau_d[c] * dv;
+            for (int a = 0; a < 3; ++a) {
+              double *yc = y + ((size_t)c * 3 + a) * n3;
+              for (int i = 0; i < n3; ++i) yc[i] += t.gphi[3 * i + a] * f;
+              if (t.enriched) {
+                double *ye = y + 3L * M->np + ((size_t)M->enr[c] * 3 + a) * M->nef;
+                for (int v = 0; v < M->nef; ++v) ye[v] += t.egphi[v][a] * f;
+              }
+            }
+          }
+    }
+    ptab_free(&t);
+  }
+  return 0;
+}
+
+/* tau_D per cell (eq. tauD): the volume average of |u| over the cell times h dt / Cr, with h the cube
+ * root of the cell volume. */
+int dgo_tau_divdiv(void *h, const double *u, double dt, double cr, double *tau_d) {
+  omesh *M = (omesh *)h;
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < M->nc; ++c) {
+      int nq[3];
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      double vol = 0.0, mag = 0.0;
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            vstate s; eval_vel(M, u, c, &t, &s);
+            double uu[3] = {s.ub[0] + s.ut[0], s.ub[1] + s.ut[1], s.ub[2] + s.ut[2]};
+            vol += dV;
+            mag += dV * sqrt(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+          }
+      tau_d[c] = (mag / vol) * cbrt(vol) * dt / cr;
+    }
+    ptab_free(&t);
+  }
+  return 0;
+}
+
+/* ----------------------------------------------------------------------------------------------
+ * Inverse of the velocity mass matrix (Sec. 4.2 mass term; the explicit convective step needs
+ * M^-1 exactly): cell by cell, the mass matrix of the cell's space (standard plus switched-on
+ * enrichment) assembled with its velocity point set and solved by Gaussian elimination with
+ * partial pivoting. x = M^-1 r; switched-off enrichment slots are zero.
+ * ---------------------------------------------------------------------------------------------- */
+int dgo_inverse_mass(void *h, const double *r, double *x) {
+  omesh *M = (omesh *)h;
+  const int n3 = M->n1 * M->n1 * M->n1, nef = M->nef, N = n3 + nef;
+  memset(x, 0, sizeof(double) * M->nu);
+  int status = 0;
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+    double *A = (double *)malloc(sizeof(double) * (size_t)N * N);
+    double *B = (double *)malloc(sizeof(double) * (size_t)N * 3);
+#pragma omp for schedule(dynamic, 2)
+    for (int c = 0; c < M->nc; ++c) {
+      int nq[3], en = M->enr[c];
+      const int Nc = en >= 0 ? N : n3;
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      memset(A, 0, sizeof(double) * (size_t)N * N);
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]}, phi[8 + MAXP * MAXP * MAXP];
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            for (int i = 0; i < n3; ++i) phi[i] = t.phi[i];
+            for (int v = 0; v < nef && en >= 0; ++v) phi[n3 + v] = t.ephi[v];
+            for (int i = 0; i < Nc; ++i)
+              for (int j = 0; j < Nc; ++j) A[(size_t)i * Nc + j] += dV * phi[i] * phi[j];
+          }
+      for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i < n3; ++i) B[(size_t)i * 3 + a] = r[((size_t)c * 3 + a) * n3 + i];
+        for (int v = 0; v < nef && en >= 0; ++v) B[(size_t)(n3 + v) * 3 + a] = r[3L * M->np + ((size_t)en * 3 + a) * nef + v];
+      }
+      if (solve_dense(Nc, A, B, 3) != 0) {
+#pragma omp atomic write
+        status = -1;
+        continue;
+      }
+      for (int a = 0; a < 3; ++a) {
+        for (int i = 0; i < n3; ++i) x[((size_t)c * 3 + a) * n3 + i] = B[(size_t)i * 3 + a];
+        for (int v = 0; v < nef && en >= 0; ++v) x[3L * M->np + ((size_t)en * 3 + a) * nef + v] = B[(size_t)(n3 + v) * 3 + a];
+      }
+    }
+    free(A); free(B);
+    ptab_free(&t);
+  }
+  return status;
+}

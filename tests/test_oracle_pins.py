@@ -737,3 +737,91 @@ def test_projection_into_switched_off_cells_keeps_polynomials():
     assert _l2_rel(m, un, u) < 1e-11
     ue = un[3 * m.n_p:].reshape(m.n_e, -1)
     assert not np.any(ue[on == 0])
+
+
+# ---------------------------------------------------------------------------------------------
+# Projection-step operators (Sec. 4.2): pressure gradient P, div-div penalty D, and the inverse
+# mass of the explicit convective step
+# ---------------------------------------------------------------------------------------------
+
+def test_gradient_of_continuous_pressure_is_the_volume_integral():
+    """For continuous p the face terms and -(div v, p) integrate by parts to (v, grad p) (also on
+    walls, where {{p}} = p^-): v . P(p) = int v . grad p; p = y^3/3 + y, v = (0, y^2, 0)."""
+    m = O.Mesh(3, 4, 2, 3, n_layers=0)
+    p = (lambda X: X[:, 1] ** 3 / 3 + X[:, 1])(m.node_coords())
+    v = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: y ** 2, lambda x, y, z: 0 * y)
+    ref = 2 * math.pi * math.pi * (2.0 / 5 + 2.0 / 3)
+    assert abs(v @ m.gradient(p) / ref - 1.0) < 1e-12
+
+
+def test_gradient_is_the_transpose_of_the_divergence_where_v_n_vanishes():
+    """On interior faces P(v, p) = -C(p, v) term by term (same average); the volume terms agree by
+    integration by parts, exact for polynomial fields with these rules; on walls they differ by
+    (p, v.n). With v_y zero on the wall node layers v.n = 0 there, so v . P(p) = p . (-C v) for a
+    discontinuous random p and a random standard v (enriched cells still use their point sets)."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    n1 = m.k + 1
+    p = I.uniform(1, m.n_p, -1, 1)
+    v = I.uniform(2, m.n_u, -1, 1)
+    v[3 * m.n_p:] = 0.0
+    std = v[: 3 * m.n_p].reshape(8, 8, 8, 3, n1, n1, n1)     # cz, cy, cx, comp, lz, ly, lx
+    std[:, 0, :, 1, :, 0, :] = 0.0
+    std[:, 7, :, 1, :, n1 - 1, :] = 0.0
+    lhs, rhs = v @ m.gradient(p), p @ m.divergence(v)
+    assert abs(lhs - rhs) < 1e-12 * (abs(v) @ np.abs(m.gradient(p)))
+
+
+def test_gradient_enriched_test_functions_against_the_point_rule():
+    """p = y (continuous): the enriched outputs of component y sum to
+    -int d(psi)/dy y dV + (psi y n_y) on the face away from the wall (psi = 0 on the wall; the enriched
+    test functions psi N_v e_y sum to psi e_y). The volume integral is the q_w-point Gauss rule of the
+    wall-normal direction, written out here with NumPy's rule and the oracle's pinned psi, psi'."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    y = m.gradient(m.node_coords()[:, 1].copy())
+    ye = y[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    s = w.u_tau / w.nu
+    xq, wq = np.polynomial.legendre.leggauss(8)
+    xq, wq = 0.5 * (xq + 1.0), 0.5 * wq
+    vol = -sum(wi * dy * O.psi_spalding(xi * dy * s)[1] * s * (-1.0 + xi * dy) for xi, wi in zip(xq, wq))
+    face = O.psi_spalding(dy * s)[0] * (-1.0 + dy)
+    ref = 2 * (2 * math.pi * math.pi) * (vol + face)
+    assert abs(ye[:, 1, :].sum() / ref - 1.0) < 1e-12
+
+
+def test_divdiv_closed_form_null_space_and_tau():
+    """D(u, u) = sum_K tau_K int (div u)^2 for u = (0, y^2, 0) with constant tau (= c int 4 y^2);
+    D u = 0 for divergence-free shear flows with equal-weight enrichment; tau_D of a uniform flow U
+    is U h dt / Cr with h the cube root of the cell volume."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    c = 0.37
+    tau = np.full(m.nc, c)
+    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: y ** 2, lambda x, y, z: 0 * y)
+    ref = c * 2 * math.pi * math.pi * 8.0 / 3.0
+    assert abs(u @ m.divdiv(tau, u) / ref - 1.0) < 1e-12
+    s = _std_field(m, lambda x, y, z: 1 - y ** 2, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    s[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = w.u_tau
+    assert np.abs(m.divdiv(tau, s)).max() < 1e-13
+    U, dt, cr = 0.8, 1e-3, 0.14
+    uu = _std_field(m, lambda x, y, z: U + 0 * y, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    vol = np.array([(np.ptp(X[k, :, 0])) * np.ptp(X[k, :, 1]) * np.ptp(X[k, :, 2]) for k in range(m.nc)])
+    assert np.allclose(m.tau_divdiv(uu, dt, cr), U * np.cbrt(vol) * dt / cr, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_inverse_mass_inverts_the_mass_operator(geometry):
+    """M^-1 (M u) = u for a velocity with enrichment, measured as functions (L2 norm): the wall-cell
+    systems are ill-conditioned, so coefficients may move along nearly null directions."""
+    if geometry:
+        w = I.bump_workload("im", 5, 4, 2, 2, seed=36)
+    else:
+        w = I.Workload("im", 3, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=37)
+    m = O.Mesh(**w.mesh_kwargs())
+    u = I.workload_velocity(m.node_coords(), m.n_e, w)
+    u[3 * m.n_p:] += 0.2 * w.u_tau * I.uniform(w.seed, u.size - 3 * m.n_p, -1, 1)
+    x = m.inverse_mass(m.vmass(u))
+    assert _l2_rel(m, x, u) < 1e-10
