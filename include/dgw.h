@@ -138,6 +138,22 @@ dgw_status dgw_set_wall_shear_stress(dgw_mesh_t mesh, const double *tau_nodes_de
 dgw_status dgw_project_velocity(dgw_mesh_t mesh, const double *tau_nodes_dev, const double *u_old_dev,
                                 double *u_new_dev, void *stream);
 
+/* Operators of the projection step (Sec. 4.2, eq. projectionspat), FP64, device buffers:
+ * pressure gradient y = P(v, p) = -(div v, p)_K + (v, {{p}} n)_dK with {{p}} = p^- on walls, for every
+ * velocity test function (standard and enriched). p: n_p doubles, y: n_u doubles. */
+dgw_status dgw_apply_gradient(dgw_mesh_t mesh, const double *p, double *y, void *stream);
+/* tau_D per cell (eq. tauD): tau_D = |u|_K h dt / Cr with |u|_K the volume average of the velocity
+ * magnitude over the cell and h the cube root of the cell volume. u: n_u doubles, tau_d: nc
+ * doubles (cells lexicographic). */
+dgw_status dgw_tau_divdiv(dgw_mesh_t mesh, const double *u, double dt, double cr, double *tau_d, void *stream);
+/* div-div penalty y = D(v, u) = (div v, tau_D div u)_K (eq. div-div), cell-local; u, y: n_u doubles. */
+dgw_status dgw_apply_divdiv(dgw_mesh_t mesh, const double *tau_d, const double *u, double *y, void *stream);
+/* x = M^-1 r (Sec. 4.2 mass term), exactly: cells without switched-on enrichment by the collocation
+ * inverse S^-1 W^-1 S^-T, the others by the Cholesky factor of the cell mass matrix (computed on the
+ * first call after every change of the space, then kept). r, x: n_u doubles, distinct buffers.
+ * Synchronises `stream` when it factorises. */
+dgw_status dgw_apply_inverse_mass(dgw_mesh_t mesh, const double *r, double *x, void *stream);
+
 /* Switch-off of the wall model (Sec. 3.2): from now on, and again after every change of tau_w, a
  * wall column is switched off when every point of the velocity point set of its wall-nearest
  * enriched cell has y+ < yplus_off (y+ from the linear y_h and tau_w,h); the paper takes 30 and

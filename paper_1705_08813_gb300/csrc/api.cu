@@ -425,11 +425,38 @@ dgw_status dgw_project_velocity(dgw_mesh_t M, const double *tau_nodes, const dou
   if (st != DGW_OK) return st;
   dgw_helm_free(M);
   int bad = -1;
-  st = cuda_check(launch_projection(M, tau_nodes, u_old, u_new, s, &bad), "dgw_project_velocity");
+  st = cuda_check(launch_projection(M, tau_nodes, 1, &u_old, &u_new, s, &bad), "dgw_project_velocity");
   if (st == DGW_OK && bad >= 0)
     return set_error(DGW_EDEVICE, "dgw_project_velocity: the mass matrix of cell " + std::to_string(bad) +
                                       " is not numerically positive definite in the new space");
   return st;
+}
+
+dgw_status dgw_apply_gradient(dgw_mesh_t M, const double *p, double *y, void *stream) {
+  if (!M || !p || !y) return set_error(DGW_EINVAL, "dgw_apply_gradient: null argument");
+  return cuda_check(launch_ns_op(0, M, p, nullptr, 0.0, y, (cudaStream_t)stream), "dgw_apply_gradient");
+}
+
+dgw_status dgw_tau_divdiv(dgw_mesh_t M, const double *u, double dt, double cr, double *tau_d, void *stream) {
+  if (!M || !u || !tau_d) return set_error(DGW_EINVAL, "dgw_tau_divdiv: null argument");
+  if (!(dt > 0.0) || !(cr > 0.0)) return set_error(DGW_EINVAL, "dgw_tau_divdiv: dt and cr must be positive");
+  return cuda_check(launch_ns_op(2, M, u, nullptr, dt / cr, tau_d, (cudaStream_t)stream), "dgw_tau_divdiv");
+}
+
+dgw_status dgw_apply_divdiv(dgw_mesh_t M, const double *tau_d, const double *u, double *y, void *stream) {
+  if (!M || !tau_d || !u || !y) return set_error(DGW_EINVAL, "dgw_apply_divdiv: null argument");
+  return cuda_check(launch_ns_op(1, M, u, tau_d, 0.0, y, (cudaStream_t)stream), "dgw_apply_divdiv");
+}
+
+dgw_status dgw_apply_inverse_mass(dgw_mesh_t M, const double *r, double *x, void *stream) {
+  if (!M || !r || !x) return set_error(DGW_EINVAL, "dgw_apply_inverse_mass: null argument");
+  if (r == x) return set_error(DGW_EINVAL, "dgw_apply_inverse_mass: r and x must not overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_collocation_inverse_mass(M, r, x, s);
+  if (e == cudaSuccess) e = launch_inverse_mass_cells(M, r, x, s);
+  if (e == cudaErrorInvalidValue)
+    return set_error(DGW_EDEVICE, "dgw_apply_inverse_mass: a wall-cell mass matrix is not numerically positive definite");
+  return cuda_check(e, "dgw_apply_inverse_mass");
 }
 
 dgw_status dgw_apply_laplace(dgw_mesh_t M, int prec, const void *p, void *y, void *stream) {

@@ -123,6 +123,8 @@ struct dgw_mesh {
   double *proj_A = nullptr;         // L2 projection scratch: [ne][N][N] cell matrices (lazily allocated)
   double *proj_P = nullptr;         // [ne][points][3] old field at the points
   int *proj_err = nullptr;
+  int proj_nvec = 0;                // vectors proj_P has room for
+  bool mass_factor_valid = false;   // proj_A holds the Cholesky factors of the current space
   double *aux_vol = nullptr, *aux_face = nullptr;   // (y_h, y+) at linear-set points
   double *dye_dev = nullptr;
   double *diag64 = nullptr;     // Jacobi diagonal of the Laplace operator
@@ -222,8 +224,12 @@ cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, cudaStream_t s);
 cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s);
 cudaError_t launch_switch(dgw_mesh *M, cudaStream_t s);
-cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, const double *u_old, double *u_new, cudaStream_t s,
-                              int *bad_cell);
+cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, int nvec, const double *const *u_old,
+                              double *const *u_new, cudaStream_t s, int *bad_cell);
+cudaError_t launch_inverse_mass_cells(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
+cudaError_t launch_collocation_inverse_mass(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
+cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *tau_d, double dt_over_cr, double *y,
+                         cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 

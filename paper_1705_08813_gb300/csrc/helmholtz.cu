@@ -318,6 +318,8 @@ static cudaError_t helm_setup(dgw_mesh *M, int restart) {
       detw_kernel<<<1216, 256, 0, s>>>(M->v64, H->vol, H->detw);
       e = cudaGetLastError();
     }
+    // the tables are read on other streams too (the exact inverse mass): finish them here
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   // enriched blocks: M applied to the enrichment unit vectors of component x; the nef x nef blocks
   // are inverted on the host (stored with a stride of 64 per wall cell)
@@ -490,6 +492,20 @@ dgw_status helmholtz_solve(dgw_mesh *M, double gamma, const double *rhs, double 
   return DGW_OK;
 }
 
+}  // namespace dgw
+
+namespace dgw {
+// x = M^-1 r in every cell without switched-on enrichment (S^-1 W^-1 S^-T, exact there); cells with
+// the wall model on get the block-diagonal approximation (the caller overwrites them)
+cudaError_t launch_collocation_inverse_mass(dgw_mesh *M, const double *r, double *x, cudaStream_t s) {
+  cudaError_t e = helm_setup(M, M->helm ? M->helm->m : 1);
+  if (e != cudaSuccess) return e;
+  dgw_helm *H = M->helm;
+  note_launch();
+  inverse_mass_kernel<<<M->nc, 128, 0, s>>>(r, x, H->m1inv, H->detw, M->v64.enr, M->v64.slot, H->meeinv, M->n1, M->nef,
+                                            M->np, 1.0);
+  return cudaGetLastError();
+}
 }  // namespace dgw
 
 void dgw_helm_free(dgw_mesh *M) {

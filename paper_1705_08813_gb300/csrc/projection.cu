@@ -97,6 +97,9 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
   const ProjLayout L = proj_layout(n, q0, q1, m.nef);
   double *W = sm + L.W, *PSI = sm + L.PSI, *T1 = sm + L.T1, *T2 = sm + L.T2, *R = sm + L.RHS, *col = sm + L.COL;
   const int e = blockIdx.x, c = enr_cell[e], tid = threadIdx.x, nt = blockDim.x;
+  // P == nullptr: factorise only (the inverse mass of cells with the wall model switched on)
+  const bool rhs = P != nullptr;
+  if (!rhs && m.enr[c] < 0) return;
   // switched off in the new space: the standard block alone (stride N kept), zero enrichment
   const int nef = m.enr[c] >= 0 ? m.nef : 0, Nc = n3 + nef;
   double *A = Ag + (size_t)e * N * N;
@@ -141,7 +144,7 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
     A[(size_t)i * N + j] = s;
   }
   // 4. enriched-standard blocks and the standard right-hand sides
-  for (int p = tid; p < n3 * (nef + 3); p += nt) {
+  for (int p = tid; p < n3 * (nef + (rhs ? 3 : 0)); p += nt) {
     const int i = p % n3, k = p / n3;   // k < nef: enriched column v = k; else component k - nef
     const int a1 = i % n, b1 = (i / n) % n, c1 = i / n2;
     double s = 0.0;
@@ -163,7 +166,7 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
     }
   }
   // 5. enriched-enriched block and the enriched right-hand sides
-  for (int p = tid; p < nef * (nef + 3); p += nt) {
+  for (int p = tid; p < nef * (nef + (rhs ? 3 : 0)); p += nt) {
     const int v = p % nef, k = p / nef;
     double s = 0.0;
     for (int t = 0; t < npts; ++t) {
@@ -198,6 +201,7 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
     }
     __syncthreads();
   }
+  if (!rhs) return;
   // 7. L y = r, then L^T x = y, for the three components
   for (int j = 0; j < Nc; ++j) {
     const double ljj = A[(size_t)j * N + j];
@@ -230,50 +234,136 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
   }
 }
 
+// x = M^-1 r in the cells with the wall model switched on, from the Cholesky factor of the cell
+// mass matrix in Ag (one CTA per enriched cell; the other cells are left untouched)
+__global__ void chol_solve_kernel(MeshView<double> m, const int *__restrict__ enr_cell, const double *__restrict__ Ag,
+                                  const double *__restrict__ r, double *__restrict__ x) {
+  extern __shared__ double R[];
+  const int e = blockIdx.x, c = enr_cell[e], tid = threadIdx.x, nt = blockDim.x;
+  if (m.enr[c] < 0) return;
+  const int n = m.n1, n3 = n * n * n, nef = m.nef, N = n3 + nef;
+  const double *A = Ag + (size_t)e * N * N;
+  for (int p = tid; p < 3 * N; p += nt) {
+    const int a = p / N, i = p % N;
+    R[p] = i < n3 ? r[((size_t)c * 3 + a) * n3 + i] : r[3 * m.np + ((size_t)e * 3 + a) * nef + (i - n3)];
+  }
+  __syncthreads();
+  for (int j = 0; j < N; ++j) {
+    if (tid < 3) R[tid * N + j] /= A[(size_t)j * N + j];
+    __syncthreads();
+    for (int p = tid; p < 3 * (N - j - 1); p += nt) {
+      const int a = p / (N - j - 1), i = j + 1 + p % (N - j - 1);
+      R[a * N + i] -= A[(size_t)i * N + j] * R[a * N + j];
+    }
+    __syncthreads();
+  }
+  for (int j = N - 1; j >= 0; --j) {
+    if (tid < 3) R[tid * N + j] /= A[(size_t)j * N + j];
+    __syncthreads();
+    for (int p = tid; p < 3 * j; p += nt) {
+      const int a = p / j, i = p % j;
+      R[a * N + i] -= A[(size_t)j * N + i] * R[a * N + j];
+    }
+    __syncthreads();
+  }
+  for (int p = tid; p < 3 * N; p += nt) {
+    const int a = p / N, i = p % N;
+    if (i < n3) x[((size_t)c * 3 + a) * n3 + i] = R[p];
+    else x[3 * m.np + ((size_t)e * 3 + a) * nef + (i - n3)] = R[p];
+  }
+}
+
 }  // namespace
 
-cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, const double *u_old, double *u_new, cudaStream_t s,
-                              int *bad_cell) {
-  *bad_cell = -1;
+static cudaError_t proj_scratch(dgw_mesh *M, int nvec) {
   const int n = M->n1, N = n * n * n + M->nef;
-  const int q0 = M->basis64.q[QSET_LIN], q1 = M->basis64.q[QSET_WALL], npts = q0 * q1 * q0;
+  const int npts = M->basis64.q[QSET_LIN] * M->basis64.q[QSET_WALL] * M->basis64.q[QSET_LIN];
   cudaError_t e = cudaSuccess;
-  if (M->ne > 0 && !M->proj_A) {
-    // scratch: cell matrices, point values of the old field, error word
-    void *a = nullptr, *p = nullptr, *w = nullptr;
+  if (!M->proj_A) {
+    void *a = nullptr, *w = nullptr;
     e = cudaMalloc(&a, (size_t)M->ne * N * N * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&p, (size_t)M->ne * npts * 3 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(int));
-    for (void *q : {a, p, w})
+    for (void *q : {a, w})
       if (q) M->allocs.push_back(q);
     if (e != cudaSuccess) return e;
-    M->hbm_bytes += ((size_t)M->ne * N * N + (size_t)M->ne * npts * 3) * sizeof(double) + sizeof(int);
+    M->hbm_bytes += (size_t)M->ne * N * N * sizeof(double) + sizeof(int);
     M->proj_A = (double *)a;
-    M->proj_P = (double *)p;
     M->proj_err = (int *)w;
   }
-  if (M->ne > 0) {
+  if (M->proj_nvec < nvec) {
+    void *p = nullptr;
+    e = cudaMalloc(&p, (size_t)nvec * M->ne * npts * 3 * sizeof(double));
+    if (e != cudaSuccess) return e;
+    M->allocs.push_back(p);
+    M->hbm_bytes += (size_t)nvec * M->ne * npts * 3 * sizeof(double);
+    M->proj_P = (double *)p;
+    M->proj_nvec = nvec;
+  }
+  return e;
+}
+
+cudaError_t launch_inverse_mass_cells(dgw_mesh *M, const double *r, double *x, cudaStream_t s) {
+  if (M->ne == 0) return cudaSuccess;
+  cudaError_t e = proj_scratch(M, 1);
+  if (e != cudaSuccess) return e;
+  const int n = M->n1, N = n * n * n + M->nef;
+  const int q0 = M->basis64.q[QSET_LIN], q1 = M->basis64.q[QSET_WALL];
+  if (!M->mass_factor_valid) {
+    const ProjLayout L = proj_layout(n, q0, q1, M->nef);
+    const size_t smem = (size_t)L.total * sizeof(double);
+    e = cudaFuncSetAttribute(project_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M->proj_err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     note_launch();
-    project_eval_kernel<<<M->ne, 128, 0, s>>>(M->v64, M->enr_cell_dev, u_old, M->v64.wt_vol[0], M->v64.nvol[0],
-                                              M->proj_P);
+    project_solve_kernel<<<M->ne, 256, smem, s>>>(M->v64, M->enr_cell_dev, M->v64.wt_vol[0], M->v64.nvol[0], nullptr,
+                                                  M->proj_A, nullptr, M->proj_err);
+    int h = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, M->proj_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (h) return cudaErrorInvalidValue;   // a cell mass matrix is not numerically positive definite
+    M->mass_factor_valid = true;
+  }
+  note_launch();
+  chol_solve_kernel<<<M->ne, 128, (size_t)3 * N * sizeof(double), s>>>(M->v64, M->enr_cell_dev, M->proj_A, r, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, int nvec, const double *const *u_old,
+                              double *const *u_new, cudaStream_t s, int *bad_cell) {
+  *bad_cell = -1;
+  const int n = M->n1;
+  const int q0 = M->basis64.q[QSET_LIN], q1 = M->basis64.q[QSET_WALL], npts = q0 * q1 * q0;
+  cudaError_t e = M->ne > 0 ? proj_scratch(M, nvec) : cudaSuccess;
+  const size_t pstride = (size_t)M->ne * npts * 3;
+  // every vector is evaluated in the old space before the tables change
+  for (int v = 0; v < nvec && e == cudaSuccess && M->ne > 0; ++v) {
+    note_launch();
+    project_eval_kernel<<<M->ne, 128, 0, s>>>(M->v64, M->enr_cell_dev, u_old[v], M->v64.wt_vol[0], M->v64.nvol[0],
+                                              M->proj_P + v * pstride);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_set_tau_nodes(M, tau_new, s);
-  if (e == cudaSuccess && u_new != u_old) e = cudaMemcpyAsync(u_new, u_old, M->nu * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  for (int v = 0; v < nvec && e == cudaSuccess; ++v)
+    if (u_new[v] != u_old[v]) e = cudaMemcpyAsync(u_new[v], u_old[v], M->nu * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess || M->ne == 0) return e;
   const ProjLayout L = proj_layout(n, q0, q1, M->nef);
   const size_t smem = (size_t)L.total * sizeof(double);
   e = cudaFuncSetAttribute(project_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(M->proj_err, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  note_launch();
-  project_solve_kernel<<<M->ne, 256, smem, s>>>(M->v64, M->enr_cell_dev, M->v64.wt_vol[0], M->v64.nvol[0], M->proj_P,
-                                                M->proj_A, u_new, M->proj_err);
-  e = cudaGetLastError();
+  for (int v = 0; v < nvec && e == cudaSuccess; ++v) {
+    note_launch();
+    project_solve_kernel<<<M->ne, 256, smem, s>>>(M->v64, M->enr_cell_dev, M->v64.wt_vol[0], M->v64.nvol[0],
+                                                  M->proj_P + v * pstride, M->proj_A, u_new[v], M->proj_err);
+    e = cudaGetLastError();
+  }
   int h = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, M->proj_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && h) *bad_cell = h - 1;
+  // the last factorisation is that of the new space: the inverse mass can reuse it
+  if (e == cudaSuccess && !h) M->mass_factor_valid = true;
   return e;
 }
 

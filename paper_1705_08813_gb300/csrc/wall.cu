@@ -390,6 +390,7 @@ __global__ void switch_kernel(const double *__restrict__ aux_vol, int nvol, cons
 }
 
 cudaError_t launch_switch(dgw_mesh *M, cudaStream_t s) {
+  M->mass_factor_valid = false;   // the cell spaces may change
   if (M->ne == 0) return cudaSuccess;
   note_launch();
   switch_kernel<<<(M->ne + 127) / 128, 128, 0, s>>>(M->aux_vol, M->v64.nvol[0], M->wslot_dev, M->enr_cell_dev, M->ne,

@@ -21,7 +21,8 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
            "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
-           "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active"]
+           "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active",
+           "dgw_apply_gradient", "dgw_tau_divdiv", "dgw_apply_divdiv", "dgw_apply_inverse_mass"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -91,6 +92,10 @@ def load(path: str = LIB_PATH):
     lib.dgw_set_wall_shear_stress.argtypes = [vp, vp, vp]
     lib.dgw_project_velocity.argtypes = [vp, vp, vp, vp, vp]
     lib.dgw_set_enrichment_switch.argtypes = [vp, ctypes.c_double, vp]
+    lib.dgw_apply_gradient.argtypes = [vp, vp, vp, vp]
+    lib.dgw_tau_divdiv.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
+    lib.dgw_apply_divdiv.argtypes = [vp, vp, vp, vp, vp]
+    lib.dgw_apply_inverse_mass.argtypes = [vp, vp, vp, vp]
     lib.dgw_enrichment_active.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]
     lib.dgw_helmholtz_solve.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.POINTER(HelmholtzOpts),
                                         ctypes.POINTER(SolveInfo), vp]
@@ -150,6 +155,7 @@ class Mesh:
         a, b, c, d = ctypes.c_long(), ctypes.c_long(), ctypes.c_long(), ctypes.c_size_t()
         _check(lib.dgw_mesh_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         self.n_p, self.n_u, self.n_e, self.hbm_bytes = a.value, b.value, c.value, d.value
+        self.nc = nx * ny * nz
         self.k = k
 
     def close(self):
@@ -225,6 +231,36 @@ class Mesh:
                                              _ptr(u_old, torch.float64, self.n_u, "u_old"),
                                              _ptr(u_new, torch.float64, self.n_u, "u_new"), _stream(stream)))
         return u_new
+
+    def gradient(self, p, y, stream=None):
+        """y = P(v, p), the pressure gradient of the projection step (FP64)."""
+        import torch
+        _check(self.lib.dgw_apply_gradient(self.h, _ptr(p, torch.float64, self.n_p, "p"),
+                                           _ptr(y, torch.float64, self.n_u, "y"), _stream(stream)))
+        return y
+
+    def tau_divdiv(self, u, dt, cr, tau_d, stream=None):
+        """Per-cell tau_D = |u|_K h dt / Cr into tau_d (nc doubles)."""
+        import torch
+        _check(self.lib.dgw_tau_divdiv(self.h, _ptr(u, torch.float64, self.n_u, "u"), ctypes.c_double(dt),
+                                       ctypes.c_double(cr), _ptr(tau_d, torch.float64, self.nc, "tau_d"),
+                                       _stream(stream)))
+        return tau_d
+
+    def divdiv(self, tau_d, u, y, stream=None):
+        """y = D(v, u) = (div v, tau_D div u) per cell."""
+        import torch
+        _check(self.lib.dgw_apply_divdiv(self.h, _ptr(tau_d, torch.float64, self.nc, "tau_d"),
+                                         _ptr(u, torch.float64, self.n_u, "u"), _ptr(y, torch.float64, self.n_u, "y"),
+                                         _stream(stream)))
+        return y
+
+    def inverse_mass(self, r, x, stream=None):
+        """x = M^-1 r (exact, cell by cell)."""
+        import torch
+        _check(self.lib.dgw_apply_inverse_mass(self.h, _ptr(r, torch.float64, self.n_u, "r"),
+                                               _ptr(x, torch.float64, self.n_u, "x"), _stream(stream)))
+        return x
 
     def set_enrichment_switch(self, yplus_off: float, stream=None):
         """Switch the wall model off in wall columns whose wall-nearest cell has y+ < yplus_off."""
