@@ -245,14 +245,56 @@ typedef struct {
  * with the nu_t frozen by the last dgw_update_eddy_viscosity (the paper's right-hand side is
  * gamma M u^^ of the projected velocity). u: on entry the initial guess, on exit the solution
  * (n_u doubles, device); rhs: n_u doubles. Restarted GMRES with right preconditioning by the
- * inverse of gamma times the block-diagonal mass (exact on the standard DoFs of box cells, the
- * volume-scaled reference inverse on curved cells, the 8 x 8 enriched blocks inverted), FP64;
+ * inverse of gamma times the block-diagonal mass (the collocation inverse S^-1 W^-1 S^-T of each
+ * cell's standard block, exact off the wall cells, and the inverted enriched blocks), FP64;
  * the workspace ((restart + 1) + restart vectors of n_u doubles) is allocated on first use and kept
  * with the mesh. info->iterations = Krylov vectors built, rel_residual = the true relative residual
  * of the returned u, ms = host wall time. Synchronises `stream`. Returns DGW_ENOTCONV (u and info
  * filled) when max_iter is reached first. */
 dgw_status dgw_helmholtz_solve(dgw_mesh_t mesh, double gamma, const double *rhs, double *u,
                                const dgw_helmholtz_opts *opts, dgw_solve_info *info, void *stream);
+
+/* ---- Dual-splitting time step ------------------------------------------------------------- */
+
+typedef struct dgw_ns *dgw_ns_t;
+
+typedef struct {
+  double dt;              /* constant time step */
+  double cr;              /* Courant number of tau_D (eq. tauD; the paper takes 0.14) */
+  double force[3];        /* constant body force f (e.g. the mean pressure gradient driving a channel) */
+  double rtol_pressure;   /* relative residual of the pressure solve */
+  double rtol_projection; /* relative residual of the (M + D) solve of the projection step */
+  double rtol_viscous;    /* relative residual of the Helmholtz solve */
+  int max_iter;           /* limit on iterations of every solve */
+  int pressure_mode;      /* dgw_solve_opts.mode of the pressure solve */
+  int update_wall_model;  /* 1: at the start of every step tau_w,B from u^n, the velocity history
+                             L2-projected onto the new space, the convective history recomputed */
+} dgw_ns_params;
+
+typedef struct {
+  int pressure_iterations, projection_iterations, viscous_iterations;
+  double ms;              /* host wall time of the step */
+} dgw_ns_step_info;
+
+/* A time integrator of the dual-splitting scheme (Sec. 4.1, Galerkin forms of Sec. 4.2) on `mesh`,
+ * starting from the velocity u0 (n_u doubles, device, copied). The integrator owns its vectors;
+ * the mesh must outlive it. Synchronises `stream`. */
+dgw_status dgw_ns_create(dgw_mesh_t mesh, const dgw_ns_params *params, const double *u0, void *stream, dgw_ns_t *out);
+dgw_status dgw_ns_destroy(dgw_ns_t ns);
+/* One time step, BDF2 with second-order extrapolation (first order in the first step), constant dt:
+ *   u^  = (sum alpha_i u^{n-i} + dt f - dt M^-1 sum beta_i F^c(u^{n-i})) / gamma_0 (eq. convstepspat)
+ *   A p = (gamma_0 / dt)(-C u^), homogeneous Neumann data on walls (eq. poissonspat)
+ *   (M + D) u^^ = M u^ - (dt / gamma_0) P(v, p)                      (eq. projectionspat)
+ *   (gamma_0 / dt) M u^{n+1} - F^nu(u^{n+1}) = (gamma_0 / dt) M u^^   (eq. helmholtzspat)
+ * with tau_D and nu_t from u^n, CG with the exact inverse mass for the projection and GMRES for the
+ * viscous step. Synchronises `stream`. DGW_ENOTCONV if a solve reaches max_iter. */
+dgw_status dgw_ns_step(dgw_ns_t ns, dgw_ns_step_info *info, void *stream);
+/* Device pointers of the current velocity u^n and pressure p^n (owned by the integrator, valid until
+ * the next step) and the number of steps taken. */
+dgw_status dgw_ns_state(dgw_ns_t ns, const double **u_dev, const double **p_dev, int *steps);
+/* Copy the current velocity (n_u doubles) and/or pressure (n_p doubles) into caller-owned device
+ * buffers (either may be NULL). Asynchronous on `stream`. */
+dgw_status dgw_ns_copy_state(dgw_ns_t ns, double *u_dev, double *p_dev, void *stream);
 
 /* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32): number of
  * levels, the estimated largest eigenvalue of D^-1 A per level (the Chebyshev smoother works on

@@ -318,3 +318,117 @@ class Mesh:
         u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(4096)
         n = self.lib.dgo_nut_cell(self.h, _ptr(u), int(e), _ptr(out))
         return out[:n]
+
+
+def _gmres(apply, b, x0, prec, rtol, restart=60, maxit=3000):
+    """Restarted right-preconditioned GMRES (Saad's algorithm, modified Gram-Schmidt), numpy."""
+    x = x0.copy()
+    nb = np.linalg.norm(b)
+    it = 0
+    while it < maxit:
+        r = b - apply(x)
+        beta = np.linalg.norm(r)
+        if beta <= rtol * nb:
+            return x, it
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        for j in range(restart):
+            z = prec(V[j])
+            Z.append(z)
+            w = apply(z)
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            it += 1
+            e1 = np.zeros(j + 2)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[: j + 2, : j + 1], e1, rcond=None)[0]
+            res = np.linalg.norm(H[: j + 2, : j + 1] @ y - e1)
+            if res <= rtol * nb * 0.5 or H[j + 1, j] == 0.0 or it >= maxit:
+                break
+            V.append(w / H[j + 1, j])
+        x = x + sum(yi * zi for yi, zi in zip(y, Z))
+    return x, it
+
+
+def _pcg(apply, b, x0, prec, rtol, maxit=5000):
+    """Preconditioned conjugate gradients (Hestenes-Stiefel), numpy."""
+    x = x0.copy()
+    r = b - apply(x)
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    nb = np.linalg.norm(b)
+    for it in range(maxit):
+        if np.linalg.norm(r) <= rtol * nb:
+            return x, it
+        q = apply(p)
+        a = rz / (p @ q)
+        x += a * p
+        r -= a * q
+        z = prec(r)
+        rz2 = r @ z
+        p = z + (rz2 / rz) * p
+        rz = rz2
+    raise RuntimeError("projection CG did not converge")
+
+
+class DualSplitting:
+    """One constant-step BDF2/extrapolation step of the dual-splitting scheme after Sec. 4.1 with the
+    Galerkin forms of Sec. 4.2, written with this module's operators (first order in the first step):
+    convective step with the exact inverse mass, pressure Poisson solve (homogeneous Neumann), the
+    projection (M + D) u^^ = M u^ - (dt / gamma_0) P(p) by preconditioned CG, and the viscous
+    Helmholtz step by GMRES, nu_t and tau_D from u^n. With update_wall_model the step starts with the
+    wall shear stress of u^n, the L2 projection of u^n and u^{n-1} onto the new space and a new
+    F^c(u^{n-1})."""
+
+    def __init__(self, mesh: "Mesh", u0, dt, cr=0.14, force=(0.0, 0.0, 0.0), rtol=1e-13,
+                 update_wall_model=False, tau_nodes=None):
+        self.m, self.dt, self.cr, self.rtol = mesh, float(dt), float(cr), float(rtol)
+        self.u = [np.array(u0, dtype=np.float64), None]
+        self.fc_old = None
+        self.p = np.zeros(mesh.n_p)
+        self.steps = 0
+        self.update = update_wall_model
+        self.tau = (np.full(mesh.n_wall_nodes, mesh.params.tau_w) if tau_nodes is None
+                    else np.array(tau_nodes, dtype=np.float64))
+        n3 = (mesh.k + 1) ** 3
+        self.f = np.zeros(mesh.n_u)
+        std = self.f[: 3 * mesh.n_p].reshape(mesh.nc, 3, n3)
+        for a in range(3):
+            std[:, a, :] = force[a]
+
+    def step(self):
+        m, dt = self.m, self.dt
+        second = self.steps > 0
+        g0, a0, a1, b0, b1 = (1.5, 2.0, -0.5, 2.0, -1.0) if second else (1.0, 1.0, 0.0, 1.0, 0.0)
+        if self.update and m.n_e > 0:
+            tn = m.wall_shear(self.u[0])
+            old = self.tau
+            un = m.project(tn, self.u[0])
+            if second:
+                m.set_tau_nodes(old)
+                self.u[1] = m.project(tn, self.u[1])
+                self.fc_old = m.convective(self.u[1])
+            self.u[0] = un
+            self.tau = tn
+        un, unm = self.u
+        fc = m.convective(un)
+        w = b0 * fc + (b1 * self.fc_old if second else 0.0)
+        uh = (a0 * un + (a1 * unm if second else 0.0) + dt * self.f - dt * m.inverse_mass(w)) / g0
+        b = (g0 / dt) * m.divergence(uh)
+        p, _, _ = m.solve(b, rtol=self.rtol, maxit=200000)
+        tau_d = m.tau_divdiv(un, dt, self.cr)
+        rhs = m.vmass(uh) - (dt / g0) * m.gradient(p)
+        uhh, _ = _pcg(lambda v: m.vmass(v) + m.divdiv(tau_d, v), rhs, uh, m.inverse_mass, self.rtol)
+        gam = g0 / dt
+        rhs3 = gam * m.vmass(uhh)
+        unew, _ = _gmres(lambda v: gam * m.vmass(v) + m.viscous(un, v), rhs3, uhh,
+                         lambda v: m.inverse_mass(v) / gam, self.rtol)
+        self.u = [unew, un]
+        self.fc_old = fc
+        self.p = p
+        self.steps += 1
+        return unew, p

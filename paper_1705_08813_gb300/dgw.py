@@ -22,7 +22,8 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
            "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
            "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active",
-           "dgw_apply_gradient", "dgw_tau_divdiv", "dgw_apply_divdiv", "dgw_apply_inverse_mass"]
+           "dgw_apply_gradient", "dgw_tau_divdiv", "dgw_apply_divdiv", "dgw_apply_inverse_mass",
+           "dgw_ns_create", "dgw_ns_destroy", "dgw_ns_step", "dgw_ns_state", "dgw_ns_copy_state"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -31,6 +32,18 @@ class DGWError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class NSParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("cr", ctypes.c_double), ("force", ctypes.c_double * 3),
+                ("rtol_pressure", ctypes.c_double), ("rtol_projection", ctypes.c_double),
+                ("rtol_viscous", ctypes.c_double), ("max_iter", ctypes.c_int), ("pressure_mode", ctypes.c_int),
+                ("update_wall_model", ctypes.c_int)]
+
+
+class NSStepInfo(ctypes.Structure):
+    _fields_ = [("pressure_iterations", ctypes.c_int), ("projection_iterations", ctypes.c_int),
+                ("viscous_iterations", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class MeshParams(ctypes.Structure):
@@ -93,6 +106,11 @@ def load(path: str = LIB_PATH):
     lib.dgw_project_velocity.argtypes = [vp, vp, vp, vp, vp]
     lib.dgw_set_enrichment_switch.argtypes = [vp, ctypes.c_double, vp]
     lib.dgw_apply_gradient.argtypes = [vp, vp, vp, vp]
+    lib.dgw_ns_create.argtypes = [vp, ctypes.POINTER(NSParams), vp, vp, ctypes.POINTER(vp)]
+    lib.dgw_ns_destroy.argtypes = [vp]
+    lib.dgw_ns_step.argtypes = [vp, ctypes.POINTER(NSStepInfo), vp]
+    lib.dgw_ns_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
+    lib.dgw_ns_copy_state.argtypes = [vp, vp, vp, vp]
     lib.dgw_tau_divdiv.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
     lib.dgw_apply_divdiv.argtypes = [vp, vp, vp, vp, vp]
     lib.dgw_apply_inverse_mass.argtypes = [vp, vp, vp, vp]
@@ -367,6 +385,62 @@ def counters():
     a, b = ctypes.c_ulonglong(), ctypes.c_ulonglong()
     lib.dgw_counters(ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
+
+
+class DualSplitting:
+    """Time integrator of the dual-splitting scheme on a Mesh (dgw_ns_*): u0 is copied; velocity()
+    and pressure() return copies of the current state as CUDA tensors."""
+
+    def __init__(self, mesh: Mesh, u0, *, dt, cr=0.14, force=(0.0, 0.0, 0.0), rtol_pressure=1e-10,
+                 rtol_projection=1e-10, rtol_viscous=1e-10, max_iter=2000, pressure_mode=1,
+                 update_wall_model=False, stream=None):
+        import torch
+        self.mesh, self.lib = mesh, mesh.lib
+        self.params = NSParams(dt, cr, (ctypes.c_double * 3)(*force), rtol_pressure, rtol_projection, rtol_viscous,
+                               max_iter, pressure_mode, 1 if update_wall_model else 0)
+        h = ctypes.c_void_p()
+        _check(self.lib.dgw_ns_create(mesh.h, ctypes.byref(self.params), _ptr(u0, torch.float64, mesh.n_u, "u0"),
+                                      _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, stream=None) -> dict:
+        info = NSStepInfo()
+        _check(self.lib.dgw_ns_step(self.h, ctypes.byref(info), _stream(stream)))
+        return {"pressure_iterations": info.pressure_iterations, "projection_iterations": info.projection_iterations,
+                "viscous_iterations": info.viscous_iterations, "ms": info.ms}
+
+    def _state(self):
+        u, p, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()
+        _check(self.lib.dgw_ns_state(self.h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(n)))
+        return u.value, p.value, n.value
+
+    def velocity(self, stream=None):
+        return self._copy_state(True, stream)
+
+    def pressure(self, stream=None):
+        return self._copy_state(False, stream)
+
+    def _copy_state(self, vel, stream):
+        import torch
+        out = torch.empty(self.mesh.n_u if vel else self.mesh.n_p, dtype=torch.float64, device="cuda")
+        ptr = ctypes.c_void_p(out.data_ptr())
+        _check(self.lib.dgw_ns_copy_state(self.h, ptr if vel else None, None if vel else ptr, _stream(stream)))
+        return out
+
+    @property
+    def steps(self) -> int:
+        return self._state()[2]
+
+    def close(self):
+        if self.h:
+            self.lib.dgw_ns_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mesh_for(workload, **kw) -> Mesh:

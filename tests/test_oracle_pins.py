@@ -825,3 +825,22 @@ def test_inverse_mass_inverts_the_mass_operator(geometry):
     u[3 * m.n_p:] += 0.2 * w.u_tau * I.uniform(w.seed, u.size - 3 * m.n_p, -1, 1)
     x = m.inverse_mass(m.vmass(u))
     assert _l2_rel(m, x, u) < 1e-10
+
+
+# ---------------------------------------------------------------------------------------------
+# Dual-splitting step (Sec. 4.1, eqs. convstepspat, poissonspat, projectionspat, helmholtzspat)
+# ---------------------------------------------------------------------------------------------
+
+def test_dual_splitting_keeps_poiseuille_flow_steady():
+    """Laminar channel flow u = U (1 - y^2) e_x driven by f = 2 nu U e_x is a steady solution: the
+    convective term vanishes for the shear flow, u^ = u + dt f / gamma_0 is divergence-free (p = 0),
+    the div-div term vanishes, and -F^nu(u) = M f for the quadratic profile (Q2, exact quadrature).
+    A wrong sign, a BDF coefficient that does not sum to gamma_0 or a dropped dt/gamma_0 breaks it."""
+    nu, U = 1e-2, 1.0
+    m = O.Mesh(4, 4, 2, 2, n_layers=0, nu=nu)
+    u0 = _std_field(m, lambda x, y, z: U * (1 - y ** 2), lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    ds = O.DualSplitting(m, u0, dt=5e-3, force=(2 * nu * U, 0.0, 0.0))
+    for _ in range(3):
+        u, p = ds.step()
+    assert _l2_rel(m, u, u0) < 1e-11
+    assert np.abs(p).max() < 1e-10
