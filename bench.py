@@ -573,6 +573,41 @@ def run_wall_update(args):
     return 0
 
 
+def run_ns_step(args):
+    """Dual-splitting time steps on the workload (convective step, pressure solve, projection, viscous
+    step; with --wall-update-steps also tau_w and the L2 projection at the start of every step),
+    constant dt, body force u_tau^2 / delta along x; host wall time per step after --warmup steps."""
+    import torch
+    from paper_1705_08813_gb300 import dgw, inputs as I
+    torch.cuda.set_device(0)
+    w = I.WORKLOADS[args.workload]
+    m = dgw.mesh_for(w, enrich_l=args.enrich_l)
+    nef = 8 if args.enrich_l == 1 else 1
+    u0 = torch.from_numpy(I.workload_velocity(m.node_coords(), m.n_e, w, nef=nef)).cuda()
+    delta = 0.5 * w.ly
+    ns = dgw.DualSplitting(m, u0, dt=args.dt, force=(w.tau_w / delta, 0.0, 0.0), rtol_pressure=1e-10,
+                           rtol_projection=1e-10, rtol_viscous=1e-10, pressure_mode=args.solve_mode,
+                           update_wall_model=args.wall_update_steps)
+    infos = []
+    for it in range(args.warmup + max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = ns.step()
+        torch.cuda.synchronize()
+        info["wall_ms"] = 1e3 * (time.perf_counter() - t0)
+        if it >= args.warmup:
+            infos.append(info)
+    med = lambda k: statistics.median(i[k] for i in infos)
+    print(json.dumps({"metric": "dual-splitting time step (ms per step)", "workload": w.name,
+                      "enrich_l": args.enrich_l, "n_u": m.n_u, "n_p": m.n_p, "dt": args.dt,
+                      "wall_model_update": bool(args.wall_update_steps), "pressure_mode": args.solve_mode,
+                      "steps": len(infos), "ms_per_step": med("wall_ms"),
+                      "pressure_iterations": med("pressure_iterations"),
+                      "projection_iterations": med("projection_iterations"),
+                      "viscous_iterations": med("viscous_iterations")}), flush=True)
+    return 0
+
+
 def run_profile_kernel(args):
     """A few launches of one operator kernel on a channel of the given size (used for ncu captures:
     a small number of launches, inputs larger than L2 when the mesh is large enough)."""
@@ -639,6 +674,8 @@ def main():
     ap.add_argument("--enrich-l", type=int, default=1, choices=[0, 1],
                     help="enrichment weight degree (--helmholtz, --wall-update)")
     ap.add_argument("--wall-update", action="store_true", help="time the tau_w update and the L2 projection")
+    ap.add_argument("--ns-step", action="store_true", help="time dual-splitting time steps")
+    ap.add_argument("--wall-update-steps", action="store_true", help="--ns-step: update the wall model every step")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["laplace64", "laplace32", "divergence", "convective", "convective32", "viscous",
                              "viscous32"])
@@ -654,6 +691,8 @@ def main():
         return run_helmholtz(args)
     if args.wall_update:
         return run_wall_update(args)
+    if args.ns_step:
+        return run_ns_step(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
