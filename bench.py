@@ -59,10 +59,15 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 3 s) for the first sample so that the sampling covers the whole timed region
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -151,8 +156,10 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_sample(w, target_s=2.0, max_cells=64)
     vals, secs = [], []
+    # each step is a bounded sample; the whole run stays within a few minutes
+    per_step = min(args.ref_seconds, max(1.0, 150.0 / max(1, args.steps)))
     for _ in range(args.steps):
-        v, s, threads, desc = oracle_sample(w, target_s=args.ref_seconds)
+        v, s, threads, desc = oracle_sample(w, target_s=per_step)
         vals.append(v)
         secs.append(s)
     val = statistics.mean(vals)
@@ -653,7 +660,7 @@ def run_profile_kernel(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgw", choices=["dgw", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
