@@ -123,6 +123,7 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     for (int t = tid; t < P; t += blockDim.x) f[t] = 0.0;
     for (int a = 0; a < 3; ++a) {
       for (int d = 0; d < (MODE == NS_TAU ? 1 : 3); ++d) {
+        if (MODE == NS_DIVDIV && !curved && d != a) continue;   // boxes: J^-1 is diagonal
         axis_pass(coef + a * n3, X, (MODE == NS_DIVDIV && d == 0) ? D0 : S0, n, false, 0, n, n, n, q0, false);
         axis_pass(X, Y, (MODE == NS_DIVDIV && d == 1) ? Dy : Sy, n, false, 1, q0, n, n, q1, false);
         axis_pass(Y, Z, (MODE == NS_DIVDIV && d == 2) ? D0 : S0, n, false, 2, q0, q1, n, q0, false);
@@ -186,6 +187,7 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
   // ---- volume: r_a += sum_t f(t) J^-1[d][a] d phi / d xi_d ----
   for (int a = 0; a < 3; ++a)
     for (int d = 0; d < 3; ++d) {
+      if (!curved && d != a) continue;   // boxes: J^-1 is diagonal
       for (int t = tid; t < P; t += blockDim.x) {
         double Ji[3][3], dV;
         metric(t, Ji, dV);
