@@ -83,6 +83,8 @@ def _load():
         lib.dgo_project.argtypes = [vp, dp, dp, dp]
         lib.dgo_set_switch.argtypes = [vp, ctypes.c_double]
         lib.dgo_gradient.argtypes = [vp, dp, dp]
+        lib.dgo_curl.argtypes = [vp, dp, dp]
+        lib.dgo_pressure_neumann.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.dgo_divdiv.argtypes = [vp, dp, dp, dp]
         lib.dgo_tau_divdiv.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp]
         lib.dgo_inverse_mass.argtypes = [vp, dp, dp]
@@ -281,6 +283,25 @@ class Mesh:
         """Pressure gradient P(v, p) = -(div v, p) + (v, {{p}} n), {{p}} = p^- on walls (n_p in, n_u out)."""
         p = np.ascontiguousarray(p, dtype=np.float64); y = np.zeros(self.n_u)
         self.lib.dgo_gradient(self.h, _ptr(p), _ptr(y))
+        return y
+
+    def curl(self, u: np.ndarray) -> np.ndarray:
+        """y = (v, curl u)_K for every velocity test function; the vorticity is inverse_mass(y)."""
+        u = np.ascontiguousarray(u, dtype=np.float64); y = np.zeros(self.n_u)
+        self.lib.dgo_curl(self.h, _ptr(u), _ptr(y))
+        return y
+
+    def vorticity(self, u: np.ndarray) -> np.ndarray:
+        """omega_h: L2 projection of curl u onto the velocity space."""
+        return self.inverse_mass(self.curl(u))
+
+    def pressure_neumann(self, u0, w0, b0, u1=None, w1=None, b1=0.0, f=(0.0, 0.0, 0.0)) -> np.ndarray:
+        """Wall integrals (q, g), g = -(sum beta_i (div(u x u) + nu curl omega)(history i) - f) . n."""
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (u0, w0)]
+        b = [np.ascontiguousarray(x if x is not None else u0, dtype=np.float64) for x in (u1, w1)]
+        fv = np.ascontiguousarray(f, dtype=np.float64); y = np.zeros(self.n_p)
+        self.lib.dgo_pressure_neumann(self.h, _ptr(a[0]), _ptr(b[0]), _ptr(a[1]), _ptr(b[1]), float(b0),
+                                      float(b1 if u1 is not None else 0.0), _ptr(fv), _ptr(y))
         return y
 
     def tau_divdiv(self, u: np.ndarray, dt: float, cr: float) -> np.ndarray:

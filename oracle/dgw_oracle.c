@@ -1710,3 +1710,97 @@ int dgo_inverse_mass(void *h, const double *r, double *x) {
   }
   return status;
 }
+
+/* ----------------------------------------------------------------------------------------------
+ * Vorticity and the high-order pressure Neumann data (Sec. 4.1 eq. bc_d_pres, Sec. 4.2 ipflux).
+ * dgo_curl: y = (v, curl u)_K for every velocity test function (the right-hand side of the L2
+ * projection omega_h = M^-1 y). dgo_pressure_neumann: adds to a pressure vector the wall integrals
+ * (q, g) with g = -(sum_i beta_i (div(u^{n-i} x u^{n-i}) + nu curl omega^{n-i}) - f) . n, evaluated
+ * with the interior traces (k+1 Gauss points per tangential direction, as the Laplace faces).
+ * ---------------------------------------------------------------------------------------------- */
+int dgo_curl(void *h, const double *u, double *y) {
+  omesh *M = (omesh *)h;
+  int n3 = M->n1 * M->n1 * M->n1;
+  memset(y, 0, sizeof(double) * M->nu);
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < M->nc; ++c) {
+      int nq[3];
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            double dV = fabs(t.detJ) * gw[q0] * gwy[q1] * gw[q2];
+            vstate s; eval_vel(M, u, c, &t, &s);
+            double G[3][3];
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) G[a][b] = s.gb[a][b] + s.gt[a][b];
+            double w[3] = {G[2][1] - G[1][2], G[0][2] - G[2][0], G[1][0] - G[0][1]};
+            for (int a = 0; a < 3; ++a) {
+              double *yc = y + ((size_t)c * 3 + a) * n3;
+              for (int i = 0; i < n3; ++i) yc[i] += dV * t.phi[i] * w[a];
+              if (t.enriched) {
+                double *ye = y + 3L * M->np + ((size_t)M->enr[c] * 3 + a) * M->nef;
+                for (int v = 0; v < M->nef; ++v) ye[v] += dV * t.ephi[v] * w[a];
+              }
+            }
+          }
+    }
+    ptab_free(&t);
+  }
+  return 0;
+}
+
+int dgo_pressure_neumann(void *h, const double *u0, const double *u1, const double *w0, const double *w1, double b0,
+                         double b1, const double *f, double *y) {
+  omesh *M = (omesh *)h;
+  const int nx = M->P.nx, ny = M->P.ny, nz = M->P.nz, n1 = M->n1, n3 = n1 * n1 * n1;
+  double gx[MAXP], gw[MAXP];
+  dgo_gauss(n1, gx, gw);
+  ptab t; ptab_alloc(&t, M);
+  const double *us[2] = {u0, u1}, *ws[2] = {w0, w1};
+  const double bs[2] = {b0, b1};
+  for (int wall = 0; wall < 2; ++wall)
+    for (int kz = 0; kz < nz; ++kz)
+      for (int i = 0; i < nx; ++i) {
+        const int j = wall ? ny - 1 : 0, c = cell_id(M, i, j, kz);
+        double *yc = y + (size_t)c * n3;
+        for (int q2 = 0; q2 < n1; ++q2)
+          for (int q0 = 0; q0 < n1; ++q0) {
+            double xi[3] = {gx[q0], wall ? 1.0 : 0.0, gx[q2]}, nrm[3];
+            tabulate(M, c, xi, &t);
+            double dA = face_geom(t.Ji, t.detJ, 1, wall, nrm) * gw[q0] * gw[q2];
+            double acc[3] = {-f[0], -f[1], -f[2]};
+            for (int h2 = 0; h2 < 2; ++h2) {
+              if (bs[h2] == 0.0 || !us[h2]) continue;
+              vstate s; eval_vel(M, us[h2], c, &t, &s);
+              vstate so; eval_vel(M, ws[h2], c, &t, &so);
+              double U[3], G[3][3], GW[3][3];
+              for (int a = 0; a < 3; ++a) {
+                U[a] = s.ub[a] + s.ut[a];
+                for (int b = 0; b < 3; ++b) {
+                  G[a][b] = s.gb[a][b] + s.gt[a][b];
+                  GW[a][b] = so.gb[a][b] + so.gt[a][b];
+                }
+              }
+              double dv = G[0][0] + G[1][1] + G[2][2];
+              double cw[3] = {GW[2][1] - GW[1][2], GW[0][2] - GW[2][0], GW[1][0] - GW[0][1]};
+              for (int a = 0; a < 3; ++a) {
+                double conv = U[a] * dv;
+                for (int b = 0; b < 3; ++b) conv += U[b] * G[a][b];
+                acc[a] += bs[h2] * (conv + M->P.nu * cw[a]);
+              }
+            }
+            double g = -(acc[0] * nrm[0] + acc[1] * nrm[1] + acc[2] * nrm[2]);
+            for (int q = 0; q < n3; ++q) yc[q] += dA * t.phi[q] * g;
+          }
+      }
+  ptab_free(&t);
+  return 0;
+}

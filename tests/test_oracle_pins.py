@@ -844,3 +844,57 @@ def test_dual_splitting_keeps_poiseuille_flow_steady():
         u, p = ds.step()
     assert _l2_rel(m, u, u0) < 1e-11
     assert np.abs(p).max() < 1e-10
+
+
+# ---------------------------------------------------------------------------------------------
+# Vorticity and the high-order pressure Neumann data (Sec. 4.1 eq. bc_d_pres)
+# ---------------------------------------------------------------------------------------------
+
+def test_curl_weak_form_closed_forms():
+    """(v, curl u) for u = (-y^2, 0, 0): curl u = (0, 0, 2y), and v = (0, 0, y) gives int 2 y^2; a
+    gradient field u = grad(y^2) has no curl."""
+    m = O.Mesh(3, 4, 2, 2, n_layers=0)
+    u = _std_field(m, lambda x, y, z: -y ** 2, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    v = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y, lambda x, y, z: y)
+    ref = 2 * math.pi * math.pi * 4.0 / 3.0
+    assert abs(v @ m.curl(u) / ref - 1.0) < 1e-12
+    g = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: 2 * y, lambda x, y, z: 0 * y)
+    assert np.abs(m.curl(g)).max() < 1e-13
+
+
+def test_vorticity_of_a_polynomial_is_exact_with_enrichment():
+    """u = (y^3 - y, 0, y^2) (Q3): curl u = (2y, 0, 1 - 3y^2) lies in the velocity space (enrichment
+    coefficients zero), so its L2 projection is itself (compared as functions)."""
+    w = I.Workload("vo", 3, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=46)
+    m = O.Mesh(**w.mesh_kwargs())
+    u = _std_field(m, lambda x, y, z: y ** 3 - y, lambda x, y, z: 0 * y, lambda x, y, z: y ** 2)
+    ref = _std_field(m, lambda x, y, z: 2 * y, lambda x, y, z: 0 * y, lambda x, y, z: 1 - 3 * y ** 2)
+    assert _l2_rel(m, m.vorticity(u), ref) < 1e-10
+
+
+def test_pressure_neumann_convective_part():
+    """u = (0, y, 0): div(u x u) = (0, 2y, 0), curl u = 0, so g = -beta 2y n_y = -2 beta on both walls
+    and the wall integrals of q = 1 sum to -2 beta times the wall area of both walls."""
+    m = O.Mesh(3, 4, 2, 2, n_layers=0)
+    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: y, lambda x, y, z: 0 * y)
+    beta = 1.5
+    y = m.pressure_neumann(u, m.vorticity(u), beta)
+    ref = -2 * beta * 2 * (2 * math.pi * math.pi)
+    assert abs(y.sum() / ref - 1.0) < 1e-12
+
+
+def test_pressure_neumann_viscous_part():
+    """u = (0, sin(kx), 0): curl u = (0, 0, k cos kx), curl curl u = (0, k^2 sin kx, 0), the convective
+    part vanishes; with q = y sin(kx), sum of q g over both walls = -2 beta nu k^2 (L_x/2) L_z. The
+    vorticity is the L2 projection of the interpolated sine's curl (tolerance: interpolation error)."""
+    nu, beta = 1e-2, 2.0
+    m = O.Mesh(16, 2, 1, 4, n_layers=0, nu=nu)
+    kap = 1.0
+    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: np.sin(kap * x), lambda x, y, z: 0 * y)
+    X = m.node_coords()
+    q = X[:, 1] * np.sin(kap * X[:, 0])
+    y = m.pressure_neumann(u, m.vorticity(u), beta)
+    ref = -2 * beta * nu * kap ** 2 * math.pi * math.pi
+    # the degree-4 interpolant of the sine on h = 2 pi / 16 differs by ~(h/2)^5 / 5! ~ 2e-6, and the
+    # curl-curl takes two derivatives of it
+    assert abs(q @ y / ref - 1.0) < 1e-4
