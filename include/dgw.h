@@ -148,6 +148,18 @@ dgw_status dgw_apply_gradient(dgw_mesh_t mesh, const double *p, double *y, void 
 dgw_status dgw_tau_divdiv(dgw_mesh_t mesh, const double *u, double dt, double cr, double *tau_d, void *stream);
 /* div-div penalty y = D(v, u) = (div v, tau_D div u)_K (eq. div-div), cell-local; u, y: n_u doubles. */
 dgw_status dgw_apply_divdiv(dgw_mesh_t mesh, const double *tau_d, const double *u, double *y, void *stream);
+/* y = (v, curl u)_K for every velocity test function (standard and enriched), the right-hand side of
+ * the vorticity's L2 projection omega_h = M^-1 y (Sec. 4.2, pressure Laplace term). u, y: n_u doubles. */
+dgw_status dgw_apply_curl(dgw_mesh_t mesh, const double *u, double *y, void *stream);
+/* High-order pressure Neumann data (Sec. 4.1 eq. bc_d_pres, Sec. 4.2 eq. ipflux): adds to the pressure
+ * vector b (n_p doubles) the wall integrals (q, g) with
+ *   g = -(beta0 (div(u0 x u0) + nu curl w0) + beta1 (div(u1 x u1) + nu curl w1) - f) . n,
+ * interior traces at k+1 Gauss points per tangential direction of every wall face; w0, w1 are the
+ * vorticities of u0, u1 (dgw_apply_curl then dgw_apply_inverse_mass); beta1 = 0 ignores u1, w1
+ * (may be NULL). force: 3 doubles (host). */
+dgw_status dgw_add_pressure_neumann(dgw_mesh_t mesh, const double *u0, const double *w0, double beta0,
+                                    const double *u1, const double *w1, double beta1, const double *force, double *b,
+                                    void *stream);
 /* x = M^-1 r (Sec. 4.2 mass term), exactly: cells without switched-on enrichment by the collocation
  * inverse S^-1 W^-1 S^-T, the others by the Cholesky factor of the cell mass matrix (computed on the
  * first call after every change of the space, then kept). r, x: n_u doubles, distinct buffers.
@@ -269,6 +281,8 @@ typedef struct {
   int pressure_mode;      /* dgw_solve_opts.mode of the pressure solve */
   int update_wall_model;  /* 1: at the start of every step tau_w,B from u^n, the velocity history
                              L2-projected onto the new space, the convective history recomputed */
+  int pressure_bc;        /* 0: homogeneous Neumann data for the pressure; 1: the high-order data of
+                             eq. bc_d_pres from u^{n-i} and their vorticities */
 } dgw_ns_params;
 
 typedef struct {
@@ -283,7 +297,8 @@ dgw_status dgw_ns_create(dgw_mesh_t mesh, const dgw_ns_params *params, const dou
 dgw_status dgw_ns_destroy(dgw_ns_t ns);
 /* One time step, BDF2 with second-order extrapolation (first order in the first step), constant dt:
  *   u^  = (sum alpha_i u^{n-i} + dt f - dt M^-1 sum beta_i F^c(u^{n-i})) / gamma_0 (eq. convstepspat)
- *   A p = (gamma_0 / dt)(-C u^), homogeneous Neumann data on walls (eq. poissonspat)
+ *   A p = (gamma_0 / dt)(-C u^) + (q, g)_walls (eq. poissonspat), g = 0 or the high-order data of
+ *         eq. bc_d_pres (pressure_bc = 1) from u^n, u^{n-1} and their vorticities
  *   (M + D) u^^ = M u^ - (dt / gamma_0) P(v, p)                      (eq. projectionspat)
  *   (gamma_0 / dt) M u^{n+1} - F^nu(u^{n+1}) = (gamma_0 / dt) M u^^   (eq. helmholtzspat)
  * with tau_D and nu_t from u^n, CG with the exact inverse mass for the projection and GMRES for the

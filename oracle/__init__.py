@@ -399,20 +399,23 @@ def _pcg(apply, b, x0, prec, rtol, maxit=5000):
 class DualSplitting:
     """One constant-step BDF2/extrapolation step of the dual-splitting scheme after Sec. 4.1 with the
     Galerkin forms of Sec. 4.2, written with this module's operators (first order in the first step):
-    convective step with the exact inverse mass, pressure Poisson solve (homogeneous Neumann), the
+    convective step with the exact inverse mass, pressure Poisson solve (homogeneous Neumann data, or
+    with high_order_pressure_bc the data of eq. bc_d_pres from u^{n-i} and their vorticities), the
     projection (M + D) u^^ = M u^ - (dt / gamma_0) P(p) by preconditioned CG, and the viscous
     Helmholtz step by GMRES, nu_t and tau_D from u^n. With update_wall_model the step starts with the
     wall shear stress of u^n, the L2 projection of u^n and u^{n-1} onto the new space and a new
     F^c(u^{n-1})."""
 
     def __init__(self, mesh: "Mesh", u0, dt, cr=0.14, force=(0.0, 0.0, 0.0), rtol=1e-13,
-                 update_wall_model=False, tau_nodes=None):
+                 update_wall_model=False, tau_nodes=None, high_order_pressure_bc=False):
         self.m, self.dt, self.cr, self.rtol = mesh, float(dt), float(cr), float(rtol)
         self.u = [np.array(u0, dtype=np.float64), None]
         self.fc_old = None
         self.p = np.zeros(mesh.n_p)
         self.steps = 0
         self.update = update_wall_model
+        self.hobc = high_order_pressure_bc
+        self.force = tuple(float(x) for x in force)
         self.tau = (np.full(mesh.n_wall_nodes, mesh.params.tau_w) if tau_nodes is None
                     else np.array(tau_nodes, dtype=np.float64))
         n3 = (mesh.k + 1) ** 3
@@ -437,9 +440,14 @@ class DualSplitting:
             self.tau = tn
         un, unm = self.u
         fc = m.convective(un)
+        if self.hobc:
+            wn = m.vorticity(un)
+            wnm = m.vorticity(unm) if second else None
         w = b0 * fc + (b1 * self.fc_old if second else 0.0)
         uh = (a0 * un + (a1 * unm if second else 0.0) + dt * self.f - dt * m.inverse_mass(w)) / g0
         b = (g0 / dt) * m.divergence(uh)
+        if self.hobc:
+            b = b + m.pressure_neumann(un, wn, b0, unm if second else None, wnm, b1 if second else 0.0, self.force)
         p, _, _ = m.solve(b, rtol=self.rtol, maxit=200000)
         tau_d = m.tau_divdiv(un, dt, self.cr)
         rhs = m.vmass(uh) - (dt / g0) * m.gradient(p)

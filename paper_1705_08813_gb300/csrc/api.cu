@@ -448,6 +448,20 @@ dgw_status dgw_apply_divdiv(dgw_mesh_t M, const double *tau_d, const double *u, 
   return cuda_check(launch_ns_op(1, M, u, tau_d, 0.0, y, (cudaStream_t)stream), "dgw_apply_divdiv");
 }
 
+dgw_status dgw_apply_curl(dgw_mesh_t M, const double *u, double *y, void *stream) {
+  if (!M || !u || !y) return set_error(DGW_EINVAL, "dgw_apply_curl: null argument");
+  return cuda_check(launch_ns_op(3, M, u, nullptr, 0.0, y, (cudaStream_t)stream), "dgw_apply_curl");
+}
+
+dgw_status dgw_add_pressure_neumann(dgw_mesh_t M, const double *u0, const double *w0, double beta0, const double *u1,
+                                    const double *w1, double beta1, const double *force, double *b, void *stream) {
+  if (!M || !u0 || !w0 || !force || !b) return set_error(DGW_EINVAL, "dgw_add_pressure_neumann: null argument");
+  if (beta1 != 0.0 && (!u1 || !w1)) return set_error(DGW_EINVAL, "dgw_add_pressure_neumann: beta1 needs u1 and w1");
+  return cuda_check(launch_pressure_neumann(M, u0, w0, beta0, beta1 != 0.0 ? u1 : nullptr, beta1 != 0.0 ? w1 : nullptr,
+                                            beta1, force, b, (cudaStream_t)stream),
+                    "dgw_add_pressure_neumann");
+}
+
 dgw_status dgw_apply_inverse_mass(dgw_mesh_t M, const double *r, double *x, void *stream) {
   if (!M || !r || !x) return set_error(DGW_EINVAL, "dgw_apply_inverse_mass: null argument");
   if (r == x) return set_error(DGW_EINVAL, "dgw_apply_inverse_mass: r and x must not overlap");

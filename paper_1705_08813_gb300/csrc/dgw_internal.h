@@ -230,6 +230,8 @@ cudaError_t launch_inverse_mass_cells(dgw_mesh *M, const double *r, double *x, c
 cudaError_t launch_collocation_inverse_mass(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
 cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *tau_d, double dt_over_cr, double *y,
                          cudaStream_t s);
+cudaError_t launch_pressure_neumann(dgw_mesh *M, const double *u0, const double *w0, double b0, const double *u1,
+                                    const double *w1, double b1, const double *f, double *y, cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 

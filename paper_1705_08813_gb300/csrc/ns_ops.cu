@@ -2,6 +2,7 @@
 //   NS_GRAD   y = P(v, p) = -(div v, p)_K + (v, {{p}} n)_dK, {{p}} = p^- on walls
 //   NS_DIVDIV y = D(v, u) = (div v, tau_D div u)_K (eq. div-div), tau_D constant per cell
 //   NS_TAU    tau_D = |u|_K h dt / Cr per cell (eq. tauD), |u|_K the volume average, h = vol^(1/3)
+//   NS_CURL   y = (v, curl u)_K, the right-hand side of the vorticity's L2 projection (Sec. 4.2)
 // One CTA per cell with shared-memory sum factorisation over the cell's velocity point set (k+1
 // Gauss points, q_w wall-normal in cells with the wall model switched on); enriched test
 // functions psi N_v e_a through the wall tables. Both operators map a scalar per point, f(t), to
@@ -15,7 +16,7 @@
 
 namespace dgw {
 
-enum { NS_GRAD = 0, NS_DIVDIV = 1, NS_TAU = 2 };
+enum { NS_GRAD = 0, NS_DIVDIV = 1, NS_TAU = 2, NS_CURL = 3 };
 
 namespace {
 
@@ -119,17 +120,34 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     }
     __syncthreads();
   } else {
-    // f accumulates sum_a du_a/dx_a (NS_DIVDIV) or |u| (NS_TAU) at the points
+    // f accumulates sum_a du_a/dx_a (NS_DIVDIV) or |u| (NS_TAU) at the points; uv the curl (NS_CURL)
     for (int t = tid; t < P; t += blockDim.x) f[t] = 0.0;
+    if (MODE == NS_CURL)
+      for (int t = tid; t < 3 * P; t += blockDim.x) uv[t] = 0.0;
     for (int a = 0; a < 3; ++a) {
       for (int d = 0; d < (MODE == NS_TAU ? 1 : 3); ++d) {
         if (MODE == NS_DIVDIV && !curved && d != a) continue;   // boxes: J^-1 is diagonal
-        axis_pass(coef + a * n3, X, (MODE == NS_DIVDIV && d == 0) ? D0 : S0, n, false, 0, n, n, n, q0, false);
-        axis_pass(X, Y, (MODE == NS_DIVDIV && d == 1) ? Dy : Sy, n, false, 1, q0, n, n, q1, false);
-        axis_pass(Y, Z, (MODE == NS_DIVDIV && d == 2) ? D0 : S0, n, false, 2, q0, q1, n, q0, false);
+        if (MODE == NS_CURL && !curved && d == a) continue;     // the curl has no du_a/dx_a
+        constexpr bool DER = MODE == NS_DIVDIV || MODE == NS_CURL;
+        axis_pass(coef + a * n3, X, (DER && d == 0) ? D0 : S0, n, false, 0, n, n, n, q0, false);
+        axis_pass(X, Y, (DER && d == 1) ? Dy : Sy, n, false, 1, q0, n, n, q1, false);
+        axis_pass(Y, Z, (DER && d == 2) ? D0 : S0, n, false, 2, q0, q1, n, q0, false);
         for (int t = tid; t < P; t += blockDim.x) {
           if (MODE == NS_TAU) {
             uv[a * P + t] = Z[t];
+          } else if (MODE == NS_CURL) {
+            double Ji[3][3], dV;
+            metric(t, Ji, dV);
+            // du_a/dx_e += J^-1[d][e] du_a/dxi_d, into curl = (du2/dx1 - du1/dx2, du0/dx2 - du2/dx0, ...)
+            for (int e2 = 0; e2 < 3; ++e2) {
+              const double g = Ji[d][e2] * Z[t];
+              if (a == 2 && e2 == 1) uv[t] += g;
+              if (a == 1 && e2 == 2) uv[t] -= g;
+              if (a == 0 && e2 == 2) uv[P + t] += g;
+              if (a == 2 && e2 == 0) uv[P + t] -= g;
+              if (a == 1 && e2 == 0) uv[2 * P + t] += g;
+              if (a == 0 && e2 == 1) uv[2 * P + t] -= g;
+            }
           } else {
             double Ji[3][3], dV;
             metric(t, Ji, dV);
@@ -142,7 +160,7 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     for (int t = tid; t < P; t += blockDim.x) {
       double Ji[3][3], dV;
       metric(t, Ji, dV);
-      double uu[3] = {0.0, 0.0, 0.0}, dv = 0.0;
+      double uu[3] = {0.0, 0.0, 0.0}, dv = 0.0, ge[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       if (MODE == NS_TAU) for (int a = 0; a < 3; ++a) uu[a] = uv[a * P + t];
       if (enr) {
         double xi[3], N[8], dN[8][3];
@@ -155,11 +173,19 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
           for (int a = 0; a < 3; ++a) {
             uu[a] += w[0] * N[v] * ec[a * 8 + v];
             dv += ec[a * 8 + v] * (w[0] * g[a] + N[v] * w[1 + a]);
+            for (int e2 = 0; e2 < 3; ++e2) ge[a][e2] += ec[a * 8 + v] * (w[0] * g[e2] + N[v] * w[1 + e2]);
           }
         }
       }
-      if (MODE == NS_TAU) f[t] = dV * sqrt(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
-      else f[t] = dV * tau_d[c] * (f[t] + dv);
+      if (MODE == NS_TAU) {
+        f[t] = dV * sqrt(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+      } else if (MODE == NS_CURL) {
+        uv[t] = dV * (uv[t] + ge[2][1] - ge[1][2]);
+        uv[P + t] = dV * (uv[P + t] + ge[0][2] - ge[2][0]);
+        uv[2 * P + t] = dV * (uv[2 * P + t] + ge[1][0] - ge[0][1]);
+      } else {
+        f[t] = dV * tau_d[c] * (f[t] + dv);
+      }
     }
     __syncthreads();
   }
@@ -183,7 +209,27 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     return;
   }
 
-  if constexpr (MODE != NS_TAU) {
+  if constexpr (MODE == NS_CURL) {
+    // values: r_a += sum_t dV curl_a(t) phi(t); enriched: sum_t dV curl_a psi N_v
+    for (int a = 0; a < 3; ++a) {
+      axis_pass(uv + a * P, Y, S0, n, true, 2, q0, q1, q0, n, false);
+      axis_pass(Y, X, Sy, n, true, 1, q0, q1, n, n, false);
+      axis_pass(X, r + a * n3, S0, n, true, 0, q0, n, n, n, true);
+    }
+    if (enr && tid < 24) {
+      const int a = tid / 8, v = tid % 8;
+      double sacc = 0.0;
+      for (int t = 0; t < P; ++t) {
+        double xi[3], N[8], dN[8][3];
+        xi_of(t, xi);
+        q1_weights(xi, N, dN);
+        sacc += uv[a * P + t] * wtv[(size_t)t * WT] * N[v];
+      }
+      re[tid] += sacc;
+    }
+    __syncthreads();
+  }
+  if constexpr (MODE != NS_TAU && MODE != NS_CURL) {
   // ---- volume: r_a += sum_t f(t) J^-1[d][a] d phi / d xi_d ----
   for (int a = 0; a < 3; ++a)
     for (int d = 0; d < 3; ++d) {
@@ -214,6 +260,8 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     re[tid] += s;
   }
   __syncthreads();
+  }
+  if constexpr (MODE != NS_TAU) {
 
   // ---- faces (gradient only): (v, {{p}} n) ----
   if (MODE == NS_GRAD) {
@@ -315,7 +363,118 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
   }
 }
 
+// Value and physical gradient of a velocity-type field at wall-face point (a1, a2) of the face
+// xi_1 = side (Gauss-Lobatto nodes: the face trace is the node row jend), enrichment included.
+__device__ void wall_face_state(const Basis<double> &B, const double *su, const double *ce, const double *wt,
+                                const double xi[3], const double Ji[3][3], int n, int a1, int a2, int side,
+                                double U[3], double G[3][3]) {
+  const double *S = B.S[QSET_LIN], *D = B.D[QSET_LIN], *de = B.dend[side];
+  const int n3 = n * n * n, jend = side ? n - 1 : 0;
+  for (int a = 0; a < 3; ++a) {
+    const double *ua = su + a * n3;
+    double v = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int l = 0; l < n; ++l)
+      for (int ii = 0; ii < n; ++ii) {
+        const double ul = ua[ii + n * (jend + n * l)];
+        v += S[a1 * n + ii] * S[a2 * n + l] * ul;
+        g[0] += D[a1 * n + ii] * S[a2 * n + l] * ul;
+        g[2] += S[a1 * n + ii] * D[a2 * n + l] * ul;
+        double s1 = 0.0;
+        for (int jj = 0; jj < n; ++jj) s1 += de[jj] * ua[ii + n * (jj + n * l)];
+        g[1] += S[a1 * n + ii] * S[a2 * n + l] * s1;
+      }
+    U[a] = v;
+    ref_to_phys(Ji, g, G[a]);
+  }
+  if (wt) {
+    double N[8], dN[8][3];
+    q1_weights(xi, N, dN);
+    for (int v = 0; v < 8; ++v) {
+      double gN[3];
+      ref_to_phys(Ji, dN[v], gN);
+      for (int a = 0; a < 3; ++a) {
+        U[a] += ce[a * 8 + v] * wt[0] * N[v];
+        for (int d = 0; d < 3; ++d) G[a][d] += ce[a * 8 + v] * (wt[0] * gN[d] + N[v] * wt[1 + d]);
+      }
+    }
+  }
+}
+
+// Wall integrals (q, g) of the high-order pressure Neumann data (eq. bc_d_pres), added to y:
+// g = -(sum_i beta_i (div(u_i x u_i) + nu curl omega_i) - f) . n at the (k+1)^2 Gauss points of each
+// wall face (interior traces), one CTA per wall face (wall, i, k).
+__global__ void pressure_neumann_kernel(MeshView<double> m, const double *__restrict__ u0,
+                                        const double *__restrict__ w0, double b0, const double *__restrict__ u1,
+                                        const double *__restrict__ w1, double b1, double f0, double f1, double f2,
+                                        double nu, const double *__restrict__ wt_face, int fpmax,
+                                        double *__restrict__ y) {
+  const Basis<double> &B = *m.basis;
+  const int n = m.n1, nn = n * n, n3 = nn * n;
+  const int b = blockIdx.x, wall = b / (m.nx * m.nz), r = b % (m.nx * m.nz), i = r % m.nx, kz = r / m.nx;
+  const int j = wall ? m.ny - 1 : 0, c = i + m.nx * (j + m.ny * kz), side = wall, jend = side ? n - 1 : 0;
+  __shared__ double su[4][3 * NMAX * NMAX * NMAX], ce[4][24], gp[NMAX * NMAX];
+  const double *src[4] = {u0, w0, u1, w1};
+  const int e = m.enr[c];
+  for (int fld = 0; fld < 4; ++fld) {
+    const double *v = src[fld];
+    for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) su[fld][t] = v ? v[(size_t)c * 3 * n3 + t] : 0.0;
+    for (int t = threadIdx.x; t < 24; t += blockDim.x)
+      ce[fld][t] = (v && e >= 0) ? v[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int a1 = t % n, a2 = t / n;
+    const double xi[3] = {B.x[QSET_LIN][a1], (double)side, B.x[QSET_LIN][a2]};
+    double Ji[3][3], det;
+    if (m.geo == GEO_CURVED) {
+      load_rec(face_rec(m, B, metric_col(m, c), 1, side, QSET_LIN, QSET_LIN, a1, a2), Ji, det);
+    } else {
+      const double h[3] = {m.hx, m.hy[j], m.hz};
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) Ji[p][q] = p == q ? 1.0 / h[p] : 0.0;
+      det = h[0] * h[1] * h[2];
+    }
+    const double gl = sqrt(Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1] + Ji[1][2] * Ji[1][2]);
+    const double sg = side ? 1.0 : -1.0;
+    const double nrm[3] = {sg * Ji[1][0] / gl, sg * Ji[1][1] / gl, sg * Ji[1][2] / gl};
+    const double dA = fabs(det) * gl * B.w[QSET_LIN][a1] * B.w[QSET_LIN][a2];
+    const double *wt = e >= 0 ? wt_face + (((size_t)e * 6 + 2 + side) * fpmax + t) * WT : nullptr;
+    double acc[3] = {-f0, -f1, -f2};
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const double beta = h2 ? b1 : b0;
+      if (beta == 0.0 || !src[2 * h2]) continue;
+      double U[3], G[3][3], W[3], GW[3][3];
+      wall_face_state(B, su[2 * h2], ce[2 * h2], wt, xi, Ji, n, a1, a2, side, U, G);
+      wall_face_state(B, su[2 * h2 + 1], ce[2 * h2 + 1], wt, xi, Ji, n, a1, a2, side, W, GW);
+      const double dv = G[0][0] + G[1][1] + G[2][2];
+      const double cw[3] = {GW[2][1] - GW[1][2], GW[0][2] - GW[2][0], GW[1][0] - GW[0][1]};
+      for (int a = 0; a < 3; ++a) {
+        const double conv = U[a] * dv + U[0] * G[a][0] + U[1] * G[a][1] + U[2] * G[a][2];
+        acc[a] += beta * (conv + nu * cw[a]);
+      }
+    }
+    gp[t] = -dA * (acc[0] * nrm[0] + acc[1] * nrm[1] + acc[2] * nrm[2]);
+  }
+  __syncthreads();
+  const double *S = B.S[QSET_LIN];
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i1 = t % n, i2 = t / n;
+    double acc = 0.0;
+    for (int a2 = 0; a2 < n; ++a2)
+      for (int a1 = 0; a1 < n; ++a1) acc += S[a1 * n + i1] * S[a2 * n + i2] * gp[a1 + n * a2];
+    y[(size_t)c * n3 + i1 + n * (jend + n * i2)] += acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pressure_neumann(dgw_mesh *M, const double *u0, const double *w0, double b0, const double *u1,
+                                    const double *w1, double b1, const double *f, double *y, cudaStream_t s) {
+  note_launch();
+  pressure_neumann_kernel<<<2 * M->P.nx * M->P.nz, 64, 0, s>>>(M->v64, u0, w0, b0, u1, w1, b1, f[0], f[1], f[2],
+                                                               M->P.nu, M->v64.wt_face[0], M->v64.fpmax[0], y);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *tau_d, double dt_over_cr, double *y,
                          cudaStream_t s) {
@@ -331,9 +490,12 @@ cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *
   } else if (mode == NS_DIVDIV) {
     e = cudaFuncSetAttribute(ns_op_kernel<NS_DIVDIV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) ns_op_kernel<NS_DIVDIV><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
-  } else {
+  } else if (mode == NS_TAU) {
     e = cudaFuncSetAttribute(ns_op_kernel<NS_TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) ns_op_kernel<NS_TAU><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
+  } else {
+    e = cudaFuncSetAttribute(ns_op_kernel<NS_CURL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) ns_op_kernel<NS_CURL><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -4,7 +4,9 @@
 //   1. explicit convective step (eq. convstepspat), BDF/extrapolation of order J = 2 (J = 1 in the
 //      first step), with the exact cell-wise inverse mass:
 //        u^ = (sum_i alpha_i u^{n-i} + dt f - dt M^-1 sum_i beta_i F^c(u^{n-i})) / gamma_0
-//   2. pressure Poisson equation (eq. poissonspat): A p = (gamma_0 / dt) (-C u^), homogeneous Neumann
+//   2. pressure Poisson equation (eq. poissonspat): A p = (gamma_0 / dt) (-C u^) + (q, g)_walls with the
+//      high-order Neumann data g of eq. bc_d_pres (vorticities omega^{n-i} = M^-1 (v, curl u^{n-i})),
+//      or g = 0
 //   3. projection (eq. projectionspat): (M + D) u^^ = M u^ - (dt / gamma_0) P(v, p), D with tau_D from
 //      u^n, solved by CG preconditioned with the exact inverse mass
 //   4. viscous step (eq. helmholtzspat): (gamma_0 / dt) M u^{n+1} - F^nu(u^{n+1}) = (gamma_0 / dt) M u^^,
@@ -26,6 +28,7 @@ struct dgw_ns {
   int steps = 0;
   double *u[2] = {nullptr, nullptr};    // u^n, u^{n-1}
   double *fc[2] = {nullptr, nullptr};   // F^c(u^n), F^c(u^{n-1})
+  double *om[2] = {nullptr, nullptr};   // vorticities of u^n, u^{n-1} (high-order pressure data)
   double *p = nullptr, *b = nullptr;
   double *uh = nullptr, *uhh = nullptr, *w = nullptr, *x = nullptr, *t1 = nullptr, *t2 = nullptr;
   double *f = nullptr;                  // body force as a velocity field (standard coefficients)
@@ -198,7 +201,7 @@ dgw_status dgw_ns_create(dgw_mesh_t M, const dgw_ns_params *params, const double
       e = cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(double), s);
     }
   };
-  for (int i = 0; i < 2; ++i) { alloc(&S->u[i], S->nu); alloc(&S->fc[i], S->nu); }
+  for (int i = 0; i < 2; ++i) { alloc(&S->u[i], S->nu); alloc(&S->fc[i], S->nu); alloc(&S->om[i], S->nu); }
   for (double **p : {&S->uh, &S->uhh, &S->w, &S->x, &S->t1, &S->t2, &S->f, &S->cg_r, &S->cg_z, &S->cg_p, &S->cg_q})
     alloc(p, S->nu);
   alloc(&S->p, S->np);
@@ -280,6 +283,15 @@ dgw_status dgw_ns_step(dgw_ns_t S, dgw_ns_step_info *info, void *stream) {
       dgw_helm_free(M);
     }
     if (st == DGW_OK && second) st = dgw_apply_convective(M, DGW_FP64, S->u[1], S->fc[1], s);
+    if (st == DGW_OK && second && S->P.pressure_bc) {   // vorticity of the projected u^{n-1}
+      st = dgw_apply_curl(M, S->u[1], S->t1, s);
+      if (st == DGW_OK) st = dgw_apply_inverse_mass(M, S->t1, S->om[1], s);
+    }
+    if (st != DGW_OK) return st;
+  }
+  if (S->P.pressure_bc) {   // vorticity of u^n
+    st = dgw_apply_curl(M, S->u[0], S->t1, s);
+    if (st == DGW_OK) st = dgw_apply_inverse_mass(M, S->t1, S->om[0], s);
     if (st != DGW_OK) return st;
   }
   // 1. convective step
@@ -295,6 +307,9 @@ dgw_status dgw_ns_step(dgw_ns_t S, dgw_ns_step_info *info, void *stream) {
   // 2. pressure
   if (st == DGW_OK) st = dgw_apply_divergence(M, S->uh, S->b, s);
   if (st == DGW_OK) st = cuda_check(lincomb(S->b, g0 / dt, S->b, 0.0, nullptr, 0.0, nullptr, S->np, s), "dgw_ns_step");
+  if (st == DGW_OK && S->P.pressure_bc)
+    st = dgw_add_pressure_neumann(M, S->u[0], S->om[0], b0, second ? S->u[1] : nullptr, second ? S->om[1] : nullptr,
+                                  second ? b1 : 0.0, S->P.force, S->b, s);
   if (st == DGW_OK) {
     dgw_solve_opts o{};
     o.rtol = S->P.rtol_pressure;
@@ -331,6 +346,7 @@ dgw_status dgw_ns_step(dgw_ns_t S, dgw_ns_step_info *info, void *stream) {
   std::swap(S->u[0], S->u[1]);
   e = cudaMemcpyAsync(S->u[0], S->x, nu * sizeof(double), cudaMemcpyDeviceToDevice, s);
   std::swap(S->fc[0], S->fc[1]);
+  std::swap(S->om[0], S->om[1]);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_check(e, "dgw_ns_step");
   S->steps++;

@@ -23,7 +23,8 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
            "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active",
            "dgw_apply_gradient", "dgw_tau_divdiv", "dgw_apply_divdiv", "dgw_apply_inverse_mass",
-           "dgw_ns_create", "dgw_ns_destroy", "dgw_ns_step", "dgw_ns_state", "dgw_ns_copy_state"]
+           "dgw_ns_create", "dgw_ns_destroy", "dgw_ns_step", "dgw_ns_state", "dgw_ns_copy_state",
+           "dgw_apply_curl", "dgw_add_pressure_neumann"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -38,7 +39,7 @@ class NSParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("cr", ctypes.c_double), ("force", ctypes.c_double * 3),
                 ("rtol_pressure", ctypes.c_double), ("rtol_projection", ctypes.c_double),
                 ("rtol_viscous", ctypes.c_double), ("max_iter", ctypes.c_int), ("pressure_mode", ctypes.c_int),
-                ("update_wall_model", ctypes.c_int)]
+                ("update_wall_model", ctypes.c_int), ("pressure_bc", ctypes.c_int)]
 
 
 class NSStepInfo(ctypes.Structure):
@@ -106,6 +107,9 @@ def load(path: str = LIB_PATH):
     lib.dgw_project_velocity.argtypes = [vp, vp, vp, vp, vp]
     lib.dgw_set_enrichment_switch.argtypes = [vp, ctypes.c_double, vp]
     lib.dgw_apply_gradient.argtypes = [vp, vp, vp, vp]
+    lib.dgw_apply_curl.argtypes = [vp, vp, vp, vp]
+    lib.dgw_add_pressure_neumann.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double), vp, vp]
     lib.dgw_ns_create.argtypes = [vp, ctypes.POINTER(NSParams), vp, vp, ctypes.POINTER(vp)]
     lib.dgw_ns_destroy.argtypes = [vp]
     lib.dgw_ns_step.argtypes = [vp, ctypes.POINTER(NSStepInfo), vp]
@@ -257,6 +261,26 @@ class Mesh:
                                            _ptr(y, torch.float64, self.n_u, "y"), _stream(stream)))
         return y
 
+    def curl(self, u, y, stream=None):
+        """y = (v, curl u) per cell; the vorticity is inverse_mass(y)."""
+        import torch
+        _check(self.lib.dgw_apply_curl(self.h, _ptr(u, torch.float64, self.n_u, "u"),
+                                       _ptr(y, torch.float64, self.n_u, "y"), _stream(stream)))
+        return y
+
+    def add_pressure_neumann(self, b, u0, w0, beta0, u1=None, w1=None, beta1=0.0, force=(0.0, 0.0, 0.0),
+                             stream=None):
+        """b += (q, g)_walls, the high-order pressure Neumann data of eq. bc_d_pres."""
+        import torch
+        f = (ctypes.c_double * 3)(*force)
+        p1 = _ptr(u1, torch.float64, self.n_u, "u1") if u1 is not None else None
+        q1 = _ptr(w1, torch.float64, self.n_u, "w1") if w1 is not None else None
+        _check(self.lib.dgw_add_pressure_neumann(self.h, _ptr(u0, torch.float64, self.n_u, "u0"),
+                                                 _ptr(w0, torch.float64, self.n_u, "w0"), ctypes.c_double(beta0),
+                                                 p1, q1, ctypes.c_double(beta1), f,
+                                                 _ptr(b, torch.float64, self.n_p, "b"), _stream(stream)))
+        return b
+
     def tau_divdiv(self, u, dt, cr, tau_d, stream=None):
         """Per-cell tau_D = |u|_K h dt / Cr into tau_d (nc doubles)."""
         import torch
@@ -393,11 +417,12 @@ class DualSplitting:
 
     def __init__(self, mesh: Mesh, u0, *, dt, cr=0.14, force=(0.0, 0.0, 0.0), rtol_pressure=1e-10,
                  rtol_projection=1e-10, rtol_viscous=1e-10, max_iter=2000, pressure_mode=1,
-                 update_wall_model=False, stream=None):
+                 update_wall_model=False, high_order_pressure_bc=False, stream=None):
         import torch
         self.mesh, self.lib = mesh, mesh.lib
         self.params = NSParams(dt, cr, (ctypes.c_double * 3)(*force), rtol_pressure, rtol_projection, rtol_viscous,
-                               max_iter, pressure_mode, 1 if update_wall_model else 0)
+                               max_iter, pressure_mode, 1 if update_wall_model else 0,
+                               1 if high_order_pressure_bc else 0)
         h = ctypes.c_void_p()
         _check(self.lib.dgw_ns_create(mesh.h, ctypes.byref(self.params), _ptr(u0, torch.float64, mesh.n_u, "u0"),
                                       _stream(stream), ctypes.byref(h)))

@@ -79,6 +79,27 @@ def test_projection_step_operators_match_oracle(dgw, name, w, kw):
          om.divdiv(tau_ref, v), TOL64, "div-div")
 
 
+@pytest.mark.parametrize("name,w,kw", CASES, ids=[c[0] for c in CASES])
+def test_curl_and_pressure_neumann_match_oracle(dgw, name, w, kw):
+    """(v, curl u) element by element; the wall integrals of the high-order pressure Neumann data
+    (eq. bc_d_pres) with two history levels, given the same vorticities, element by element."""
+    om, gm = _meshes(dgw, w, **kw)
+    dev = torch.device("cuda:0")
+    u = _velocity(om, w, kw)
+    u1 = u + 0.05 * I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=84)
+    y = torch.full((gm.n_u,), float("nan"), dtype=torch.float64, device=dev)
+    _cmp(gm.curl(torch.tensor(u, device=dev), y).cpu().numpy(), om.curl(u), TOL64, "curl")
+    w0 = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=85)
+    w1 = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=86)
+    force = (0.3, -0.2, 0.1)
+    base = I.uniform(w.seed, om.n_p, -1.0, 1.0, stream=87)
+    ref = base + om.pressure_neumann(u, w0, 2.0, u1, w1, -1.0, force)
+    b = torch.tensor(base, device=dev)
+    t = lambda a: torch.tensor(a, device=dev)
+    gm.add_pressure_neumann(b, t(u), t(w0), 2.0, t(u1), t(w1), -1.0, force)
+    _cmp(b.cpu().numpy(), ref, TOL64, "pressure Neumann data")
+
+
 def _l2(om, d, ref):
     return float(np.sqrt(abs(d @ om.vmass(d)) / (ref @ om.vmass(ref))))
 
@@ -123,25 +144,29 @@ def test_dual_splitting_keeps_poiseuille_flow_steady(dgw):
     om = O.Mesh(**w.mesh_kwargs(), n_layers=0)
     gm = dgw.mesh_for(w, n_layers=0)
     u0 = _std_field(om, lambda x, y, z: U * (1 - y ** 2), lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
-    ns = dgw.DualSplitting(gm, torch.tensor(u0, device="cuda"), dt=5e-3, force=(2 * nu * U, 0.0, 0.0),
-                           rtol_pressure=1e-12, rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0)
-    for _ in range(3):
-        ns.step()
-    u = ns.velocity().cpu().numpy()
-    assert _l2(om, u - u0, u0) < 1e-10
-    assert ns.pressure().abs().max().item() < 1e-9
+    for hobc in (False, True):
+        ns = dgw.DualSplitting(gm, torch.tensor(u0, device="cuda"), dt=5e-3, force=(2 * nu * U, 0.0, 0.0),
+                               rtol_pressure=1e-12, rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0,
+                               high_order_pressure_bc=hobc)
+        for _ in range(3):
+            ns.step()
+        u = ns.velocity().cpu().numpy()
+        assert _l2(om, u - u0, u0) < 1e-10
+        assert ns.pressure().abs().max().item() < 1e-9
 
 
 NS_CASES = [
-    ("channel_q2_4x4x2", I.Workload("ns", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=41), {}, False, 3),
-    ("channel_q3_l0", I.Workload("ns3", 3, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=43), {"enrich_l": 0}, False, 3),
-    ("bump_q2_6x4x2", I.bump_workload("nsb", 6, 4, 2, 2, seed=44), {}, False, 2),
-    ("channel_q2_wall_update", I.Workload("nsw", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=45), {}, True, 2),
+    ("channel_q2_4x4x2", I.Workload("ns", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=41), {}, False, 3, False),
+    ("channel_q3_l0", I.Workload("ns3", 3, 4, 2, 3, 395.0, 1.0 / 6000.0, seed=43), {"enrich_l": 0}, False, 3, False),
+    ("bump_q2_6x4x2", I.bump_workload("nsb", 6, 4, 2, 2, seed=44), {}, False, 2, False),
+    ("channel_q2_wall_update", I.Workload("nsw", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=45), {}, True, 2, False),
+    ("channel_q2_high_order_bc", I.Workload("nsh", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=47), {}, False, 3, True),
+    ("bump_q2_high_order_bc_wall_update", I.bump_workload("nsbh", 6, 4, 2, 2, seed=48), {}, True, 2, True),
 ]
 
 
-@pytest.mark.parametrize("name,w,kw,update,nsteps", NS_CASES, ids=[c[0] for c in NS_CASES])
-def test_dual_splitting_matches_oracle(dgw, name, w, kw, update, nsteps):
+@pytest.mark.parametrize("name,w,kw,update,nsteps,hobc", NS_CASES, ids=[c[0] for c in NS_CASES])
+def test_dual_splitting_matches_oracle(dgw, name, w, kw, update, nsteps, hobc):
     """Time steps of the GPU integrator against the oracle's, step by step. The GPU solves stop at
     1e-12 and the oracle's at 1e-13 relative residual; with condition numbers up to ~1e4 for these
     meshes the velocities agree to ~1e-8 as functions. The pressure solves for the divergence of a
@@ -151,9 +176,11 @@ def test_dual_splitting_matches_oracle(dgw, name, w, kw, update, nsteps):
     nef = 1 if kw.get("enrich_l", 1) == 0 else 8
     u0 = I.workload_velocity(om.node_coords(), om.n_e, w, nef=nef)
     dt, force = 2e-3, (w.tau_w / (0.5 * w.ly), 0.0, 0.0)
-    ref = O.DualSplitting(om, u0, dt=dt, force=force, rtol=1e-13, update_wall_model=update)
+    ref = O.DualSplitting(om, u0, dt=dt, force=force, rtol=1e-13, update_wall_model=update,
+                          high_order_pressure_bc=hobc)
     ns = dgw.DualSplitting(gm, torch.tensor(u0, device="cuda"), dt=dt, force=force, rtol_pressure=1e-12,
-                           rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0, update_wall_model=update)
+                           rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0, update_wall_model=update,
+                           high_order_pressure_bc=hobc)
     pscale = None
     for step in range(nsteps):
         info = ns.step()
