@@ -639,9 +639,12 @@ def run_profile_kernel(args):
         m.update_eddy_viscosity(u)
         x = u.to(dt)
         y = torch.empty(m.n_p if kind.startswith("divergence") else m.n_u, dtype=dt, device="cuda")
+        tau = torch.full((m.nc,), 1e-3, dtype=torch.float64, device="cuda")
         op = {"divergence": lambda: m.divergence(x, y), "convective": lambda: m.convective(x, y),
               "convective32": lambda: m.convective(x, y), "viscous": lambda: m.viscous(x, y),
-              "viscous32": lambda: m.viscous(x, y)}[kind]
+              "viscous32": lambda: m.viscous(x, y), "mass": lambda: m.mass(x, y),
+              "divdiv": lambda: m.divdiv(tau, x, y), "curl": lambda: m.curl(x, y),
+              "inverse_mass": lambda: m.inverse_mass(x, y)}[kind]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(2):
         op()
@@ -685,7 +688,7 @@ def main():
     ap.add_argument("--wall-update-steps", action="store_true", help="--ns-step: update the wall model every step")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["laplace64", "laplace32", "divergence", "convective", "convective32", "viscous",
-                             "viscous32"])
+                             "viscous32", "mass", "divdiv", "curl", "inverse_mass"])
     ap.add_argument("--profile-cells", type=int, nargs=4, default=[64, 48, 48, 4], metavar=("NX", "NY", "NZ", "K"))
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-geometry", type=int, default=0, choices=[0, 1], help="0 channel, 1 bump")

@@ -77,6 +77,7 @@ struct MeshView {
   const T *wt_face[2];
   int nvol[2], fpmax[2];
   // frozen eddy viscosity (linear quadrature set): [ne][nvol[0]], [ne][6][fpmax[0]]
+  const T *tau_d = nullptr;   // [nc] div-div penalty per cell (OP_DIVDIV; set per call)
   const T *nut_vol;
   const T *nut_face;
 };
@@ -228,13 +229,12 @@ cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, int nvec, cons
                               double *const *u_new, cudaStream_t s, int *bad_cell);
 cudaError_t launch_inverse_mass_cells(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
 cudaError_t launch_collocation_inverse_mass(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
-cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *tau_d, double dt_over_cr, double *y,
-                         cudaStream_t s);
+cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, double dt_over_cr, double *y, cudaStream_t s);
 cudaError_t launch_pressure_neumann(dgw_mesh *M, const double *u0, const double *w0, double b0, const double *u1,
                                     const double *w1, double b1, const double *f, double *y, cudaStream_t s);
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 
-enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3, OP_MASS = 4 };
+enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3, OP_MASS = 4, OP_DIVDIV = 5 };
 
 }  // namespace dgw

@@ -1,13 +1,12 @@
 // Operators of the projection step of the dual-splitting scheme (Sec. 4.2, eq. projectionspat):
 //   NS_GRAD   y = P(v, p) = -(div v, p)_K + (v, {{p}} n)_dK, {{p}} = p^- on walls
-//   NS_DIVDIV y = D(v, u) = (div v, tau_D div u)_K (eq. div-div), tau_D constant per cell
 //   NS_TAU    tau_D = |u|_K h dt / Cr per cell (eq. tauD), |u|_K the volume average, h = vol^(1/3)
 //   NS_CURL   y = (v, curl u)_K, the right-hand side of the vorticity's L2 projection (Sec. 4.2)
 // One CTA per cell with shared-memory sum factorisation over the cell's velocity point set (k+1
 // Gauss points, q_w wall-normal in cells with the wall model switched on); enriched test
-// functions psi N_v e_a through the wall tables. Both operators map a scalar per point, f(t), to
-// the test functions' divergences: the coefficient of d phi / d xi_d in output component a is
-// f J^-1[d][a].
+// functions psi N_v e_a through the wall tables. The gradient maps a scalar per point, f(t), to the
+// test functions' divergences: the coefficient of d phi / d xi_d in output component a is
+// f J^-1[d][a]. (The div-div penalty of the same step runs in the general operator kernel.)
 #include <cmath>
 
 #include "dgw_internal.h"
@@ -16,7 +15,7 @@
 
 namespace dgw {
 
-enum { NS_GRAD = 0, NS_DIVDIV = 1, NS_TAU = 2, NS_CURL = 3 };
+enum { NS_GRAD = 0, NS_TAU = 2, NS_CURL = 3 };
 
 namespace {
 
@@ -64,8 +63,8 @@ __host__ __device__ inline NsLayout ns_layout(int n, int qmax) {
 }
 
 template <int MODE>
-__global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, const double *__restrict__ tau_d,
-                             double dt_over_cr, double *__restrict__ y, int qmax) {
+__global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, double dt_over_cr,
+                             double *__restrict__ y, int qmax) {
   extern __shared__ double sm[];
   const Basis<double> &B = *m.basis;
   const int n = m.n1, nn = n * n, n3 = nn * n, c = blockIdx.x, tid = threadIdx.x;
@@ -89,6 +88,7 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
   const bool curved = m.geo == GEO_CURVED;
   const int col = curved ? metric_col(m, c) : 0;
   const double h[3] = {m.hx, curved ? 1.0 : m.hy[(c / m.nx) % m.ny], m.hz};
+  const double hinv[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]}, hvol = h[0] * h[1] * h[2];   // once per cell
   auto metric = [&](int t, double Ji[3][3], double &dV) {
     const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
     const double w3 = B.w[sx][i0] * B.w[sy][i1] * B.w[sx][i2];
@@ -98,8 +98,8 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
       dV = fabs(det) * w3;
     } else {
       for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) Ji[a][b] = a == b ? 1.0 / h[a] : 0.0;
-      dV = h[0] * h[1] * h[2] * w3;
+        for (int b = 0; b < 3; ++b) Ji[a][b] = a == b ? hinv[a] : 0.0;
+      dV = hvol * w3;
     }
   };
   const double *wtv = enr ? m.wt_vol[0] + (size_t)e * m.nvol[0] * WT : nullptr;
@@ -120,15 +120,14 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     }
     __syncthreads();
   } else {
-    // f accumulates sum_a du_a/dx_a (NS_DIVDIV) or |u| (NS_TAU) at the points; uv the curl (NS_CURL)
+    // point values of u (NS_TAU) or the curl (NS_CURL) accumulate in uv
     for (int t = tid; t < P; t += blockDim.x) f[t] = 0.0;
     if (MODE == NS_CURL)
       for (int t = tid; t < 3 * P; t += blockDim.x) uv[t] = 0.0;
     for (int a = 0; a < 3; ++a) {
       for (int d = 0; d < (MODE == NS_TAU ? 1 : 3); ++d) {
-        if (MODE == NS_DIVDIV && !curved && d != a) continue;   // boxes: J^-1 is diagonal
         if (MODE == NS_CURL && !curved && d == a) continue;     // the curl has no du_a/dx_a
-        constexpr bool DER = MODE == NS_DIVDIV || MODE == NS_CURL;
+        constexpr bool DER = MODE == NS_CURL;
         axis_pass(coef + a * n3, X, (DER && d == 0) ? D0 : S0, n, false, 0, n, n, n, q0, false);
         axis_pass(X, Y, (DER && d == 1) ? Dy : Sy, n, false, 1, q0, n, n, q1, false);
         axis_pass(Y, Z, (DER && d == 2) ? D0 : S0, n, false, 2, q0, q1, n, q0, false);
@@ -148,10 +147,6 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
               if (a == 1 && e2 == 0) uv[2 * P + t] += g;
               if (a == 0 && e2 == 1) uv[2 * P + t] -= g;
             }
-          } else {
-            double Ji[3][3], dV;
-            metric(t, Ji, dV);
-            f[t] += Ji[d][a] * Z[t];
           }
         }
         __syncthreads();
@@ -160,7 +155,7 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
     for (int t = tid; t < P; t += blockDim.x) {
       double Ji[3][3], dV;
       metric(t, Ji, dV);
-      double uu[3] = {0.0, 0.0, 0.0}, dv = 0.0, ge[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      double uu[3] = {0.0, 0.0, 0.0}, ge[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       if (MODE == NS_TAU) for (int a = 0; a < 3; ++a) uu[a] = uv[a * P + t];
       if (enr) {
         double xi[3], N[8], dN[8][3];
@@ -172,19 +167,16 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
           ref_to_phys(Ji, dN[v], g);
           for (int a = 0; a < 3; ++a) {
             uu[a] += w[0] * N[v] * ec[a * 8 + v];
-            dv += ec[a * 8 + v] * (w[0] * g[a] + N[v] * w[1 + a]);
             for (int e2 = 0; e2 < 3; ++e2) ge[a][e2] += ec[a * 8 + v] * (w[0] * g[e2] + N[v] * w[1 + e2]);
           }
         }
       }
       if (MODE == NS_TAU) {
         f[t] = dV * sqrt(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
-      } else if (MODE == NS_CURL) {
+      } else {
         uv[t] = dV * (uv[t] + ge[2][1] - ge[1][2]);
         uv[P + t] = dV * (uv[P + t] + ge[0][2] - ge[2][0]);
         uv[2 * P + t] = dV * (uv[2 * P + t] + ge[1][0] - ge[0][1]);
-      } else {
-        f[t] = dV * tau_d[c] * (f[t] + dv);
       }
     }
     __syncthreads();
@@ -476,8 +468,7 @@ cudaError_t launch_pressure_neumann(dgw_mesh *M, const double *u0, const double 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *tau_d, double dt_over_cr, double *y,
-                         cudaStream_t s) {
+cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, double dt_over_cr, double *y, cudaStream_t s) {
   const int n = M->n1;
   const int qmax = std::max(n, M->basis64.q[QSET_WALL]);
   const NsLayout L = ns_layout(n, qmax);
@@ -486,16 +477,14 @@ cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, const double *
   note_launch();
   if (mode == NS_GRAD) {
     e = cudaFuncSetAttribute(ns_op_kernel<NS_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) ns_op_kernel<NS_GRAD><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
-  } else if (mode == NS_DIVDIV) {
-    e = cudaFuncSetAttribute(ns_op_kernel<NS_DIVDIV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) ns_op_kernel<NS_DIVDIV><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
+    if (e == cudaSuccess) ns_op_kernel<NS_GRAD><<<M->nc, 128, smem, s>>>(M->v64, in, dt_over_cr, y, qmax);
+
   } else if (mode == NS_TAU) {
     e = cudaFuncSetAttribute(ns_op_kernel<NS_TAU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) ns_op_kernel<NS_TAU><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
+    if (e == cudaSuccess) ns_op_kernel<NS_TAU><<<M->nc, 128, smem, s>>>(M->v64, in, dt_over_cr, y, qmax);
   } else {
     e = cudaFuncSetAttribute(ns_op_kernel<NS_CURL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) ns_op_kernel<NS_CURL><<<M->nc, 128, smem, s>>>(M->v64, in, tau_d, dt_over_cr, y, qmax);
+    if (e == cudaSuccess) ns_op_kernel<NS_CURL><<<M->nc, 128, smem, s>>>(M->v64, in, dt_over_cr, y, qmax);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -7,6 +7,7 @@
 //   OP_VISC y = -F^nu(vbar,v~;ubar,u~)    (eq. viscous_multiscale, harmweights, minvt)
 //   OP_LAP  y = A_L p, SIPG               (eq. ipflux; curved cells only, boxes use laplace_box.cu)
 //   OP_MASS y = M(v,u) = (v,u)            (Sec. 4.2 mass term; volume only, enriched DoFs included)
+//   OP_DIVDIV y = D(v,u) = (div v, tau_D div u) (eq. div-div; volume only, tau_D per cell in m.tau_d)
 //
 // Wall-layer cells add the enrichment u~ = psi sum_B N_B u~_B (eq. enrichment) at q_wall
 // wall-normal Gauss points, with psi and grad psi read from the wall tables.
@@ -163,7 +164,7 @@ struct VecPlan {
 __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin, int qw) {
   VecPlan p;
   if (op == OP_LAP) qw = qin;   // the Laplacian has no enriched point sets
-  const bool grad = op == OP_VISC || op == OP_LAP;
+  const bool grad = op == OP_VISC || op == OP_LAP || op == OP_DIVDIV;
   const int nin = op == OP_LAP ? 1 : 3, nout = (op == OP_DIV || op == OP_LAP) ? 1 : 3;
   const int nca = op == OP_LAP ? 1 : ((op == OP_DIV && !curved) ? 1 : 3);
   const int ns = 4 * nca;
@@ -193,8 +194,8 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   p.vA = v; v += (has_v && 3 * p.P > ka * SX) ? 3 * p.P : ka * SX;
   p.vV = p.vA;
   p.vB = v; v += kb * SZ;
-  p.vG = v; v += (op == OP_CONV || op == OP_VISC ? 9 : 3) * p.P;
-  p.vGt = v; v += op == OP_VISC ? 9 * p.P : 0;
+  p.vG = v; v += (op == OP_CONV || op == OP_VISC || op == OP_DIVDIV ? 9 : 3) * p.P;
+  p.vGt = v; v += op == OP_VISC ? 9 * p.P : (op == OP_DIVDIV ? p.P : 0);
   p.vol_end = v;
   int f = o;   // trace slots: 2 faces x 2 sides x nca components
   p.fV2 = f; f += ns * nn;
@@ -218,7 +219,7 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   p.fF2 = g; g += 2 * nout * nn;
   p.fG2 = g; g += 2 * nout * nn;
   if (g > p.face_end) p.face_end = g;
-  if (op == OP_MASS) p.face_end = p.work;   // no face terms
+  if (op == OP_MASS || op == OP_DIVDIV) p.face_end = p.work;   // no face terms
   p.total = p.vol_end > p.face_end ? p.vol_end : p.face_end;
   return p;
 }
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   T *S0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Basis<T>) + 15) / 16) * 16);
   load_basis(m.basis, &B);
   constexpr bool CURVED = GEO == GEO_CURVED;
-  constexpr bool GRAD = OP == OP_VISC || OP == OP_LAP;
+  constexpr bool GRAD = OP == OP_VISC || OP == OP_LAP || OP == OP_DIVDIV;
   constexpr int NIN = OP == OP_LAP ? 1 : 3;                             // input components
   constexpr int NOUT = (OP == OP_DIV || OP == OP_LAP) ? 1 : 3;          // output components
   const int n = NC > 0 ? NC : m.n1, nn = n * n;
@@ -374,6 +375,20 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
             for (int d = 0; d < 3; ++d) gb[a][d] = G[(a * 3 + d) * P + t] * hinv[d];
           }
         }
+        if (OP == OP_DIVDIV) {
+          // tau_D div u, with the enrichment's divergence sum_a d(psi sum_v N_v e_av)/dx_a
+          T dv = gb[0][0] + gb[1][1] + gb[2][2];
+          if (enr_c)
+            for (int a = 0; a < 3; ++a) {
+              T g[3];
+              if (CURVED) ref_to_phys(Ji, sD[a], g);
+              dv += w[0] * (CURVED ? g[a] : sD[a][a] * hinv[a]) + sN[a] * w[1 + a];
+            }
+          const T fd = m.tau_d[c] * dv;
+          for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) tb[a][d] = a == d ? fd : T(0);
+          Gt[t] = dV * fd;
+        } else {
         for (int a = 0; a < 3; ++a)
           for (int d = 0; d < 3; ++d) tb[a][d] = nu * (gb[a][d] + gb[d][a]);
         if (enr_c) {
@@ -390,6 +405,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           for (int a = 0; a < 3; ++a)
             for (int d = 0; d < 3; ++d) tb[a][d] += nuh * (gt[a][d] + gt[d][a]);
         }
+        }
         for (int a = 0; a < 3; ++a) {
           if (CURVED) {
             T cf[3];
@@ -402,8 +418,9 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       }
     }
     __syncthreads();
-    // enriched test functions: -(grad(psi N_v) e_a, u x u) or (eps(psi N_v e_a), 2(nu+nu_t) eps(u~))
-    if (enr_c && (OP == OP_CONV || OP == OP_VISC)) {
+    // enriched test functions: -(grad(psi N_v) e_a, u x u), (eps(psi N_v e_a), 2(nu+nu_t) eps(u~)) or
+    // (div(psi N_v e_a), tau_D div u)
+    if (enr_c && (OP == OP_CONV || OP == OP_VISC || OP == OP_DIVDIV)) {
       auto contrib = [&](int t, T *acc) {
         const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
@@ -419,6 +436,11 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int d = 0; d < 3; ++d) cf[a][d] = -dV * uu[a] * uu[d];
+        } else if (OP == OP_DIVDIV) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cf[a][d] = a == d ? Gt[t] : T(0);
         } else {
           const T nd = dV * (nu + nutv[t]);
 #pragma unroll
@@ -492,7 +514,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
   }
 
-  if constexpr (OP != OP_MASS) {
+  if constexpr (OP != OP_MASS && OP != OP_DIVDIV) {
   // ================= faces, one direction (two faces) at a time =================
   // trace slots per direction: (face s, side, component); on boxes the divergence needs the normal
   // component only
@@ -1018,6 +1040,7 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
       case OP_CONV: return launch_vec<T, OP_CONV, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_VISC: return launch_vec<T, OP_VISC, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_MASS: return launch_vec<T, OP_MASS, GEO_CURVED>(m, u, y, s, nullptr);
+      case OP_DIVDIV: return launch_vec<T, OP_DIVDIV, GEO_CURVED>(m, u, y, s, nullptr);
       case OP_LAP:
         switch (m.n1) {
           case 2: return launch_vec<T, OP_LAP, GEO_CURVED, 2>(m, u, y, s, epi);
@@ -1035,6 +1058,7 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
     case OP_CONV: return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s, nullptr);
     case OP_VISC: return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s, nullptr);
     case OP_MASS: return launch_vec<T, OP_MASS, GEO_BOX>(m, u, y, s, nullptr);
+    case OP_DIVDIV: return launch_vec<T, OP_DIVDIV, GEO_BOX>(m, u, y, s, nullptr);
   }
   return cudaErrorInvalidValue;
 }
