@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("k", ctypes.c_int), ("enrich_l", ctypes.c_int), ("q_wall", ctypes.c_int),
         ("geometry", ctypes.c_int), ("wall_law", ctypes.c_int), ("n_layers", ctypes.c_int),
-        ("extra_q", ctypes.c_int),
+        ("extra_q", ctypes.c_int), ("full_q", ctypes.c_int),
         ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
         ("gamma", ctypes.c_double), ("nu", ctypes.c_double), ("tau_w", ctypes.c_double),
     ]
@@ -158,10 +158,11 @@ class Mesh:
     """Oracle mesh of a channel (geometry 0) or bump channel (geometry 1)."""
 
     def __init__(self, nx, ny, nz, k, *, lx=2 * np.pi, ly=2.0, lz=np.pi, gamma=1.8, nu=1.0 / 3250,
-                 tau_w=1.0, enrich_l=1, q_wall=8, geometry=0, wall_law=0, n_layers=1, extra_q=0):
+                 tau_w=1.0, enrich_l=1, q_wall=8, geometry=0, wall_law=0, n_layers=1, extra_q=0,
+                 full_quadrature=False):
         self.lib = _load()
         self.params = Params(nx, ny, nz, k, enrich_l, q_wall, geometry, wall_law, n_layers, extra_q,
-                             lx, ly, lz, gamma, nu, tau_w)
+                             1 if full_quadrature else 0, lx, ly, lz, gamma, nu, tau_w)
         h = self.lib.dgo_mesh_create(ctypes.byref(self.params))
         if not h:
             raise ValueError("oracle: invalid mesh parameters")

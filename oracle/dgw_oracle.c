@@ -57,6 +57,8 @@ typedef struct {
   int wall_law;          /* 0 Spalding, 1 van Driest */
   int n_layers;          /* enriched cell layers per wall; 0 disables enrichment */
   int extra_q;           /* extra quadrature points per direction (pins only) */
+  int full_q;            /* 1: enriched cells take q_wall points in every direction and faces touching
+                            them q_wall per tangential direction (the paper's 8^3 rule, Sec. 4.4) */
   double lx, ly, lz;     /* domain lengths; channel walls at y = +-ly/2, bump y in [yw(x), ly] */
   double gamma;          /* tanh grading factor */
   double nu;             /* kinematic viscosity */
@@ -627,7 +629,10 @@ static int inplane_points(const omesh *M, int op) {
 static void cell_points(const omesh *M, int c, int op, int nq[3]) {
   int n = inplane_points(M, op);
   nq[0] = nq[1] = nq[2] = n;
-  if (op != OP_LAPLACE && M->enr[c] >= 0) nq[1] = M->P.q_wall + M->P.extra_q;
+  if (op != OP_LAPLACE && M->enr[c] >= 0) {
+    nq[1] = M->P.q_wall + M->P.extra_q;
+    if (M->P.full_q) nq[0] = nq[2] = nq[1];
+  }
 }
 
 /* Neighbour across face f (d = f/2, side = f%2) of cell c: returns cell or -1 for a wall. */
@@ -649,8 +654,8 @@ static void face_points(const omesh *M, int c, int nb, int d, int op, int *t1, i
   *t2 = d == 2 ? 1 : 2;
   int n = inplane_points(M, op);
   int enr = op != OP_LAPLACE && (M->enr[c] >= 0 || (nb >= 0 && M->enr[nb] >= 0));
-  *n_t1 = (*t1 == 1 && enr) ? M->P.q_wall + M->P.extra_q : n;
-  *n_t2 = (*t2 == 1 && enr) ? M->P.q_wall + M->P.extra_q : n;
+  *n_t1 = ((*t1 == 1 || M->P.full_q) && enr) ? M->P.q_wall + M->P.extra_q : n;
+  *n_t2 = ((*t2 == 1 || M->P.full_q) && enr) ? M->P.q_wall + M->P.extra_q : n;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -1310,7 +1315,8 @@ static void apply_switch(omesh *M) {
   double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
   dgo_gauss(n1 + M->P.extra_q, gx, gw);
   dgo_gauss(qw, gy, gwy);
-  const int nin = n1 + M->P.extra_q;
+  const int nin = M->P.full_q ? qw : n1 + M->P.extra_q;
+  if (M->P.full_q) dgo_gauss(qw, gx, gw);
   for (int c = 0; c < M->nc; ++c) {
     int e = M->slot[c];
     if (e < 0) continue;
@@ -1439,7 +1445,8 @@ int dgo_project(void *h, const double *tau_new, const double *u_old, double *u_n
   if (M->ne == 0) { dgo_set_tau_nodes(h, tau_new); return 0; }
   /* old field at the points of every enriched cell */
   /* the wall cells' velocity point set, whether switched on or off */
-  const int nq[3] = {M->n1 + M->P.extra_q, M->P.q_wall + M->P.extra_q, M->n1 + M->P.extra_q};
+  const int qin = M->P.full_q ? M->P.q_wall + M->P.extra_q : M->n1 + M->P.extra_q;
+  const int nq[3] = {qin, M->P.q_wall + M->P.extra_q, qin};
   const int npts = nq[0] * nq[1] * nq[2];
   double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
   dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);

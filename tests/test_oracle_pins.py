@@ -899,3 +899,35 @@ def test_pressure_neumann_viscous_part():
     # the degree-4 interpolant of the sine on h = 2 pi / 16 differs by ~(h/2)^5 / 5! ~ 2e-6, and the
     # curl-curl takes two derivatives of it
     assert abs(q @ y / ref - 1.0) < 1e-4
+
+
+# ---------------------------------------------------------------------------------------------
+# Paper-literal enriched quadrature (Sec. 4.4: q_w points in every direction of enriched cells and
+# per tangential direction of faces touching them)
+# ---------------------------------------------------------------------------------------------
+
+def test_full_enriched_quadrature_keeps_the_pinned_invariants():
+    """With q_w^3 points in the wall cells: the shear-flow invariant of the convective term, the psi and
+    psi^2 integrals of the mass, and polynomial exactness of the Laplace-free operators hold as before;
+    for polynomial fields (no enrichment content) both rules integrate exactly, so the standard outputs
+    agree with the default rule to rounding."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs(), full_quadrature=True)
+    m0 = O.Mesh(**w.mesh_kwargs())
+    f = [lambda x, y, z: 0 * y] * 3
+    f[0] = lambda x, y, z: 1 - y ** 2
+    u = _std_field(m, *f)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = w.u_tau
+    assert np.abs(m.convective(u)).max() < 1e-14
+    e = np.zeros(m.n_u)
+    e[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 1.0
+    y = m.vmass(e)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    ref2 = 2 * (2 * math.pi * math.pi) * quad(lambda s: O.psi_spalding(s * w.u_tau / w.nu)[0] ** 2, 0.0, dy,
+                                              epsabs=1e-14, epsrel=1e-13, limit=200)[0]
+    assert abs(y[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :].sum() / ref2 - 1.0) < 1e-6
+    p = _std_field(m, lambda x, y, z: y ** 2, lambda x, y, z: 1 + y + 0 * x, lambda x, y, z: y * z)
+    for op in ("vmass", "divergence"):
+        a, b = getattr(m, op)(p), getattr(m0, op)(p)
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
