@@ -84,6 +84,9 @@ typedef struct {
   double nu;           /* kinematic viscosity */
   double tau_w;        /* wall shear stress (rho = 1) */
   int precision_mask;  /* bit 0: FP64 tables, bit 1: FP32 tables (for DGW_FP32 applies) */
+  int full_quadrature; /* 1: enriched cells take q_wall Gauss points in every direction and faces
+                          touching them q_wall per tangential direction (the paper's 8^3 to 12^3
+                          rule, Sec. 4.4); 0: q_wall wall-normal only. Channel geometry only. */
 } dgw_mesh_params;
 
 /* Build a mesh: geometry, penalty parameters tau_IP (Sec. 4.2: (k+1)^2 A(dK)/V(K), interior

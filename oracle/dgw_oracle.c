@@ -1365,14 +1365,16 @@ int dgo_wall_shear(void *h, const double *u, double *tn) {
   double *num = (double *)calloc((size_t)3 * nn, sizeof(double));
   double *den = (double *)calloc((size_t)nn, sizeof(double));
   double gx[MAXP], gw[MAXP];
-  dgo_gauss(n1, gx, gw);
   ptab t; ptab_alloc(&t, M);
   for (int wall = 0; wall < 2; ++wall)
     for (int kz = 0; kz < nz; ++kz)
       for (int i = 0; i < nx; ++i) {
         const int j = wall ? ny - 1 : 0, c = cell_id(M, i, j, kz);
-        for (int q2 = 0; q2 < n1; ++q2)
-          for (int q0 = 0; q0 < n1; ++q0) {
+        /* k+1 points per direction; q_w on the wall faces of enriched cells under the q_w^3 rule */
+        const int nf = (M->P.full_q && M->enr[c] >= 0) ? M->P.q_wall : n1;
+        dgo_gauss(nf, gx, gw);
+        for (int q2 = 0; q2 < nf; ++q2)
+          for (int q0 = 0; q0 < nf; ++q0) {
             double xi[3] = {gx[q0], wall ? 1.0 : 0.0, gx[q2]}, nrm[3];
             tabulate(M, c, xi, &t);
             double dA = face_geom(t.Ji, t.detJ, 1, wall, nrm) * gw[q0] * gw[q2];
@@ -1769,7 +1771,6 @@ int dgo_pressure_neumann(void *h, const double *u0, const double *u1, const doub
   omesh *M = (omesh *)h;
   const int nx = M->P.nx, ny = M->P.ny, nz = M->P.nz, n1 = M->n1, n3 = n1 * n1 * n1;
   double gx[MAXP], gw[MAXP];
-  dgo_gauss(n1, gx, gw);
   ptab t; ptab_alloc(&t, M);
   const double *us[2] = {u0, u1}, *ws[2] = {w0, w1};
   const double bs[2] = {b0, b1};
@@ -1778,8 +1779,10 @@ int dgo_pressure_neumann(void *h, const double *u0, const double *u1, const doub
       for (int i = 0; i < nx; ++i) {
         const int j = wall ? ny - 1 : 0, c = cell_id(M, i, j, kz);
         double *yc = y + (size_t)c * n3;
-        for (int q2 = 0; q2 < n1; ++q2)
-          for (int q0 = 0; q0 < n1; ++q0) {
+        const int nf = (M->P.full_q && M->enr[c] >= 0) ? M->P.q_wall : n1;
+        dgo_gauss(nf, gx, gw);
+        for (int q2 = 0; q2 < nf; ++q2)
+          for (int q0 = 0; q0 < nf; ++q0) {
             double xi[3] = {gx[q0], wall ? 1.0 : 0.0, gx[q2]}, nrm[3];
             tabulate(M, c, xi, &t);
             double dA = face_geom(t.Ji, t.detJ, 1, wall, nrm) * gw[q0] * gw[q2];

@@ -58,7 +58,7 @@ template <typename T>
 static void fill_view(dgw_mesh *M, MeshView<T> &v) {
   v.nx = M->P.nx; v.ny = M->P.ny; v.nz = M->P.nz;
   v.n1 = M->n1; v.nc = M->nc; v.ne = M->ne;
-  v.np = M->np; v.nu = M->nu; v.nef = M->nef;
+  v.np = M->np; v.nu = M->nu; v.nef = M->nef; v.full_q = M->P.full_quadrature ? 1 : 0;
   v.hx = (T)(M->P.lx / M->P.nx);
   v.hz = (T)(M->P.lz / M->P.nz);
   v.visc = (T)M->P.nu;
@@ -89,6 +89,10 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   if (P->n_layers < 0 || 2 * P->n_layers > P->ny)
     return set_error(DGW_EINVAL, "dgw_mesh_create: need 0 <= n_layers and 2*n_layers <= ny");
   if (P->enrich_l != 0 && P->enrich_l != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: enrich_l must be 0 or 1");
+  if (P->full_quadrature != 0 && P->full_quadrature != 1)
+    return set_error(DGW_EINVAL, "dgw_mesh_create: full_quadrature must be 0 or 1");
+  if (P->full_quadrature && P->geometry != 0)
+    return set_error(DGW_EINVAL, "dgw_mesh_create: full_quadrature is implemented for the channel geometry only");
   if (P->q_wall < 1 || P->q_wall > QW_MAX) return set_error(DGW_EINVAL, "dgw_mesh_create: q_wall must be in 1..10");
   if (!(P->lx > 0 && P->ly > 0 && P->lz > 0 && P->stretch_gamma > 0 && P->nu > 0 && P->tau_w > 0))
     return set_error(DGW_EINVAL, "dgw_mesh_create: lengths, gamma, nu and tau_w must be positive");
@@ -257,7 +261,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   const int qw = P->q_wall;
   for (int cls = 0; cls < 2; ++cls) {
     const int qi = cls == 0 ? n : qc;
-    const int nvol = qi * qi * qw, fpmax = std::max(qw * qi, qi * qi);
+    const int nvol = P->full_quadrature ? qw * qw * qw : qi * qi * qw;
+    const int fpmax = P->full_quadrature ? qw * qw : std::max(qw * qi, qi * qi);
     M->v64.nvol[cls] = M->v32.nvol[cls] = nvol;
     M->v64.fpmax[cls] = M->v32.fpmax[cls] = fpmax;
     M->v64.wt_vol[cls] = dalloc<double>(M, (size_t)ne * nvol * WT, &err);

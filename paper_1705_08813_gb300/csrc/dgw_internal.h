@@ -52,6 +52,7 @@ struct MeshView {
   int q[NQSET];       // point counts of the quadrature sets (host-visible copy)
   long np, nu;
   int nef;            // enrichment coefficients per component and wall cell: 8 (l = 1) or 1 (l = 0)
+  int full_q;         // 1: enriched cells use the q_wall set in every direction (faces: both tangential)
   int geo;            // GEO_BOX or GEO_CURVED
   T hx, hz;
   const T *hy;        // [ny] row heights (boxes)

@@ -82,7 +82,7 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
   }
   for (int t = tid; t < 3 * n3; t += blockDim.x) r[t] = 0.0;
   __syncthreads();
-  const int sx = QSET_LIN, sy = enr ? QSET_WALL : QSET_LIN;
+  const int sx = (enr && m.full_q) ? QSET_WALL : QSET_LIN, sy = enr ? QSET_WALL : QSET_LIN;
   const int q0 = B.q[sx], q1 = B.q[sy], P = q0 * q1 * q0;
   const double *S0 = B.S[sx], *D0 = B.D[sx], *Sy = B.S[sy], *Dy = B.D[sy];
   const bool curved = m.geo == GEO_CURVED;
@@ -263,7 +263,8 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
       face_axes(d, t1, t2);
       const bool enr_nb = nb >= 0 ? m.enr[nb] >= 0 : enr;
       const bool enr_any = enr || enr_nb;
-      const int s1 = (t1 == 1 && enr_any) ? QSET_WALL : QSET_LIN, s2 = (t2 == 1 && enr_any) ? QSET_WALL : QSET_LIN;
+      const int s1 = ((t1 == 1 || m.full_q) && enr_any) ? QSET_WALL : QSET_LIN;
+      const int s2 = ((t2 == 1 || m.full_q) && enr_any) ? QSET_WALL : QSET_LIN;
       const int p1 = B.q[s1], p2 = B.q[s2], FP = p1 * p2;
       // own and neighbour face layers (node index along d: side ? n-1 : 0, and the opposite)
       double *lo = X, *ln = X + nn, *tmp = Y, *g = Z;   // X holds 2 nn <= P, Y p1 n, Z 3 FP + FP
@@ -357,10 +358,10 @@ __global__ void ns_op_kernel(MeshView<double> m, const double *__restrict__ in, 
 
 // Value and physical gradient of a velocity-type field at wall-face point (a1, a2) of the face
 // xi_1 = side (Gauss-Lobatto nodes: the face trace is the node row jend), enrichment included.
-__device__ void wall_face_state(const Basis<double> &B, const double *su, const double *ce, const double *wt,
+__device__ void wall_face_state(const Basis<double> &B, int sq, const double *su, const double *ce, const double *wt,
                                 const double xi[3], const double Ji[3][3], int n, int a1, int a2, int side,
                                 double U[3], double G[3][3]) {
-  const double *S = B.S[QSET_LIN], *D = B.D[QSET_LIN], *de = B.dend[side];
+  const double *S = B.S[sq], *D = B.D[sq], *de = B.dend[side];
   const int n3 = n * n * n, jend = side ? n - 1 : 0;
   for (int a = 0; a < 3; ++a) {
     const double *ua = su + a * n3;
@@ -404,7 +405,7 @@ __global__ void pressure_neumann_kernel(MeshView<double> m, const double *__rest
   const int n = m.n1, nn = n * n, n3 = nn * n;
   const int b = blockIdx.x, wall = b / (m.nx * m.nz), r = b % (m.nx * m.nz), i = r % m.nx, kz = r / m.nx;
   const int j = wall ? m.ny - 1 : 0, c = i + m.nx * (j + m.ny * kz), side = wall, jend = side ? n - 1 : 0;
-  __shared__ double su[4][3 * NMAX * NMAX * NMAX], ce[4][24], gp[NMAX * NMAX];
+  __shared__ double su[4][3 * NMAX * NMAX * NMAX], ce[4][24], gp[QMAX * QMAX];
   const double *src[4] = {u0, w0, u1, w1};
   const int e = m.enr[c];
   for (int fld = 0; fld < 4; ++fld) {
@@ -414,12 +415,14 @@ __global__ void pressure_neumann_kernel(MeshView<double> m, const double *__rest
       ce[fld][t] = (v && e >= 0) ? v[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : 0.0;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-    const int a1 = t % n, a2 = t / n;
-    const double xi[3] = {B.x[QSET_LIN][a1], (double)side, B.x[QSET_LIN][a2]};
+  // k+1 points per direction; q_w on the wall faces of enriched cells under the q_w^3 rule
+  const int sq = (m.full_q && e >= 0) ? QSET_WALL : QSET_LIN, pq = B.q[sq];
+  for (int t = threadIdx.x; t < pq * pq; t += blockDim.x) {
+    const int a1 = t % pq, a2 = t / pq;
+    const double xi[3] = {B.x[sq][a1], (double)side, B.x[sq][a2]};
     double Ji[3][3], det;
     if (m.geo == GEO_CURVED) {
-      load_rec(face_rec(m, B, metric_col(m, c), 1, side, QSET_LIN, QSET_LIN, a1, a2), Ji, det);
+      load_rec(face_rec(m, B, metric_col(m, c), 1, side, sq, sq, a1, a2), Ji, det);
     } else {
       const double h[3] = {m.hx, m.hy[j], m.hz};
       for (int p = 0; p < 3; ++p)
@@ -429,15 +432,15 @@ __global__ void pressure_neumann_kernel(MeshView<double> m, const double *__rest
     const double gl = sqrt(Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1] + Ji[1][2] * Ji[1][2]);
     const double sg = side ? 1.0 : -1.0;
     const double nrm[3] = {sg * Ji[1][0] / gl, sg * Ji[1][1] / gl, sg * Ji[1][2] / gl};
-    const double dA = fabs(det) * gl * B.w[QSET_LIN][a1] * B.w[QSET_LIN][a2];
+    const double dA = fabs(det) * gl * B.w[sq][a1] * B.w[sq][a2];
     const double *wt = e >= 0 ? wt_face + (((size_t)e * 6 + 2 + side) * fpmax + t) * WT : nullptr;
     double acc[3] = {-f0, -f1, -f2};
     for (int h2 = 0; h2 < 2; ++h2) {
       const double beta = h2 ? b1 : b0;
       if (beta == 0.0 || !src[2 * h2]) continue;
       double U[3], G[3][3], W[3], GW[3][3];
-      wall_face_state(B, su[2 * h2], ce[2 * h2], wt, xi, Ji, n, a1, a2, side, U, G);
-      wall_face_state(B, su[2 * h2 + 1], ce[2 * h2 + 1], wt, xi, Ji, n, a1, a2, side, W, GW);
+      wall_face_state(B, sq, su[2 * h2], ce[2 * h2], wt, xi, Ji, n, a1, a2, side, U, G);
+      wall_face_state(B, sq, su[2 * h2 + 1], ce[2 * h2 + 1], wt, xi, Ji, n, a1, a2, side, W, GW);
       const double dv = G[0][0] + G[1][1] + G[2][2];
       const double cw[3] = {GW[2][1] - GW[1][2], GW[0][2] - GW[2][0], GW[1][0] - GW[0][1]};
       for (int a = 0; a < 3; ++a) {
@@ -448,12 +451,12 @@ __global__ void pressure_neumann_kernel(MeshView<double> m, const double *__rest
     gp[t] = -dA * (acc[0] * nrm[0] + acc[1] * nrm[1] + acc[2] * nrm[2]);
   }
   __syncthreads();
-  const double *S = B.S[QSET_LIN];
+  const double *S = B.S[sq];
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
     const int i1 = t % n, i2 = t / n;
     double acc = 0.0;
-    for (int a2 = 0; a2 < n; ++a2)
-      for (int a1 = 0; a1 < n; ++a1) acc += S[a1 * n + i1] * S[a2 * n + i2] * gp[a1 + n * a2];
+    for (int a2 = 0; a2 < pq; ++a2)
+      for (int a1 = 0; a1 < pq; ++a1) acc += S[a1 * n + i1] * S[a2 * n + i2] * gp[a1 + pq * a2];
     y[(size_t)c * n3 + i1 + n * (jend + n * i2)] += acc;
   }
 }

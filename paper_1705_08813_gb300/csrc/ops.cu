@@ -224,6 +224,12 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   return p;
 }
 
+// in-plane point count the shared-memory plan must hold: the wall set in wall cells under the q_w^3 rule
+template <typename T>
+__host__ __device__ inline int plan_qin(const MeshView<T> &m, int qset) {
+  return m.full_q && m.q[QSET_WALL] > m.q[qset] ? m.q[QSET_WALL] : m.q[qset];
+}
+
 // NC > 0: the node count per direction as a compile-time constant (the curved Laplacian, whose point
 // sets are all k+1 Gauss points, is instantiated per degree so the pass index arithmetic folds).
 template <typename T, int OP, int GEO, int NC = 0>
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   const int n = NC > 0 ? NC : m.n1, nn = n * n;
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const int opc = OP == OP_CONV ? 1 : 0;   // wall-table class
-  const VecPlan L = vec_plan(OP, CURVED, n, NC > 0 ? NC : m.q[qset], NC > 0 ? NC : m.q[QSET_WALL]);
+  const VecPlan L = vec_plan(OP, CURVED, n, NC > 0 ? NC : plan_qin(m, qset), NC > 0 ? NC : m.q[QSET_WALL]);
   const int n3 = L.n3;
   T *uo = S0 + L.uo, *r = S0 + L.r, *eo = S0 + L.eo, *re = S0 + L.re, *un = S0 + L.fUn, *en = S0 + L.en;
   const int c = blockIdx.x;
@@ -260,7 +266,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   T h[3] = {T(1), T(1), T(1)};
   if (!CURVED) { h[0] = m.hx; h[1] = m.hy[(c / m.nx) % m.ny]; h[2] = m.hz; }
   const T hinv[3] = {T(1) / h[0], T(1) / h[1], T(1) / h[2]};
-  const int sets[3] = {qset, enr_c ? QSET_WALL : qset, qset};
+  const bool fq = enr_c && m.full_q;   // the paper's q_w^3 rule in wall cells
+  const int sets[3] = {fq ? QSET_WALL : qset, enr_c ? QSET_WALL : qset, fq ? QSET_WALL : qset};
   const int q0 = NC > 0 ? NC : B.q[sets[0]], q1 = NC > 0 ? NC : B.q[sets[1]], q2 = NC > 0 ? NC : B.q[sets[2]];
   const int P = q0 * q1 * q2;
   const T vol = h[0] * h[1] * h[2];
@@ -534,8 +541,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     // point sets of the faces normal to d: the same for both faces (x/z neighbours share the row,
     // y-faces have only in-plane tangential axes)
     const bool enr_any = enr_c || enr_o[0] || enr_o[1];
-    const int s1 = (t1 == 1 && enr_any) ? QSET_WALL : qset;
-    const int s2 = (t2 == 1 && enr_any) ? QSET_WALL : qset;
+    const int s1 = ((t1 == 1 || m.full_q) && enr_any) ? QSET_WALL : qset;
+    const int s2 = ((t2 == 1 || m.full_q) && enr_any) ? QSET_WALL : qset;
     const int p1 = NC > 0 ? NC : B.q[s1], p2 = NC > 0 ? NC : B.q[s2], FP = p1 * p2;
     for (int t = threadIdx.x; t < 2 * NIN * n3; t += blockDim.x) {
       const int s = t / (NIN * n3), e = t - s * NIN * n3;
@@ -1011,7 +1018,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
 template <typename T, int OP, int GEO, int NC = 0>
 static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
-  const VecPlan L = vec_plan(OP, GEO == GEO_CURVED, m.n1, m.q[qset], m.q[QSET_WALL]);
+  const VecPlan L = vec_plan(OP, GEO == GEO_CURVED, m.n1, plan_qin(m, qset), m.q[QSET_WALL]);
   const size_t sm = ((sizeof(Basis<T>) + 15) / 16) * 16 + (size_t)L.total * sizeof(T);
   if (sm > 220 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set = false;

@@ -38,11 +38,12 @@ __global__ void project_eval_kernel(MeshView<double> m, const int *__restrict__ 
   for (int t = threadIdx.x; t < 24; t += blockDim.x)
     ce[t] = on ? u[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : 0.0;
   __syncthreads();
-  const int q0 = B.q[QSET_LIN], q1 = B.q[QSET_WALL];
-  const double *S0 = B.S[QSET_LIN], *Sw = B.S[QSET_WALL];
+  const int sx = m.full_q ? QSET_WALL : QSET_LIN;   // in-plane set of the wall cells
+  const int q0 = B.q[sx], q1 = B.q[QSET_WALL];
+  const double *S0 = B.S[sx], *Sw = B.S[QSET_WALL];
   for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
     const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-    const double xi[3] = {B.x[QSET_LIN][i0], B.x[QSET_WALL][i1], B.x[QSET_LIN][i2]};
+    const double xi[3] = {B.x[sx][i0], B.x[QSET_WALL][i1], B.x[sx][i2]};
     double val[3] = {0.0, 0.0, 0.0};
     for (int cc = 0; cc < n; ++cc)
       for (int bb = 0; bb < n; ++bb) {
@@ -93,7 +94,8 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
   extern __shared__ double sm[];
   const Basis<double> &B = *m.basis;
   const int n = m.n1, n2 = n * n, n3 = n2 * n, N = n3 + m.nef;
-  const int q0 = B.q[QSET_LIN], q1 = B.q[QSET_WALL], npts = q0 * q1 * q0;
+  const int sx = m.full_q ? QSET_WALL : QSET_LIN;   // in-plane set of the wall cells
+  const int q0 = B.q[sx], q1 = B.q[QSET_WALL], npts = q0 * q1 * q0;
   const ProjLayout L = proj_layout(n, q0, q1, m.nef);
   double *W = sm + L.W, *PSI = sm + L.PSI, *T1 = sm + L.T1, *T2 = sm + L.T2, *R = sm + L.RHS, *col = sm + L.COL;
   const int e = blockIdx.x, c = enr_cell[e], tid = threadIdx.x, nt = blockDim.x;
@@ -103,8 +105,8 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
   // switched off in the new space: the standard block alone (stride N kept), zero enrichment
   const int nef = m.enr[c] >= 0 ? m.nef : 0, Nc = n3 + nef;
   double *A = Ag + (size_t)e * N * N;
-  const double *S0 = B.S[QSET_LIN], *Sw = B.S[QSET_WALL];
-  const double *w0 = B.w[QSET_LIN], *w1 = B.w[QSET_WALL];
+  const double *S0 = B.S[sx], *Sw = B.S[QSET_WALL];
+  const double *w0 = B.w[sx], *w1 = B.w[QSET_WALL];
   // 0. weights |det J| w at the points and psi_new
   const double hbox = m.geo == GEO_CURVED ? 0.0 : m.hx * m.hy[(c / m.nx) % m.ny] * m.hz;
   const int colm = m.geo == GEO_CURVED ? metric_col(m, c) : 0;
@@ -152,7 +154,7 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
       const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
       const double ph = S0[i0 * n + a1] * Sw[i1 * n + b1] * S0[i2 * n + c1] * W[t];
       if (k < nef) {
-        const double xi[3] = {B.x[QSET_LIN][i0], B.x[QSET_WALL][i1], B.x[QSET_LIN][i2]};
+        const double xi[3] = {B.x[sx][i0], B.x[QSET_WALL][i1], B.x[sx][i2]};
         s += ph * PSI[t] * enr_weight(nef, k, xi);
       } else {
         s += ph * P[((size_t)e * npts + t) * 3 + (k - nef)];
@@ -171,7 +173,7 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
     double s = 0.0;
     for (int t = 0; t < npts; ++t) {
       const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-      const double xi[3] = {B.x[QSET_LIN][i0], B.x[QSET_WALL][i1], B.x[QSET_LIN][i2]};
+      const double xi[3] = {B.x[sx][i0], B.x[QSET_WALL][i1], B.x[sx][i2]};
       const double f = W[t] * PSI[t] * enr_weight(nef, v, xi);
       s += k < nef ? f * PSI[t] * enr_weight(nef, k, xi) : f * P[((size_t)e * npts + t) * 3 + (k - nef)];
     }
@@ -277,7 +279,8 @@ __global__ void chol_solve_kernel(MeshView<double> m, const int *__restrict__ en
 
 static cudaError_t proj_scratch(dgw_mesh *M, int nvec) {
   const int n = M->n1, N = n * n * n + M->nef;
-  const int npts = M->basis64.q[QSET_LIN] * M->basis64.q[QSET_WALL] * M->basis64.q[QSET_LIN];
+  const int qx = M->basis64.q[M->P.full_quadrature ? QSET_WALL : QSET_LIN];
+  const int npts = qx * M->basis64.q[QSET_WALL] * qx;
   cudaError_t e = cudaSuccess;
   if (!M->proj_A) {
     void *a = nullptr, *w = nullptr;
@@ -307,7 +310,7 @@ cudaError_t launch_inverse_mass_cells(dgw_mesh *M, const double *r, double *x, c
   cudaError_t e = proj_scratch(M, 1);
   if (e != cudaSuccess) return e;
   const int n = M->n1, N = n * n * n + M->nef;
-  const int q0 = M->basis64.q[QSET_LIN], q1 = M->basis64.q[QSET_WALL];
+  const int q0 = M->basis64.q[M->P.full_quadrature ? QSET_WALL : QSET_LIN], q1 = M->basis64.q[QSET_WALL];
   if (!M->mass_factor_valid) {
     const ProjLayout L = proj_layout(n, q0, q1, M->nef);
     const size_t smem = (size_t)L.total * sizeof(double);
@@ -334,7 +337,7 @@ cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, int nvec, cons
                               double *const *u_new, cudaStream_t s, int *bad_cell) {
   *bad_cell = -1;
   const int n = M->n1;
-  const int q0 = M->basis64.q[QSET_LIN], q1 = M->basis64.q[QSET_WALL], npts = q0 * q1 * q0;
+  const int q0 = M->basis64.q[M->P.full_quadrature ? QSET_WALL : QSET_LIN], q1 = M->basis64.q[QSET_WALL], npts = q0 * q1 * q0;
   cudaError_t e = M->ne > 0 ? proj_scratch(M, nvec) : cudaSuccess;
   const size_t pstride = (size_t)M->ne * npts * 3;
   // every vector is evaluated in the old space before the tables change

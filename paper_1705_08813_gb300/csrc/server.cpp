@@ -47,7 +47,7 @@ bool same_params(const dgw_mesh_params &a, const dgw_mesh_params &b) {
   return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.degree == b.degree && a.enrich_l == b.enrich_l &&
          a.q_wall == b.q_wall && a.geometry == b.geometry && a.wall_law == b.wall_law && a.n_layers == b.n_layers &&
          a.lx == b.lx && a.ly == b.ly && a.lz == b.lz && a.stretch_gamma == b.stretch_gamma && a.nu == b.nu &&
-         a.tau_w == b.tau_w && a.precision_mask == b.precision_mask;
+         a.tau_w == b.tau_w && a.precision_mask == b.precision_mask && a.full_quadrature == b.full_quadrature;
 }
 
 // Device bytes a job needs beyond its caller-owned vectors: the mesh and, for solves, the CG

@@ -125,6 +125,7 @@ __device__ void wall_point(const WallCellData &w, int e, const double xi[3], con
 // point's metric.
 __device__ __forceinline__ void vol_xi(const WallCellData &w, const Basis<double> &B, int c, int qs, int t, double xi[3],
                                        double Ji[3][3]) {
+  if (w.mv.full_q) qs = QSET_WALL;   // the q_w^3 rule
   const int q0 = B.q[qs], q1 = B.q[QSET_WALL];
   const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
   xi[0] = B.x[qs][i0]; xi[1] = B.x[QSET_WALL][i1]; xi[2] = B.x[qs][i2];
@@ -135,7 +136,7 @@ __device__ __forceinline__ bool face_xi(const WallCellData &w, const Basis<doubl
   const int d = f >> 1, side = f & 1;
   int t1, t2;
   face_axes(d, t1, t2);
-  const int s1 = t1 == 1 ? QSET_WALL : qs, s2 = t2 == 1 ? QSET_WALL : qs;
+  const int s1 = (t1 == 1 || w.mv.full_q) ? QSET_WALL : qs, s2 = (t2 == 1 || w.mv.full_q) ? QSET_WALL : qs;
   const int p1 = B.q[s1], p2 = B.q[s2];
   if (t >= p1 * p2) return false;
   xi[d] = side; xi[t1] = B.x[s1][t % p1]; xi[t2] = B.x[s2][t / p1];
@@ -273,23 +274,25 @@ cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s) 
 __global__ void wall_shear_face_kernel(MeshView<double> m, const double *__restrict__ u, const double *__restrict__ wt_face,
                                        int fpmax, double nu, double *__restrict__ out) {
   const Basis<double> &B = *m.basis;
-  const int n = m.n1, n3 = n * n * n, np2 = n * n;
+  const int n = m.n1, n3 = n * n * n;
   const int b = blockIdx.x, wall = b / (m.nx * m.nz), r = b % (m.nx * m.nz), i = r % m.nx, kz = r / m.nx;
   const int j = wall ? m.ny - 1 : 0, c = i + m.nx * (j + m.ny * kz), side = wall;
-  __shared__ double su[3 * NMAX * NMAX * NMAX], ce[24], mom[NMAX * NMAX][16];
+  __shared__ double su[3 * NMAX * NMAX * NMAX], ce[24], mom[QMAX * QMAX][16];
   for (int t = threadIdx.x; t < 3 * n3; t += blockDim.x) su[t] = u[(size_t)c * 3 * n3 + t];
   const int e = m.enr ? m.enr[c] : -1;
   for (int t = threadIdx.x; t < 24; t += blockDim.x)
     ce[t] = e >= 0 ? u[3 * m.np + (size_t)e * 3 * m.nef + (m.nef == 8 ? t : t >> 3)] : 0.0;
   __syncthreads();
-  const double *S = B.S[QSET_LIN], *D = B.D[QSET_LIN], *de = B.dend[side];
+  // k+1 points per direction; q_w on the wall faces of enriched cells under the q_w^3 rule
+  const int sq = (m.full_q && e >= 0) ? QSET_WALL : QSET_LIN, pq = B.q[sq], npts = pq * pq;
+  const double *S = B.S[sq], *D = B.D[sq], *de = B.dend[side];
   const int jend = side ? n - 1 : 0;
-  for (int t = threadIdx.x; t < np2; t += blockDim.x) {
-    const int a1 = t % n, a2 = t / n;
-    const double xi[3] = {B.x[QSET_LIN][a1], (double)side, B.x[QSET_LIN][a2]};
+  for (int t = threadIdx.x; t < npts; t += blockDim.x) {
+    const int a1 = t % pq, a2 = t / pq;
+    const double xi[3] = {B.x[sq][a1], (double)side, B.x[sq][a2]};
     double Ji[3][3], det;
     if (m.geo == GEO_CURVED) {
-      load_rec(face_rec(m, B, metric_col(m, c), 1, side, QSET_LIN, QSET_LIN, a1, a2), Ji, det);
+      load_rec(face_rec(m, B, metric_col(m, c), 1, side, sq, sq, a1, a2), Ji, det);
     } else {
       const double h[3] = {m.hx, m.hy[j], m.hz};
       for (int p = 0; p < 3; ++p)
@@ -328,7 +331,7 @@ __global__ void wall_shear_face_kernel(MeshView<double> m, const double *__restr
     const double gl = sqrt(Ji[1][0] * Ji[1][0] + Ji[1][1] * Ji[1][1] + Ji[1][2] * Ji[1][2]);
     const double sg = side ? 1.0 : -1.0;
     const double nrm[3] = {sg * Ji[1][0] / gl, sg * Ji[1][1] / gl, sg * Ji[1][2] / gl};
-    const double dA = fabs(det) * gl * B.w[QSET_LIN][a1] * B.w[QSET_LIN][a2];
+    const double dA = fabs(det) * gl * B.w[sq][a1] * B.w[sq][a2];
     double tw[3];
     for (int a = 0; a < 3; ++a) tw[a] = nu * (G[a][0] * nrm[0] + G[a][1] * nrm[1] + G[a][2] * nrm[2]);
     for (int v = 0; v < 4; ++v) {
@@ -340,7 +343,7 @@ __global__ void wall_shear_face_kernel(MeshView<double> m, const double *__restr
   __syncthreads();
   if (threadIdx.x < 16) {
     double acc = 0.0;
-    for (int t = 0; t < np2; ++t) acc += mom[t][threadIdx.x];
+    for (int t = 0; t < npts; ++t) acc += mom[t][threadIdx.x];
     out[(size_t)b * 16 + threadIdx.x] = acc;
   }
 }

@@ -53,7 +53,7 @@ class MeshParams(ctypes.Structure):
                 ("geometry", ctypes.c_int), ("wall_law", ctypes.c_int), ("n_layers", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
                 ("stretch_gamma", ctypes.c_double), ("nu", ctypes.c_double), ("tau_w", ctypes.c_double),
-                ("precision_mask", ctypes.c_int)]
+                ("precision_mask", ctypes.c_int), ("full_quadrature", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -166,11 +166,11 @@ class Mesh:
     """A device-resident mesh of the channel with its metric and wall tables."""
 
     def __init__(self, nx, ny, nz, k, *, lx, ly=2.0, lz, gamma=1.8, nu, tau_w, n_layers=1, q_wall=8,
-                 wall_law=0, enrich_l=1, geometry=0, fp32=True, stream=None):
+                 wall_law=0, enrich_l=1, geometry=0, fp32=True, full_quadrature=False, stream=None):
         lib = load()
         self.lib = lib
         self.params = MeshParams(nx, ny, nz, k, enrich_l, q_wall, geometry, wall_law, n_layers,
-                                 lx, ly, lz, gamma, nu, tau_w, 3 if fp32 else 1)
+                                 lx, ly, lz, gamma, nu, tau_w, 3 if fp32 else 1, 1 if full_quadrature else 0)
         h = ctypes.c_void_p()
         _check(lib.dgw_mesh_create(ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
         self.h = h
