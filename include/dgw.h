@@ -86,10 +86,7 @@ typedef struct {
   int precision_mask;  /* bit 0: FP64 tables, bit 1: FP32 tables (for DGW_FP32 applies) */
   int full_quadrature; /* 1: enriched cells take q_wall Gauss points in every direction and faces
                           touching them q_wall per tangential direction (the paper's 8^3 to 12^3
-                          rule, Sec. 4.4); 0: q_wall wall-normal only. Channel geometry only. The
-                          velocity operators give both faces of a cell normal to one direction the same
-                          rule, so the y-face between the first and second standard rows also takes
-                          q_wall per direction under 1. */
+                          rule, Sec. 4.4); 0: q_wall wall-normal only. Channel geometry only. */
 } dgw_mesh_params;
 
 /* Build a mesh: geometry, penalty parameters tau_IP (Sec. 4.2: (k+1)^2 A(dK)/V(K), interior

@@ -538,9 +538,14 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       enb[s] = (OP != OP_LAP && nbr[s] >= 0) ? m.enr[nbr[s]] : -1;
       enr_o[s] = nbr[s] >= 0 ? enb[s] >= 0 : enr_c;   // the mirror side carries c's class
     }
-    // point sets of the faces normal to d: the same for both faces (x/z neighbours share the row,
-    // y-faces have only in-plane tangential axes)
-    const bool enr_any = enr_c || enr_o[0] || enr_o[1];
+    // point sets of the faces normal to d: each face takes q_w along its tangential axis y (every
+    // tangential axis under the q_w^3 rule) if it touches an enriched cell. When that rule differs
+    // between the two faces (the q_w^3 rule above the enriched layer, switched-off columns), the
+    // faces are done in two passes, each zeroing the other face's coefficients.
+    const bool ef0 = enr_c || enr_o[0], ef1 = enr_c || enr_o[1];
+    const int ngrp = ((t1 == 1 || t2 == 1 || m.full_q) && ef0 != ef1) ? 2 : 1;
+    for (int grp = 0; grp < ngrp; ++grp) {
+    const bool enr_any = ngrp == 2 ? (grp ? ef1 : ef0) : (ef0 || ef1);
     const int s1 = ((t1 == 1 || m.full_q) && enr_any) ? QSET_WALL : qset;
     const int s2 = ((t2 == 1 || m.full_q) && enr_any) ? QSET_WALL : qset;
     const int p1 = NC > 0 ? NC : B.q[s1], p2 = NC > 0 ? NC : B.q[s2], FP = p1 * p2;
@@ -588,6 +593,15 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     T *C = S0 + L.fC, *E = S0 + L.fE;
     for (int t = threadIdx.x; t < 2 * FP; t += blockDim.x) {
       const int s = t / FP, pt = t - s * FP;
+      if (ngrp == 2 && s != grp) {   // the other face is done in its own pass
+        T *Cz = C + s * 3 * 4 * L.FP;
+        for (int j = 0; j < 12; ++j) Cz[j * L.FP + pt] = T(0);
+        if (OP == OP_CONV || OP == OP_VISC) {
+          T *Ez = E + s * 3 * 4 * L.FP;
+          for (int j = 0; j < 12; ++j) Ez[j * L.FP + pt] = T(0);
+        }
+        continue;
+      }
       const int f = 2 * d + s, side = s;
       const int nb = nbr[s], eb = enb[s];
       const int a1 = pt % p1, a2 = pt / p1;
@@ -980,6 +994,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       r[t] += add;
     }
     __syncthreads();
+    }   // face groups
   }
   }
   // ================= store =================

@@ -66,6 +66,10 @@ def test_operators_match_oracle(dgw, name, w, kw):
     y = torch.empty(gm.n_u, dtype=torch.float64, device=dev)
     refc = om.convective(u)
     _cmp(gm.convective(ud, y).cpu().numpy(), refc, TOL64, "convective")
+    # a random field: the normal velocity changes sign on every face, so the Lax-Friedrichs flux is not
+    # polynomial there and each face's point rule matters (the faces above the enriched layer)
+    ur = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=101)
+    _cmp(gm.convective(torch.tensor(ur, device=dev), y).cpu().numpy(), om.convective(ur), TOL64, "convective (random)")
     y32 = torch.empty(gm.n_u, dtype=torch.float32, device=dev)
     _cmp(gm.convective(ud.float(), y32).cpu().numpy(), refc, 2e-5, "convective fp32")
     gm.update_eddy_viscosity(ud)
@@ -118,12 +122,10 @@ def test_projection_and_time_steps_match_oracle(dgw):
     ds = O.DualSplitting(om2, u0, dt=2e-3, force=force, rtol=1e-13, high_order_pressure_bc=True)
     ns = dgw.DualSplitting(gm2, torch.tensor(u0, device=dev), dt=2e-3, force=force, rtol_pressure=1e-12,
                            rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0, high_order_pressure_bc=True)
-    # the steps stack four iterative solves (GPU 1e-12, oracle 1e-13) whose differences the explicit
-    # step amplifies; under this rule they agree to about 1e-7 as functions (3e-10 under the default rule)
     for _ in range(2):
         ns.step()
         ur, _ = ds.step()
-        assert _l2(om2, ns.velocity().cpu().numpy() - ur, ur) < 2e-7
+        assert _l2(om2, ns.velocity().cpu().numpy() - ur, ur) < 1e-8
 
 
 def test_full_quadrature_rejected_on_curved_meshes(dgw):

@@ -239,6 +239,10 @@ def test_switch_off_operators_match_oracle(dgw, name, w, kw):
     ud = torch.tensor(u, device=dev)
     y = torch.full((gm.n_u,), float("nan"), dtype=torch.float64, device=dev)
     _cmp(gm.convective(ud, y).cpu().numpy(), om.convective(u), TOL64, "convective")
+    # random field: sign-changing normal velocity makes each face's point rule matter (faces of a
+    # switched-off cell next to a switched-on one take q_w along y, the others the standard rule)
+    ur = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=102)
+    _cmp(gm.convective(torch.tensor(ur, device=dev), y).cpu().numpy(), om.convective(ur), TOL64, "convective (random)")
     y.fill_(float("nan"))
     _cmp(gm.mass(ud, y).cpu().numpy(), om.vmass(u), TOL64, "mass")
     b = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
