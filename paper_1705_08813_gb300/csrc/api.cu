@@ -439,13 +439,13 @@ dgw_status dgw_project_velocity(dgw_mesh_t M, const double *tau_nodes, const dou
 
 dgw_status dgw_apply_gradient(dgw_mesh_t M, const double *p, double *y, void *stream) {
   if (!M || !p || !y) return set_error(DGW_EINVAL, "dgw_apply_gradient: null argument");
-  return cuda_check(launch_ns_op(0, M, p, 0.0, y, (cudaStream_t)stream), "dgw_apply_gradient");
+  return cuda_check(launch_ns_op(NS_GRAD, M, p, 0.0, y, (cudaStream_t)stream), "dgw_apply_gradient");
 }
 
 dgw_status dgw_tau_divdiv(dgw_mesh_t M, const double *u, double dt, double cr, double *tau_d, void *stream) {
   if (!M || !u || !tau_d) return set_error(DGW_EINVAL, "dgw_tau_divdiv: null argument");
   if (!(dt > 0.0) || !(cr > 0.0)) return set_error(DGW_EINVAL, "dgw_tau_divdiv: dt and cr must be positive");
-  return cuda_check(launch_ns_op(2, M, u, dt / cr, tau_d, (cudaStream_t)stream), "dgw_tau_divdiv");
+  return cuda_check(launch_ns_op(NS_TAU, M, u, dt / cr, tau_d, (cudaStream_t)stream), "dgw_tau_divdiv");
 }
 
 dgw_status dgw_apply_divdiv(dgw_mesh_t M, const double *tau_d, const double *u, double *y, void *stream) {
@@ -457,7 +457,7 @@ dgw_status dgw_apply_divdiv(dgw_mesh_t M, const double *tau_d, const double *u, 
 
 dgw_status dgw_apply_curl(dgw_mesh_t M, const double *u, double *y, void *stream) {
   if (!M || !u || !y) return set_error(DGW_EINVAL, "dgw_apply_curl: null argument");
-  return cuda_check(launch_ns_op(3, M, u, 0.0, y, (cudaStream_t)stream), "dgw_apply_curl");
+  return cuda_check(launch_ns_op(NS_CURL, M, u, 0.0, y, (cudaStream_t)stream), "dgw_apply_curl");
 }
 
 dgw_status dgw_add_pressure_neumann(dgw_mesh_t M, const double *u0, const double *w0, double beta0, const double *u1,

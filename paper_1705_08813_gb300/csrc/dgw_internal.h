@@ -230,6 +230,8 @@ cudaError_t launch_projection(dgw_mesh *M, const double *tau_new, int nvec, cons
                               double *const *u_new, cudaStream_t s, int *bad_cell);
 cudaError_t launch_inverse_mass_cells(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
 cudaError_t launch_collocation_inverse_mass(dgw_mesh *M, const double *r, double *x, cudaStream_t s);
+// modes of the projection-step kernel: pressure gradient P(v, p), tau_D per cell, (v, curl u)
+enum { NS_GRAD = 0, NS_TAU = 2, NS_CURL = 3 };
 cudaError_t launch_ns_op(int mode, dgw_mesh *M, const double *in, double dt_over_cr, double *y, cudaStream_t s);
 cudaError_t launch_pressure_neumann(dgw_mesh *M, const double *u0, const double *w0, double b0, const double *u1,
                                     const double *w1, double b1, const double *f, double *y, cudaStream_t s);

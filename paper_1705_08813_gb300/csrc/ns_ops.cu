@@ -15,8 +15,6 @@
 
 namespace dgw {
 
-enum { NS_GRAD = 0, NS_TAU = 2, NS_CURL = 3 };
-
 namespace {
 
 // out[t] over a 3-D tensor (x fastest): a pass along axis ax maps extent ni -> no with the 1-D
