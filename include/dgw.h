@@ -95,6 +95,8 @@ typedef struct {
  * (y_h, y+, psi, grad psi at every enriched quadrature point, Sec. 3.2 and Appendix A) and the
  * operator diagonal. Synchronises `stream`. *out receives a library-owned handle. */
 dgw_status dgw_mesh_create(const dgw_mesh_params *params, void *stream, dgw_mesh_t *out);
+/* Free a mesh and everything the library holds for it (solver, Helmholtz and projection workspaces).
+ * Waits for the device; NULL is accepted. Handles, not paper operations: no passage defines these. */
 dgw_status dgw_mesh_destroy(dgw_mesh_t mesh);
 /* n_p = nc (k+1)^3, n_u = 3 n_p + 24 n_enriched (enrich_l = 1) or 3 n_p + 3 n_enriched
  * (enrich_l = 0); hbm_bytes = device memory the mesh holds. */
@@ -297,6 +299,7 @@ typedef struct {
  * starting from the velocity u0 (n_u doubles, device, copied). The integrator owns its vectors;
  * the mesh must outlive it. Synchronises `stream`. */
 dgw_status dgw_ns_create(dgw_mesh_t mesh, const dgw_ns_params *params, const double *u0, void *stream, dgw_ns_t *out);
+/* Free the integrator's vectors (not the mesh); NULL is accepted. */
 dgw_status dgw_ns_destroy(dgw_ns_t ns);
 /* One time step, BDF2 with second-order extrapolation (first order in the first step), constant dt:
  *   u^  = (sum alpha_i u^{n-i} + dt f - dt M^-1 sum beta_i F^c(u^{n-i})) / gamma_0 (eq. convstepspat)
@@ -341,7 +344,8 @@ typedef struct {
   dgw_solve_opts opts;    /* solves only */
 } dgw_job;
 
-/* Start a request loop with `max_inflight` worker slots (1..64) and a device-memory budget for
+/* Serving (no counterpart in the paper; a service of the library around the solve of Sec. 4.1).
+ * Start a request loop with `max_inflight` worker slots (1..64) and a device-memory budget for
  * resident meshes and solver state. */
 dgw_status dgw_server_create(size_t hbm_budget, int max_inflight, dgw_server_t *out);
 /* Queue a job. Its input must be complete on the device when submitted (synchronise the stream
