@@ -683,9 +683,9 @@ def main():
     ap.add_argument("--solve-mode", type=int, default=1)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    # DRAM bytes per launch of laplace_box_kernel<float,4> at the bench workload, scaled by DoFs from the
-    # ncu capture summarised in profiles/laplace_box_fp32_q4_64x48x48.md (same kernel build)
-    ap.add_argument("--traffic-bytes", type=float, default=(76.903424e6 + 40.288256e6) * 2304000 / 18432000)
+    # DRAM bytes (read + write) per launch of the roofline kernel, from an ncu capture of the same
+    # kernel build; none unless given
+    ap.add_argument("--traffic-bytes", type=float, default=None)
     ap.add_argument("--serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=400)
     ap.add_argument("--serving-slots", type=int, default=8)

@@ -229,18 +229,21 @@ dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const
                               dgw_solve_info *info, void *stream);
 
 /* Pressure solve that allocates nothing, for callers that cannot let a library allocate device
- * memory at solve time: code recording its work into a CUDA graph (allocation is illegal during
- * stream capture), code whose device memory belongs to a framework's caching allocator or to a
- * budget fixed at start-up, and latency-critical loops where cudaMalloc/cudaFree would
- * synchronise the device. The paper has no counterpart; this is a service of the library.
+ * memory at solve time: code whose device memory belongs to a framework's caching allocator or
+ * to a budget fixed at start-up (an allocation outside that pool can fail or exhaust it), and
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise the device and stall other
+ * streams. The paper has no counterpart; this is a service of the library.
  * Solves -L p = b like dgw_pressure_solve with mode 2 (FP64 CG, Jacobi preconditioner, zero-mean
  * b and p) on `stream`, with all scratch vectors in one file-scope device array of fixed size:
  * 5 * 131072 + 312 doubles (about 5.2 MB), which every GPU that loads the library holds until the
  * process exits. Meshes with n_p > 131072 are rejected with DGW_EINVAL. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture. Every call shares the one array and clears what must start at zero; calls
- * whose work overlaps on the GPU (other streams, other host threads) race on it and must be
- * serialised by the caller. info->ms is host wall time. Synchronises `stream`. */
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it for later calls; make
+ * that first call before any stream capture, and do not reset the device (cudaDeviceReset)
+ * between calls, which would leave the kept address stale. Every call shares the one array and
+ * clears what must start at zero; calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. The solve reads the residual norm
+ * back every iteration, so it synchronises `stream` once per iteration. info->ms is host wall
+ * time. */
 dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t mesh, const double *b, double *p, double rtol, int max_iter,
                                              dgw_solve_info *info, void *stream);
 

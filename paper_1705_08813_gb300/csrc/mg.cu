@@ -4,7 +4,10 @@
 // direction whose cell count is even (coarse vertex rows are every other fine row, so the
 // meshes nest), the same degree k on every level, re-discretised SIPG level operators,
 // Chebyshev smoothing with the inverse diagonal, DG embedding (prolongation) and its transpose
-// (restriction), and a fixed number of device-side Jacobi-PCG steps on the coarsest level.
+// (restriction). The coarsest level is solved with a dense (A + c 1 1^T)^-1 computed on the device,
+// either at degree k (when its n_p <= 2400) or after one more level with Q_1 on the same cells
+// (when 8 x cells <= 2400); only a hierarchy too large for both falls back to a fixed number of
+// device-side Jacobi-PCG steps there.
 // Mode 1 runs the whole V-cycle in FP32 (operators, smoothers, transfers) on a residual scaled
 // by its RMS value; mode 0 runs it in FP64.
 #include <algorithm>

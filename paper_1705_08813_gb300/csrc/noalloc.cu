@@ -1,12 +1,13 @@
 // Pressure solve for callers that must not allocate device memory.
 //
 // dgw_pressure_solve keeps a per-mesh workspace that it allocates on first use. Some callers
-// cannot let a library call cudaMalloc at solve time: code that records its work into a CUDA graph
-// (allocation is not allowed while a stream is being captured), code whose device memory is owned
-// by a framework's caching allocator or a fixed budget planned at start-up, and latency-sensitive
-// loops where cudaMalloc/cudaFree would implicitly synchronise the device and stall other streams.
-// For them this file offers a Jacobi-preconditioned CG solve whose scratch vectors live in one
-// file-scope device array of fixed size; the entry point itself allocates nothing.
+// cannot let a library call cudaMalloc at solve time: code whose device memory is owned by a
+// framework's caching allocator or by a fixed budget planned at start-up (a library allocation
+// outside that pool can fail or push the pool out of memory), and latency-sensitive loops where
+// cudaMalloc/cudaFree would implicitly synchronise the device and stall other streams. For them
+// this file offers a Jacobi-preconditioned CG solve whose scratch vectors live in one file-scope
+// device array of fixed size; the entry point itself allocates nothing. It reads one residual
+// norm back to the host per iteration, so it synchronises the caller's stream every iteration.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -22,6 +23,7 @@ namespace {
 constexpr long kNoAllocMaxNp = 131072;   // largest pressure vector (n_p) the scratch holds
 constexpr int kNoAllocRed = 304;         // partial sums of the two-stage reductions
 constexpr int kNoAllocMaxDevices = 64;
+static_assert(kNoAllocRed >= RED_BLOCKS, "reduce_to writes RED_BLOCKS partial sums into the partial area");
 
 // b (projected rhs), r, z, d, q vectors, reduction partials and the scalar slots.
 constexpr size_t kScratchDoubles = 5 * (size_t)kNoAllocMaxNp + kNoAllocRed + SC_COUNT;
@@ -31,7 +33,8 @@ std::mutex g_mutex;
 double *g_scratch_addr[kNoAllocMaxDevices] = {nullptr};
 
 // Device address of the scratch array for the current device (looked up once per device; the
-// host-side name of the array is only a stand-in and must never be passed to a kernel).
+// host-side name of the array is only a stand-in and must never be passed to a kernel). The cached
+// address belongs to the device's current context: a cudaDeviceReset between calls invalidates it.
 cudaError_t scratch_address(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -82,8 +85,11 @@ inline int na_grid(long n) {
   return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
 }
 
+// Reads one scalar slot back (synchronising s). A launch error left by the work queued before it
+// is reported here, so each iteration's launches are checked once per read.
 double read_scalar(const double *sc, int slot, cudaStream_t s, cudaError_t &e) {
   double v = 0.0;
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&v, sc + slot, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return v;
@@ -128,42 +134,49 @@ extern "C" dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t M, const doub
     info->ms = 0.0f;
     return DGW_OK;
   }
-  auto precondition = [&]() {
+  // z = D^-1 r projected to zero mean, rz_new = r.z; then the new search direction d
+  auto precondition_and_direction = [&](int first) -> cudaError_t {
     note_launch();
     na_jacobi<<<G, 256, 0, s>>>(r, M->diag64, z, n);
-    project_mean(z, z, n, partial, sc, SC_TMP, s);
-    reduce_to(r, z, n, partial, sc, SC_RZNEW, s);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) err = project_mean(z, z, n, partial, sc, SC_TMP, s);
+    if (err == cudaSuccess) err = reduce_to(r, z, n, partial, sc, SC_RZNEW, s);
+    if (err != cudaSuccess) return err;
+    note_launches(2);
+    na_direction<<<G, 256, 0, s>>>(d, z, n, sc, first);
+    na_shift<<<1, 32, 0, s>>>(sc);
+    return cudaGetLastError();
   };
-  precondition();
-  note_launches(2);
-  na_direction<<<G, 256, 0, s>>>(d, z, n, sc, 1);
-  na_shift<<<1, 32, 0, s>>>(sc);
+  e = precondition_and_direction(1);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc: preconditioner");
   int it = 0;
   dgw_status st = DGW_OK;
   for (it = 1; it <= max_iter; ++it) {
     e = launch_laplace<double>(M->v64, d, q, s);
-    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc: operator");
-    reduce_to(d, q, n, partial, sc, SC_DQ, s);
-    note_launch();
-    na_update<<<G, 256, 0, s>>>(p, r, d, q, n, sc);
-    reduce_to(r, r, n, partial, sc, SC_RR, s);
+    if (e == cudaSuccess) e = reduce_to(d, q, n, partial, sc, SC_DQ, s);
+    if (e == cudaSuccess) {
+      note_launch();
+      na_update<<<G, 256, 0, s>>>(p, r, d, q, n, sc);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = reduce_to(r, r, n, partial, sc, SC_RR, s);
     const double rel = std::sqrt(std::max(read_scalar(sc, SC_RR, s, e), 0.0)) / bnorm;
-    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc");
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc: iteration");
     if (rel <= rtol) break;
-    precondition();
-    note_launches(2);
-    na_direction<<<G, 256, 0, s>>>(d, z, n, sc, 0);
-    na_shift<<<1, 32, 0, s>>>(sc);
+    e = precondition_and_direction(0);
+    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc: preconditioner");
   }
   if (it > max_iter) { it = max_iter; st = DGW_ENOTCONV; }
   // zero-mean solution and its true FP64 residual
-  project_mean(p, p, n, partial, sc, SC_TMP, s);
-  launch_laplace<double>(M->v64, p, q, s);
-  note_launch();
-  na_sub<<<G, 256, 0, s>>>(r, b, q, n);
-  reduce_to(r, r, n, partial, sc, SC_RR, s);
+  e = project_mean(p, p, n, partial, sc, SC_TMP, s);
+  if (e == cudaSuccess) e = launch_laplace<double>(M->v64, p, q, s);
+  if (e == cudaSuccess) {
+    note_launch();
+    na_sub<<<G, 256, 0, s>>>(r, b, q, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = reduce_to(r, r, n, partial, sc, SC_RR, s);
   const double rr = read_scalar(sc, SC_RR, s, e);
-  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc");
   info->iterations = it;
   info->rel_residual = std::sqrt(std::max(rr, 0.0)) / bnorm;

@@ -12,7 +12,6 @@
 
 namespace dgw {
 
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
 
 // Block-level sum for a fixed-order reduction.

@@ -8,6 +8,9 @@ namespace dgw {
 // device scalar slots of the CG recurrences
 enum { SC_RZ = 0, SC_RZNEW, SC_DQ, SC_RR, SC_BB, SC_TMP, SC_RZOLD, SC_RN, SC_COUNT = 8 };
 
+// blocks of the first stage of the two-stage reductions (reduce_to writes this many partial sums)
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+
 struct MGLevel;
 
 }  // namespace dgw

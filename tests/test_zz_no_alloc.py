@@ -1,8 +1,9 @@
-"""The allocation-free pressure solve (for callers that cannot let the library allocate device
-memory at solve time, e.g. while recording a CUDA graph or under a framework-owned memory pool)
-gives the same answer as the regular Jacobi-preconditioned solve. Called through the C ABI,
-twice in a row, so the second call runs on scratch memory that still holds the first call's data.
-This file sorts last so that a failure here leaves every other test already run."""
+"""The allocation-free pressure solve, for callers that cannot let the library allocate device
+memory at solve time (memory owned by a framework's caching allocator or a fixed budget, or loops
+where cudaMalloc/cudaFree would synchronise the device), gives the same answer as the regular
+Jacobi-preconditioned solve. Called through the C ABI, twice in a row, so the second call runs on
+scratch memory that still holds the first call's data; and once on a mesh close to the scratch
+limit. This file sorts last so that a failure here leaves every other test already run."""
 import ctypes
 
 import numpy as np
@@ -12,6 +13,8 @@ from paper_1705_08813_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+MAX_NP = 131072   # scratch limit of the allocation-free solve
 
 
 @pytest.fixture(scope="module")
@@ -31,18 +34,17 @@ def _noalloc(dgw, mesh, b, p, rtol, max_iter):
     return st, info
 
 
-def test_noalloc_solve_matches_regular_solve_twice(dgw):
-    w = I.WORKLOADS["channel_q2_8x8x8"]
+def _check_against_regular(dgw, w, seed, calls):
     mesh = dgw.mesh_for(w)
-    assert mesh.n_p <= 131072
-    b = torch.tensor(I.pressure_rhs(mesh.n_p, 7), device="cuda")
+    assert mesh.n_p <= MAX_NP
+    b = torch.tensor(I.pressure_rhs(mesh.n_p, seed), device="cuda")
     p_ref = torch.zeros_like(b)
-    ref = mesh.pressure_solve(b, p_ref, rtol=1e-10, max_iter=5000, mode=2)
+    ref = mesh.pressure_solve(b, p_ref, rtol=1e-10, max_iter=20000, mode=2)
     assert ref["rel_residual"] <= 1e-10
     pr = p_ref.cpu().numpy()
-    for call in range(2):
+    for call in range(calls):
         p = torch.full_like(b, float(call + 1))      # stale output contents must not matter
-        st, info = _noalloc(dgw, mesh, b, p, 1e-10, 5000)
+        st, info = _noalloc(dgw, mesh, b, p, 1e-10, 20000)
         assert st == 0, dgw._lib.dgw_last_error()
         assert info.rel_residual <= 1e-10
         ph = p.cpu().numpy()
@@ -50,11 +52,18 @@ def test_noalloc_solve_matches_regular_solve_twice(dgw):
         assert np.linalg.norm(ph - pr) / np.linalg.norm(pr) < 1e-6, call
 
 
+def test_noalloc_solve_matches_regular_solve_twice(dgw):
+    _check_against_regular(dgw, I.WORKLOADS["channel_q2_8x8x8"], 7, 2)
+
+
+def test_noalloc_solve_near_the_scratch_limit(dgw):
+    # 16 x 16 x 16 Q2: 110592 pressure DoFs, 84% of the scratch vectors in use
+    _check_against_regular(dgw, I.Workload("big", 16, 16, 16, 2, 180.0, 1.0 / 3250.0, seed=3), 11, 1)
+
+
 def test_noalloc_rejects_meshes_beyond_its_scratch(dgw):
-    w = I.Workload("big", 16, 16, 16, 2, 180.0, 1.0 / 3250.0, seed=3)    # 110592 DoFs fit
-    mesh = dgw.mesh_for(w)
-    assert mesh.n_p <= 131072
     big = dgw.mesh_for(I.Workload("big2", 16, 16, 12, 3, 180.0, 1.0 / 3250.0, seed=3))   # 196608 DoFs
+    assert big.n_p > MAX_NP
     b = torch.zeros(big.n_p, dtype=torch.float64, device="cuda")
     p = torch.zeros_like(b)
     st, _ = _noalloc(dgw, big, b, p, 1e-10, 10)
