@@ -297,6 +297,51 @@ def test_convective_conservation_equals_wall_flux():
     assert abs(sums[0]) < 1e-12 and abs(sums[2]) < 1e-12
 
 
+@pytest.mark.parametrize("alpha,beta", [(0.3, 0.7), (0.8, 0.25)])
+def test_convective_interior_flux_with_sign_changing_normal_velocity(alpha, beta):
+    """Two cells along x (periodic, so both x-faces are interior), constant u = alpha e_x in cell 0
+    and -beta e_x in cell 1: on every x-face u^-.n and u^+.n have opposite signs. The local
+    Lax-Friedrichs flux of Sec. 4.2, F = 1/2 (u^- (u^-.n) + u^+ (u^+.n)) + Lambda/2 (u^- - u^+) with
+    Lambda = max(2|u^-.n|, 2|u^+.n|), is evaluated here by hand; y- and z-faces carry no flux
+    (u.n = 0 on both sides). With Gauss-Lobatto nodes the integral of a nodal basis function over a
+    face is the product of the 1-D Lobatto weights, so every output has a closed form:
+    y_{c,x,(a,b,c)} = W_bc [delta_{a,k} (F_R - u_c^2) + delta_{a,0} (F_L + u_c^2)], u_c the cell's
+    x-velocity, F_R, F_L the x-fluxes through its right and left face (outward normals)."""
+    k = 2
+    m = O.Mesh(2, 1, 1, k, n_layers=0)
+    n = k + 1
+    u = np.zeros(m.n_u)
+    std = u[: 3 * m.n_p].reshape(m.nc, 3, n ** 3)
+    uc = [alpha, -beta]
+    std[0, 0, :] = uc[0]
+    std[1, 0, :] = uc[1]
+    y = m.convective(u)[: 3 * m.n_p].reshape(m.nc, 3, n, n, n)   # [cell][comp][z][y][x]
+
+    def flux(um, up, nrm):
+        unm, unp = um * nrm, up * nrm
+        lam = max(2 * abs(unm), 2 * abs(unp))
+        return 0.5 * (um * unm + up * unp) + 0.5 * lam * (um - up)
+
+    # independent Lobatto weights on [0, 1]: integrals of the Lagrange polynomials on the nodes
+    z = np.concatenate(([-1.0], np.polynomial.legendre.Legendre.basis(k).deriv().roots(), [1.0]))
+    wl = 2.0 / (k * (k + 1) * np.polynomial.legendre.legval(z, [0] * k + [1]) ** 2) / 2.0
+    W = np.outer(wl, wl) * (2.0 * math.pi)          # [z][y] weights times the face area Ly Lz
+    for c in range(2):
+        o = 1 - c
+        FR = flux(uc[c], uc[o], 1.0)                   # right face: n = +e_x
+        FL = flux(uc[c], uc[o], -1.0)                  # left face: n = -e_x
+        ref = np.zeros((n, n, n))
+        ref[:, :, k] = W * (FR - uc[c] ** 2)
+        ref[:, :, 0] = W * (FL + uc[c] ** 2)
+        assert np.abs(y[c, 0] - ref).max() < 1e-13 * np.abs(ref).max()
+        assert np.abs(y[c, 1:]).max() < 1e-14
+        # the cell's total: the hand value 2 max(alpha, beta) (alpha + beta) L_y L_z with the sign
+        # of its own velocity (a min in Lambda or a dropped 1/2 changes it)
+        tot = y[c, 0].sum()
+        expect = (1 if c == 0 else -1) * 2 * max(alpha, beta) * (alpha + beta) * 2 * math.pi
+        assert abs(tot - expect) < 1e-13 * abs(expect)
+
+
 # ---------------------------------------------------------------------------------------------
 # Viscous multiscale term, eq. (viscous_multiscale)
 # ---------------------------------------------------------------------------------------------
@@ -362,6 +407,193 @@ def test_viscous_symmetric_part_is_volume_plus_penalty_and_psd():
     assert np.abs(K[np.ix_(rows, np.arange(3 * n3, 6 * n3))]).max() > 1e-6 * np.abs(S).max()
 
 
+class _BoxFields:
+    """Independent evaluation (NumPy, not the oracle's tabulation) of ubar, u~ and their physical
+    gradients at reference points of the box cells of a channel mesh with one enriched layer per
+    wall and a constant wall shear stress tau_w: Lagrange polynomials on Gauss-Lobatto nodes for
+    ubar (Sec. 4.2), u~ = psi(y+) sum_B N_B u~_B with y_h the distance to the wall and
+    y+ = y_h sqrt(tau_w) / nu, grad u~ = sum_B u~_B (psi grad N_B + N_B psi' grad y+) (Sec. 3.1-3.2).
+    psi and psi' come from the wall-law routine pinned on its own (Spalding)."""
+
+    def __init__(self, m, nx, ny, nz, k, nu, tau_w):
+        self.m, self.nx, self.ny, self.nz, self.k, self.nu, self.tau_w = m, nx, ny, nz, k, nu, tau_w
+        self.n = k + 1
+        z = np.concatenate(([-1.0], np.polynomial.legendre.Legendre.basis(k).deriv().roots(), [1.0]))
+        self.gll = 0.5 * (np.sort(z) + 1.0)
+        X = m.node_coords().reshape(m.nc, -1, 3)
+        self.lo, self.hi = X.min(axis=1), X.max(axis=1)
+
+    def lagrange(self, s):
+        """values and derivatives of the n Lagrange polynomials on the Lobatto nodes at s"""
+        x, n = self.gll, self.n
+        v, d = np.ones(n), np.zeros(n)
+        for a in range(n):
+            for b in range(n):
+                if b == a:
+                    continue
+                v[a] *= (s - x[b]) / (x[a] - x[b])
+            for c in range(n):
+                if c == a:
+                    continue
+                t = 1.0 / (x[a] - x[c])
+                for b in range(n):
+                    if b != a and b != c:
+                        t *= (s - x[b]) / (x[a] - x[b])
+                d[a] += t
+        return v, d
+
+    def enr_index(self, c):
+        i, j, kz = c % self.nx, (c // self.nx) % self.ny, c // (self.nx * self.ny)
+        if j == 0:
+            return i + self.nx * kz
+        if j == self.ny - 1:
+            return self.nx * self.nz + i + self.nx * kz
+        return -1
+
+    def eval(self, u, c, xi):
+        """(ubar, grad ubar, u~, grad u~) at reference point xi of cell c; G[a][e] = d u_a / d x_e"""
+        m, n = self.m, self.n
+        h = self.hi[c] - self.lo[c]
+        L = [self.lagrange(xi[d]) for d in range(3)]
+        U = u[: 3 * m.n_p].reshape(m.nc, 3, n, n, n)[c]           # [comp][z][y][x]
+        ub = np.einsum("azyx,z,y,x->a", U, L[2][0], L[1][0], L[0][0])
+        gb = np.stack([np.einsum("azyx,z,y,x->a", U, L[2][0], L[1][0], L[0][1]) / h[0],
+                       np.einsum("azyx,z,y,x->a", U, L[2][0], L[1][1], L[0][0]) / h[1],
+                       np.einsum("azyx,z,y,x->a", U, L[2][1], L[1][0], L[0][0]) / h[2]], axis=1)
+        ut, gt = np.zeros(3), np.zeros((3, 3))
+        e = self.enr_index(c)
+        if e >= 0:
+            y = self.lo[c][1] + xi[1] * h[1]
+            bottom = (c // self.nx) % self.ny == 0
+            yh = y + 1.0 if bottom else 1.0 - y
+            st = math.sqrt(self.tau_w)
+            yp = yh * st / self.nu
+            gyp = np.array([0.0, (1.0 if bottom else -1.0) * st / self.nu, 0.0])
+            psi, dpsi = O.psi_spalding(yp)
+            E = u[3 * m.n_p:].reshape(-1, 3, 8)[e]
+            for v in range(8):
+                f = [xi[d] if (v >> d) & 1 else 1.0 - xi[d] for d in range(3)]
+                df = [1.0 if (v >> d) & 1 else -1.0 for d in range(3)]
+                N = f[0] * f[1] * f[2]
+                gN = np.array([df[0] * f[1] * f[2] / h[0], f[0] * df[1] * f[2] / h[1], f[0] * f[1] * df[2] / h[2]])
+                ut += psi * N * E[:, v]
+                gt += np.outer(E[:, v], psi * gN + N * dpsi * gyp)
+        return ub, gb, ut, gt
+
+
+def _eps(G):
+    return 0.5 * (G + G.T)
+
+
+def test_viscous_energy_identity_as_a_value():
+    """Energy identity of eq. (viscous_multiscale) (Sec. 4.2-4.3, P7): testing -F^nu with u itself,
+    every consistency term cancels against the adjoint term of the other side (also on the
+    mirrored walls), so
+      u^T (-F^nu) u = sum_points dV [2 nu eps(ubar):eps(ubar) + 2 nuhat eps(ubar):eps(u~)
+                                     + 2 (nu + nu_t) eps(u~):eps(u~)]
+                      + sum_interior faces int tau_F nu |u^- - u^+|^2 + sum_walls int 2 tau_F nu |u^-|^2,
+    nuhat = min(nu + nu_t, 2 sqrt(nu (nu + nu_t))) (eq. minvt), tau_F = max(tau^-, tau^+) inside and
+    10 tau on walls. The right side is summed here from the independent point evaluation, with the
+    same quadrature (k+1 Gauss points, q_w wall-normal in and next to enriched cells), nu_t from
+    the frozen field, and tau from its definition (k+1)^2 A/V. The clip is active (nu_t > 3 nu) and
+    the ubar/u~ cross term is large, so exchanging nuhat and nu + nu_t in the two enriched volume
+    terms changes the value by far more than the tolerance (asserted below)."""
+    nx, ny, nz, k, qw = 2, 3, 2, 2, 8
+    nu, tau_w = 1e-4, 1e-2
+    m = O.Mesh(nx, ny, nz, k, n_layers=1, nu=nu, tau_w=tau_w, gamma=1.8, q_wall=qw)
+    uf = np.zeros(m.n_u)
+    uf[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 0.1
+    uf[3 * m.n_p:] += 0.02 * I.uniform(5, m.n_e * 24, -1, 1)
+    u = I.uniform(6, m.n_u, -1, 1)
+    u[3 * m.n_p:] *= 0.5
+    val = u @ m.viscous(uf, u)
+    F = _BoxFields(m, nx, ny, nz, k, nu, tau_w)
+    n = k + 1
+    # penalty parameter from its definition: (k+1)^2 A(dK)/V(K), interior faces weighted 1/2
+    tau = np.zeros(m.nc)
+    for c in range(m.nc):
+        h = F.hi[c] - F.lo[c]
+        j = (c // nx) % ny
+        A = 0.0
+        for d in range(3):
+            t = [e for e in range(3) if e != d]
+            for side in (0, 1):
+                wall = d == 1 and ((side == 0 and j == 0) or (side == 1 and j == ny - 1))
+                A += (1.0 if wall else 0.5) * h[t[0]] * h[t[1]]
+        tau[c] = n * n * A / np.prod(h)
+    assert np.abs(tau - m.cell_tau()).max() < 1e-12 * tau.max()
+
+    def gauss(q):
+        x, w = np.polynomial.legendre.leggauss(q)
+        return 0.5 * (x + 1), 0.5 * w
+
+    vol = np.zeros(3)      # the three volume parts: nu eps(ub):eps(ub), nuhat cross, (nu+nut) eps(ut):eps(ut)
+    swapped = 0.0
+    for c in range(m.nc):
+        h = F.hi[c] - F.lo[c]
+        e = F.enr_index(c)
+        nq = [n, qw if e >= 0 else n, n]
+        (x0, w0), (x1, w1), (x2, w2) = gauss(nq[0]), gauss(nq[1]), gauss(nq[2])
+        nut = m.nut_cell(uf, e).reshape(nq[2], nq[1], nq[0]) if e >= 0 else None
+        for i2 in range(nq[2]):
+            for i1 in range(nq[1]):
+                for i0 in range(nq[0]):
+                    dV = np.prod(h) * w0[i0] * w1[i1] * w2[i2]
+                    ub, gb, ut, gt = F.eval(u, c, (x0[i0], x1[i1], x2[i2]))
+                    eb, et = _eps(gb), _eps(gt)
+                    vol[0] += dV * 2 * nu * np.sum(eb * eb)
+                    if e >= 0:
+                        nt = nut[i2, i1, i0]
+                        nuh = min(nu + nt, 2 * math.sqrt(nu * (nu + nt)))
+                        vol[1] += dV * 2 * nuh * np.sum(eb * et)
+                        vol[2] += dV * 2 * (nu + nt) * np.sum(et * et)
+                        swapped += dV * (2 * (nu + nt) * np.sum(eb * et) + 2 * nuh * np.sum(et * et))
+    pen = 0.0
+    for c in range(m.nc):
+        i, j, kz = c % nx, (c // nx) % ny, c // (nx * ny)
+        h = F.hi[c] - F.lo[c]
+        for d in range(3):
+            for side in (0, 1):
+                # every interior face once (from its lower cell), both walls
+                if d == 1:
+                    jn = j + (1 if side else -1)
+                    if 0 <= jn < ny and side == 0:
+                        continue
+                    nb = None if not (0 <= jn < ny) else i + nx * (jn + ny * kz)
+                elif side == 0:
+                    continue
+                else:
+                    nb = ((i + 1) % nx + nx * (j + ny * kz)) if d == 0 else (i + nx * (j + ny * ((kz + 1) % nz)))
+                t1 = 1 if d == 0 else 0
+                t2 = 1 if d == 2 else 2
+                enr = F.enr_index(c) >= 0 or (nb is not None and F.enr_index(nb) >= 0)
+                q1 = qw if (t1 == 1 and enr) else n
+                q2 = qw if (t2 == 1 and enr) else n
+                (a1, b1), (a2, b2) = gauss(q1), gauss(q2)
+                for p2 in range(q2):
+                    for p1 in range(q1):
+                        xi = [0.0, 0.0, 0.0]
+                        xi[d] = float(side)
+                        xi[t1], xi[t2] = a1[p1], a2[p2]
+                        dA = h[t1] * h[t2] * b1[p1] * b2[p2]
+                        ub, _, ut, _ = F.eval(u, c, xi)
+                        um = ub + ut
+                        if nb is None:
+                            pen += dA * 2 * 10 * tau[c] * nu * um @ um
+                        else:
+                            xo = list(xi)
+                            xo[d] = 1.0 - side
+                            ubo, _, uto, _ = F.eval(u, nb, xo)
+                            jmp = um - ubo - uto
+                            pen += dA * max(tau[c], tau[nb]) * nu * jmp @ jmp
+    ref = vol.sum() + pen
+    assert abs(val - ref) < 1e-12 * abs(ref), (val, ref)
+    # the identity distinguishes the two enriched volume coefficients
+    alt = vol[0] + swapped + pen
+    assert abs(alt - ref) > 1e-6 * abs(ref)
+    assert max(m.nut_cell(uf, e).max() for e in range(m.n_e)) > 3 * nu
+
+
 # ---------------------------------------------------------------------------------------------
 # Enrichment and eddy viscosity (Sec. 3, Sec. 2.2)
 # ---------------------------------------------------------------------------------------------
@@ -398,6 +630,35 @@ def test_eddy_viscosity_log_layer_limit():
     v = nut.reshape(nq, 8, nq)[0, 0, 0]
     assert abs(v / (0.41 * y0) - 1.0) < 0.05
     assert np.all(nut >= 0)
+
+
+def test_eddy_viscosity_des_limiter_and_wall_branches():
+    """y_DES = (y^-6 + (C_DES h)^-6)^(-1/6) (eq. ydes, h = wall-normal cell width / (k+1)) tends
+    to C_DES h far from the wall (y >> C_DES h: the mixing length saturates at the grid scale) and
+    to y near it. With the enriched log-law field u~ = u_tau psi(y+) e_x the strain is closed-form,
+    sqrt(2 eps:eps) = u_tau^2 psi'(y+) / nu, so nu_t = (kappa y_DES (1 - exp(-y+/26)))^2 u_tau^2
+    psi' / nu (eq. mix, lmix) must approach both limits at the points of the wall cell."""
+    k, nu, tau_w = 4, 1e-5, 1.0
+    m = O.Mesh(1, 2, 1, k, gamma=1e-3, nu=nu, tau_w=tau_w, n_layers=1)
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 1.0     # u_tau = 1
+    nut = m.nut_cell(u, 0).reshape(k + 1, 8, k + 1)[0, :, 0]   # along the wall normal
+    gy, _ = O.gauss(8)
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    dy = X[0, :, 1].max() - X[0, :, 1].min()
+    ch = 0.85 * dy / (k + 1)
+    far = near = 0
+    for y, v in zip(gy * dy, nut):
+        yp = y * math.sqrt(tau_w) / nu
+        psi, dpsi = O.psi_spalding(yp)
+        core = (0.41 * (1 - math.exp(-yp / 26.0))) ** 2 * dpsi / nu
+        if y >= 4 * ch:
+            assert abs(v / (core * ch ** 2) - 1) < 2e-4, (y, v)      # (1/4)^6 / 3 away from the limit
+            far += 1
+        if y <= 0.25 * ch:
+            assert abs(v / (core * y ** 2) - 1) < 2e-4, (y, v)
+            near += 1
+    assert far >= 2 and near >= 1
 
 
 def test_oracle_solve_reaches_tolerance_zero_mean():
