@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the DG wall-model hot path on one GB300 (or N replicas under torchrun).
 
-One step = one pass of the whole hot path over the workload: eddy-viscosity update of the
-enriched cells, FP64 applies of the SIPG Laplacian, the velocity divergence, the convective and
-the viscous operator, and one pressure Poisson solve to a 1e-10 relative residual (mixed precision:
-FP64 iterative refinement around FP32 CG with the FP32 multigrid preconditioner) whose right-hand
-side is the step's divergence.
+One step = one pass of the FP64 operator-apply path over the workload (the Q4 32x24x24 channel
+by default, plain FP64): the eddy-viscosity update of the enriched cells, then FP64 applies of the
+SIPG Laplacian, the velocity divergence, the convective and the viscous operator.
 
-value = operator DoF applications of the step (output DoFs of every operator apply, including the
-applies inside the solve) / step time, in GDoF/s. Per-operator GDoF/s and FP64-vs-mixed solves/s
-are reported beside it.
+value = output DoFs of the step's four FP64 applies (n_p + n_p + n_u + n_u) / step time, in GDoF/s
+(every unit counted is an FP64 operator application; nothing of the solves is in it).
+
+The same run then times, each in its own loop, the pressure solves to a 1e-10 relative residual in
+plain FP64 (FP64 CG + FP64 multigrid) and mixed precision (FP64 refinement around FP32 CG with the
+FP32 multigrid), on this workload (rhs = the step's divergence) and on the Q3 64x32x32 channel
+(seeded zero-mean uniform rhs), reported as solves/s under "solves"; and the FP32 SIPG Laplacian,
+the operator the FP32 multigrid applies most, with its HBM roofline under "fp32_laplace".
 
 --impl reference times the CPU oracle (the plain FP64 implementation the tests check against) on a
 bounded sample of the same workload: the four operator applies on a subset of cells.
@@ -209,6 +212,60 @@ def laplace_flops_per_cell(k, curved=False):
     return 2 * (7 * n ** 4 + 30 * n ** 3)
 
 
+def vector_flops_per_cell(op, k):
+    """Floating-point operations (2 per multiply-add) of one standard box cell of the divergence,
+    convective and viscous operators, counted for sum factorisation at the operator's own Gauss
+    points (Sec. 4.4: k+1 per direction, floor(3k/2)+1 for the convective term), n = k + 1 nodes:
+      values of one scalar at the points    F = q n^3 + q^2 n^2 + q^3 n
+      gradients of one scalar               G = 2 q n^3 + 3 q^2 n^2 + 3 q^3 n
+      integration against grad phi          B = 2 q n^3 + 3 q^2 n^2 + 3 q^3 n
+    faces (six per cell, each side's own integrals): traces interpolated from the face layer,
+    normal derivatives n^3 per component, flux at q^2 points, integration back.
+      divergence  3F + B + 3 q^3 (point scaling)  + 6 [2 (q n^2 + q^2 n) + q^2 + (q^2 n + q n^2)]
+      convective  3F + 3B + 18 q^3 (u x u)        + 6 [6 (q n^2 + q^2 n) + 30 q^2 + 3 (q^2 n + q n^2)]
+      viscous     3G + 3B + 30 q^3 (strain)       + 6 [6 (n^3 + 3 q n^2 + 4 q^2 n) + 60 q^2
+                                                        + 3 (3 q^2 n + 2 q n^2 + n^3)]"""
+    n = k + 1
+    q = (3 * k) // 2 + 1 if op == "convective" else n
+    F = q * n ** 3 + q * q * n * n + q ** 3 * n
+    G = 2 * q * n ** 3 + 3 * q * q * n * n + 3 * q ** 3 * n
+    B = 2 * q * n ** 3 + 3 * q * q * n * n + 3 * q ** 3 * n
+    if op == "divergence":
+        fma = 3 * F + B + 6 * (2 * (q * n * n + q * q * n) + (q * q * n + q * n * n))
+        return 2 * fma + 3 * q ** 3 + 6 * q * q
+    if op == "convective":
+        fma = 3 * F + 3 * B + 6 * (6 * (q * n * n + q * q * n) + 3 * (q * q * n + q * n * n))
+        return 2 * fma + 18 * q ** 3 + 6 * 30 * q * q
+    fma = 3 * G + 3 * B + 6 * (6 * (n ** 3 + 3 * q * n * n + 4 * q * q * n) + 3 * (3 * q * q * n + 2 * q * n * n + n ** 3))
+    return 2 * fma + 30 * q ** 3 + 6 * 60 * q * q
+
+
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz
+
+
+def _time_solves(m, b, p, modes, reps, flush):
+    """solves/s of dgw_pressure_solve per mode (median host time of `reps` solves after one
+    untimed solve that builds the hierarchy; L2 flushed before each)."""
+    import torch
+    out = {}
+    for name, mode in modes:
+        m.pressure_solve(b, p, rtol=1e-10, max_iter=500, mode=mode)
+        ts, its, res = [], [], []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = m.pressure_solve(b, p, rtol=1e-10, max_iter=500, mode=mode)
+            ts.append(time.perf_counter() - t0)
+            its.append(info["iterations"])
+            res.append(info["rel_residual"])
+        out[name] = {"solves_per_s": 1.0 / statistics.median(ts), "ms": 1e3 * statistics.median(ts),
+                     "iterations": statistics.mean(its), "rel_residual": max(res)}
+    out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -229,20 +286,15 @@ def run_gpu(args):
     ud = u_host.to(dev)
     pd = p_host.to(dev)
     y_lap = torch.empty(m.n_p, dtype=torch.float64, device=dev)
-    p32 = pd.float()
-    y_lap32 = torch.empty(m.n_p, dtype=torch.float32, device=dev)
     b_div = torch.empty(m.n_p, dtype=torch.float64, device=dev)
     y_conv = torch.empty(m.n_u, dtype=torch.float64, device=dev)
     y_visc = torch.empty(m.n_u, dtype=torch.float64, device=dev)
-    p_sol = torch.zeros(m.n_p, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
     stream = torch.cuda.current_stream()
-    ops = ["eddy_viscosity", "laplace", "laplace32", "divergence", "convective", "viscous", "solve"]
+    ops = ["eddy_viscosity", "laplace", "divergence", "convective", "viscous"]
     ev = {o: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for o in ops}
 
     def step(timed):
-        times = {}
-        solve = None
         for o in ops:
             if timed:
                 ev[o][0].record(stream)
@@ -250,21 +302,15 @@ def run_gpu(args):
                 m.update_eddy_viscosity(ud)
             elif o == "laplace":
                 m.laplace(pd, y_lap)
-            elif o == "laplace32":
-                m.laplace(p32, y_lap32)
             elif o == "divergence":
                 m.divergence(ud, b_div)
             elif o == "convective":
                 m.convective(ud, y_conv)
-            elif o == "viscous":
-                m.viscous(ud, y_visc)
             else:
-                solve = m.pressure_solve(b_div, p_sol, rtol=1e-10, max_iter=500, mode=args.solve_mode)
+                m.viscous(ud, y_visc)
             if timed:
                 ev[o][1].record(stream)
-        return solve
 
-    # warm-up (includes multigrid setup)
     for _ in range(max(args.warmup, 1)):
         step(False)
     torch.cuda.synchronize()
@@ -274,7 +320,6 @@ def run_gpu(args):
     clocks.start()
     launches0, _ = dgw.counters()
     step_ms, op_ms = [], {o: [] for o in ops}
-    solves = []
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -282,13 +327,12 @@ def run_gpu(args):
     for _ in range(args.steps):
         flush.zero_()                       # evict the previous step's data from L2 (not timed)
         torch.cuda.nvtx.range_push("dgw_step")
-        s = step(True)
+        step(True)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         for o in ops:
             op_ms[o].append(ev[o][0].elapsed_time(ev[o][1]))
         step_ms.append(ev[ops[0]][0].elapsed_time(ev[ops[-1]][1]))
-        solves.append(s)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -296,76 +340,87 @@ def run_gpu(args):
     launches1, _ = dgw.counters()
     clk = clocks.stop()
     ms_max = replica_time(statistics.mean(step_ms), world, dev)
-    # DoF applications of one step
-    dofs_ops = {"laplace": m.n_p, "laplace32": m.n_p, "divergence": m.n_p, "convective": m.n_u, "viscous": m.n_u}
-    solve_dofs = statistics.mean(s["dof_applies"] for s in solves)
-    dofs_step = sum(dofs_ops.values()) + solve_dofs
+    dofs_ops = {"laplace": m.n_p, "divergence": m.n_p, "convective": m.n_u, "viscous": m.n_u}
+    dofs_step = float(sum(dofs_ops.values()))
     value = weak_value(dofs_step, world, ms_max)
+    nc = w.nx * w.ny * w.nz
+    curved = w.geometry == 1
     per_op = {o: {"ms": statistics.mean(op_ms[o])} for o in ops}
     for o, d in dofs_ops.items():
         per_op[o]["gdofs"] = d / (per_op[o]["ms"] * 1e-3) / 1e9
-    per_op["solve"]["iterations"] = statistics.mean(s["iterations"] for s in solves)
-    per_op["solve"]["rel_residual"] = max(s["rel_residual"] for s in solves)
+        fl = laplace_flops_per_cell(w.k, curved) if o == "laplace" else vector_flops_per_cell(o, w.k)
+        per_op[o]["flops_per_cell"] = fl
+        per_op[o]["fp64_tflops"] = nc * fl / (per_op[o]["ms"] * 1e-3) / 1e12
+        per_op[o]["fp64_frac"] = per_op[o]["fp64_tflops"] / FP64_PEAK_TFLOPS
+        nbytes = 8.0 * (m.n_p + m.n_p if o == "laplace" else (m.n_u + m.n_p if o == "divergence" else 2 * m.n_u))
+        per_op[o]["hbm_gbs"] = nbytes / (per_op[o]["ms"] * 1e-3) / 1e9
 
-    # solves/s: FP64 (FP64 CG + FP64 multigrid) vs mixed (FP64 CG + FP32 multigrid)
-    solve_rates = {}
-    for name, mode in (("fp64", 0), ("mixed", 1)):
-        m.pressure_solve(b_div, p_sol, rtol=1e-10, max_iter=500, mode=mode)   # setup
-        ts, its = [], []
-        for _ in range(3):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            info = m.pressure_solve(b_div, p_sol, rtol=1e-10, max_iter=500, mode=mode)
-            ts.append(time.perf_counter() - t0)
-            its.append(info["iterations"])
-        solve_rates[name] = {"solves_per_s": 1.0 / statistics.median(ts), "iterations": statistics.mean(its),
-                             "rel_residual": info["rel_residual"]}
-
-    # roofline of the dominant kernel (by share of the step: the FP32 box Laplacian, applied ~11 times
-    # per multigrid V-cycle on the fine level and once explicitly in the step), timed live with CUDA
-    # events around its launch in the step; the FP64 apply is reported beside it against the FP64 peak
     peaks, src = _peaks()
-    k = w.k
-    nc = w.nx * w.ny * w.nz
-    curved = w.geometry == 1
-    lap32_ms = per_op["laplace32"]["ms"]
-    achieved32 = 8.0 * m.n_p / (lap32_ms * 1e-3) / 1e9
-    fl_cell = laplace_flops_per_cell(k, curved)
-    lap_ms = per_op["laplace"]["ms"]
-    fp64_peak = 152 * 4 * 2.07e9 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
-    achieved_tf = nc * fl_cell / (lap_ms * 1e-3) / 1e12
-    kname32 = "vector_op_kernel<float,OP_LAP,GEO_CURVED>" if curved else f"laplace_box_kernel<float,{k}>"
-    kname64 = "vector_op_kernel<double,OP_LAP,GEO_CURVED>" if curved else f"laplace_box_kernel<double,{k}>"
-    if w.name != DEFAULT_WORKLOAD:
-        args.traffic_bytes = None   # the ncu capture of record covers the Q4 box kernel of the default workload
-    roofline = {"kernel": kname32, "bound": "hbm", "achieved": achieved32,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved32 / peaks["hbm_gbs"],
-                "traffic": args.traffic_bytes, "algorithmic_bytes_per_launch": 8.0 * m.n_p,
-                "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" if src == "measured" else "fallback 6800 GB/s",
-                "fp32_flop_frac": nc * fl_cell / (lap32_ms * 1e-3) / 1e12 / (152 * 256 * 2.07e9 / 1e12),
-                "fp64_apply": {"kernel": kname64, "bound": "alu", "achieved": achieved_tf,
-                               "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
-                               "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz (probe measured 1.19)",
-                               "hbm_frac": 16.0 * m.n_p / (lap_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+    dom = max(dofs_ops, key=lambda o: per_op[o]["ms"])
+    geo = "GEO_CURVED" if curved else "GEO_BOX"
+    opname = {"divergence": "OP_DIV", "convective": "OP_CONV", "viscous": "OP_VISC"}
+    kname = ((f"curved_laplace_kernel<double,{w.k}>" if curved else f"laplace_box_kernel<double,{w.k}>")
+             if dom == "laplace" else f"vector_op_kernel<double,{opname[dom]},{geo}>")
+    roofline = {"kernel": kname, "bound": "alu", "achieved": per_op[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": per_op[dom]["fp64_frac"],
+                "traffic": args.traffic_bytes,
+                "algorithmic_flops_per_launch": nc * per_op[dom]["flops_per_cell"],
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                "hbm_frac": per_op[dom]["hbm_gbs"] / peaks["hbm_gbs"],
+                "hbm_peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" if src == "measured" else "fallback 6800 GB/s"}
+
+    # FP32 SIPG Laplacian (the operator of the FP32 multigrid), timed alone with CUDA events after an
+    # L2 flush, per launch: HBM roofline with 8 B per DoF (read p, write y)
+    p32 = pd.float()
+    y32 = torch.empty(m.n_p, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        m.laplace(p32, y32)
+    lap32 = []
+    for _ in range(10):
+        flush.zero_()
+        e0.record(stream)
+        m.laplace(p32, y32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lap32.append(e0.elapsed_time(e1))
+    lap32_ms = statistics.median(lap32)
+    ach32 = 8.0 * m.n_p / (lap32_ms * 1e-3) / 1e9
+    fp32_laplace = {"kernel": ("curved_laplace_kernel<float,%d>" if curved else "laplace_box_kernel<float,%d>") % w.k,
+                    "bound": "hbm", "ms": lap32_ms, "gdofs": m.n_p / (lap32_ms * 1e-3) / 1e9,
+                    "achieved": ach32, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach32 / peaks["hbm_gbs"],
+                    "fp32_flop_frac": nc * laplace_flops_per_cell(w.k, curved) / (lap32_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
+
+    # pressure solves to 1e-10: FP64 (FP64 CG + FP64 multigrid) vs mixed, on this workload (rhs = the
+    # step's divergence) and on the Q3 64x32x32 channel (seeded zero-mean rhs)
+    solves = {}
+    p_sol = torch.zeros(m.n_p, dtype=torch.float64, device=dev)
+    solves[w.name] = _time_solves(m, b_div, p_sol, (("fp64", 0), ("mixed", 1)), 3, flush)
+    if not args.no_extra_solves and world == 1:
+        w3 = I.WORKLOADS["channel_q3_64x32x32"]
+        m3 = dgw.mesh_for(w3)
+        b3 = torch.tensor(I.pressure_rhs(m3.n_p, w3.seed), device=dev)
+        p3 = torch.zeros_like(b3)
+        solves[w3.name] = _time_solves(m3, b3, p3, (("fp64", 0), ("mixed", 1)), 2, flush)
+        m3.close()
 
     # end to end through the public API with host buffers (copies inside the timed region)
     out_host = {n: torch.empty(t.numel(), dtype=torch.float64).pin_memory()
-                for n, t in (("lap", y_lap), ("div", b_div), ("conv", y_conv), ("visc", y_visc), ("p", p_sol))}
+                for n, t in (("lap", y_lap), ("div", b_div), ("conv", y_conv), ("visc", y_visc))}
     e2e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ud.copy_(u_host, non_blocking=True)
         pd.copy_(p_host, non_blocking=True)
         step(False)
-        for n, t in (("lap", y_lap), ("div", b_div), ("conv", y_conv), ("visc", y_visc), ("p", p_sol)):
+        for n, t in (("lap", y_lap), ("div", b_div), ("conv", y_conv), ("visc", y_visc)):
             out_host[n].copy_(t, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d = 8 * (m.n_u + m.n_p)
-    d2h = 8 * (3 * m.n_p + 2 * m.n_u)
+    d2h = 8 * (2 * m.n_p + 2 * m.n_u)
     e2e_ms_max = replica_time(statistics.mean(e2e_ms), world, dev)
     e2e = {"value": weak_value(dofs_step, world, e2e_ms_max), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max}
@@ -380,10 +435,11 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": w.name, "cells": [w.nx, w.ny, w.nz], "degree": w.k, "re_tau": w.re_tau,
-                           "n_p": m.n_p, "n_u": m.n_u, "n_enriched": m.n_e, "solve_mode": args.solve_mode,
+                           "n_p": m.n_p, "n_u": m.n_u, "n_enriched": m.n_e,
+                           "step": "nu_t update + FP64 Laplace, divergence, convective, viscous applies",
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
-                "per_op": per_op, "solves": solve_rates, "dof_applies_per_step": dofs_step,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "per_op": per_op, "dof_applies_per_step": dofs_step, "solves": solves,
+                "roofline": roofline, "fp32_laplace": fp32_laplace, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches1 - launches0), "launches_before_timed": int(launches0),
                 "wall_s": t_wall}
         print(json.dumps(line), flush=True)
@@ -680,7 +736,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dgw", choices=["dgw", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    ap.add_argument("--solve-mode", type=int, default=1)
+    ap.add_argument("--solve-mode", type=int, default=1, help="pressure solve mode of --ns-step")
+    ap.add_argument("--no-extra-solves", action="store_true", help="skip the Q3 64x32x32 solves")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # DRAM bytes (read + write) per launch of the roofline kernel, from an ncu capture of the same

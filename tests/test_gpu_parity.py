@@ -2,6 +2,7 @@
 inputs, element by element. Bar: relative 2-norm error <= 1e-12 and max elementwise error
 <= 1e-12 * max |y| for FP64; 1e-5 for FP32 applies."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -216,9 +217,11 @@ def test_full_size_sampled_parity(dgw, wname):
 @pytest.mark.parametrize("wname,mode", [("channel_q4_32x24x24", 1), ("channel_q4_32x24x24", 0),
                                         ("bump_q4_48x32x24", 1), ("bump_q4_48x32x24", 0)])
 def test_full_size_solve_residual_checked_by_oracle(dgw, wname, mode):
-    """Mixed and FP64 solves of the Q4 channel and bump workloads reach 1e-10; the oracle
-    re-evaluates A p on a sample of cells and must agree with the GPU's FP64 operator there, and
-    the GPU's own FP64 residual is checked against the target."""
+    """Mixed and FP64 solves of the Q4 channel and bump workloads, with the rhs the divergence of
+    the workload's velocity: the oracle's own SIPG operator, applied to the whole GPU solution,
+    gives ||b - A_oracle p|| / ||b|| <= 1.5e-10 (b projected to zero mean, as the solve does; the
+    margin above the 1e-10 target covers the rounding difference of two FP64 operator
+    evaluations), and p has zero mean."""
     w = I.WORKLOADS[wname]
     gm = dgw.mesh_for(w)
     dev = torch.device("cuda:0")
@@ -228,20 +231,14 @@ def test_full_size_solve_residual_checked_by_oracle(dgw, wname, mode):
     p = torch.zeros_like(b)
     info = gm.pressure_solve(b, p, rtol=1e-10, max_iter=300, mode=mode)
     assert info["rel_residual"] <= 1e-10, info
+    O.set_threads(os.cpu_count() or 1)
     om = O.Mesh(**w.mesh_kwargs())
-    nc = w.nx * w.ny * w.nz
-    cells = [0, 517, 9000, nc - 1]
-    om.set_active(cells)
-    n3 = (w.k + 1) ** 3
     bh = b.cpu().numpy()
     bh = bh - bh.mean()
-    ap = om.laplace(p.cpu().numpy())
-    y_gpu = torch.empty_like(p)
-    gm.laplace(p, y_gpu)
-    yg = y_gpu.cpu().numpy()
-    for c in cells:
-        sl = slice(c * n3, (c + 1) * n3)
-        assert np.abs(ap[sl] - yg[sl]).max() <= 1e-12 * np.abs(yg).max()
+    ph = p.cpu().numpy()
+    res = np.linalg.norm(bh - om.laplace(ph)) / np.linalg.norm(bh)
+    assert res <= 1.5e-10, (res, info["rel_residual"])
+    assert abs(ph.mean()) <= 1e-14 * np.abs(ph).max()
 
 
 @pytest.mark.parametrize("dims,k", [((8, 8, 8), 4), ((8, 8, 8), 2), ((16, 12, 12), 3)])
