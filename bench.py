@@ -391,6 +391,33 @@ def run_gpu(args):
                     "achieved": ach32, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach32 / peaks["hbm_gbs"],
                     "fp32_flop_frac": nc * laplace_flops_per_cell(w.k, curved) / (lap32_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
 
+    # the same Laplacian with double vectors in double-float arithmetic on the FP32 units (FP64-accurate
+    # emulation) against the native FP64 apply, each timed alone after an L2 flush (box cells only)
+    emulation = None
+    if not curved:
+        def t_alone(fn):
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(10):
+                flush.zero_()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+        ydf = torch.empty_like(y_lap)
+        ms64 = t_alone(lambda: m.laplace(pd, y_lap))
+        msdf = t_alone(lambda: m.laplace(pd, ydf, prec=dgw.DGW_DF64))
+        diff = float(torch.linalg.norm(ydf - y_lap) / torch.linalg.norm(y_lap))
+        fl = nc * laplace_flops_per_cell(w.k)
+        emulation = {"kernel": f"laplace_box_kernel<double,df64,{w.k}>", "fp64_ms": ms64, "df64_ms": msdf,
+                     "speedup": ms64 / msdf, "rel_diff_vs_fp64": diff,
+                     "df64_gdofs": m.n_p / (msdf * 1e-3) / 1e9,
+                     "fp64_equiv_tflops": fl / (msdf * 1e-3) / 1e12,
+                     "hbm_frac": 16.0 * m.n_p / (msdf * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+
     # pressure solves to 1e-10: FP64 (FP64 CG + FP64 multigrid) vs mixed, on this workload (rhs = the
     # step's divergence) and on the Q3 64x32x32 channel (seeded zero-mean rhs)
     solves = {}
@@ -439,7 +466,8 @@ def run_gpu(args):
                            "step": "nu_t update + FP64 Laplace, divergence, convective, viscous applies",
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
                 "per_op": per_op, "dof_applies_per_step": dofs_step, "solves": solves,
-                "roofline": roofline, "fp32_laplace": fp32_laplace, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "fp32_laplace": fp32_laplace, "df64_emulation": emulation,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches1 - launches0), "launches_before_timed": int(launches0),
                 "wall_s": t_wall}
         print(json.dumps(line), flush=True)
@@ -702,7 +730,8 @@ def run_profile_kernel(args):
     if kind.startswith("laplace"):
         x = torch.rand(m.n_p, dtype=dt, device="cuda", generator=gen)
         y = torch.empty_like(x)
-        op = lambda: m.laplace(x, y)
+        prec = dgw.DGW_DF64 if kind == "laplace_df64" else None
+        op = lambda: m.laplace(x, y, prec=prec)
     else:
         u = torch.rand(m.n_u, dtype=torch.float64, device="cuda", generator=gen)
         m.update_eddy_viscosity(u)
@@ -757,7 +786,7 @@ def main():
     ap.add_argument("--ns-step", action="store_true", help="time dual-splitting time steps")
     ap.add_argument("--wall-update-steps", action="store_true", help="--ns-step: update the wall model every step")
     ap.add_argument("--profile-kernel", default=None,
-                    choices=["laplace64", "laplace32", "divergence", "convective", "convective32", "viscous",
+                    choices=["laplace64", "laplace32", "laplace_df64", "divergence", "convective", "convective32", "viscous",
                              "viscous32", "mass", "divdiv", "curl", "inverse_mass"])
     ap.add_argument("--profile-cells", type=int, nargs=4, default=[64, 48, 48, 4], metavar=("NX", "NY", "NZ", "K"))
     ap.add_argument("--profile-reps", type=int, default=3)

@@ -32,7 +32,11 @@
  *     a constant weight, Sec. 5.1) of the enriched cells; enriched cells are
  *     numbered bottom layer(s) first, then top layer(s), lexicographic (x fastest, then z)
  *     within a layer.
- *   - prec: DGW_FP64 -> buffers are double*, DGW_FP32 -> float*.
+ *   - prec: DGW_FP64 -> buffers are double*, DGW_FP32 -> float*; DGW_DF64 -> buffers are
+ *     double*, arithmetic in double-float (pairs of FP32 numbers with error-free
+ *     transformations, about 48 significant bits) on the FP32 units, which GB300 runs at 64 times
+ *     its FP64 rate; the result agrees with the FP64 apply to about 1e-14 relative to the
+ *     magnitude of the summed terms. Only the applies that say so accept DGW_DF64.
  */
 #ifndef DGW_H
 #define DGW_H
@@ -57,7 +61,7 @@ typedef enum {
   DGW_EDEVICE = -7    /* a kernel set its device-side error word */
 } dgw_status;
 
-enum { DGW_FP64 = 0, DGW_FP32 = 1 };
+enum { DGW_FP64 = 0, DGW_FP32 = 1, DGW_DF64 = 2 };
 
 /* Mesh and discretisation parameters.
  * Channel (geometry 0): [0,lx] x [-ly/2, ly/2] x [0,lz], periodic in x and z, no-slip walls at
@@ -186,7 +190,8 @@ dgw_status dgw_set_enrichment_switch(dgw_mesh_t mesh, double yplus_off, void *st
 dgw_status dgw_enrichment_active(dgw_mesh_t mesh, int *active_host, int *n_active, void *stream);
 
 /* y = -L(q, p) (Sec. 4.2, SIPG Laplace term with the flux of eq. ipflux on interior and
- * periodic faces; homogeneous Neumann on walls). p, y: n_p values of type `prec`. */
+ * periodic faces; homogeneous Neumann on walls). p, y: n_p values of type `prec`; DGW_DF64 is
+ * accepted on the channel (box cells), DGW_EINVAL on curved meshes. */
 dgw_status dgw_apply_laplace(dgw_mesh_t mesh, int prec, const void *p, void *y, void *stream);
 
 /* b = -C(q, u) = (grad q, u) - (q, {{u}}.n) with {{u}} = u^- on walls (Sec. 4.2, velocity

@@ -489,7 +489,11 @@ dgw_status dgw_apply_laplace(dgw_mesh_t M, int prec, const void *p, void *y, voi
     if (!M->has32) return set_error(DGW_EINVAL, "dgw_apply_laplace: mesh built without FP32 tables");
     return cuda_check(launch_laplace<float>(M->v32, (const float *)p, (float *)y, s), "dgw_apply_laplace");
   }
-  return set_error(DGW_EINVAL, "dgw_apply_laplace: prec must be DGW_FP64 or DGW_FP32");
+  if (prec == DGW_DF64) {
+    if (M->P.geometry != 0) return set_error(DGW_EINVAL, "dgw_apply_laplace: DGW_DF64 needs box cells (geometry 0)");
+    return cuda_check(launch_laplace_df(M->v64, (const double *)p, (double *)y, s), "dgw_apply_laplace");
+  }
+  return set_error(DGW_EINVAL, "dgw_apply_laplace: prec must be DGW_FP64, DGW_FP32 or DGW_DF64");
 }
 
 static dgw_status apply_vec(dgw_mesh_t M, int op, int prec, const void *u, void *y, void *stream, const char *name) {

@@ -212,6 +212,8 @@ template <typename T>
 cudaError_t launch_laplace(const MeshView<T> &m, const T *p, T *y, cudaStream_t s);
 template <typename T>
 cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s);
+// y = A_L p with double vectors in double-float arithmetic on the FP32 units (box cells only)
+cudaError_t launch_laplace_df(const MeshView<double> &m, const double *p, double *y, cudaStream_t s);
 // Jacobi diagonal of the SIPG Laplacian of a curved mesh (FP64, one thread per DoF)
 cudaError_t launch_curved_diagonal(const MeshView<double> &m, double *dg, cudaStream_t s);
 // SIPG Laplacian on curved cells from the lvol/lface tables (degree-specialised line passes)

@@ -21,7 +21,9 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
+#include "df64.cuh"
 #include "sumfac.cuh"
 
 namespace dgw {
@@ -38,6 +40,7 @@ struct BoxConst {
 };
 __constant__ BoxConst<float> c_box32[5];
 __constant__ BoxConst<double> c_box64[5];
+__constant__ BoxConst<df64> c_boxdf[5];   // double-float copies for the FP64-accurate FP32-pipe path
 
 template <typename T>
 __device__ __forceinline__ const BoxConst<T> &box_const(int k);
@@ -45,13 +48,18 @@ template <>
 __device__ __forceinline__ const BoxConst<float> &box_const<float>(int k) { return c_box32[k - 1]; }
 template <>
 __device__ __forceinline__ const BoxConst<double> &box_const<double>(int k) { return c_box64[k - 1]; }
+template <>
+__device__ __forceinline__ const BoxConst<df64> &box_const<df64>(int k) { return c_boxdf[k - 1]; }
 
 // FP32: up to 3 CTAs of <= 256 threads per SM for k <= 4 (register budget ~85/thread), 2 for k = 5;
-// FP64 is FP64-pipe bound and keeps the default budget.
+// FP64 is FP64-pipe bound and keeps the default budget; double-float (two registers per value,
+// about fifteen instructions per multiply-add) keeps two CTAs per SM.
 template <typename T, int K>
 struct BoxOcc { static constexpr int min_blocks = 1; };
 template <int K>
 struct BoxOcc<float, K> { static constexpr int min_blocks = K <= 4 ? 3 : 2; };
+template <int K>
+struct BoxOcc<df64, K> { static constexpr int min_blocks = 2; };
 
 // One line of L_d u + N_d (tv, td) (see the file comment); R = the 8 scalars of direction d.
 template <typename T, int K>
@@ -60,21 +68,22 @@ __device__ __forceinline__ void line_op(const T (&u)[K + 1], const T *R, T tv0, 
   const BoxConst<T> &C = box_const<T>(K);
   const T a = R[0], p0 = R[1], p1 = R[2], t0 = R[3], t1 = R[4], e0 = R[5], e1 = R[6];
   const T j0 = tv0 - u[0], j1 = tv1 - u[n - 1];
-  T d0 = T(0), d1 = T(0);
+  T d0 = r_zero<T>(), d1 = r_zero<T>();
 #pragma unroll
   for (int b = 0; b < n; ++b) {
-    d0 += C.D[0][b] * u[b];
-    d1 += C.D[1][b] * u[b];
+    d0 = r_fma(C.D[0][b], u[b], d0);
+    d1 = r_fma(C.D[1][b], u[b], d1);
   }
+  const T q0 = p0 * j0, q1 = p1 * j1;
 #pragma unroll
   for (int r = 0; r < n; ++r) {
-    T s = T(0);
+    T s = r_zero<T>();
 #pragma unroll
-    for (int b = 0; b < n; ++b) s += C.K[r * n + b] * u[b];
-    out[r] = a * s + p0 * C.D[0][r] * j0 + p1 * C.D[1][r] * j1;
+    for (int b = 0; b < n; ++b) s = r_fma(C.K[r * n + b], u[b], s);
+    out[r] = r_fma(C.D[1][r], q1, r_fma(C.D[0][r], q0, a * s));
   }
-  out[0] += -p0 * d0 - t0 * j0 - e0 * td0;
-  out[n - 1] += -p1 * d1 - t1 * j1 - e1 * td1;
+  out[0] = out[0] - r_fma(p0, d0, r_fma(t0, j0, e0 * td0));
+  out[n - 1] = out[n - 1] - r_fma(p1, d1, r_fma(t1, j1, e1 * td1));
 }
 
 // v <- M v along a line of n values
@@ -84,34 +93,36 @@ __device__ __forceinline__ void mass_line(const T (&v)[K + 1], T (&out)[K + 1]) 
   const BoxConst<T> &C = box_const<T>(K);
 #pragma unroll
   for (int r = 0; r < n; ++r) {
-    T s = T(0);
+    T s = r_zero<T>();
 #pragma unroll
-    for (int b = 0; b < n; ++b) s += C.M[r * n + b] * v[b];
+    for (int b = 0; b < n; ++b) s = r_fma(C.M[r * n + b], v[b], s);
     out[r] = s;
   }
 }
 
-template <typename T, int K>
-__global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p,
+// T: storage type of p and y; R: compute type (T itself, or df64 for FP64-accurate arithmetic on the
+// FP32 units with double vectors; that variant supports the plain epilogue only).
+template <typename T, typename R, int K>
+__global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p,
                                                                                 T *__restrict__ y, int cpb,
                                                                                 LapEpi<T> epi) {
   constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Rs = reinterpret_cast<T *>(smem_raw);     // kRowScal
-  T *U = Rs + kRowScal;                         // cpb n3 (input, then output)
-  T *A = U + cpb * n3;                          // cpb n3 (T1 -> W)
-  T *B = A + cpb * n3;                          // cpb n3 (T2 -> T3)
-  T *TR = B + cpb * n3;                         // cpb * 6 faces * 2 (val, der) * n2
-  T *TY = TR + cpb * 24 * n2;                   // cpb * 2 faces * 2 * n2 : y-face traces after M_x
-  T *TZ = TY + cpb * 8 * n2;                    // cpb * 2 * 2 * n2 : z-face traces after M_x
-  const BoxConst<T> &C = box_const<T>(K);
+  R *Rs = reinterpret_cast<R *>(smem_raw);     // kRowScal
+  R *U = Rs + kRowScal;                         // cpb n3 (input, then output)
+  R *A = U + cpb * n3;                          // cpb n3 (T1 -> W)
+  R *B = A + cpb * n3;                          // cpb n3 (T2 -> T3)
+  R *TR = B + cpb * n3;                         // cpb * 6 faces * 2 (val, der) * n2
+  R *TY = TR + cpb * 24 * n2;                   // cpb * 2 faces * 2 * n2 : y-face traces after M_x
+  R *TZ = TY + cpb * 8 * n2;                    // cpb * 2 * 2 * n2 : z-face traces after M_x
+  const BoxConst<R> &C = box_const<R>(K);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int c0 = blockIdx.x * cpb;
   const int i0 = c0 % m.nx, j = (c0 / m.nx) % m.ny, kz = c0 / (m.nx * m.ny);
   const T *Rg = m.rowops + (size_t)j * kRowScal;
-  for (int t = tid; t < kRowScal; t += nt) Rs[t] = Rg[t];
+  for (int t = tid; t < kRowScal; t += nt) Rs[t] = r_load<R>(Rg[t]);
   const T *pc = p + (size_t)c0 * n3;
-  for (int t = tid; t < cpb * n3; t += nt) U[t] = pc[t];
+  for (int t = tid; t < cpb * n3; t += nt) U[t] = r_load<R>(pc[t]);
   // Every thread owns line l of cell cl in all three passes (x-, y- then z-lines; l indexes the
   // face nodes of the same two tangential axes), so the index arithmetic is done once here.
   const bool line = tid < cpb * n2;
@@ -132,19 +143,25 @@ __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_k
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, side = f & 1, nb = nbr[cl * 6 + f];
-      T val = T(0), der = T(0);
+      R val = r_zero<R>(), der = r_zero<R>();
       if (nb >= 0) {
-        // x-neighbours inside this CTA's row segment are already in shared memory
-        const T *pn = (nb >= c0 && nb < c0 + cpb) ? U + (nb - c0) * n3 : p + (size_t)nb * n3;
         // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
         const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
         const int base = d == 0 ? n * l : (d == 1 ? lr + n2 * lq : l);
-        T v[n];
+        R v[n];
+        // x-neighbours inside this CTA's row segment are already in shared memory
+        if (nb >= c0 && nb < c0 + cpb) {
+          const R *pn = U + (nb - c0) * n3;
 #pragma unroll
-        for (int b = 0; b < n; ++b) v[b] = pn[base + b * stride];
+          for (int b = 0; b < n; ++b) v[b] = pn[base + b * stride];
+        } else {
+          const T *pn = p + (size_t)nb * n3;
+#pragma unroll
+          for (int b = 0; b < n; ++b) v[b] = r_load<R>(pn[base + b * stride]);
+        }
         val = side ? v[0] : v[n - 1];
 #pragma unroll
-        for (int b = 0; b < n; ++b) der += (side ? C.D[0][b] : C.D[1][b]) * v[b];
+        for (int b = 0; b < n; ++b) der = r_fma(side ? C.D[0][b] : C.D[1][b], v[b], der);
       }
       TR[((cl * 6 + f) * 2 + 0) * n2 + l] = val;
       TR[((cl * 6 + f) * 2 + 1) * n2 + l] = der;
@@ -155,13 +172,13 @@ __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_k
   // it = l, l + n^2, ... < 4n: face (it / n) >> 1, array (it / n) & 1, t2 = it % n)
   if (line) {
     const int base = cl * n3 + n * l;
-    T u[n], o1[n], o2[n];
+    R u[n], o1[n], o2[n];
 #pragma unroll
     for (int b = 0; b < n; ++b) u[b] = U[base + b];
-    const T v0 = TR[((cl * 6 + 0) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 0) * 2 + 1) * n2 + l];
-    const T v1 = TR[((cl * 6 + 1) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 1) * 2 + 1) * n2 + l];
-    line_op<T, K>(u, Rs, v0, d0, v1, d1, o1);
-    mass_line<T, K>(u, o2);
+    const R v0 = TR[((cl * 6 + 0) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 0) * 2 + 1) * n2 + l];
+    const R v1 = TR[((cl * 6 + 1) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 1) * 2 + 1) * n2 + l];
+    line_op<R, K>(u, Rs, v0, d0, v1, d1, o1);
+    mass_line<R, K>(u, o2);
 #pragma unroll
     for (int a = 0; a < n; ++a) { A[base + a] = o1[a]; B[base + a] = o2[a]; }
     for (int it = l; it < 4 * n; it += n2) {   // one item per thread for k >= 3
@@ -169,12 +186,12 @@ __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_k
       const int fl = iq >> 1, arr = iq & 1;
 #pragma unroll
       for (int isz = 0; isz < 2; ++isz) {
-        const T *src = TR + ((cl * 6 + (isz ? 4 : 2) + fl) * 2 + arr) * n2 + n * ir;
-        T *dst = (isz ? TZ : TY) + ((cl * 2 + fl) * 2 + arr) * n2 + n * ir;
-        T v[n], o[n];
+        const R *src = TR + ((cl * 6 + (isz ? 4 : 2) + fl) * 2 + arr) * n2 + n * ir;
+        R *dst = (isz ? TZ : TY) + ((cl * 2 + fl) * 2 + arr) * n2 + n * ir;
+        R v[n], o[n];
 #pragma unroll
         for (int b = 0; b < n; ++b) v[b] = src[b];
-        mass_line<T, K>(v, o);
+        mass_line<R, K>(v, o);
 #pragma unroll
         for (int a = 0; a < n; ++a) dst[a] = o[a];
       }
@@ -185,25 +202,25 @@ __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_k
   // traces (indexed x + n*y) <- M_y (items it as in phase A, x = it % n)
   if (line) {
     const int base = cl * n3 + lr + n2 * lq;
-    T a1[n], a2[n], w[n], t3[n], ly[n];
+    R a1[n], a2[n], w[n], t3[n], ly[n];
 #pragma unroll
     for (int c = 0; c < n; ++c) { a1[c] = A[base + n * c]; a2[c] = B[base + n * c]; }
-    const T v0 = TY[((cl * 2 + 0) * 2 + 0) * n2 + l], d0 = TY[((cl * 2 + 0) * 2 + 1) * n2 + l];
-    const T v1 = TY[((cl * 2 + 1) * 2 + 0) * n2 + l], d1 = TY[((cl * 2 + 1) * 2 + 1) * n2 + l];
-    line_op<T, K>(a2, Rs + 8, v0, d0, v1, d1, ly);
-    mass_line<T, K>(a1, w);
-    mass_line<T, K>(a2, t3);
+    const R v0 = TY[((cl * 2 + 0) * 2 + 0) * n2 + l], d0 = TY[((cl * 2 + 0) * 2 + 1) * n2 + l];
+    const R v1 = TY[((cl * 2 + 1) * 2 + 0) * n2 + l], d1 = TY[((cl * 2 + 1) * 2 + 1) * n2 + l];
+    line_op<R, K>(a2, Rs + 8, v0, d0, v1, d1, ly);
+    mass_line<R, K>(a1, w);
+    mass_line<R, K>(a2, t3);
 #pragma unroll
     for (int b = 0; b < n; ++b) { A[base + n * b] = w[b] + ly[b]; B[base + n * b] = t3[b]; }
     for (int it = l; it < 4 * n; it += n2) {
       const int iq = it / n, ir = it - iq * n;
       const int fl = iq >> 1, arr = iq & 1;
-      const T *src = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + ir;
-      T *dst = TR + ((cl * 6 + 4 + fl) * 2 + arr) * n2 + ir;
-      T v[n], o[n];
+      const R *src = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + ir;
+      R *dst = TR + ((cl * 6 + 4 + fl) * 2 + arr) * n2 + ir;
+      R v[n], o[n];
 #pragma unroll
       for (int b = 0; b < n; ++b) v[b] = src[n * b];
-      mass_line<T, K>(v, o);
+      mass_line<R, K>(v, o);
 #pragma unroll
       for (int a = 0; a < n; ++a) dst[n * a] = o[a];
     }
@@ -212,28 +229,30 @@ __global__ void __launch_bounds__(256, (BoxOcc<T, K>::min_blocks)) laplace_box_k
   // ---- phase C: z-lines at l = x + n*y (y = M_z W + Lz T3 + nbr_z'')
   if (line) {
     const int base = cl * n3 + l;
-    T a1[n], a2[n], w[n], lz[n];
+    R a1[n], a2[n], w[n], lz[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) { a1[e] = A[base + n2 * e]; a2[e] = B[base + n2 * e]; }
-    const T v0 = TR[((cl * 6 + 4) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 4) * 2 + 1) * n2 + l];
-    const T v1 = TR[((cl * 6 + 5) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 5) * 2 + 1) * n2 + l];
-    line_op<T, K>(a2, Rs + 16, v0, d0, v1, d1, lz);
-    mass_line<T, K>(a1, w);
+    const R v0 = TR[((cl * 6 + 4) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 4) * 2 + 1) * n2 + l];
+    const R v1 = TR[((cl * 6 + 5) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 5) * 2 + 1) * n2 + l];
+    line_op<R, K>(a2, Rs + 16, v0, d0, v1, d1, lz);
+    mass_line<R, K>(a1, w);
 #pragma unroll
     for (int c = 0; c < n; ++c) U[base + n2 * c] = w[c] + lz[c];
   }
   __syncthreads();
   const size_t o = (size_t)c0 * n3;
   if (epi.mode == LAP_PLAIN) {
-    for (int t = tid; t < cpb * n3; t += nt) y[o + t] = U[t];
-  } else if (epi.mode == LAP_RESIDUAL) {
-    for (int t = tid; t < cpb * n3; t += nt) y[o + t] = epi.b[o + t] - U[t];
-  } else {
-    for (int t = tid; t < cpb * n3; t += nt) {
-      const size_t i = o + t;
-      const T dn = (epi.first ? T(0) : epi.c1 * epi.d[i]) + epi.c2 * epi.dinv[i] * (epi.b[i] - U[t]);
-      epi.d[i] = dn;
-      epi.xout[i] = p[i] + dn;
+    for (int t = tid; t < cpb * n3; t += nt) y[o + t] = r_store<T>(U[t]);
+  } else if constexpr (std::is_same<T, R>::value) {
+    if (epi.mode == LAP_RESIDUAL) {
+      for (int t = tid; t < cpb * n3; t += nt) y[o + t] = epi.b[o + t] - U[t];
+    } else {
+      for (int t = tid; t < cpb * n3; t += nt) {
+        const size_t i = o + t;
+        const T dn = (epi.first ? T(0) : epi.c1 * epi.d[i]) + epi.c2 * epi.dinv[i] * (epi.b[i] - U[t]);
+        epi.d[i] = dn;
+        epi.xout[i] = p[i] + dn;
+      }
     }
   }
 }
@@ -290,29 +309,42 @@ cudaError_t box_constants_init() {
     for (int sd = 0; sd < 2; ++sd)
       for (int i = 0; i < NMAX; ++i) h32[k - 1].D[sd][i] = (float)h64[k - 1].D[sd][i];
   }
+  // double-float copies: hi = nearest float, lo = nearest float to the remainder
+  BoxConst<df64> hdf[5];
+  std::memset(hdf, 0, sizeof(hdf));
+  auto split = [](double v) { const float h = (float)v; return df64{h, (float)(v - (double)h)}; };
+  for (int k = 0; k < 5; ++k) {
+    for (int i = 0; i < NMAX * NMAX; ++i) {
+      hdf[k].M[i] = split(h64[k].M[i]);
+      hdf[k].K[i] = split(h64[k].K[i]);
+    }
+    for (int sd = 0; sd < 2; ++sd)
+      for (int i = 0; i < NMAX; ++i) hdf[k].D[sd][i] = split(h64[k].D[sd][i]);
+  }
   e = cudaMemcpyToSymbol(c_box64, h64, sizeof(h64));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_box32, h32, sizeof(h32));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_boxdf, hdf, sizeof(hdf));
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
 
-template <typename T, int K>
+template <typename T, typename R, int K>
 static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
   constexpr int n = K + 1;
   const int cpb = box_cpb(m.nx, n);
-  const size_t sm = box_smem<T>(n, cpb);
+  const size_t sm = box_smem<R>(n, cpb);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(laplace_box_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(laplace_box_kernel<T, R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e == cudaSuccess)   // the whole unified L1/shared array as shared memory: more CTAs per SM
-      e = cudaFuncSetAttribute(laplace_box_kernel<T, K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      e = cudaFuncSetAttribute(laplace_box_kernel<T, R, K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int threads = ((cpb * n * n + 31) / 32) * 32;
   note_launch();
   note_dofs(m.np);
-  laplace_box_kernel<T, K><<<m.nc / cpb, threads, sm, s>>>(m, p, y, cpb, epi);
+  laplace_box_kernel<T, R, K><<<m.nc / cpb, threads, sm, s>>>(m, p, y, cpb, epi);
   return cudaGetLastError();
 }
 
@@ -324,11 +356,26 @@ cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const Lap
     return launch_vector_op<T>(OP_LAP, m, p, y, s, &epi);
   }
   switch (m.n1) {
-    case 2: return launch_box_k<T, 1>(m, p, y, epi, s);
-    case 3: return launch_box_k<T, 2>(m, p, y, epi, s);
-    case 4: return launch_box_k<T, 3>(m, p, y, epi, s);
-    case 5: return launch_box_k<T, 4>(m, p, y, epi, s);
-    case 6: return launch_box_k<T, 5>(m, p, y, epi, s);
+    case 2: return launch_box_k<T, T, 1>(m, p, y, epi, s);
+    case 3: return launch_box_k<T, T, 2>(m, p, y, epi, s);
+    case 4: return launch_box_k<T, T, 3>(m, p, y, epi, s);
+    case 5: return launch_box_k<T, T, 4>(m, p, y, epi, s);
+    case 6: return launch_box_k<T, T, 5>(m, p, y, epi, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// y = A_L p with double vectors and double-float arithmetic (boxes only; plain epilogue)
+cudaError_t launch_laplace_df(const MeshView<double> &m, const double *p, double *y, cudaStream_t s) {
+  if (m.geo == GEO_CURVED) return cudaErrorNotSupported;
+  LapEpi<double> epi{};
+  epi.mode = LAP_PLAIN;
+  switch (m.n1) {
+    case 2: return launch_box_k<double, df64, 1>(m, p, y, epi, s);
+    case 3: return launch_box_k<double, df64, 2>(m, p, y, epi, s);
+    case 4: return launch_box_k<double, df64, 3>(m, p, y, epi, s);
+    case 5: return launch_box_k<double, df64, 4>(m, p, y, epi, s);
+    case 6: return launch_box_k<double, df64, 5>(m, p, y, epi, s);
   }
   return cudaErrorInvalidValue;
 }

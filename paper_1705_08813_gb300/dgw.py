@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libdgw.so")
 
 DGW_FP64 = 0
 DGW_FP32 = 1
+DGW_DF64 = 2   # double vectors, double-float arithmetic on the FP32 units
 STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -4: "DGW_ETIMEOUT",
           -5: "DGW_EBUSY", -6: "DGW_ECUDA", -7: "DGW_EDEVICE"}
 
@@ -206,9 +207,12 @@ class Mesh:
         import torch
         _check(self.lib.dgw_update_eddy_viscosity(self.h, _ptr(u, torch.float64, self.n_u, "u"), _stream(stream)))
 
-    def laplace(self, p, y, stream=None):
-        _check(self.lib.dgw_apply_laplace(self.h, self._prec(p), _ptr(p, None, self.n_p, "p"),
-                                          _ptr(y, p.dtype, self.n_p, "y"), _stream(stream)))
+    def laplace(self, p, y, stream=None, prec=None):
+        """y = A_L p; prec defaults to the tensors' dtype (DGW_DF64: double tensors, double-float
+        arithmetic)."""
+        _check(self.lib.dgw_apply_laplace(self.h, self._prec(p) if prec is None else prec,
+                                          _ptr(p, None, self.n_p, "p"), _ptr(y, p.dtype, self.n_p, "y"),
+                                          _stream(stream)))
         return y
 
     def divergence(self, u, b, stream=None):

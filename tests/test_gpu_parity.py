@@ -86,6 +86,29 @@ def test_operators_match_oracle(dgw, name, w, kw):
     _cmp(gm.viscous(ud.float(), yv32).cpu().numpy(), refv, 2 * TOL32, "viscous fp32")
 
 
+@pytest.mark.parametrize("name,w,kw", CASES, ids=[c[0] for c in CASES])
+def test_df64_laplace_matches_oracle(dgw, name, w, kw):
+    """The double-float Laplacian (double vectors, FP32-unit arithmetic) meets the FP64 bar against
+    the oracle and stays within 1e-13 of the native FP64 apply."""
+    om, gm = _meshes(dgw, w, **kw)
+    dev = torch.device("cuda:0")
+    p = I.pressure_field(om.n_p, w.seed)
+    pd = torch.tensor(p, device=dev)
+    ref = om.laplace(p)
+    y = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
+    ydf = gm.laplace(pd, y, prec=dgw.DGW_DF64).cpu().numpy()
+    _cmp(ydf, ref, TOL64, "laplace df64")
+    y64 = gm.laplace(pd, torch.empty_like(y)).cpu().numpy()
+    assert np.linalg.norm(ydf - y64) / np.linalg.norm(y64) < 1e-13
+
+
+def test_df64_rejected_on_curved_cells(dgw):
+    gm = dgw.mesh_for(I.bump_workload("b", 4, 4, 2, 2, seed=3))
+    x = torch.zeros(gm.n_p, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgw.DGWError):
+        gm.laplace(x, torch.empty_like(x), prec=dgw.DGW_DF64)
+
+
 def test_viscous_frozen_field_differs_from_input(dgw):
     """nu_t comes from the field of the last update, not from the applied vector (frozen)."""
     w = I.WORKLOADS["channel_q2_8x8x8"]
@@ -203,6 +226,8 @@ def test_full_size_sampled_parity(dgw, wname):
 
     y = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
     _cmp(sel_p(gm.laplace(pd, y).cpu().numpy()), sel_p(om.laplace(p)), TOL64, "laplace fp64")
+    if w.geometry == 0:
+        _cmp(sel_p(gm.laplace(pd, y, prec=dgw.DGW_DF64).cpu().numpy()), sel_p(om.laplace(p)), TOL64, "laplace df64")
     y32 = torch.empty(gm.n_p, dtype=torch.float32, device=dev)
     _cmp(sel_p(gm.laplace(pd.float(), y32).cpu().numpy()), sel_p(om.laplace(p)), TOL32, "laplace fp32")
     b = torch.empty(gm.n_p, dtype=torch.float64, device=dev)
