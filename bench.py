@@ -737,8 +737,13 @@ def run_profile_kernel(args):
         m.update_eddy_viscosity(u)
         x = u.to(dt)
         y = torch.empty(m.n_p if kind.startswith("divergence") else m.n_u, dtype=dt, device="cuda")
+        if kind.startswith("divergence"):
+            x = u
         tau = torch.full((m.nc,), 1e-3, dtype=torch.float64, device="cuda")
+        DF = dgw.DGW_DF64
         op = {"divergence": lambda: m.divergence(x, y), "convective": lambda: m.convective(x, y),
+              "divergence_df64": lambda: m.divergence(x, y, prec=DF), "viscous_df64": lambda: m.viscous(x, y, prec=DF),
+              "convective_df64": lambda: m.convective(x, y, prec=DF),
               "convective32": lambda: m.convective(x, y), "viscous": lambda: m.viscous(x, y),
               "viscous32": lambda: m.viscous(x, y), "mass": lambda: m.mass(x, y),
               "divdiv": lambda: m.divdiv(tau, x, y), "curl": lambda: m.curl(x, y),
@@ -786,7 +791,8 @@ def main():
     ap.add_argument("--ns-step", action="store_true", help="time dual-splitting time steps")
     ap.add_argument("--wall-update-steps", action="store_true", help="--ns-step: update the wall model every step")
     ap.add_argument("--profile-kernel", default=None,
-                    choices=["laplace64", "laplace32", "laplace_df64", "divergence", "convective", "convective32", "viscous",
+                    choices=["laplace64", "laplace32", "laplace_df64", "divergence_df64", "viscous_df64",
+                             "convective_df64", "divergence", "convective", "convective32", "viscous",
                              "viscous32", "mass", "divdiv", "curl", "inverse_mass"])
     ap.add_argument("--profile-cells", type=int, nargs=4, default=[64, 48, 48, 4], metavar=("NX", "NY", "NZ", "K"))
     ap.add_argument("--profile-reps", type=int, default=3)

@@ -198,15 +198,22 @@ dgw_status dgw_apply_laplace(dgw_mesh_t mesh, int prec, const void *p, void *y, 
  * divergence; boundary rule below eq. poissonspat). u: n_u doubles, b: n_p doubles. */
 dgw_status dgw_apply_divergence(dgw_mesh_t mesh, const double *u, double *b, void *stream);
 
+/* The same divergence with a precision: DGW_FP64 (as dgw_apply_divergence) or DGW_DF64 (double
+ * vectors, double-float arithmetic on the box rows whose cells and neighbours are standard cells;
+ * the rows of and next to the enriched layers are computed in FP64; box cells only, DGW_EINVAL on
+ * curved meshes). u: n_u doubles, b: n_p doubles. */
+dgw_status dgw_apply_divergence_prec(dgw_mesh_t mesh, int prec, const double *u, double *b, void *stream);
+
 /* y = F^c(v, u) = -(grad v, u x u) + (v, F^c*.n), local Lax-Friedrichs flux with
  * Lambda = max(2|u^-.n|, 2|u^+.n|), mirror state u^+ = -u^- on walls (Sec. 4.2). Over-integrated
  * with floor(3k/2)+1 Gauss points per direction, q_wall wall-normal points in enriched cells
- * (Sec. 4.4). u, y: n_u values of type `prec`. */
+ * (Sec. 4.4). u, y: n_u values of type `prec`; DGW_DF64 as for dgw_apply_divergence_prec. */
 dgw_status dgw_apply_convective(dgw_mesh_t mesh, int prec, const void *u, void *y, void *stream);
 
 /* y = -F^nu(vbar, v~; ubar, u~), eq. (viscous_multiscale), with the frozen nu_t of the last
  * dgw_update_eddy_viscosity, harmonic weights eq. (harmweights), clipped viscosity eq. (minvt),
- * penalty with nu only, mirror state on walls. u, y: n_u values of type `prec`. */
+ * penalty with nu only, mirror state on walls. u, y: n_u values of type `prec`; DGW_DF64 as for
+ * dgw_apply_divergence_prec. */
 dgw_status dgw_apply_viscous(dgw_mesh_t mesh, int prec, const void *u, void *y, void *stream);
 
 typedef struct {

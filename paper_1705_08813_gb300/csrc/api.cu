@@ -62,6 +62,15 @@ static void fill_view(dgw_mesh *M, MeshView<T> &v) {
   v.hx = (T)(M->P.lx / M->P.nx);
   v.hz = (T)(M->P.lz / M->P.nz);
   v.visc = (T)M->P.nu;
+  // plain rows: no enrichment slot in the row or in the rows next to it (layers are whole rows)
+  const int nx = M->P.nx, ny = M->P.ny;
+  int nb = 0, nt = 0;
+  while (nb < ny && M->enr[(size_t)nx * nb] >= 0) ++nb;
+  while (nt < ny - nb && M->enr[(size_t)nx * (ny - 1 - nt)] >= 0) ++nt;
+  int lo = nb == 0 ? 0 : nb + 1, hi = nt == 0 ? ny : ny - nt - 1;
+  if (M->P.geometry != 0 || lo >= hi) lo = hi = ny;
+  v.plain_lo = lo;
+  v.plain_hi = hi;
 }
 
 }  // namespace dgw
@@ -273,8 +282,8 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
     }
   }
   const size_t nv0 = (size_t)ne * M->v64.nvol[0], nf0 = (size_t)ne * 6 * M->v64.fpmax[0];
-  M->aux_vol = dalloc<double>(M, nv0 * 2, &err);
-  M->aux_face = dalloc<double>(M, nf0 * 2, &err);
+  M->aux_vol = dalloc<double>(M, nv0 * 3, &err);    // (y_h, y+, l_mix^2) per point
+  M->aux_face = dalloc<double>(M, nf0 * 3, &err);
   M->v64.nut_vol = dalloc<double>(M, nv0, &err);
   M->v64.nut_face = dalloc<double>(M, nf0, &err);
   if (M->has32) {
@@ -500,15 +509,26 @@ static dgw_status apply_vec(dgw_mesh_t M, int op, int prec, const void *u, void 
   if (!M || !u || !y) return set_error(DGW_EINVAL, std::string(name) + ": null argument");
   cudaStream_t s = (cudaStream_t)stream;
   if (prec == DGW_FP64) return cuda_check(launch_vector_op<double>(op, M->v64, (const double *)u, (double *)y, s), name);
-  if (prec == DGW_FP32) {
+  if (prec == DGW_FP32 && op != OP_DIV) {
     if (!M->has32) return set_error(DGW_EINVAL, std::string(name) + ": mesh built without FP32 tables");
     return cuda_check(launch_vector_op<float>(op, M->v32, (const float *)u, (float *)y, s), name);
   }
-  return set_error(DGW_EINVAL, std::string(name) + ": prec must be DGW_FP64 or DGW_FP32");
+  if (prec == DGW_DF64) {
+    if (M->P.geometry != 0 || (op != OP_DIV && op != OP_VISC && op != OP_CONV))
+      return set_error(DGW_EINVAL, std::string(name) + ": DGW_DF64 needs box cells (geometry 0)");
+    return cuda_check(launch_vector_op_df(op, M->v64, (const double *)u, (double *)y, s), name);
+  }
+  return set_error(DGW_EINVAL, std::string(name) + ": unsupported prec");
 }
 
 dgw_status dgw_apply_divergence(dgw_mesh_t M, const double *u, double *b, void *stream) {
   return apply_vec(M, OP_DIV, DGW_FP64, u, b, stream, "dgw_apply_divergence");
+}
+
+dgw_status dgw_apply_divergence_prec(dgw_mesh_t M, int prec, const double *u, double *b, void *stream) {
+  if (prec != DGW_FP64 && prec != DGW_DF64)
+    return set_error(DGW_EINVAL, "dgw_apply_divergence_prec: prec must be DGW_FP64 or DGW_DF64");
+  return apply_vec(M, OP_DIV, prec, u, b, stream, "dgw_apply_divergence_prec");
 }
 
 dgw_status dgw_apply_convective(dgw_mesh_t M, int prec, const void *u, void *y, void *stream) {

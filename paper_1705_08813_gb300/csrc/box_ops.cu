@@ -1,0 +1,966 @@
+// Degree-specialised DG operators on the box cells of the channel whose six neighbours are
+// standard cells (Sec. 4.2 weak forms, Sec. 4.4 sum factorisation); the enriched wall layers and
+// the rows next to them take the general kernel of ops.cu.
+//
+// On an axis-aligned box every integrand of the divergence and of the viscous term is a
+// polynomial of degree <= 2k per direction, which the k+1 Gauss points of these terms integrate
+// exactly. Their volume integrals are therefore Kronecker products of 1-D matrices over the
+// Gauss-Lobatto nodes, M_ij = (l_i, l_j), K_ij = (l_i', l_j'), A_ij = (l_i', l_j) (test
+// derivative, trial value) and B = A^T, with no interpolation to points; on the faces the traces
+// are the nodal values of the face layer (the end nodes of the Lobatto lines), normal derivatives
+// come from the end-point derivatives l_j'(0), l_j'(1), tangential ones from the nodal
+// differentiation matrix, and the face integrals are (M x M)-type products on the n x n face grid.
+// The result equals the Gauss-point evaluation up to rounding.
+//
+// Every kernel is templated on the storage type T of the vectors and the compute type R (T itself,
+// or df64 for FP64-accurate double-float arithmetic on the FP32 units with double vectors). A CTA
+// holds cpb consecutive cells of one row segment along x; each thread owns one line of one cell in
+// every pass (x-, y- then z-lines) and, in the face phase of direction d, the d-line through its
+// face node.
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "df64.cuh"
+#include "metric.cuh"
+#include "sumfac.cuh"
+
+namespace dgw {
+
+// 1-D tables of one degree on the Gauss-Lobatto nodes; Sc, Dc, wc: the convective point set
+// (floor(3k/2)+1 Gauss points), rows = points.
+template <typename R>
+struct VecConst {
+  R M[NMAX * NMAX];
+  R K[NMAX * NMAX];
+  R A[NMAX * NMAX];
+  R Dg[NMAX * NMAX];   // Dg[i * n + j] = l_j'(x_i) at the Lobatto nodes
+  R de[2][NMAX];       // l_j'(0), l_j'(1)
+  R Sc[QMAX * NMAX];
+  R Dc[QMAX * NMAX];
+  R wc[QMAX];
+};
+__constant__ VecConst<double> c_vec64[5];
+__constant__ VecConst<float> c_vec32[5];
+__constant__ VecConst<df64> c_vecdf[5];
+
+template <typename R>
+__device__ __forceinline__ const VecConst<R> &vconst(int k);
+template <>
+__device__ __forceinline__ const VecConst<double> &vconst<double>(int k) { return c_vec64[k - 1]; }
+template <>
+__device__ __forceinline__ const VecConst<float> &vconst<float>(int k) { return c_vec32[k - 1]; }
+template <>
+__device__ __forceinline__ const VecConst<df64> &vconst<df64>(int k) { return c_vecdf[k - 1]; }
+
+template <typename R>
+__device__ __forceinline__ R r_from_double(double x);
+template <>
+__device__ __forceinline__ double r_from_double<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float r_from_double<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ df64 r_from_double<df64>(double x) { return df_from(x); }
+
+// out = Mat in along a line (Mat n x n row-major, or its transpose)
+template <typename R, int n, bool TR = false>
+__device__ __forceinline__ void matvec(const R *Mat, const R (&in)[n], R (&out)[n]) {
+#pragma unroll
+  for (int r = 0; r < n; ++r) {
+    R s = r_zero<R>();
+#pragma unroll
+    for (int b = 0; b < n; ++b) s = r_fma(TR ? Mat[b * n + r] : Mat[r * n + b], in[b], s);
+    out[r] = s;
+  }
+}
+// out += c * Mat in
+template <typename R, int n, bool TR = false>
+__device__ __forceinline__ void matvec_acc(const R *Mat, R c, const R (&in)[n], R (&out)[n]) {
+#pragma unroll
+  for (int r = 0; r < n; ++r) {
+    R s = r_zero<R>();
+#pragma unroll
+    for (int b = 0; b < n; ++b) s = r_fma(TR ? Mat[b * n + r] : Mat[r * n + b], in[b], s);
+    out[r] = r_fma(c, s, out[r]);
+  }
+}
+
+template <typename R, int n>
+__device__ __forceinline__ void load_line(const R *p, int stride, R (&v)[n]) {
+#pragma unroll
+  for (int b = 0; b < n; ++b) v[b] = p[b * stride];
+}
+template <typename R, int n>
+__device__ __forceinline__ void store_line(R *p, int stride, const R (&v)[n]) {
+#pragma unroll
+  for (int b = 0; b < n; ++b) p[b * stride] = v[b];
+}
+
+// line of a pass: x-lines (base n l, stride 1), y-lines (base lr + n^2 lq, stride n), z-lines
+// (base l, stride n^2)
+template <int n>
+__device__ __forceinline__ void line_geom(int d, int l, int &base, int &stride) {
+  const int lr = l % n, lq = l / n;
+  if (d == 0) { base = n * l; stride = 1; }
+  else if (d == 1) { base = lr + n * n * lq; stride = n; }
+  else { base = l; stride = n * n; }
+}
+
+// Cells of one CTA: cpb consecutive cells of row j0 + (blockIdx / segments) % nrows, plane kz.
+struct BoxBlock {
+  int c0, i0, j, kz;
+};
+template <typename T>
+__device__ __forceinline__ BoxBlock box_block(const MeshView<T> &m, int cpb, int j0, int nrows) {
+  const int segs = m.nx / cpb;
+  const int b = blockIdx.x;
+  BoxBlock r;
+  r.i0 = (b % segs) * cpb;
+  r.j = j0 + (b / segs) % nrows;
+  r.kz = b / (segs * nrows);
+  r.c0 = r.i0 + m.nx * (r.j + m.ny * r.kz);
+  return r;
+}
+
+// The d-line of the neighbour across face (d, s) of cell c (component a, ncomp components per
+// cell): from shared memory when the neighbour is one of the CTA's cells, else from global memory.
+template <typename T, typename R, int n>
+__device__ __forceinline__ void neighbour_line(const R *U, const T *__restrict__ u, int nb, const BoxBlock &bk, int cpb,
+                                               int ncomp, int a, int base, int stride, R (&v)[n]) {
+  constexpr int n3 = n * n * n;
+  const int rel = nb - bk.c0;
+  if (rel >= 0 && rel < cpb) {
+    load_line<R, n>(U + (rel * ncomp + a) * n3 + base, stride, v);
+  } else {
+    const T *p = u + ((size_t)nb * ncomp + a) * n3 + base;
+#pragma unroll
+    for (int b = 0; b < n; ++b) v[b] = r_load<R>(p[b * stride]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Divergence b = -C(q, u) (Sec. 4.2): sum_d (d q / d x_d, u_d)_K - (q, {{u}}.n)_dK with {{u}} = u^-
+// on walls. Volume: V sum_d (1/h_d) (A_d x M x M) u_d. Faces (normal d, side s, sgn = 2s - 1):
+// -|F| sgn (M x M) {{u_d}} on the face layer.
+// ------------------------------------------------------------------------------------------------
+template <typename T, typename R, int K>
+__global__ void __launch_bounds__(128) box_div_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y, int cpb,
+                                                      int j0, int nrows) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *U = reinterpret_cast<R *>(smem_raw);   // cpb x 3 x n3
+  R *Y = U + cpb * 3 * n3;                   // cpb x n3
+  R *S = Y + cpb * n3;                       // cpb x 3 x n3 scratch
+  const VecConst<R> &C = vconst<R>(K);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const BoxBlock bk = box_block(m, cpb, j0, nrows);
+  for (int t = tid; t < cpb * 3 * n3; t += nt) U[t] = r_load<R>(u[(size_t)bk.c0 * 3 * n3 + t]);
+  const double hd[3] = {(double)m.hx, (double)m.hy[bk.j], (double)m.hz};
+  const double V = hd[0] * hd[1] * hd[2];
+  const R sx = r_from_double<R>(V / hd[0]), sy = r_from_double<R>(V / hd[1]), sz = r_from_double<R>(V / hd[2]);
+  __syncthreads();
+  const bool line = tid < cpb * n2;
+  const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
+  R *Uc = U + cl * 3 * n3, *Yc = Y + cl * n3, *Sc = S + cl * 3 * n3;
+  // x-lines: P0 = A_x u0, P1 = M_x u1, P2 = M_x u2
+  if (line) {
+    int base, st;
+    line_geom<n>(0, l, base, st);
+    R v[n], o[n];
+    load_line<R, n>(Uc + base, st, v);
+    matvec<R, n>(C.A, v, o);
+    store_line<R, n>(Sc + base, st, o);
+    load_line<R, n>(Uc + n3 + base, st, v);
+    matvec<R, n>(C.M, v, o);
+    store_line<R, n>(Sc + n3 + base, st, o);
+    load_line<R, n>(Uc + 2 * n3 + base, st, v);
+    matvec<R, n>(C.M, v, o);
+    store_line<R, n>(Sc + 2 * n3 + base, st, o);
+  }
+  __syncthreads();
+  // y-lines: W = sx M_y P0 + sy A_y P1, T = M_y P2
+  if (line) {
+    int base, st;
+    line_geom<n>(1, l, base, st);
+    R p0[n], p1[n], p2[n], w[n], t[n];
+    load_line<R, n>(Sc + base, st, p0);
+    load_line<R, n>(Sc + n3 + base, st, p1);
+    load_line<R, n>(Sc + 2 * n3 + base, st, p2);
+#pragma unroll
+    for (int r = 0; r < n; ++r) w[r] = r_zero<R>();
+    matvec_acc<R, n>(C.M, sx, p0, w);
+    matvec_acc<R, n>(C.A, sy, p1, w);
+    matvec<R, n>(C.M, p2, t);
+    store_line<R, n>(Sc + base, st, w);
+    store_line<R, n>(Sc + n3 + base, st, t);
+  }
+  __syncthreads();
+  // z-lines: y = M_z W + sz A_z T
+  if (line) {
+    int base, st;
+    line_geom<n>(2, l, base, st);
+    R w[n], t[n], o[n];
+    load_line<R, n>(Sc + base, st, w);
+    load_line<R, n>(Sc + n3 + base, st, t);
+    matvec<R, n>(C.M, w, o);
+    matvec_acc<R, n>(C.A, sz, t, o);
+    store_line<R, n>(Yc + base, st, o);
+  }
+  __syncthreads();
+  // faces: -|F| sgn (M x M) {{u_d}} on the layer of each face
+  R *F = S + cl * 4 * n2;   // [face s][stage][n2] (the volume scratch is free now)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int t1, t2;
+    face_axes(d, t1, t2);
+    const R area = r_from_double<R>(-V / hd[d]);
+    const int i1 = l % n, i2 = l / n;
+    int base, st;
+    line_geom<n>(d, l, base, st);
+    if (line) {
+      for (int s = 0; s < 2; ++s) {
+        const int c = bk.c0 + cl;
+        const int nb = neighbour(m, c, 2 * d + s);
+        const R own = Uc[d * n3 + base + (s ? n - 1 : 0) * st];
+        R avg = own;
+        if (nb >= 0) {
+          R v[n];
+          neighbour_line<T, R, n>(U, u, nb, bk, cpb, 3, d, base, st, v);
+          avg = r_half<R>() * (own + v[s ? 0 : n - 1]);
+        }
+        F[s * 2 * n2 + l] = (s ? area : -area) * avg;   // sgn(s) * (-|F|) * avg
+      }
+    }
+    __syncthreads();
+    if (line) {   // along t1
+      for (int s = 0; s < 2; ++s) {
+        R acc = r_zero<R>();
+#pragma unroll
+        for (int r = 0; r < n; ++r) acc = r_fma(C.M[i1 * n + r], F[s * 2 * n2 + r + n * i2], acc);
+        F[s * 2 * n2 + n2 + l] = acc;
+      }
+    }
+    __syncthreads();
+    if (line) {   // along t2, add to the layer
+      for (int s = 0; s < 2; ++s) {
+        R acc = r_zero<R>();
+#pragma unroll
+        for (int r = 0; r < n; ++r) acc = r_fma(C.M[i2 * n + r], F[s * 2 * n2 + n2 + i1 + n * r], acc);
+        Yc[base + (s ? n - 1 : 0) * st] += acc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < cpb * n3; t += nt) y[(size_t)bk.c0 * n3 + t] = r_store<T>(Y[t]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Viscous term -F^nu(v, u) of standard cells (eq. viscous_multiscale with no enrichment on either
+// side of any face): (eps(v), 2 nu eps(u))_K + on each face (1/2 F^nu(v), [[u]]) - (v, {{F^nu(u)}}.n)
+// + (v, tau_F nu [[u]].n), tau_F = max of the two cells, 10 tau on walls, mirror state on walls.
+// Volume for output a: nu V [ sum_d (1 + delta_ad)/h_d^2 (K_d x M x M) u_a
+//                             + sum_{b != a} 1/(h_a h_b) (A_b x B_a x M) u_b ].
+// ------------------------------------------------------------------------------------------------
+template <typename T, typename R, int K>
+__global__ void __launch_bounds__(128) box_visc_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y, int cpb,
+                                                       int j0, int nrows) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  constexpr int WS = (4 * n3 > 36 * n2) ? 4 * n3 : 36 * n2;   // scratch per cell
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *U = reinterpret_cast<R *>(smem_raw);   // cpb x 3 x n3
+  R *Y = U + cpb * 3 * n3;                   // cpb x 3 x n3
+  R *S = Y + cpb * 3 * n3;                   // cpb x WS
+  __shared__ R sc[64];                       // row scalars (one division each, done once per CTA)
+  const VecConst<R> &C = vconst<R>(K);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const BoxBlock bk = box_block(m, cpb, j0, nrows);
+  for (int t = tid; t < cpb * 3 * n3; t += nt) U[t] = r_load<R>(u[(size_t)bk.c0 * 3 * n3 + t]);
+  for (int ti = tid; ti < 51; ti += nt) {
+    // [5a + 0..2]: nu V (1 + delta_ad) / h_d^2; [5a + 3, 4]: nu V / (h_a h_b) for the two other
+    // components b; [15 + 12 d + ...]: 1/h_d, 2/h_d, 1/h_t1, 1/h_t2, then per face s: 1/h'_d (the
+    // neighbour's spacing), -nu sgn |F| / 2, nu sgn |F| / 2, tau_F nu |F|
+    const double nu = (double)m.visc;
+    const double hy = (double)m.hy[bk.j];
+    auto hd = [&](int e) { return e == 0 ? (double)m.hx : (e == 1 ? hy : (double)m.hz); };
+    const double V = (double)m.hx * hy * (double)m.hz;
+    double v = 0.0;
+    if (ti < 15) {
+      const int a = ti / 5, k = ti % 5;
+      if (k < 3) v = nu * V * (a == k ? 2.0 : 1.0) / (hd(k) * hd(k));
+      else {
+        const int b = k == 3 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2);
+        v = nu * V / (hd(a) * hd(b));
+      }
+    } else {
+      const int d = (ti - 15) / 12, k = (ti - 15) % 12;
+      const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      const double area = V / hd(d);
+      if (k == 0) v = 1.0 / hd(d);
+      else if (k == 1) v = 2.0 / hd(d);
+      else if (k == 2) v = 1.0 / hd(t1);
+      else if (k == 3) v = 1.0 / hd(t2);
+      else {
+        const int s = k & 1;
+        const double sgn = s ? 1.0 : -1.0;
+        const int jn = bk.j + (s ? 1 : -1);
+        const bool wall = d == 1 && (jn < 0 || jn >= m.ny);
+        if (k < 6) v = 1.0 / ((d == 1 && !wall) ? (double)m.hy[jn] : hd(d));
+        else if (k < 8) v = -0.5 * nu * sgn * area;
+        else if (k < 10) v = 0.5 * nu * sgn * area;
+        else {
+          const double tc = (double)m.tau[bk.c0];
+          const double tauF = wall ? 10.0 * tc : (d == 1 ? fmax(tc, (double)m.tau[bk.c0 + (s ? m.nx : -m.nx)]) : tc);
+          v = tauF * nu * area;
+        }
+      }
+    }
+    sc[ti] = r_from_double<R>(v);
+  }
+  __syncthreads();
+  const bool line = tid < cpb * n2;
+  const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
+  R *Uc = U + cl * 3 * n3, *Yc = Y + cl * 3 * n3, *Sc = S + cl * WS;
+
+  // ---- volume, one output component per sweep (x-, y-, z-lines)
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;   // the other two components
+    // diagonal coefficients nu V (1 + delta_ad) / h_d^2 and cross coefficients nu V / (h_a h_b)
+    const R cd0 = sc[5 * a], cd1 = sc[5 * a + 1], cd2 = sc[5 * a + 2];
+    const R cx1 = sc[5 * a + 3], cx2 = sc[5 * a + 4];
+    // 1-D factor of cross term (a <- b) along direction e: A where e = b, B (= A^T) where e = a,
+    // M otherwise
+    auto xfac = [&](int b, int e, const R (&in)[n], R (&out)[n]) {
+      if (e == b) matvec<R, n>(C.A, in, out);
+      else if (e == a) matvec<R, n, true>(C.A, in, out);
+      else matvec<R, n>(C.M, in, out);
+    };
+    if (line) {   // x: S0 = K_x u_a, S1 = M_x u_a, S2 = X_x u_b1, S3 = X_x u_b2
+      int base, st;
+      line_geom<n>(0, l, base, st);
+      R v[n], o[n];
+      load_line<R, n>(Uc + a * n3 + base, st, v);
+      matvec<R, n>(C.K, v, o);
+      store_line<R, n>(Sc + base, st, o);
+      matvec<R, n>(C.M, v, o);
+      store_line<R, n>(Sc + n3 + base, st, o);
+      load_line<R, n>(Uc + b1 * n3 + base, st, v);
+      xfac(b1, 0, v, o);
+      store_line<R, n>(Sc + 2 * n3 + base, st, o);
+      load_line<R, n>(Uc + b2 * n3 + base, st, v);
+      xfac(b2, 0, v, o);
+      store_line<R, n>(Sc + 3 * n3 + base, st, o);
+    }
+    __syncthreads();
+    if (line) {   // y: W = cd0 M_y S0 + cd1 K_y S1, T = M_y S1, cross arrays
+      int base, st;
+      line_geom<n>(1, l, base, st);
+      R s0[n], s1[n], s2[n], s3[n], w[n], t[n], x1[n], x2[n];
+      load_line<R, n>(Sc + base, st, s0);
+      load_line<R, n>(Sc + n3 + base, st, s1);
+      load_line<R, n>(Sc + 2 * n3 + base, st, s2);
+      load_line<R, n>(Sc + 3 * n3 + base, st, s3);
+#pragma unroll
+      for (int r = 0; r < n; ++r) w[r] = r_zero<R>();
+      matvec_acc<R, n>(C.M, cd0, s0, w);
+      matvec_acc<R, n>(C.K, cd1, s1, w);
+      matvec<R, n>(C.M, s1, t);
+      xfac(b1, 1, s2, x1);
+      xfac(b2, 1, s3, x2);
+      // fold the cross terms whose z-factor is M into W (scaled), keep the others apart
+#pragma unroll
+      for (int r = 0; r < n; ++r) {
+        x1[r] = cx1 * x1[r];
+        x2[r] = cx2 * x2[r];
+      }
+      if (a == 2) {   // both cross terms take B along z
+#pragma unroll
+        for (int r = 0; r < n; ++r) x1[r] = x1[r] + x2[r];
+      } else {        // b1 takes M along z, b2 = 2 takes A along z
+#pragma unroll
+        for (int r = 0; r < n; ++r) w[r] = w[r] + x1[r];
+      }
+      store_line<R, n>(Sc + base, st, w);
+      store_line<R, n>(Sc + n3 + base, st, t);
+      store_line<R, n>(Sc + 2 * n3 + base, st, a == 2 ? x1 : x2);
+    }
+    __syncthreads();
+    if (line) {   // z: y_a = M_z W + cd2 K_z T + (B_z | A_z) X
+      int base, st;
+      line_geom<n>(2, l, base, st);
+      R w[n], t[n], x[n], o[n], o2[n];
+      load_line<R, n>(Sc + base, st, w);
+      load_line<R, n>(Sc + n3 + base, st, t);
+      load_line<R, n>(Sc + 2 * n3 + base, st, x);
+      matvec<R, n>(C.M, w, o);
+      matvec_acc<R, n>(C.K, cd2, t, o);
+      if (a == 2) matvec<R, n, true>(C.A, x, o2);
+      else matvec<R, n>(C.A, x, o2);
+#pragma unroll
+      for (int r = 0; r < n; ++r) o[r] = o[r] + o2[r];
+      store_line<R, n>(Yc + a * n3 + base, st, o);
+    }
+    __syncthreads();
+  }
+
+  // ---- faces, one direction (both faces) at a time
+  R *FU = Sc;               // [s][n2] own trace of u_d
+  R *FN = FU + 2 * n2;      // [s][n2] neighbour trace of u_d
+  R *FC = FN + 2 * n2;      // [s][8][n2] coefficients: C0 (3), Cn (3), Ct1, Ct2
+  R *FP = FC + 16 * n2;     // [s][8][n2] after the t1-pass
+  const int c = bk.c0 + cl;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int t1, t2;
+    face_axes(d, t1, t2);
+    const int i1 = l % n, i2 = l / n;
+    int base, st;
+    line_geom<n>(d, l, base, st);
+    const R *scd = sc + 15 + 12 * d;
+    // own and neighbour traces and physical normal derivatives at this face node (both faces)
+    R Uo[2][3], Nb[2][3], G[2][3], Gn[2][3];
+    int nbs[2];
+    if (line) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) nbs[s] = neighbour(m, c, 2 * d + s);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        R v[n];
+        load_line<R, n>(Uc + a * n3 + base, st, v);
+        const R ih = scd[0];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          Uo[s][a] = v[s ? n - 1 : 0];
+          R g = r_zero<R>();
+#pragma unroll
+          for (int b = 0; b < n; ++b) g = r_fma(C.de[s][b], v[b], g);
+          G[s][a] = ih * g;
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (nbs[s] >= 0) {
+            R w[n];
+            neighbour_line<T, R, n>(U, u, nbs[s], bk, cpb, 3, a, base, st, w);
+            Nb[s][a] = w[s ? 0 : n - 1];
+            R g = r_zero<R>();
+#pragma unroll
+            for (int b = 0; b < n; ++b) g = r_fma(C.de[1 - s][b], w[b], g);
+            Gn[s][a] = scd[4 + s] * g;
+          } else {   // mirror state on a no-slip wall: u+ = -u-, grad u+ = grad u-
+            Nb[s][a] = -Uo[s][a];
+            Gn[s][a] = G[s][a];
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        FU[s * n2 + l] = Uo[s][d];
+        FN[s * n2 + l] = Nb[s][d];
+      }
+    }
+    __syncthreads();
+    if (line) {
+      const R ih1 = scd[2], ih2 = scd[3];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        // tangential derivatives of the normal component's traces (wall: the neighbour's gradient
+        // is the own one)
+        R To1 = r_zero<R>(), To2 = r_zero<R>(), Tn1 = r_zero<R>(), Tn2 = r_zero<R>();
+#pragma unroll
+        for (int r = 0; r < n; ++r) {
+          To1 = r_fma(C.Dg[i1 * n + r], FU[s * n2 + r + n * i2], To1);
+          To2 = r_fma(C.Dg[i2 * n + r], FU[s * n2 + i1 + n * r], To2);
+          Tn1 = r_fma(C.Dg[i1 * n + r], FN[s * n2 + r + n * i2], Tn1);
+          Tn2 = r_fma(C.Dg[i2 * n + r], FN[s * n2 + i1 + n * r], Tn2);
+        }
+        To1 = ih1 * To1; To2 = ih2 * To2; Tn1 = ih1 * Tn1; Tn2 = ih2 * Tn2;
+        if (nbs[s] < 0) { Tn1 = To1; Tn2 = To2; }
+        const R hc = scd[6 + s];    // consistency
+        const R ac = scd[8 + s];    // adjoint
+        const R pc = scd[10 + s];   // penalty
+        R *Fc = FC + s * 8 * n2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const R To = a == t1 ? To1 : To2, Tn = a == t1 ? Tn1 : Tn2;
+          const R So = G[s][a] + (a == d ? G[s][d] : To);
+          const R Sn = Gn[s][a] + (a == d ? Gn[s][d] : Tn);
+          const R J = Uo[s][a] - Nb[s][a];
+          Fc[a * n2 + l] = r_fma(hc, So + Sn, pc * J);
+          Fc[(3 + a) * n2 + l] = scd[a == d ? 1 : 0] * (ac * J);
+        }
+        Fc[6 * n2 + l] = ih1 * (ac * (Uo[s][t1] - Nb[s][t1]));
+        Fc[7 * n2 + l] = ih2 * (ac * (Uo[s][t2] - Nb[s][t2]));
+      }
+    }
+    __syncthreads();
+    if (line) {   // along t1: M for C0, Cn, Ct2; A for Ct1
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const R *Fc = FC + s * 8 * n2;
+        R *Fp = FP + s * 8 * n2;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const R *Mat = k == 6 ? C.A : C.M;
+          R acc = r_zero<R>();
+#pragma unroll
+          for (int r = 0; r < n; ++r) acc = r_fma(Mat[i1 * n + r], Fc[k * n2 + r + n * i2], acc);
+          Fp[k * n2 + l] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    if (line) {   // along t2: M (A for Ct2), then add to the own d-line
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const R *Fp = FP + s * 8 * n2;
+        R z[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const R *Mat = k == 7 ? C.A : C.M;
+          R acc = r_zero<R>();
+#pragma unroll
+          for (int r = 0; r < n; ++r) acc = r_fma(Mat[i2 * n + r], Fp[k * n2 + i1 + n * r], acc);
+          z[k] = acc;
+        }
+        const int lay = s ? n - 1 : 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          R *ya = Yc + a * n3 + base;
+#pragma unroll
+          for (int mm = 0; mm < n; ++mm) ya[mm * st] = r_fma(C.de[s][mm], z[3 + a], ya[mm * st]);
+          ya[lay * st] = ya[lay * st] + z[a];
+        }
+        Yc[d * n3 + base + lay * st] = Yc[d * n3 + base + lay * st] + (z[6] + z[7]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < cpb * 3 * n3; t += nt) y[(size_t)bk.c0 * 3 * n3 + t] = r_store<T>(Y[t]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Convective term F^c(v, u) of standard cells (Sec. 4.2): -(grad v, u x u)_K + (v, F*.n)_dK with the
+// local Lax-Friedrichs flux F* = 1/2 (u^- (u^-.n) + u^+ (u^+.n)) + Lambda/2 (u^- - u^+),
+// Lambda = max(2|u^-.n|, 2|u^+.n|), u^+ = -u^- on walls. The integrand is not a polynomial of the
+// nodal degree (the flux has |.| and max), so it is evaluated at the operator's own
+// q = floor(3k/2) + 1 Gauss points per direction (Sec. 4.4), by sum factorisation in point space:
+// values of the three components at the q^3 points, the nine products u_a u_d, integration against
+// d phi / d x_d; on each face the traces of both sides at q x q points, the flux, integration back
+// to the face layer. Passes assign whole lines to threads (a thread may take several lines).
+// ------------------------------------------------------------------------------------------------
+template <int n, int q>
+struct ConvPlan {
+  static constexpr int n2 = n * n, n3 = n2 * n, q2 = q * q, q3 = q2 * q;
+  static constexpr int A1 = (3 * q * n2 > 3 * q2 * n) ? 3 * q * n2 : 3 * q2 * n;   // fwd x / bwd z (one output)
+  static constexpr int A2 = (3 * q2 * n > 2 * q * n2) ? 3 * q2 * n : 2 * q * n2;   // fwd y / bwd y (one output)
+  static constexpr int FACE = 12 * n2 + 12 * q * n + 12 * q2 + 6 * q2 + 6 * q * n;
+  static constexpr int WORK = (3 * q3 + A1 + A2 > FACE) ? 3 * q3 + A1 + A2 : FACE;
+  static constexpr int PER_CELL = 3 * n3 + 3 * n3 + WORK;   // U, Y, work
+};
+
+template <typename T, typename R, int K>
+__global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y, int cpb,
+                                                       int j0, int nrows) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  constexpr int q = (3 * K) / 2 + 1, q2 = q * q, q3 = q2 * q;
+  using P = ConvPlan<n, q>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *U = reinterpret_cast<R *>(smem_raw);   // cpb x 3 x n3
+  R *Y = U + cpb * 3 * n3;                   // cpb x 3 x n3
+  R *W = Y + cpb * 3 * n3;                   // cpb x WORK
+  __shared__ R sc[6];                        // -V/h_d (volume), V/h_d (face area)
+  const VecConst<R> &C = vconst<R>(K);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const BoxBlock bk = box_block(m, cpb, j0, nrows);
+  for (int t = tid; t < cpb * 3 * n3; t += nt) {
+    U[t] = r_load<R>(u[(size_t)bk.c0 * 3 * n3 + t]);
+    Y[t] = r_zero<R>();
+  }
+  if (tid < 6) {
+    const double hy = (double)m.hy[bk.j];
+    const double V = (double)m.hx * hy * (double)m.hz;
+    const int d = tid % 3;
+    const double h = d == 0 ? (double)m.hx : (d == 1 ? hy : (double)m.hz);
+    sc[tid] = r_from_double<R>((tid < 3 ? -1.0 : 1.0) * V / h);
+  }
+  __syncthreads();
+  auto Wc = [&](int cl) { return W + cl * P::WORK; };
+  // ---- volume: values at the points (x: n -> q, then y, then z)
+  for (int t = tid; t < cpb * 3 * n2; t += nt) {
+    const int cl = t / (3 * n2), r = t - cl * 3 * n2, a = r / n2, l = r - a * n2;
+    R v[n];
+    load_line<R, n>(U + (cl * 3 + a) * n3 + n * l, 1, v);
+    R *out = Wc(cl) + 3 * q3 + a * q * n2 + q * l;
+#pragma unroll
+    for (int i = 0; i < q; ++i) {
+      R acc = r_zero<R>();
+#pragma unroll
+      for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
+      out[i] = acc;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < cpb * 3 * q * n; t += nt) {   // lines (i0, i2), i0 < q, i2 < n
+    const int cl = t / (3 * q * n), r = t - cl * 3 * q * n, a = r / (q * n), l = r - a * q * n;
+    const int i0 = l % q, i2 = l / q;
+    R v[n];
+    load_line<R, n>(Wc(cl) + 3 * q3 + a * q * n2 + i0 + q * n * i2, q, v);
+    R *out = Wc(cl) + 3 * q3 + P::A1 + a * q2 * n + i0 + q2 * i2;
+#pragma unroll
+    for (int i = 0; i < q; ++i) {
+      R acc = r_zero<R>();
+#pragma unroll
+      for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
+      out[q * i] = acc;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < cpb * 3 * q2; t += nt) {   // lines (i0, i1)
+    const int cl = t / (3 * q2), r = t - cl * 3 * q2, a = r / q2, l = r - a * q2;
+    R v[n];
+    load_line<R, n>(Wc(cl) + 3 * q3 + P::A1 + a * q2 * n + l, q2, v);
+    R *out = Wc(cl) + a * q3 + l;
+#pragma unroll
+    for (int i = 0; i < q; ++i) {
+      R acc = r_zero<R>();
+#pragma unroll
+      for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
+      out[q2 * i] = acc;
+    }
+  }
+  __syncthreads();
+  // ---- volume: -sum_d (V/h_d) sum_points w (d phi / d xi_d) u_a u_d, one output component at a time
+  for (int a = 0; a < 3; ++a) {
+    for (int t = tid; t < cpb * q2; t += nt) {   // z-lines (i0, i1): F_ad along z, integrate along z
+      const int cl = t / q2, l = t - cl * q2, i0 = l % q, i1 = l / q;
+      const R *V = Wc(cl);
+      R z0[n], z1[n], z2[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) { z0[b] = r_zero<R>(); z1[b] = r_zero<R>(); z2[b] = r_zero<R>(); }
+      const R w01 = C.wc[i0] * C.wc[i1];
+#pragma unroll
+      for (int j = 0; j < q; ++j) {
+        const int pt = l + q2 * j;
+        const R ua = V[a * q3 + pt];
+        const R wa = (w01 * C.wc[j]) * ua;
+        const R f0 = sc[0] * (wa * V[pt]);            // F_a0 = -(V/h_x) w u_a u_x
+        const R f1 = sc[1] * (wa * V[q3 + pt]);
+        const R f2 = sc[2] * (wa * V[2 * q3 + pt]);
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          z0[b] = r_fma(C.Dc[j * n + b], f2, z0[b]);   // D_z^T F_a2
+          z1[b] = r_fma(C.Sc[j * n + b], f1, z1[b]);   // S_z^T F_a1
+          z2[b] = r_fma(C.Sc[j * n + b], f0, z2[b]);   // S_z^T F_a0
+        }
+      }
+      R *Z = Wc(cl) + 3 * q3;
+      store_line<R, n>(Z + l, q2, z0);
+      store_line<R, n>(Z + q2 * n + l, q2, z1);
+      store_line<R, n>(Z + 2 * q2 * n + l, q2, z2);
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * q * n; t += nt) {   // y-lines (i0, m): Y0 = S_y^T Z0 + D_y^T Z1, Y1 = S_y^T Z2
+      const int cl = t / (q * n), l = t - cl * q * n, i0 = l % q, mz = l / q;
+      const R *Z = Wc(cl) + 3 * q3;
+      R y0[n], y1[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) { y0[b] = r_zero<R>(); y1[b] = r_zero<R>(); }
+#pragma unroll
+      for (int j = 0; j < q; ++j) {
+        const int pt = i0 + q * j + q2 * mz;
+        const R za = Z[pt], zb = Z[q2 * n + pt], zc = Z[2 * q2 * n + pt];
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          y0[b] = r_fma(C.Sc[j * n + b], za, r_fma(C.Dc[j * n + b], zb, y0[b]));
+          y1[b] = r_fma(C.Sc[j * n + b], zc, y1[b]);
+        }
+      }
+      R *Yb = Wc(cl) + 3 * q3 + P::A1;
+      store_line<R, n>(Yb + i0 + q * n * mz, q, y0);
+      store_line<R, n>(Yb + q * n2 + i0 + q * n * mz, q, y1);
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * n2; t += nt) {   // x-lines (b, m): y_a = S_x^T Y0 + D_x^T Y1
+      const int cl = t / n2, l = t - cl * n2;
+      const R *Yb = Wc(cl) + 3 * q3 + P::A1 + q * l;
+      R o[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) o[b] = r_zero<R>();
+#pragma unroll
+      for (int j = 0; j < q; ++j) {
+        const R ya = Yb[j], yb = Yb[q * n2 + j];
+#pragma unroll
+        for (int b = 0; b < n; ++b) o[b] = r_fma(C.Sc[j * n + b], ya, r_fma(C.Dc[j * n + b], yb, o[b]));
+      }
+      R *yo = Y + (cl * 3 + a) * n3 + n * l;
+#pragma unroll
+      for (int b = 0; b < n; ++b) yo[b] = o[b];
+    }
+    __syncthreads();
+  }
+  // ---- faces, one direction (both faces) at a time: slots k = (s * 2 + side) * 3 + a
+  for (int d = 0; d < 3; ++d) {
+    int t1, t2;
+    face_axes(d, t1, t2);
+    // layer values of both sides (side 0: own layer at xi_d = s; side 1: the neighbour's opposite
+    // layer; walls leave side 1 unused, the mirror state is taken at the flux)
+    for (int t = tid; t < cpb * 12 * n2; t += nt) {
+      const int cl = t / (12 * n2), r = t - cl * 12 * n2, k = r / n2, l = r - k * n2;
+      const int a = k % 3, side = (k / 3) & 1, s = k / 6;
+      const int i1 = l % n, i2 = l / n;
+      R val = r_zero<R>();
+      if (side == 0) {
+        val = U[(cl * 3 + a) * n3 + node_index(d, t1, t2, s ? n - 1 : 0, i1, i2, n)];
+      } else {
+        const int nb = neighbour(m, bk.c0 + cl, 2 * d + s);
+        if (nb >= 0) {
+          const int idx = node_index(d, t1, t2, s ? 0 : n - 1, i1, i2, n);
+          const int rel = nb - bk.c0;
+          val = (rel >= 0 && rel < cpb) ? U[(rel * 3 + a) * n3 + idx] : r_load<R>(u[((size_t)nb * 3 + a) * n3 + idx]);
+        }
+      }
+      Wc(cl)[k * n2 + l] = val;
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * 12 * n; t += nt) {   // along t1: n -> q
+      const int cl = t / (12 * n), r = t - cl * 12 * n, k = r / n, i2 = r - k * n;
+      R v[n];
+      load_line<R, n>(Wc(cl) + k * n2 + n * i2, 1, v);
+      R *out = Wc(cl) + 12 * n2 + k * q * n + q * i2;
+#pragma unroll
+      for (int i = 0; i < q; ++i) {
+        R acc = r_zero<R>();
+#pragma unroll
+        for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
+        out[i] = acc;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * 12 * q; t += nt) {   // along t2: n -> q
+      const int cl = t / (12 * q), r = t - cl * 12 * q, k = r / q, j1 = r - k * q;
+      R v[n];
+      load_line<R, n>(Wc(cl) + 12 * n2 + k * q * n + j1, q, v);
+      R *out = Wc(cl) + 12 * n2 + 12 * q * n + k * q2 + j1;
+#pragma unroll
+      for (int i = 0; i < q; ++i) {
+        R acc = r_zero<R>();
+#pragma unroll
+        for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
+        out[q * i] = acc;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * 2 * q2; t += nt) {   // local Lax-Friedrichs flux at the face points
+      const int cl = t / (2 * q2), r = t - cl * 2 * q2, s = r / q2, pt = r - s * q2;
+      const R *Tr = Wc(cl) + 12 * n2 + 12 * q * n;
+      const bool wall = neighbour(m, bk.c0 + cl, 2 * d + s) < 0;
+      R um[3], up[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        um[a] = Tr[((s * 2 + 0) * 3 + a) * q2 + pt];
+        up[a] = wall ? -um[a] : Tr[((s * 2 + 1) * 3 + a) * q2 + pt];
+      }
+      const R umd = d == 0 ? um[0] : (d == 1 ? um[1] : um[2]);
+      const R upd = d == 0 ? up[0] : (d == 1 ? up[1] : up[2]);
+      const R unm = s ? umd : -umd, unp = s ? upd : -upd;
+      // Lambda / 2 = max(|u^-.n|, |u^+.n|)
+      const R lam = r_abs_ge(unm, unp) ? r_abs(unm) : r_abs(unp);
+      const R wq = sc[3 + d] * (C.wc[pt % q] * C.wc[pt / q]);
+      R *Fl = Wc(cl) + 12 * n2 + 12 * q * n + 12 * q2;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        // 1/2 (u^-_a (u^-.n) + u^+_a (u^+.n)) + (Lambda/2)(u^-_a - u^+_a), Lambda/2 = max(|u^-.n|, |u^+.n|)
+        const R F = r_fma(lam, um[a] - up[a], r_half<R>() * r_fma(um[a], unm, up[a] * unp));
+        Fl[(s * 3 + a) * q2 + pt] = wq * F;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * 6 * q; t += nt) {   // back along t2: q -> n
+      const int cl = t / (6 * q), r = t - cl * 6 * q, k = r / q, j1 = r - k * q;
+      const R *Fl = Wc(cl) + 12 * n2 + 12 * q * n + 12 * q2 + k * q2;
+      R o[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) o[b] = r_zero<R>();
+#pragma unroll
+      for (int j = 0; j < q; ++j) {
+        const R f = Fl[j1 + q * j];
+#pragma unroll
+        for (int b = 0; b < n; ++b) o[b] = r_fma(C.Sc[j * n + b], f, o[b]);
+      }
+      R *Bt = Wc(cl) + 12 * n2 + 12 * q * n + 18 * q2 + k * q * n;
+      store_line<R, n>(Bt + j1, q, o);
+    }
+    __syncthreads();
+    for (int t = tid; t < cpb * 6 * n; t += nt) {   // back along t1: q -> n, add to the face layer
+      const int cl = t / (6 * n), r = t - cl * 6 * n, k = r / n, i2 = r - k * n;
+      const int s = k / 3, a = k % 3;
+      const R *Bt = Wc(cl) + 12 * n2 + 12 * q * n + 18 * q2 + k * q * n + q * i2;
+      R o[n];
+#pragma unroll
+      for (int b = 0; b < n; ++b) o[b] = r_zero<R>();
+#pragma unroll
+      for (int j = 0; j < q; ++j) {
+        const R f = Bt[j];
+#pragma unroll
+        for (int b = 0; b < n; ++b) o[b] = r_fma(C.Sc[j * n + b], f, o[b]);
+      }
+      R *ya = Y + (cl * 3 + a) * n3;
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        const int idx = node_index(d, t1, t2, s ? n - 1 : 0, b, i2, n);
+        ya[idx] = ya[idx] + o[b];
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < cpb * 3 * n3; t += nt) y[(size_t)bk.c0 * 3 * n3 + t] = r_store<T>(Y[t]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+
+cudaError_t box_vec_constants_init() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  static VecConst<double> h64[5];
+  static VecConst<float> h32[5];
+  static VecConst<df64> hdf[5];
+  std::memset(h64, 0, sizeof(h64));
+  for (int k = 1; k <= 5; ++k) {
+    VecConst<double> &V = h64[k - 1];
+    Basis<double> B;
+    fill_basis<double>(k, (3 * k) / 2 + 1, k + 1, &B);
+    const int n = k + 1, q = B.q[QSET_LIN];
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        double mv = 0.0, kv = 0.0, av = 0.0;
+        for (int t = 0; t < q; ++t) {
+          const double w = B.w[QSET_LIN][t];
+          mv += w * B.S[QSET_LIN][t * n + a] * B.S[QSET_LIN][t * n + b];
+          kv += w * B.D[QSET_LIN][t * n + a] * B.D[QSET_LIN][t * n + b];
+          av += w * B.D[QSET_LIN][t * n + a] * B.S[QSET_LIN][t * n + b];
+        }
+        V.M[a * n + b] = mv;
+        V.K[a * n + b] = kv;
+        V.A[a * n + b] = av;
+      }
+    double z[NMAX];
+    lobatto_nodes(n, z);
+    for (int i = 0; i < n; ++i) {
+      double val[NMAX], der[NMAX];
+      lagrange_row(n, z, z[i], val, der);
+      for (int j = 0; j < n; ++j) V.Dg[i * n + j] = der[j];
+    }
+    for (int s = 0; s < 2; ++s)
+      for (int j = 0; j < n; ++j) V.de[s][j] = B.dend[s][j];
+    const int qc = B.q[QSET_CONV];
+    for (int t = 0; t < qc; ++t) {
+      for (int j = 0; j < n; ++j) {
+        V.Sc[t * n + j] = B.S[QSET_CONV][t * n + j];
+        V.Dc[t * n + j] = B.D[QSET_CONV][t * n + j];
+      }
+      V.wc[t] = B.w[QSET_CONV][t];
+    }
+  }
+  auto split = [](double v) { const float h = (float)v; return df64{h, (float)(v - (double)h)}; };
+  const double *src = reinterpret_cast<const double *>(h64);
+  float *d32 = reinterpret_cast<float *>(h32);
+  df64 *ddf = reinterpret_cast<df64 *>(hdf);
+  static_assert(sizeof(VecConst<double>) == 2 * sizeof(VecConst<float>), "layout");
+  static_assert(sizeof(VecConst<double>) == sizeof(VecConst<df64>), "layout");
+  for (size_t i = 0; i < sizeof(h64) / sizeof(double); ++i) {
+    d32[i] = (float)src[i];
+    ddf[i] = split(src[i]);
+  }
+  e = cudaMemcpyToSymbol(c_vec64, h64, sizeof(h64));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_vec32, h32, sizeof(h32));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_vecdf, hdf, sizeof(hdf));
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+// cells per CTA: the largest power of two dividing nx with cpb * lines <= 128 and cpb <= 8
+static int vec_cpb(int nx, int lines) {
+  int c = 1;
+  while (c * 2 <= 8 && (c * 2) * lines <= 128 && nx % (c * 2) == 0) c *= 2;
+  return c;
+}
+
+template <typename T, typename R, int K, int OP>
+static cudaError_t launch_box_op_k(const MeshView<T> &m, const T *u, T *y, int j0, int nrows, cudaStream_t s) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n, q = (3 * K) / 2 + 1;
+  int cpb, threads;
+  size_t per_cell;
+  if (OP == OP_CONV) {
+    cpb = vec_cpb(m.nx, q * q);
+    threads = 128;
+    per_cell = ConvPlan<n, q>::PER_CELL;
+  } else {
+    cpb = vec_cpb(m.nx, n2);
+    threads = ((cpb * n2 + 31) / 32) * 32;
+    per_cell = OP == OP_DIV ? 7 * n3 : 6 * n3 + ((4 * n3 > 36 * n2) ? 4 * n3 : 36 * n2);
+  }
+  const size_t sm = sizeof(R) * per_cell * cpb;
+  auto kern = OP == OP_DIV ? box_div_kernel<T, R, K> : (OP == OP_VISC ? box_visc_kernel<T, R, K> : box_conv_kernel<T, R, K>);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
+  const int blocks = (m.nx / cpb) * nrows * m.nz;
+  note_launch();
+  kern<<<blocks, threads, sm, s>>>(m, u, y, cpb, j0, nrows);
+  return cudaGetLastError();
+}
+
+template <typename T, typename R>
+cudaError_t launch_box_vec_rows(int op, const MeshView<T> &m, const T *u, T *y, int j0, int nrows, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  cudaError_t e = box_vec_constants_init();
+  if (e != cudaSuccess) return e;
+  if (op == OP_DIV) {
+    switch (m.n1) {
+      case 2: return launch_box_op_k<T, R, 1, OP_DIV>(m, u, y, j0, nrows, s);
+      case 3: return launch_box_op_k<T, R, 2, OP_DIV>(m, u, y, j0, nrows, s);
+      case 4: return launch_box_op_k<T, R, 3, OP_DIV>(m, u, y, j0, nrows, s);
+      case 5: return launch_box_op_k<T, R, 4, OP_DIV>(m, u, y, j0, nrows, s);
+      case 6: return launch_box_op_k<T, R, 5, OP_DIV>(m, u, y, j0, nrows, s);
+    }
+  } else if (op == OP_VISC) {
+    switch (m.n1) {
+      case 2: return launch_box_op_k<T, R, 1, OP_VISC>(m, u, y, j0, nrows, s);
+      case 3: return launch_box_op_k<T, R, 2, OP_VISC>(m, u, y, j0, nrows, s);
+      case 4: return launch_box_op_k<T, R, 3, OP_VISC>(m, u, y, j0, nrows, s);
+      case 5: return launch_box_op_k<T, R, 4, OP_VISC>(m, u, y, j0, nrows, s);
+      case 6: return launch_box_op_k<T, R, 5, OP_VISC>(m, u, y, j0, nrows, s);
+    }
+  } else if (op == OP_CONV) {
+    switch (m.n1) {
+      case 2: return launch_box_op_k<T, R, 1, OP_CONV>(m, u, y, j0, nrows, s);
+      case 3: return launch_box_op_k<T, R, 2, OP_CONV>(m, u, y, j0, nrows, s);
+      case 4: return launch_box_op_k<T, R, 3, OP_CONV>(m, u, y, j0, nrows, s);
+      case 5: return launch_box_op_k<T, R, 4, OP_CONV>(m, u, y, j0, nrows, s);
+      case 6: return launch_box_op_k<T, R, 5, OP_CONV>(m, u, y, j0, nrows, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_box_vec_rows<double, double>(int, const MeshView<double> &, const double *, double *, int,
+                                                         int, cudaStream_t);
+template cudaError_t launch_box_vec_rows<float, float>(int, const MeshView<float> &, const float *, float *, int, int,
+                                                       cudaStream_t);
+template cudaError_t launch_box_vec_rows<double, df64>(int, const MeshView<double> &, const double *, double *, int,
+                                                       int, cudaStream_t);
+
+}  // namespace dgw

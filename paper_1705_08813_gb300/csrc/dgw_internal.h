@@ -54,6 +54,10 @@ struct MeshView {
   int nef;            // enrichment coefficients per component and wall cell: 8 (l = 1) or 1 (l = 0)
   int full_q;         // 1: enriched cells use the q_wall set in every direction (faces: both tangential)
   int geo;            // GEO_BOX or GEO_CURVED
+  // rows [plain_lo, plain_hi) hold box cells whose six neighbours are standard cells (no enrichment
+  // slot in the row or the rows above and below): the degree-specialised kernels of box_ops.cu
+  // take them, the general kernel the other rows (plain_lo = plain_hi = ny: all general)
+  int plain_lo = 0, plain_hi = 0;
   T hx, hz;
   const T *hy;        // [ny] row heights (boxes)
   const T *tau;       // [nc] penalty tau_IP per cell
@@ -127,7 +131,7 @@ struct dgw_mesh {
   int *proj_err = nullptr;
   int proj_nvec = 0;                // vectors proj_P has room for
   bool mass_factor_valid = false;   // proj_A holds the Cholesky factors of the current space
-  double *aux_vol = nullptr, *aux_face = nullptr;   // (y_h, y+) at linear-set points
+  double *aux_vol = nullptr, *aux_face = nullptr;   // (y_h, y+, l_mix^2) at linear-set points
   double *dye_dev = nullptr;
   double *diag64 = nullptr;     // Jacobi diagonal of the Laplace operator
   float *diag32 = nullptr;
@@ -224,6 +228,14 @@ cudaError_t curved_constants_init();
 template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s,
                              const LapEpi<T> *epi = nullptr);
+// the same operator with double vectors and double-float arithmetic on the box rows the
+// specialised kernels take (the general kernel computes the other rows in FP64); OP_DIV, OP_VISC,
+// OP_CONV
+cudaError_t launch_vector_op_df(int op, const MeshView<double> &m, const double *u, double *y, cudaStream_t s);
+struct df64;
+// degree-specialised box-cell kernels on rows [j0, j0 + nrows) (box_ops.cu); R = compute type
+template <typename T, typename R>
+cudaError_t launch_box_vec_rows(int op, const MeshView<T> &m, const T *u, T *y, int j0, int nrows, cudaStream_t s);
 cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s);
 cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, cudaStream_t s);
 cudaError_t launch_set_tau_nodes(dgw_mesh *M, const double *tau_nodes, cudaStream_t s);

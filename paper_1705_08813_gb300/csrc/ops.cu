@@ -20,6 +20,7 @@
 // Every sum-factorisation phase is batched over the velocity components, over both faces normal
 // to one direction and over both sides of those faces, so one barrier separates phases that each
 // carry enough independent outputs to occupy the CTA (about 35 barriers per cell).
+#include "df64.cuh"
 #include "metric.cuh"
 #include "sumfac.cuh"
 
@@ -232,9 +233,10 @@ __host__ __device__ inline int plan_qin(const MeshView<T> &m, int qset) {
 
 // NC > 0: the node count per direction as a compile-time constant (the curved Laplacian, whose point
 // sets are all k+1 Gauss points, is instantiated per degree so the pass index arithmetic folds).
+// One CTA per cell of rows [0, rb) and [rt, ny) (rb = rt = ny: every row), x fastest.
 template <typename T, int OP, int GEO, int NC = 0>
 __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y,
-                                                        LapEpi<T> epi) {
+                                                        LapEpi<T> epi, int rb, int rt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Basis<T> &B = *reinterpret_cast<Basis<T> *>(smem_raw);
   T *S0 = reinterpret_cast<T *>(smem_raw + ((sizeof(Basis<T>) + 15) / 16) * 16);
@@ -249,7 +251,12 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   const VecPlan L = vec_plan(OP, CURVED, n, NC > 0 ? NC : plan_qin(m, qset), NC > 0 ? NC : m.q[QSET_WALL]);
   const int n3 = L.n3;
   T *uo = S0 + L.uo, *r = S0 + L.r, *eo = S0 + L.eo, *re = S0 + L.re, *un = S0 + L.fUn, *en = S0 + L.en;
-  const int c = blockIdx.x;
+  int c;
+  {
+    const int nr = rb + (m.ny - rt), b = blockIdx.x;
+    const int i = b % m.nx, r = (b / m.nx) % nr, kz = b / (m.nx * nr);
+    c = i + m.nx * ((r < rb ? r : rt + (r - rb)) + m.ny * kz);
+  }
   const int ec = OP == OP_LAP ? -1 : m.enr[c];
   const bool enr_c = ec >= 0;
   const T nu = m.visc;
@@ -1030,8 +1037,13 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   }
 }
 
+// rows [0, rb) and [rt, ny) (default: every row)
 template <typename T, int OP, int GEO, int NC = 0>
-static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
+static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi, int rb = -1,
+                              int rt = -1) {
+  if (rb < 0) rb = rt = m.ny;
+  const int nr = rb + (m.ny - rt);
+  if (nr <= 0) return cudaSuccess;
   const int qset = OP == OP_CONV ? QSET_CONV : QSET_LIN;
   const VecPlan L = vec_plan(OP, GEO == GEO_CURVED, m.n1, plan_qin(m, qset), m.q[QSET_WALL]);
   const size_t sm = ((sizeof(Basis<T>) + 15) / 16) * 16 + (size_t)L.total * sizeof(T);
@@ -1046,16 +1058,25 @@ static cudaError_t launch_vec(const MeshView<T> &m, const T *u, T *y, cudaStream
     attr_set = true;
   }
   note_launch();
-  note_dofs((OP == OP_DIV || OP == OP_LAP) ? m.np : m.nu);
   LapEpi<T> e{};
   e.mode = LAP_PLAIN;
   if (epi) e = *epi;
-  vector_op_kernel<T, OP, GEO, NC><<<m.nc, 128, sm, s>>>(m, u, y, e);
+  vector_op_kernel<T, OP, GEO, NC><<<m.nx * nr * m.nz, 128, sm, s>>>(m, u, y, e, rb, rt);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
+  note_dofs((op == OP_DIV || op == OP_LAP) ? m.np : m.nu);
+  if (m.geo == GEO_BOX && (op == OP_DIV || op == OP_VISC || op == OP_CONV) && m.plain_hi > m.plain_lo) {
+    // rows of standard cells with standard neighbours: degree-specialised kernels; the rows of and
+    // next to the enriched layers: the general kernel
+    cudaError_t e = launch_box_vec_rows<T, T>(op, m, u, y, m.plain_lo, m.plain_hi - m.plain_lo, s);
+    if (e != cudaSuccess) return e;
+    if (op == OP_DIV) return launch_vec<T, OP_DIV, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
+    if (op == OP_CONV) return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
+    return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
+  }
   if (m.geo == GEO_CURVED) {
     switch (op) {
       case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s, nullptr);
@@ -1087,6 +1108,18 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
 
 template cudaError_t launch_vector_op<double>(int, const MeshView<double> &, const double *, double *, cudaStream_t,
                                               const LapEpi<double> *);
+
+cudaError_t launch_vector_op_df(int op, const MeshView<double> &m, const double *u, double *y, cudaStream_t s) {
+  if (m.geo != GEO_BOX || (op != OP_DIV && op != OP_VISC && op != OP_CONV)) return cudaErrorNotSupported;
+  note_dofs(op == OP_DIV ? m.np : m.nu);
+  if (m.plain_hi > m.plain_lo) {
+    cudaError_t e = launch_box_vec_rows<double, df64>(op, m, u, y, m.plain_lo, m.plain_hi - m.plain_lo, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (op == OP_DIV) return launch_vec<double, OP_DIV, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
+  if (op == OP_CONV) return launch_vec<double, OP_CONV, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
+  return launch_vec<double, OP_VISC, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
+}
 template cudaError_t launch_vector_op<float>(int, const MeshView<float> &, const float *, float *, cudaStream_t,
                                              const LapEpi<float> *);
 

@@ -144,24 +144,46 @@ __device__ __forceinline__ bool face_xi(const WallCellData &w, const Basis<doubl
   return true;
 }
 
+// Squared mixing length l_mix^2 = (kappa y_DES (1 - exp(-y+/A+)))^2 (eq. lmix) with the smooth DES
+// limiter y_DES = (y_h^-6 + (C_DES h)^-6)^(-1/6) (eq. ydes), h = wall-normal cell width / (k+1). It
+// depends on the geometry and tau_w only, so it is tabulated with the wall tables and the eddy
+// viscosity update multiplies it by the strain of the current field.
+__device__ __forceinline__ double lmix_sq(double yh, double yp, double hdes) {
+  double ydes = 0.0;
+  if (yh > 0.0) ydes = pow(pow(yh, -kBetaDes) + pow(hdes, -kBetaDes), -1.0 / kBetaDes);
+  const double lmix = kKappa * ydes * (1.0 - exp(-yp / kAplus));
+  return lmix * lmix;
+}
+
+// aux records per linear-set point: (y_h, y+, l_mix^2)
+constexpr int kAux = 3;
+
 __global__ void wall_table_kernel(WallCellData w, const Basis<double> *Bg, int qs, int nvol, int fpmax,
-                                  double *vol, double *face, double *aux_vol, double *aux_face) {
+                                  double *vol, double *face, double *aux_vol, double *aux_face, const double *dye,
+                                  int k) {
   const Basis<double> &B = *Bg;
   const int e = blockIdx.x;
   const int c = w.enr_cell[e];
+  const double hdes = dye ? kCdes * dye[e] / (k + 1) : 0.0;
   for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
     double xi[3], Ji[3][3], out[WT], aux[2];
     vol_xi(w, B, c, qs, t, xi, Ji);
     wall_point(w, e, xi, Ji, out, aux);
     for (int r = 0; r < WT; ++r) vol[((size_t)e * nvol + t) * WT + r] = out[r];
-    if (aux_vol) { aux_vol[((size_t)e * nvol + t) * 2] = aux[0]; aux_vol[((size_t)e * nvol + t) * 2 + 1] = aux[1]; }
+    if (aux_vol) {
+      double *a = aux_vol + ((size_t)e * nvol + t) * kAux;
+      a[0] = aux[0]; a[1] = aux[1]; a[2] = lmix_sq(aux[0], aux[1], hdes);
+    }
   }
   for (int t = threadIdx.x; t < 6 * fpmax; t += blockDim.x) {
     const int f = t / fpmax, pt = t % fpmax;
     double xi[3], Ji[3][3], out[WT] = {0, 0, 0, 0}, aux[2] = {0, 0};
     if (face_xi(w, B, c, qs, f, pt, xi, Ji)) wall_point(w, e, xi, Ji, out, aux);
     for (int r = 0; r < WT; ++r) face[((size_t)e * 6 * fpmax + t) * WT + r] = out[r];
-    if (aux_face) { aux_face[((size_t)e * 6 * fpmax + t) * 2] = aux[0]; aux_face[((size_t)e * 6 * fpmax + t) * 2 + 1] = aux[1]; }
+    if (aux_face) {
+      double *a = aux_face + ((size_t)e * 6 * fpmax + t) * kAux;
+      a[0] = aux[0]; a[1] = aux[1]; a[2] = lmix_sq(aux[0], aux[1], hdes);
+    }
   }
 }
 
@@ -177,7 +199,6 @@ __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, i
   __shared__ double cu[24];
   for (int t = threadIdx.x; t < 24; t += blockDim.x) cu[t] = u_enr[(size_t)e * 3 * nef + (nef == 8 ? t : t >> 3)];
   __syncthreads();
-  const double hdes = kCdes * dye[e] / (k + 1);
   auto nut_at = [&](const double xi[3], const double Ji[3][3], const double *wt, const double *aux) -> double {
     double N[8], dN[8][3];
     q1_weights(xi, N, dN);
@@ -196,17 +217,13 @@ __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, i
         const double eps = 0.5 * (G[a][d] + G[d][a]);
         e2 += eps * eps;
       }
-    const double yh = aux[0], yp = aux[1];
-    double ydes = 0.0;
-    if (yh > 0.0) ydes = pow(pow(yh, -kBetaDes) + pow(hdes, -kBetaDes), -1.0 / kBetaDes);
-    const double lmix = kKappa * ydes * (1.0 - exp(-yp / kAplus));
-    return lmix * lmix * sqrt(2.0 * e2);
+    return aux[2] * sqrt(2.0 * e2);   // l_mix^2 |eps| (eq. mix), l_mix^2 tabulated per point
   };
   for (int t = threadIdx.x; t < nvol; t += blockDim.x) {
     double xi[3], Ji[3][3];
     vol_xi(w, B, c, QSET_LIN, t, xi, Ji);
     const size_t i = (size_t)e * nvol + t;
-    const double v = nut_at(xi, Ji, wt_vol + i * WT, aux_vol + i * 2);
+    const double v = nut_at(xi, Ji, wt_vol + i * WT, aux_vol + i * kAux);
     nut_vol[i] = v;
     if (nut_vol32) nut_vol32[i] = (float)v;
   }
@@ -215,7 +232,7 @@ __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, i
     double xi[3], Ji[3][3];
     const size_t i = (size_t)e * 6 * fpmax + t;
     double v = 0.0;
-    if (face_xi(w, B, c, QSET_LIN, f, pt, xi, Ji)) v = nut_at(xi, Ji, wt_face + i * WT, aux_face + i * 2);
+    if (face_xi(w, B, c, QSET_LIN, f, pt, xi, Ji)) v = nut_at(xi, Ji, wt_face + i * WT, aux_face + i * kAux);
     nut_face[i] = v;
     if (nut_face32) nut_face32[i] = (float)v;
   }
@@ -247,7 +264,7 @@ cudaError_t launch_wall_tables(dgw_mesh *M, cudaStream_t s) {
     wall_table_kernel<<<M->ne, 128, 0, s>>>(w, M->v64.basis, qs, M->v64.nvol[cls], M->v64.fpmax[cls],
                                             const_cast<double *>(M->v64.wt_vol[cls]),
                                             const_cast<double *>(M->v64.wt_face[cls]), cls == 0 ? M->aux_vol : nullptr,
-                                            cls == 0 ? M->aux_face : nullptr);
+                                            cls == 0 ? M->aux_face : nullptr, M->dye_dev, M->P.degree);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -380,14 +397,14 @@ cudaError_t launch_wall_shear(dgw_mesh *M, const double *u, double *tau_nodes, c
 }
 
 // Switch-off of the wall model (Sec. 3.2): enriched cell e is on iff some point of the velocity point
-// set of the wall-nearest cell of its column has y+ >= yp_off (aux_vol holds (y_h, y+) per point of
+// set of the wall-nearest cell of its column has y+ >= yp_off (aux_vol holds (y_h, y+, l_mix^2) per point of
 // every enriched cell, switched on or not). Writes the operators' view enr[c].
 __global__ void switch_kernel(const double *__restrict__ aux_vol, int nvol, const int *__restrict__ wslot,
                               const int *__restrict__ enr_cell, int ne, double yp_off, int *__restrict__ enr) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-    const double *a = aux_vol + (size_t)wslot[e] * nvol * 2;
+    const double *a = aux_vol + (size_t)wslot[e] * nvol * kAux;
     double ymax = 0.0;
-    for (int t = 0; t < nvol; ++t) ymax = fmax(ymax, a[2 * t + 1]);
+    for (int t = 0; t < nvol; ++t) ymax = fmax(ymax, a[kAux * t + 1]);
     enr[enr_cell[e]] = ymax < yp_off ? -1 : e;
   }
 }

@@ -18,7 +18,7 @@ STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -
 # every symbol include/dgw.h declares
 EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
-           "dgw_apply_convective", "dgw_apply_viscous", "dgw_pressure_solve", "dgw_last_error",
+           "dgw_apply_convective", "dgw_apply_viscous", "dgw_apply_divergence_prec", "dgw_pressure_solve", "dgw_last_error",
            "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
            "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.dgw_update_eddy_viscosity.argtypes = [vp, vp, vp]
     lib.dgw_apply_laplace.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_apply_divergence.argtypes = [vp, vp, vp, vp]
+    lib.dgw_apply_divergence_prec.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_apply_convective.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_apply_viscous.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_pressure_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
@@ -215,20 +216,27 @@ class Mesh:
                                           _stream(stream)))
         return y
 
-    def divergence(self, u, b, stream=None):
+    def divergence(self, u, b, stream=None, prec=None):
+        """b = -C(q, u) (FP64; prec=DGW_DF64: double-float arithmetic on the box rows)."""
         import torch
-        _check(self.lib.dgw_apply_divergence(self.h, _ptr(u, torch.float64, self.n_u, "u"),
-                                             _ptr(b, torch.float64, self.n_p, "b"), _stream(stream)))
+        if prec is None or prec == DGW_FP64:
+            _check(self.lib.dgw_apply_divergence(self.h, _ptr(u, torch.float64, self.n_u, "u"),
+                                                 _ptr(b, torch.float64, self.n_p, "b"), _stream(stream)))
+        else:
+            _check(self.lib.dgw_apply_divergence_prec(self.h, prec, _ptr(u, torch.float64, self.n_u, "u"),
+                                                      _ptr(b, torch.float64, self.n_p, "b"), _stream(stream)))
         return b
 
-    def convective(self, u, y, stream=None):
-        _check(self.lib.dgw_apply_convective(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
-                                             _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
+    def convective(self, u, y, stream=None, prec=None):
+        _check(self.lib.dgw_apply_convective(self.h, self._prec(u) if prec is None else prec,
+                                             _ptr(u, None, self.n_u, "u"), _ptr(y, u.dtype, self.n_u, "y"),
+                                             _stream(stream)))
         return y
 
-    def viscous(self, u, y, stream=None):
-        _check(self.lib.dgw_apply_viscous(self.h, self._prec(u), _ptr(u, None, self.n_u, "u"),
-                                          _ptr(y, u.dtype, self.n_u, "y"), _stream(stream)))
+    def viscous(self, u, y, stream=None, prec=None):
+        _check(self.lib.dgw_apply_viscous(self.h, self._prec(u) if prec is None else prec,
+                                          _ptr(u, None, self.n_u, "u"), _ptr(y, u.dtype, self.n_u, "y"),
+                                          _stream(stream)))
         return y
 
     @property
