@@ -214,30 +214,27 @@ def laplace_flops_per_cell(k, curved=False):
 
 def vector_flops_per_cell(op, k):
     """Floating-point operations (2 per multiply-add) of one standard box cell of the divergence,
-    convective and viscous operators, counted for sum factorisation at the operator's own Gauss
-    points (Sec. 4.4: k+1 per direction, floor(3k/2)+1 for the convective term), n = k + 1 nodes:
-      values of one scalar at the points    F = q n^3 + q^2 n^2 + q^3 n
-      gradients of one scalar               G = 2 q n^3 + 3 q^2 n^2 + 3 q^3 n
-      integration against grad phi          B = 2 q n^3 + 3 q^2 n^2 + 3 q^3 n
-    faces (six per cell, each side's own integrals): traces interpolated from the face layer,
-    normal derivatives n^3 per component, flux at q^2 points, integration back.
-      divergence  3F + B + 3 q^3 (point scaling)  + 6 [2 (q n^2 + q^2 n) + q^2 + (q^2 n + q n^2)]
-      convective  3F + 3B + 18 q^3 (u x u)        + 6 [6 (q n^2 + q^2 n) + 30 q^2 + 3 (q^2 n + q n^2)]
-      viscous     3G + 3B + 30 q^3 (strain)       + 6 [6 (n^3 + 3 q n^2 + 4 q^2 n) + 60 q^2
-                                                        + 3 (3 q^2 n + 2 q n^2 + n^3)]"""
+    convective and viscous operators, n = k + 1 nodes, counted for the algorithms the box kernels
+    use. The divergence and the viscous term have polynomial integrands that the k+1 Gauss points
+    integrate exactly, so they are Kronecker products of 1-D n x n matrices on the nodes:
+      divergence  8 n^4 (volume) + 12 n^3 (faces: averages, two face-grid passes)
+      viscous     36 n^4 (volume: 12 line passes per output component)
+                  + 174 n^3 (faces: normal and tangential derivatives, two face-grid passes of
+                  eight coefficient arrays, normal-derivative test terms) + 180 n^2 (coefficients)
+    The convective term is evaluated at q = floor(3k/2)+1 Gauss points (Sec. 4.4):
+      values F = q n^3 + q^2 n^2 + q^3 n per component, integration B = 3 q^3 n + 3 q^2 n^2 + 2 q n^3
+      per output component, 9 q^3 for the products, and per face direction 12 (q n^2 + q^2 n)
+      (traces of both sides), 40 q^2 (flux), 6 (q^2 n + q n^2) (integration back)."""
     n = k + 1
-    q = (3 * k) // 2 + 1 if op == "convective" else n
-    F = q * n ** 3 + q * q * n * n + q ** 3 * n
-    G = 2 * q * n ** 3 + 3 * q * q * n * n + 3 * q ** 3 * n
-    B = 2 * q * n ** 3 + 3 * q * q * n * n + 3 * q ** 3 * n
     if op == "divergence":
-        fma = 3 * F + B + 6 * (2 * (q * n * n + q * q * n) + (q * q * n + q * n * n))
-        return 2 * fma + 3 * q ** 3 + 6 * q * q
-    if op == "convective":
-        fma = 3 * F + 3 * B + 6 * (6 * (q * n * n + q * q * n) + 3 * (q * q * n + q * n * n))
-        return 2 * fma + 18 * q ** 3 + 6 * 30 * q * q
-    fma = 3 * G + 3 * B + 6 * (6 * (n ** 3 + 3 * q * n * n + 4 * q * q * n) + 3 * (3 * q * q * n + 2 * q * n * n + n ** 3))
-    return 2 * fma + 30 * q ** 3 + 6 * 60 * q * q
+        return 2 * (8 * n ** 4 + 12 * n ** 3)
+    if op == "viscous":
+        return 2 * (36 * n ** 4 + 174 * n ** 3) + 180 * n * n
+    q = (3 * k) // 2 + 1
+    F = q * n ** 3 + q * q * n * n + q ** 3 * n
+    B = 3 * q ** 3 * n + 3 * q * q * n * n + 2 * q * n ** 3
+    fma = 3 * F + 3 * B + 3 * (12 * (q * n * n + q * q * n) + 6 * (q * q * n + q * n * n))
+    return 2 * fma + 9 * q ** 3 + 3 * 40 * q * q
 
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
@@ -359,8 +356,14 @@ def run_gpu(args):
     dom = max(dofs_ops, key=lambda o: per_op[o]["ms"])
     geo = "GEO_CURVED" if curved else "GEO_BOX"
     opname = {"divergence": "OP_DIV", "convective": "OP_CONV", "viscous": "OP_VISC"}
-    kname = ((f"curved_laplace_kernel<double,{w.k}>" if curved else f"laplace_box_kernel<double,{w.k}>")
-             if dom == "laplace" else f"vector_op_kernel<double,{opname[dom]},{geo}>")
+    boxname = {"divergence": "box_div_kernel", "convective": "box_conv_kernel", "viscous": "box_visc_kernel"}
+    if dom == "laplace":
+        kname = f"curved_laplace_kernel<double,{w.k}>" if curved else f"laplace_box_kernel<double,double,{w.k}>"
+    elif curved:
+        kname = f"vector_op_kernel<double,{opname[dom]},GEO_CURVED>"
+    else:
+        kname = (f"{boxname[dom]}<double,double,{w.k}> (standard rows) + vector_op_kernel<double,{opname[dom]},GEO_BOX> "
+                 "(rows of and next to the enriched layers)")
     roofline = {"kernel": kname, "bound": "alu", "achieved": per_op[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": per_op[dom]["fp64_frac"],
                 "traffic": args.traffic_bytes,
@@ -391,6 +394,43 @@ def run_gpu(args):
                     "achieved": ach32, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach32 / peaks["hbm_gbs"],
                     "fp32_flop_frac": nc * laplace_flops_per_cell(w.k, curved) / (lap32_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
 
+    # the same step with every apply in double-float arithmetic on the FP32 units (DGW_DF64: double
+    # vectors, FP64-accurate; the rows of and next to the enriched layers stay in FP64), box cells
+    df64_step = None
+    if not curved:
+        DF = dgw.DGW_DF64
+        dsteps, dops = [], {o: [] for o in ops}
+        def dstep(timed):
+            for o in ops:
+                if timed:
+                    ev[o][0].record(stream)
+                if o == "eddy_viscosity":
+                    m.update_eddy_viscosity(ud)
+                elif o == "laplace":
+                    m.laplace(pd, y_lap, prec=DF)
+                elif o == "divergence":
+                    m.divergence(ud, b_div, prec=DF)
+                elif o == "convective":
+                    m.convective(ud, y_conv, prec=DF)
+                else:
+                    m.viscous(ud, y_visc, prec=DF)
+                if timed:
+                    ev[o][1].record(stream)
+        for _ in range(3):
+            dstep(False)
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            dstep(True)
+            torch.cuda.synchronize()
+            for o in ops:
+                dops[o].append(ev[o][0].elapsed_time(ev[o][1]))
+            dsteps.append(ev[ops[0]][0].elapsed_time(ev[ops[-1]][1]))
+        dms = statistics.mean(dsteps)
+        df64_step = {"value": dofs_step / (dms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": dms,
+                     "dtype": "df64 (double vectors, FP32-pair arithmetic)",
+                     "per_op_ms": {o: statistics.mean(dops[o]) for o in ops}}
+        step(False)   # restore the FP64 outputs used below
+
     # the same Laplacian with double vectors in double-float arithmetic on the FP32 units (FP64-accurate
     # emulation) against the native FP64 apply, each timed alone after an L2 flush (box cells only)
     emulation = None
@@ -412,7 +452,7 @@ def run_gpu(args):
         msdf = t_alone(lambda: m.laplace(pd, ydf, prec=dgw.DGW_DF64))
         diff = float(torch.linalg.norm(ydf - y_lap) / torch.linalg.norm(y_lap))
         fl = nc * laplace_flops_per_cell(w.k)
-        emulation = {"kernel": f"laplace_box_kernel<double,df64,{w.k}>", "fp64_ms": ms64, "df64_ms": msdf,
+        emulation = {"kernel": f"laplace_box_kernel<double,df64,{w.k}> vs laplace_box_kernel<double,double,{w.k}>", "fp64_ms": ms64, "df64_ms": msdf,
                      "speedup": ms64 / msdf, "rel_diff_vs_fp64": diff,
                      "df64_gdofs": m.n_p / (msdf * 1e-3) / 1e9,
                      "fp64_equiv_tflops": fl / (msdf * 1e-3) / 1e12,
@@ -466,7 +506,7 @@ def run_gpu(args):
                            "step": "nu_t update + FP64 Laplace, divergence, convective, viscous applies",
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
                 "per_op": per_op, "dof_applies_per_step": dofs_step, "solves": solves,
-                "roofline": roofline, "fp32_laplace": fp32_laplace, "df64_emulation": emulation,
+                "roofline": roofline, "fp32_laplace": fp32_laplace, "df64_emulation": emulation, "df64_step": df64_step,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches1 - launches0), "launches_before_timed": int(launches0),
                 "wall_s": t_wall}
