@@ -240,6 +240,21 @@ typedef struct {
 dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const dgw_solve_opts *opts,
                               dgw_solve_info *info, void *stream);
 
+/* Mixed-precision solves (mode 1 of dgw_pressure_solve) of ncols right-hand sides on one mesh, run
+ * as one block: up to 8 columns share every launch (the FP32 operator, one captured V-cycle over the
+ * block, the FP64 operator of the refinement), dot products are kept per column in a fixed order, so
+ * each column's result does not depend on the other columns (the same bits alone or in any block).
+ * When ncols > 8, further columns join the block as columns finish (between refinement rounds).
+ * b[c], p[c]: device pointers to n_p doubles each (host arrays of ncols pointers); b is projected to
+ * zero mean internally, p is returned with zero mean; infos[c] per column (iterations: inner FP32
+ * iterations of that column; ms: host time from the column's admission to its completion;
+ * dof_applies: the block's applications divided evenly). opts->mode must be 1. Box cells only
+ * (geometry 0) and meshes whose coarsest multigrid level is solved densely; otherwise DGW_EINVAL.
+ * The block workspace (8 columns) is allocated on first use and kept with the mesh. Synchronises
+ * `stream`. DGW_ENOTCONV if some column reached max_iter. */
+dgw_status dgw_pressure_solve_batch(dgw_mesh_t mesh, int ncols, const double *const *b, double *const *p,
+                                    const dgw_solve_opts *opts, dgw_solve_info *infos, void *stream);
+
 /* Pressure solve that allocates nothing, for callers that cannot let a library allocate device
  * memory at solve time: code whose device memory belongs to a framework's caching allocator or
  * to a budget fixed at start-up (an allocation outside that pool can fail or exhaust it), and

@@ -542,10 +542,12 @@ dgw_status dgw_apply_viscous(dgw_mesh_t M, int prec, const void *u, void *y, voi
 }  // extern "C"
 
 void dgw_solver_free(dgw_mesh *M);
+void dgw_batch_free(dgw_mesh *M);
 
 namespace dgw {
 static void free_mesh(dgw_mesh *M) {
   if (!M) return;
+  dgw_batch_free(M);
   dgw_solver_free(M);
   dgw_helm_free(M);
   for (void *p : M->allocs) cudaFree(p);

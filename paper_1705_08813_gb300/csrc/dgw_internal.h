@@ -89,6 +89,7 @@ struct MeshView {
 
 // One multigrid level (a nested coarser channel mesh with the same degree).
 struct Level;
+struct Batch;
 
 struct MeshHost;
 
@@ -137,6 +138,8 @@ struct dgw_mesh {
   float *diag32 = nullptr;
   struct dgw_solver *solver = nullptr;   // lazily built solver workspace and multigrid hierarchy
   struct dgw_helm *helm = nullptr;       // lazily built Helmholtz (GMRES) workspace
+  dgw::Batch *batch = nullptr;           // lazily built block solver (batched mixed-precision solves)
+  int batch_cheb = 0;                    // its Chebyshev degree
 };
 
 namespace dgw {
@@ -200,6 +203,8 @@ void bump_point(const dgw_mesh_params &P, int nx, int ny, double a0, double a1, 
 //   LAP_CHEB  Chebyshev step d = (first ? 0 : c1 d) + c2 D^-1 (b - t), xout = x + d (xout != x:
 //             neighbouring cells still read x; y is not written).
 enum { LAP_PLAIN = 0, LAP_RESIDUAL = 1, LAP_CHEB = 2 };
+//   ncols > 1 (boxes): the vectors hold ncols columns of np values each (dinv is shared), one
+//             launch applies the operator to every column (gridDim.y = ncols).
 template <typename T>
 struct LapEpi {
   int mode;
@@ -209,6 +214,7 @@ struct LapEpi {
   T *xout;
   T c1, c2;
   int first;
+  int ncols;
 };
 
 // kernels (launched by api.cu)

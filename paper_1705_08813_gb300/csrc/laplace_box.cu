@@ -160,6 +160,14 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
   const int c0 = blockIdx.x * cpb;
   const int i0 = c0 % m.nx, j = (c0 / m.nx) % m.ny, kz = c0 / (m.nx * m.ny);
   const bool has_ym = j > 0, has_yp = j < m.ny - 1, ext_x = m.nx > cpb;
+  if (blockIdx.y > 0) {   // column blockIdx.y of a block of vectors (the diagonal dinv is shared)
+    const size_t co = (size_t)blockIdx.y * m.np;
+    p += co;
+    if (y) y += co;
+    if (epi.b) epi.b += co;
+    if (epi.d) epi.d += co;
+    if (epi.xout) epi.xout += co;
+  }
   // ---- stage the inputs
   {
     const size_t plane = (size_t)m.nx * m.ny;
@@ -383,15 +391,17 @@ static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, const La
     attr = true;
   }
   const int threads = ((cpb * n * n + 31) / 32) * 32;
+  const int ncols = epi.ncols > 1 ? epi.ncols : 1;
   note_launch();
-  note_dofs(m.np);
-  laplace_box_kernel<T, R, K><<<m.nc / cpb, threads, sm, s>>>(m, p, y, cpb, epi);
+  note_dofs(m.np * ncols);
+  laplace_box_kernel<T, R, K><<<dim3(m.nc / cpb, ncols), threads, sm, s>>>(m, p, y, cpb, epi);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_laplace_epi(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
   if (epi.mode == LAP_CHEB && epi.xout == p) return cudaErrorInvalidValue;   // neighbours read p
+  if (epi.ncols > 1 && m.geo == GEO_CURVED) return cudaErrorNotSupported;      // columns: boxes only
   if (m.geo == GEO_CURVED) {   // per-point metrics: the table-driven kernel, else the general one
     if (m.lvol && m.lface) return launch_curved_laplace<T>(m, p, y, epi, s);
     return launch_vector_op<T>(OP_LAP, m, p, y, s, &epi);

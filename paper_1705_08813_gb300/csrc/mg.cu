@@ -29,8 +29,12 @@ constexpr long kDenseMax = 2400;       // coarsest systems up to this size are s
 // vector kernels (templated on the level precision; reductions accumulate in double)
 // ------------------------------------------------------------------------------------------
 
+// column blockIdx.y of a block of vectors (n values each); partial sums per column
 template <typename T>
 __global__ void mg_dot_partial(const T *__restrict__ a, const T *__restrict__ b, long n, double *__restrict__ partial) {
+  a += (size_t)blockIdx.y * n;
+  if (b) b += (size_t)blockIdx.y * n;
+  partial += (size_t)blockIdx.y * gridDim.x;
   double s = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     s += b ? (double)a[i] * (double)b[i] : (double)a[i];
@@ -45,7 +49,10 @@ __global__ void mg_dot_partial(const T *__restrict__ a, const T *__restrict__ b,
   }
 }
 
+// one warp per column (blockIdx.x); the column's scalars are out[column * MS_COUNT + slot]
 __global__ void mg_dot_finish(const double *__restrict__ partial, int np, double *out, int slot) {
+  partial += (size_t)blockIdx.x * np;
+  out += (size_t)blockIdx.x * 8;
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) s += partial[i];
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
@@ -54,12 +61,14 @@ __global__ void mg_dot_finish(const double *__restrict__ partial, int np, double
 
 constexpr int MG_RED = 152;
 
+// per column c < ncols: sc[c * MS_COUNT + slot] = sum_i a_ci b_ci (b null: sum_i a_ci)
 template <typename T>
-static void mg_reduce(const T *a, const T *b, long n, double *partial, double *sc, int slot, cudaStream_t s) {
+static void mg_reduce(const T *a, const T *b, long n, double *partial, double *sc, int slot, cudaStream_t s,
+                      int ncols = 1) {
   note_launch();
-  mg_dot_partial<T><<<MG_RED, 256, 0, s>>>(a, b, n, partial);
+  mg_dot_partial<T><<<dim3(MG_RED, ncols), 256, 0, s>>>(a, b, n, partial);
   note_launch();
-  mg_dot_finish<<<1, 32, 0, s>>>(partial, MG_RED, sc, slot);
+  mg_dot_finish<<<ncols, 32, 0, s>>>(partial, MG_RED, sc, slot);
 }
 
 static inline int mg_grid(long n) {
@@ -67,13 +76,16 @@ static inline int mg_grid(long n) {
   return (int)std::min<long>(std::max<long>(g, 1), 152 * 8);
 }
 
-// slots of the level scalars
+// slots of the level scalars (MS_COUNT per column; mg_dot_finish strides columns by 8)
 enum { MS_RZ = 0, MS_RZNEW, MS_DQ, MS_SUM, MS_COUNT = 8 };
+static_assert(MS_COUNT == 8, "mg_dot_finish column stride");
 
 // Chebyshev step: r = b - t (t = A x); d = c1 d + c2 D^-1 r; x += d (first: d = c2 D^-1 r)
 template <typename T>
 __global__ void cheb_step(T *__restrict__ x, T *__restrict__ d, const T *__restrict__ b, const T *__restrict__ t,
                           const T *__restrict__ dinv, long n, T c1, T c2, int first, int zero_x) {
+  const size_t co = (size_t)blockIdx.y * n;   // column of a block of vectors (dinv shared)
+  x += co; d += co; b += co; t += co;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const T r = zero_x ? b[i] : b[i] - t[i];
     const T dn = (first ? T(0) : c1 * d[i]) + c2 * dinv[i] * r;
@@ -105,7 +117,8 @@ __global__ void cpcg_precond(T *__restrict__ z, const T *__restrict__ r, const T
 
 template <typename T>
 __global__ void sub_mean_T(T *__restrict__ z, long n, const double *sc, int slot) {
-  const double m = sc[slot] / (double)n;
+  z += (size_t)blockIdx.y * n;
+  const double m = sc[(size_t)blockIdx.y * MS_COUNT + slot] / (double)n;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     z[i] = (T)((double)z[i] - m);
 }
@@ -190,6 +203,8 @@ __global__ void __launch_bounds__(256) prolong_cell_kernel(const Basis<T> *Bg, X
   __shared__ T Pm[3][2][n2];
   __shared__ T Xc[n3], A[2 * n3], Bm[4 * n3];
   const int cc = blockIdx.x;
+  xc += (size_t)blockIdx.y * gridDim.x * n3;   // column of a block of vectors
+  xf += (size_t)blockIdx.y * X.fnx * X.fny * X.fnz * n3;
   const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
   const int c0 = X.cf[0], c1 = X.cf[1], c2 = X.cf[2];
   load_xfer_matrices<T, K>(*Bg, X, cj, Pm);
@@ -248,6 +263,8 @@ __global__ void __launch_bounds__(256) restrict_cell_kernel(const Basis<T> *Bg, 
   __shared__ T Pm[3][2][n2];
   __shared__ T Rf[8 * n3], Zs[4 * n3], Ys[2 * n3];
   const int cc = blockIdx.x;
+  rc += (size_t)blockIdx.y * gridDim.x * n3;   // column of a block of vectors
+  rf += (size_t)blockIdx.y * X.fnx * X.fny * X.fnz * n3;
   const int ci = cc % X.cnx, cj = (cc / X.cnx) % X.cny, ck = cc / (X.cnx * X.cny);
   const int c0 = X.cf[0], c1 = X.cf[1], c2 = X.cf[2];
   load_xfer_matrices<T, K>(*Bg, X, cj, Pm);
@@ -314,27 +331,29 @@ __global__ void __launch_bounds__(256) restrict_cell_kernel(const Basis<T> *Bg, 
 
 template <typename T>
 static void launch_restrict(const Basis<T> *B, const XferDims &X, int n, const T *rf, T *rc, int ncoarse,
-                            cudaStream_t s) {
+                            cudaStream_t s, int ncols = 1) {
   note_launch();
+  const dim3 g(ncoarse, ncols);
   switch (n) {
-    case 2: restrict_cell_kernel<T, 1><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
-    case 3: restrict_cell_kernel<T, 2><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
-    case 4: restrict_cell_kernel<T, 3><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
-    case 5: restrict_cell_kernel<T, 4><<<ncoarse, 128, 0, s>>>(B, X, rf, rc); break;
-    default: restrict_cell_kernel<T, 5><<<ncoarse, 160, 0, s>>>(B, X, rf, rc); break;
+    case 2: restrict_cell_kernel<T, 1><<<g, 128, 0, s>>>(B, X, rf, rc); break;
+    case 3: restrict_cell_kernel<T, 2><<<g, 128, 0, s>>>(B, X, rf, rc); break;
+    case 4: restrict_cell_kernel<T, 3><<<g, 128, 0, s>>>(B, X, rf, rc); break;
+    case 5: restrict_cell_kernel<T, 4><<<g, 128, 0, s>>>(B, X, rf, rc); break;
+    default: restrict_cell_kernel<T, 5><<<g, 160, 0, s>>>(B, X, rf, rc); break;
   }
 }
 
 template <typename T>
 static void launch_prolong(const Basis<T> *B, const XferDims &X, int n, const T *xc, T *xf, int ncoarse,
-                           cudaStream_t s) {
+                           cudaStream_t s, int ncols = 1) {
   note_launch();
+  const dim3 g(ncoarse, ncols);
   switch (n) {
-    case 2: prolong_cell_kernel<T, 1><<<ncoarse, 64, 0, s>>>(B, X, xc, xf); break;
-    case 3: prolong_cell_kernel<T, 2><<<ncoarse, 96, 0, s>>>(B, X, xc, xf); break;
-    case 4: prolong_cell_kernel<T, 3><<<ncoarse, 128, 0, s>>>(B, X, xc, xf); break;
-    case 5: prolong_cell_kernel<T, 4><<<ncoarse, 224, 0, s>>>(B, X, xc, xf); break;
-    default: prolong_cell_kernel<T, 5><<<ncoarse, 256, 0, s>>>(B, X, xc, xf); break;
+    case 2: prolong_cell_kernel<T, 1><<<g, 64, 0, s>>>(B, X, xc, xf); break;
+    case 3: prolong_cell_kernel<T, 2><<<g, 96, 0, s>>>(B, X, xc, xf); break;
+    case 4: prolong_cell_kernel<T, 3><<<g, 128, 0, s>>>(B, X, xc, xf); break;
+    case 5: prolong_cell_kernel<T, 4><<<g, 224, 0, s>>>(B, X, xc, xf); break;
+    default: prolong_cell_kernel<T, 5><<<g, 256, 0, s>>>(B, X, xc, xf); break;
   }
 }
 
@@ -344,6 +363,8 @@ template <typename T>
 __global__ void p_prolongate_add(const T *__restrict__ P1, int n, const T *__restrict__ x1, T *__restrict__ xk) {
   __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX], Pm[NMAX * 2];
   const int c = blockIdx.x, n3 = n * n * n;
+  x1 += (size_t)blockIdx.y * gridDim.x * 8;    // column of a block of vectors
+  xk += (size_t)blockIdx.y * gridDim.x * n3;
   for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) Pm[t] = P1[t];
   for (int t = threadIdx.x; t < 8; t += blockDim.x) A[t] = x1[(size_t)c * 8 + t];
   __syncthreads();
@@ -360,6 +381,8 @@ template <typename T>
 __global__ void p_restrict(const T *__restrict__ P1, int n, const T *__restrict__ rk, T *__restrict__ r1) {
   __shared__ T A[NMAX * NMAX * NMAX], Bv[NMAX * NMAX * NMAX], Pm[NMAX * 2];
   const int c = blockIdx.x, n3 = n * n * n;
+  rk += (size_t)blockIdx.y * gridDim.x * n3;   // column of a block of vectors
+  r1 += (size_t)blockIdx.y * gridDim.x * 8;
   for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) Pm[t] = P1[t];
   for (int t = threadIdx.x; t < n3; t += blockDim.x) A[t] = rk[(size_t)c * n3 + t];
   __syncthreads();
@@ -375,6 +398,8 @@ __global__ void p_restrict(const T *__restrict__ P1, int n, const T *__restrict_
 // x = Ainv b (one warp per row, lanes stride the row)
 template <typename T>
 __global__ void dense_gemv(const T *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ x, int N) {
+  b += (size_t)blockIdx.y * N;   // column of a block of vectors
+  x += (size_t)blockIdx.y * N;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= N) return;
   const T *row = Ainv + (size_t)warp * N;
@@ -404,11 +429,14 @@ struct Lvl {
   std::vector<void *> allocs;
 };
 
+// cols: columns every level vector holds (a block of right-hand sides); ncols: columns one V-cycle
+// processes (<= cols)
 template <typename T>
 struct Hierarchy {
   std::vector<Lvl<T> *> L;
   int cheb = 5;
   const Basis<T> *basis = nullptr;
+  int cols = 1, ncols = 1;
 };
 
 }  // namespace dgw
@@ -715,14 +743,15 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     if (e == cudaSuccess) { note_launch(); inv_kernel<T><<<mg_grid(L->n), 256, 0, s>>>(dg_dev, L->dinv, L->n); }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (dg_dev) cudaFree(dg_dev);
-    L->x = lalloc<T>(L, L->n, e, s); L->b = lalloc<T>(L, L->n, e, s); L->r = lalloc<T>(L, L->n, e, s);
-    L->d = lalloc<T>(L, L->n, e, s); L->t = lalloc<T>(L, L->n, e, s); L->z = lalloc<T>(L, L->n, e, s);
-    L->x2 = lalloc<T>(L, L->n, e, s);
+    const size_t nb = (size_t)L->n * H->cols;   // every column of the block of right-hand sides
+    L->x = lalloc<T>(L, nb, e, s); L->b = lalloc<T>(L, nb, e, s); L->r = lalloc<T>(L, nb, e, s);
+    L->d = lalloc<T>(L, nb, e, s); L->t = lalloc<T>(L, nb, e, s); L->z = lalloc<T>(L, L->n, e, s);
+    L->x2 = lalloc<T>(L, nb, e, s);
     void *p = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * H->cols * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * H->cols * sizeof(double), s);
     if (e == cudaSuccess) { L->allocs.push_back(p); L->sc = (double *)p; }
-    if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * H->cols * sizeof(double));
     if (e == cudaSuccess) { L->allocs.push_back(p); L->partial = (double *)p; }
     if (e == cudaSuccess) e = estimate_lmax(L, s);
     // next coarser level: halve every even direction
@@ -797,12 +826,12 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     D->view = C->view;
     D->view.n1 = 2;
     D->view.np = D->n;
-    D->x = lalloc<T>(D, D->n, e, s); D->b = lalloc<T>(D, D->n, e, s);
+    D->x = lalloc<T>(D, (size_t)D->n * H->cols, e, s); D->b = lalloc<T>(D, (size_t)D->n * H->cols, e, s);
     void *p = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMalloc(&p, MS_COUNT * H->cols * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, MS_COUNT * H->cols * sizeof(double), s);
     if (e == cudaSuccess) { D->allocs.push_back(p); D->sc = (double *)p; }
-    if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p, MG_RED * H->cols * sizeof(double));
     if (e == cudaSuccess) { D->allocs.push_back(p); D->partial = (double *)p; }
     if (curved) {
       // degree-1 tables and basis of the coarsest cells for the dense assembly
@@ -854,17 +883,18 @@ static void chebyshev(const Hierarchy<T> *H, Lvl<T> *L, bool zero_init, cudaStre
   const double lmax = 1.2 * L->lmax, lmin = lmax / kSmoothRange;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
-  const int G = mg_grid(L->n);
+  const int G = mg_grid(L->n), nc = H->ncols;
   T *cur = L->x;
   int k = 0;
   if (zero_init) {   // x = 0: the first step needs no operator apply
     note_launch();
-    cheb_step<T><<<G, 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, T(0), (T)(1.0 / theta), 1, 1);
+    cheb_step<T><<<dim3(G, nc), 256, 0, s>>>(L->x, L->d, L->b, L->t, L->dinv, L->n, T(0), (T)(1.0 / theta), 1, 1);
     k = 1;
   }
   for (; k < H->cheb; ++k) {
     LapEpi<T> epi{};
     epi.mode = LAP_CHEB;
+    epi.ncols = nc;
     epi.b = L->b;
     epi.d = L->d;
     epi.dinv = L->dinv;
@@ -883,19 +913,21 @@ static void chebyshev(const Hierarchy<T> *H, Lvl<T> *L, bool zero_init, cudaStre
     launch_laplace_epi<T>(L->view, cur, nullptr, epi, s);
     cur = epi.xout;
   }
-  if (cur != L->x) cudaMemcpyAsync(L->x, cur, L->n * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  if (cur != L->x) cudaMemcpyAsync(L->x, cur, (size_t)L->n * nc * sizeof(T), cudaMemcpyDeviceToDevice, s);
 }
 
+// Coarsest level: the dense (pseudo-)inverse for every column, or (one column only) the iterative
+// coarse PCG.
 template <typename T>
-static void coarse_solve(Lvl<T> *L, cudaStream_t s) {
+static void coarse_solve(const Hierarchy<T> *H, Lvl<T> *L, cudaStream_t s) {
   const long n = L->n;
-  const int G = mg_grid(n);
+  const int G = mg_grid(n), nc = H->ncols;
   if (L->ainv) {
     // consistent right-hand side, then the exact (pseudo-)inverse
-    mg_reduce<T>(L->b, nullptr, n, L->partial, L->sc, MS_SUM, s);
+    mg_reduce<T>(L->b, nullptr, n, L->partial, L->sc, MS_SUM, s, nc);
     note_launches(2);
-    sub_mean_T<T><<<G, 256, 0, s>>>(L->b, n, L->sc, MS_SUM);
-    dense_gemv<T><<<(int)((n * 32 + 255) / 256), 256, 0, s>>>(L->ainv, L->b, L->x, (int)n);
+    sub_mean_T<T><<<dim3(G, nc), 256, 0, s>>>(L->b, n, L->sc, MS_SUM);
+    dense_gemv<T><<<dim3((int)((n * 32 + 255) / 256), nc), 256, 0, s>>>(L->ainv, L->b, L->x, (int)n);
     return;
   }
   cudaMemsetAsync(L->x, 0, n * sizeof(T), s);
@@ -925,8 +957,9 @@ static void coarse_solve(Lvl<T> *L, cudaStream_t s) {
 template <typename T>
 static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
   Lvl<T> *L = H->L[lev];
+  const int nc = H->ncols;
   if (lev + 1 == H->L.size()) {
-    coarse_solve(L, s);
+    coarse_solve(H, L, s);
     return;
   }
   Lvl<T> *C = H->L[lev + 1];
@@ -934,14 +967,15 @@ static void vcycle(const Hierarchy<T> *H, size_t lev, cudaStream_t s) {
   LapEpi<T> res{};
   res.mode = LAP_RESIDUAL;
   res.b = L->b;
+  res.ncols = nc;
   launch_laplace_epi<T>(L->view, L->x, L->r, res, s);   // r = b - A x
   note_launch();
-  if (L->p1) p_restrict<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, L->r, C->b);
-  else launch_restrict<T>(H->basis, L->to_coarse, L->view.n1, L->r, C->b, C->view.nc, s);
+  if (L->p1) p_restrict<T><<<dim3(L->view.nc, nc), 64, 0, s>>>(L->p1, L->view.n1, L->r, C->b);
+  else launch_restrict<T>(H->basis, L->to_coarse, L->view.n1, L->r, C->b, C->view.nc, s, nc);
   vcycle(H, lev + 1, s);
   note_launch();
-  if (L->p1) p_prolongate_add<T><<<L->view.nc, 64, 0, s>>>(L->p1, L->view.n1, C->x, L->x);
-  else launch_prolong<T>(H->basis, L->to_coarse, L->view.n1, C->x, L->x, C->view.nc, s);
+  if (L->p1) p_prolongate_add<T><<<dim3(L->view.nc, nc), 64, 0, s>>>(L->p1, L->view.n1, C->x, L->x);
+  else launch_prolong<T>(H->basis, L->to_coarse, L->view.n1, C->x, L->x, C->view.nc, s, nc);
   chebyshev(H, L, false, s);
 }
 
@@ -1012,6 +1046,43 @@ cudaError_t mg_vcycle_f32(dgw_solver *S, cudaStream_t s) {
   MGLevel *ml = S->levels.empty() ? nullptr : S->levels[0];
   if (!ml || ml->prec != 1) return cudaErrorNotReady;
   vcycle((Hierarchy<float> *)ml->h, 0, s);
+  return cudaGetLastError();
+}
+
+// FP32 hierarchy over a block of cols right-hand sides (box cells, dense coarsest solve): the
+// batched mixed-precision solve runs one V-cycle for every column at once.
+cudaError_t mg_batch_create(dgw_mesh *M, int cols, int cheb, cudaStream_t s, void **out) {
+  *out = nullptr;
+  if (M->P.geometry != 0 || !M->has32 || cols < 1) return cudaErrorNotSupported;
+  auto *H = new Hierarchy<float>();
+  H->cheb = cheb;
+  H->basis = M->v32.basis;
+  H->cols = cols;
+  H->ncols = 1;
+  cudaError_t e = build_hierarchy<float>(M, H, M->v32, nullptr, s);
+  if (e == cudaSuccess && !H->L.back()->ainv) e = cudaErrorNotSupported;   // the iterative coarse solve is one column
+  if (e != cudaSuccess) {
+    free_hier(H);
+    return e;
+  }
+  *out = H;
+  return cudaSuccess;
+}
+
+void mg_batch_free(void *h) { free_hier(static_cast<Hierarchy<float> *>(h)); }
+
+void mg_batch_level0(void *h, float **b0, float **x0) {
+  auto *H = static_cast<Hierarchy<float> *>(h);
+  *b0 = H->L[0]->b;
+  *x0 = H->L[0]->x;
+}
+
+cudaError_t mg_batch_vcycle(void *h, int ncols, cudaStream_t s) {
+  auto *H = static_cast<Hierarchy<float> *>(h);
+  if (ncols < 1 || ncols > H->cols) return cudaErrorInvalidValue;
+  H->ncols = ncols;
+  vcycle(H, 0, s);
+  H->ncols = 1;
   return cudaGetLastError();
 }
 

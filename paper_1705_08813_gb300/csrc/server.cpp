@@ -2,10 +2,17 @@
 //
 // Jobs are admitted as worker slots and device memory free up: a job needs a resident mesh with
 // the job's parameters (meshes and their solver state stay on the device between jobs and are
-// reused; at most one job uses a mesh instance at a time, further instances are created while
+// reused; at most one worker uses a mesh instance at a time, further instances are created while
 // the HBM budget allows, idle meshes are evicted least-recently-used when it does not). Each
-// worker thread owns a CUDA stream, so the work of concurrent jobs overlaps on the device. Results
-// do not depend on what else is running (no shared scratch between jobs, deterministic kernels).
+// worker thread owns a CUDA stream, so the work of concurrent jobs overlaps on the device.
+//
+// Continuous batching of solves: a worker that takes a mixed-precision solve on a channel mesh
+// drives a block solve on that mesh (batch.cu). Between refinement rounds it admits queued solves
+// with the same mesh parameters and multigrid settings into free columns (up to 8), and every
+// column that converges is reported and frees its column for the next request, so requests that
+// arrive while others are on the GPU join the running block. Results do not depend on what else is
+// running: a column's arithmetic is the same alone and in any block (per-column reductions, no
+// shared scratch between jobs, deterministic kernels).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -21,6 +28,7 @@
 #include <vector>
 
 #include "dgw_internal.h"
+#include "solver.h"
 
 namespace {
 
@@ -32,6 +40,8 @@ struct MeshSlot {
   size_t bytes = 0;
   bool busy = false;
   clock_type::time_point last_used;
+  int batch_room = 0;   // free columns of the block solve running on this mesh (0: none running)
+  int batch_cheb = 0;
 };
 
 struct JobRec {
@@ -41,6 +51,7 @@ struct JobRec {
   dgw_solve_info info{};
   clock_type::time_point t_submit, t_start, t_done;
   bool started = false, done = false;
+  const dgw_mesh *in_batch = nullptr;   // the mesh whose block solve runs this job
 };
 
 bool same_params(const dgw_mesh_params &a, const dgw_mesh_params &b) {
@@ -58,7 +69,10 @@ size_t footprint_estimate(const dgw_mesh_params &p, int kind) {
   const size_t ne = (size_t)2 * p.n_layers * p.nx * p.nz;
   const size_t qi = (3 * (size_t)p.degree) / 2 + 1, qw = p.q_wall > 0 ? (size_t)p.q_wall : 8;
   size_t mesh = np * 8 * 2 + nc * 16 + ne * (qi * qi * qw + 6 * qw * qi) * 8 * 12 + (1 << 20);
-  if (kind == DGW_JOB_SOLVE) mesh += np * 8 * 6 + np * 8 * 8 * 8 / 7;   // CG vectors + MG levels (FP64 bound)
+  if (kind == DGW_JOB_SOLVE) {
+    mesh += np * 8 * 6 + np * 8 * 8 * 8 / 7;   // CG vectors + MG levels (FP64 bound)
+    mesh += (size_t)dgw::kBatchMax * np * 96;  // block solve: 4 FP64 + 4 FP32 columns, FP32 levels
+  }
   return mesh;
 }
 
@@ -110,6 +124,112 @@ struct dgw_server {
     return &meshes.back();
   }
 
+  static bool batchable(const dgw_job &j) {
+    return j.kind == DGW_JOB_SOLVE && j.opts.mode == 1 && j.mesh.geometry == 0 && (j.mesh.precision_mask & 2);
+  }
+  static bool same_batch(const dgw_job &a, const dgw_job &b) {
+    return same_params(a.mesh, b.mesh) && a.opts.cheb_degree == b.opts.cheb_degree;
+  }
+
+  // Block solve on the mesh of r's job: admits r, then, between refinement rounds, every queued
+  // solve that fits the block, until no column is left. Returns false (nothing done) when the mesh
+  // cannot host a block (its multigrid needs the iterative coarse solve).
+  bool run_batch(JobRec *r, MeshSlot *slot, cudaStream_t s) {
+    dgw_mesh *M = slot->mesh;
+    const int cheb = r->job.opts.cheb_degree > 0 ? r->job.opts.cheb_degree : 5;
+    if (M->batch && M->batch_cheb != cheb) { dgw::batch_destroy(M->batch); M->batch = nullptr; }
+    if (!M->batch) {
+      dgw::Batch *B = nullptr;
+      if (dgw::batch_create(M, dgw::kBatchMax, cheb, &B) != cudaSuccess) return false;
+      M->batch = B;
+      M->batch_cheb = cheb;
+    }
+    dgw::Batch *B = M->batch;
+    std::vector<JobRec *> incoming{r};
+    std::vector<dgw::BatchColumn> done;
+    for (;;) {
+      for (JobRec *q : incoming) {
+        dgw::BatchColumn c;
+        c.b_in = (const double *)q->job.in;
+        c.p_out = (double *)q->job.out;
+        c.tag = q->ticket;
+        c.rtol = q->job.opts.rtol;
+        c.max_iter = q->job.opts.max_iter;
+        if (dgw::batch_admit(B, c, s) != cudaSuccess) finish(q, DGW_ECUDA, dgw_solve_info{});
+      }
+      incoming.clear();
+      if (dgw::batch_active(B) == 0) break;
+      done.clear();
+      const cudaError_t e = dgw::batch_round(B, done);
+      if (e != cudaSuccess) {
+        // a failed round: every column of the block fails, and the block is rebuilt on next use
+        dgw::batch_destroy(M->batch);
+        M->batch = nullptr;
+        std::lock_guard<std::mutex> lock(mu);
+        for (auto &kv : jobs)
+          if (kv.second->started && !kv.second->done && kv.second->in_batch == M) fail_locked(kv.second.get(), DGW_ECUDA);
+        slot->batch_room = 0;
+        return true;
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      for (const dgw::BatchColumn &c : done) {
+        auto it = jobs.find(c.tag);
+        if (it == jobs.end()) continue;
+        dgw_solve_info inf{};
+        inf.iterations = c.iterations;
+        inf.rel_residual = c.rel_residual;
+        inf.ms = (float)std::chrono::duration<double, std::milli>(clock_type::now() - c.t_admit).count();
+        finish_locked(it->second.get(), c.status, inf);
+      }
+      // continuous batching: queued solves on this mesh join the block in its free columns
+      int room = dgw::kBatchMax - dgw::batch_active(B);
+      slot->batch_cheb = cheb;
+      for (auto qi = queue.begin(); qi != queue.end() && room > 0;) {
+        JobRec *q = jobs[*qi].get();
+        if (batchable(q->job) && same_batch(q->job, r->job)) {
+          q->started = true;
+          q->t_start = clock_type::now();
+          q->in_batch = M;
+          ++running;
+          incoming.push_back(q);
+          qi = queue.erase(qi);
+          --room;
+        } else {
+          ++qi;
+        }
+      }
+      // other workers leave matching solves to this block while it has room
+      slot->batch_room = (dgw::batch_active(B) + (int)incoming.size() > 0) ? std::max(room, 0) : 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    slot->batch_room = 0;
+    return true;
+  }
+
+  // a running block solve with free columns will take this job at its next round
+  bool block_will_take(const dgw_job &j) const {
+    if (!batchable(j)) return false;
+    const int cheb = j.opts.cheb_degree > 0 ? j.opts.cheb_degree : 5;
+    for (const auto &m : meshes)
+      if (m.busy && m.batch_room > 0 && m.batch_cheb == cheb && same_params(m.params, j.mesh)) return true;
+    return false;
+  }
+
+  void finish_locked(JobRec *r, dgw_status st, const dgw_solve_info &inf) {
+    r->status = st;
+    r->info = inf;
+    r->t_done = clock_type::now();
+    r->done = true;
+    --running;
+    cv_done.notify_all();
+    cv_work.notify_all();
+  }
+  void fail_locked(JobRec *r, dgw_status st) { finish_locked(r, st, dgw_solve_info{}); }
+  void finish(JobRec *r, dgw_status st, const dgw_solve_info &inf) {
+    std::lock_guard<std::mutex> lock(mu);
+    finish_locked(r, st, inf);
+  }
+
   void run_job(JobRec *r, MeshSlot *slot, cudaStream_t s) {
     dgw_status st = DGW_OK;
     if (!slot->mesh) {
@@ -121,6 +241,19 @@ struct dgw_server {
       }
     }
     const dgw_job &j = r->job;
+    if (st == DGW_OK && batchable(j)) {
+      {
+        std::lock_guard<std::mutex> lock(mu);
+        r->in_batch = slot->mesh;
+      }
+      if (run_batch(r, slot, s)) {   // r and every job that joined the block are reported
+        std::lock_guard<std::mutex> lock(mu);
+        slot->busy = false;
+        slot->last_used = clock_type::now();
+        cv_work.notify_all();
+        return;
+      }
+    }
     if (st == DGW_OK) {
       switch (j.kind) {
         case DGW_JOB_SOLVE:
@@ -166,6 +299,7 @@ struct dgw_server {
       bool rescan = false;
       for (auto it = queue.begin(); it != queue.end(); ++it) {
         JobRec *r = jobs[*it].get();
+        if (block_will_take(r->job)) continue;
         bool fatal = false;
         slot = reserve(r->job, &fatal);
         if (fatal) {   // can never fit the budget: fail it and look again

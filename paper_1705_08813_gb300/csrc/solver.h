@@ -1,6 +1,8 @@
 // Solver workspace and multigrid interface (internal).
 #pragma once
 
+#include <chrono>
+
 #include "dgw_internal.h"
 
 namespace dgw {
@@ -48,6 +50,37 @@ cudaError_t mg_vcycle(dgw_mesh *M, dgw_solver *S, int mode, const double *r, dou
 cudaError_t mg_level0_f32(dgw_solver *S, float **b0, float **x0);
 cudaError_t mg_vcycle_f32(dgw_solver *S, cudaStream_t s);
 void mg_free(dgw_solver *S);
+// FP32 hierarchy over a block of cols right-hand sides (boxes, dense coarsest solve; otherwise
+// cudaErrorNotSupported), its level-0 rhs / iterate blocks (cols x np) and one V-cycle over the
+// first ncols columns
+cudaError_t mg_batch_create(dgw_mesh *M, int cols, int cheb, cudaStream_t s, void **out);
+void mg_batch_free(void *h);
+void mg_batch_level0(void *h, float **b0, float **x0);
+cudaError_t mg_batch_vcycle(void *h, int ncols, cudaStream_t s);
+
+// ---- block mixed-precision solves (batch.cu): columns of right-hand sides on one mesh
+constexpr int kBatchMax = 8;   // columns of a batch
+struct BatchColumn {
+  const double *b_in = nullptr;    // caller's right-hand side (n_p doubles)
+  double *p_out = nullptr;         // caller's solution buffer
+  void *caller_stream = nullptr;
+  long tag = 0;                    // the caller's identifier of the column
+  double rtol = 1e-10;             // the column's target ||b - A p|| / ||b||
+  int max_iter = 1000;             // limit on its inner iterations
+  bool used = false, finished = false;
+  double bnorm = 0.0, rel_residual = 0.0;
+  int iterations = 0;              // inner FP32 iterations, all refinement rounds
+  dgw_status status = DGW_OK;
+  std::chrono::steady_clock::time_point t_admit;
+};
+struct Batch;
+cudaError_t batch_create(dgw_mesh *M, int cap, int cheb, Batch **out);
+void batch_destroy(Batch *B);
+int batch_active(const Batch *B);   // active columns (they occupy slots 0..active-1)
+// a new column in the first free slot (between rounds; the caller checks batch_active < cap)
+cudaError_t batch_admit(Batch *B, const BatchColumn &c, cudaStream_t caller);
+// one refinement round; finished columns are written to their p_out and appended to done
+cudaError_t batch_round(Batch *B, std::vector<BatchColumn> &done);
 dgw_solver *get_solver(dgw_mesh *M);
 int mg_levels(dgw_solver *S);
 int mg_describe(dgw_solver *S, double *lmax, int *cells, int max_levels);

@@ -19,7 +19,7 @@ STATUS = {0: "DGW_OK", -1: "DGW_EINVAL", -2: "DGW_ENOMEM", -3: "DGW_ENOTCONV", -
 EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_node_coords",
            "dgw_update_eddy_viscosity", "dgw_apply_laplace", "dgw_apply_divergence",
            "dgw_apply_convective", "dgw_apply_viscous", "dgw_apply_divergence_prec", "dgw_pressure_solve", "dgw_last_error",
-           "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc",
+           "dgw_counters", "dgw_solver_describe", "dgw_pressure_solve_jacobi_noalloc", "dgw_pressure_solve_batch",
            "dgw_server_create", "dgw_submit", "dgw_poll", "dgw_server_stats", "dgw_server_destroy",
            "dgw_apply_mass", "dgw_helmholtz_solve", "dgw_wall_shear_stress", "dgw_set_wall_shear_stress",
            "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active",
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
     lib.dgw_apply_convective.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_apply_viscous.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.dgw_pressure_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.dgw_pressure_solve_batch.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                             ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.dgw_solver_describe.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp]
     lib.dgw_pressure_solve_jacobi_noalloc.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int,
@@ -358,6 +360,24 @@ class Mesh:
             _check(st)
         return {"iterations": info.iterations, "rel_residual": info.rel_residual, "ms": info.ms, "status": st,
                 "dof_applies": info.dof_applies}
+
+
+def pressure_solve_batch(mesh, bs, ps, rtol=1e-10, max_iter=1000, cheb_degree=5, stream=None, check=True):
+    """Mixed-precision solves of the right-hand sides bs (list of CUDA float64 tensors of n_p) into ps
+    as one block (dgw_pressure_solve_batch). Returns one info dict per column."""
+    import torch
+    nc = len(bs)
+    if nc != len(ps) or nc == 0:
+        raise ValueError("bs and ps must be non-empty lists of equal length")
+    B = (ctypes.c_void_p * nc)(*[_ptr(b, torch.float64, mesh.n_p, "b") for b in bs])
+    P = (ctypes.c_void_p * nc)(*[_ptr(p, torch.float64, mesh.n_p, "p") for p in ps])
+    opts = SolveOpts(rtol, max_iter, 1, cheb_degree)
+    infos = (SolveInfo * nc)()
+    st = mesh.lib.dgw_pressure_solve_batch(mesh.h, nc, B, P, ctypes.byref(opts), infos, _stream(stream))
+    if check:
+        _check(st)
+    return [{"iterations": i.iterations, "rel_residual": i.rel_residual, "ms": i.ms, "status": st,
+             "dof_applies": i.dof_applies} for i in infos]
 
 
 def describe_solver(mesh, mode=1):

@@ -1,5 +1,6 @@
 """Request loop: mixed solve/apply jobs on different meshes and degrees, admitted as slots and
-memory free up, overlapping on the device. Each result must equal the same job run alone."""
+memory free up, overlapping on the device. Each result must equal the same job run alone (mixed
+solves on channels run as block solves: alone means a block of one column)."""
 import time
 
 import numpy as np
@@ -46,7 +47,11 @@ def _inputs(dgw, kind, w, prec, j):
 
 
 def _alone(m, kind, inp, out, mode, aux=None):
-    if kind == 0:
+    if kind == 0 and mode == 1:
+        # the request loop runs mixed solves on channels as block solves: alone is a block of one
+        from paper_1705_08813_gb300 import dgw
+        dgw.pressure_solve_batch(m, [inp], [out], rtol=1e-10, max_iter=500)
+    elif kind == 0:
         m.pressure_solve(inp, out, rtol=1e-10, max_iter=500, mode=mode)
     elif kind == 1:
         m.laplace(inp, out)
