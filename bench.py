@@ -11,8 +11,12 @@ value = output DoFs of the step's four FP64 applies (n_p + n_p + n_u + n_u) / st
 The same run then times, each in its own loop, the pressure solves to a 1e-10 relative residual in
 plain FP64 (FP64 CG + FP64 multigrid) and mixed precision (FP64 refinement around FP32 CG with the
 FP32 multigrid), on this workload (rhs = the step's divergence) and on the Q3 64x32x32 channel
-(seeded zero-mean uniform rhs), reported as solves/s under "solves"; and the FP32 SIPG Laplacian,
-the operator the FP32 multigrid applies most, with its HBM roofline under "fp32_laplace".
+(seeded zero-mean uniform rhs), reported as solves/s under "solves"; the FP32 SIPG Laplacian,
+the operator the FP32 multigrid applies most, with its HBM roofline under "fp32_laplace"; the same
+step with every apply in double-float arithmetic under "df64_step"; and a short serving stream
+(Poisson arrivals of solve and apply jobs on channels of different sizes and degrees through the
+request loop with continuous batching, p50/p99 latency and solves/s against the same jobs run one at
+a time with FP64 solves) under "serving".
 
 --impl reference times the CPU oracle (the plain FP64 implementation the tests check against) on a
 bounded sample of the same workload: the four operator applies on a subset of cells.
@@ -492,6 +496,10 @@ def run_gpu(args):
     e2e = {"value": weak_value(dofs_step, world, e2e_ms_max), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max}
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_stream(args.serving_short_jobs, args.rate, args.serving_slots, args.serving_budget_gb)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs, threads, desc = oracle_sample(w, target_s=args.ref_seconds)
@@ -507,7 +515,7 @@ def run_gpu(args):
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (512 MB write)"},
                 "per_op": per_op, "dof_applies_per_step": dofs_step, "solves": solves,
                 "roofline": roofline, "fp32_laplace": fp32_laplace, "df64_emulation": emulation, "df64_step": df64_step,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "serving": serving, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": int(launches1 - launches0), "launches_before_timed": int(launches0),
                 "wall_s": t_wall}
         print(json.dumps(line), flush=True)
@@ -517,20 +525,18 @@ def run_gpu(args):
     return 0
 
 
-def run_serving(args):
-    """Serving workload: Poisson arrivals (mean args.rate jobs/s, seed 999) of pressure solves (3/4,
-    mixed precision, 1e-10) and operator applies (1/4) on channels with N_x uniform in
-    {8,16,24,32,40,48}, N_y = N_z = max(8, N_x/2), k uniform in {2,3,4,5}; per-job seeded inputs.
-    Reports p50/p99 latency (arrival to completion) and solves/s through the request loop, and the
-    same job stream run one at a time with FP64 solves."""
+def serving_stream(n, rate, slots, budget_gb, seed=999):
+    """Serving workload: Poisson arrivals (mean `rate` jobs/s, seeded) of pressure solves (3/4, mixed
+    precision to 1e-10) and operator applies (1/4) on channels with N_x uniform in
+    {8,16,24,32,40,48}, N_y = N_z = max(8, N_x/2), k uniform in {2,3,4,5}; per-job seeded inputs. Every
+    distinct (mesh, job kind) is warmed first (resident mesh, multigrid and block solver). Returns
+    p50/p99 latency (arrival to completion) and solves/s through the request loop, and the same jobs
+    run one at a time with FP64 solves on meshes warmed the same way."""
     import numpy as np
     import torch
     from paper_1705_08813_gb300 import dgw, inputs as I
-    torch.cuda.set_device(0)
-    dgw.load()
-    n = args.serving_jobs
-    rng_u = I.uniform(999, 4 * n, 0.0, 1.0, stream=41)
-    gaps = -np.log(1.0 - rng_u[:n]) / args.rate
+    rng_u = I.uniform(seed, 4 * n, 0.0, 1.0, stream=41)
+    gaps = -np.log(1.0 - rng_u[:n]) / rate
     arrivals = np.cumsum(gaps)
     nxs = [8, 16, 24, 32, 40, 48]
     specs = []
@@ -555,7 +561,16 @@ def run_serving(args):
         aux = inp if kind == 4 else None
         bufs.append((inp, torch.zeros(nout, dtype=torch.float64, device="cuda"), aux))
     torch.cuda.synchronize()
-    srv = dgw.Server(int(args.serving_budget_gb * (1 << 30)), max_inflight=args.serving_slots)
+    srv = dgw.Server(int(budget_gb * (1 << 30)), max_inflight=slots)
+
+    def drain(tickets):
+        pend = set(tickets)
+        while pend:
+            for t in list(pend):
+                if srv.poll(t) is not None:
+                    pend.discard(t)
+            time.sleep(0.001)
+
     # warm the resident meshes and solver state: one job per distinct (mesh, kind)
     seen, warm = set(), []
     for j, (kind, w) in enumerate(specs):
@@ -564,16 +579,10 @@ def run_serving(args):
             seen.add(key)
             inp, out, aux = bufs[j]
             warm.append(srv.submit(kind, dgw.mesh_params(w), inp, out, aux=aux, mode=1))
-    pend = set(warm)
-    while pend:
-        for t in list(pend):
-            if srv.poll(t) is not None:
-                pend.discard(t)
-        time.sleep(0.001)
+    drain(warm)
     # timed stream
     t0 = time.perf_counter()
-    tickets, submitted = {}, 0
-    done = {}
+    tickets, submitted, done = {}, 0, {}
     while len(done) < n:
         now = time.perf_counter() - t0
         while submitted < n and arrivals[submitted] <= now:
@@ -589,37 +598,61 @@ def run_serving(args):
         time.sleep(0.0002)
     makespan = max(v[1] for v in done.values())
     lat = np.array([1e3 * (done[j][1] - arrivals[j]) for j in range(n)])
+    slat = np.array([lat[j] for j in range(n) if specs[j][0] == 0])
     ok = all(done[j][0]["status"] == 0 for j in range(n))
+    failures = [{"job": j, "kind": specs[j][0], "cells": [specs[j][1].nx, specs[j][1].ny, specs[j][1].nz],
+                 "degree": specs[j][1].k, "status": done[j][0]["status"]} for j in range(n) if done[j][0]["status"] != 0]
     n_solves = sum(1 for kind, _ in specs if kind == 0)
     srv.close()
-    # one at a time, FP64 solves
+    # one at a time, FP64 solves, meshes and hierarchies warmed by one untimed job each
     meshes = {}
-    t1 = time.perf_counter()
+    def run_one(j, mesh):
+        kind, w = specs[j]
+        inp, out, aux = bufs[j]
+        if kind == 0:
+            mesh.pressure_solve(inp, out, rtol=1e-10, max_iter=500, mode=0)
+        elif kind == 1:
+            mesh.laplace(inp, out)
+        elif kind == 2:
+            mesh.divergence(inp, out)
+        elif kind == 3:
+            mesh.convective(inp, out)
+        else:
+            mesh.update_eddy_viscosity(aux)
+            mesh.viscous(inp, out)
+    warmed = set()
     for j, (kind, w) in enumerate(specs):
         key = (w.nx, w.k)
         if key not in meshes:
             meshes[key] = dgw.mesh_for(w)
-        m = meshes[key]
-        inp, out, aux = bufs[j]
-        if kind == 0:
-            m.pressure_solve(inp, out, rtol=1e-10, max_iter=500, mode=0)
-        elif kind == 1:
-            m.laplace(inp, out)
-        elif kind == 2:
-            m.divergence(inp, out)
-        elif kind == 3:
-            m.convective(inp, out)
-        else:
-            m.update_eddy_viscosity(aux)
-            m.viscous(inp, out)
+        if (key, kind) not in warmed:
+            warmed.add((key, kind))
+            run_one(j, meshes[key])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for j in range(n):
+        run_one(j, meshes[(specs[j][1].nx, specs[j][1].k)])
         torch.cuda.synchronize()
     seq = time.perf_counter() - t1
-    line = {"metric": "serving: p50/p99 latency and solves/s (mixed, request loop) vs one-at-a-time FP64",
-            "jobs": n, "solves": n_solves, "rate_per_s": args.rate, "slots": args.serving_slots,
-            "all_ok": ok, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "solves_per_s": n_solves / makespan, "makespan_s": makespan,
-            "sequential_fp64_solves_per_s": n_solves / seq, "sequential_s": seq,
-            "note": "sequential FP64 includes first-use multigrid setup of each mesh"}
+    for mm in meshes.values():
+        mm.close()
+    return {"metric": "serving: p50/p99 latency and solves/s (mixed, request loop with continuous batching) vs "
+                      "one-at-a-time FP64",
+            "jobs": n, "solves": n_solves, "rate_per_s": rate, "slots": slots, "all_ok": ok, "failures": failures[:10],
+            "arrival_span_s": float(arrivals[-1]), "makespan_s": makespan,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solve_p50_ms": float(np.percentile(slat, 50)) if len(slat) else None,
+            "solve_p99_ms": float(np.percentile(slat, 99)) if len(slat) else None,
+            "solves_per_s": n_solves / makespan, "sequential_fp64_solves_per_s": n_solves / seq,
+            "sequential_s": seq, "speedup_solves": (n_solves / makespan) / (n_solves / seq)}
+
+
+def run_serving(args):
+    import torch
+    from paper_1705_08813_gb300 import dgw
+    torch.cuda.set_device(0)
+    dgw.load()
+    line = serving_stream(args.serving_jobs, args.rate, args.serving_slots, args.serving_budget_gb)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -819,6 +852,8 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None)
     ap.add_argument("--serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=400)
+    ap.add_argument("--serving-short-jobs", type=int, default=120, help="serving stream of the default run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream of the default run")
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--serving-budget-gb", type=float, default=120.0)
     ap.add_argument("--rate", type=float, default=200.0)

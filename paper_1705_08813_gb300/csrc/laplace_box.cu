@@ -100,66 +100,24 @@ __device__ __forceinline__ void mass_line(const T (&v)[K + 1], T (&out)[K + 1]) 
   }
 }
 
-// Asynchronous global -> shared copies (cp.async): every thread issues its share, one wait per
-// thread before the barrier that publishes the data; contiguous aligned spans move in 16-byte
-// chunks, anything else element by element.
-__device__ __forceinline__ void cpa16(void *dst, const void *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_elem(void *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_elem(void *dst, const double *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-// count elements of T from src to dst (dst holds sizeof(T)-byte slots)
-template <typename T>
-__device__ __forceinline__ void copy_span(void *dst, const T *src, int count, int tid, int nt) {
-  const size_t bytes = (size_t)count * sizeof(T);
-  if (((reinterpret_cast<size_t>(src) | reinterpret_cast<size_t>(dst) | bytes) & 15) == 0) {
-    char *d = static_cast<char *>(dst);
-    const char *g = reinterpret_cast<const char *>(src);
-    for (int t = tid; t < (int)(bytes >> 4); t += nt) cpa16(d + 16 * t, g + 16 * t);
-  } else {
-    T *d = static_cast<T *>(dst);
-    for (int t = tid; t < count; t += nt) cpa_elem(d + t, src + t);
-  }
-}
-
 // T: storage type of p and y; R: compute type (T itself, or df64 for FP64-accurate arithmetic on the
 // FP32 units with double vectors; that variant supports the plain epilogue only).
-//
-// The CTA stages its row segment of cpb cells, the segments of the rows above and below and of the
-// planes in front and behind (the neighbours across the y- and z-faces), and the two cells beyond
-// the segment's ends in x, all at once with asynchronous copies; every face trace is then taken from
-// shared memory.
 template <typename T, typename R, int K>
 __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p,
                                                                                 T *__restrict__ y, int cpb,
                                                                                 LapEpi<T> epi) {
-  static_assert(sizeof(R) == sizeof(T) || std::is_same<R, df64>::value, "staging copies T into R slots");
   constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *Rs = reinterpret_cast<R *>(smem_raw);     // kRowScal (32 slots keep the next array 16-byte aligned)
-  R *U = Rs + 32;                               // cpb n3 (input, then output)
-  R *NB = U + cpb * n3;                         // 4 x cpb n3: rows j-1, j+1, planes k-1, k+1
-  R *NX = NB + 4 * cpb * n3;                    // 2 x n3: cells i0-1 and i0+cpb (when nx > cpb)
-  R *A = NX + 2 * n3;                           // cpb n3 (T1 -> W)
+  R *Rs = reinterpret_cast<R *>(smem_raw);     // kRowScal
+  R *U = Rs + kRowScal;                         // cpb n3 (input, then output)
+  R *A = U + cpb * n3;                          // cpb n3 (T1 -> W)
   R *B = A + cpb * n3;                          // cpb n3 (T2 -> T3)
-  R *TY = B + cpb * n3;                         // cpb x 2 faces x 2 (val, der) x n2: y-face traces after M_x
-  R *TZ = TY + cpb * 4 * n2;                    // cpb x 2 x 2 x n2: z-face traces after M_x, then M_y
+  R *TR = B + cpb * n3;                         // cpb * 6 faces * 2 (val, der) * n2
+  R *TY = TR + cpb * 24 * n2;                   // cpb * 2 faces * 2 * n2 : y-face traces after M_x
+  R *TZ = TY + cpb * 8 * n2;                    // cpb * 2 * 2 * n2 : z-face traces after M_x
   const BoxConst<R> &C = box_const<R>(K);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int c0 = blockIdx.x * cpb;
-  const int i0 = c0 % m.nx, j = (c0 / m.nx) % m.ny, kz = c0 / (m.nx * m.ny);
-  const bool has_ym = j > 0, has_yp = j < m.ny - 1, ext_x = m.nx > cpb;
   if (blockIdx.y > 0) {   // column blockIdx.y of a block of vectors (the diagonal dinv is shared)
     const size_t co = (size_t)blockIdx.y * m.np;
     p += co;
@@ -168,89 +126,88 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
     if (epi.d) epi.d += co;
     if (epi.xout) epi.xout += co;
   }
-  // ---- stage the inputs
-  {
-    const size_t plane = (size_t)m.nx * m.ny;
-    copy_span<T>(U, p + (size_t)c0 * n3, cpb * n3, tid, nt);
-    if (has_ym) copy_span<T>(NB, p + (size_t)(c0 - m.nx) * n3, cpb * n3, tid, nt);
-    if (has_yp) copy_span<T>(NB + cpb * n3, p + (size_t)(c0 + m.nx) * n3, cpb * n3, tid, nt);
-    const int km = (kz + m.nz - 1) % m.nz, kp = (kz + 1) % m.nz;
-    copy_span<T>(NB + 2 * cpb * n3, p + ((size_t)km * plane + (size_t)(c0 % plane)) * n3, cpb * n3, tid, nt);
-    copy_span<T>(NB + 3 * cpb * n3, p + ((size_t)kp * plane + (size_t)(c0 % plane)) * n3, cpb * n3, tid, nt);
-    if (ext_x) {
-      const size_t row0 = (size_t)c0 - i0;
-      copy_span<T>(NX, p + (row0 + (i0 + m.nx - 1) % m.nx) * n3, n3, tid, nt);
-      copy_span<T>(NX + n3, p + (row0 + (i0 + cpb) % m.nx) * n3, n3, tid, nt);
-    }
-    const T *Rg = m.rowops + (size_t)j * kRowScal;
-    for (int t = tid; t < kRowScal; t += nt) Rs[t] = r_load<R>(Rg[t]);
-    cpa_wait_all();
-  }
-  __syncthreads();
-  if constexpr (!std::is_same<R, T>::value) {   // the copies hold T bits: convert in place
-    const int total = (5 * cpb + 2) * n3;      // U, NB, NX are contiguous
-    for (int t = tid; t < total; t += nt) {
-      const T v = reinterpret_cast<const T *>(U)[t];
-      U[t] = r_load<R>(v);
-    }
-    __syncthreads();
-  }
+  const int i0 = c0 % m.nx, j = (c0 / m.nx) % m.ny, kz = c0 / (m.nx * m.ny);
+  const T *Rg = m.rowops + (size_t)j * kRowScal;
+  for (int t = tid; t < kRowScal; t += nt) Rs[t] = r_load<R>(Rg[t]);
+  const T *pc = p + (size_t)c0 * n3;
+  for (int t = tid; t < cpb * n3; t += nt) U[t] = r_load<R>(pc[t]);
+  // Every thread owns line l of cell cl in all three passes (x-, y- then z-lines; l indexes the
+  // face nodes of the same two tangential axes), so the index arithmetic is done once here.
   const bool line = tid < cpb * n2;
   const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
   const int lq = l / n, lr = l - lq * n;   // l = lr + n * lq
-  // ---- phase A: x-lines (T1 = Lx u + nbr_x, T2 = M_x u); y- and z-face traces of the neighbours,
-  // transformed by M_x (items it < 4n: face direction it / 2n, face side (it / n) & 1, t2 index it % n)
+  int *nbr = reinterpret_cast<int *>(TZ + cpb * 8 * n2);   // [cpb][6] neighbour cells (-1: wall)
+  if (tid < cpb * 6) {
+    const int c = tid / 6, f = tid - c * 6, d = f >> 1, sg = (f & 1) ? 1 : -1;
+    int ii = i0 + c, jj = j, kk = kz;
+    if (d == 0) ii = (ii + sg + m.nx) % m.nx;
+    else if (d == 2) kk = (kk + sg + m.nz) % m.nz;
+    else jj += sg;
+    nbr[tid] = (jj < 0 || jj >= m.ny) ? -1 : ii + m.nx * (jj + m.ny * kk);
+  }
+  __syncthreads();
+  // neighbour traces at face node l of the six faces: value and reference normal derivative
+  if (line) {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, side = f & 1, nb = nbr[cl * 6 + f];
+      R val = r_zero<R>(), der = r_zero<R>();
+      if (nb >= 0) {
+        // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
+        const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
+        const int base = d == 0 ? n * l : (d == 1 ? lr + n2 * lq : l);
+        R v[n];
+        // x-neighbours inside this CTA's row segment are already in shared memory
+        if (nb >= c0 && nb < c0 + cpb) {
+          const R *pn = U + (nb - c0) * n3;
+#pragma unroll
+          for (int b = 0; b < n; ++b) v[b] = pn[base + b * stride];
+        } else {
+          const T *pn = p + (size_t)nb * n3;
+#pragma unroll
+          for (int b = 0; b < n; ++b) v[b] = r_load<R>(pn[base + b * stride]);
+        }
+        val = side ? v[0] : v[n - 1];
+#pragma unroll
+        for (int b = 0; b < n; ++b) der = r_fma(side ? C.D[0][b] : C.D[1][b], v[b], der);
+      }
+      TR[((cl * 6 + f) * 2 + 0) * n2 + l] = val;
+      TR[((cl * 6 + f) * 2 + 1) * n2 + l] = der;
+    }
+  }
+  __syncthreads();
+  // ---- phase A: x-lines (T1 = Lx u + nbr_x, T2 = M_x u); y- and z-traces <- M_x (items
+  // it = l, l + n^2, ... < 4n: face (it / n) >> 1, array (it / n) & 1, t2 = it % n)
   if (line) {
     const int base = cl * n3 + n * l;
-    R u[n], o1[n], o2[n], v[n];
+    R u[n], o1[n], o2[n];
 #pragma unroll
     for (int b = 0; b < n; ++b) u[b] = U[base + b];
-    // x-neighbours: inside the segment, or the staged cells beyond its ends (periodic in x)
-    const R *lm = cl > 0 ? U + (cl - 1) * n3 : (ext_x ? NX : U + (cpb - 1) * n3);
-    const R *lp = cl < cpb - 1 ? U + (cl + 1) * n3 : (ext_x ? NX + n3 : U);
-    R v0, d0 = r_zero<R>(), v1, d1 = r_zero<R>();
-#pragma unroll
-    for (int b = 0; b < n; ++b) v[b] = lm[n * l + b];
-    v0 = v[n - 1];
-#pragma unroll
-    for (int b = 0; b < n; ++b) d0 = r_fma(C.D[1][b], v[b], d0);
-#pragma unroll
-    for (int b = 0; b < n; ++b) v[b] = lp[n * l + b];
-    v1 = v[0];
-#pragma unroll
-    for (int b = 0; b < n; ++b) d1 = r_fma(C.D[0][b], v[b], d1);
+    const R v0 = TR[((cl * 6 + 0) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 0) * 2 + 1) * n2 + l];
+    const R v1 = TR[((cl * 6 + 1) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 1) * 2 + 1) * n2 + l];
     line_op<R, K>(u, Rs, v0, d0, v1, d1, o1);
     mass_line<R, K>(u, o2);
 #pragma unroll
     for (int a = 0; a < n; ++a) { A[base + a] = o1[a]; B[base + a] = o2[a]; }
-  }
-  for (int it = (line ? l : 4 * n); it < 4 * n; it += n2) {
-    const int dz = it / (2 * n), fl = (it / n) & 1, r = it % n;   // dz: 0 y-faces, 1 z-faces
-    R tv[n], td[n], ov[n], od[n];
-    const bool present = dz == 1 || (fl ? has_yp : has_ym);
-    const R *src = NB + (dz * 2 + fl) * cpb * n3 + cl * n3;
+    for (int it = l; it < 4 * n; it += n2) {   // one item per thread for k >= 3
+      const int iq = it / n, ir = it - iq * n;
+      const int fl = iq >> 1, arr = iq & 1;
 #pragma unroll
-    for (int x = 0; x < n; ++x) {
-      // the neighbour's line normal to the face at (x, r); its end on the shared face: fl 0 -> xi = 1
-      R w[n];
-      const int b0 = dz == 0 ? x + n2 * r : x + n * r, st = dz == 0 ? n : n2;
+      for (int isz = 0; isz < 2; ++isz) {
+        const R *src = TR + ((cl * 6 + (isz ? 4 : 2) + fl) * 2 + arr) * n2 + n * ir;
+        R *dst = (isz ? TZ : TY) + ((cl * 2 + fl) * 2 + arr) * n2 + n * ir;
+        R v[n], o[n];
 #pragma unroll
-      for (int b = 0; b < n; ++b) w[b] = present ? src[b0 + b * st] : r_zero<R>();
-      tv[x] = fl ? w[0] : w[n - 1];
-      R dsum = r_zero<R>();
+        for (int b = 0; b < n; ++b) v[b] = src[b];
+        mass_line<R, K>(v, o);
 #pragma unroll
-      for (int b = 0; b < n; ++b) dsum = r_fma(fl ? C.D[0][b] : C.D[1][b], w[b], dsum);
-      td[x] = dsum;
+        for (int a = 0; a < n; ++a) dst[a] = o[a];
+      }
     }
-    mass_line<R, K>(tv, ov);
-    mass_line<R, K>(td, od);
-    R *dst = (dz == 0 ? TY : TZ) + ((cl * 2 + fl) * 2) * n2 + n * r;
-#pragma unroll
-    for (int a = 0; a < n; ++a) { dst[a] = ov[a]; dst[n2 + a] = od[a]; }
   }
   __syncthreads();
   // ---- phase B: y-lines at (x, z) = (lr, lq): W = M_y T1 + Ly T2 + nbr_y', T3 = M_y T2; z-face
-  // traces (indexed x + n*y) <- M_y (items it < 4n: face (it / n) >> 1, array (it / n) & 1, x = it % n)
+  // traces (indexed x + n*y) <- M_y (items it as in phase A, x = it % n)
   if (line) {
     const int base = cl * n3 + lr + n2 * lq;
     R a1[n], a2[n], w[n], t3[n], ly[n];
@@ -263,17 +220,18 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
     mass_line<R, K>(a2, t3);
 #pragma unroll
     for (int b = 0; b < n; ++b) { A[base + n * b] = w[b] + ly[b]; B[base + n * b] = t3[b]; }
-  }
-  for (int it = (line ? l : 4 * n); it < 4 * n; it += n2) {
-    const int iq = it / n, ir = it - iq * n;
-    const int fl = iq >> 1, arr = iq & 1;
-    R *ln = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + ir;   // in place: this item owns the line
-    R v[n], o[n];
+    for (int it = l; it < 4 * n; it += n2) {
+      const int iq = it / n, ir = it - iq * n;
+      const int fl = iq >> 1, arr = iq & 1;
+      const R *src = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + ir;
+      R *dst = TR + ((cl * 6 + 4 + fl) * 2 + arr) * n2 + ir;
+      R v[n], o[n];
 #pragma unroll
-    for (int b = 0; b < n; ++b) v[b] = ln[n * b];
-    mass_line<R, K>(v, o);
+      for (int b = 0; b < n; ++b) v[b] = src[n * b];
+      mass_line<R, K>(v, o);
 #pragma unroll
-    for (int a = 0; a < n; ++a) ln[n * a] = o[a];
+      for (int a = 0; a < n; ++a) dst[n * a] = o[a];
+    }
   }
   __syncthreads();
   // ---- phase C: z-lines at l = x + n*y (y = M_z W + Lz T3 + nbr_z'')
@@ -282,8 +240,8 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
     R a1[n], a2[n], w[n], lz[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) { a1[e] = A[base + n2 * e]; a2[e] = B[base + n2 * e]; }
-    const R v0 = TZ[((cl * 2 + 0) * 2 + 0) * n2 + l], d0 = TZ[((cl * 2 + 0) * 2 + 1) * n2 + l];
-    const R v1 = TZ[((cl * 2 + 1) * 2 + 0) * n2 + l], d1 = TZ[((cl * 2 + 1) * 2 + 1) * n2 + l];
+    const R v0 = TR[((cl * 6 + 4) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 4) * 2 + 1) * n2 + l];
+    const R v1 = TR[((cl * 6 + 5) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 5) * 2 + 1) * n2 + l];
     line_op<R, K>(a2, Rs + 16, v0, d0, v1, d1, lz);
     mass_line<R, K>(a1, w);
 #pragma unroll
@@ -307,10 +265,11 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
   }
 }
 
-template <typename R>
+template <typename T>
 static size_t box_smem(int n, int cpb) {
   const int n2 = n * n, n3 = n2 * n;
-  return sizeof(R) * ((size_t)32 + (7 * (size_t)cpb + 2) * n3 + 8 * (size_t)cpb * n2);
+  return sizeof(T) * ((size_t)kRowScal + 3 * (size_t)cpb * n3 + (size_t)cpb * (24 + 8 + 8) * n2) +
+         sizeof(int) * (size_t)cpb * 6;
 }
 
 // cells per CTA: the largest power of two dividing nx with cpb*(k+1)^2 <= 256 and cpb <= 8

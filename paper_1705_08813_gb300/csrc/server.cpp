@@ -136,7 +136,10 @@ struct dgw_server {
   // cannot host a block (its multigrid needs the iterative coarse solve).
   bool run_batch(JobRec *r, MeshSlot *slot, cudaStream_t s) {
     dgw_mesh *M = slot->mesh;
-    const int cheb = r->job.opts.cheb_degree > 0 ? r->job.opts.cheb_degree : 5;
+    // r is finished after its first rounds and its record freed once the client polls it: keep
+    // what later admissions compare against
+    const dgw_job key = r->job;
+    const int cheb = key.opts.cheb_degree > 0 ? key.opts.cheb_degree : 5;
     if (M->batch && M->batch_cheb != cheb) { dgw::batch_destroy(M->batch); M->batch = nullptr; }
     if (!M->batch) {
       dgw::Batch *B = nullptr;
@@ -155,7 +158,10 @@ struct dgw_server {
         c.tag = q->ticket;
         c.rtol = q->job.opts.rtol;
         c.max_iter = q->job.opts.max_iter;
-        if (dgw::batch_admit(B, c, s) != cudaSuccess) finish(q, DGW_ECUDA, dgw_solve_info{});
+        if (dgw::batch_admit(B, c, s) != cudaSuccess) {
+          (void)cudaGetLastError();   // handled here: must not surface in a later call of this thread
+          finish(q, DGW_ECUDA, dgw_solve_info{});
+        }
       }
       incoming.clear();
       if (dgw::batch_active(B) == 0) break;
@@ -163,6 +169,7 @@ struct dgw_server {
       const cudaError_t e = dgw::batch_round(B, done);
       if (e != cudaSuccess) {
         // a failed round: every column of the block fails, and the block is rebuilt on next use
+        (void)cudaGetLastError();
         dgw::batch_destroy(M->batch);
         M->batch = nullptr;
         std::lock_guard<std::mutex> lock(mu);
@@ -186,7 +193,7 @@ struct dgw_server {
       slot->batch_cheb = cheb;
       for (auto qi = queue.begin(); qi != queue.end() && room > 0;) {
         JobRec *q = jobs[*qi].get();
-        if (batchable(q->job) && same_batch(q->job, r->job)) {
+        if (batchable(q->job) && same_batch(q->job, key)) {
           q->started = true;
           q->t_start = clock_type::now();
           q->in_batch = M;
@@ -231,6 +238,7 @@ struct dgw_server {
   }
 
   void run_job(JobRec *r, MeshSlot *slot, cudaStream_t s) {
+    (void)cudaGetLastError();   // an error an earlier job of this thread handled is not this job's
     dgw_status st = DGW_OK;
     if (!slot->mesh) {
       st = dgw_mesh_create(&slot->params, s, &slot->mesh);

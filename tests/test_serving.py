@@ -128,3 +128,42 @@ def test_admission_by_memory_budget(dgw):
         assert torch.equal(y, out)
     assert srv.stats()["reserved_bytes"] <= 24 << 20
     srv.close()
+
+
+def test_stream_of_block_solves_on_two_meshes(dgw):
+    """Solves arrive one by one on two meshes of the same degree while finished ones are polled (and
+    their records freed) as soon as they complete: a block keeps admitting only solves of its own
+    mesh, and every solve meets its tolerance with the result it has alone."""
+    wx = I.Workload("x", 8, 6, 4, 3, 395.0, 1.0 / 6000.0, seed=51)
+    wy = I.Workload("y", 6, 6, 4, 3, 395.0, 1.0 / 6000.0, seed=52)
+    jobs = []
+    for j in range(24):
+        w = wx if j % 3 else wy
+        m, inp, out = _inputs(dgw, 0, w, 0, 200 + j)
+        jobs.append((w, m, inp, out))
+    refs = [_alone(m, 0, inp, torch.zeros_like(out), 1) for (w, m, inp, out) in jobs]
+    srv = dgw.Server(16 << 30, max_inflight=4)
+    tickets, res = {}, {}
+    t0 = time.time()
+    for j, (w, m, inp, out) in enumerate(jobs):
+        tickets[srv.submit(0, dgw.mesh_params(w), inp, out, mode=1)] = j
+        for t in list(tickets):
+            if t not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.002)
+    while len(res) < len(tickets):
+        for t in list(tickets):
+            if t not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[t] = r
+        assert time.time() - t0 < 120.0, "jobs did not complete"
+        time.sleep(0.001)
+    srv.close()
+    for t, j in tickets.items():
+        assert res[t]["status"] == 0, (j, res[t])
+        assert res[t]["rel_residual"] <= 1e-10
+        got, ref = jobs[j][3].cpu().numpy(), refs[j].cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max(), j
