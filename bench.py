@@ -267,6 +267,26 @@ def _time_solves(m, b, p, modes, reps, flush):
     return out
 
 
+def _time_block_solves(m, b, ncols, reps, flush):
+    """solves/s of one block solve of ncols right-hand sides (dgw_pressure_solve_batch; the columns
+    are b scaled by 1..ncols, so every column runs the same iterations as b alone)."""
+    import torch
+    from paper_1705_08813_gb300 import dgw
+    bs = [b * (c + 1) for c in range(ncols)]
+    ps = [torch.zeros_like(b) for _ in range(ncols)]
+    dgw.pressure_solve_batch(m, bs, ps, rtol=1e-10, max_iter=500)
+    ts, infos = [], None
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = dgw.pressure_solve_batch(m, bs, ps, rtol=1e-10, max_iter=500)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    return {"columns": ncols, "solves_per_s": ncols / t, "ms": 1e3 * t,
+            "iterations": max(i["iterations"] for i in infos), "rel_residual": max(i["rel_residual"] for i in infos)}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -467,6 +487,9 @@ def run_gpu(args):
     solves = {}
     p_sol = torch.zeros(m.n_p, dtype=torch.float64, device=dev)
     solves[w.name] = _time_solves(m, b_div, p_sol, (("fp64", 0), ("mixed", 1)), 3, flush)
+    # the same mixed solve as a block of 8 right-hand sides (the request loop's batched form)
+    solves[w.name]["mixed_block"] = _time_block_solves(m, b_div, 8, 3, flush)
+    solves[w.name]["block_over_mixed"] = solves[w.name]["mixed_block"]["solves_per_s"] / solves[w.name]["mixed"]["solves_per_s"]
     if not args.no_extra_solves and world == 1:
         w3 = I.WORKLOADS["channel_q3_64x32x32"]
         m3 = dgw.mesh_for(w3)
@@ -658,7 +681,8 @@ def run_serving(args):
 
 
 def run_helmholtz(args):
-    """Viscous step of the dual-splitting scheme on the workload: velocity mass apply (FP64, FP32) and the
+    """Viscous step of the dual-splitting scheme on the workload: velocity mass apply (FP64, FP32; the FP64
+    viscous, convective and divergence applies beside it) and the
     Helmholtz solve gamma M u - F^nu(u) = gamma M u^ (gamma = 1.5 / dt, BDF2, dt = args.dt) to 1e-10 with
     restarted GMRES, nu_t frozen from the workload's velocity field, initial guess u^. --enrich-l 0 takes the
     constant enrichment weight (one coefficient per component and wall cell) instead of the trilinear one."""
@@ -679,7 +703,10 @@ def run_helmholtz(args):
     y32 = torch.empty(m.n_u, dtype=torch.float32, device="cuda")
     u32 = u_hat.float()
     times = {}
-    for name, fn in (("mass64", lambda: m.mass(u_hat, y)), ("mass32", lambda: m.mass(u32, y32))):
+    b = torch.empty(m.n_p, dtype=torch.float64, device="cuda")
+    for name, fn in (("mass64", lambda: m.mass(u_hat, y)), ("mass32", lambda: m.mass(u32, y32)),
+                     ("viscous64", lambda: m.viscous(u_hat, y)), ("convective64", lambda: m.convective(u_hat, y)),
+                     ("divergence64", lambda: m.divergence(u_hat, b))):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -704,6 +731,8 @@ def run_helmholtz(args):
                       "workload": w.name, "enrich_l": args.enrich_l, "n_u": m.n_u, "gamma": gamma, "dt": args.dt, "restart": args.restart,
                       "mass_fp64_ms": times["mass64"], "mass_fp64_gdofs": m.n_u / (times["mass64"] * 1e-3) / 1e9,
                       "mass_fp32_ms": times["mass32"], "mass_fp32_gdofs": m.n_u / (times["mass32"] * 1e-3) / 1e9,
+                      "viscous_fp64_ms": times["viscous64"], "convective_fp64_ms": times["convective64"],
+                      "divergence_fp64_ms": times["divergence64"],
                       "solve_ms": ms, "solves_per_s": 1e3 / ms, "iterations": infos[-1]["iterations"],
                       "rel_residual": infos[-1]["rel_residual"]}), flush=True)
     return 0

@@ -90,7 +90,8 @@ typedef struct {
   int precision_mask;  /* bit 0: FP64 tables, bit 1: FP32 tables (for DGW_FP32 applies) */
   int full_quadrature; /* 1: enriched cells take q_wall Gauss points in every direction and faces
                           touching them q_wall per tangential direction (the paper's 8^3 to 12^3
-                          rule, Sec. 4.4); 0: q_wall wall-normal only. Channel geometry only. */
+                          rule, Sec. 4.4); 0: q_wall wall-normal only. Both geometries (curved
+                          meshes then also tabulate their metric at the q_wall^2 in-plane points). */
 } dgw_mesh_params;
 
 /* Build a mesh: geometry, penalty parameters tau_IP (Sec. 4.2: (k+1)^2 A(dK)/V(K), interior

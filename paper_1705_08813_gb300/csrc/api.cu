@@ -100,8 +100,6 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
   if (P->enrich_l != 0 && P->enrich_l != 1) return set_error(DGW_EINVAL, "dgw_mesh_create: enrich_l must be 0 or 1");
   if (P->full_quadrature != 0 && P->full_quadrature != 1)
     return set_error(DGW_EINVAL, "dgw_mesh_create: full_quadrature must be 0 or 1");
-  if (P->full_quadrature && P->geometry != 0)
-    return set_error(DGW_EINVAL, "dgw_mesh_create: full_quadrature is implemented for the channel geometry only");
   if (P->q_wall < 1 || P->q_wall > QW_MAX) return set_error(DGW_EINVAL, "dgw_mesh_create: q_wall must be in 1..10");
   if (!(P->lx > 0 && P->ly > 0 && P->lz > 0 && P->stretch_gamma > 0 && P->nu > 0 && P->tau_w > 0))
     return set_error(DGW_EINVAL, "dgw_mesh_create: lengths, gamma, nu and tau_w must be positive");
@@ -234,9 +232,11 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *P, void *stream, dgw_mesh_t *o
         *d32 = upload(M, f.data(), f.size(), s, &err);
       }
     };
-    for (int t = 0; t < NMVOL; ++t) up2(cg.mvol[t], &M->v64.mvol[t], &M->v32.mvol[t]);
+    for (int t = 0; t < NMVOL; ++t)
+      if (!cg.mvol[t].empty()) up2(cg.mvol[t], &M->v64.mvol[t], &M->v32.mvol[t]);
     for (int t = 0; t < NQSET; ++t) up2(cg.mxf[t], &M->v64.mxf[t], &M->v32.mxf[t]);
-    for (int t = 0; t < 2; ++t) up2(cg.myf[t], &M->v64.myf[t], &M->v32.myf[t]);
+    for (int t = 0; t < NQSET; ++t)
+      if (!cg.myf[t].empty()) up2(cg.myf[t], &M->v64.myf[t], &M->v32.myf[t]);
     up2(cg.lvol, &M->v64.lvol, &M->v32.lvol);
     up2(cg.lface, &M->v64.lface, &M->v32.lface);
   } else {

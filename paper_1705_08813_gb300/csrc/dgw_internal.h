@@ -42,8 +42,10 @@ enum { GEO_BOX = 0, GEO_CURVED = 1 };
 
 // Metric record of a curved cell at one point: J^-1 row-major ([r*3+c] = d xi_r / d x_c), det J.
 constexpr int MREC = 10;
-// Volume metric tables by (x-set, y-set): (lin, lin), (conv, conv), (lin, wall), (conv, wall).
-constexpr int NMVOL = 4;
+// Volume metric tables by (x-set, y-set): (lin, lin), (conv, conv), (lin, wall), (conv, wall) and,
+// for the q_w^3 rule in enriched cells (full_quadrature), (wall, wall).
+constexpr int NMVOL = 5;
+constexpr int MVOL_WALL_WALL = 4;
 
 // Device-side view of a mesh in precision T.
 template <typename T>
@@ -64,10 +66,11 @@ struct MeshView {
   const T *rowops;    // [ny][24] per-row scalars of the factorised Laplace operator (boxes)
   // curved metric tables per metric column m = i + nx*j (the map is an extrusion along z):
   // mvol[pair]: [m][a1][a0][MREC]; mxf[y-set]: [m][side][a1][MREC] (faces xi_0 = side);
-  // myf[x-set]: [m][side][a0][MREC] (faces xi_1 = side); faces xi_2 = side use mvol
+  // myf[x-set]: [m][side][a0][MREC] (faces xi_1 = side); faces xi_2 = side use mvol. The tables of
+  // the (wall, wall) pair and myf[QSET_WALL] exist only on meshes with the q_w^3 rule.
   const T *mvol[NMVOL];
   const T *mxf[NQSET];
-  const T *myf[2];
+  const T *myf[NQSET];
   // curved SIPG Laplacian tables per metric column (k+1 Gauss points): lvol [m][(k+1)^3][6] =
   // |det J| w J^-1 J^-T (xx yy zz xy xz yz); lface [m][6][(k+1)^2][7] = dA, dA J^-1 n of the own
   // side, dA J^-1 n of the neighbour at the shared point (n the own outward normal; zero on walls)
@@ -189,7 +192,7 @@ void host_box_apply(const BoxGeometry &g, const Basis<double> &B, const std::vec
 // with nx x ny x nz cells of degree k over the bump map of the parameters.
 struct CurvedHost {
   int nx, ny, nz, k;
-  std::vector<double> mvol[NMVOL], mxf[NQSET], myf[2];   // layouts as in MeshView
+  std::vector<double> mvol[NMVOL], mxf[NQSET], myf[NQSET];   // layouts as in MeshView
   std::vector<double> tau;                               // [nx*ny] per metric column
   std::vector<double> lvol, lface;                       // Laplace tables (layout as in MeshView)
   std::vector<double> xn, yn;                            // [nx*ny][n*n] nodal (x, y), x-node fastest

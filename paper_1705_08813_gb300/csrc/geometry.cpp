@@ -154,8 +154,11 @@ void curved_geometry(const dgw_mesh_params &P, int nx, int ny, int nz, int k, co
           bump_point(P, nx, ny, i + z[a], j + z[b], &G.xn[o], &G.yn[o]);
         }
   const int xsets[2] = {QSET_LIN, QSET_CONV};
+  const bool fq = P.full_quadrature != 0;   // the q_w^3 rule needs the wall set along x as well
   for (int pair = 0; pair < NMVOL; ++pair) {
-    const int sx = xsets[pair & 1], sy = (pair & 2) ? QSET_WALL : sx;
+    if (pair == MVOL_WALL_WALL && !fq) continue;
+    const int sx = pair == MVOL_WALL_WALL ? QSET_WALL : xsets[pair & 1];
+    const int sy = (pair & 2) || pair == MVOL_WALL_WALL ? QSET_WALL : sx;
     const int qx = B.q[sx], qy = B.q[sy];
     G.mvol[pair].assign((size_t)ncol * qx * qy * MREC, 0.0);
     for (int m = 0; m < ncol; ++m)
@@ -173,13 +176,14 @@ void curved_geometry(const dgw_mesh_params &P, int nx, int ny, int nz, int k, co
           column_metric(n, z, &G.xn[(size_t)m * n * n], &G.yn[(size_t)m * n * n], hz, (double)side, B.x[set][a],
                         &G.mxf[set][(((size_t)m * 2 + side) * q + a) * MREC]);
   }
-  for (int set = 0; set < 2; ++set) {
-    const int q = B.q[xsets[set]];
+  for (int set = 0; set < NQSET; ++set) {
+    if (set == QSET_WALL && !fq) continue;
+    const int q = B.q[set];
     G.myf[set].assign((size_t)ncol * 2 * q * MREC, 0.0);
     for (int m = 0; m < ncol; ++m)
       for (int side = 0; side < 2; ++side)
         for (int a = 0; a < q; ++a)
-          column_metric(n, z, &G.xn[(size_t)m * n * n], &G.yn[(size_t)m * n * n], hz, B.x[xsets[set]][a], (double)side,
+          column_metric(n, z, &G.xn[(size_t)m * n * n], &G.yn[(size_t)m * n * n], hz, B.x[set][a], (double)side,
                         &G.myf[set][(((size_t)m * 2 + side) * q + a) * MREC]);
   }
   // penalty tau_IP = (k+1)^2 A/V with (k+2)-point Gauss integration of the curved cell (interior

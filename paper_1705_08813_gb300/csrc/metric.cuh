@@ -37,7 +37,8 @@ __device__ __forceinline__ int metric_col(const MeshView<T> &m, int c) { return 
 template <typename T>
 __device__ __forceinline__ const T *vol_rec(const MeshView<T> &m, const Basis<T> &B, int col, int sx, int sy, int a0,
                                             int a1) {
-  const int pair = (sx == QSET_CONV ? 1 : 0) + (sy == QSET_WALL ? 2 : 0);
+  // (wall, wall): the q_w^3 rule, where a wall x-set always comes with a wall y-set
+  const int pair = sx == QSET_WALL ? MVOL_WALL_WALL : (sx == QSET_CONV ? 1 : 0) + (sy == QSET_WALL ? 2 : 0);
   const int qx = B.q[sx], qy = B.q[sy];
   return m.mvol[pair] + ((size_t)col * qx * qy + a0 + qx * a1) * MREC;
 }

@@ -640,9 +640,10 @@ static void upload_curved(Lvl<X> *L, const CurvedHost &g, MeshView<X> &v, cudaEr
     return d;
   };
   v.geo = GEO_CURVED;
-  for (int t = 0; t < NMVOL; ++t) v.mvol[t] = up(g.mvol[t]);
+  // the pressure levels carry no enrichment: the tables of the default point sets only
+  for (int t = 0; t < NMVOL; ++t) v.mvol[t] = g.mvol[t].empty() ? nullptr : up(g.mvol[t]);
   for (int t = 0; t < NQSET; ++t) v.mxf[t] = up(g.mxf[t]);
-  for (int t = 0; t < 2; ++t) v.myf[t] = up(g.myf[t]);
+  for (int t = 0; t < NQSET; ++t) v.myf[t] = g.myf[t].empty() ? nullptr : up(g.myf[t]);
   v.lvol = up(g.lvol);
   v.lface = up(g.lface);
   std::vector<double> tau((size_t)g.nx * g.ny * g.nz);
@@ -702,7 +703,9 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
       L->view.slot = nullptr;
       if (curved) {
         CurvedHost cg;
-        curved_geometry(M->P, nx, ny, nz, k, M->basis64, cg);
+        dgw_mesh_params Pl = M->P;
+        Pl.full_quadrature = 0;   // no enriched cells on the pressure levels
+        curved_geometry(Pl, nx, ny, nz, k, M->basis64, cg);
         upload_curved<T>(L, cg, L->view, e, s);
         v64 = M->v64;
         v64.nx = nx; v64.ny = ny; v64.nz = nz;
@@ -836,7 +839,9 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
     if (curved) {
       // degree-1 tables and basis of the coarsest cells for the dense assembly
       CurvedHost cg;
-      curved_geometry(M->P, C->geo.nx, C->geo.ny, C->geo.nz, 1, b1d, cg);
+      dgw_mesh_params Pl = M->P;
+      Pl.full_quadrature = 0;
+      curved_geometry(Pl, C->geo.nx, C->geo.ny, C->geo.nz, 1, b1d, cg);
       Lvl<double> tmp;
       d64.n1 = 2;
       d64.np = D->n;

@@ -20,6 +20,8 @@
 // Every sum-factorisation phase is batched over the velocity components, over both faces normal
 // to one direction and over both sides of those faces, so one barrier separates phases that each
 // carry enough independent outputs to occupy the CTA (about 35 barriers per cell).
+#include <type_traits>
+
 #include "df64.cuh"
 #include "metric.cuh"
 #include "sumfac.cuh"
@@ -152,6 +154,70 @@ __device__ void reduce24(int npts, F contrib, T *out, T *part) {
   __syncthreads();
 }
 
+// The same for the 3 enriched test functions psi e_a of the constant weight (l = 0): plain warp
+// sums, then the warps' partial sums in a fixed order. part holds 3 T per warp. Ends with a barrier.
+template <typename T, typename F>
+__device__ void reduce3(int npts, F contrib, T *out, T *part) {
+  T acc[3] = {T(0), T(0), T(0)};
+  for (int p = threadIdx.x; p < npts; p += blockDim.x) contrib(p, acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+  if (lane == 0)
+    for (int i = 0; i < 3; ++i) part[warp * 3 + i] = acc[i];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    T sum = T(0);
+    for (int w = 0; w < nw; ++w) sum += part[w * 3 + threadIdx.x];
+    out[threadIdx.x] += sum;
+  }
+  __syncthreads();
+}
+
+// Enriched test-function integrals over npts points into out: contrib(p, acc, NV) adds the
+// contributions of point p for NV weights per component (8: the trilinear weights of l = 1, output
+// a * 8 + v; 1: the constant weight of l = 0, output a).
+template <typename T, typename F>
+__device__ __forceinline__ void reduce_enr(bool l0, int npts, F contrib, T *out, T *part) {
+  if (l0) reduce3<T>(npts, [&](int p, T *acc) { contrib(p, acc, std::integral_constant<int, 1>{}); }, out, part);
+  else reduce24<T>(npts, [&](int p, T *acc) { contrib(p, acc, std::integral_constant<int, 8>{}); }, out, part);
+}
+
+// Enrichment of one component at a point with 1-D weight factors f: sN = sum_v N_v e_v and
+// sD_d = sum_v dN_v/dxi_d e_v over the 8 trilinear weights (e: 8 coefficients); with the constant
+// weight (l = 0) sN = e_0 and sD = 0.
+template <typename T, bool GRADN>
+__device__ __forceinline__ void enr_trial(const T f[3][2], const T *e, bool l0, T &sN, T sD[3]) {
+  sN = T(0);
+  sD[0] = sD[1] = sD[2] = T(0);
+  if (l0) {
+    sN = e[0];
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    T Nv, dN[3];
+    q1_vertex(f, v, Nv, dN);
+    sN += Nv * e[v];
+    if (GRADN)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) sD[d] += dN[d] * e[v];
+  }
+}
+
+// Value and reference gradient of the enrichment weight v of NV at the point (l = 0: 1 and 0).
+template <typename T, int NV>
+__device__ __forceinline__ void enr_weight(const T f[3][2], int v, T &Nv, T dN[3]) {
+  if (NV == 1) {
+    Nv = T(1);
+    dN[0] = dN[1] = dN[2] = T(0);
+  } else {
+    q1_vertex(f, v, Nv, dN);
+  }
+}
+
 // Shared-memory plan (in T words) for one cell. The volume and face phases share one work
 // region; inside the face region the neighbour coefficients share room with the arrays written
 // after the layer traces are taken, and the integration arrays with the trace arrays.
@@ -259,6 +325,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
   }
   const int ec = OP == OP_LAP ? -1 : m.enr[c];
   const bool enr_c = ec >= 0;
+  const bool l0 = m.nef == 1;   // constant enrichment weight: 3 test functions psi e_a per cell
   const T nu = m.visc;
   const int col = CURVED ? metric_col(m, c) : 0;
   for (int t = threadIdx.x; t < NIN * n3; t += blockDim.x) uo[t] = u[(size_t)c * NIN * n3 + t];
@@ -335,17 +402,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
         const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          T Nv, dN[3];
-          q1_vertex(f, v, Nv, dN);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            sN[a] += Nv * eo[a * 8 + v];
-            if (GRAD)
-#pragma unroll
-              for (int d = 0; d < 3; ++d) sD[a][d] += dN[d] * eo[a * 8 + v];
-          }
-        }
+        for (int a = 0; a < 3; ++a) enr_trial<T, GRAD>(f, eo + a * 8, l0, sN[a], sD[a]);
         w = wtv + t * WT;
       }
       if (OP == OP_DIV || OP == OP_CONV || OP == OP_MASS) {
@@ -435,7 +492,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     // enriched test functions: -(grad(psi N_v) e_a, u x u), (eps(psi N_v e_a), 2(nu+nu_t) eps(u~)) or
     // (div(psi N_v e_a), tau_D div u)
     if (enr_c && (OP == OP_CONV || OP == OP_VISC || OP == OP_DIVDIV)) {
-      auto contrib = [&](int t, T *acc) {
+      auto contrib = [&](int t, T *acc, auto nvc) {
+        constexpr int NV = decltype(nvc)::value;
         const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
         const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
         const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
@@ -463,11 +521,14 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
             for (int d = 0; d < 3; ++d) cf[a][d] = nd * (Gt[(a * 3 + d) * P + t] + Gt[(d * 3 + a) * P + t]);
         }
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < NV; ++v) {
           T Nv, dN[3];
-          q1_vertex(f, v, Nv, dN);
+          enr_weight<T, NV>(f, v, Nv, dN);
           T g[3];
-          if (CURVED) {
+          if (NV == 1) {   // grad psi
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[d] = w[1 + d];
+          } else if (CURVED) {
             T gp[3];
             ref_to_phys(Ji, dN, gp);
 #pragma unroll
@@ -477,29 +538,30 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
             for (int d = 0; d < 3; ++d) g[d] = w[0] * dN[d] * hinv[d] + Nv * w[1 + d];
           }
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cf[a][0] * g[0] + cf[a][1] * g[1] + cf[a][2] * g[2];
+          for (int a = 0; a < 3; ++a) acc[a * NV + v] += cf[a][0] * g[0] + cf[a][1] * g[1] + cf[a][2] * g[2];
         }
       };
-      reduce24<T>(P, contrib, re, S0 + L.part);
+      reduce_enr<T>(l0, P, contrib, re, S0 + L.part);
     }
     if (OP == OP_MASS) {
       // enriched test functions: (psi N_v e_a, u)
       if (enr_c) {
-        auto contrib = [&](int t, T *acc) {
+        auto contrib = [&](int t, T *acc, auto nvc) {
+          constexpr int NV = decltype(nvc)::value;
           const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
           const T xi[3] = {B.x[sets[0]][i0], B.x[sets[1]][i1], B.x[sets[2]][i2]};
           const T f[3][2] = {{T(1) - xi[0], xi[0]}, {T(1) - xi[1], xi[1]}, {T(1) - xi[2], xi[2]}};
           const T psi = wtv[t * WT];
           const T pv[3] = {psi * G[t], psi * G[P + t], psi * G[2 * P + t]};   // dV psi u_a
 #pragma unroll
-          for (int v = 0; v < 8; ++v) {
+          for (int v = 0; v < NV; ++v) {
             T Nv, dN[3];
-            q1_vertex(f, v, Nv, dN);
+            enr_weight<T, NV>(f, v, Nv, dN);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc[a * 8 + v] += Nv * pv[a];
+            for (int a = 0; a < 3; ++a) acc[a * NV + v] += Nv * pv[a];
           }
         };
-        reduce24<T>(P, contrib, re, S0 + L.part);
+        reduce_enr<T>(l0, P, contrib, re, S0 + L.part);
       }
       // integrate the value coefficients back to the nodes: S_z^T, S_y^T, S_x^T
       pass_batch<T>([&](int a) -> Pass<T> {
@@ -648,16 +710,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           // enrichment u~_a = psi sum_v N_v e_av and its physical gradient
           if (enr_c) {
             const T *w = wts + pt * WT;
-            T sN = T(0), sD[3] = {0, 0, 0};
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              T Nv, dN[3];
-              q1_vertex(fs, v, Nv, dN);
-              sN += Nv * eo[a * 8 + v];
-              if (GRAD)
-#pragma unroll
-                for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eo[a * 8 + v];
-            }
+            T sN, sD[3];
+            enr_trial<T, GRAD>(fs, eo + a * 8, l0, sN, sD);
             ut_s[a] = w[0] * sN;
             if (GRAD)
 #pragma unroll
@@ -675,17 +729,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
             }
             if (wto) {
               const T *w = wto + pt * WT;
-              const T *eb_a = en + s * 24 + a * 8;
-              T sN = T(0), sD[3] = {0, 0, 0};
-#pragma unroll
-              for (int v = 0; v < 8; ++v) {
-                T Nv, dN[3];
-                q1_vertex(fo, v, Nv, dN);
-                sN += Nv * eb_a[v];
-                if (GRAD)
-#pragma unroll
-                  for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eb_a[v];
-              }
+              T sN, sD[3];
+              enr_trial<T, GRAD>(fo, en + s * 24 + a * 8, l0, sN, sD);
               ut_o[a] = w[0] * sN;
               if (GRAD)
 #pragma unroll
@@ -784,16 +829,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           }
           if (OP != OP_LAP && enr_c) {
             const T *w = wts + pt * WT;
-            T sN = T(0), sD[3] = {0, 0, 0};
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              T Nv, dN[3];
-              q1_vertex(fs, v, Nv, dN);
-              sN += Nv * eo[a * 8 + v];
-              if (GRAD)
-#pragma unroll
-                for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eo[a * 8 + v];
-            }
+            T sN, sD[3];
+            enr_trial<T, GRAD>(fs, eo + a * 8, l0, sN, sD);
             ut_s[a] = w[0] * sN;
             if (GRAD) {
               T gp[3];
@@ -813,17 +850,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
             }
             if (OP != OP_LAP && wto) {
               const T *w = wto + pt * WT;
-              const T *eb_a = en + s * 24 + a * 8;
-              T sN = T(0), sD[3] = {0, 0, 0};
-#pragma unroll
-              for (int v = 0; v < 8; ++v) {
-                T Nv, dN[3];
-                q1_vertex(fo, v, Nv, dN);
-                sN += Nv * eb_a[v];
-                if (GRAD)
-#pragma unroll
-                  for (int e = 0; e < 3; ++e) sD[e] += dN[e] * eb_a[v];
-              }
+              T sN, sD[3];
+              enr_trial<T, GRAD>(fo, en + s * 24 + a * 8, l0, sN, sD);
               ut_o[a] = w[0] * sN;
               if (GRAD) {
                 T gp[3];
@@ -928,7 +956,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     __syncthreads();
     // enriched tests on these two faces
     if (enr_c && (OP == OP_CONV || OP == OP_VISC)) {
-      auto contrib = [&](int t, T *acc) {
+      auto contrib = [&](int t, T *acc, auto nvc) {
+        constexpr int NV = decltype(nvc)::value;
         const int s = t / FP, pt = t - s * FP;
         const int a1 = pt % p1, a2 = pt / p1;
         T xs[3];
@@ -947,12 +976,15 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           for (int b = 0; b < 3; ++b) cg[a][b] = OP == OP_VISC ? Es[(a * 4 + 1 + b) * L.FP + pt] : T(0);
         }
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < NV; ++v) {
           T Nv, dN[3];
-          q1_vertex(f, v, Nv, dN);
+          enr_weight<T, NV>(f, v, Nv, dN);
           if (OP == OP_VISC) {
             T g[3];
-            if (CURVED) {
+            if (NV == 1) {   // grad psi
+#pragma unroll
+              for (int b = 0; b < 3; ++b) g[b] = w[1 + b];
+            } else if (CURVED) {
               T gp[3];
               ref_to_phys(Js, dN, gp);
 #pragma unroll
@@ -962,14 +994,14 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
               for (int b = 0; b < 3; ++b) g[b] = w[0] * dN[b] * hinv[b] + Nv * w[1 + b];
             }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cv[a] * Nv + cg[a][0] * g[0] + cg[a][1] * g[1] + cg[a][2] * g[2];
+            for (int a = 0; a < 3; ++a) acc[a * NV + v] += cv[a] * Nv + cg[a][0] * g[0] + cg[a][1] * g[1] + cg[a][2] * g[2];
           } else {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc[a * 8 + v] += cv[a] * Nv;
+            for (int a = 0; a < 3; ++a) acc[a * NV + v] += cv[a] * Nv;
           }
         }
       };
-      reduce24<T>(2 * FP, contrib, re, S0 + L.part);
+      reduce_enr<T>(l0, 2 * FP, contrib, re, S0 + L.part);
     }
     // I1: along t2 (p2 -> n); I2: along t1 (p1 -> n); item k = (face s, component a)
     T *I0 = S0 + L.fI0, *I1 = S0 + L.fI1, *I2 = S0 + L.fI2, *F2 = S0 + L.fF2, *G2 = S0 + L.fG2;
@@ -1028,12 +1060,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       for (int t = threadIdx.x; t < 3 * m.nef; t += blockDim.x) y[3 * m.np + (size_t)m.slot[c] * 3 * m.nef + t] = T(0);
     } else if (enr_c && m.nef == 8)
       for (int t = threadIdx.x; t < 24; t += blockDim.x) y[3 * m.np + (size_t)ec * 24 + t] = re[t];
-    else if (enr_c && threadIdx.x < 3) {
-      // l = 0: the test function psi e_a is the sum of the 8 weighted ones
-      T acc = T(0);
-      for (int v = 0; v < 8; ++v) acc += re[threadIdx.x * 8 + v];
-      y[3 * m.np + (size_t)ec * 3 + threadIdx.x] = acc;
-    }
+    else if (enr_c && threadIdx.x < 3)   // l = 0: the integrals of psi e_a, accumulated in re[a]
+      y[3 * m.np + (size_t)ec * 3 + threadIdx.x] = re[threadIdx.x];
   }
 }
 

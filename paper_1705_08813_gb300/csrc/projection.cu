@@ -112,7 +112,7 @@ __global__ void project_solve_kernel(MeshView<double> m, const int *__restrict__
   const int colm = m.geo == GEO_CURVED ? metric_col(m, c) : 0;
   for (int t = tid; t < npts; t += nt) {
     const int i0 = t % q0, i1 = (t / q0) % q1, i2 = t / (q0 * q1);
-    const double det = m.geo == GEO_CURVED ? fabs(vol_rec(m, B, colm, QSET_LIN, QSET_WALL, i0, i1)[9]) : hbox;
+    const double det = m.geo == GEO_CURVED ? fabs(vol_rec(m, B, colm, sx, QSET_WALL, i0, i1)[9]) : hbox;
     W[t] = det * w0[i0] * w1[i1] * w0[i2];
     PSI[t] = wt_vol[((size_t)e * nvol + t) * WT];
   }

@@ -80,14 +80,14 @@ def test_null_handles_and_bad_options_are_rejected_without_a_device(lib):
 
 
 def test_mesh_options_are_validated_without_a_device(lib):
-    """enrich_l outside {0, 1}, full_quadrature outside {0, 1}, and the q_w^3 rule on the curved
-    geometry are rejected by dgw_mesh_create before any device work."""
+    """enrich_l outside {0, 1}, full_quadrature outside {0, 1} and q_wall outside 1..10 are rejected
+    by dgw_mesh_create before any device work."""
     from paper_1705_08813_gb300 import dgw
     L = dgw.load()
     bad = [
         (dgw.MeshParams(4, 4, 4, 2, 2, 8, 0, 0, 1, 6.28, 2.0, 3.14, 1.8, 1e-3, 1e-2, 3, 0), b"enrich_l"),
         (dgw.MeshParams(4, 4, 4, 2, 1, 8, 0, 0, 1, 6.28, 2.0, 3.14, 1.8, 1e-3, 1e-2, 3, 2), b"full_quadrature"),
-        (dgw.MeshParams(4, 4, 4, 2, 1, 8, 1, 0, 1, 9.0, 3.036, 4.5, 1.8, 1e-3, 1e-2, 3, 1), b"channel geometry"),
+        (dgw.MeshParams(4, 4, 4, 2, 1, 11, 1, 0, 1, 9.0, 3.036, 4.5, 1.8, 1e-3, 1e-2, 3, 1), b"q_wall"),
     ]
     for p, word in bad:
         h = ctypes.c_void_p()

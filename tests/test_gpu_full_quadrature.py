@@ -1,7 +1,8 @@
 """GPU parity under the paper-literal enriched quadrature (Sec. 4.4: q_w Gauss points in every
 direction of the enriched cells, q_w per tangential direction on faces touching them): every
 velocity operator, the wall shear stress, the L2 projection and dual-splitting steps against the
-oracle built with the same rule, on channel meshes (the option is implemented for boxes)."""
+oracle built with the same rule, on channel meshes and on curved bump meshes (whose metric is then
+also tabulated at the q_w^2 in-plane points of the enriched cells)."""
 import numpy as np
 import pytest
 
@@ -52,6 +53,10 @@ CASES = [
     ("ragged_q3_5x3x2_qwall_10", I.Workload("f3", 5, 3, 2, 3, 395.0, 1.0 / 6000.0, seed=92), {"q_wall": 10}),
     ("q4_two_layers_l0_vandriest", I.Workload("f4", 3, 4, 3, 4, 590.0, 1.0 / 12000.0, seed=93),
      {"n_layers": 2, "enrich_l": 0, "wall_law": 1}),
+    ("bump_q3_6x4x3", I.bump_workload("fb3", 6, 4, 3, 3, seed=102), {}),
+    ("bump_q2_5x4x2_qwall_10_l0", I.bump_workload("fb2", 5, 4, 2, 2, seed=103), {"q_wall": 10, "enrich_l": 0}),
+    ("bump_q4_4x4x2_two_layers_vandriest", I.bump_workload("fb4", 4, 4, 2, 4, seed=104),
+     {"n_layers": 2, "wall_law": 1}),
 ]
 
 
@@ -105,8 +110,14 @@ def _l2(om, d, ref):
     return float(np.sqrt(abs(d @ om.vmass(d)) / (ref @ om.vmass(ref))))
 
 
-def test_projection_and_time_steps_match_oracle(dgw):
-    w = I.Workload("fs", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=96)
+STEP_CASES = [
+    ("channel_q2_4x4x2", I.Workload("fs", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=96)),
+    ("bump_q2_6x4x2", I.bump_workload("fsb", 6, 4, 2, 2, seed=105)),
+]
+
+
+@pytest.mark.parametrize("name,w", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+def test_projection_and_time_steps_match_oracle(dgw, name, w):
     om, gm = _meshes(dgw, w)
     dev = torch.device("cuda:0")
     u = _velocity(om, w, {})
@@ -118,7 +129,7 @@ def test_projection_and_time_steps_match_oracle(dgw):
     assert _l2(om, got - ref, ref) < 1e-9
     om2, gm2 = _meshes(dgw, w)
     u0 = I.workload_velocity(om2.node_coords(), om2.n_e, w)
-    force = (w.tau_w, 0.0, 0.0)
+    force = (w.tau_w / (0.5 * w.ly), 0.0, 0.0)
     ds = O.DualSplitting(om2, u0, dt=2e-3, force=force, rtol=1e-13, high_order_pressure_bc=True)
     ns = dgw.DualSplitting(gm2, torch.tensor(u0, device=dev), dt=2e-3, force=force, rtol_pressure=1e-12,
                            rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0, high_order_pressure_bc=True)
@@ -127,7 +138,3 @@ def test_projection_and_time_steps_match_oracle(dgw):
         ur, _ = ds.step()
         assert _l2(om2, ns.velocity().cpu().numpy() - ur, ur) < 1e-8
 
-
-def test_full_quadrature_rejected_on_curved_meshes(dgw):
-    with pytest.raises(dgw.DGWError):
-        dgw.mesh_for(I.bump_workload("fb", 4, 4, 2, 2, seed=98), full_quadrature=True)
