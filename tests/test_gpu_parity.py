@@ -165,8 +165,24 @@ def test_pressure_solve_multigrid_modes(dgw, mode):
     bh = bh - bh.mean()
     res = np.linalg.norm(bh - om.laplace(p.cpu().numpy())) / np.linalg.norm(bh)
     assert info["rel_residual"] <= 1e-10 and res <= 1.5e-10, (info, res)
-    assert info["iterations"] < 60, info
+    assert info["iterations"] <= 20, info   # 35 with full coarsening of the graded rows
     assert abs(p.cpu().numpy().mean()) < 1e-14
+
+
+def test_multigrid_semi_coarsens_the_wall_normal_direction(dgw):
+    """The thin wall cells of the graded channel are coarsened along y alone (18432 -> 9216 cells)
+    until twice the thinnest row is above half the in-plane spacing; then every even direction; the
+    coarsest cells go to Q_1 and a dense solve. The mixed solve of a random right-hand side then takes
+    about half the iterations of full coarsening (41 -> 20)."""
+    w = I.WORKLOADS["channel_q4_32x24x24"]
+    gm = dgw.mesh_for(w)
+    cells = [c for c, _ in dgw.describe_solver(gm, 1)]
+    assert cells == [18432, 9216, 1152, 144, 144], cells
+    b = torch.tensor(I.pressure_rhs(gm.n_p, 3), device="cuda")
+    p = torch.zeros_like(b)
+    info = gm.pressure_solve(b, p, rtol=1e-10, max_iter=200, mode=1)
+    assert info["rel_residual"] <= 1e-10 and info["iterations"] <= 24, info
+    gm.close()
 
 
 @pytest.mark.parametrize("dims,k", [((6, 4, 4), 3), ((5, 6, 3), 2), ((4, 2, 4), 4)])
