@@ -19,6 +19,7 @@
 // three line passes (one thread owns a whole 1-D line in registers), with the y-face traces
 // transformed by M_x and the z-face traces by M_x M_y. A CTA holds cpb consecutive cells along x.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -51,15 +52,18 @@ __device__ __forceinline__ const BoxConst<double> &box_const<double>(int k) { re
 template <>
 __device__ __forceinline__ const BoxConst<df64> &box_const<df64>(int k) { return c_boxdf[k - 1]; }
 
-// FP32: up to 3 CTAs of <= 256 threads per SM for k <= 4 (register budget ~85/thread), 2 for k = 5;
-// FP64 is FP64-pipe bound and keeps the default budget; double-float (two registers per value,
-// about fifteen instructions per multiply-add) keeps two CTAs per SM.
-template <typename T, int K>
+// Register budget through the CTAs per SM the kernel is compiled for: FP32 56 registers a thread
+// (5 CTAs of 224 threads for k = 4), FP64 is FP64-pipe bound and keeps the default budget,
+// double-float (two registers per value, about fifteen instructions per multiply-add) two CTAs.
+template <typename T, int NT>
 struct BoxOcc { static constexpr int min_blocks = 1; };
-template <int K>
-struct BoxOcc<float, K> { static constexpr int min_blocks = K <= 4 ? 3 : 2; };
-template <int K>
-struct BoxOcc<df64, K> { static constexpr int min_blocks = 2; };
+template <int NT>
+struct BoxOcc<float, NT> {
+  static constexpr int v = 65536 / (NT * 56);
+  static constexpr int min_blocks = v < 1 ? 1 : (v > 8 ? 8 : v);
+};
+template <int NT>
+struct BoxOcc<df64, NT> { static constexpr int min_blocks = 2; };
 
 // One line of L_d u + N_d (tv, td) (see the file comment); R = the 8 scalars of direction d.
 template <typename T, int K>
@@ -100,24 +104,114 @@ __device__ __forceinline__ void mass_line(const T (&v)[K + 1], T (&out)[K + 1]) 
   }
 }
 
+// Shared-memory bank layout. Thread t owns line t / CPB of cell t % CPB (the cells of a warp
+// interleave), and every per-cell array has a padded cell stride. bank_cost counts the wavefronts
+// (the largest number of lanes on one 4-byte bank, summed over the warps) of the accesses
+// a(t) = stride * cell + f(line) of the three line passes: x-lines n l, y-lines (l mod n) + n^2 (l / n),
+// z-lines l (and the face-node index l of the traces); the stride with the fewest wavefronts in
+// [base, base + 32) wins. For k = 4 and 8 cells the stride 148 (= 20 mod 32) makes all three passes
+// conflict-free.
+constexpr int bank_cost(int stride, int n, int cpb, int pattern, bool cell_major = false, int lim = 1 << 30) {
+  int total = 0;
+  const int lines = cpb * n * n;
+  for (int w = 0; w * 32 < lines; ++w) {
+    int cnt[32] = {};
+    int mx = 0;
+    for (int i = 0; i < 32; ++i) {
+      const int t = w * 32 + i;
+      if (t >= lines) break;
+      const int cl = cell_major ? t / (n * n) : t % cpb, l = cell_major ? t % (n * n) : t / cpb;
+      if (l >= lim) continue;
+      const int f = pattern == 0 ? n * l : (pattern == 1 ? (l % n) + n * n * (l / n) : l);
+      const int b = (stride * cl + f) % 32;
+      if (++cnt[b] > mx) mx = cnt[b];
+    }
+    total += mx;
+  }
+  return total;
+}
+// kind 0: U, A, B (the three line passes); 1: the six-face trace array (written cell-major, 12 stores
+// a thread; read by the x- and z-passes, 4 loads each; M_x and M_y transform items of the first 4n
+// lines); 2: the y- and z-face arrays after M_x (transform writes, 4 loads of the y-pass)
+constexpr int stride_cost(int st, int n, int cpb, int kind) {
+  if (kind == 0) return bank_cost(st, n, cpb, 0) + bank_cost(st, n, cpb, 1) + bank_cost(st, n, cpb, 2);
+  if (kind == 1)
+    return 12 * bank_cost(st, n, cpb, 2, true) + 8 * bank_cost(st, n, cpb, 2) + 2 * n * bank_cost(st, n, cpb, 0, false, 4 * n) +
+           n * bank_cost(st, n, cpb, 1, false, 4 * n);
+  return 2 * n * bank_cost(st, n, cpb, 0, false, 4 * n) + 4 * bank_cost(st, n, cpb, 2) + n * bank_cost(st, n, cpb, 1, false, 4 * n);
+}
+constexpr int best_stride(int base, int n, int cpb, int kind) {
+  int best = base, cost = 1 << 30;
+  for (int pad = 0; pad < 32; ++pad) {
+    const int c = stride_cost(base + pad, n, cpb, kind);
+    if (c < cost) { cost = c; best = base + pad; }
+  }
+  return best;
+}
+
+// Launch shape of a CTA of CPB cells (a row segment along x): one thread per line of every cell.
+template <int K, int CPB>
+struct BoxShape {
+  static constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  static constexpr int lines = CPB * n2;
+  static constexpr int threads = ((lines + 31) / 32) * 32;
+  static constexpr int S = best_stride(n3, n, CPB, 0);        // cell stride of U, A, B
+  static constexpr int TS = best_stride(12 * n2, n, CPB, 1);  // six faces x (value, derivative)
+  static constexpr int YS = best_stride(4 * n2, n, CPB, 2);   // two faces x (value, derivative)
+  // shared memory in compute-type words: row scalars (padded to 32), U, A, B, traces of the six
+  // faces, y- and z-face traces after M_x
+  static constexpr int rs = 32;
+  static constexpr int words = rs + 3 * CPB * S + CPB * TS + 2 * CPB * YS;
+};
+
+// 16-byte vector of the storage type
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> { using type = float4; static constexpr int w = 4; };
+template <>
+struct Vec16<double> { using type = double2; static constexpr int w = 2; };
+
+template <typename V>
+__device__ __forceinline__ V vload(const void *p) { return *reinterpret_cast<const V *>(p); }
+
+// y_j = f(j) over the CTA's CPB n^3 values: 16-byte vectors when the element type allows it (T == R)
+// and every pointer of the call is 16-byte aligned, else one value per thread and step.
+template <typename T, int N, int NT, typename F>
+__device__ __forceinline__ void span_for(bool vec, F f) {
+  constexpr int W = Vec16<T>::w;
+  if (vec) {
+#pragma unroll 4
+    for (int v = threadIdx.x; v < N / W; v += NT) f(v * W, std::integral_constant<int, W>{});
+  } else {
+#pragma unroll 4
+    for (int t = threadIdx.x; t < N; t += NT) f(t, std::integral_constant<int, 1>{});
+  }
+}
+
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // T: storage type of p and y; R: compute type (T itself, or df64 for FP64-accurate arithmetic on the
-// FP32 units with double vectors; that variant supports the plain epilogue only).
-template <typename T, typename R, int K>
-__global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_kernel(MeshView<T> m, const T *__restrict__ p,
-                                                                                T *__restrict__ y, int cpb,
-                                                                                LapEpi<T> epi) {
-  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+// FP32 units with double vectors; that variant supports the plain epilogue only). CPB cells per CTA.
+template <typename T, typename R, int K, int CPB>
+__global__ void __launch_bounds__(BoxShape<K, CPB>::threads, (BoxOcc<R, BoxShape<K, CPB>::threads>::min_blocks))
+    laplace_box_kernel(MeshView<T> m, const T *__restrict__ p, T *__restrict__ y, LapEpi<T> epi) {
+  using S = BoxShape<K, CPB>;
+  constexpr int n = S::n, n2 = S::n2, n3 = S::n3, NT = S::threads, NV = CPB * n3;
+  constexpr int CS = S::S, TS = S::TS, YS = S::YS;
+  constexpr bool SAME = std::is_same<T, R>::value;
+  constexpr bool VECOK = SAME && (NV * sizeof(T)) % 16 == 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *Rs = reinterpret_cast<R *>(smem_raw);     // kRowScal
-  R *U = Rs + kRowScal;                         // cpb n3 (input, then output)
-  R *A = U + cpb * n3;                          // cpb n3 (T1 -> W)
-  R *B = A + cpb * n3;                          // cpb n3 (T2 -> T3)
-  R *TR = B + cpb * n3;                         // cpb * 6 faces * 2 (val, der) * n2
-  R *TY = TR + cpb * 24 * n2;                   // cpb * 2 faces * 2 * n2 : y-face traces after M_x
-  R *TZ = TY + cpb * 8 * n2;                    // cpb * 2 * 2 * n2 : z-face traces after M_x
+  R *U = Rs + S::rs;                            // CPB cells of stride CS (input, then output)
+  R *A = U + CPB * CS;                          // (T1 -> W)
+  R *B = A + CPB * CS;                          // (T2 -> T3)
+  R *TR = B + CPB * CS;                         // CPB x [6 faces x 2 (val, der) x n2], stride TS
+  R *TY = TR + CPB * TS;                        // CPB x [2 faces x 2 x n2], stride YS: y-face traces after M_x
+  R *TZ = TY + CPB * YS;                        // the same for the z-faces
   const BoxConst<R> &C = box_const<R>(K);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int c0 = blockIdx.x * cpb;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * CPB;
   if (blockIdx.y > 0) {   // column blockIdx.y of a block of vectors (the diagonal dinv is shared)
     const size_t co = (size_t)blockIdx.y * m.np;
     p += co;
@@ -126,66 +220,80 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
     if (epi.d) epi.d += co;
     if (epi.xout) epi.xout += co;
   }
-  const int i0 = c0 % m.nx, j = (c0 / m.nx) % m.ny, kz = c0 / (m.nx * m.ny);
+  const int nx = m.nx, ny = m.ny, nz = m.nz;
+  const int rowid = c0 / nx, kz = rowid / ny;
+  const int i0 = c0 - rowid * nx, j = rowid - kz * ny;
   const T *Rg = m.rowops + (size_t)j * kRowScal;
-  for (int t = tid; t < kRowScal; t += nt) Rs[t] = r_load<R>(Rg[t]);
-  const T *pc = p + (size_t)c0 * n3;
-  for (int t = tid; t < cpb * n3; t += nt) U[t] = r_load<R>(pc[t]);
+  if (tid < kRowScal) Rs[tid] = r_load<R>(Rg[tid]);
+  const size_t o = (size_t)c0 * n3;
+  const T *pc = p + o;
+  // value t of the CTA's cells -> its padded slot
+  auto slot = [](int t) { const int c = t / n3; return c * CS + (t - c * n3); };
+  // one value per thread and step: consecutive lanes store consecutive slots (16-byte loads would
+  // store four slots 4 apart per lane, a 4-way bank conflict in the padded layout)
+#pragma unroll 4
+  for (int t = tid; t < NV; t += NT) U[slot(t)] = r_load<R>(pc[t]);
   // Every thread owns line l of cell cl in all three passes (x-, y- then z-lines; l indexes the
   // face nodes of the same two tangential axes), so the index arithmetic is done once here.
-  const bool line = tid < cpb * n2;
-  const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
+  const bool line = tid < S::lines;
+  const int cl = line ? tid % CPB : 0, l = line ? tid / CPB : 0;
   const int lq = l / n, lr = l - lq * n;   // l = lr + n * lq
-  int *nbr = reinterpret_cast<int *>(TZ + cpb * 8 * n2);   // [cpb][6] neighbour cells (-1: wall)
-  if (tid < cpb * 6) {
-    const int c = tid / 6, f = tid - c * 6, d = f >> 1, sg = (f & 1) ? 1 : -1;
-    int ii = i0 + c, jj = j, kk = kz;
-    if (d == 0) ii = (ii + sg + m.nx) % m.nx;
-    else if (d == 2) kk = (kk + sg + m.nz) % m.nz;
-    else jj += sg;
-    nbr[tid] = (jj < 0 || jj >= m.ny) ? -1 : ii + m.nx * (jj + m.ny * kk);
-  }
   __syncthreads();
-  // neighbour traces at face node l of the six faces: value and reference normal derivative
+  // neighbour traces at face node l of the six faces: value and reference normal derivative. This
+  // phase maps threads to lines cell by cell (tc = tid / n^2), so a warp's neighbour loads fall on
+  // one or two neighbour cells and the in-segment test for the x-faces is uniform in most warps.
   if (line) {
+    const int cl = tid / n2, l = tid - cl * n2, lq = l / n, lr = l - lq * n;
+    const int ci = i0 + cl;
+    R *tr = TR + cl * TS + l;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-      const int d = f >> 1, side = f & 1, nb = nbr[cl * 6 + f];
-      R val = r_zero<R>(), der = r_zero<R>();
-      if (nb >= 0) {
-        // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
-        const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
-        const int base = d == 0 ? n * l : (d == 1 ? lr + n2 * lq : l);
-        R v[n];
-        // x-neighbours inside this CTA's row segment are already in shared memory
-        if (nb >= c0 && nb < c0 + cpb) {
-          const R *pn = U + (nb - c0) * n3;
+      const int d = f >> 1, side = f & 1;
+      const int sg = side ? 1 : -1;
+      // neighbour endpoint on the shared face: side 0 -> its xi_d = 1, side 1 -> its xi_d = 0
+      const int stride = d == 0 ? 1 : (d == 1 ? n : n2);
+      const int base = d == 0 ? n * l : (d == 1 ? lr + n2 * lq : l);
+      R v[n];
+      bool has = true;
+      if (d == 0 && cl + sg >= 0 && cl + sg < CPB) {   // x-neighbour inside the row segment
+        const R *pn = U + (cl + sg) * CS + base;
 #pragma unroll
-          for (int b = 0; b < n; ++b) v[b] = pn[base + b * stride];
+        for (int b = 0; b < n; ++b) v[b] = pn[b * stride];
+      } else {
+        int ii = ci, jj = j, kk = kz;   // periodic in x and z
+        if (d == 0) {
+          ii = ci + sg;
+          ii += ii < 0 ? nx : 0;
+          ii -= ii >= nx ? nx : 0;
+        } else if (d == 1) {
+          jj = j + sg;
         } else {
-          const T *pn = p + (size_t)nb * n3;
-#pragma unroll
-          for (int b = 0; b < n; ++b) v[b] = r_load<R>(pn[base + b * stride]);
+          kk = kz + sg;
+          kk += kk < 0 ? nz : 0;
+          kk -= kk >= nz ? nz : 0;
         }
-        val = side ? v[0] : v[n - 1];
+        has = jj >= 0 && jj < ny;
+        const T *pn = p + (size_t)(ii + nx * (jj + ny * kk)) * n3 + base;
 #pragma unroll
-        for (int b = 0; b < n; ++b) der = r_fma(side ? C.D[0][b] : C.D[1][b], v[b], der);
+        for (int b = 0; b < n; ++b) v[b] = has ? r_load<R>(pn[b * stride]) : r_zero<R>();
       }
-      TR[((cl * 6 + f) * 2 + 0) * n2 + l] = val;
-      TR[((cl * 6 + f) * 2 + 1) * n2 + l] = der;
+      R der = r_zero<R>();
+#pragma unroll
+      for (int b = 0; b < n; ++b) der = r_fma(side ? C.D[0][b] : C.D[1][b], v[b], der);
+      tr[(f * 2 + 0) * n2] = has ? (side ? v[0] : v[n - 1]) : r_zero<R>();
+      tr[(f * 2 + 1) * n2] = der;
     }
   }
   __syncthreads();
   // ---- phase A: x-lines (T1 = Lx u + nbr_x, T2 = M_x u); y- and z-traces <- M_x (items
   // it = l, l + n^2, ... < 4n: face (it / n) >> 1, array (it / n) & 1, t2 = it % n)
   if (line) {
-    const int base = cl * n3 + n * l;
+    const int base = cl * CS + n * l;
+    const R *tr = TR + cl * TS + l;
     R u[n], o1[n], o2[n];
 #pragma unroll
     for (int b = 0; b < n; ++b) u[b] = U[base + b];
-    const R v0 = TR[((cl * 6 + 0) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 0) * 2 + 1) * n2 + l];
-    const R v1 = TR[((cl * 6 + 1) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 1) * 2 + 1) * n2 + l];
-    line_op<R, K>(u, Rs, v0, d0, v1, d1, o1);
+    line_op<R, K>(u, Rs, tr[0], tr[n2], tr[2 * n2], tr[3 * n2], o1);
     mass_line<R, K>(u, o2);
 #pragma unroll
     for (int a = 0; a < n; ++a) { A[base + a] = o1[a]; B[base + a] = o2[a]; }
@@ -194,14 +302,14 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
       const int fl = iq >> 1, arr = iq & 1;
 #pragma unroll
       for (int isz = 0; isz < 2; ++isz) {
-        const R *src = TR + ((cl * 6 + (isz ? 4 : 2) + fl) * 2 + arr) * n2 + n * ir;
-        R *dst = (isz ? TZ : TY) + ((cl * 2 + fl) * 2 + arr) * n2 + n * ir;
-        R v[n], o[n];
+        const R *src = TR + cl * TS + (((isz ? 4 : 2) + fl) * 2 + arr) * n2 + n * ir;
+        R *dst = (isz ? TZ : TY) + cl * YS + (fl * 2 + arr) * n2 + n * ir;
+        R v[n], ov[n];
 #pragma unroll
         for (int b = 0; b < n; ++b) v[b] = src[b];
-        mass_line<R, K>(v, o);
+        mass_line<R, K>(v, ov);
 #pragma unroll
-        for (int a = 0; a < n; ++a) dst[a] = o[a];
+        for (int a = 0; a < n; ++a) dst[a] = ov[a];
       }
     }
   }
@@ -209,13 +317,12 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
   // ---- phase B: y-lines at (x, z) = (lr, lq): W = M_y T1 + Ly T2 + nbr_y', T3 = M_y T2; z-face
   // traces (indexed x + n*y) <- M_y (items it as in phase A, x = it % n)
   if (line) {
-    const int base = cl * n3 + lr + n2 * lq;
+    const int base = cl * CS + lr + n2 * lq;
+    const R *ty = TY + cl * YS + l;
     R a1[n], a2[n], w[n], t3[n], ly[n];
 #pragma unroll
     for (int c = 0; c < n; ++c) { a1[c] = A[base + n * c]; a2[c] = B[base + n * c]; }
-    const R v0 = TY[((cl * 2 + 0) * 2 + 0) * n2 + l], d0 = TY[((cl * 2 + 0) * 2 + 1) * n2 + l];
-    const R v1 = TY[((cl * 2 + 1) * 2 + 0) * n2 + l], d1 = TY[((cl * 2 + 1) * 2 + 1) * n2 + l];
-    line_op<R, K>(a2, Rs + 8, v0, d0, v1, d1, ly);
+    line_op<R, K>(a2, Rs + 8, ty[0], ty[n2], ty[2 * n2], ty[3 * n2], ly);
     mass_line<R, K>(a1, w);
     mass_line<R, K>(a2, t3);
 #pragma unroll
@@ -223,53 +330,98 @@ __global__ void __launch_bounds__(256, (BoxOcc<R, K>::min_blocks)) laplace_box_k
     for (int it = l; it < 4 * n; it += n2) {
       const int iq = it / n, ir = it - iq * n;
       const int fl = iq >> 1, arr = iq & 1;
-      const R *src = TZ + ((cl * 2 + fl) * 2 + arr) * n2 + ir;
-      R *dst = TR + ((cl * 6 + 4 + fl) * 2 + arr) * n2 + ir;
-      R v[n], o[n];
+      const R *src = TZ + cl * YS + (fl * 2 + arr) * n2 + ir;
+      R *dst = TR + cl * TS + ((4 + fl) * 2 + arr) * n2 + ir;
+      R v[n], ov[n];
 #pragma unroll
       for (int b = 0; b < n; ++b) v[b] = src[n * b];
-      mass_line<R, K>(v, o);
+      mass_line<R, K>(v, ov);
 #pragma unroll
-      for (int a = 0; a < n; ++a) dst[n * a] = o[a];
+      for (int a = 0; a < n; ++a) dst[n * a] = ov[a];
     }
   }
   __syncthreads();
   // ---- phase C: z-lines at l = x + n*y (y = M_z W + Lz T3 + nbr_z'')
   if (line) {
-    const int base = cl * n3 + l;
+    const int base = cl * CS + l;
+    const R *tz = TR + cl * TS + 8 * n2 + l;
     R a1[n], a2[n], w[n], lz[n];
 #pragma unroll
     for (int e = 0; e < n; ++e) { a1[e] = A[base + n2 * e]; a2[e] = B[base + n2 * e]; }
-    const R v0 = TR[((cl * 6 + 4) * 2 + 0) * n2 + l], d0 = TR[((cl * 6 + 4) * 2 + 1) * n2 + l];
-    const R v1 = TR[((cl * 6 + 5) * 2 + 0) * n2 + l], d1 = TR[((cl * 6 + 5) * 2 + 1) * n2 + l];
-    line_op<R, K>(a2, Rs + 16, v0, d0, v1, d1, lz);
+    line_op<R, K>(a2, Rs + 16, tz[0], tz[n2], tz[2 * n2], tz[3 * n2], lz);
     mass_line<R, K>(a1, w);
 #pragma unroll
     for (int c = 0; c < n; ++c) U[base + n2 * c] = w[c] + lz[c];
   }
   __syncthreads();
-  const size_t o = (size_t)c0 * n3;
   if (epi.mode == LAP_PLAIN) {
-    for (int t = tid; t < cpb * n3; t += nt) y[o + t] = r_store<T>(U[t]);
-  } else if constexpr (std::is_same<T, R>::value) {
-    if (epi.mode == LAP_RESIDUAL) {
-      for (int t = tid; t < cpb * n3; t += nt) y[o + t] = epi.b[o + t] - U[t];
+    T *yo = y + o;
+    if constexpr (VECOK) {
+      using V = typename Vec16<T>::type;
+      span_for<T, NV, NT>(aligned16(yo), [&](int t, auto w) {
+        if constexpr (decltype(w)::value > 1) {
+          T v[Vec16<T>::w];
+#pragma unroll
+          for (int q = 0; q < Vec16<T>::w; ++q) v[q] = U[slot(t + q)];
+          *reinterpret_cast<V *>(yo + t) = *reinterpret_cast<const V *>(v);
+        } else {
+          yo[t] = U[slot(t)];
+        }
+      });
     } else {
-      for (int t = tid; t < cpb * n3; t += nt) {
-        const size_t i = o + t;
-        const T dn = (epi.first ? T(0) : epi.c1 * epi.d[i]) + epi.c2 * epi.dinv[i] * (epi.b[i] - U[t]);
-        epi.d[i] = dn;
-        epi.xout[i] = p[i] + dn;
-      }
+      for (int t = tid; t < NV; t += NT) yo[t] = r_store<T>(U[slot(t)]);
+    }
+  } else if constexpr (SAME) {
+    constexpr int W = Vec16<T>::w;
+    if (epi.mode == LAP_RESIDUAL) {
+      T *yo = y + o;
+      const T *bo = epi.b + o;
+      span_for<T, NV, NT>(VECOK && aligned16(yo) && aligned16(bo), [&](int t, auto w) {
+        if constexpr (decltype(w)::value > 1) {
+          using V = typename Vec16<T>::type;
+          T bv[W], r[W];
+          *reinterpret_cast<V *>(bv) = vload<V>(bo + t);
+#pragma unroll
+          for (int q = 0; q < W; ++q) r[q] = bv[q] - U[slot(t + q)];
+          *reinterpret_cast<V *>(yo + t) = *reinterpret_cast<const V *>(r);
+        } else {
+          yo[t] = bo[t] - U[slot(t)];
+        }
+      });
+    } else {
+      const T *bo = epi.b + o, *dio = epi.dinv + o, *po = p + o;
+      T *dd = epi.d + o, *xo = epi.xout + o;
+      const T c1 = epi.first ? T(0) : epi.c1, c2 = epi.c2;
+      const bool first = epi.first != 0;
+      const bool vec = VECOK && aligned16(bo) && aligned16(dio) && aligned16(po) && aligned16(dd) && aligned16(xo);
+      span_for<T, NV, NT>(vec, [&](int t, auto w) {
+        if constexpr (decltype(w)::value > 1) {
+          using V = typename Vec16<T>::type;
+          T bv[W], di[W], pv[W], dv[W], dn[W], xv[W];
+          *reinterpret_cast<V *>(bv) = vload<V>(bo + t);
+          *reinterpret_cast<V *>(di) = vload<V>(dio + t);
+          *reinterpret_cast<V *>(pv) = vload<V>(po + t);
+          if (!first) *reinterpret_cast<V *>(dv) = vload<V>(dd + t);
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            dn[q] = (first ? T(0) : c1 * dv[q]) + c2 * di[q] * (bv[q] - U[slot(t + q)]);
+            xv[q] = pv[q] + dn[q];
+          }
+          *reinterpret_cast<V *>(dd + t) = *reinterpret_cast<const V *>(dn);
+          *reinterpret_cast<V *>(xo + t) = *reinterpret_cast<const V *>(xv);
+        } else {
+          const T dn = (first ? T(0) : c1 * dd[t]) + c2 * dio[t] * (bo[t] - U[slot(t)]);
+          dd[t] = dn;
+          xo[t] = po[t] + dn;
+        }
+      });
     }
   }
 }
 
-template <typename T>
-static size_t box_smem(int n, int cpb) {
-  const int n2 = n * n, n3 = n2 * n;
-  return sizeof(T) * ((size_t)kRowScal + 3 * (size_t)cpb * n3 + (size_t)cpb * (24 + 8 + 8) * n2) +
-         sizeof(int) * (size_t)cpb * 6;
+template <typename T, int K, int CPB>
+static size_t box_smem() {
+  return sizeof(T) * (size_t)BoxShape<K, CPB>::words;
 }
 
 // cells per CTA: the largest power of two dividing nx with cpb*(k+1)^2 <= 256 and cpb <= 8
@@ -336,25 +488,39 @@ cudaError_t box_constants_init() {
   return e;
 }
 
-template <typename T, typename R, int K>
-static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
-  constexpr int n = K + 1;
-  const int cpb = box_cpb(m.nx, n);
-  const size_t sm = box_smem<R>(n, cpb);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(laplace_box_kernel<T, R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    if (e == cudaSuccess)   // the whole unified L1/shared array as shared memory: more CTAs per SM
-      e = cudaFuncSetAttribute(laplace_box_kernel<T, R, K>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int threads = ((cpb * n * n + 31) / 32) * 32;
+template <typename T, typename R, int K, int CPB>
+static cudaError_t launch_box_kc(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
+  using S = BoxShape<K, CPB>;
+  const size_t sm = box_smem<R, K, CPB>();
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    // the whole unified L1/shared array as shared memory: more CTAs per SM
+    attr_err = cudaFuncSetAttribute(laplace_box_kernel<T, R, K, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    160 * 1024);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(laplace_box_kernel<T, R, K, CPB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   const int ncols = epi.ncols > 1 ? epi.ncols : 1;
   note_launch();
   note_dofs(m.np * ncols);
-  laplace_box_kernel<T, R, K><<<dim3(m.nc / cpb, ncols), threads, sm, s>>>(m, p, y, cpb, epi);
+  laplace_box_kernel<T, R, K, CPB><<<dim3(m.nc / CPB, ncols), S::threads, sm, s>>>(m, p, y, epi);
   return cudaGetLastError();
+}
+
+template <typename T, typename R, int K>
+static cudaError_t launch_box_k(const MeshView<T> &m, const T *p, T *y, const LapEpi<T> &epi, cudaStream_t s) {
+  constexpr int n = K + 1;
+  switch (box_cpb(m.nx, n)) {
+    case 8:
+      if constexpr (8 * n * n <= 256) return launch_box_kc<T, R, K, 8>(m, p, y, epi, s);
+      break;
+    case 4: return launch_box_kc<T, R, K, 4>(m, p, y, epi, s);
+    case 2: return launch_box_kc<T, R, K, 2>(m, p, y, epi, s);
+    case 1: return launch_box_kc<T, R, K, 1>(m, p, y, epi, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
