@@ -785,7 +785,8 @@ def run_wall_update(args):
 def run_ns_step(args):
     """Dual-splitting time steps on the workload (convective step, pressure solve, projection, viscous
     step; with --wall-update-steps also tau_w and the L2 projection at the start of every step),
-    constant dt, body force u_tau^2 / delta along x; host wall time per step after --warmup steps."""
+    constant dt (with --adaptive-dt the CFL step with Cr = 0.14, dt as its upper bound), body force
+    u_tau^2 / delta along x; host wall time per step after --warmup steps."""
     import torch
     from paper_1705_08813_gb300 import dgw, inputs as I
     torch.cuda.set_device(0)
@@ -796,7 +797,7 @@ def run_ns_step(args):
     delta = 0.5 * w.ly
     ns = dgw.DualSplitting(m, u0, dt=args.dt, force=(w.tau_w / delta, 0.0, 0.0), rtol_pressure=1e-10,
                            rtol_projection=1e-10, rtol_viscous=1e-10, pressure_mode=args.solve_mode,
-                           update_wall_model=args.wall_update_steps)
+                           update_wall_model=args.wall_update_steps, adaptive_dt=args.adaptive_dt)
     infos = []
     for it in range(args.warmup + max(1, args.steps)):
         torch.cuda.synchronize()
@@ -810,6 +811,7 @@ def run_ns_step(args):
     print(json.dumps({"metric": "dual-splitting time step (ms per step)", "workload": w.name,
                       "enrich_l": args.enrich_l, "n_u": m.n_u, "n_p": m.n_p, "dt": args.dt,
                       "wall_model_update": bool(args.wall_update_steps), "pressure_mode": args.solve_mode,
+                      "adaptive_dt": bool(args.adaptive_dt), "dt_taken": [i["dt"] for i in infos],
                       "steps": len(infos), "ms_per_step": med("wall_ms"),
                       "pressure_iterations": med("pressure_iterations"),
                       "projection_iterations": med("projection_iterations"),
@@ -897,6 +899,7 @@ def main():
     ap.add_argument("--wall-update", action="store_true", help="time the tau_w update and the L2 projection")
     ap.add_argument("--ns-step", action="store_true", help="time dual-splitting time steps")
     ap.add_argument("--wall-update-steps", action="store_true", help="--ns-step: update the wall model every step")
+    ap.add_argument("--adaptive-dt", action="store_true", help="--ns-step: the CFL step (Cr = 0.14), --dt its upper bound")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["laplace64", "laplace32", "laplace_df64", "divergence_df64", "viscous_df64",
                              "convective_df64", "divergence", "convective", "convective32", "viscous",

@@ -302,6 +302,14 @@ typedef struct {
 dgw_status dgw_helmholtz_solve(dgw_mesh_t mesh, double gamma, const double *rhs, double *u,
                                const dgw_helmholtz_opts *opts, dgw_solve_info *info, void *stream);
 
+/* Rate of the adaptive time step (Sec. 4.1: the step follows a CFL condition with the Courant number
+ * Cr, whose exact form the paper takes from its reference; reading: rate = the largest Euclidean norm
+ * of J^-1 (ubar + u~), the velocity in reference-cell lengths per unit time, over the volume points of
+ * the linear point set of every cell (k+1 Gauss points per direction, q_wall wall-normal in enriched
+ * cells), and dt = Cr / (k^1.5 rate)). u: n_u doubles (device); *rate: host double. FP64, needs the
+ * mesh's FP64 tables. Synchronises `stream`. */
+dgw_status dgw_cfl_rate(dgw_mesh_t mesh, const double *u, double *rate, void *stream);
+
 /* ---- Dual-splitting time step ------------------------------------------------------------- */
 
 typedef struct dgw_ns *dgw_ns_t;
@@ -319,11 +327,16 @@ typedef struct {
                              L2-projected onto the new space, the convective history recomputed */
   int pressure_bc;        /* 0: homogeneous Neumann data for the pressure; 1: the high-order data of
                              eq. bc_d_pres from u^{n-i} and their vorticities */
+  int adaptive_dt;        /* 0: constant step dt; 1: dt_n = min(dt, Cr / (k^1.5 dgw_cfl_rate(u^n)))
+                             (Sec. 4.1, Cr = cr) with the BDF2 and extrapolation constants of the
+                             step ratio w = dt_n / dt_{n-1}: gamma_0 = (1 + 2w) / (1 + w),
+                             alpha_0 = 1 + w, alpha_1 = -w^2 / (1 + w), beta_0 = 1 + w, beta_1 = -w */
 } dgw_ns_params;
 
 typedef struct {
   int pressure_iterations, projection_iterations, viscous_iterations;
   double ms;              /* host wall time of the step */
+  double dt;              /* the step size taken */
 } dgw_ns_step_info;
 
 /* A time integrator of the dual-splitting scheme (Sec. 4.1, Galerkin forms of Sec. 4.2) on `mesh`,
@@ -332,7 +345,8 @@ typedef struct {
 dgw_status dgw_ns_create(dgw_mesh_t mesh, const dgw_ns_params *params, const double *u0, void *stream, dgw_ns_t *out);
 /* Free the integrator's vectors (not the mesh); NULL is accepted. */
 dgw_status dgw_ns_destroy(dgw_ns_t ns);
-/* One time step, BDF2 with second-order extrapolation (first order in the first step), constant dt:
+/* One time step, BDF2 with second-order extrapolation (first order in the first step), constant dt
+ * or (adaptive_dt) the CFL step of dgw_cfl_rate with the variable-step constants:
  *   u^  = (sum alpha_i u^{n-i} + dt f - dt M^-1 sum beta_i F^c(u^{n-i})) / gamma_0 (eq. convstepspat)
  *   A p = (gamma_0 / dt)(-C u^) + (q, g)_walls (eq. poissonspat), g = 0 or the high-order data of
  *         eq. bc_d_pres (pressure_bc = 1) from u^n, u^{n-1} and their vorticities

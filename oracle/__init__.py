@@ -87,6 +87,8 @@ def _load():
         lib.dgo_pressure_neumann.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.dgo_divdiv.argtypes = [vp, dp, dp, dp]
         lib.dgo_tau_divdiv.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp]
+        lib.dgo_cfl_rate.argtypes = [vp, dp]
+        lib.dgo_cfl_rate.restype = ctypes.c_double
         lib.dgo_inverse_mass.argtypes = [vp, dp, dp]
         lib.dgo_inverse_mass.restype = ctypes.c_int
         lib.dgo_active.argtypes = [vp, ip]
@@ -305,6 +307,12 @@ class Mesh:
                                       float(b1 if u1 is not None else 0.0), _ptr(fv), _ptr(y))
         return y
 
+    def cfl_rate(self, u: np.ndarray) -> float:
+        """Largest |J^-1 (ubar + u~)|_2 over the linear volume point set of every cell: the speed in
+        reference-cell lengths per unit time that sets the adaptive time step Cr / (k^1.5 rate)."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        return float(self.lib.dgo_cfl_rate(self.h, _ptr(u)))
+
     def tau_divdiv(self, u: np.ndarray, dt: float, cr: float) -> np.ndarray:
         """Per-cell tau_D = |u|_K h dt / Cr (volume-averaged |u|, h = cube root of the cell volume)."""
         u = np.ascontiguousarray(u, dtype=np.float64); out = np.zeros(self.nc)
@@ -397,6 +405,16 @@ def _pcg(apply, b, x0, prec, rtol, maxit=5000):
     raise RuntimeError("projection CG did not converge")
 
 
+def bdf2_variable(omega):
+    """(gamma_0, alpha_0, alpha_1, beta_0, beta_1) of the second-order BDF and extrapolation for the
+    step ratio omega = dt_n / dt_{n-1} (Sec. 4.1: the constants follow the variable increments): the
+    derivative at t_{n+1} of the quadratic through u^{n+1}, u^n, u^{n-1} times dt_n is
+    gamma_0 u^{n+1} - alpha_0 u^n - alpha_1 u^{n-1}, and beta_0 u^n + beta_1 u^{n-1} is the linear
+    extrapolation to t_{n+1}."""
+    w = float(omega)
+    return (1.0 + 2.0 * w) / (1.0 + w), 1.0 + w, -w * w / (1.0 + w), 1.0 + w, -w
+
+
 class DualSplitting:
     """One constant-step BDF2/extrapolation step of the dual-splitting scheme after Sec. 4.1 with the
     Galerkin forms of Sec. 4.2, written with this module's operators (first order in the first step):
@@ -405,11 +423,15 @@ class DualSplitting:
     projection (M + D) u^^ = M u^ - (dt / gamma_0) P(p) by preconditioned CG, and the viscous
     Helmholtz step by GMRES, nu_t and tau_D from u^n. With update_wall_model the step starts with the
     wall shear stress of u^n, the L2 projection of u^n and u^{n-1} onto the new space and a new
-    F^c(u^{n-1})."""
+    F^c(u^{n-1}). With adaptive the step is dt_n = min(dt, Cr / (k^1.5 cfl_rate(u^n))) and the
+    constants those of bdf2_variable for dt_n / dt_{n-1}."""
 
     def __init__(self, mesh: "Mesh", u0, dt, cr=0.14, force=(0.0, 0.0, 0.0), rtol=1e-13,
-                 update_wall_model=False, tau_nodes=None, high_order_pressure_bc=False):
+                 update_wall_model=False, tau_nodes=None, high_order_pressure_bc=False, adaptive=False):
         self.m, self.dt, self.cr, self.rtol = mesh, float(dt), float(cr), float(rtol)
+        self.adaptive = bool(adaptive)
+        self.dt_prev = None
+        self.dts = []
         self.u = [np.array(u0, dtype=np.float64), None]
         self.fc_old = None
         self.p = np.zeros(mesh.n_p)
@@ -428,7 +450,16 @@ class DualSplitting:
     def step(self):
         m, dt = self.m, self.dt
         second = self.steps > 0
-        g0, a0, a1, b0, b1 = (1.5, 2.0, -0.5, 2.0, -1.0) if second else (1.0, 1.0, 0.0, 1.0, 0.0)
+        if self.adaptive:
+            rate = m.cfl_rate(self.u[0])
+            if rate > 0.0:
+                dt = min(dt, self.cr / (m.k ** 1.5 * rate))
+        if not second:
+            g0, a0, a1, b0, b1 = (1.0, 1.0, 0.0, 1.0, 0.0)
+        elif self.adaptive:
+            g0, a0, a1, b0, b1 = bdf2_variable(dt / self.dt_prev)
+        else:
+            g0, a0, a1, b0, b1 = (1.5, 2.0, -0.5, 2.0, -1.0)
         if self.update and m.n_e > 0:
             tn = m.wall_shear(self.u[0])
             old = self.tau
@@ -461,4 +492,6 @@ class DualSplitting:
         self.fc_old = fc
         self.p = p
         self.steps += 1
+        self.dt_prev = dt
+        self.dts.append(dt)
         return unew, p

@@ -1635,6 +1635,46 @@ int dgo_divdiv(void *h, const double *tau_d, const double *u, double *y) {
 
 /* tau_D per cell (eq. tauD): the volume average of |u| over the cell times h dt / Cr, with h the cube
  * root of the cell volume. */
+/* Rate of the adaptive time step (Sec. 4.1: the step is chosen from a CFL condition with the
+ * Courant number Cr; the condition itself is not restated there, reading in the design notes): the
+ * largest Euclidean norm of J^-1 (ubar + u~), the velocity in reference-cell lengths per unit time,
+ * over the volume points of the linear point set of every cell (k+1 Gauss points per direction, q_w
+ * wall-normal in enriched cells). The step is then Cr / (k^1.5 rate). */
+double dgo_cfl_rate(void *h, const double *u) {
+  omesh *M = (omesh *)h;
+  double best = 0.0;
+#pragma omp parallel
+  {
+    ptab t; ptab_alloc(&t, M);
+    double gx[MAXP], gw[MAXP], gy[MAXP], gwy[MAXP];
+    double mine = 0.0;
+#pragma omp for schedule(dynamic, 4)
+    for (int c = 0; c < M->nc; ++c) {
+      int nq[3];
+      cell_points(M, c, OP_LINEAR, nq);
+      dgo_gauss(nq[0], gx, gw); dgo_gauss(nq[1], gy, gwy);
+      for (int q2 = 0; q2 < nq[2]; ++q2)
+        for (int q1 = 0; q1 < nq[1]; ++q1)
+          for (int q0 = 0; q0 < nq[0]; ++q0) {
+            double xi[3] = {gx[q0], gy[q1], gx[q2]};
+            tabulate(M, c, xi, &t);
+            vstate sv; eval_vel(M, u, c, &t, &sv);
+            double uu[3] = {sv.ub[0] + sv.ut[0], sv.ub[1] + sv.ut[1], sv.ub[2] + sv.ut[2]};
+            double r2 = 0.0;
+            for (int r = 0; r < 3; ++r) {
+              double w = t.Ji[r][0] * uu[0] + t.Ji[r][1] * uu[1] + t.Ji[r][2] * uu[2];
+              r2 += w * w;
+            }
+            if (sqrt(r2) > mine) mine = sqrt(r2);
+          }
+    }
+#pragma omp critical
+    if (mine > best) best = mine;
+    ptab_free(&t);
+  }
+  return best;
+}
+
 int dgo_tau_divdiv(void *h, const double *u, double dt, double cr, double *tau_d) {
   omesh *M = (omesh *)h;
 #pragma omp parallel

@@ -457,6 +457,19 @@ dgw_status dgw_tau_divdiv(dgw_mesh_t M, const double *u, double dt, double cr, d
   return cuda_check(launch_ns_op(NS_TAU, M, u, dt / cr, tau_d, (cudaStream_t)stream), "dgw_tau_divdiv");
 }
 
+dgw_status dgw_cfl_rate(dgw_mesh_t M, const double *u, double *rate, void *stream) {
+  if (!M || !u || !rate) return set_error(DGW_EINVAL, "dgw_cfl_rate: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!M->rate_dev) M->rate_dev = dalloc<double>(M, 1, &e);
+  if (e != cudaSuccess) return cuda_check(e, "dgw_cfl_rate");
+  e = cudaMemsetAsync(M->rate_dev, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = launch_cfl_rate(M->v64, u, M->rate_dev, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rate, M->rate_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_check(e, "dgw_cfl_rate");
+}
+
 dgw_status dgw_apply_divdiv(dgw_mesh_t M, const double *tau_d, const double *u, double *y, void *stream) {
   if (!M || !tau_d || !u || !y) return set_error(DGW_EINVAL, "dgw_apply_divdiv: null argument");
   MeshView<double> v = M->v64;

@@ -142,6 +142,7 @@ struct dgw_mesh {
   struct dgw_solver *solver = nullptr;   // lazily built solver workspace and multigrid hierarchy
   struct dgw_helm *helm = nullptr;       // lazily built Helmholtz (GMRES) workspace
   dgw::Batch *batch = nullptr;           // lazily built block solver (batched mixed-precision solves)
+  double *rate_dev = nullptr;            // device scalar of dgw_cfl_rate (allocated on first use)
   int batch_cheb = 0;                    // its Chebyshev degree
 };
 
@@ -261,6 +262,9 @@ cudaError_t launch_pressure_neumann(dgw_mesh *M, const double *u0, const double 
 cudaError_t launch_eddy_viscosity(dgw_mesh *M, const double *u, cudaStream_t s);
 cudaError_t launch_to_float(const double *a, float *b, size_t n, cudaStream_t s);
 
-enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3, OP_MASS = 4, OP_DIVDIV = 5 };
+enum { OP_DIV = 0, OP_CONV = 1, OP_VISC = 2, OP_LAP = 3, OP_MASS = 4, OP_DIVDIV = 5, OP_CFL = 6 };
+// max over cells and the linear volume point set of |J^-1 (ubar + u~)|_2 into *rate (a device double,
+// zeroed by the caller; FP64 only): the speed that sets the adaptive time step
+cudaError_t launch_cfl_rate(const MeshView<double> &m, const double *u, double *rate, cudaStream_t s);
 
 }  // namespace dgw

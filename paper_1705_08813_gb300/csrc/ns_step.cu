@@ -11,7 +11,10 @@
 //      u^n, solved by CG preconditioned with the exact inverse mass
 //   4. viscous step (eq. helmholtzspat): (gamma_0 / dt) M u^{n+1} - F^nu(u^{n+1}) = (gamma_0 / dt) M u^^,
 //      nu_t frozen from u^n, restarted GMRES
-// Constant time step. Every operator is a library kernel; the host sequences them.
+// Constant time step, or (adaptive_dt) the CFL step dt_n = min(dt, Cr / (k^1.5 rate(u^n))) with the
+// BDF2 / extrapolation constants of the step ratio. Every operator is a library kernel; the host
+// sequences them.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -26,6 +29,7 @@ struct dgw_ns {
   dgw_ns_params P{};
   long nu = 0, np = 0;
   int steps = 0;
+  double dt_prev = 0.0;                 // the previous step size (variable-step constants)
   double *u[2] = {nullptr, nullptr};    // u^n, u^{n-1}
   double *fc[2] = {nullptr, nullptr};   // F^c(u^n), F^c(u^{n-1})
   double *om[2] = {nullptr, nullptr};   // vorticities of u^n, u^{n-1} (high-order pressure data)
@@ -34,7 +38,8 @@ struct dgw_ns {
   double *f = nullptr;                  // body force as a velocity field (standard coefficients)
   double *tau_d = nullptr, *tau_nodes = nullptr;
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr;
-  double *partial = nullptr, *host = nullptr;
+  double *partial = nullptr;
+  double *cg_sc = nullptr, *cg_host = nullptr;   // projection CG scalars on the device and their host copy
   std::vector<void *> allocs;
 };
 
@@ -69,7 +74,11 @@ __global__ void dot_partial_kernel(const double *__restrict__ x, const double *_
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-__global__ void dot_finish_kernel(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+// Projection CG with the scalars on the device: slots of cg_sc
+enum { CG_RR = 0, CG_PQ, CG_RZ, CG_RZNEW, CG_DONE, CG_ITER, CG_TARGET, CG_COUNT };
+
+// sc[slot] = sum of the partials; with flag: the convergence test sqrt(rr) <= target raises CG_DONE
+__global__ void cg_finish_kernel(const double *__restrict__ partial, int nb, double *__restrict__ sc, int slot, int flag) {
   __shared__ double red[512];
   red[threadIdx.x] = threadIdx.x < nb ? partial[threadIdx.x] : 0.0;
   __syncthreads();
@@ -77,7 +86,37 @@ __global__ void dot_finish_kernel(const double *__restrict__ partial, int nb, do
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = red[0];
+  if (threadIdx.x == 0) {
+    sc[slot] = red[0];
+    if (flag && sc[CG_DONE] == 0.0 && sqrt(red[0]) <= sc[CG_TARGET]) sc[CG_DONE] = 1.0;
+  }
+}
+
+// x += alpha p, r -= alpha q with alpha = rz / pq (nothing once the iteration has converged)
+__global__ void cg_update_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                 const double *__restrict__ q, long n, double *__restrict__ sc) {
+  if (sc[CG_DONE] != 0.0) return;
+  const double alpha = sc[CG_RZ] / sc[CG_PQ];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// p = z + (rz_new / rz) p
+__global__ void cg_direction_kernel(double *__restrict__ p, const double *__restrict__ z, long n,
+                                    const double *__restrict__ sc) {
+  if (sc[CG_DONE] != 0.0) return;
+  const double beta = sc[CG_RZNEW] / sc[CG_RZ];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// rz <- rz_new and the iteration count, after every block of the direction update has read rz
+__global__ void cg_shift_kernel(double *sc) {
+  if (sc[CG_DONE] != 0.0) return;
+  sc[CG_RZ] = sc[CG_RZNEW];
+  sc[CG_ITER] += 1.0;
 }
 
 // force field: every standard coefficient of component a equals f[a]; enrichment zero
@@ -107,18 +146,6 @@ cudaError_t lincomb(double *out, double a, const double *x, double b, const doub
   return cudaGetLastError();
 }
 
-// host value of x . y (synchronises s)
-cudaError_t dot(dgw_ns *S, const double *x, const double *y, long n, cudaStream_t s, double *out) {
-  note_launches(2);
-  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(x, y, n, S->partial);
-  dot_finish_kernel<<<1, 512, 0, s>>>(S->partial, kDotBlocks, S->partial + kDotBlocks);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(S->host, S->partial + kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  *out = *S->host;
-  return e;
-}
-
 // y = (M + D) x
 dgw_status apply_md(dgw_ns *S, const double *x, double *y, cudaStream_t s) {
   dgw_status st = dgw_apply_mass(S->M, DGW_FP64, x, y, s);
@@ -127,52 +154,85 @@ dgw_status apply_md(dgw_ns *S, const double *x, double *y, cudaStream_t s) {
   return st;
 }
 
-// (M + D) x = rhs by CG preconditioned with M^-1; x holds the initial guess
+// sc[slot] = x . y on the device (with flag: the convergence test of sc[CG_RR])
+cudaError_t dot_dev(dgw_ns *S, const double *x, const double *y, long n, int slot, int flag, cudaStream_t s) {
+  note_launches(2);
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(x, y, n, S->partial);
+  cg_finish_kernel<<<1, 512, 0, s>>>(S->partial, kDotBlocks, S->cg_sc, slot, flag);
+  return cudaGetLastError();
+}
+
+// (M + D) x = rhs by CG preconditioned with M^-1; x holds the initial guess. The scalars stay on the
+// device: each iteration is launches only, a converged iteration leaves x, r and p unchanged, and the
+// host reads the convergence flag and the iteration count every kCgCheck iterations (at most
+// kCgCheck - 1 operator applies after convergence; the result and the count are those of a test in
+// every iteration).
+constexpr int kCgCheck = 4;
 dgw_status projection_cg(dgw_ns *S, const double *rhs, double *x, cudaStream_t s, int *iters) {
   const long n = S->nu;
-  double bb = 0.0, rz = 0.0;
+  const int G = grid_of(n);
   dgw_status st = apply_md(S, x, S->cg_q, s);
   cudaError_t e = cudaSuccess;
   if (st == DGW_OK) e = lincomb(S->cg_r, 1.0, rhs, -1.0, S->cg_q, 0.0, nullptr, n, s);
-  if (st == DGW_OK && e == cudaSuccess) e = dot(S, rhs, rhs, n, s, &bb);
+  if (st == DGW_OK && e == cudaSuccess) e = dot_dev(S, rhs, rhs, n, CG_RR, 0, s);
   if (st == DGW_OK && e == cudaSuccess) st = dgw_apply_inverse_mass(S->M, S->cg_r, S->cg_z, s);
   if (st == DGW_OK && e == cudaSuccess) e = cudaMemcpyAsync(S->cg_p, S->cg_z, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  if (st == DGW_OK && e == cudaSuccess) e = dot(S, S->cg_r, S->cg_z, n, s, &rz);
+  if (st == DGW_OK && e == cudaSuccess) e = dot_dev(S, S->cg_r, S->cg_z, n, CG_RZ, 0, s);
+  if (st == DGW_OK && e == cudaSuccess) e = cudaMemcpyAsync(S->cg_host, S->cg_sc, CG_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (st == DGW_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (st != DGW_OK) return st;
   if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
-  const double target = S->P.rtol_projection * std::sqrt(bb);
-  int it = 0;
-  for (; it < S->P.max_iter; ++it) {
-    double rr = 0.0;
-    e = dot(S, S->cg_r, S->cg_r, n, s, &rr);
-    if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
-    if (std::sqrt(rr) <= target || bb == 0.0) break;
-    st = apply_md(S, S->cg_p, S->cg_q, s);
-    if (st != DGW_OK) return st;
-    double pq = 0.0;
-    e = dot(S, S->cg_p, S->cg_q, n, s, &pq);
-    if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
-    const double alpha = rz / pq;
-    e = lincomb(x, 1.0, x, alpha, S->cg_p, 0.0, nullptr, n, s);
-    if (e == cudaSuccess) e = lincomb(S->cg_r, 1.0, S->cg_r, -alpha, S->cg_q, 0.0, nullptr, n, s);
-    if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
-    st = dgw_apply_inverse_mass(S->M, S->cg_r, S->cg_z, s);
-    if (st != DGW_OK) return st;
-    double rz2 = 0.0;
-    e = dot(S, S->cg_r, S->cg_z, n, s, &rz2);
-    if (e == cudaSuccess) e = lincomb(S->cg_p, 1.0, S->cg_z, rz2 / rz, S->cg_p, 0.0, nullptr, n, s);
-    if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
-    rz = rz2;
+  const double bb = S->cg_host[CG_RR];
+  if (bb == 0.0) {   // x already solves the system exactly
+    *iters = 0;
+    return DGW_OK;
   }
+  S->cg_host[CG_TARGET] = S->P.rtol_projection * std::sqrt(bb);
+  S->cg_host[CG_DONE] = 0.0;
+  S->cg_host[CG_ITER] = 0.0;
+  e = cudaMemcpyAsync(S->cg_sc, S->cg_host, CG_COUNT * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
+  int launched = 0;
+  for (;;) {
+    for (int k = 0; k < kCgCheck && launched < S->P.max_iter + 1; ++k, ++launched) {
+      e = dot_dev(S, S->cg_r, S->cg_r, n, CG_RR, 1, s);
+      if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
+      st = apply_md(S, S->cg_p, S->cg_q, s);
+      if (st != DGW_OK) return st;
+      e = dot_dev(S, S->cg_p, S->cg_q, n, CG_PQ, 0, s);
+      if (e == cudaSuccess) {
+        note_launch();
+        cg_update_kernel<<<G, 256, 0, s>>>(x, S->cg_r, S->cg_p, S->cg_q, n, S->cg_sc);
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
+      st = dgw_apply_inverse_mass(S->M, S->cg_r, S->cg_z, s);
+      if (st != DGW_OK) return st;
+      e = dot_dev(S, S->cg_r, S->cg_z, n, CG_RZNEW, 0, s);
+      if (e == cudaSuccess) {
+        note_launches(2);
+        cg_direction_kernel<<<G, 256, 0, s>>>(S->cg_p, S->cg_z, n, S->cg_sc);
+        cg_shift_kernel<<<1, 1, 0, s>>>(S->cg_sc);
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
+    }
+    e = cudaMemcpyAsync(S->cg_host, S->cg_sc, CG_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ns_fail(e, "dgw_ns_step");
+    if (S->cg_host[CG_DONE] != 0.0) break;
+    if (launched > S->P.max_iter) break;
+  }
+  const int it = (int)S->cg_host[CG_ITER];
   *iters = it;
-  if (it >= S->P.max_iter) return set_error(DGW_ENOTCONV, "dgw_ns_step: projection CG reached max_iter");
+  if (S->cg_host[CG_DONE] == 0.0) return set_error(DGW_ENOTCONV, "dgw_ns_step: projection CG reached max_iter");
   return DGW_OK;
 }
 
 void ns_free(dgw_ns *S) {
   if (!S) return;
   for (void *p : S->allocs) cudaFree(p);
-  if (S->host) cudaFreeHost(S->host);
+  if (S->cg_host) cudaFreeHost(S->cg_host);
   delete S;
 }
 
@@ -209,7 +269,8 @@ dgw_status dgw_ns_create(dgw_mesh_t M, const dgw_ns_params *params, const double
   alloc(&S->tau_d, M->nc);
   alloc(&S->tau_nodes, (size_t)2 * M->P.nx * M->P.nz);
   alloc(&S->partial, kDotBlocks + 1);
-  if (e == cudaSuccess) e = cudaMallocHost(&S->host, sizeof(double));
+  alloc(&S->cg_sc, CG_COUNT);
+  if (e == cudaSuccess) e = cudaMallocHost(&S->cg_host, CG_COUNT * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpyAsync(S->u[0], u0, S->nu * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) {
     note_launch();
@@ -255,12 +316,31 @@ dgw_status dgw_ns_step(dgw_ns_t S, dgw_ns_step_info *info, void *stream) {
   const auto t0 = std::chrono::steady_clock::now();
   const long nu = S->nu;
   const bool second = S->steps > 0;
-  // BDF2 / extrapolation of order 2 with a constant step (order 1 in the first step)
-  const double g0 = second ? 1.5 : 1.0, a0 = second ? 2.0 : 1.0, a1 = second ? -0.5 : 0.0;
-  const double b0 = second ? 2.0 : 1.0, b1 = second ? -1.0 : 0.0, dt = S->P.dt;
   dgw_ns_step_info inf{};
   dgw_status st = DGW_OK;
   cudaError_t e = cudaSuccess;
+  // step size: constant, or the CFL step of u^n (Sec. 4.1, Cr = cr)
+  double dt = S->P.dt;
+  if (S->P.adaptive_dt) {
+    double rate = 0.0;
+    st = dgw_cfl_rate(M, S->u[0], &rate, s);
+    if (st != DGW_OK) return st;
+    if (rate > 0.0) dt = std::min(dt, S->P.cr / (std::pow((double)M->P.degree, 1.5) * rate));
+  }
+  // BDF2 / extrapolation of order 2 (order 1 in the first step); step ratio w = dt_n / dt_{n-1}
+  double g0 = 1.0, a0 = 1.0, a1 = 0.0, b0 = 1.0, b1 = 0.0;
+  if (second) {
+    const double w = S->P.adaptive_dt ? dt / S->dt_prev : 1.0;
+    if (w == 1.0) {
+      g0 = 1.5; a0 = 2.0; a1 = -0.5; b0 = 2.0; b1 = -1.0;
+    } else {
+      g0 = (1.0 + 2.0 * w) / (1.0 + w);
+      a0 = 1.0 + w;
+      a1 = -w * w / (1.0 + w);
+      b0 = 1.0 + w;
+      b1 = -w;
+    }
+  }
   // 0. wall model: new tau_w and the history moved into the new space
   if (S->P.update_wall_model && M->ne > 0) {
     st = dgw_wall_shear_stress(M, S->u[0], S->tau_nodes, s);
@@ -350,6 +430,8 @@ dgw_status dgw_ns_step(dgw_ns_t S, dgw_ns_step_info *info, void *stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_check(e, "dgw_ns_step");
   S->steps++;
+  S->dt_prev = dt;
+  inf.dt = dt;
   inf.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
   return DGW_OK;

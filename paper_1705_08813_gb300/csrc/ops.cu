@@ -257,7 +257,7 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   int v = o;
   // the point values V (written by the last forward pass, read until the enriched reduction) share
   // room with A, which is dead between the second forward pass and the second integration pass
-  const bool has_v = op == OP_DIV || op == OP_CONV || op == OP_MASS;
+  const bool has_v = op == OP_DIV || op == OP_CONV || op == OP_MASS || op == OP_CFL;
   p.vA = v; v += (has_v && 3 * p.P > ka * SX) ? 3 * p.P : ka * SX;
   p.vV = p.vA;
   p.vB = v; v += kb * SZ;
@@ -286,7 +286,7 @@ __host__ __device__ inline VecPlan vec_plan(int op, bool curved, int n, int qin,
   p.fF2 = g; g += 2 * nout * nn;
   p.fG2 = g; g += 2 * nout * nn;
   if (g > p.face_end) p.face_end = g;
-  if (op == OP_MASS || op == OP_DIVDIV) p.face_end = p.work;   // no face terms
+  if (op == OP_MASS || op == OP_DIVDIV || op == OP_CFL) p.face_end = p.work;   // no face terms
   p.total = p.vol_end > p.face_end ? p.vol_end : p.face_end;
   return p;
 }
@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       // k = 0: d/dz from Y00; 1: d/dy from Y01; 2: d/dx from Y10
       return {Bv + b * SZ, k == 0 ? D_[2] : S_[2], nullptr, nullptr, G + (a * 3 + 2 - k) * P};
     }, (GRAD ? 3 : 1) * NIN, q0, q1, n, 2, n, q2, false, false);
+    T cfl_max = T(0);   // OP_CFL: this thread's largest rate
     // P4: pointwise test-function coefficients (H_{a,d} multiplies d phi / d xi_d)
     const T *nutv = (OP == OP_VISC && enr_c) ? m.nut_vol + (size_t)ec * m.nvol[0] : nullptr;
     for (int t = threadIdx.x; t < P; t += blockDim.x) {
@@ -405,13 +406,20 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         for (int a = 0; a < 3; ++a) enr_trial<T, GRAD>(f, eo + a * 8, l0, sN[a], sD[a]);
         w = wtv + t * WT;
       }
-      if (OP == OP_DIV || OP == OP_CONV || OP == OP_MASS) {
+      if (OP == OP_DIV || OP == OP_CONV || OP == OP_MASS || OP == OP_CFL) {
         T uu[3] = {V[t], V[P + t], V[2 * P + t]};
         if (enr_c)
           for (int a = 0; a < 3; ++a) {
             uu[a] += w[0] * sN[a];
             V[a * P + t] = uu[a];
           }
+        if (OP == OP_CFL) {   // |J^-1 u|_2: the velocity in reference-cell lengths per unit time
+          T cf[3];
+          if (CURVED) phys_to_ref(Ji, uu, cf);
+          else for (int d = 0; d < 3; ++d) cf[d] = uu[d] * hinv[d];
+          cfl_max = max(cfl_max, sqrt(cf[0] * cf[0] + cf[1] * cf[1] + cf[2] * cf[2]));
+          continue;
+        }
         if (OP == OP_MASS) {   // value coefficients of the test functions
           for (int a = 0; a < 3; ++a) G[a * P + t] = dV * uu[a];
         } else if (CURVED) {
@@ -489,6 +497,20 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       }
     }
     __syncthreads();
+    if constexpr (OP == OP_CFL) {
+      // the block's largest rate, then one atomic maximum on the bit pattern (non-negative doubles
+      // order like their bits)
+      __shared__ T wmax[4];
+      for (int off = 16; off > 0; off >>= 1) cfl_max = max(cfl_max, __shfl_xor_sync(0xffffffffu, cfl_max, off));
+      if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = cfl_max;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        T b = wmax[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = max(b, wmax[w]);
+        atomicMax(reinterpret_cast<unsigned long long *>(y), (unsigned long long)__double_as_longlong((double)b));
+      }
+      return;
+    }
     // enriched test functions: -(grad(psi N_v) e_a, u x u), (eps(psi N_v e_a), 2(nu+nu_t) eps(u~)) or
     // (div(psi N_v e_a), tau_D div u)
     if (enr_c && (OP == OP_CONV || OP == OP_VISC || OP == OP_DIVDIV)) {
@@ -590,7 +612,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }
   }
 
-  if constexpr (OP != OP_MASS && OP != OP_DIVDIV) {
+  if constexpr (OP != OP_MASS && OP != OP_DIVDIV && OP != OP_CFL) {
   // ================= faces, one direction (two faces) at a time =================
   // trace slots per direction: (face s, side, component); on boxes the divergence needs the normal
   // component only
@@ -1136,6 +1158,11 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
 
 template cudaError_t launch_vector_op<double>(int, const MeshView<double> &, const double *, double *, cudaStream_t,
                                               const LapEpi<double> *);
+
+cudaError_t launch_cfl_rate(const MeshView<double> &m, const double *u, double *rate, cudaStream_t s) {
+  if (m.geo == GEO_CURVED) return launch_vec<double, OP_CFL, GEO_CURVED>(m, u, rate, s, nullptr);
+  return launch_vec<double, OP_CFL, GEO_BOX>(m, u, rate, s, nullptr);
+}
 
 cudaError_t launch_vector_op_df(int op, const MeshView<double> &m, const double *u, double *y, cudaStream_t s) {
   if (m.geo != GEO_BOX || (op != OP_DIV && op != OP_VISC && op != OP_CONV)) return cudaErrorNotSupported;

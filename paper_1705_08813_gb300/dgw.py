@@ -25,7 +25,7 @@ EXPORTS = ["dgw_mesh_create", "dgw_mesh_destroy", "dgw_mesh_info", "dgw_mesh_nod
            "dgw_project_velocity", "dgw_set_enrichment_switch", "dgw_enrichment_active",
            "dgw_apply_gradient", "dgw_tau_divdiv", "dgw_apply_divdiv", "dgw_apply_inverse_mass",
            "dgw_ns_create", "dgw_ns_destroy", "dgw_ns_step", "dgw_ns_state", "dgw_ns_copy_state",
-           "dgw_apply_curl", "dgw_add_pressure_neumann"]
+           "dgw_apply_curl", "dgw_add_pressure_neumann", "dgw_cfl_rate"]
 
 JOB_SOLVE, JOB_LAPLACE, JOB_DIVERGENCE, JOB_CONVECTIVE, JOB_VISCOUS = 0, 1, 2, 3, 4
 
@@ -40,12 +40,12 @@ class NSParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("cr", ctypes.c_double), ("force", ctypes.c_double * 3),
                 ("rtol_pressure", ctypes.c_double), ("rtol_projection", ctypes.c_double),
                 ("rtol_viscous", ctypes.c_double), ("max_iter", ctypes.c_int), ("pressure_mode", ctypes.c_int),
-                ("update_wall_model", ctypes.c_int), ("pressure_bc", ctypes.c_int)]
+                ("update_wall_model", ctypes.c_int), ("pressure_bc", ctypes.c_int), ("adaptive_dt", ctypes.c_int)]
 
 
 class NSStepInfo(ctypes.Structure):
     _fields_ = [("pressure_iterations", ctypes.c_int), ("projection_iterations", ctypes.c_int),
-                ("viscous_iterations", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("viscous_iterations", ctypes.c_int), ("ms", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
 class MeshParams(ctypes.Structure):
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
     lib.dgw_ns_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
     lib.dgw_ns_copy_state.argtypes = [vp, vp, vp, vp]
     lib.dgw_tau_divdiv.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
+    lib.dgw_cfl_rate.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), vp]
     lib.dgw_apply_divdiv.argtypes = [vp, vp, vp, vp, vp]
     lib.dgw_apply_inverse_mass.argtypes = [vp, vp, vp, vp]
     lib.dgw_enrichment_active.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]
@@ -295,6 +296,14 @@ class Mesh:
                                                  _ptr(b, torch.float64, self.n_p, "b"), _stream(stream)))
         return b
 
+    def cfl_rate(self, u, stream=None):
+        """Largest |J^-1 (ubar + u~)|_2 over the linear volume point set (dgw_cfl_rate): the rate of the
+        adaptive time step Cr / (k^1.5 rate)."""
+        import torch
+        r = ctypes.c_double()
+        _check(self.lib.dgw_cfl_rate(self.h, _ptr(u, torch.float64, self.n_u, "u"), ctypes.byref(r), _stream(stream)))
+        return r.value
+
     def tau_divdiv(self, u, dt, cr, tau_d, stream=None):
         """Per-cell tau_D = |u|_K h dt / Cr into tau_d (nc doubles)."""
         import torch
@@ -449,12 +458,12 @@ class DualSplitting:
 
     def __init__(self, mesh: Mesh, u0, *, dt, cr=0.14, force=(0.0, 0.0, 0.0), rtol_pressure=1e-10,
                  rtol_projection=1e-10, rtol_viscous=1e-10, max_iter=2000, pressure_mode=1,
-                 update_wall_model=False, high_order_pressure_bc=False, stream=None):
+                 update_wall_model=False, high_order_pressure_bc=False, adaptive_dt=False, stream=None):
         import torch
         self.mesh, self.lib = mesh, mesh.lib
         self.params = NSParams(dt, cr, (ctypes.c_double * 3)(*force), rtol_pressure, rtol_projection, rtol_viscous,
                                max_iter, pressure_mode, 1 if update_wall_model else 0,
-                               1 if high_order_pressure_bc else 0)
+                               1 if high_order_pressure_bc else 0, 1 if adaptive_dt else 0)
         h = ctypes.c_void_p()
         _check(self.lib.dgw_ns_create(mesh.h, ctypes.byref(self.params), _ptr(u0, torch.float64, mesh.n_u, "u0"),
                                       _stream(stream), ctypes.byref(h)))
@@ -464,7 +473,7 @@ class DualSplitting:
         info = NSStepInfo()
         _check(self.lib.dgw_ns_step(self.h, ctypes.byref(info), _stream(stream)))
         return {"pressure_iterations": info.pressure_iterations, "projection_iterations": info.projection_iterations,
-                "viscous_iterations": info.viscous_iterations, "ms": info.ms}
+                "viscous_iterations": info.viscous_iterations, "ms": info.ms, "dt": info.dt}
 
     def _state(self):
         u, p, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int()

@@ -191,3 +191,58 @@ def test_dual_splitting_matches_oracle(dgw, name, w, kw, update, nsteps, hobc):
         du = _l2(om, u - ur, ur)
         dp = np.linalg.norm(p - pr) / pscale
         assert du < 1e-8 and dp < 1e-6, (step, du, dp, info)
+
+
+RATE_CASES = [
+    ("channel_q2_4x4x2", I.Workload("cr", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=61), {}),
+    ("channel_q3_two_layers_l0", I.Workload("cr3", 3, 6, 2, 3, 395.0, 1.0 / 6000.0, seed=62), {"n_layers": 2, "enrich_l": 0}),
+    ("bump_q3_6x4x2", I.bump_workload("crb", 6, 4, 2, 3, seed=63), {}),
+]
+
+
+@pytest.mark.parametrize("name,w,kw", RATE_CASES, ids=[c[0] for c in RATE_CASES])
+def test_cfl_rate_matches_oracle(dgw, name, w, kw):
+    """dgw_cfl_rate against the oracle on the workload field and on a random field whose enrichment
+    coefficients are as large as the standard ones (the largest rate then sits in a wall cell)."""
+    om, gm = _meshes(dgw, w, **kw)
+    nef = 1 if kw.get("enrich_l", 1) == 0 else 8
+    u0 = I.workload_velocity(om.node_coords(), om.n_e, w, n_layers=kw.get("n_layers", 1), nef=nef)
+    ur = I.uniform(w.seed, om.n_u, -1.0, 1.0, stream=64)
+    for u in (u0, ur):
+        ref = om.cfl_rate(u)
+        got = gm.cfl_rate(torch.tensor(u, device="cuda"))
+        assert abs(got / ref - 1.0) < 1e-12, (got, ref)
+
+
+ADAPTIVE_CASES = [
+    ("channel_q2_4x4x2", I.Workload("ad", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=65), {}, False),
+    ("bump_q2_6x4x2_high_order_bc", I.bump_workload("adb", 6, 4, 2, 2, seed=66), {}, True),
+]
+
+
+@pytest.mark.parametrize("name,w,kw,hobc", ADAPTIVE_CASES, ids=[c[0] for c in ADAPTIVE_CASES])
+def test_adaptive_dual_splitting_matches_oracle(dgw, name, w, kw, hobc):
+    """Adaptive steps (the CFL step binds: dt_max is large) against the oracle: the step sizes to
+    1e-12 (they follow from u^n, so the GPU's rounding in u^n moves them by ~1e-8 relative at most in
+    later steps) and the fields as in the constant-step test."""
+    om, gm = _meshes(dgw, w, **kw)
+    u0 = I.workload_velocity(om.node_coords(), om.n_e, w)
+    force = (w.tau_w / (0.5 * w.ly), 0.0, 0.0)
+    ref = O.DualSplitting(om, u0, dt=1.0, cr=0.14, force=force, rtol=1e-13, high_order_pressure_bc=hobc,
+                          adaptive=True)
+    ns = dgw.DualSplitting(gm, torch.tensor(u0, device="cuda"), dt=1.0, cr=0.14, force=force, rtol_pressure=1e-12,
+                           rtol_projection=1e-12, rtol_viscous=1e-12, pressure_mode=0, high_order_pressure_bc=hobc,
+                           adaptive_dt=True)
+    pscale = None
+    for step in range(3):
+        info = ns.step()
+        ur, pr = ref.step()
+        assert info["dt"] < 1.0
+        assert abs(info["dt"] / ref.dts[-1] - 1.0) < (1e-12 if step == 0 else 1e-7), (step, info["dt"], ref.dts[-1])
+        u = ns.velocity().cpu().numpy()
+        p = ns.pressure().cpu().numpy()
+        pscale = pscale or np.linalg.norm(pr)
+        du = _l2(om, u - ur, ur)
+        dp = np.linalg.norm(p - pr) / pscale
+        assert du < 1e-8 and dp < 1e-6, (step, du, dp, info)
+    assert len(set(ref.dts)) > 1   # the step changed, so the variable-step constants were used

@@ -1108,6 +1108,83 @@ def test_dual_splitting_keeps_poiseuille_flow_steady():
         assert np.abs(p).max() < 1e-10
 
 
+def test_cfl_rate_of_a_uniform_flow_is_the_thinnest_row_closed_form():
+    """For a constant velocity (U, V, W) without enrichment on the boxes of the graded channel,
+    |J^-1 u|_2 = sqrt((U/h_x)^2 + (V/h_y)^2 + (W/h_z)^2) at every point of a cell, so the rate is
+    that of the thinnest row (cell sizes read from the node coordinates)."""
+    m = O.Mesh(4, 6, 3, 2, n_layers=0)
+    U, V, W = 1.0, 0.5, -0.25
+    u = _std_field(m, lambda x, y, z: U + 0 * y, lambda x, y, z: V + 0 * y, lambda x, y, z: W + 0 * y)
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    h = X.max(axis=1) - X.min(axis=1)
+    ref = np.sqrt((U / h[:, 0]) ** 2 + (V / h[:, 1]) ** 2 + (W / h[:, 2]) ** 2).max()
+    assert abs(m.cfl_rate(u) / ref - 1.0) < 1e-13
+    assert abs(m.cfl_rate(-3.0 * u) / (3.0 * ref) - 1.0) < 1e-13
+
+
+def test_cfl_rate_includes_the_enrichment_at_the_wall_normal_points():
+    """With ubar = 0 and u~_B = u_tau e_x the velocity is u_tau psi(y+) e_x, largest at the outermost
+    of the q_w wall-normal Gauss points of a wall cell: rate = u_tau psi(y+_q) / h_x there."""
+    k, nu, tau_w = 2, 1e-3, 4e-2
+    m = O.Mesh(2, 4, 2, k, nu=nu, tau_w=tau_w, n_layers=1)
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = math.sqrt(tau_w)
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    hx = X[0, :, 0].max() - X[0, :, 0].min()
+    hy = X[0, :, 1].max() - X[0, :, 1].min()
+    gy, _ = O.gauss(8)
+    ut = math.sqrt(tau_w)
+    ref = max(ut * O.psi_spalding(y * hy * ut / nu)[0] for y in gy) / hx
+    assert abs(m.cfl_rate(u) / ref - 1.0) < 1e-12
+
+
+def test_variable_step_bdf2_and_extrapolation_constants():
+    """gamma_0, alpha_i: dt_n times the derivative at t_{n+1} of the quadratic interpolant through three
+    unevenly spaced times (NumPy polynomial fit); beta_i: the linear extrapolation; omega = 1 gives the
+    constant-step constants exactly."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        d1, d0 = rng.uniform(0.1, 2.0, 2)     # dt_{n-1}, dt_n
+        t = np.array([0.0, d1, d1 + d0])       # t_{n-1}, t_n, t_{n+1}
+        g0, a0, a1, b0, b1 = O.bdf2_variable(d0 / d1)
+        for j in range(3):                     # the quadratic interpolant of the j-th unit vector
+            y = np.zeros(3); y[j] = 1.0
+            c = np.polyfit(t, y, 2)
+            deriv = d0 * np.polyval(np.polyder(c), t[2])
+            ref = [-a1, -a0, g0][j]            # u^{n-1}: -alpha_1, u^n: -alpha_0, u^{n+1}: gamma_0
+            assert abs(deriv - ref) < 1e-10 * max(1.0, abs(ref))
+        c = np.polyfit(t[:2], [1.0, 0.0], 1)    # extrapolation weight of u^{n-1}
+        assert abs(np.polyval(c, t[2]) - b1) < 1e-12
+        c = np.polyfit(t[:2], [0.0, 1.0], 1)
+        assert abs(np.polyval(c, t[2]) - b0) < 1e-12
+    assert O.bdf2_variable(1.0) == (1.5, 2.0, -0.5, 2.0, -1.0)
+
+
+def test_adaptive_dual_splitting_reduces_to_the_constant_step():
+    """When the CFL step is larger than dt the adaptive integrator takes dt in every step and equals the
+    constant-step one (velocities bit for bit; the pressure to the rounding of the oracle's threaded
+    CG reductions); when it binds, dt_n = Cr / (k^1.5 rate(u^n)) and Poiseuille flow
+    still stays steady (variable BDF2 constants sum to zero on a steady state)."""
+    nu, U = 1e-2, 1.0
+    m = O.Mesh(4, 4, 2, 2, n_layers=0, nu=nu)
+    u0 = _std_field(m, lambda x, y, z: U * (1 - y ** 2), lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    force = (2 * nu * U, 0.0, 0.0)
+    a = O.DualSplitting(m, u0, dt=5e-3, cr=100.0, force=force, adaptive=True)
+    b = O.DualSplitting(m, u0, dt=5e-3, cr=100.0, force=force)
+    for _ in range(3):
+        ua, pa = a.step()
+        ub, pb = b.step()
+        assert np.array_equal(ua, ub)
+        assert np.abs(pa - pb).max() <= 1e-12 * max(np.abs(pb).max(), 1e-300) or np.abs(pa - pb).max() < 1e-14
+    assert a.dts == [5e-3] * 3
+    c = O.DualSplitting(m, u0, dt=1.0, cr=0.14, force=force, adaptive=True)
+    for _ in range(3):
+        u, p = c.step()
+    rate = m.cfl_rate(u0)
+    assert abs(c.dts[0] / (0.14 / (2 ** 1.5 * rate)) - 1.0) < 1e-14
+    assert _l2_rel(m, u, u0) < 1e-11
+
+
 # ---------------------------------------------------------------------------------------------
 # Vorticity and the high-order pressure Neumann data (Sec. 4.1 eq. bc_d_pres)
 # ---------------------------------------------------------------------------------------------
