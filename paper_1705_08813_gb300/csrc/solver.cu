@@ -3,6 +3,7 @@
 // SIPG operator is the constant vector). Deterministic two-stage reductions; FP64 vectors,
 // residuals and dot products.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -95,12 +96,31 @@ __global__ void axpby_kernel(double *__restrict__ y, const double *__restrict__ 
 
 // ---- FP32 vectors of the mixed-precision inner solve (reductions accumulate in FP64)
 
-// partial[blockIdx] = sum_i a_i b_i (b == nullptr: sum_i a_i), FP32 inputs
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// x . y of four FP32 pairs in FP32 (the group sum then goes into an FP64 accumulator)
+__device__ __forceinline__ float dot4(float4 x, float4 y) {
+  return fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+}
+
+// partial[blockIdx] = sum_i a_i b_i (b == nullptr: sum_i a_i), FP32 inputs: 16-byte loads, each group
+// of four products summed in FP32 and accumulated in FP64 (the FP64 units of this part do a quarter
+// of the work of a per-element FP64 accumulation); fixed order for a given launch shape.
 __global__ void dot32_partial_kernel(const float *__restrict__ a, const float *__restrict__ b, long n,
                                      double *__restrict__ partial) {
   double s = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    s += b ? (double)a[i] * (double)b[i] : (double)a[i];
+  const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x, stride = (long)gridDim.x * blockDim.x;
+  long i0 = 0;
+  if (aligned16(a) && (!b || aligned16(b))) {
+    const long n4 = n >> 2;
+    const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
+    for (long i = gid; i < n4; i += stride) {
+      const float4 x = a4[i];
+      s += (double)(b ? dot4(x, b4[i]) : (x.x + x.y) + (x.z + x.w));
+    }
+    i0 = n4 << 2;
+  }
+  for (long i = i0 + gid; i < n; i += stride) s += b ? (double)a[i] * (double)b[i] : (double)a[i];
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
@@ -113,13 +133,46 @@ __global__ void to_unit32_kernel(float *__restrict__ r32, const double *__restri
     r32[i] = (float)(r[i] * s);
 }
 
-// e += alpha d; r -= alpha q with alpha = sc[RZ] / sc[DQ]
-__global__ void pcg32_update_kernel(float *__restrict__ e, float *__restrict__ r, const float *__restrict__ d,
-                                    const float *__restrict__ q, long n, const double *sc) {
+
+// e += alpha d, r -= alpha q (alpha = sc[RZ] / sc[DQ]) and, in the same pass, the partial sums of
+// r.r (partial[blk]) and r.z (partial[RED_BLOCKS + blk]) of the updated r with z, which still holds
+// the previous preconditioned residual (the r.z_old of the flexible beta)
+__global__ void pcg32_update_dots_kernel(float *__restrict__ e, float *__restrict__ r, const float *__restrict__ d,
+                                         const float *__restrict__ q, const float *__restrict__ z, long n,
+                                         const double *sc, double *__restrict__ partial) {
   const float alpha = (float)(sc[SC_RZ] / sc[SC_DQ]);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+  double srr = 0.0, srz = 0.0;
+  const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x, stride = (long)gridDim.x * blockDim.x;
+  long i0 = 0;
+  if (aligned16(e) && aligned16(r) && aligned16(d) && aligned16(q) && aligned16(z)) {
+    const long n4 = n >> 2;
+    float4 *e4 = reinterpret_cast<float4 *>(e), *r4 = reinterpret_cast<float4 *>(r);
+    const float4 *d4 = reinterpret_cast<const float4 *>(d), *q4 = reinterpret_cast<const float4 *>(q);
+    const float4 *z4 = reinterpret_cast<const float4 *>(z);
+    for (long i = gid; i < n4; i += stride) {
+      float4 ev = e4[i], rv = r4[i];
+      const float4 dv = d4[i], qv = q4[i], zv = z4[i];
+      ev.x += alpha * dv.x; ev.y += alpha * dv.y; ev.z += alpha * dv.z; ev.w += alpha * dv.w;
+      rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+      e4[i] = ev;
+      r4[i] = rv;
+      srr += (double)dot4(rv, rv);
+      srz += (double)dot4(rv, zv);
+    }
+    i0 = n4 << 2;
+  }
+  for (long i = i0 + gid; i < n; i += stride) {
     e[i] += alpha * d[i];
-    r[i] -= alpha * q[i];
+    const float rn = r[i] - alpha * q[i];
+    r[i] = rn;
+    srr += (double)rn * (double)rn;
+    srz += (double)rn * (double)z[i];
+  }
+  srr = block_sum(srr);
+  srz = block_sum(srz);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = srr;
+    partial[RED_BLOCKS + blockIdx.x] = srz;
   }
 }
 
@@ -182,7 +235,7 @@ dgw_solver *get_solver(dgw_mesh *M) {
   const long n = M->np;
   cudaError_t e = cudaSuccess;
   double **vecs[] = {&S->b, &S->r, &S->z, &S->d, &S->q, &S->zold, &S->partial, &S->sc};
-  const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)RED_BLOCKS,
+  const size_t sizes[] = {(size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)n, (size_t)2 * RED_BLOCKS,
                           (size_t)SC_COUNT};
   e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
@@ -273,8 +326,8 @@ static dgw_status pressure_solve_mixed(dgw_mesh *M, dgw_solver *S, const dgw_sol
   cudaError_t e = mg_level0_f32(S, &r32, &z32);
   if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: mixed hierarchy");
   if (!S->d32) {
-    float **v32[] = {&S->d32, &S->q32, &S->e32, &S->zold32};
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    float **v32[] = {&S->d32, &S->q32, &S->e32};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
       e = cudaMalloc(v32[i], n * sizeof(float));
       if (e == cudaSuccess) e = cudaMemsetAsync(*v32[i], 0, n * sizeof(float), s);
     }
@@ -306,19 +359,19 @@ static dgw_status pressure_solve_mixed(dgw_mesh *M, dgw_solver *S, const dgw_sol
       e = launch_laplace<float>(M->v32, S->d32, S->q32, s);
       if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: operator");
       reduce32_to(S->d32, S->q32, n, S->partial, S->sc, SC_DQ, s);
-      note_launch();
-      pcg32_update_kernel<<<G, 256, 0, s>>>(S->e32, r32, S->d32, S->q32, n, S->sc);
-      reduce32_to(r32, r32, n, S->partial, S->sc, SC_RR, s);
+      // the update with r.r and r.z_old (z32 still holds the previous preconditioned residual)
+      note_launches(3);
+      pcg32_update_dots_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(S->e32, r32, S->d32, S->q32, z32, n, S->sc, S->partial);
+      dot_finish_kernel<<<1, 32, 0, s>>>(S->partial, RED_BLOCKS, S->sc, SC_RR);
+      dot_finish_kernel<<<1, 32, 0, s>>>(S->partial + RED_BLOCKS, RED_BLOCKS, S->sc, SC_RZOLD);
       cudaMemcpyAsync(S->host_sc, S->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve");
       ++it;
       if (std::sqrt(std::max(S->host_sc[SC_RR], 0.0)) <= tol_in || it >= o->max_iter) break;
-      cudaMemcpyAsync(S->zold32, z32, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
       e = vcycle32_graph(M, S, z32, s);
       if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve: preconditioner");
       reduce32_to(r32, z32, n, S->partial, S->sc, SC_RZNEW, s);
-      reduce32_to(r32, S->zold32, n, S->partial, S->sc, SC_RZOLD, s);
       note_launch();
       pcg32_direction_kernel<<<G, 256, 0, s>>>(S->d32, z32, n, S->sc, 0);
       note_launch();
@@ -454,7 +507,7 @@ void dgw_solver_free(dgw_mesh *M) {
   dgw::mg_free(S);
   cudaFree(S->b); cudaFree(S->r); cudaFree(S->z); cudaFree(S->d); cudaFree(S->q); cudaFree(S->zold);
   cudaFree(S->partial); cudaFree(S->sc);
-  cudaFree(S->d32); cudaFree(S->q32); cudaFree(S->e32); cudaFree(S->zold32);
+  cudaFree(S->d32); cudaFree(S->q32); cudaFree(S->e32);
   if (S->vgraph32) cudaGraphExecDestroy(S->vgraph32);
   if (S->host_sc) cudaFreeHost(S->host_sc);
   if (S->ev0) cudaEventDestroy(S->ev0);

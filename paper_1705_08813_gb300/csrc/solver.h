@@ -27,7 +27,7 @@ struct dgw_solver {
   unsigned long long vgraph_launches = 0, vgraph_dofs = 0;
   // mixed mode: FP32 inner PCG vectors (r and z alias the finest level's b and x) and the captured
   // FP32 V-cycle with its mean projection
-  float *d32 = nullptr, *q32 = nullptr, *e32 = nullptr, *zold32 = nullptr;
+  float *d32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   cudaGraphExec_t vgraph32 = nullptr;
   unsigned long long vgraph32_launches = 0, vgraph32_dofs = 0;
   // multigrid hierarchy (built on first use per mode)
