@@ -14,6 +14,8 @@
 // converged stop updating while the rest continue) and applies the refinement. Columns join and
 // leave only between rounds; the caller compacts the block so the active columns are 0..ncols-1.
 #include <algorithm>
+#include <cstdint>
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -48,15 +50,33 @@ __device__ double bblock_sum(double v) {
   return s;
 }
 
-// per column (blockIdx.y): partial[col][blockIdx.x] = sum a b (b null: sum a), FP64 accumulation
+__device__ __forceinline__ bool baligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+__device__ __forceinline__ float bdot4(float4 x, float4 y) {
+  return fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+}
+
+// per column (blockIdx.y): partial[col][blockIdx.x] = sum a b (b null: sum a), FP64 accumulation (FP32
+// columns: 16-byte loads, groups of four products summed in FP32 first)
 template <typename T>
 __global__ void bdot_partial(const T *__restrict__ a, const T *__restrict__ b, long n, double *__restrict__ partial) {
   const size_t co = (size_t)blockIdx.y * n;
   a += co;
   if (b) b += co;
   double s = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    s += b ? (double)a[i] * (double)b[i] : (double)a[i];
+  const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x, stride = (long)gridDim.x * blockDim.x;
+  long i0 = 0;
+  if constexpr (std::is_same<T, float>::value) {
+    if (baligned16(a) && (!b || baligned16(b))) {
+      const long n4 = n >> 2;
+      const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
+      for (long i = gid; i < n4; i += stride) {
+        const float4 x = a4[i];
+        s += (double)(b ? bdot4(x, b4[i]) : (x.x + x.y) + (x.z + x.w));
+      }
+      i0 = n4 << 2;
+    }
+  }
+  for (long i = i0 + gid; i < n; i += stride) s += b ? (double)a[i] * (double)b[i] : (double)a[i];
   s = bblock_sum<T>(s);
   if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
@@ -94,17 +114,52 @@ __global__ void bto_unit32(float *__restrict__ r32, const double *__restrict__ r
     r32[co + i] = (float)(r[co + i] * s);
 }
 
-// e += alpha d, r -= alpha q (alpha = rz / dq) for the columns whose inner solve still runs
-__global__ void bpcg_update(float *__restrict__ e, float *__restrict__ r, const float *__restrict__ d,
-                            const float *__restrict__ q, long n, const double *__restrict__ sc,
-                            const int *__restrict__ run) {
-  if (!run[blockIdx.y]) return;
-  const size_t co = (size_t)blockIdx.y * n;
-  const double *c = sc + (size_t)blockIdx.y * BS_COUNT;
-  const float alpha = (float)(c[BS_RZ] / c[BS_DQ]);
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    e[co + i] += alpha * d[co + i];
-    r[co + i] -= alpha * q[co + i];
+// e += alpha d, r -= alpha q (alpha = rz / dq) for the columns whose inner solve still runs and, in the
+// same pass, the partial sums of r.r (partial[col][blk]) and of r.z (partial[ncols + col][blk]) of the
+// updated r and z, which still holds the previous preconditioned residual (the r.z_old of the
+// flexible beta); columns that have stopped write zeros.
+__global__ void bpcg_update_dots(float *__restrict__ e, float *__restrict__ r, const float *__restrict__ d,
+                                 const float *__restrict__ q, const float *__restrict__ z, long n,
+                                 const double *__restrict__ sc, const int *__restrict__ run, double *__restrict__ partial) {
+  const int col = blockIdx.y, ncols = gridDim.y;
+  double srr = 0.0, srz = 0.0;
+  if (run[col]) {
+    const size_t co = (size_t)col * n;
+    e += co; r += co; d += co; q += co; z += co;
+    const double *c = sc + (size_t)col * BS_COUNT;
+    const float alpha = (float)(c[BS_RZ] / c[BS_DQ]);
+    const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x, stride = (long)gridDim.x * blockDim.x;
+    long i0 = 0;
+    if (baligned16(e) && baligned16(r) && baligned16(d) && baligned16(q) && baligned16(z)) {
+      const long n4 = n >> 2;
+      float4 *e4 = reinterpret_cast<float4 *>(e), *r4 = reinterpret_cast<float4 *>(r);
+      const float4 *d4 = reinterpret_cast<const float4 *>(d), *q4 = reinterpret_cast<const float4 *>(q);
+      const float4 *z4 = reinterpret_cast<const float4 *>(z);
+      for (long i = gid; i < n4; i += stride) {
+        float4 ev = e4[i], rv = r4[i];
+        const float4 dv = d4[i], qv = q4[i], zv = z4[i];
+        ev.x += alpha * dv.x; ev.y += alpha * dv.y; ev.z += alpha * dv.z; ev.w += alpha * dv.w;
+        rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+        e4[i] = ev;
+        r4[i] = rv;
+        srr += (double)bdot4(rv, rv);
+        srz += (double)bdot4(rv, zv);
+      }
+      i0 = n4 << 2;
+    }
+    for (long i = i0 + gid; i < n; i += stride) {
+      e[i] += alpha * d[i];
+      const float rn = r[i] - alpha * q[i];
+      r[i] = rn;
+      srr += (double)rn * (double)rn;
+      srz += (double)rn * (double)z[i];
+    }
+  }
+  srr = bblock_sum<float>(srr);
+  srz = bblock_sum<float>(srz);
+  if (threadIdx.x == 0) {
+    partial[(size_t)col * gridDim.x + blockIdx.x] = srr;
+    partial[(size_t)(ncols + col) * gridDim.x + blockIdx.x] = srz;
   }
 }
 
@@ -156,7 +211,7 @@ struct Batch {
   void *mg = nullptr;
   int cheb = 5;
   float *r32 = nullptr, *z32 = nullptr;   // the hierarchy's level-0 blocks
-  float *d32 = nullptr, *q32 = nullptr, *e32 = nullptr, *zold32 = nullptr;
+  float *d32 = nullptr, *q32 = nullptr, *e32 = nullptr;
   double *b64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
   double *partial = nullptr, *sc = nullptr, *host_sc = nullptr;
   int *run = nullptr, *host_run = nullptr;
@@ -249,12 +304,11 @@ cudaError_t batch_create(dgw_mesh *M, int cap, int cheb, Batch **out) {
   B->d32 = balloc<float>(B, nb, e);
   B->q32 = balloc<float>(B, nb, e);
   B->e32 = balloc<float>(B, nb, e);
-  B->zold32 = balloc<float>(B, nb, e);
   B->b64 = balloc<double>(B, nb, e);
   B->r64 = balloc<double>(B, nb, e);
   B->p64 = balloc<double>(B, nb, e);
   B->q64 = balloc<double>(B, nb, e);
-  B->partial = balloc<double>(B, (size_t)BR * cap, e);
+  B->partial = balloc<double>(B, (size_t)2 * BR * cap, e);   // two partial sums per column (update + dots)
   B->sc = balloc<double>(B, (size_t)BS_COUNT * cap, e);
   B->run = balloc<int>(B, cap, e);
   if (e == cudaSuccess) e = cudaMallocHost(&B->host_sc, (size_t)BS_COUNT * cap * sizeof(double));
@@ -398,9 +452,12 @@ cudaError_t batch_round(Batch *B, std::vector<BatchColumn> &done) {
     e = launch_laplace_epi<float>(B->M->v32, B->d32, B->q32, e32, s);
     if (e != cudaSuccess) return e;
     breduce<float>(B->d32, B->q32, n, ncols, B->partial, B->sc, BS_DQ, s);
-    note_launch();
-    bpcg_update<<<dim3(G, ncols), 256, 0, s>>>(B->e32, B->r32, B->d32, B->q32, n, B->sc, B->run);
-    breduce<float>(B->r32, B->r32, n, ncols, B->partial, B->sc, BS_RR, s);
+    // the update with r.r and r.z_old (z32 still holds the previous preconditioned residuals)
+    note_launches(3);
+    bpcg_update_dots<<<dim3(BR, ncols), 256, 0, s>>>(B->e32, B->r32, B->d32, B->q32, B->z32, n, B->sc, B->run,
+                                                     B->partial);
+    bdot_finish<<<ncols, 32, 0, s>>>(B->partial, BR, B->sc, BS_RR);
+    bdot_finish<<<ncols, 32, 0, s>>>(B->partial + (size_t)ncols * BR, BR, B->sc, BS_RZOLD);
     e = sync_scalars(B, ncols);
     if (e != cudaSuccess) return e;
     bool any = false;
@@ -414,12 +471,9 @@ cudaError_t batch_round(Batch *B, std::vector<BatchColumn> &done) {
     }
     if (!any) break;
     e = upload_run(B, ncols);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(B->zold32, B->z32, (size_t)ncols * n * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = vcycle_block(B, ncols);
     if (e != cudaSuccess) return e;
     breduce<float>(B->r32, B->z32, n, ncols, B->partial, B->sc, BS_RZNEW, s);
-    breduce<float>(B->r32, B->zold32, n, ncols, B->partial, B->sc, BS_RZOLD, s);
     note_launches(2);
     bpcg_direction<<<dim3(G, ncols), 256, 0, s>>>(B->d32, B->z32, n, B->sc, 0, B->run);
     bshift_rz<<<1, 32, 0, s>>>(B->sc, ncols, B->run);
