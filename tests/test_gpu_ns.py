@@ -246,3 +246,22 @@ def test_adaptive_dual_splitting_matches_oracle(dgw, name, w, kw, hobc):
         dp = np.linalg.norm(p - pr) / pscale
         assert du < 1e-8 and dp < 1e-6, (step, du, dp, info)
     assert len(set(ref.dts)) > 1   # the step changed, so the variable-step constants were used
+
+
+def test_time_step_reports_a_capped_solve(dgw):
+    """With max_iter below what the solves of a step need at rtol 1e-12 the step fails with
+    DGW_ENOTCONV (raised by the binding) instead of returning an unconverged field; the same
+    integrator created with enough iterations takes the step."""
+    w = I.Workload("cap", 4, 4, 2, 2, 180.0, 1.0 / 3250.0, seed=67)
+    om, gm = _meshes(dgw, w)
+    u0 = torch.tensor(I.workload_velocity(om.node_coords(), om.n_e, w), device="cuda")
+    force = (w.tau_w, 0.0, 0.0)
+    capped = dgw.DualSplitting(gm, u0, dt=2e-3, force=force, rtol_pressure=1e-12, rtol_projection=1e-12,
+                               rtol_viscous=1e-12, max_iter=3, pressure_mode=0)
+    with pytest.raises(dgw.DGWError) as err:
+        capped.step()
+    assert err.value.status == -3
+    ok = dgw.DualSplitting(gm, u0, dt=2e-3, force=force, rtol_pressure=1e-12, rtol_projection=1e-12,
+                           rtol_viscous=1e-12, max_iter=2000, pressure_mode=0)
+    info = ok.step()
+    assert info["projection_iterations"] > 3
