@@ -228,20 +228,26 @@ def vector_flops_per_cell(op, k):
       viscous     36 n^4 (volume: 12 line passes per output component)
                   + 174 n^3 (faces: normal and tangential derivatives, two face-grid passes of
                   eight coefficient arrays, normal-derivative test terms) + 180 n^2 (coefficients)
-    The convective term is evaluated at q = floor(3k/2)+1 Gauss points (Sec. 4.4):
-      values F = q n^3 + q^2 n^2 + q^3 n per component, integration B = 3 q^3 n + 3 q^2 n^2 + 2 q n^3
-      per output component, 9 q^3 for the products, and per face direction 12 (q n^2 + q^2 n)
-      (traces of both sides), 40 q^2 (flux), 6 (q^2 n + q n^2) (integration back)."""
+    The convective term is evaluated at q = floor(3k/2)+1 Gauss points (Sec. 4.4). Its 1-D products
+    (n nodes -> q points and back) use the even-odd form: with P(a, b) the flops of one product from a
+    inputs to b outputs (sums and differences of mirrored inputs, half-size products per mirrored pair
+    of outputs, the middle row),
+      values (n^2 + q n + q^2) P(n, q) per component, integration (3 q^2 + 3 q n + 2 n^2) P(q, n)
+      + (q n + n^2) n per output component, 9 q^3 for the products, and per face direction
+      12 (n + q) P(n, q) (traces of both sides), 40 q^2 (flux), 6 (q + n) P(q, n) (integration back)."""
     n = k + 1
     if op == "divergence":
         return 2 * (8 * n ** 4 + 12 * n ** 3)
     if op == "viscous":
         return 2 * (36 * n ** 4 + 174 * n ** 3) + 180 * n * n
     q = (3 * k) // 2 + 1
-    F = q * n ** 3 + q * q * n * n + q ** 3 * n
-    B = 3 * q ** 3 * n + 3 * q * q * n * n + 2 * q * n ** 3
-    fma = 3 * F + 3 * B + 3 * (12 * (q * n * n + q * q * n) + 6 * (q * q * n + q * n * n))
-    return 2 * fma + 9 * q ** 3 + 3 * 40 * q * q
+
+    def P(a, b):
+        return 2 * (a // 2) + (b // 2) * (4 * (a // 2) + a % 2 + 2) + (b % 2) * (2 * (a // 2) + a % 2)
+    fwd, bwd = P(n, q), P(q, n)
+    vol = 3 * (n * n + q * n + q * q) * fwd + 3 * ((3 * q * q + 3 * q * n + 2 * n * n) * bwd + (q * n + n * n) * n)
+    faces = 3 * (12 * (n + q) * fwd + 6 * (q + n) * bwd)
+    return vol + faces + 9 * q ** 3 + 3 * 40 * q * q
 
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz

@@ -39,6 +39,13 @@ struct VecConst {
   R Sc[QMAX * NMAX];
   R Dc[QMAX * NMAX];
   R wc[QMAX];
+  // Even-odd halves of Sc and Dc (the point set and the nodes are symmetric about 1/2, so
+  // Sc[q-1-j][n-1-b] = Sc[j][b] and Dc[q-1-j][n-1-b] = -Dc[j][b]), rows j < q/2, columns b < n/2,
+  // stride n: SE/SO = (Sc[j][b] +/- Sc[j][n-1-b]) / 2, DA/DB = (Dc[j][b] -/+ Dc[j][n-1-b]) / 2
+  R SE[QMAX * NMAX];
+  R SO[QMAX * NMAX];
+  R DA[QMAX * NMAX];
+  R DB[QMAX * NMAX];
 };
 __constant__ VecConst<double> c_vec64[5];
 __constant__ VecConst<float> c_vec32[5];
@@ -94,6 +101,88 @@ template <typename R, int n>
 __device__ __forceinline__ void store_line(R *p, int stride, const R (&v)[n]) {
 #pragma unroll
   for (int b = 0; b < n; ++b) p[b * stride] = v[b];
+}
+
+// Even-odd forms of the 1-D products with the convective point set (Kronbichler and Kormann's even-odd
+// decomposition for symmetric 1-D bases): with v_e/v_o the sums and differences of mirrored entries,
+// each pair of mirrored outputs takes one product with a half-size table, about 4/5 of the
+// multiply-adds of the plain product at n = 5, q = 7.
+// out = Sc v (q points from n nodes)
+template <typename R, int n, int q>
+__device__ __forceinline__ void interp_eo(const VecConst<R> &C, const R (&v)[n], R (&out)[q]) {
+  constexpr int nh = n / 2, qh = q / 2;
+  R ve[nh > 0 ? nh : 1], vo[nh > 0 ? nh : 1];
+#pragma unroll
+  for (int b = 0; b < nh; ++b) { ve[b] = v[b] + v[n - 1 - b]; vo[b] = v[b] - v[n - 1 - b]; }
+#pragma unroll
+  for (int i = 0; i < qh; ++i) {
+    R e = (n & 1) ? C.Sc[i * n + nh] * v[nh] : r_zero<R>(), o = r_zero<R>();
+#pragma unroll
+    for (int b = 0; b < nh; ++b) {
+      e = r_fma(C.SE[i * n + b], ve[b], e);
+      o = r_fma(C.SO[i * n + b], vo[b], o);
+    }
+    out[i] = e + o;
+    out[q - 1 - i] = e - o;
+  }
+  if constexpr ((q & 1) != 0) {
+    R m = (n & 1) ? C.Sc[qh * n + nh] * v[nh] : r_zero<R>();
+#pragma unroll
+    for (int b = 0; b < nh; ++b) m = r_fma(C.Sc[qh * n + b], ve[b], m);
+    out[qh] = m;
+  }
+}
+// sums and differences of mirrored point values
+template <typename R, int q>
+__device__ __forceinline__ void point_eo(const R (&f)[q], R (&fe)[q / 2 > 0 ? q / 2 : 1], R (&fo)[q / 2 > 0 ? q / 2 : 1]) {
+#pragma unroll
+  for (int j = 0; j < q / 2; ++j) { fe[j] = f[j] + f[q - 1 - j]; fo[j] = f[j] - f[q - 1 - j]; }
+}
+// out (+)= Sc^T f (n nodes from q points; fe/fo from point_eo, fm = f[q/2] when q is odd)
+template <typename R, int n, int q, bool ACC>
+__device__ __forceinline__ void tinterp_s_eo(const VecConst<R> &C, const R (&fe)[q / 2 > 0 ? q / 2 : 1],
+                                             const R (&fo)[q / 2 > 0 ? q / 2 : 1], R fm, R (&out)[n]) {
+  constexpr int nh = n / 2, qh = q / 2;
+#pragma unroll
+  for (int b = 0; b < nh; ++b) {
+    R e = (q & 1) ? C.Sc[qh * n + b] * fm : r_zero<R>(), o = r_zero<R>();
+#pragma unroll
+    for (int j = 0; j < qh; ++j) {
+      e = r_fma(C.SE[j * n + b], fe[j], e);
+      o = r_fma(C.SO[j * n + b], fo[j], o);
+    }
+    out[b] = ACC ? out[b] + (e + o) : e + o;
+    out[n - 1 - b] = ACC ? out[n - 1 - b] + (e - o) : e - o;
+  }
+  if constexpr ((n & 1) != 0) {
+    R m = (q & 1) ? C.Sc[qh * n + nh] * fm : r_zero<R>();
+#pragma unroll
+    for (int j = 0; j < qh; ++j) m = r_fma(C.Sc[j * n + nh], fe[j], m);
+    out[nh] = ACC ? out[nh] + m : m;
+  }
+}
+// out (+)= Dc^T f
+template <typename R, int n, int q, bool ACC>
+__device__ __forceinline__ void tinterp_d_eo(const VecConst<R> &C, const R (&fe)[q / 2 > 0 ? q / 2 : 1],
+                                             const R (&fo)[q / 2 > 0 ? q / 2 : 1], R fm, R (&out)[n]) {
+  constexpr int nh = n / 2, qh = q / 2;
+#pragma unroll
+  for (int b = 0; b < nh; ++b) {
+    R e = (q & 1) ? C.Dc[qh * n + b] * fm : r_zero<R>(), o = r_zero<R>();
+#pragma unroll
+    for (int j = 0; j < qh; ++j) {
+      e = r_fma(C.DA[j * n + b], fe[j], e);
+      o = r_fma(C.DB[j * n + b], fo[j], o);
+    }
+    out[b] = ACC ? out[b] + (e + o) : e + o;
+    out[n - 1 - b] = ACC ? out[n - 1 - b] + (o - e) : o - e;
+  }
+  if constexpr ((n & 1) != 0) {
+    R m = r_zero<R>();   // the middle node's derivative is odd about the middle point
+#pragma unroll
+    for (int j = 0; j < qh; ++j) m = r_fma(C.Dc[j * n + nh], fo[j], m);
+    out[nh] = ACC ? out[nh] + m : m;
+  }
 }
 
 // line of a pass: x-lines (base n l, stride 1), y-lines (base lr + n^2 lq, stride n), z-lines
@@ -591,13 +680,10 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
     R v[n];
     load_line<R, n>(U + (cl * 3 + a) * n3 + n * l, 1, v);
     R *out = Wc(cl) + 3 * q3 + a * q * n2 + q * l;
+    R o[q];
+    interp_eo<R, n, q>(C, v, o);
 #pragma unroll
-    for (int i = 0; i < q; ++i) {
-      R acc = r_zero<R>();
-#pragma unroll
-      for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
-      out[i] = acc;
-    }
+    for (int i = 0; i < q; ++i) out[i] = o[i];
   }
   __syncthreads();
   for (int t = tid; t < cpb * 3 * q * n; t += nt) {   // lines (i0, i2), i0 < q, i2 < n
@@ -606,13 +692,10 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
     R v[n];
     load_line<R, n>(Wc(cl) + 3 * q3 + a * q * n2 + i0 + q * n * i2, q, v);
     R *out = Wc(cl) + 3 * q3 + P::A1 + a * q2 * n + i0 + q2 * i2;
+    R o[q];
+    interp_eo<R, n, q>(C, v, o);
 #pragma unroll
-    for (int i = 0; i < q; ++i) {
-      R acc = r_zero<R>();
-#pragma unroll
-      for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
-      out[q * i] = acc;
-    }
+    for (int i = 0; i < q; ++i) out[q * i] = o[i];
   }
   __syncthreads();
   for (int t = tid; t < cpb * 3 * q2; t += nt) {   // lines (i0, i1)
@@ -620,13 +703,10 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
     R v[n];
     load_line<R, n>(Wc(cl) + 3 * q3 + P::A1 + a * q2 * n + l, q2, v);
     R *out = Wc(cl) + a * q3 + l;
+    R o[q];
+    interp_eo<R, n, q>(C, v, o);
 #pragma unroll
-    for (int i = 0; i < q; ++i) {
-      R acc = r_zero<R>();
-#pragma unroll
-      for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
-      out[q2 * i] = acc;
-    }
+    for (int i = 0; i < q; ++i) out[q2 * i] = o[i];
   }
   __syncthreads();
   // ---- volume: -sum_d (V/h_d) sum_points w (d phi / d xi_d) u_a u_d, one output component at a time
@@ -635,23 +715,26 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
       const int cl = t / q2, l = t - cl * q2, i0 = l % q, i1 = l / q;
       const R *V = Wc(cl);
       R z0[n], z1[n], z2[n];
-#pragma unroll
-      for (int b = 0; b < n; ++b) { z0[b] = r_zero<R>(); z1[b] = r_zero<R>(); z2[b] = r_zero<R>(); }
+      R F0[q], F1[q], F2[q];
       const R w01 = C.wc[i0] * C.wc[i1];
 #pragma unroll
       for (int j = 0; j < q; ++j) {
         const int pt = l + q2 * j;
         const R ua = V[a * q3 + pt];
         const R wa = (w01 * C.wc[j]) * ua;
-        const R f0 = sc[0] * (wa * V[pt]);            // F_a0 = -(V/h_x) w u_a u_x
-        const R f1 = sc[1] * (wa * V[q3 + pt]);
-        const R f2 = sc[2] * (wa * V[2 * q3 + pt]);
-#pragma unroll
-        for (int b = 0; b < n; ++b) {
-          z0[b] = r_fma(C.Dc[j * n + b], f2, z0[b]);   // D_z^T F_a2
-          z1[b] = r_fma(C.Sc[j * n + b], f1, z1[b]);   // S_z^T F_a1
-          z2[b] = r_fma(C.Sc[j * n + b], f0, z2[b]);   // S_z^T F_a0
-        }
+        F0[j] = sc[0] * (wa * V[pt]);            // F_a0 = -(V/h_x) w u_a u_x
+        F1[j] = sc[1] * (wa * V[q3 + pt]);
+        F2[j] = sc[2] * (wa * V[2 * q3 + pt]);
+      }
+      {
+        constexpr int qh = q / 2 > 0 ? q / 2 : 1;
+        R fe[qh], fo[qh];
+        point_eo<R, q>(F2, fe, fo);
+        tinterp_d_eo<R, n, q, false>(C, fe, fo, F2[q / 2], z0);   // D_z^T F_a2
+        point_eo<R, q>(F1, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, F1[q / 2], z1);   // S_z^T F_a1
+        point_eo<R, q>(F0, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, F0[q / 2], z2);   // S_z^T F_a0
       }
       R *Z = Wc(cl) + 3 * q3;
       store_line<R, n>(Z + l, q2, z0);
@@ -663,17 +746,23 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
       const int cl = t / (q * n), l = t - cl * q * n, i0 = l % q, mz = l / q;
       const R *Z = Wc(cl) + 3 * q3;
       R y0[n], y1[n];
-#pragma unroll
-      for (int b = 0; b < n; ++b) { y0[b] = r_zero<R>(); y1[b] = r_zero<R>(); }
+      R za[q], zb[q], zc[q];
 #pragma unroll
       for (int j = 0; j < q; ++j) {
         const int pt = i0 + q * j + q2 * mz;
-        const R za = Z[pt], zb = Z[q2 * n + pt], zc = Z[2 * q2 * n + pt];
-#pragma unroll
-        for (int b = 0; b < n; ++b) {
-          y0[b] = r_fma(C.Sc[j * n + b], za, r_fma(C.Dc[j * n + b], zb, y0[b]));
-          y1[b] = r_fma(C.Sc[j * n + b], zc, y1[b]);
-        }
+        za[j] = Z[pt];
+        zb[j] = Z[q2 * n + pt];
+        zc[j] = Z[2 * q2 * n + pt];
+      }
+      {
+        constexpr int qh = q / 2 > 0 ? q / 2 : 1;
+        R fe[qh], fo[qh];
+        point_eo<R, q>(za, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, za[q / 2], y0);
+        point_eo<R, q>(zb, fe, fo);
+        tinterp_d_eo<R, n, q, true>(C, fe, fo, zb[q / 2], y0);
+        point_eo<R, q>(zc, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, zc[q / 2], y1);
       }
       R *Yb = Wc(cl) + 3 * q3 + P::A1;
       store_line<R, n>(Yb + i0 + q * n * mz, q, y0);
@@ -684,13 +773,16 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
       const int cl = t / n2, l = t - cl * n2;
       const R *Yb = Wc(cl) + 3 * q3 + P::A1 + q * l;
       R o[n];
+      R ya[q], yb[q];
 #pragma unroll
-      for (int b = 0; b < n; ++b) o[b] = r_zero<R>();
-#pragma unroll
-      for (int j = 0; j < q; ++j) {
-        const R ya = Yb[j], yb = Yb[q * n2 + j];
-#pragma unroll
-        for (int b = 0; b < n; ++b) o[b] = r_fma(C.Sc[j * n + b], ya, r_fma(C.Dc[j * n + b], yb, o[b]));
+      for (int j = 0; j < q; ++j) { ya[j] = Yb[j]; yb[j] = Yb[q * n2 + j]; }
+      {
+        constexpr int qh = q / 2 > 0 ? q / 2 : 1;
+        R fe[qh], fo[qh];
+        point_eo<R, q>(ya, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, ya[q / 2], o);
+        point_eo<R, q>(yb, fe, fo);
+        tinterp_d_eo<R, n, q, true>(C, fe, fo, yb[q / 2], o);
       }
       R *yo = Y + (cl * 3 + a) * n3 + n * l;
 #pragma unroll
@@ -727,13 +819,10 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
       R v[n];
       load_line<R, n>(Wc(cl) + k * n2 + n * i2, 1, v);
       R *out = Wc(cl) + 12 * n2 + k * q * n + q * i2;
+      R o[q];
+      interp_eo<R, n, q>(C, v, o);
 #pragma unroll
-      for (int i = 0; i < q; ++i) {
-        R acc = r_zero<R>();
-#pragma unroll
-        for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
-        out[i] = acc;
-      }
+      for (int i = 0; i < q; ++i) out[i] = o[i];
     }
     __syncthreads();
     for (int t = tid; t < cpb * 12 * q; t += nt) {   // along t2: n -> q
@@ -741,13 +830,10 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
       R v[n];
       load_line<R, n>(Wc(cl) + 12 * n2 + k * q * n + j1, q, v);
       R *out = Wc(cl) + 12 * n2 + 12 * q * n + k * q2 + j1;
+      R o[q];
+      interp_eo<R, n, q>(C, v, o);
 #pragma unroll
-      for (int i = 0; i < q; ++i) {
-        R acc = r_zero<R>();
-#pragma unroll
-        for (int b = 0; b < n; ++b) acc = r_fma(C.Sc[i * n + b], v[b], acc);
-        out[q * i] = acc;
-      }
+      for (int i = 0; i < q; ++i) out[q * i] = o[i];
     }
     __syncthreads();
     for (int t = tid; t < cpb * 2 * q2; t += nt) {   // local Lax-Friedrichs flux at the face points
@@ -778,14 +864,14 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
     for (int t = tid; t < cpb * 6 * q; t += nt) {   // back along t2: q -> n
       const int cl = t / (6 * q), r = t - cl * 6 * q, k = r / q, j1 = r - k * q;
       const R *Fl = Wc(cl) + 12 * n2 + 12 * q * n + 12 * q2 + k * q2;
-      R o[n];
+      R o[n], f[q];
 #pragma unroll
-      for (int b = 0; b < n; ++b) o[b] = r_zero<R>();
-#pragma unroll
-      for (int j = 0; j < q; ++j) {
-        const R f = Fl[j1 + q * j];
-#pragma unroll
-        for (int b = 0; b < n; ++b) o[b] = r_fma(C.Sc[j * n + b], f, o[b]);
+      for (int j = 0; j < q; ++j) f[j] = Fl[j1 + q * j];
+      {
+        constexpr int qh = q / 2 > 0 ? q / 2 : 1;
+        R fe[qh], fo[qh];
+        point_eo<R, q>(f, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, f[q / 2], o);
       }
       R *Bt = Wc(cl) + 12 * n2 + 12 * q * n + 18 * q2 + k * q * n;
       store_line<R, n>(Bt + j1, q, o);
@@ -795,14 +881,14 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
       const int cl = t / (6 * n), r = t - cl * 6 * n, k = r / n, i2 = r - k * n;
       const int s = k / 3, a = k % 3;
       const R *Bt = Wc(cl) + 12 * n2 + 12 * q * n + 18 * q2 + k * q * n + q * i2;
-      R o[n];
+      R o[n], f[q];
 #pragma unroll
-      for (int b = 0; b < n; ++b) o[b] = r_zero<R>();
-#pragma unroll
-      for (int j = 0; j < q; ++j) {
-        const R f = Bt[j];
-#pragma unroll
-        for (int b = 0; b < n; ++b) o[b] = r_fma(C.Sc[j * n + b], f, o[b]);
+      for (int j = 0; j < q; ++j) f[j] = Bt[j];
+      {
+        constexpr int qh = q / 2 > 0 ? q / 2 : 1;
+        R fe[qh], fo[qh];
+        point_eo<R, q>(f, fe, fo);
+        tinterp_s_eo<R, n, q, false>(C, fe, fo, f[q / 2], o);
       }
       R *ya = Y + (cl * 3 + a) * n3;
 #pragma unroll
@@ -868,6 +954,15 @@ cudaError_t box_vec_constants_init() {
       }
       V.wc[t] = B.w[QSET_CONV][t];
     }
+    for (int t = 0; t < qc / 2; ++t)
+      for (int j = 0; j < n / 2; ++j) {
+        const double s0 = B.S[QSET_CONV][t * n + j], s1 = B.S[QSET_CONV][t * n + n - 1 - j];
+        const double d0 = B.D[QSET_CONV][t * n + j], d1 = B.D[QSET_CONV][t * n + n - 1 - j];
+        V.SE[t * n + j] = 0.5 * (s0 + s1);
+        V.SO[t * n + j] = 0.5 * (s0 - s1);
+        V.DA[t * n + j] = 0.5 * (d0 - d1);
+        V.DB[t * n + j] = 0.5 * (d0 + d1);
+      }
   }
   auto split = [](double v) { const float h = (float)v; return df64{h, (float)(v - (double)h)}; };
   const double *src = reinterpret_cast<const double *>(h64);
