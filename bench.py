@@ -396,7 +396,7 @@ def run_gpu(args):
         kname = f"vector_op_kernel<double,{opname[dom]},GEO_CURVED>"
     else:
         kname = (f"{boxname[dom]}<double,double,{w.k}> (standard rows) + vector_op_kernel<double,{opname[dom]},GEO_BOX> "
-                 "(rows of and next to the enriched layers)")
+                 "(rows of the enriched layers)")
     roofline = {"kernel": kname, "bound": "alu", "achieved": per_op[dom]["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": per_op[dom]["fp64_frac"],
                 "traffic": args.traffic_bytes,
@@ -428,7 +428,7 @@ def run_gpu(args):
                     "fp32_flop_frac": nc * laplace_flops_per_cell(w.k, curved) / (lap32_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
 
     # the same step with every apply in double-float arithmetic on the FP32 units (DGW_DF64: double
-    # vectors, FP64-accurate; the rows of and next to the enriched layers stay in FP64), box cells
+    # vectors, FP64-accurate; the rows of the enriched layers stay in FP64), box cells
     df64_step = None
     if not curved:
         DF = dgw.DGW_DF64

@@ -62,12 +62,15 @@ static void fill_view(dgw_mesh *M, MeshView<T> &v) {
   v.hx = (T)(M->P.lx / M->P.nx);
   v.hz = (T)(M->P.lz / M->P.nz);
   v.visc = (T)M->P.nu;
-  // plain rows: no enrichment slot in the row or in the rows next to it (layers are whole rows)
+  // box-kernel rows: no enrichment slot in the row (layers are whole rows); the rows next to the
+  // layers are included when their y-faces take the standard point sets (no q_w^3 rule): the box
+  // kernels add the neighbour's enrichment on those faces
   const int nx = M->P.nx, ny = M->P.ny;
   int nb = 0, nt = 0;
   while (nb < ny && M->enr[(size_t)nx * nb] >= 0) ++nb;
   while (nt < ny - nb && M->enr[(size_t)nx * (ny - 1 - nt)] >= 0) ++nt;
-  int lo = nb == 0 ? 0 : nb + 1, hi = nt == 0 ? ny : ny - nt - 1;
+  const int pad = M->P.full_quadrature ? 1 : 0;
+  int lo = nb == 0 ? 0 : nb + pad, hi = nt == 0 ? ny : ny - nt - pad;
   if (M->P.geometry != 0 || lo >= hi) lo = hi = ny;
   v.plain_lo = lo;
   v.plain_hi = hi;

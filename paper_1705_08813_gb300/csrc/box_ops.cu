@@ -17,8 +17,10 @@
 // holds cpb consecutive cells of one row segment along x; each thread owns one line of one cell in
 // every pass (x-, y- then z-lines) and, in the face phase of direction d, the d-line through its
 // face node.
+#include <cmath>
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <type_traits>
 
 #include "df64.cuh"
@@ -42,10 +44,16 @@ struct VecConst {
   // Even-odd halves of Sc and Dc (the point set and the nodes are symmetric about 1/2, so
   // Sc[q-1-j][n-1-b] = Sc[j][b] and Dc[q-1-j][n-1-b] = -Dc[j][b]), rows j < q/2, columns b < n/2,
   // stride n: SE/SO = (Sc[j][b] +/- Sc[j][n-1-b]) / 2, DA/DB = (Dc[j][b] -/+ Dc[j][n-1-b]) / 2
-  R SE[QMAX * NMAX];
-  R SO[QMAX * NMAX];
-  R DA[QMAX * NMAX];
-  R DB[QMAX * NMAX];
+  R SE[(QMAX / 2) * NMAX];
+  R SO[(QMAX / 2) * NMAX];
+  R DA[(QMAX / 2) * NMAX];
+  R DB[(QMAX / 2) * NMAX];
+  // the enriched neighbour's trace on a y-face: positions of the k+1 Gauss points (xg) and of the
+  // convective points (xc) on [0, 1], and Sinv[b * n + t], the inverse of the k+1-point value table
+  // (nodal values whose interpolant takes given values at the Gauss points)
+  R xg[NMAX];
+  R xc[QMAX];
+  R Sinv[NMAX * NMAX];
 };
 __constant__ VecConst<double> c_vec64[5];
 __constant__ VecConst<float> c_vec32[5];
@@ -185,6 +193,63 @@ __device__ __forceinline__ void tinterp_d_eo(const VecConst<R> &C, const R (&fe)
   }
 }
 
+// Enrichment of a neighbour across a y-face, as seen from a standard cell of the rows next to the
+// enriched layers (Sec. 3, u~ = psi sum_B N_B u~_B on the neighbour). On the face the neighbour sits
+// at xi_y = 1 - s (s: the own face side), so only its four trilinear weights of that layer are
+// nonzero there, bilinear in the tangential positions x, z; with l = 0 the sum is the single
+// coefficient. e4 holds those four coefficients (x fastest), or the single one in e4[0].
+template <typename T, typename R>
+__device__ __forceinline__ void enr_face_coeffs(const MeshView<T> &m, const T *__restrict__ u, int eb, int s, int a,
+                                                R (&e4)[4]) {
+  const T *e = u + 3 * m.np + ((size_t)eb * 3 + a) * m.nef;
+  if (m.nef == 1) {
+    e4[0] = e4[1] = e4[2] = e4[3] = r_load<R>(e[0]);
+    return;
+  }
+  const int by = 2 * (1 - s);
+  e4[0] = r_load<R>(e[by]);
+  e4[1] = r_load<R>(e[by + 1]);
+  e4[2] = r_load<R>(e[by + 4]);
+  e4[3] = r_load<R>(e[by + 5]);
+}
+template <typename R>
+__device__ __forceinline__ R enr_face_sum(const R (&e4)[4], bool l0, R x, R z) {
+  if (l0) return e4[0];
+  const R one = r_from_double<R>(1.0);
+  const R x0 = one - x, z0 = one - z;
+  return r_fma(x * z, e4[3], r_fma(x0 * z, e4[2], r_fma(x * z0, e4[1], (x0 * z0) * e4[0])));
+}
+// Nodal values g at face node (i1, i2) (t1 = x, t2 = z) of components a0 .. a0 + NA - 1 whose
+// interpolant takes the neighbour eb's enrichment psi sum_v N_v e_av at the k+1 Gauss points of the
+// face (psi from the neighbour's wall table of that face). The node-space face integrals use
+// M = S^T W S, so integrating g reproduces the Gauss-point integral of the enrichment exactly.
+template <typename T, typename R, int n, int NA>
+__device__ __forceinline__ void enr_face_nodal(const VecConst<R> &C, const MeshView<T> &m, const T *__restrict__ u,
+                                               int eb, int s, int a0, int i1, int i2, R (&g)[NA]) {
+  const T *w = m.wt_face[0] + ((size_t)eb * 6 + 2 + (1 - s)) * m.fpmax[0] * WT;
+  const bool l0 = m.nef == 1;
+  R e4[NA][4];
+#pragma unroll
+  for (int c = 0; c < NA; ++c) {
+    enr_face_coeffs<T, R>(m, u, eb, s, a0 + c, e4[c]);
+    g[c] = r_zero<R>();
+  }
+#pragma unroll 1
+  for (int j2 = 0; j2 < n; ++j2) {
+    R row[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) row[c] = r_zero<R>();
+#pragma unroll
+    for (int j1 = 0; j1 < n; ++j1) {
+      const R sp = C.Sinv[i1 * n + j1] * r_load<R>(w[(j1 + n * j2) * WT]);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) row[c] = r_fma(sp, enr_face_sum<R>(e4[c], l0, C.xg[j1], C.xg[j2]), row[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NA; ++c) g[c] = r_fma(C.Sinv[i2 * n + j2], row[c], g[c]);
+  }
+}
+
 // line of a pass: x-lines (base n l, stride 1), y-lines (base lr + n^2 lq, stride n), z-lines
 // (base l, stride n^2)
 template <int n>
@@ -315,7 +380,14 @@ __global__ void __launch_bounds__(128) box_div_kernel(MeshView<T> m, const T *__
         if (nb >= 0) {
           R v[n];
           neighbour_line<T, R, n>(U, u, nb, bk, cpb, 3, d, base, st, v);
-          avg = r_half<R>() * (own + v[s ? 0 : n - 1]);
+          R other = v[s ? 0 : n - 1];
+          const int eb = d == 1 ? m.enr[nb] : -1;
+          if (eb >= 0) {   // the enriched neighbour's u~_y on the face
+            R g[1];
+            enr_face_nodal<T, R, n, 1>(C, m, u, eb, s, 1, i1, i2, g);
+            other = other + g[0];
+          }
+          avg = r_half<R>() * (own + other);
         }
         F[s * 2 * n2 + l] = (s ? area : -area) * avg;   // sgn(s) * (-|F|) * avg
       }
@@ -351,7 +423,7 @@ __global__ void __launch_bounds__(128) box_div_kernel(MeshView<T> m, const T *__
 //                             + sum_{b != a} 1/(h_a h_b) (A_b x B_a x M) u_b ].
 // ------------------------------------------------------------------------------------------------
 template <typename T, typename R, int K>
-__global__ void __launch_bounds__(128) box_visc_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y, int cpb,
+__global__ void __launch_bounds__(128, std::is_same<R, df64>::value ? 3 : 4) box_visc_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y, int cpb,
                                                        int j0, int nrows) {
   constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
   constexpr int WS = (4 * n3 > 36 * n2) ? 4 * n3 : 36 * n2;   // scratch per cell
@@ -545,6 +617,20 @@ __global__ void __launch_bounds__(128) box_visc_kernel(MeshView<T> m, const T *_
       for (int s = 0; s < 2; ++s) {
         FU[s * n2 + l] = Uo[s][d];
         FN[s * n2 + l] = Nb[s][d];
+      }
+      // an enriched neighbour across a y-face: its u~ enters the jumps (penalty and adjoint terms);
+      // the flux average keeps the polynomial gradients (FN above is the polynomial trace)
+      if (d == 1) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const int eb = nbs[s] >= 0 ? m.enr[nbs[s]] : -1;
+          if (eb >= 0) {
+            R g[3];
+            enr_face_nodal<T, R, n, 3>(C, m, u, eb, s, 0, i1, i2, g);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Nb[s][a] = Nb[s][a] + g[a];
+          }
+        }
       }
     }
     __syncthreads();
@@ -846,6 +932,17 @@ __global__ void __launch_bounds__(128) box_conv_kernel(MeshView<T> m, const T *_
         um[a] = Tr[((s * 2 + 0) * 3 + a) * q2 + pt];
         up[a] = wall ? -um[a] : Tr[((s * 2 + 1) * 3 + a) * q2 + pt];
       }
+      const int eb = (d == 1 && !wall) ? m.enr[neighbour(m, bk.c0 + cl, 2 + s)] : -1;
+      if (eb >= 0) {   // the enriched neighbour's u~ at the point (psi from its convective wall table)
+        const R psi = r_load<R>(m.wt_face[1][(((size_t)eb * 6 + 2 + (1 - s)) * m.fpmax[1] + pt) * WT]);
+        const R x = C.xc[pt % q], z = C.xc[pt / q];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          R e4[4];
+          enr_face_coeffs<T, R>(m, u, eb, s, a, e4);
+          up[a] = r_fma(psi, enr_face_sum<R>(e4, m.nef == 1, x, z), up[a]);
+        }
+      }
       const R umd = d == 0 ? um[0] : (d == 1 ? um[1] : um[2]);
       const R upd = d == 0 ? up[0] : (d == 1 ? up[1] : up[2]);
       const R unm = s ? umd : -umd, unp = s ? upd : -upd;
@@ -953,6 +1050,30 @@ cudaError_t box_vec_constants_init() {
         V.Dc[t * n + j] = B.D[QSET_CONV][t * n + j];
       }
       V.wc[t] = B.w[QSET_CONV][t];
+    }
+    for (int t = 0; t < qc; ++t) V.xc[t] = B.x[QSET_CONV][t];
+    if (q != n) return cudaErrorInvalidValue;   // the node-space face integrals assume k+1 points
+    for (int t = 0; t < n; ++t) V.xg[t] = B.x[QSET_LIN][t];
+    {
+      // Gauss-Jordan inverse of the n x n table S[t][b] = l_b(x_t), partial pivoting
+      double a[NMAX][2 * NMAX];
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) a[r][c] = c < n ? B.S[QSET_LIN][r * n + c] : (c - n == r ? 1.0 : 0.0);
+      for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+          if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+        for (int x = 0; x < 2 * n; ++x) std::swap(a[c][x], a[piv][x]);
+        const double inv = 1.0 / a[c][c];
+        for (int x = 0; x < 2 * n; ++x) a[c][x] *= inv;
+        for (int r = 0; r < n; ++r)
+          if (r != c) {
+            const double f = a[r][c];
+            for (int x = 0; x < 2 * n; ++x) a[r][x] -= f * a[c][x];
+          }
+      }
+      for (int b = 0; b < n; ++b)
+        for (int t = 0; t < n; ++t) V.Sinv[b * n + t] = a[b][n + t];
     }
     for (int t = 0; t < qc / 2; ++t)
       for (int j = 0; j < n / 2; ++j) {

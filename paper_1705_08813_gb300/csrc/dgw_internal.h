@@ -56,9 +56,10 @@ struct MeshView {
   int nef;            // enrichment coefficients per component and wall cell: 8 (l = 1) or 1 (l = 0)
   int full_q;         // 1: enriched cells use the q_wall set in every direction (faces: both tangential)
   int geo;            // GEO_BOX or GEO_CURVED
-  // rows [plain_lo, plain_hi) hold box cells whose six neighbours are standard cells (no enrichment
-  // slot in the row or the rows above and below): the degree-specialised kernels of box_ops.cu
-  // take them, the general kernel the other rows (plain_lo = plain_hi = ny: all general)
+  // rows [plain_lo, plain_hi) hold standard box cells (no enrichment slot in the row; with the q_w^3
+  // rule none in the rows above and below either): the degree-specialised kernels of box_ops.cu take
+  // them, adding an enriched y-neighbour's u~ on the faces between; the general kernel the other rows
+  // (plain_lo = plain_hi = ny: all general)
   int plain_lo = 0, plain_hi = 0;
   T hx, hz;
   const T *hy;        // [ny] row heights (boxes)

@@ -1119,8 +1119,8 @@ template <typename T>
 cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cudaStream_t s, const LapEpi<T> *epi) {
   note_dofs((op == OP_DIV || op == OP_LAP) ? m.np : m.nu);
   if (m.geo == GEO_BOX && (op == OP_DIV || op == OP_VISC || op == OP_CONV) && m.plain_hi > m.plain_lo) {
-    // rows of standard cells with standard neighbours: degree-specialised kernels; the rows of and
-    // next to the enriched layers: the general kernel
+    // rows of standard cells: degree-specialised kernels; the rows of the enriched layers (and, with
+    // the q_w^3 rule, the rows next to them): the general kernel
     cudaError_t e = launch_box_vec_rows<T, T>(op, m, u, y, m.plain_lo, m.plain_hi - m.plain_lo, s);
     if (e != cudaSuccess) return e;
     if (op == OP_DIV) return launch_vec<T, OP_DIV, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
