@@ -196,14 +196,50 @@ __device__ __forceinline__ void enr_trial(const T f[3][2], const T *e, bool l0, 
     sN = e[0];
     return;
   }
+  // nested linear interpolation, x then y then z (FP64 operations are the scarce resource of this
+  // kernel): the value, and each derivative as the difference along its axis interpolated along the
+  // other two; cx/dx per (b1, b2), j = b1 + 2 b2
+  T cx[4], dx[4];
 #pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    T Nv, dN[3];
-    q1_vertex(f, v, Nv, dN);
-    sN += Nv * e[v];
-    if (GRADN)
+  for (int j = 0; j < 4; ++j) {
+    const T e0 = e[2 * j], e1 = e[2 * j + 1];
+    cx[j] = f[0][0] * e0 + f[0][1] * e1;
+    dx[j] = e1 - e0;
+  }
+  T cy[2], dy[2], dxy[2];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) sD[d] += dN[d] * e[v];
+  for (int b2 = 0; b2 < 2; ++b2) {
+    cy[b2] = f[1][0] * cx[2 * b2] + f[1][1] * cx[2 * b2 + 1];
+    dy[b2] = cx[2 * b2 + 1] - cx[2 * b2];
+    dxy[b2] = f[1][0] * dx[2 * b2] + f[1][1] * dx[2 * b2 + 1];
+  }
+  sN = f[2][0] * cy[0] + f[2][1] * cy[1];
+  if (GRADN) {
+    sD[0] = f[2][0] * dxy[0] + f[2][1] * dxy[1];
+    sD[1] = f[2][0] * dy[0] + f[2][1] * dy[1];
+    sD[2] = cy[1] - cy[0];
+  }
+}
+
+// acc[a * 8 + v] += beta_a N_v + sum_e alpha_a[e] dN_v/dxi_e over the 8 trilinear weights at a point
+// with 1-D factors f. With N_v = F0 F1 F2 (F_e = f[e][b_e]) and dN_v/dxi_e = s_e (product of the
+// other two), s_e = +1 for b_e = 1 and -1 for b_e = 0, the term is
+// F1 F2 (beta F0 + s0 alpha_0) + F0 (s1 alpha_1 F2 + s2 alpha_2 F1).
+template <typename T>
+__device__ __forceinline__ void acc_trilinear(const T f[3][2], const T beta[3], const T alpha[3][3], T *acc) {
+  T F12[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) F12[j] = f[1][j & 1] * f[2][j >> 1];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T P0 = beta[a] * f[0][0] - alpha[a][0], P1 = beta[a] * f[0][1] + alpha[a][0];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b1 = j & 1, b2 = j >> 1;
+      const T Q = (b1 ? alpha[a][1] : -alpha[a][1]) * f[2][b2] + (b2 ? alpha[a][2] : -alpha[a][2]) * f[1][b1];
+      acc[a * 8 + 2 * j] += F12[j] * P0 + f[0][0] * Q;
+      acc[a * 8 + 2 * j + 1] += F12[j] * P1 + f[0][1] * Q;
+    }
   }
 }
 
@@ -542,25 +578,28 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
 #pragma unroll
             for (int d = 0; d < 3; ++d) cf[a][d] = nd * (Gt[(a * 3 + d) * P + t] + Gt[(d * 3 + a) * P + t]);
         }
+        // grad(psi N_v) = psi grad N_v + N_v grad psi: the coefficient of N_v is beta_a = cf_a . grad psi,
+        // that of dN_v/dxi_e is alpha_a[e] = psi (J^-1 cf_a)_e
+        T beta[3], alpha[3][3];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T Nv, dN[3];
-          enr_weight<T, NV>(f, v, Nv, dN);
-          T g[3];
-          if (NV == 1) {   // grad psi
+        for (int a = 0; a < 3; ++a) {
+          beta[a] = cf[a][0] * w[1] + cf[a][1] * w[2] + cf[a][2] * w[3];
+          if (NV == 8) {
+            if (CURVED) {
+              phys_to_ref(Ji, cf[a], alpha[a]);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) g[d] = w[1 + d];
-          } else if (CURVED) {
-            T gp[3];
-            ref_to_phys(Ji, dN, gp);
+              for (int e = 0; e < 3; ++e) alpha[a][e] *= w[0];
+            } else {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) g[d] = w[0] * gp[d] + Nv * w[1 + d];
-          } else {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) g[d] = w[0] * dN[d] * hinv[d] + Nv * w[1 + d];
+              for (int e = 0; e < 3; ++e) alpha[a][e] = w[0] * cf[a][e] * hinv[e];
+            }
           }
+        }
+        if (NV == 1) {
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[a * NV + v] += cf[a][0] * g[0] + cf[a][1] * g[1] + cf[a][2] * g[2];
+          for (int a = 0; a < 3; ++a) acc[a] += beta[a];
+        } else {
+          acc_trilinear<T>(f, beta, alpha, acc);
         }
       };
       reduce_enr<T>(l0, P, contrib, re, S0 + L.part);
@@ -682,6 +721,9 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
     }, GRAD ? 4 * NS : NS, p1, n, 1, 1, n, p2, false, false);
     // pointwise fluxes -> coefficients of the own test functions
     T *C = S0 + L.fC, *E = S0 + L.fE;
+    T hinv_nb1[2];   // the y-spacing of each neighbour, inverted once (walls: the own)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) hinv_nb1[s] = (!CURVED && nbr[s] >= 0) ? T(1) / cell_h(m, nbr[s], 1) : hinv[1];
     for (int t = threadIdx.x; t < 2 * FP; t += blockDim.x) {
       const int s = t / FP, pt = t - s * FP;
       if (ngrp == 2 && s != grp) {   // the other face is done in its own pass
@@ -712,11 +754,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
       T *Cs = C + s * 3 * 4 * L.FP, *Es = E + s * 3 * 4 * L.FP;
       if constexpr (!CURVED) {
         const T dA = h[t1] * h[t2] * B.w[s1][a1] * B.w[s2][a2];
-        const T hdo = nb >= 0 ? cell_h(m, nb, d) : h[d];
         T ub_s[3] = {0, 0, 0}, ub_o[3] = {0, 0, 0}, ut_s[3] = {0, 0, 0}, ut_o[3] = {0, 0, 0};
         T gbs[3][3], gbo[3][3], gts[3][3], gto[3][3];
-        const T hob1 = nb >= 0 ? cell_h(m, nb, 1) : h[1];
-        const T hob[3] = {m.hx, hob1, m.hz};
+        // the neighbour's inverse spacings (x and z spacings are uniform)
+        const T hio[3] = {hinv[0], hinv_nb1[s], hinv[2]};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (OP == OP_DIV && a != d) continue;   // the divergence needs the normal component only
@@ -744,10 +785,9 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           if (nb >= 0) {
             ub_o[a] = tr_o[pt];
             if (GRAD) {
-              const T ht1 = t1 == 1 ? hob1 : h[t1], ht2 = t2 == 1 ? hob1 : h[t2];
-              gbo[a][d] = tr_o[L.FP + pt] / hdo;
-              gbo[a][t1] = tr_o[2 * L.FP + pt] / ht1;
-              gbo[a][t2] = tr_o[3 * L.FP + pt] / ht2;
+              gbo[a][d] = tr_o[L.FP + pt] * hio[d];
+              gbo[a][t1] = tr_o[2 * L.FP + pt] * hio[t1];
+              gbo[a][t2] = tr_o[3 * L.FP + pt] * hio[t2];
             }
             if (wto) {
               const T *w = wto + pt * WT;
@@ -756,7 +796,7 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
               ut_o[a] = w[0] * sN;
               if (GRAD)
 #pragma unroll
-                for (int e = 0; e < 3; ++e) gto[a][e] = w[0] * sD[e] / hob[e] + sN * w[1 + e];
+                for (int e = 0; e < 3; ++e) gto[a][e] = w[0] * sD[e] * hio[e] + sN * w[1 + e];
             } else if (GRAD) {
               gto[a][0] = gto[a][1] = gto[a][2] = T(0);
             }
@@ -798,8 +838,9 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           T wt_s = T(0.5);
           if (both) {
             const T den = T(2) * nu + nut_s + nut_o;
-            wt_s = (nu + nut_o) / den;
-            const T wt_o = (nu + nut_s) / den;
+            const T iden = T(1) / den;
+            wt_s = (nu + nut_o) * iden;
+            const T wt_o = (nu + nut_s) * iden;
             for (int a = 0; a < 3; ++a)
               avgt_n[a] = sgn * (wt_s * (nu + nut_s) * (gts[a][d] + gts[d][a]) + wt_o * (nu + nut_o) * (gto[a][d] + gto[d][a]));
           }
@@ -832,7 +873,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         load_rec(face_rec(m, B, col, d, s, s1, s2, a1, a2), Js, dets);
         if (nb >= 0) load_rec(face_rec(m, B, metric_col(m, nb), d, 1 - s, s1, s2, a1, a2), Jo, deto);
         const T nrm = sqrt(Js[d][0] * Js[d][0] + Js[d][1] * Js[d][1] + Js[d][2] * Js[d][2]);
-        const T nv[3] = {sgn * Js[d][0] / nrm, sgn * Js[d][1] / nrm, sgn * Js[d][2] / nrm};
+        const T snrm = sgn / nrm;
+        const T nv[3] = {snrm * Js[d][0], snrm * Js[d][1], snrm * Js[d][2]};
         const T dA = fabs(dets) * nrm * B.w[s1][a1] * B.w[s2][a2];
         T vJ[3];   // J^-1 n: the normal derivative is grad_xi . (J^-1 n)
         phys_to_ref(Js, nv, vJ);
@@ -940,8 +982,9 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
           T wt_s = T(0.5);
           if (both) {
             const T den = T(2) * nu + nut_s + nut_o;
-            wt_s = (nu + nut_o) / den;
-            const T wt_o = (nu + nut_s) / den;
+            const T iden = T(1) / den;
+            wt_s = (nu + nut_o) * iden;
+            const T wt_o = (nu + nut_s) * iden;
             for (int a = 0; a < 3; ++a) {
               T sn = T(0);
               for (int e = 0; e < 3; ++e)
@@ -997,30 +1040,33 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
 #pragma unroll
           for (int b = 0; b < 3; ++b) cg[a][b] = OP == OP_VISC ? Es[(a * 4 + 1 + b) * L.FP + pt] : T(0);
         }
+        // value test psi N_v: beta_a = cv_a (+ cg_a . grad psi); gradient test grad(psi N_v):
+        // alpha_a[e] = psi (J^-1 cg_a)_e
+        T beta[3], alpha[3][3];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T Nv, dN[3];
-          enr_weight<T, NV>(f, v, Nv, dN);
+        for (int a = 0; a < 3; ++a) {
+          beta[a] = cv[a];
+#pragma unroll
+          for (int e = 0; e < 3; ++e) alpha[a][e] = T(0);
           if (OP == OP_VISC) {
-            T g[3];
-            if (NV == 1) {   // grad psi
+            beta[a] += cg[a][0] * w[1] + cg[a][1] * w[2] + cg[a][2] * w[3];
+            if (NV == 8) {
+              if (CURVED) {
+                phys_to_ref(Js, cg[a], alpha[a]);
 #pragma unroll
-              for (int b = 0; b < 3; ++b) g[b] = w[1 + b];
-            } else if (CURVED) {
-              T gp[3];
-              ref_to_phys(Js, dN, gp);
+                for (int e = 0; e < 3; ++e) alpha[a][e] *= w[0];
+              } else {
 #pragma unroll
-              for (int b = 0; b < 3; ++b) g[b] = w[0] * gp[b] + Nv * w[1 + b];
-            } else {
-#pragma unroll
-              for (int b = 0; b < 3; ++b) g[b] = w[0] * dN[b] * hinv[b] + Nv * w[1 + b];
+                for (int e = 0; e < 3; ++e) alpha[a][e] = w[0] * cg[a][e] * hinv[e];
+              }
             }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) acc[a * NV + v] += cv[a] * Nv + cg[a][0] * g[0] + cg[a][1] * g[1] + cg[a][2] * g[2];
-          } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) acc[a * NV + v] += cv[a] * Nv;
           }
+        }
+        if (NV == 1) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) acc[a] += beta[a];
+        } else {
+          acc_trilinear<T>(f, beta, alpha, acc);
         }
       };
       reduce_enr<T>(l0, 2 * FP, contrib, re, S0 + L.part);
