@@ -222,28 +222,30 @@ def laplace_flops_per_cell(k, curved=False):
 def vector_flops_per_cell(op, k):
     """Floating-point operations (2 per multiply-add) of one standard box cell of the divergence,
     convective and viscous operators, n = k + 1 nodes, counted for the algorithms the box kernels
-    use. The divergence and the viscous term have polynomial integrands that the k+1 Gauss points
+    use. Every 1-D product of a volume pass uses the even-odd form: with P(a, b) the flops of one
+    product from a inputs to b outputs (sums and differences of mirrored inputs, half-size products
+    per mirrored pair of outputs, the middle row); a product scaled into an accumulator adds 2 b.
+    The divergence and the viscous term have polynomial integrands that the k+1 Gauss points
     integrate exactly, so they are Kronecker products of 1-D n x n matrices on the nodes:
-      divergence  8 n^4 (volume) + 12 n^3 (faces: averages, two face-grid passes)
-      viscous     36 n^4 (volume: 12 line passes per output component)
-                  + 174 n^3 (faces: normal and tangential derivatives, two face-grid passes of
+      divergence  n^2 (8 P(n, n) + 6 n) (volume: 8 line products, 3 of them scaled)
+                  + 2 * 12 n^3 (faces: averages, two face-grid passes)
+      viscous     3 n^2 (12 P(n, n) + 6 n) (volume: 12 line products per output component)
+                  + 2 * 174 n^3 (faces: normal and tangential derivatives, two face-grid passes of
                   eight coefficient arrays, normal-derivative test terms) + 180 n^2 (coefficients)
-    The convective term is evaluated at q = floor(3k/2)+1 Gauss points (Sec. 4.4). Its 1-D products
-    (n nodes -> q points and back) use the even-odd form: with P(a, b) the flops of one product from a
-    inputs to b outputs (sums and differences of mirrored inputs, half-size products per mirrored pair
-    of outputs, the middle row),
+    The convective term is evaluated at q = floor(3k/2)+1 Gauss points (Sec. 4.4), its products
+    (n nodes -> q points and back) in the same even-odd form:
       values (n^2 + q n + q^2) P(n, q) per component, integration (3 q^2 + 3 q n + 2 n^2) P(q, n)
       + (q n + n^2) n per output component, 9 q^3 for the products, and per face direction
       12 (n + q) P(n, q) (traces of both sides), 40 q^2 (flux), 6 (q + n) P(q, n) (integration back)."""
     n = k + 1
-    if op == "divergence":
-        return 2 * (8 * n ** 4 + 12 * n ** 3)
-    if op == "viscous":
-        return 2 * (36 * n ** 4 + 174 * n ** 3) + 180 * n * n
-    q = (3 * k) // 2 + 1
 
     def P(a, b):
         return 2 * (a // 2) + (b // 2) * (4 * (a // 2) + a % 2 + 2) + (b % 2) * (2 * (a // 2) + a % 2)
+    if op == "divergence":
+        return n * n * (8 * P(n, n) + 6 * n) + 2 * 12 * n ** 3
+    if op == "viscous":
+        return 3 * n * n * (12 * P(n, n) + 6 * n) + 2 * 174 * n ** 3 + 180 * n * n
+    q = (3 * k) // 2 + 1
     fwd, bwd = P(n, q), P(q, n)
     vol = 3 * (n * n + q * n + q * q) * fwd + 3 * ((3 * q * q + 3 * q * n + 2 * n * n) * bwd + (q * n + n * n) * n)
     faces = 3 * (12 * (n + q) * fwd + 6 * (q + n) * bwd)

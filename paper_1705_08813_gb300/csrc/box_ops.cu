@@ -54,7 +54,16 @@ struct VecConst {
   R xg[NMAX];
   R xc[QMAX];
   R Sinv[NMAX * NMAX];
+  // even-odd halves of the n x n node matrices, rows r < n/2, columns b < n/2, stride n:
+  // X_E/X_O = (X[r][b] +/- X[r][n-1-b]) / 2 for X = M, K (centro-symmetric), A and A^T
+  // (centro-antisymmetric: X[n-1-r][n-1-b] = -X[r][b])
+  R ME[(NMAX / 2) * NMAX], MO[(NMAX / 2) * NMAX];
+  R KE[(NMAX / 2) * NMAX], KO[(NMAX / 2) * NMAX];
+  R AE[(NMAX / 2) * NMAX], AO[(NMAX / 2) * NMAX];
+  R TE[(NMAX / 2) * NMAX], TO[(NMAX / 2) * NMAX];
 };
+// the three tables share the 64 KB constant bank of this translation unit
+static_assert(5 * (2 * sizeof(VecConst<double>) + sizeof(VecConst<float>)) <= 62 * 1024, "constant tables too large");
 __constant__ VecConst<double> c_vec64[5];
 __constant__ VecConst<float> c_vec32[5];
 __constant__ VecConst<df64> c_vecdf[5];
@@ -88,6 +97,64 @@ __device__ __forceinline__ void matvec(const R *Mat, const R (&in)[n], R (&out)[
     out[r] = s;
   }
 }
+// Even-odd form of out (=|+= c *) X in for an n x n node matrix X with X[n-1-r][n-1-b] = SIG X[r][b]
+// (E, O its halves, F the full matrix, read transposed when TR, for the middle row and column):
+// out[r] = e_r + o_r and out[n-1-r] = SIG (e_r - o_r) from products with the sums and differences of
+// mirrored inputs; the middle row (odd n) takes the sums (SIG = 1) or the differences (SIG = -1).
+template <typename R, int n, int SIG, bool TR, bool ACC>
+__device__ __forceinline__ void matvec_eo(const R *E, const R *O, const R *F, R c, const R (&v)[n], R (&out)[n]) {
+  constexpr int nh = n / 2;
+  R ve[nh > 0 ? nh : 1], vo[nh > 0 ? nh : 1];
+#pragma unroll
+  for (int b = 0; b < nh; ++b) { ve[b] = v[b] + v[n - 1 - b]; vo[b] = v[b] - v[n - 1 - b]; }
+#pragma unroll
+  for (int r = 0; r < nh; ++r) {
+    R e = (n & 1) ? (TR ? F[nh * n + r] : F[r * n + nh]) * v[nh] : r_zero<R>(), o = r_zero<R>();
+#pragma unroll
+    for (int b = 0; b < nh; ++b) {
+      e = r_fma(E[r * n + b], ve[b], e);
+      o = r_fma(O[r * n + b], vo[b], o);
+    }
+    const R lo = e + o, hi = SIG > 0 ? e - o : o - e;
+    out[r] = ACC ? r_fma(c, lo, out[r]) : lo;
+    out[n - 1 - r] = ACC ? r_fma(c, hi, out[n - 1 - r]) : hi;
+  }
+  if constexpr ((n & 1) != 0) {
+    R m = SIG > 0 ? F[nh * n + nh] * v[nh] : r_zero<R>();
+#pragma unroll
+    for (int b = 0; b < nh; ++b) m = r_fma(TR ? F[b * n + nh] : F[nh * n + b], SIG > 0 ? ve[b] : vo[b], m);
+    out[nh] = ACC ? r_fma(c, m, out[nh]) : m;
+  }
+}
+template <typename R, int n>
+__device__ __forceinline__ void mv_M(const VecConst<R> &C, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, 1, false, false>(C.ME, C.MO, C.M, r_zero<R>(), v, o);
+}
+template <typename R, int n>
+__device__ __forceinline__ void mv_K(const VecConst<R> &C, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, 1, false, false>(C.KE, C.KO, C.K, r_zero<R>(), v, o);
+}
+template <typename R, int n>
+__device__ __forceinline__ void mv_A(const VecConst<R> &C, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, -1, false, false>(C.AE, C.AO, C.A, r_zero<R>(), v, o);
+}
+template <typename R, int n>
+__device__ __forceinline__ void mv_AT(const VecConst<R> &C, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, -1, true, false>(C.TE, C.TO, C.A, r_zero<R>(), v, o);
+}
+template <typename R, int n>
+__device__ __forceinline__ void mva_M(const VecConst<R> &C, R c, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, 1, false, true>(C.ME, C.MO, C.M, c, v, o);
+}
+template <typename R, int n>
+__device__ __forceinline__ void mva_K(const VecConst<R> &C, R c, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, 1, false, true>(C.KE, C.KO, C.K, c, v, o);
+}
+template <typename R, int n>
+__device__ __forceinline__ void mva_A(const VecConst<R> &C, R c, const R (&v)[n], R (&o)[n]) {
+  matvec_eo<R, n, -1, false, true>(C.AE, C.AO, C.A, c, v, o);
+}
+
 // out += c * Mat in
 template <typename R, int n, bool TR = false>
 __device__ __forceinline__ void matvec_acc(const R *Mat, R c, const R (&in)[n], R (&out)[n]) {
@@ -322,13 +389,13 @@ __global__ void __launch_bounds__(128) box_div_kernel(MeshView<T> m, const T *__
     line_geom<n>(0, l, base, st);
     R v[n], o[n];
     load_line<R, n>(Uc + base, st, v);
-    matvec<R, n>(C.A, v, o);
+    mv_A<R, n>(C, v, o);
     store_line<R, n>(Sc + base, st, o);
     load_line<R, n>(Uc + n3 + base, st, v);
-    matvec<R, n>(C.M, v, o);
+    mv_M<R, n>(C, v, o);
     store_line<R, n>(Sc + n3 + base, st, o);
     load_line<R, n>(Uc + 2 * n3 + base, st, v);
-    matvec<R, n>(C.M, v, o);
+    mv_M<R, n>(C, v, o);
     store_line<R, n>(Sc + 2 * n3 + base, st, o);
   }
   __syncthreads();
@@ -342,9 +409,9 @@ __global__ void __launch_bounds__(128) box_div_kernel(MeshView<T> m, const T *__
     load_line<R, n>(Sc + 2 * n3 + base, st, p2);
 #pragma unroll
     for (int r = 0; r < n; ++r) w[r] = r_zero<R>();
-    matvec_acc<R, n>(C.M, sx, p0, w);
-    matvec_acc<R, n>(C.A, sy, p1, w);
-    matvec<R, n>(C.M, p2, t);
+    mva_M<R, n>(C, sx, p0, w);
+    mva_A<R, n>(C, sy, p1, w);
+    mv_M<R, n>(C, p2, t);
     store_line<R, n>(Sc + base, st, w);
     store_line<R, n>(Sc + n3 + base, st, t);
   }
@@ -356,8 +423,8 @@ __global__ void __launch_bounds__(128) box_div_kernel(MeshView<T> m, const T *__
     R w[n], t[n], o[n];
     load_line<R, n>(Sc + base, st, w);
     load_line<R, n>(Sc + n3 + base, st, t);
-    matvec<R, n>(C.M, w, o);
-    matvec_acc<R, n>(C.A, sz, t, o);
+    mv_M<R, n>(C, w, o);
+    mva_A<R, n>(C, sz, t, o);
     store_line<R, n>(Yc + base, st, o);
   }
   __syncthreads();
@@ -492,18 +559,18 @@ __global__ void __launch_bounds__(128, std::is_same<R, df64>::value ? 3 : 4) box
     // 1-D factor of cross term (a <- b) along direction e: A where e = b, B (= A^T) where e = a,
     // M otherwise
     auto xfac = [&](int b, int e, const R (&in)[n], R (&out)[n]) {
-      if (e == b) matvec<R, n>(C.A, in, out);
-      else if (e == a) matvec<R, n, true>(C.A, in, out);
-      else matvec<R, n>(C.M, in, out);
+      if (e == b) mv_A<R, n>(C, in, out);
+      else if (e == a) mv_AT<R, n>(C, in, out);
+      else mv_M<R, n>(C, in, out);
     };
     if (line) {   // x: S0 = K_x u_a, S1 = M_x u_a, S2 = X_x u_b1, S3 = X_x u_b2
       int base, st;
       line_geom<n>(0, l, base, st);
       R v[n], o[n];
       load_line<R, n>(Uc + a * n3 + base, st, v);
-      matvec<R, n>(C.K, v, o);
+      mv_K<R, n>(C, v, o);
       store_line<R, n>(Sc + base, st, o);
-      matvec<R, n>(C.M, v, o);
+      mv_M<R, n>(C, v, o);
       store_line<R, n>(Sc + n3 + base, st, o);
       load_line<R, n>(Uc + b1 * n3 + base, st, v);
       xfac(b1, 0, v, o);
@@ -523,9 +590,9 @@ __global__ void __launch_bounds__(128, std::is_same<R, df64>::value ? 3 : 4) box
       load_line<R, n>(Sc + 3 * n3 + base, st, s3);
 #pragma unroll
       for (int r = 0; r < n; ++r) w[r] = r_zero<R>();
-      matvec_acc<R, n>(C.M, cd0, s0, w);
-      matvec_acc<R, n>(C.K, cd1, s1, w);
-      matvec<R, n>(C.M, s1, t);
+      mva_M<R, n>(C, cd0, s0, w);
+      mva_K<R, n>(C, cd1, s1, w);
+      mv_M<R, n>(C, s1, t);
       xfac(b1, 1, s2, x1);
       xfac(b2, 1, s3, x2);
       // fold the cross terms whose z-factor is M into W (scaled), keep the others apart
@@ -553,10 +620,10 @@ __global__ void __launch_bounds__(128, std::is_same<R, df64>::value ? 3 : 4) box
       load_line<R, n>(Sc + base, st, w);
       load_line<R, n>(Sc + n3 + base, st, t);
       load_line<R, n>(Sc + 2 * n3 + base, st, x);
-      matvec<R, n>(C.M, w, o);
-      matvec_acc<R, n>(C.K, cd2, t, o);
-      if (a == 2) matvec<R, n, true>(C.A, x, o2);
-      else matvec<R, n>(C.A, x, o2);
+      mv_M<R, n>(C, w, o);
+      mva_K<R, n>(C, cd2, t, o);
+      if (a == 2) mv_AT<R, n>(C, x, o2);
+      else mv_A<R, n>(C, x, o2);
 #pragma unroll
       for (int r = 0; r < n; ++r) o[r] = o[r] + o2[r];
       store_line<R, n>(Yc + a * n3 + base, st, o);
@@ -1075,6 +1142,19 @@ cudaError_t box_vec_constants_init() {
       for (int b = 0; b < n; ++b)
         for (int t = 0; t < n; ++t) V.Sinv[b * n + t] = a[b][n + t];
     }
+    for (int r = 0; r < n / 2; ++r)
+      for (int b = 0; b < n / 2; ++b) {
+        const int i = r * n + b, j = r * n + n - 1 - b;
+        V.ME[i] = 0.5 * (V.M[i] + V.M[j]);
+        V.MO[i] = 0.5 * (V.M[i] - V.M[j]);
+        V.KE[i] = 0.5 * (V.K[i] + V.K[j]);
+        V.KO[i] = 0.5 * (V.K[i] - V.K[j]);
+        V.AE[i] = 0.5 * (V.A[i] + V.A[j]);
+        V.AO[i] = 0.5 * (V.A[i] - V.A[j]);
+        const double t0 = V.A[b * n + r], t1 = V.A[(n - 1 - b) * n + r];   // A^T[r][b], A^T[r][n-1-b]
+        V.TE[i] = 0.5 * (t0 + t1);
+        V.TO[i] = 0.5 * (t0 - t1);
+      }
     for (int t = 0; t < qc / 2; ++t)
       for (int j = 0; j < n / 2; ++j) {
         const double s0 = B.S[QSET_CONV][t * n + j], s1 = B.S[QSET_CONV][t * n + n - 1 - j];
