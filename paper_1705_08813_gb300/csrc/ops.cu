@@ -185,63 +185,6 @@ __device__ __forceinline__ void reduce_enr(bool l0, int npts, F contrib, T *out,
   else reduce24<T>(npts, [&](int p, T *acc) { contrib(p, acc, std::integral_constant<int, 8>{}); }, out, part);
 }
 
-// Enrichment of one component at a point with 1-D weight factors f: sN = sum_v N_v e_v and
-// sD_d = sum_v dN_v/dxi_d e_v over the 8 trilinear weights (e: 8 coefficients); with the constant
-// weight (l = 0) sN = e_0 and sD = 0.
-template <typename T, bool GRADN>
-__device__ __forceinline__ void enr_trial(const T f[3][2], const T *e, bool l0, T &sN, T sD[3]) {
-  sN = T(0);
-  sD[0] = sD[1] = sD[2] = T(0);
-  if (l0) {
-    sN = e[0];
-    return;
-  }
-  // nested linear interpolation, x then y then z (FP64 operations are the scarce resource of this
-  // kernel): the value, and each derivative as the difference along its axis interpolated along the
-  // other two; cx/dx per (b1, b2), j = b1 + 2 b2
-  T cx[4], dx[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const T e0 = e[2 * j], e1 = e[2 * j + 1];
-    cx[j] = f[0][0] * e0 + f[0][1] * e1;
-    dx[j] = e1 - e0;
-  }
-  T cy[2], dy[2], dxy[2];
-#pragma unroll
-  for (int b2 = 0; b2 < 2; ++b2) {
-    cy[b2] = f[1][0] * cx[2 * b2] + f[1][1] * cx[2 * b2 + 1];
-    dy[b2] = cx[2 * b2 + 1] - cx[2 * b2];
-    dxy[b2] = f[1][0] * dx[2 * b2] + f[1][1] * dx[2 * b2 + 1];
-  }
-  sN = f[2][0] * cy[0] + f[2][1] * cy[1];
-  if (GRADN) {
-    sD[0] = f[2][0] * dxy[0] + f[2][1] * dxy[1];
-    sD[1] = f[2][0] * dy[0] + f[2][1] * dy[1];
-    sD[2] = cy[1] - cy[0];
-  }
-}
-
-// acc[a * 8 + v] += beta_a N_v + sum_e alpha_a[e] dN_v/dxi_e over the 8 trilinear weights at a point
-// with 1-D factors f. With N_v = F0 F1 F2 (F_e = f[e][b_e]) and dN_v/dxi_e = s_e (product of the
-// other two), s_e = +1 for b_e = 1 and -1 for b_e = 0, the term is
-// F1 F2 (beta F0 + s0 alpha_0) + F0 (s1 alpha_1 F2 + s2 alpha_2 F1).
-template <typename T>
-__device__ __forceinline__ void acc_trilinear(const T f[3][2], const T beta[3], const T alpha[3][3], T *acc) {
-  T F12[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) F12[j] = f[1][j & 1] * f[2][j >> 1];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const T P0 = beta[a] * f[0][0] - alpha[a][0], P1 = beta[a] * f[0][1] + alpha[a][0];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b1 = j & 1, b2 = j >> 1;
-      const T Q = (b1 ? alpha[a][1] : -alpha[a][1]) * f[2][b2] + (b2 ? alpha[a][2] : -alpha[a][2]) * f[1][b1];
-      acc[a * 8 + 2 * j] += F12[j] * P0 + f[0][0] * Q;
-      acc[a * 8 + 2 * j + 1] += F12[j] * P1 + f[0][1] * Q;
-    }
-  }
-}
 
 // Value and reference gradient of the enrichment weight v of NV at the point (l = 0: 1 and 0).
 template <typename T, int NV>

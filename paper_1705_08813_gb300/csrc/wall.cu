@@ -200,17 +200,16 @@ __global__ void eddy_viscosity_kernel(WallCellData w, const Basis<double> *Bg, i
   for (int t = threadIdx.x; t < 24; t += blockDim.x) cu[t] = u_enr[(size_t)e * 3 * nef + (nef == 8 ? t : t >> 3)];
   __syncthreads();
   auto nut_at = [&](const double xi[3], const double Ji[3][3], const double *wt, const double *aux) -> double {
-    double N[8], dN[8][3];
-    q1_weights(xi, N, dN);
-    double gN[8][3];
-    for (int v = 0; v < 8; ++v) ref_to_phys(Ji, dN[v], gN[v]);
+    // grad(psi sum_v N_v e_av) = psi J^-T (sum_v grad_xi N_v e_av) + (sum_v N_v e_av) grad psi, the sums
+    // by nested linear interpolation
+    const double f[3][2] = {{1.0 - xi[0], xi[0]}, {1.0 - xi[1], xi[1]}, {1.0 - xi[2], xi[2]}};
     double G[3][3];
-    for (int a = 0; a < 3; ++a)
-      for (int d = 0; d < 3; ++d) {
-        double s = 0.0;
-        for (int v = 0; v < 8; ++v) s += cu[a * 8 + v] * (wt[0] * gN[v][d] + N[v] * wt[1 + d]);
-        G[a][d] = s;
-      }
+    for (int a = 0; a < 3; ++a) {
+      double sN, sD[3], gp[3];
+      enr_trial<double, true>(f, cu + a * 8, nef == 1, sN, sD);
+      ref_to_phys(Ji, sD, gp);
+      for (int d = 0; d < 3; ++d) G[a][d] = wt[0] * gp[d] + sN * wt[1 + d];
+    }
     double e2 = 0.0;
     for (int a = 0; a < 3; ++a)
       for (int d = 0; d < 3; ++d) {
@@ -335,13 +334,12 @@ __global__ void wall_shear_face_kernel(MeshView<double> m, const double *__restr
     // enrichment: grad(psi N_v) = psi grad N_v + N_v grad psi, psi and grad psi from the wall table
     if (e >= 0) {
       const double *wt = wt_face + (((size_t)e * 6 + 2 + side) * fpmax + t) * WT;
-      double N[8], dN[8][3];
-      q1_weights(xi, N, dN);
-      for (int v = 0; v < 8; ++v) {
-        double gN[3];
-        ref_to_phys(Ji, dN[v], gN);
-        for (int a = 0; a < 3; ++a)
-          for (int d = 0; d < 3; ++d) G[a][d] += ce[a * 8 + v] * (wt[0] * gN[d] + N[v] * wt[1 + d]);
+      const double f[3][2] = {{1.0 - xi[0], xi[0]}, {1.0 - xi[1], xi[1]}, {1.0 - xi[2], xi[2]}};
+      for (int a = 0; a < 3; ++a) {
+        double sN, sD[3], gp[3];
+        enr_trial<double, true>(f, ce + a * 8, m.nef == 1, sN, sD);
+        ref_to_phys(Ji, sD, gp);
+        for (int d = 0; d < 3; ++d) G[a][d] += wt[0] * gp[d] + sN * wt[1 + d];
       }
     }
     // outward unit normal and area weight of the face xi_1 = side (Nanson)
