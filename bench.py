@@ -219,7 +219,7 @@ def laplace_flops_per_cell(k, curved=False):
     return 2 * (7 * n ** 4 + 30 * n ** 3)
 
 
-def vector_flops_per_cell(op, k):
+def vector_flops_per_cell(op, k, curved=False):
     """Floating-point operations (2 per multiply-add) of one standard box cell of the divergence,
     convective and viscous operators, n = k + 1 nodes, counted for the algorithms the box kernels
     use. Every 1-D product of a volume pass uses the even-odd form: with P(a, b) the flops of one
@@ -232,6 +232,8 @@ def vector_flops_per_cell(op, k):
       viscous     3 n^2 (12 P(n, n) + 6 n) (volume: 12 line products per output component)
                   + 2 * 174 n^3 (faces: normal and tangential derivatives, two face-grid passes of
                   eight coefficient arrays, normal-derivative test terms) + 180 n^2 (coefficients)
+    Curved cells (the general kernel) take plain 1-D products, P(a, b) = 2 a b: the counts above with
+    that P and 2 n^3 per scaled line product, the metric terms not counted.
     The convective term is evaluated at q = floor(3k/2)+1 Gauss points (Sec. 4.4), its products
     (n nodes -> q points and back) in the same even-odd form:
       values (n^2 + q n + q^2) P(n, q) per component, integration (3 q^2 + 3 q n + 2 n^2) P(q, n)
@@ -240,14 +242,18 @@ def vector_flops_per_cell(op, k):
     n = k + 1
 
     def P(a, b):
+        if curved:
+            return 2 * a * b
         return 2 * (a // 2) + (b // 2) * (4 * (a // 2) + a % 2 + 2) + (b % 2) * (2 * (a // 2) + a % 2)
+    sc = 0 if curved else 6 * n   # the scaling multiply-add of a scaled product (inside P when plain)
     if op == "divergence":
-        return n * n * (8 * P(n, n) + 6 * n) + 2 * 12 * n ** 3
+        return n * n * (8 * P(n, n) + sc) + 2 * 12 * n ** 3
     if op == "viscous":
-        return 3 * n * n * (12 * P(n, n) + 6 * n) + 2 * 174 * n ** 3 + 180 * n * n
+        return 3 * n * n * (12 * P(n, n) + sc) + 2 * 174 * n ** 3 + 180 * n * n
     q = (3 * k) // 2 + 1
     fwd, bwd = P(n, q), P(q, n)
-    vol = 3 * (n * n + q * n + q * q) * fwd + 3 * ((3 * q * q + 3 * q * n + 2 * n * n) * bwd + (q * n + n * n) * n)
+    acc = 0 if curved else (q * n + n * n) * n   # adds of the accumulated even-odd products
+    vol = 3 * (n * n + q * n + q * q) * fwd + 3 * ((3 * q * q + 3 * q * n + 2 * n * n) * bwd + acc)
     faces = 3 * (12 * (n + q) * fwd + 6 * (q + n) * bwd)
     return vol + faces + 9 * q ** 3 + 3 * 40 * q * q
 
@@ -380,7 +386,7 @@ def run_gpu(args):
     per_op = {o: {"ms": statistics.mean(op_ms[o])} for o in ops}
     for o, d in dofs_ops.items():
         per_op[o]["gdofs"] = d / (per_op[o]["ms"] * 1e-3) / 1e9
-        fl = laplace_flops_per_cell(w.k, curved) if o == "laplace" else vector_flops_per_cell(o, w.k)
+        fl = laplace_flops_per_cell(w.k, curved) if o == "laplace" else vector_flops_per_cell(o, w.k, curved)
         per_op[o]["flops_per_cell"] = fl
         per_op[o]["fp64_tflops"] = nc * fl / (per_op[o]["ms"] * 1e-3) / 1e12
         per_op[o]["fp64_frac"] = per_op[o]["fp64_tflops"] / FP64_PEAK_TFLOPS
