@@ -270,8 +270,9 @@ dgw_status dgw_pressure_solve_batch(dgw_mesh_t mesh, int ncols, const double *co
  * between calls, which would leave the kept address stale. Every call shares the one array and
  * clears what must start at zero; calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller. The solve reads the residual norm
- * back every iteration, so it synchronises `stream` once per iteration. info->ms is host wall
- * time. */
+ * back every iteration, so it synchronises `stream` once per iteration and cannot be recorded into a
+ * CUDA graph: a stream that is being captured is refused with DGW_EINVAL before any work. info->ms is
+ * host wall time. */
 dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t mesh, const double *b, double *p, double rtol, int max_iter,
                                              dgw_solve_info *info, void *stream);
 

@@ -111,6 +111,17 @@ extern "C" dgw_status dgw_pressure_solve_jacobi_noalloc(dgw_mesh_t M, const doub
                                      " exceeds the fixed scratch limit of " + std::to_string(kNoAllocMaxNp) +
                                      " pressure DoFs; use dgw_pressure_solve");
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    // every iteration reads the residual back and synchronises s, which a stream capture forbids:
+    // refuse a capturing stream (or a capture elsewhere that makes s unusable) before any work
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      if (ce != cudaSuccess) (void)cudaGetLastError();
+      return set_error(DGW_EINVAL, "dgw_pressure_solve_jacobi_noalloc: the stream is being captured; this solve "
+                                   "synchronises its stream every iteration and cannot be captured");
+    }
+  }
   double *base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_jacobi_noalloc: scratch address");

@@ -1,9 +1,10 @@
-"""Degree-specialised box kernels (standard cells whose neighbours are standard cells) against the
-oracle, element by element: the divergence, the viscous and the convective operator in FP64, in
-double-float (DGW_DF64) and in FP32, on meshes whose rows exercise every path of those kernels and of the
-general kernel beside them: interior rows between one or two enriched layers, the wall rows of
-meshes without enrichment (mirror state, x10 wall penalty), a single cell periodic onto itself in x,
-odd and even cell counts along x (1 to 8 cells per CTA), degrees 1 to 5."""
+"""Degree-specialised box kernels (standard cells; on the rows next to a wall layer they add the enriched
+neighbour's u~ on the faces between) against the oracle, element by element: the divergence, the viscous
+and the convective operator in FP64, in double-float (DGW_DF64) and in FP32, on meshes whose rows exercise
+every path of those kernels and of the general kernel beside them: interior rows between one or two
+enriched layers, a row whose two y-neighbours are both enriched, enrichment with l = 1 and l = 0, the wall
+rows of meshes without enrichment (mirror state, x10 wall penalty), a single cell periodic onto itself in
+x, odd and even cell counts along x (1 to 8 cells per CTA), degrees 1 to 5."""
 import numpy as np
 import pytest
 
@@ -44,14 +45,20 @@ CASES = [
     (1, 4, 1, 2, 0),
     (3, 5, 2, 4, 0),
     (8, 10, 2, 4, 2),
+    (4, 3, 2, 3, 1),   # the middle row: enriched neighbours above and below
 ]
 
 
-@pytest.mark.parametrize("nx,ny,nz,k,layers", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}_q{c[3]}_l{c[4]}" for c in CASES])
-def test_box_kernels_match_oracle(dgw, nx, ny, nz, k, layers):
+L0_CASES = [(6, 7, 3, 2, 1), (4, 6, 3, 4, 2), (4, 3, 2, 3, 1)]
+
+
+@pytest.mark.parametrize("nx,ny,nz,k,layers,el", [c + (1,) for c in CASES] + [c + (0,) for c in L0_CASES],
+                         ids=[f"{c[0]}x{c[1]}x{c[2]}_q{c[3]}_layers{c[4]}" for c in CASES]
+                         + [f"{c[0]}x{c[1]}x{c[2]}_q{c[3]}_layers{c[4]}_l0" for c in L0_CASES])
+def test_box_kernels_match_oracle(dgw, nx, ny, nz, k, layers, el):
     w = I.Workload("box", nx, ny, nz, k, 590.0, 1.0 / 12000.0, seed=40 + k)
-    om = O.Mesh(**w.mesh_kwargs(), n_layers=layers)
-    gm = dgw.mesh_for(w, n_layers=layers)
+    om = O.Mesh(**w.mesh_kwargs(), n_layers=layers, enrich_l=el)
+    gm = dgw.mesh_for(w, n_layers=layers, enrich_l=el)
     assert (gm.n_p, gm.n_u) == (om.n_p, om.n_u)
     dev = torch.device("cuda:0")
     u = I.uniform(w.seed, gm.n_u, -1.0, 1.0, stream=5)

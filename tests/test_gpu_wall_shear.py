@@ -269,8 +269,8 @@ def test_switch_off_everywhere_equals_mesh_without_enrichment(dgw):
         y0 = torch.empty(g0.n_u, dtype=torch.float64, device=dev)
         getattr(gm, op)(u, y)
         getattr(g0, op)(u[:np3].contiguous(), y0)
-        # the rows next to the (switched-off) wall layers take the general kernel on gm and the
-        # degree-specialised one on g0: equal to rounding; the enrichment slots are exactly zero
+        # the (switched-off) wall-layer rows take the general kernel on gm and the degree-specialised
+        # one on g0: equal to rounding; the enrichment slots are exactly zero
         diff = (y[:np3] - y0).abs().max().item()
         assert diff <= 1e-13 * y0.abs().max().item() and not torch.any(y[np3:] != 0), (op, diff)
     gm.set_enrichment_switch(0.0)

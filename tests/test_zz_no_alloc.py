@@ -68,3 +68,25 @@ def test_noalloc_rejects_meshes_beyond_its_scratch(dgw):
     p = torch.zeros_like(b)
     st, _ = _noalloc(dgw, big, b, p, 1e-10, 10)
     assert st == -1 and b"exceeds" in dgw._lib.dgw_last_error()
+
+
+def test_noalloc_refuses_a_capturing_stream(dgw):
+    """The solve synchronises its stream every iteration, which a stream capture forbids: called on a
+    stream that is being captured it returns DGW_EINVAL before any work, and the capture stays valid."""
+    mesh = dgw.mesh_for(I.WORKLOADS["channel_q2_8x8x8"])
+    b = torch.zeros(mesh.n_p, dtype=torch.float64, device="cuda")
+    p = torch.zeros_like(b)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        try:
+            p.add_(1.0)                     # one captured kernel, so the graph is not empty
+            st, _ = _noalloc(dgw, mesh, b, p, 1e-10, 10)
+        finally:
+            graph.capture_end()
+    assert st == -1 and b"captured" in dgw._lib.dgw_last_error()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(p[0]) == 1.0
