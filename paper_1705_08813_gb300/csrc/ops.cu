@@ -414,8 +414,10 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         } else if (OP == OP_DIV) {
           for (int d = 0; d < 3; ++d) G[d * P + t] = dV * uu[d] * hinv[d];
         } else {
+          T sd[3];   // -dV u_d / h_d, shared by the three outputs
+          for (int d = 0; d < 3; ++d) sd[d] = -dV * uu[d] * hinv[d];
           for (int a = 0; a < 3; ++a)
-            for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = -dV * uu[a] * uu[d] * hinv[d];
+            for (int d = 0; d < 3; ++d) G[(a * 3 + d) * P + t] = uu[a] * sd[d];
         }
       } else if (OP == OP_LAP) {
         const T gr[3] = {G[t], G[P + t], G[2 * P + t]};
@@ -503,12 +505,29 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         if (CURVED) vol_metric(i0, i1, i2, Ji, dV);
         else dV = vol * B.w[sets[0]][i0] * B.w[sets[1]][i1] * B.w[sets[2]][i2];
         T cf[3][3];   // coefficient of d(psi N_v)/dx_d in output (a, v)
+        T beta[3], alpha[3][3];
         if (OP == OP_CONV) {
+          // cf_ad = -dV u_a u_d has rank one: beta_a = u_a (-dV u . grad psi), alpha_a = u_a (-dV psi J^-1 u)
           const T uu[3] = {V[t], V[P + t], V[2 * P + t]};
+          const T bs = -dV * (uu[0] * w[1] + uu[1] * w[2] + uu[2] * w[3]);
+          T av[3] = {T(0), T(0), T(0)};
+          if (NV == 8) {
+            const T pw = -dV * w[0];
+            if (CURVED) {
+              phys_to_ref(Ji, uu, av);
 #pragma unroll
-          for (int a = 0; a < 3; ++a)
+              for (int e = 0; e < 3; ++e) av[e] *= pw;
+            } else {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) cf[a][d] = -dV * uu[a] * uu[d];
+              for (int e = 0; e < 3; ++e) av[e] = pw * uu[e] * hinv[e];
+            }
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            beta[a] = uu[a] * bs;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) alpha[a][e] = uu[a] * av[e];
+          }
         } else if (OP == OP_DIVDIV) {
 #pragma unroll
           for (int a = 0; a < 3; ++a)
@@ -523,9 +542,8 @@ __global__ void __launch_bounds__(128) vector_op_kernel(MeshView<T> m, const T *
         }
         // grad(psi N_v) = psi grad N_v + N_v grad psi: the coefficient of N_v is beta_a = cf_a . grad psi,
         // that of dN_v/dxi_e is alpha_a[e] = psi (J^-1 cf_a)_e
-        T beta[3], alpha[3][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3 && OP != OP_CONV; ++a) {
           beta[a] = cf[a][0] * w[1] + cf[a][1] * w[2] + cf[a][2] * w[3];
           if (NV == 8) {
             if (CURVED) {
