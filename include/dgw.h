@@ -365,7 +365,7 @@ dgw_status dgw_ns_copy_state(dgw_ns_t ns, double *u_dev, double *p_dev, void *st
 
 /* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32): number of
  * levels, the estimated largest eigenvalue of D^-1 A per level (the Chebyshev smoother works on
- * [1.2 lmax / 15, 1.2 lmax]) and the cell count per level, finest first; at most max_levels
+ * [1.1 lmax / 45, 1.1 lmax]) and the cell count per level, finest first; at most max_levels
  * entries are written. Synchronises the library's solver stream. */
 dgw_status dgw_solver_describe(dgw_mesh_t mesh, int mode, int *n_levels, double *lmax, int *cells, int max_levels,
                                void *stream);

@@ -20,7 +20,8 @@
 
 namespace dgw {
 
-constexpr double kSmoothRange = 15.0;   // Chebyshev smooths [1.2 lmax/15, 1.2 lmax]
+constexpr double kSmoothRange = 45.0;   // Chebyshev smooths [1.1 lmax/45, 1.1 lmax]
+constexpr double kLmaxSafety = 1.1;     // on the CG-Lanczos estimate, which approaches lmax from below
 constexpr int kCoarseIters = 24;       // PCG steps on the coarsest level
 constexpr int kLanczos = 24;           // CG-Lanczos steps for lmax(D^-1 A)
 constexpr double kSemiRatio = 0.5;      // y-only coarsening while 2 min h_y <= this x min(h_x, h_z)
@@ -555,7 +556,7 @@ static cudaError_t level_apply(const Lvl<T> *L, const T *x, T *y, cudaStream_t s
 
 // Largest eigenvalue of D^-1 A from the Lanczos tridiagonal of kLanczos Jacobi-PCG steps on a
 // random zero-mean right-hand side (setup only; host-synchronising). The Ritz value approaches
-// lmax from below; the smoother applies a 1.2 safety factor.
+// lmax from below; the smoother applies the safety factor kLmaxSafety.
 static double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &b) {
   // Sturm-sequence bisection for the largest eigenvalue of the symmetric tridiagonal (a, b)
   const int m = (int)a.size();
@@ -897,7 +898,7 @@ static cudaError_t build_hierarchy(dgw_mesh *M, Hierarchy<T> *H, const MeshView<
 // the current one); the result ends in L->x.
 template <typename T>
 static void chebyshev(const Hierarchy<T> *H, Lvl<T> *L, bool zero_init, cudaStream_t s) {
-  const double lmax = 1.2 * L->lmax, lmin = lmax / kSmoothRange;
+  const double lmax = kLmaxSafety * L->lmax, lmin = lmax / kSmoothRange;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
   const int G = mg_grid(L->n), nc = H->ncols;
