@@ -74,6 +74,10 @@ static void fill_view(dgw_mesh *M, MeshView<T> &v) {
   if (M->P.geometry != 0 || lo >= hi) lo = hi = ny;
   v.plain_lo = lo;
   v.plain_hi = hi;
+  int slo = nb, shi = ny - nt;
+  if (M->P.geometry != 0 || slo >= shi) slo = shi = ny;
+  v.std_lo = slo;
+  v.std_hi = shi;
 }
 
 }  // namespace dgw

@@ -781,6 +781,107 @@ __global__ void __launch_bounds__(128, std::is_same<R, df64>::value ? 3 : 4) box
 }
 
 // ------------------------------------------------------------------------------------------------
+// Volume-only operators of standard cells, exact with the k+1 Gauss points, as Kronecker products of
+// 1-D node matrices (no face terms, so every row without enrichment slots qualifies):
+//   OP_MASS   y_a = V (M x M x M) u_a                                        (Sec. 4.2 mass term)
+//   OP_DIVDIV y_a = tau_D V sum_b 1/(h_a h_b) F_ab u_b                        (eq. div-div)
+// with F_aa = K along a and M along the other two, and for b != a: A along a (the test function
+// differentiated), A^T along b (the trial function differentiated), M along the third.
+// ------------------------------------------------------------------------------------------------
+template <typename R, int n>
+__device__ __forceinline__ void divdiv_factor(const VecConst<R> &C, int a, int b, int e, const R (&in)[n], R (&out)[n]) {
+  if (a == b) {
+    if (e == a) mv_K<R, n>(C, in, out);
+    else mv_M<R, n>(C, in, out);
+  } else if (e == a) {
+    mv_A<R, n>(C, in, out);
+  } else if (e == b) {
+    mv_AT<R, n>(C, in, out);
+  } else {
+    mv_M<R, n>(C, in, out);
+  }
+}
+
+template <typename T, typename R, int K, int OP>
+__global__ void __launch_bounds__(128) box_vol_kernel(MeshView<T> m, const T *__restrict__ u, T *__restrict__ y, int cpb,
+                                                      int j0, int nrows) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *U = reinterpret_cast<R *>(smem_raw);   // cpb x 3 x n3
+  R *Y = U + cpb * 3 * n3;                   // cpb x 3 x n3
+  R *S = Y + cpb * 3 * n3;                   // cpb x 3 x n3 scratch
+  __shared__ R sc[9];                        // V (mass) or V / (h_a h_b) (div-div), [3 a + b]
+  const VecConst<R> &C = vconst<R>(K);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const BoxBlock bk = box_block(m, cpb, j0, nrows);
+  for (int t = tid; t < cpb * 3 * n3; t += nt) U[t] = r_load<R>(u[(size_t)bk.c0 * 3 * n3 + t]);
+  if (tid < 9) {
+    const double hd[3] = {(double)m.hx, (double)m.hy[bk.j], (double)m.hz};
+    const double V = hd[0] * hd[1] * hd[2];
+    sc[tid] = r_from_double<R>(OP == OP_MASS ? V : V / (hd[tid / 3] * hd[tid % 3]));
+  }
+  __syncthreads();
+  const bool line = tid < cpb * n2;
+  const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
+  R *Uc = U + cl * 3 * n3, *Yc = Y + cl * 3 * n3, *Sc = S + cl * 3 * n3;
+  if constexpr (OP == OP_MASS) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {   // x, y, z passes over the three components
+      if (line) {
+        int base, st;
+        line_geom<n>(d, l, base, st);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          R v[n], o[n];
+          load_line<R, n>((d == 0 ? Uc : Sc) + a * n3 + base, st, v);
+          mv_M<R, n>(C, v, o);
+          if (d == 2) {
+#pragma unroll
+            for (int r = 0; r < n; ++r) o[r] = sc[0] * o[r];
+          }
+          store_line<R, n>((d == 2 ? Yc : Sc) + a * n3 + base, st, o);
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {   // one output component per sweep; S[b] holds F_ab u_b pass by pass
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (line) {
+          int base, st;
+          line_geom<n>(d, l, base, st);
+          R acc[n];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            R v[n], o[n];
+            load_line<R, n>((d == 0 ? Uc : Sc) + b * n3 + base, st, v);
+            divdiv_factor<R, n>(C, a, b, d, v, o);
+            if (d < 2) {
+              store_line<R, n>(Sc + b * n3 + base, st, o);
+            } else {
+#pragma unroll
+              for (int r = 0; r < n; ++r) acc[r] = b == 0 ? sc[3 * a] * o[r] : r_fma(sc[3 * a + b], o[r], acc[r]);
+            }
+          }
+          if (d == 2) store_line<R, n>(Yc + a * n3 + base, st, acc);
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if constexpr (OP == OP_MASS) {
+    for (int t = tid; t < cpb * 3 * n3; t += nt) y[(size_t)bk.c0 * 3 * n3 + t] = r_store<T>(Y[t]);
+  } else {
+    for (int t = tid; t < cpb * 3 * n3; t += nt) {
+      const int c = bk.c0 + t / (3 * n3);
+      y[(size_t)bk.c0 * 3 * n3 + t] = r_store<T>(r_load<R>(m.tau_d[c]) * Y[t]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Convective term F^c(v, u) of standard cells (Sec. 4.2): -(grad v, u x u)_K + (v, F*.n)_dK with the
 // local Lax-Friedrichs flux F* = 1/2 (u^- (u^-.n) + u^+ (u^+.n)) + Lambda/2 (u^- - u^+),
 // Lambda = max(2|u^-.n|, 2|u^+.n|), u^+ = -u^- on walls. The integrand is not a polynomial of the
@@ -1201,10 +1302,16 @@ static cudaError_t launch_box_op_k(const MeshView<T> &m, const T *u, T *y, int j
   } else {
     cpb = vec_cpb(m.nx, n2);
     threads = ((cpb * n2 + 31) / 32) * 32;
-    per_cell = OP == OP_DIV ? 7 * n3 : 6 * n3 + ((4 * n3 > 36 * n2) ? 4 * n3 : 36 * n2);
+    per_cell = OP == OP_DIV ? 7 * n3
+                            : (OP == OP_VISC ? 6 * n3 + ((4 * n3 > 36 * n2) ? 4 * n3 : 36 * n2) : 9 * n3);
   }
   const size_t sm = sizeof(R) * per_cell * cpb;
-  auto kern = OP == OP_DIV ? box_div_kernel<T, R, K> : (OP == OP_VISC ? box_visc_kernel<T, R, K> : box_conv_kernel<T, R, K>);
+  auto kern = [] {
+    if constexpr (OP == OP_DIV) return box_div_kernel<T, R, K>;
+    else if constexpr (OP == OP_VISC) return box_visc_kernel<T, R, K>;
+    else if constexpr (OP == OP_CONV) return box_conv_kernel<T, R, K>;
+    else return box_vol_kernel<T, R, K, OP>;
+  }();
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1247,6 +1354,26 @@ cudaError_t launch_box_vec_rows(int op, const MeshView<T> &m, const T *u, T *y, 
       case 4: return launch_box_op_k<T, R, 3, OP_CONV>(m, u, y, j0, nrows, s);
       case 5: return launch_box_op_k<T, R, 4, OP_CONV>(m, u, y, j0, nrows, s);
       case 6: return launch_box_op_k<T, R, 5, OP_CONV>(m, u, y, j0, nrows, s);
+    }
+  } else if (op == OP_MASS || op == OP_DIVDIV) {
+    if constexpr (!std::is_same<R, df64>::value) {   // native precisions only
+      if (op == OP_MASS) {
+        switch (m.n1) {
+          case 2: return launch_box_op_k<T, R, 1, OP_MASS>(m, u, y, j0, nrows, s);
+          case 3: return launch_box_op_k<T, R, 2, OP_MASS>(m, u, y, j0, nrows, s);
+          case 4: return launch_box_op_k<T, R, 3, OP_MASS>(m, u, y, j0, nrows, s);
+          case 5: return launch_box_op_k<T, R, 4, OP_MASS>(m, u, y, j0, nrows, s);
+          case 6: return launch_box_op_k<T, R, 5, OP_MASS>(m, u, y, j0, nrows, s);
+        }
+      } else {
+        switch (m.n1) {
+          case 2: return launch_box_op_k<T, R, 1, OP_DIVDIV>(m, u, y, j0, nrows, s);
+          case 3: return launch_box_op_k<T, R, 2, OP_DIVDIV>(m, u, y, j0, nrows, s);
+          case 4: return launch_box_op_k<T, R, 3, OP_DIVDIV>(m, u, y, j0, nrows, s);
+          case 5: return launch_box_op_k<T, R, 4, OP_DIVDIV>(m, u, y, j0, nrows, s);
+          case 6: return launch_box_op_k<T, R, 5, OP_DIVDIV>(m, u, y, j0, nrows, s);
+        }
+      }
     }
   }
   return cudaErrorInvalidValue;

@@ -61,6 +61,9 @@ struct MeshView {
   // them, adding an enriched y-neighbour's u~ on the faces between; the general kernel the other rows
   // (plain_lo = plain_hi = ny: all general)
   int plain_lo = 0, plain_hi = 0;
+  // rows [std_lo, std_hi) hold no enrichment slot: the volume-only operators (mass, div-div) take
+  // them with box kernels whatever the neighbours (std_lo = std_hi = ny: all general)
+  int std_lo = 0, std_hi = 0;
   T hx, hz;
   const T *hy;        // [ny] row heights (boxes)
   const T *tau;       // [nc] penalty tau_IP per cell

@@ -1134,6 +1134,14 @@ cudaError_t launch_vector_op(int op, const MeshView<T> &m, const T *u, T *y, cud
     if (op == OP_CONV) return launch_vec<T, OP_CONV, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
     return launch_vec<T, OP_VISC, GEO_BOX>(m, u, y, s, nullptr, m.plain_lo, m.plain_hi);
   }
+  if (m.geo == GEO_BOX && (op == OP_MASS || op == OP_DIVDIV) && m.std_hi > m.std_lo) {
+    // volume-only operators: box kernels on every row without enrichment slots, the general kernel
+    // on the wall layers
+    cudaError_t e = launch_box_vec_rows<T, T>(op, m, u, y, m.std_lo, m.std_hi - m.std_lo, s);
+    if (e != cudaSuccess) return e;
+    if (op == OP_MASS) return launch_vec<T, OP_MASS, GEO_BOX>(m, u, y, s, nullptr, m.std_lo, m.std_hi);
+    return launch_vec<T, OP_DIVDIV, GEO_BOX>(m, u, y, s, nullptr, m.std_lo, m.std_hi);
+  }
   if (m.geo == GEO_CURVED) {
     switch (op) {
       case OP_DIV: return launch_vec<T, OP_DIV, GEO_CURVED>(m, u, y, s, nullptr);
