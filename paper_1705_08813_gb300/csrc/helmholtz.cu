@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -36,6 +37,7 @@ struct dgw_helm {
   double *detw = nullptr;          // [nc][(k+1)^3] |det J| w at the Gauss points
   double *meeinv = nullptr;        // [ne][8][8] inverse enriched mass blocks
   double *m1inv = nullptr;         // [n][n] S_1^-1, inverse of the 1-D node-to-Gauss-point interpolation
+  double minv1[dgw::NMAX * dgw::NMAX] = {};  // host copy of the inverse 1-D mass matrix (S_1^T W S_1)^-1
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
@@ -146,12 +148,19 @@ __device__ void mss_inverse(const double *in, double *out, const double *Si, con
 
 // z = (gamma M_blocks)^-1 r, one CTA per cell: Mss^-1 per component, and the nef x nef enriched
 // block inverse of each component in wall cells.
+// One CTA per cell of rows [0, rb) and [rt, ny) (rb = rt = ny: every row), x fastest.
 __global__ void inverse_mass_kernel(const double *__restrict__ r, double *__restrict__ z, const double *__restrict__ sinv,
                                     const double *__restrict__ detw, const int *__restrict__ enr,
                                     const int *__restrict__ slot, const double *__restrict__ meeinv, int n, int nef,
-                                    long np, double inv_gamma) {
+                                    long np, double inv_gamma, int nx, int ny, int rb, int rt) {
   __shared__ double A[NMAX * NMAX * NMAX], Bs[NMAX * NMAX * NMAX], Si[NMAX * NMAX];
-  const int c = blockIdx.x, n3 = n * n * n;
+  int c;
+  {
+    const int nr = rb + (ny - rt), b = blockIdx.x;
+    const int i = b % nx, rr = (b / nx) % nr, kz = b / (nx * nr);
+    c = i + nx * ((rr < rb ? rr : rt + (rr - rb)) + ny * kz);
+  }
+  const int n3 = n * n * n;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) Si[t] = sinv[t];
   __syncthreads();
   for (int a = 0; a < 3; ++a)
@@ -168,6 +177,97 @@ __global__ void inverse_mass_kernel(const double *__restrict__ r, double *__rest
   double acc = 0.0;
   for (int w = 0; w < nef; ++w) acc += meeinv[(size_t)e * 64 + v * nef + w] * rin[w];
   z[3 * np + ((size_t)e * 3 + a) * nef + v] = inv_gamma * acc;
+}
+
+// The inverse 1-D mass matrix as a kernel parameter (read from the constant parameter bank).
+struct Minv1 {
+  double m[NMAX * NMAX];
+};
+
+// z = scale M_c^-1 r on standard box cells: the cell mass matrix is V (M_1 x M_1 x M_1), so its inverse is
+// (M_1^-1 x M_1^-1 x M_1^-1) / V, three line passes instead of the six of S^-1 W^-1 S^-T. cpb cells of
+// one row per CTA (rows [j0, j0 + nrows)), one line of one cell per thread, passes in place.
+template <int K>
+__global__ void __launch_bounds__(128) inverse_mass_box_kernel(const double *__restrict__ r, double *__restrict__ z, Minv1 Mi,
+                                                               int nx, int ny, const double *__restrict__ hy, double hx,
+                                                               double hz, int cpb, int j0, int nrows, double scale) {
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  extern __shared__ __align__(16) double X[];   // cpb x 3 x n3
+  const int segs = nx / cpb, b = blockIdx.x;
+  const int i0 = (b % segs) * cpb, j = j0 + (b / segs) % nrows, kz = b / (segs * nrows);
+  const size_t o = ((size_t)i0 + (size_t)nx * (j + (size_t)ny * kz)) * 3 * n3;
+  for (int t = threadIdx.x; t < cpb * 3 * n3; t += blockDim.x) X[t] = r[o + t];
+  __syncthreads();
+  const double sv = scale / (hx * hy[j] * hz);
+  const int tid = threadIdx.x;
+  const bool line = tid < cpb * n2;
+  const int cl = line ? tid / n2 : 0, l = line ? tid - cl * n2 : 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (line) {
+      const int base = d == 0 ? n * l : (d == 1 ? (l % n) + n2 * (l / n) : l);
+      const int st = d == 0 ? 1 : (d == 1 ? n : n2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double *xl = X + (cl * 3 + a) * n3 + base;
+        double v[n];
+#pragma unroll
+        for (int q = 0; q < n; ++q) v[q] = xl[q * st];
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+          double acc = 0.0;
+#pragma unroll
+          for (int p = 0; p < n; ++p) acc = fma(Mi.m[q * n + p], v[p], acc);
+          xl[q * st] = d == 2 ? sv * acc : acc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < cpb * 3 * n3; t += blockDim.x) z[o + t] = X[t];
+}
+
+template <int K>
+cudaError_t launch_imass_box_k(dgw_mesh *M, const Minv1 &Mi, const double *r, double *z, double scale, cudaStream_t s) {
+  const MeshView<double> &m = M->v64;
+  constexpr int n = K + 1, n2 = n * n, n3 = n2 * n;
+  int cpb = 1;
+  while (cpb * 2 <= 8 && cpb * 2 * n2 <= 128 && m.nx % (cpb * 2) == 0) cpb *= 2;
+  const int nrows = m.std_hi - m.std_lo, threads = ((cpb * n2 + 31) / 32) * 32;
+  note_launch();
+  inverse_mass_box_kernel<K><<<(m.nx / cpb) * nrows * m.nz, threads, (size_t)cpb * 3 * n3 * sizeof(double), s>>>(
+      r, z, Mi, m.nx, m.ny, m.hy, m.hx, m.hz, cpb, m.std_lo, nrows, scale);
+  return cudaGetLastError();
+}
+
+// z = scale M^-1 r in every cell without switched-on enrichment (exact there) and the block-diagonal
+// approximation in cells with the wall model on: the box kernel on the channel rows without
+// enrichment slots, the general kernel on the other rows (all of them on curved meshes)
+cudaError_t launch_inverse_mass(dgw_mesh *M, const double *r, double *z, double scale, cudaStream_t s) {
+  const dgw_helm *H = M->helm;
+  const MeshView<double> &m = M->v64;
+  int rb = m.ny, rt = m.ny;
+  if (m.geo == GEO_BOX && m.std_hi > m.std_lo) {
+    Minv1 Mi;
+    std::memcpy(Mi.m, H->minv1, sizeof(Mi.m));
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (M->n1) {
+      case 2: e = launch_imass_box_k<1>(M, Mi, r, z, scale, s); break;
+      case 3: e = launch_imass_box_k<2>(M, Mi, r, z, scale, s); break;
+      case 4: e = launch_imass_box_k<3>(M, Mi, r, z, scale, s); break;
+      case 5: e = launch_imass_box_k<4>(M, Mi, r, z, scale, s); break;
+      case 6: e = launch_imass_box_k<5>(M, Mi, r, z, scale, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    rb = m.std_lo;
+    rt = m.std_hi;
+  }
+  const int nr = rb + (m.ny - rt);
+  if (nr <= 0) return cudaSuccess;
+  note_launch();
+  inverse_mass_kernel<<<m.nx * nr * m.nz, 128, 0, s>>>(r, z, H->m1inv, H->detw, m.enr, m.slot, H->meeinv, M->n1, M->nef,
+                                                       M->np, scale, m.nx, m.ny, rb, rt);
+  return cudaGetLastError();
 }
 
 // detw[c][q] = |det J| w_q at the Gauss points: boxes vol_c w0 w1 w2, curved cells from the metric
@@ -300,6 +400,13 @@ static cudaError_t helm_setup(dgw_mesh *M, int restart) {
       for (int j = 0; j < n; ++j) inv[(size_t)i * n + j] = a[(size_t)i * 2 * n + n + j];
     e = cudaMemcpyAsync(H->m1inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // (S_1^T W S_1)^-1 = S_1^-1 W^-1 S_1^-T for the box cells' inverse mass
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int q = 0; q < n; ++q) acc += inv[(size_t)i * n + q] * inv[(size_t)j * n + q] / M->basis64.w[QSET_LIN][q];
+        H->minv1[i * n + j] = acc;
+      }
   }
   // cell volumes: M e_x summed over each cell's component-x outputs
   const long np = M->np;
@@ -426,10 +533,8 @@ dgw_status helmholtz_solve(dgw_mesh *M, double gamma, const double *rhs, double 
     int j = 0;
     for (; j < m && it < o->max_iter; ++j) {
       double *Vj = H->V + (size_t)j * nu, *Zj = H->Z + (size_t)j * nu, *Vn = H->V + (size_t)(j + 1) * nu;
-      note_launch();
-      inverse_mass_kernel<<<M->nc, 128, 0, s>>>(Vj, Zj, H->m1inv, H->detw, M->v64.enr, M->v64.slot, H->meeinv, M->n1,
-                                                M->nef, M->np, 1.0 / gamma);
-      e = helm_apply(M, gamma, Zj, H->w, H->t, s);
+      e = launch_inverse_mass(M, Vj, Zj, 1.0 / gamma, s);
+      if (e == cudaSuccess) e = helm_apply(M, gamma, Zj, H->w, H->t, s);
       if (e != cudaSuccess) return cuda_check(e, "dgw_helmholtz_solve: operator");
       // classical Gram-Schmidt, twice
       std::vector<double> hcol(j + 2, 0.0);
@@ -500,11 +605,7 @@ namespace dgw {
 cudaError_t launch_collocation_inverse_mass(dgw_mesh *M, const double *r, double *x, cudaStream_t s) {
   cudaError_t e = helm_setup(M, M->helm ? M->helm->m : 1);
   if (e != cudaSuccess) return e;
-  dgw_helm *H = M->helm;
-  note_launch();
-  inverse_mass_kernel<<<M->nc, 128, 0, s>>>(r, x, H->m1inv, H->detw, M->v64.enr, M->v64.slot, H->meeinv, M->n1, M->nef,
-                                            M->np, 1.0);
-  return cudaGetLastError();
+  return launch_inverse_mass(M, r, x, 1.0, s);
 }
 }  // namespace dgw
 
