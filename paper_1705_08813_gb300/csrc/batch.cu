@@ -524,7 +524,6 @@ extern "C" dgw_status dgw_pressure_solve_batch(dgw_mesh_t M, int ncols, const do
   }
   Batch *B = M->batch;
   const unsigned long long dof0 = dof_counter();
-  const auto t0 = std::chrono::steady_clock::now();
   int next = 0, left = ncols;
   std::vector<BatchColumn> done;
   while (left > 0) {
@@ -537,12 +536,18 @@ extern "C" dgw_status dgw_pressure_solve_batch(dgw_mesh_t M, int ncols, const do
       c.rtol = opts->rtol;
       c.max_iter = opts->max_iter;
       const cudaError_t e = batch_admit(B, c, (cudaStream_t)stream);
-      if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_batch: admission");
+      if (e != cudaSuccess) {
+        dgw_batch_free(M);   // the block holds this call's columns: the next call starts from a new one
+        return cuda_check(e, "dgw_pressure_solve_batch: admission");
+      }
       ++next;
     }
     done.clear();
     const cudaError_t e = batch_round(B, done);
-    if (e != cudaSuccess) return cuda_check(e, "dgw_pressure_solve_batch");
+    if (e != cudaSuccess) {
+      dgw_batch_free(M);
+      return cuda_check(e, "dgw_pressure_solve_batch");
+    }
     for (const BatchColumn &c : done) {
       dgw_solve_info &inf = infos[c.tag];
       inf.iterations = c.iterations;
@@ -552,7 +557,6 @@ extern "C" dgw_status dgw_pressure_solve_batch(dgw_mesh_t M, int ncols, const do
       --left;
     }
   }
-  (void)t0;
   const double dofs = (double)(dof_counter() - dof0);
   dgw_status st = DGW_OK;
   for (int c = 0; c < ncols; ++c) {
