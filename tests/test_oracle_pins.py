@@ -217,6 +217,49 @@ def test_divergence_enrichment_volume_term():
     assert abs(val / ref - 1.0) < 1e-6, (val, ref)
 
 
+@pytest.mark.parametrize("comp", [0, 2])
+def test_divergence_enrichment_tangential_components(comp):
+    """Enrichment along x (or z) with vertex coefficients f = cos(2 pi s / L) of the vertex coordinate
+    s: u = psi(y+) F(s) e_s, F the piecewise-linear interpolant of f, continuous and periodic. With the
+    continuous periodic q = G(s), G interpolating g = sin(2 pi s / L), every face term cancels or has
+    u.n = 0, so sum_i q_i b_i = int G'(s) F(s) psi dV
+    = 2 L_t int_0^dy psi dy * sum_cells (g_{i+1} - g_i)(f_i + f_{i+1}) / 2 (L_t the other in-plane
+    length), the psi integral by adaptive quadrature."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    nx, nz = w.nx, w.nz
+    L, Lt, ncs = (w.lx, w.lz, nx) if comp == 0 else (w.lz, w.lx, nz)
+    h = L / ncs
+    f = lambda s: np.cos(2 * np.pi * s / L)
+    g = lambda s: np.sin(2 * np.pi * s / L)
+    u = np.zeros(m.n_u)
+    enr = u[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    for layer in range(2):                      # enriched cells: bottom layer, then top, x fastest
+        for kz in range(nz):
+            for i in range(nx):
+                e = layer * nx * nz + i + nx * kz
+                for v in range(8):
+                    vx, vz = v & 1, (v >> 2) & 1
+                    s = (i + vx) * h if comp == 0 else (kz + vz) * h
+                    enr[e, comp, v] = f(s)
+    s = m.node_coords()[:, comp]
+    n3 = (w.k + 1) ** 3
+    c = np.repeat(np.arange(m.nc), n3)          # nodes are stored cell by cell, cells x fastest
+    ci = c % nx if comp == 0 else c // (nx * w.ny)
+    t = s / h - ci
+    q = g(ci * h) + (g((ci + 1) * h) - g(ci * h)) * t
+    val = q @ m.divergence(u)
+    edges = np.arange(ncs) * h
+    lin = np.sum((g(edges + h) - g(edges)) * (f(edges) + f(edges + h)) / 2.0)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    ipsi = quad(lambda y: O.psi_spalding(y * w.u_tau / w.nu)[0], 0.0, dy, epsabs=1e-14, epsrel=1e-13,
+                limit=200)[0]
+    ref = 2 * Lt * ipsi * lin
+    assert abs(ref) > 1e-3
+    assert abs(val / ref - 1.0) < 1e-6, (val, ref)
+
+
 # ---------------------------------------------------------------------------------------------
 # Velocity mass term (Sec. 4.2, M_e(v, u) = (v, u) per cell)
 # ---------------------------------------------------------------------------------------------
