@@ -328,6 +328,48 @@ def test_convective_vanishes_for_shear_flow_with_enrichment(comp):
     assert np.abs(y).max() < 1e-14
 
 
+def test_convective_wall_normal_transport_by_the_enrichment():
+    """u = e_x (standard part) plus a wall-normal enrichment u_y = c psi(y+) (1 - eta) in the bottom
+    wall cells (weights c on the wall-side vertices, 0 on the others; eta the cell's local y). The field
+    is continuous (psi(0) = 0 on the wall, the weights vanish at the cell's upper face) and u.n = 0 on
+    the walls, so every face term cancels and, with the continuous test field w = y for component x,
+    sum_i w_i y_x[i] = -int u_x u_y dV = -c L_x L_z int_0^dy psi (1 - s/dy) ds. With the enriched test
+    functions of component x summed over the bottom layer (the test function psi e_x) the interface
+    flux is u_x u_y = 0 there, so the sum is -int u_y dpsi/dy dV
+    = -c L_x L_z (u_tau/nu) int_0^dy psi psi' (1 - s/dy) ds. Both integrals by adaptive quadrature; the
+    second also by the 8-point Gauss rule of the wall-normal direction, which the oracle must match to
+    rounding."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    c = 0.37
+    u = _std_field(m, lambda x, y, z: 1 + 0 * y, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    enr = u[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    nb = w.nx * w.nz                            # bottom layer first
+    for v in range(8):
+        if (v >> 1) & 1 == 0:
+            enr[:nb, 1, v] = c
+    y = m.convective(u)
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    sc = w.u_tau / w.nu
+    area = w.lx * w.lz
+    std = y[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    wy = m.node_coords()[:, 1].reshape(m.nc, -1)
+    val = np.sum(wy * std[:, 0, :])
+    ref = -c * area * quad(lambda s: O.psi_spalding(s * sc)[0] * (1 - s / dy), 0.0, dy,
+                           epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+    assert abs(val / ref - 1.0) < 1e-6, (val, ref)
+    ye = y[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    val_e = ye[:nb, 0, :].sum()
+    f = lambda s: np.prod(O.psi_spalding(s * sc)) * (1 - s / dy)
+    ref_e = -c * area * sc * quad(f, 0.0, dy, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+    assert abs(val_e / ref_e - 1.0) < 2e-5, (val_e, ref_e)   # psi psi' is less smooth: rule error
+    # the same integral by the q_w = 8 point Gauss rule (NumPy) the wall cells use wall-normal
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    rule = -c * area * sc * 0.5 * dy * sum(wq * f(0.5 * dy * (xq + 1)) for xq, wq in zip(xg, wg))
+    assert abs(val_e / rule - 1.0) < 1e-12, (val_e, rule)
+
+
 def test_convective_conservation_equals_wall_flux():
     """sum over all standard test functions of component d = sum of wall fluxes (interior fluxes
     cancel). For u = (0, 1 + y^2, 0) the mirrored LF flux on the walls gives 12 (top) + 4 (bottom)."""
