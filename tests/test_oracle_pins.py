@@ -370,15 +370,18 @@ def test_convective_wall_normal_transport_by_the_enrichment():
     assert abs(val_e / rule - 1.0) < 1e-12, (val_e, rule)
 
 
-def test_convective_conservation_equals_wall_flux():
+@pytest.mark.parametrize("b,total", [(0.0, 16.0), (1.0, 28.0)])
+def test_convective_conservation_equals_wall_flux(b, total):
     """sum over all standard test functions of component d = sum of wall fluxes (interior fluxes
-    cancel). For u = (0, 1 + y^2, 0) the mirrored LF flux on the walls gives 12 (top) + 4 (bottom)."""
+    cancel). With the mirror state u+ = -u- the wall flux is u_y (u.n) + 2 |u.n| u_y. For
+    u = (0, 1 + b y + y^2, 0): b = 0 gives 12 (top, u_y = 2) + 4 (bottom); b = 1 gives 27 (top, u_y = 3)
+    + 1 (bottom, u_y = 1), which also fixes the sign of u.n on the y-faces."""
     m = O.Mesh(2, 3, 2, 2, n_layers=0)
-    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: 1 + y ** 2, lambda x, y, z: 0 * y)
+    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: 1 + b * y + y ** 2, lambda x, y, z: 0 * y)
     y = m.convective(u)[: 3 * m.n_p].reshape(m.nc, 3, -1)
     sums = y.sum(axis=(0, 2))
     area = 2 * math.pi * math.pi
-    assert abs(sums[1] - 16.0 * area) < 1e-12 * 16 * area
+    assert abs(sums[1] - total * area) < 1e-12 * total * area
     assert abs(sums[0]) < 1e-12 and abs(sums[2]) < 1e-12
 
 
