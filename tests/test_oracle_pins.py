@@ -682,6 +682,145 @@ def test_viscous_energy_identity_as_a_value():
     assert max(m.nut_cell(uf, e).max() for e in range(m.n_e)) > 3 * nu
 
 
+def _nut_point(F, uf, c, xi):
+    """nu_t = l_mix^2 sqrt(2 eps(u~):eps(u~)) of the frozen field at reference point xi of cell c
+    (eq. mix, lmix, ydes: kappa = 0.41, A+ = 26, C_DES = 0.85, beta = 6, h = cell height / (k+1)),
+    from the independent point evaluation; 0 outside the enriched cells."""
+    if F.enr_index(c) < 0:
+        return 0.0
+    _, _, _, gt = F.eval(uf, c, xi)
+    et = _eps(gt)
+    h = F.hi[c] - F.lo[c]
+    y = F.lo[c][1] + xi[1] * h[1]
+    yh = y + 1.0 if (c // F.nx) % F.ny == 0 else 1.0 - y
+    yp = yh * math.sqrt(F.tau_w) / F.nu
+    hd = 0.85 * h[1] / (F.k + 1)
+    ydes = (yh ** -6 + hd ** -6) ** (-1.0 / 6.0) if yh > 0 else 0.0
+    lmix = 0.41 * ydes * (1.0 - math.exp(-yp / 26.0))
+    return lmix * lmix * math.sqrt(2.0 * np.sum(et * et))
+
+
+def test_viscous_bilinear_form_with_harmonic_mean_viscosity():
+    """The whole bilinear form v^T (-F^nu) u of eq. (viscous_multiscale) for independent random v and u
+    and a frozen field whose nu_t differs from cell to cell, summed here from the independent point
+    evaluation. On faces between two enriched cells (and on their mirrored walls) the weighted average
+    of eq. (harmweights), w^- = (nu + nu_t^+) / (2 nu + nu_t^- + nu_t^+), makes every weighted flux
+    w^- kappa^- = w^+ kappa^+ = H / 2 with H = 2 kappa^- kappa^+ / (kappa^- + kappa^+) the harmonic
+    mean of kappa = nu + nu_t of the two sides; this reference is written in that form:
+      consistency  -(H/2) (2 eps(u~^-) + 2 eps(u~^+)) n . v^-,
+      adjoint       (H/2) (grad v~^- n . [[u]] + n . grad v~^- [[u]]),
+    together with the standard average nu (eps(ubar^-) + eps(ubar^+)) n, the standard adjoint term
+    nu/2 (grad vbar n . j + n . grad vbar j) (j = [[ubar]], plus [[u~]] on the interface faces), the
+    interface term -nu (eps(ubar^-) + eps(ubar^+)) n . v~^-, and the penalty tau nu [[u]] . v^-
+    (tau = max of both sides inside, 10 tau on walls). Volume: 2 nu eps(vbar):eps(ubar)
+    + 2 nuhat eps(vbar):eps(u~) + 2 (nu + nu_t) eps(v~):eps(u~). Replacing the harmonic mean by the
+    arithmetic one changes the value by far more than the tolerance (asserted)."""
+    nx, ny, nz, k, qw = 2, 3, 2, 2, 8
+    nu, tau_w = 1e-4, 1e-2
+    m = O.Mesh(nx, ny, nz, k, n_layers=1, nu=nu, tau_w=tau_w, gamma=1.8, q_wall=qw)
+    uf = np.zeros(m.n_u)
+    uf[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 0, :] = 0.1
+    uf[3 * m.n_p:] += 0.1 * I.uniform(7, m.n_e * 24, -1, 1)
+    u = I.uniform(8, m.n_u, -1, 1)
+    v = I.uniform(9, m.n_u, -1, 1)
+    val = v @ m.viscous(uf, u)
+    F = _BoxFields(m, nx, ny, nz, k, nu, tau_w)
+    n = k + 1
+    tau = m.cell_tau()      # pinned against its definition in the energy identity
+
+    def gauss(q):
+        x, w = np.polynomial.legendre.leggauss(q)
+        return 0.5 * (x + 1), 0.5 * w
+
+    ref = 0.0
+    for c in range(m.nc):
+        h = F.hi[c] - F.lo[c]
+        e = F.enr_index(c)
+        nq = [n, qw if e >= 0 else n, n]
+        (x0, w0), (x1, w1), (x2, w2) = gauss(nq[0]), gauss(nq[1]), gauss(nq[2])
+        nut = m.nut_cell(uf, e).reshape(nq[2], nq[1], nq[0]) if e >= 0 else None
+        for i2 in range(nq[2]):
+            for i1 in range(nq[1]):
+                for i0 in range(nq[0]):
+                    xi = (x0[i0], x1[i1], x2[i2])
+                    dV = np.prod(h) * w0[i0] * w1[i1] * w2[i2]
+                    _, gb, _, gt = F.eval(u, c, xi)
+                    _, gvb, _, gvt = F.eval(v, c, xi)
+                    ref += dV * 2 * nu * np.sum(_eps(gvb) * _eps(gb))
+                    if e >= 0:
+                        nt = _nut_point(F, uf, c, xi)
+                        assert abs(nt - nut[i2, i1, i0]) <= 1e-12 * max(nt, 1e-300) + 1e-300
+                        nuh = min(nu + nt, 2 * math.sqrt(nu * (nu + nt)))
+                        ref += dV * 2 * nuh * np.sum(_eps(gvb) * _eps(gt))
+                        ref += dV * 2 * (nu + nt) * np.sum(_eps(gvt) * _eps(gt))
+    # faces, each from both sides (the test function lives on the side it is evaluated from)
+    face = 0.0
+    arith = 0.0      # change of the enriched-face terms with the arithmetic mean of kappa
+    for c in range(m.nc):
+        i, j, kz = c % nx, (c // nx) % ny, c // (nx * ny)
+        h = F.hi[c] - F.lo[c]
+        enr_c = F.enr_index(c) >= 0
+        for d in range(3):
+            t1 = 1 if d == 0 else 0
+            t2 = 1 if d == 2 else 2
+            for side in (0, 1):
+                step = 1 if side else -1
+                if d == 0:
+                    nb = (i + step) % nx + nx * (j + ny * kz)
+                elif d == 2:
+                    nb = i + nx * (j + ny * ((kz + step) % nz))
+                else:
+                    nb = i + nx * (j + step + ny * kz) if 0 <= j + step < ny else None
+                enr_o = enr_c if nb is None else F.enr_index(nb) >= 0
+                both, iface = enr_c and enr_o, enr_c != enr_o
+                tf = 10 * tau[c] if nb is None else max(tau[c], tau[nb])
+                nvec = np.zeros(3)
+                nvec[d] = 1.0 if side else -1.0
+                q1 = qw if (t1 == 1 and (enr_c or enr_o)) else n
+                q2 = qw if (t2 == 1 and (enr_c or enr_o)) else n
+                (a1, b1), (a2, b2) = gauss(q1), gauss(q2)
+                for p2 in range(q2):
+                    for p1 in range(q1):
+                        xi = [0.0, 0.0, 0.0]
+                        xi[d] = float(side)
+                        xi[t1], xi[t2] = a1[p1], a2[p2]
+                        dA = h[t1] * h[t2] * b1[p1] * b2[p2]
+                        ub, gb, ut, gt = F.eval(u, c, xi)
+                        vb, gvb, vt, gvt = F.eval(v, c, xi)
+                        ks = nu + _nut_point(F, uf, c, xi)
+                        if nb is None:        # mirror state: u+ = -u-, grad u+ = grad u-, nu_t+ = nu_t-
+                            ubo, gbo, uto, gto, ko = -ub, gb, -ut, gt, ks
+                        else:
+                            xo = list(xi)
+                            xo[d] = 1.0 - side
+                            ubo, gbo, uto, gto = F.eval(u, nb, xo)
+                            ko = nu + _nut_point(F, uf, nb, xo)
+                        jb, jt = ub - ubo, ut - uto
+                        jtot = jb + jt
+                        sb = nu * (_eps(gb) + _eps(gbo)) @ nvec             # {{2 nu eps(ubar)}} n
+                        jadj = jb + (jt if iface else 0.0)
+                        # standard test function: consistency, adjoint, penalty
+                        t = vb @ (-sb + tf * nu * jtot)
+                        t += 0.5 * nu * (jadj @ gvb @ nvec + nvec @ gvb @ jadj)
+                        # enriched test function
+                        t += vt @ (tf * nu * jtot) - (vt @ sb if iface else 0.0)
+                        if both:
+                            # enriched flux with the harmonic mean H of kappa (and, for the
+                            # sensitivity check, with the arithmetic mean)
+                            terms = []
+                            for mean in (2 * ks * ko / (ks + ko), 0.5 * (ks + ko)):
+                                st = 0.5 * mean * (2 * _eps(gt) + 2 * _eps(gto)) @ nvec
+                                terms.append(-(vb + vt) @ st
+                                             + 0.5 * mean * (jtot @ gvt @ nvec + nvec @ gvt @ jtot))
+                            t += terms[0]
+                            arith += dA * (terms[1] - terms[0])
+                        face += dA * t
+    ref += face
+    assert abs(val - ref) < 1e-12 * abs(ref), (val, ref)
+    # the weights matter: the arithmetic mean of kappa moves the value far beyond the tolerance
+    assert abs(arith) > 1e-6 * abs(ref), (arith, ref)
+
+
 # ---------------------------------------------------------------------------------------------
 # Enrichment and eddy viscosity (Sec. 3, Sec. 2.2)
 # ---------------------------------------------------------------------------------------------
