@@ -73,6 +73,26 @@ def test_null_handles_and_bad_options_are_rejected_without_a_device(lib):
         "dgw_ns_copy_state": lambda: L.dgw_ns_copy_state(None, None, None, None),
         "dgw_ns_create": lambda: L.dgw_ns_create(None, None, None, None, ctypes.byref(vp())),
         "dgw_helmholtz_solve": lambda: L.dgw_helmholtz_solve(None, ctypes.c_double(1.0), None, None, None, None, None),
+        "dgw_mesh_destroy": lambda: L.dgw_mesh_destroy(None),
+        "dgw_mesh_info": lambda: L.dgw_mesh_info(None, None, None, None, None),
+        "dgw_mesh_node_coords": lambda: L.dgw_mesh_node_coords(None, None),
+        "dgw_update_eddy_viscosity": lambda: L.dgw_update_eddy_viscosity(None, None, None),
+        "dgw_apply_laplace": lambda: L.dgw_apply_laplace(None, 0, None, None, None),
+        "dgw_apply_divergence": lambda: L.dgw_apply_divergence(None, None, None, None),
+        "dgw_apply_divergence_prec": lambda: L.dgw_apply_divergence_prec(None, 0, None, None, None),
+        "dgw_apply_convective": lambda: L.dgw_apply_convective(None, 0, None, None, None),
+        "dgw_apply_viscous": lambda: L.dgw_apply_viscous(None, 0, None, None, None),
+        "dgw_cfl_rate": lambda: L.dgw_cfl_rate(None, None, None, None),
+        "dgw_pressure_solve": lambda: L.dgw_pressure_solve(None, None, None, None, None, None),
+        "dgw_pressure_solve_batch": lambda: L.dgw_pressure_solve_batch(None, 1, None, None, None, None, None),
+        "dgw_pressure_solve_jacobi_noalloc": lambda: L.dgw_pressure_solve_jacobi_noalloc(
+            None, None, None, ctypes.c_double(1e-10), 10, None, None),
+        "dgw_solver_describe": lambda: L.dgw_solver_describe(None, 1, None, None, None, 0, None),
+        "dgw_server_create": lambda: L.dgw_server_create(ctypes.c_size_t(1 << 30), 0, ctypes.byref(vp())),
+        "dgw_submit": lambda: L.dgw_submit(None, None, None),
+        "dgw_poll": lambda: L.dgw_poll(None, ctypes.c_long(1), None, None, None),
+        "dgw_server_stats": lambda: L.dgw_server_stats(None, None, None, None, None),
+        "dgw_server_destroy": lambda: L.dgw_server_destroy(None, 0),
     }
     for name, call in calls.items():
         assert call() == -1, name
