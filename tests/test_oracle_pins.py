@@ -112,6 +112,24 @@ def test_bump_volume_closed_form():
     assert abs(m.volume() - ref) < 1e-6 * ref
 
 
+def test_bump_nodes_lie_on_the_walls_with_rows_upward():
+    """Cell rows count upward from the bump wall (the layout the ABI fixes): the lowest nodes of row 0
+    lie on y_w(x) = 0.3 cos^2(pi (x - 4.5) / 2) for |x - 4.5| < 1 (0 elsewhere), the highest nodes of
+    the top row on y = 3.036, and every node column rises monotonically from row to row."""
+    nx, ny, nz, k = 12, 4, 2, 3
+    m = O.Mesh(nx, ny, nz, k, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
+    n = k + 1
+    X = m.node_coords().reshape(nz, ny, nx, n, n, n, 3)        # [kz][j][i][c][b][a]
+    x, y = X[..., 0], X[..., 1]
+    s = x - 4.5
+    yw = np.where(np.abs(s) < 1.0, 0.3 * np.cos(np.pi * s / 2.0) ** 2, 0.0)
+    assert np.abs(y[:, 0, :, :, 0, :] - yw[:, 0, :, :, 0, :]).max() < 1e-14
+    assert np.abs(y[:, ny - 1, :, :, n - 1, :] - 3.036).max() < 1e-14
+    col = np.transpose(y, (0, 2, 3, 5, 1, 4)).reshape(nz, nx, n, n, ny * n)   # y up each node column
+    assert np.all(np.diff(col, axis=-1) >= -1e-14)
+    assert yw.max() > 0.29
+
+
 # ---------------------------------------------------------------------------------------------
 # SIPG Laplacian, eq. (ipflux)
 # ---------------------------------------------------------------------------------------------
