@@ -127,6 +127,12 @@ def test_bump_nodes_lie_on_the_walls_with_rows_upward():
     assert np.abs(y[:, ny - 1, :, :, n - 1, :] - 3.036).max() < 1e-14
     col = np.transpose(y, (0, 2, 3, 5, 1, 4)).reshape(nz, nx, n, n, ny * n)   # y up each node column
     assert np.all(np.diff(col, axis=-1) >= -1e-14)
+    # x and z: the map is the identity along them, nodes at the Gauss-Lobatto points of each cell,
+    # local index a along x and c along z ascending
+    gl = O.lobatto(n)            # pinned against the roots of P'_{n-1} above
+    xr = 9.0 * (np.arange(nx)[None, None, :, None, None, None] + gl[None, None, None, None, None, :]) / nx
+    zr = 4.5 * (np.arange(nz)[:, None, None, None, None, None] + gl[None, None, None, :, None, None]) / nz
+    assert np.abs(x - xr).max() < 1e-13 and np.abs(X[..., 2] - zr).max() < 1e-13
     assert yw.max() > 0.29
 
 
