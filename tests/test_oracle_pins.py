@@ -1171,6 +1171,50 @@ def test_set_tau_nodes_interpolates_bilinearly_along_the_wall():
             assert abs(r["yplus"] / yp - 1.0) < 1e-12
 
 
+def test_wall_distance_and_nodal_tau_on_the_bump():
+    """On the bump every vertex of an enriched cell takes the distance to, and the tau_w of, the
+    closest wall vertex of either wall (periodic copies included), found here by brute force over the
+    node coordinates; y+ at a point is y_h sqrt(tau_h) / nu with y_h and tau_h the trilinear
+    interpolants of those vertex values (Sec. 3.2)."""
+    nx, ny, nz, k = 12, 4, 2, 2
+    nu, tau_w = 1e-3, 2e-2
+    m = O.Mesh(nx, ny, nz, k, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=1, nu=nu, tau_w=tau_w)
+    tn = tau_w * (1.0 + 0.5 * I.uniform(4, m.n_wall_nodes, -1.0, 1.0))
+    m.set_tau_nodes(tn)
+    n = k + 1
+    X = m.node_coords().reshape(nz, ny, nx, n, n, n, 3)          # [kz][j][i][c][b][a]
+    # wall vertices (wi, wk) = 0..nx, 0..nz with their node index wall * nx * nz + wi % nx + nx * (wk % nz)
+    wall_pts, wall_idx = [], []
+    for wall, (j, b) in enumerate(((0, 0), (ny - 1, n - 1))):
+        for wk in range(nz + 1):
+            for wi in range(nx + 1):
+                p = X[min(wk, nz - 1), j, min(wi, nx - 1), (n - 1) if wk == nz else 0, b,
+                      (n - 1) if wi == nx else 0].copy()
+                wall_pts.append(p)
+                wall_idx.append(wall * nx * nz + wi % nx + nx * (wk % nz))
+    wall_pts, wall_idx = np.array(wall_pts), np.array(wall_idx)
+    u = np.zeros(m.n_u)
+    checked = 0
+    for (i, j, kz) in [(0, 0, 0), (4, 0, 1), (5, 0, 0), (6, 0, 1), (7, 0, 0), (11, 0, 1), (5, ny - 1, 0)]:
+        c = i + nx * (j + ny * kz)
+        d = np.zeros(8)
+        t = np.zeros(8)
+        for v in range(8):
+            vx, vy, vz = v & 1, (v >> 1) & 1, v >> 2
+            p = X[kz, j, i, (n - 1) * vz, (n - 1) * vy, (n - 1) * vx]
+            dist = np.linalg.norm(wall_pts - p, axis=1)
+            q = int(np.argmin(dist))
+            d[v], t[v] = dist[q], tn[wall_idx[q]]
+        for xi in ([0.2, 0.3, 0.7], [0.9, 0.05, 0.4], [0.5, 0.8, 0.1]):
+            N = np.array([(xi[0] if v & 1 else 1 - xi[0]) * (xi[1] if (v >> 1) & 1 else 1 - xi[1])
+                          * (xi[2] if v >> 2 else 1 - xi[2]) for v in range(8)])
+            yp = (N @ d) * math.sqrt(N @ t) / nu
+            r = m.eval_point(u, c, xi)
+            assert abs(r["yplus"] / yp - 1.0) < 1e-12, (i, j, kz, xi, r["yplus"], yp)
+            checked += 1
+    assert checked == 21
+
+
 # ---------------------------------------------------------------------------------------------
 # Cell-wise L2 projection onto the space of a new wall shear stress (Sec. 3.2, eq. l2). The cell
 # systems are ill-conditioned (psi N_B is close to the polynomials where the cell spans few wall
