@@ -136,6 +136,61 @@ def test_bump_nodes_lie_on_the_walls_with_rows_upward():
     assert yw.max() > 0.29
 
 
+def test_penalty_on_curved_cells_against_the_mapped_cell():
+    """tau = (k+1)^2 A(dK) / V(K) (interior faces weighted 1/2, walls 1) on the curved bump cells, with
+    A and V integrated here to convergence (16 Gauss points per direction) over the isoparametric cell
+    rebuilt from the node coordinates (Lagrange interpolation on the Gauss-Lobatto nodes, dA =
+    |det J| |grad xi_d|). The oracle's k+2 point rules agree to 1e-6 (they are exact on boxes); a rule
+    of k points would be off by about 2e-5."""
+    nx, ny, nz, k = 12, 4, 2, 3
+    m = O.Mesh(nx, ny, nz, k, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
+    n = k + 1
+    X = m.node_coords().reshape(m.nc, n, n, n, 3)               # [c][cc][b][a]
+    gl = O.lobatto(n)
+
+    def lag(s):
+        v, d = np.ones(n), np.zeros(n)
+        for a in range(n):
+            for b in range(n):
+                if b != a:
+                    v[a] *= (s - gl[b]) / (gl[a] - gl[b])
+            for c in range(n):
+                if c != a:
+                    t = 1.0 / (gl[a] - gl[c])
+                    for b in range(n):
+                        if b != a and b != c:
+                            t *= (s - gl[b]) / (gl[a] - gl[b])
+                    d[a] += t
+        return v, d
+
+    def jac(c, xi):
+        L = [lag(x) for x in xi]
+        return np.array([[np.einsum("zyx,z,y,x", X[c, ..., e], *(L[2][dz], L[1][dy], L[0][dx]))
+                          for (dx, dy, dz) in ((1, 0, 0), (0, 1, 0), (0, 0, 1))] for e in range(3)])
+
+    q = 16
+    xq, wq = np.polynomial.legendre.leggauss(q)
+    xq, wq = 0.5 * (xq + 1), 0.5 * wq
+    tau = m.cell_tau()
+    for c in [4, 5, 6, 7, 4 + nx * (ny - 1), 5 + nx]:           # bump columns, bottom, top and inner rows
+        j = (c // nx) % ny
+        V = sum(abs(np.linalg.det(jac(c, (xq[a], xq[b], xq[e])))) * wq[a] * wq[b] * wq[e]
+                for a in range(q) for b in range(q) for e in range(q))
+        A = 0.0
+        for d in range(3):
+            t1, t2 = [e for e in range(3) if e != d]
+            for side in (0, 1):
+                wall = d == 1 and ((side == 0 and j == 0) or (side == 1 and j == ny - 1))
+                for p in range(q):
+                    for r in range(q):
+                        xi = [0.0, 0.0, 0.0]
+                        xi[d], xi[t1], xi[t2] = float(side), xq[p], xq[r]
+                        J = jac(c, xi)
+                        dA = abs(np.linalg.det(J)) * np.linalg.norm(np.linalg.inv(J)[d])
+                        A += (1.0 if wall else 0.5) * dA * wq[p] * wq[r]
+        assert abs(tau[c] / (n * n * A / V) - 1.0) < 1e-6, (c, tau[c], n * n * A / V)
+
+
 # ---------------------------------------------------------------------------------------------
 # SIPG Laplacian, eq. (ipflux)
 # ---------------------------------------------------------------------------------------------
