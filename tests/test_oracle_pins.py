@@ -1226,6 +1226,40 @@ def test_set_tau_nodes_interpolates_bilinearly_along_the_wall():
             assert abs(r["yplus"] / yp - 1.0) < 1e-12
 
 
+def test_enrichment_gradient_is_the_derivative_of_the_enrichment():
+    """With a nodal tau_w varying along the wall, grad u~ = sum_B u~_B (psi grad N_B + N_B psi' grad y+)
+    and grad y+ = (sqrt(tau_h) grad y_h + y_h grad tau_h / (2 sqrt(tau_h))) / nu must be the derivative
+    of the field u~ itself: nu_t = l_mix^2 sqrt(2 eps(u~):eps(u~)) (eq. mix, lmix, ydes) evaluated with
+    central differences of u~ (and y+ from the point evaluation, pinned above) matches the oracle's
+    nu_t at points of wall cells on both walls."""
+    nx, ny, nz, k = 4, 4, 4, 2
+    nu, tau_w = 1e-3, 1e-2
+    m = O.Mesh(nx, ny, nz, k, nu=nu, tau_w=tau_w, n_layers=1)
+    m.set_tau_nodes(tau_w * (1.0 + 0.5 * I.uniform(14, m.n_wall_nodes, -1.0, 1.0)))
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:] = I.uniform(15, 24 * m.n_e, -1.0, 1.0)
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    dlt = 1e-5
+    for c in [0, 1 + nx * ny * 2, 2 + nx * (ny - 1) + nx * ny * 3, 1 + nx * (ny - 1)]:   # both walls
+        lo, hi = X[c].min(axis=0), X[c].max(axis=0)
+        h = hi - lo
+        for xi in ([0.3, 0.4, 0.6], [0.8, 0.15, 0.25], [0.55, 0.9, 0.7]):
+            G = np.zeros((3, 3))
+            for d in range(3):
+                a, b = list(xi), list(xi)
+                a[d] += dlt
+                b[d] -= dlt
+                G[:, d] = (m.eval_point(u, c, a)["util"] - m.eval_point(u, c, b)["util"]) / (2 * dlt * h[d])
+            E = 0.5 * (G + G.T)
+            r = m.eval_point(u, c, xi)
+            y = lo[1] + xi[1] * h[1]
+            yh = 1.0 - abs(y)
+            ydes = (yh ** -6 + (0.85 * h[1] / (k + 1)) ** -6) ** (-1.0 / 6.0)
+            lmix = 0.41 * ydes * (1.0 - math.exp(-r["yplus"] / 26.0))
+            ref = lmix ** 2 * math.sqrt(2.0 * np.sum(E * E))
+            assert abs(r["nut"] / ref - 1.0) < 1e-7, (c, xi, r["nut"], ref)
+
+
 def test_wall_distance_and_nodal_tau_on_the_bump():
     """On the bump every vertex of an enriched cell takes the distance to, and the tau_w of, the
     closest wall vertex of either wall (periodic copies included), found here by brute force over the
