@@ -427,6 +427,26 @@ def test_convective_vanishes_for_shear_flow_with_enrichment(comp):
     assert np.abs(y).max() < 1e-14
 
 
+@pytest.mark.parametrize("k,f,g,w", [
+    (2, lambda y: 1 + y + y ** 2, lambda y: 1 - y ** 2, lambda y: y ** 2),
+    (3, lambda y: 1 + y + y ** 3, lambda y: y - y ** 3, lambda y: y ** 3)], ids=["k2", "k3"])
+def test_convective_over_integration_is_exact_for_polynomials(k, f, g, w):
+    """Sec. 4.4 over-integrates the convective term with floor(3k/2) + 1 points per direction, which
+    integrates (u x u) : grad v (degree 3k - 1 per direction) exactly for fields of degree k. With
+    u = (f(y), g(y), 0) (continuous, g(+-1) = 0 so u.n = 0 on the walls and every face term cancels or
+    vanishes) and the continuous test field w(y) for component x:
+    sum_i w_i y_x[i] = -L_x L_z int f g w' dy, which is -(8/15) L_x L_z for both cases:
+    k = 2: (1 + y + y^2)(1 - y^2) 2y, k = 3: (1 + y + y^3)(y - y^3) 3y^2 (degree 8 on the graded,
+    affine-per-cell rows: k + 1 = 4 points are not exact, 5 are)."""
+    m = O.Mesh(3, 5, 2, k, n_layers=0, gamma=1.8)
+    u = _std_field(m, lambda x, y, z: f(y), lambda x, y, z: g(y), lambda x, y, z: 0 * y)
+    y = m.convective(u)[: 3 * m.n_p].reshape(m.nc, 3, -1)
+    wy = w(m.node_coords()[:, 1]).reshape(m.nc, -1)
+    val = np.sum(wy * y[:, 0, :])
+    ref = -(8.0 / 15.0) * 2 * math.pi * math.pi
+    assert abs(val - ref) < 1e-12 * abs(ref), (val, ref)
+
+
 def test_convective_wall_normal_transport_by_the_enrichment():
     """u = e_x (standard part) plus a wall-normal enrichment u_y = c psi(y+) (1 - eta) in the bottom
     wall cells (weights c on the wall-side vertices, 0 on the others; eta the cell's local y). The field
