@@ -251,8 +251,9 @@ dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const
  * iterations of that column; ms: host time from the column's admission to its completion;
  * dof_applies: the block's applications divided evenly). opts->mode must be 1. Box cells only
  * (geometry 0) and meshes whose coarsest multigrid level is solved densely; otherwise DGW_EINVAL.
- * The block workspace (8 columns) is allocated on first use and kept with the mesh. Synchronises
- * `stream`. DGW_ENOTCONV if some column reached max_iter. */
+ * The block workspace (8 columns) is allocated on first use and kept with the mesh; a call that
+ * fails with DGW_ECUDA releases it (the next call starts a new block). Synchronises `stream`.
+ * DGW_ENOTCONV if some column reached max_iter. */
 dgw_status dgw_pressure_solve_batch(dgw_mesh_t mesh, int ncols, const double *const *b, double *const *p,
                                     const dgw_solve_opts *opts, dgw_solve_info *infos, void *stream);
 
@@ -375,8 +376,12 @@ dgw_status dgw_solver_describe(dgw_mesh_t mesh, int mode, int *n_levels, double 
  * and degree are admitted as worker slots and device memory free up; each job runs on a resident
  * mesh with its parameters (created on first use, kept for later jobs, at most one job per mesh
  * instance at a time, idle meshes evicted least-recently-used when the HBM budget is short), and
- * each worker has its own CUDA stream, so concurrent jobs overlap on the device. Results do not
- * depend on the mix (jobs share no scratch; all kernels and reductions are deterministic). */
+ * each worker has its own CUDA stream, so concurrent jobs overlap on the device. Mixed-precision
+ * solves (opts.mode 1) on channel meshes are batched continuously: the worker that takes one runs it
+ * as a block solve (dgw_pressure_solve_batch's engine) and, between refinement rounds, admits queued
+ * solves with the same mesh parameters and Chebyshev degree into free columns (up to 8); a column
+ * that converges is reported at once and frees its column. Results do not depend on the mix (jobs
+ * share no scratch; all kernels and reductions are deterministic and per column). */
 enum { DGW_JOB_SOLVE = 0, DGW_JOB_LAPLACE = 1, DGW_JOB_DIVERGENCE = 2, DGW_JOB_CONVECTIVE = 3, DGW_JOB_VISCOUS = 4 };
 
 typedef struct {
