@@ -222,6 +222,31 @@ def test_laplace_bruteforce_symmetric_psd(dims, k, geometry):
     assert np.allclose(np.diag(A), m.laplace_diag(), rtol=0, atol=1e-13 * scale)
 
 
+@pytest.mark.parametrize("op", ["laplace", "divergence", "convective", "viscous", "vmass"])
+def test_default_rules_are_exact_on_box_cells(op):
+    """On affine box cells without enrichment every integrand of a DG field of degree k is a
+    polynomial that the method's rules integrate exactly (Sec. 4.4: k+1 Gauss points for the linear
+    terms, floor(3k/2)+1 for the convective term), so adding two points per direction to every
+    cell and face rule (extra_q = 2) changes no output beyond rounding, for random fields. The
+    Lax-Friedrichs dissipation max(|u^-.n|, |u^+.n|) [[u]] is not a polynomial on a face where the
+    normal velocity varies and jumps, so the convective case takes continuous random cubics in y,
+    whose normal velocity is constant on every y-face (walls included) and whose jumps vanish inside."""
+    kw = dict(n_layers=0, gamma=1.8, nu=1e-3)
+    base = O.Mesh(3, 4, 2, 3, **kw)
+    over = O.Mesh(3, 4, 2, 3, extra_q=2, **kw)
+    p = I.uniform(21, base.n_p, -1, 1)
+    u = I.uniform(22, base.n_u, -1, 1)
+    if op == "convective":
+        cf = I.uniform(23, 12, -1, 1).reshape(3, 4)
+        u = _std_field(base, *[lambda x, y, z, a=a: cf[a, 0] + cf[a, 1] * y + cf[a, 2] * y ** 2 + cf[a, 3] * y ** 3
+                               for a in range(3)])
+    f = {"laplace": lambda m: m.laplace(p), "divergence": lambda m: m.divergence(u),
+         "convective": lambda m: m.convective(u), "viscous": lambda m: m.viscous(u, u),
+         "vmass": lambda m: m.vmass(u)}[op]
+    a, b = f(base), f(over)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(a).max(), op
+
+
 def test_laplace_bilinear_form_of_smooth_fields_closed_form():
     """For continuous fields the SIPG face terms vanish and q^T A p = int grad q . grad p."""
     m = O.Mesh(3, 5, 2, 3, n_layers=0, gamma=1.8)
