@@ -1432,6 +1432,25 @@ def test_projection_matches_the_integrals_of_the_old_wall_law():
     assert np.abs(un[: 3 * m.n_p].reshape(m.nc, 3, -1)[:, 1:, :]).max() == 0.0
 
 
+@pytest.mark.parametrize("full_q", [False, True])
+def test_projection_keeps_the_moments_against_every_standard_test_function(full_q):
+    """Galerkin condition of eq. (l2) for the standard test functions, which both spaces share: for a
+    random old field (standard and enriched coefficients varying in every direction) projected onto a
+    random nodal tau_w, int phi_i u_new (new space) = int phi_i u_old (old space) for every standard
+    phi_i, both integrals taken by the (separately pinned) velocity mass operator with the mesh holding
+    the old and then the new tau_w. With the default point set the in-plane directions are collocated
+    (k+1 points for k+1 functions), so only the q_w^3 rule exercises the in-plane weights."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(4, 4, 3, 2, lx=w.lx, lz=w.lz, nu=w.nu, tau_w=w.tau_w, full_quadrature=full_q)
+    u = I.uniform(31, m.n_u, -1, 1)
+    u[3 * m.n_p:] *= 0.3
+    y_old = m.vmass(u)[: 3 * m.n_p]
+    un = m.project(w.tau_w * (1.0 + 0.3 * I.uniform(32, m.n_wall_nodes, -1, 1)), u)
+    y_new = m.vmass(un)[: 3 * m.n_p]
+    assert np.abs(y_new - y_old).max() < 1e-9 * np.abs(y_old).max()
+    assert np.abs(un - u).max() > 1e-3                  # the space did change
+
+
 # ---------------------------------------------------------------------------------------------
 # Switch-off of the wall model where the wall-nearest cell lies below a y+ threshold (Sec. 3.2)
 # ---------------------------------------------------------------------------------------------
