@@ -1644,6 +1644,72 @@ def test_cfl_rate_of_a_uniform_flow_is_the_thinnest_row_closed_form():
     assert abs(m.cfl_rate(-3.0 * u) / (3.0 * ref) - 1.0) < 1e-13
 
 
+def test_cfl_rate_with_a_mean_flow_and_enrichment_in_every_component():
+    """ubar = (U, V, W) everywhere plus u~ = psi(y+) (a, b, c) in the wall cells (all weights equal):
+    the velocity at a wall-cell point is (U + a psi, V + b psi, W + c psi), so the rate is the largest of
+    sqrt(((U + a psi_q)/h_x)^2 + ((V + b psi_q)/h_y)^2 + ((W + c psi_q)/h_z)^2) over the q_w wall-normal
+    points and of the plain value in the other rows (a sign error in any component changes it)."""
+    k, nu, tau_w = 2, 1e-3, 4e-2
+    m = O.Mesh(2, 4, 2, k, nu=nu, tau_w=tau_w, n_layers=1)
+    U, V, W = 0.3, -0.2, 0.1
+    a, b, c = 0.05, 0.4, -0.3
+    u = _std_field(m, lambda x, y, z: U + 0 * y, lambda x, y, z: V + 0 * y, lambda x, y, z: W + 0 * y)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:] = np.array([a, b, c])[None, :, None]
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    h = X.max(axis=1) - X.min(axis=1)
+    ut = math.sqrt(tau_w)
+    gy, _ = O.gauss(8)
+    rates = [np.sqrt((U / h[cc, 0]) ** 2 + (V / h[cc, 1]) ** 2 + (W / h[cc, 2]) ** 2) for cc in range(m.nc)]
+    hw = h[0]                                            # wall rows: the same sizes at both walls
+    for yq in gy:
+        ps = O.psi_spalding(yq * hw[1] * ut / nu)[0]
+        rates.append(math.sqrt(((U + a * ps) / hw[0]) ** 2 + ((V + b * ps) / hw[1]) ** 2 + ((W + c * ps) / hw[2]) ** 2))
+    assert abs(m.cfl_rate(u) / max(rates) - 1.0) < 1e-12
+
+
+def test_cfl_rate_on_curved_cells():
+    """u = (U, V (1 + x / 9), W) on the bump: the rate is the largest |J^-1 u| over the linear point set,
+    J^-1 and x rebuilt here from the node coordinates (Lagrange interpolation on the Gauss-Lobatto
+    nodes). On the bump's slopes J^-1 is not diagonal; the x-dependent u_y breaks the mirror symmetry of
+    the bump, so the sign of every off-diagonal term matters."""
+    nx, ny, nz, k = 12, 3, 1, 2
+    m = O.Mesh(nx, ny, nz, k, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
+    U, V, W = 1.0, 0.6, -0.3
+    u = _std_field(m, lambda x, y, z: U + 0 * x, lambda x, y, z: V * (1 + x / 9.0), lambda x, y, z: W + 0 * x)
+    n = k + 1
+    X = m.node_coords().reshape(m.nc, n, n, n, 3)
+    gl = O.lobatto(n)
+
+    def lag(s):
+        v, d = np.ones(n), np.zeros(n)
+        for i in range(n):
+            for j in range(n):
+                if j != i:
+                    v[i] *= (s - gl[j]) / (gl[i] - gl[j])
+            for c in range(n):
+                if c != i:
+                    t = 1.0 / (gl[i] - gl[c])
+                    for j in range(n):
+                        if j != i and j != c:
+                            t *= (s - gl[j]) / (gl[i] - gl[j])
+                    d[i] += t
+        return v, d
+
+    gq, _ = O.gauss(n)
+    best = 0.0
+    for c in range(m.nc):
+        for x2 in gq:
+            for x1 in gq:
+                for x0 in gq:
+                    L = [lag(x0), lag(x1), lag(x2)]
+                    J = np.array([[np.einsum("zyx,z,y,x", X[c, ..., e], L[2][dz], L[1][dy], L[0][dx])
+                                   for (dx, dy, dz) in ((1, 0, 0), (0, 1, 0), (0, 0, 1))] for e in range(3)])
+                    xp = np.einsum("zyx,z,y,x", X[c, ..., 0], L[2][0], L[1][0], L[0][0])
+                    vel = np.array([U, V * (1 + xp / 9.0), W])
+                    best = max(best, np.linalg.norm(np.linalg.solve(J, vel)))
+    assert abs(m.cfl_rate(u) / best - 1.0) < 1e-12
+
+
 def test_cfl_rate_includes_the_enrichment_at_the_wall_normal_points():
     """With ubar = 0 and u~_B = u_tau e_x the velocity is u_tau psi(y+) e_x, largest at the outermost
     of the q_w wall-normal Gauss points of a wall cell: rate = u_tau psi(y+_q) / h_x there."""
