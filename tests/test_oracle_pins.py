@@ -1595,6 +1595,35 @@ def test_divdiv_closed_form_null_space_and_tau():
     assert np.allclose(m.tau_divdiv(uu, dt, cr), U * np.cbrt(vol) * dt / cr, rtol=1e-12, atol=0)
 
 
+def test_divdiv_of_the_wall_normal_enrichment():
+    """u = psi(y+) e_y from enrichment only (all weights 1): div u = psi'(y+) u_tau / nu, so
+    u^T D u = tau int (div u)^2 over the wall cells = 2 tau L_x L_z (u_tau/nu)^2 int_0^dy psi'^2 ds
+    (by the 8-point wall-normal Gauss rule to rounding, and by adaptive quadrature within the rule's
+    error). For the x and z components the enriched test functions of a cell sum to psi e_x (psi e_z),
+    whose divergence is zero, so their outputs sum to zero in every cell."""
+    from scipy.integrate import quad
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    c = 0.37
+    u = np.zeros(m.n_u)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 1, :] = 1.0
+    y = m.divdiv(np.full(m.nc, c), u)
+    sc = w.u_tau / w.nu
+    dy = 1.0 + math.tanh(1.8 * (2.0 / 8 - 1.0)) / math.tanh(1.8)
+    f = lambda s: O.psi_spalding(s * sc)[1] ** 2
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    rule = 0.5 * dy * sum(wq * f(0.5 * dy * (xq + 1)) for xq, wq in zip(xg, wg))
+    ref = 2 * c * w.lx * w.lz * sc ** 2 * rule
+    val = u @ y
+    assert abs(val / ref - 1.0) < 1e-12, (val, ref)
+    exact = 2 * c * w.lx * w.lz * sc ** 2 * quad(f, 0.0, dy, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+    assert abs(val / exact - 1.0) < 1e-4
+    ye = y[3 * m.n_p:].reshape(m.n_e, 3, 8)
+    big = np.abs(ye[:, 1, :]).max()
+    for a in (0, 2):
+        assert np.abs(ye[:, a, :].sum(axis=1)).max() < 1e-12 * big
+
+
 @pytest.mark.parametrize("geometry", [0, 1])
 def test_inverse_mass_inverts_the_mass_operator(geometry):
     """M^-1 (M u) = u for a velocity with enrichment, measured as functions (L2 norm): the wall-cell
