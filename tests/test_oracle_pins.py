@@ -1595,6 +1595,33 @@ def test_divdiv_closed_form_null_space_and_tau():
     assert np.allclose(m.tau_divdiv(uu, dt, cr), U * np.cbrt(vol) * dt / cr, rtol=1e-12, atol=0)
 
 
+def test_tau_divdiv_of_wall_cells_with_enrichment():
+    """tau_D = (volume average of |u|) h dt / Cr (eq. tauD, h the cube root of the cell volume) in wall
+    cells where u = (U, V, W) + psi(y+) (a, b, c): the average of
+    sqrt((U + a psi)^2 + (V + b psi)^2 + (W + c psi)^2) over the cell is taken along y by the q_w = 8
+    point Gauss rule (NumPy) the wall cells use; every component's sign enters."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    U, V, W = 0.3, -0.2, 0.1
+    a, b, c = 0.05, 0.04, -0.03
+    u = _std_field(m, lambda x, y, z: U + 0 * y, lambda x, y, z: V + 0 * y, lambda x, y, z: W + 0 * y)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:] = np.array([a, b, c])[None, :, None]
+    dt, cr = 1e-3, 0.14
+    tau = m.tau_divdiv(u, dt, cr)
+    X = m.node_coords().reshape(m.nc, -1, 3)
+    h = X[0].max(axis=0) - X[0].min(axis=0)                 # a bottom wall cell
+    sc = w.u_tau / w.nu
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    mean = 0.0
+    for xq, wq in zip(xg, wg):
+        ps = O.psi_spalding(0.5 * (xq + 1) * h[1] * sc)[0]
+        mean += 0.5 * wq * math.sqrt((U + a * ps) ** 2 + (V + b * ps) ** 2 + (W + c * ps) ** 2)
+    ref = mean * np.cbrt(np.prod(h)) * dt / cr
+    assert abs(tau[0] / ref - 1.0) < 1e-12, (tau[0], ref)
+    top = w.nx * (w.ny - 1)                                  # a top wall cell: the same by symmetry
+    assert abs(tau[top] / ref - 1.0) < 1e-12
+
+
 def test_divdiv_of_the_wall_normal_enrichment():
     """u = psi(y+) e_y from enrichment only (all weights 1): div u = psi'(y+) u_tau / nu, so
     u^T D u = tau int (div u)^2 over the wall cells = 2 tau L_x L_z (u_tau/nu)^2 int_0^dy psi'^2 ds
