@@ -1845,6 +1845,19 @@ def test_curl_weak_form_closed_forms():
     assert np.abs(m.curl(g)).max() < 1e-13
 
 
+def test_curl_of_a_linear_field_with_every_gradient_entry():
+    """The curl term has no face integrals, so cell-wise linear fields need no continuity: for
+    u = (a z + d y, b x + e z, c y + f x) every entry of grad u is set and curl u = (c - e, a - f, b - d),
+    so the standard outputs of component i summed over all test functions give V curl_i."""
+    m = O.Mesh(3, 4, 2, 2, n_layers=0)
+    a, b, c, d, e, f = 0.3, -0.7, 1.1, 0.4, 0.9, -0.2
+    u = _std_field(m, lambda x, y, z: a * z + d * y, lambda x, y, z: b * x + e * z, lambda x, y, z: c * y + f * x)
+    y = m.curl(u)[: 3 * m.n_p].reshape(m.nc, 3, -1).sum(axis=(0, 2))
+    vol = 4 * math.pi ** 2
+    ref = vol * np.array([c - e, a - f, b - d])
+    assert np.abs(y - ref).max() < 1e-12 * vol
+
+
 def test_vorticity_of_a_polynomial_is_exact_with_enrichment():
     """u = (y^3 - y, 0, y^2) (Q3): curl u = (2y, 0, 1 - 3y^2) lies in the velocity space (enrichment
     coefficients zero), so its L2 projection is itself (compared as functions)."""
