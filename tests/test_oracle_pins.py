@@ -1879,6 +1879,25 @@ def test_pressure_neumann_convective_part():
     assert abs(y.sum() / ref - 1.0) < 1e-12
 
 
+def test_pressure_neumann_convective_part_with_enrichment():
+    """ubar = (0, V, W z) and u~ = psi(y+) (0, b, 0) (all weights b), omega = 0: at a wall psi = 0, so
+    u = ubar there while grad u~ = b psi'(0) grad y+ = +-b (u_tau/nu) e_y (sign of the wall's normal
+    distance), and div(u x u) . e_y = u_y div u + u . grad u_y = V (2 s b + W) on the bottom wall and
+    V (W - 2 s b) on the top wall (s = u_tau / nu). With n = -e_y and +e_y the wall integrals of q = 1
+    are L_x L_z beta V (2 s b + W) and L_x L_z beta V (2 s b - W), each wall on its own."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(**w.mesh_kwargs())
+    V, W, b, beta = 0.4, 0.3, 1e-3, 1.5
+    u = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: V + 0 * y, lambda x, y, z: W * z)
+    u[3 * m.n_p:].reshape(m.n_e, 3, 8)[:, 1, :] = b
+    y = m.pressure_neumann(u, np.zeros(m.n_u), beta).reshape(w.nz, w.ny, w.nx, -1)
+    s = w.u_tau / w.nu
+    area = w.lx * w.lz
+    bottom, top = y[:, 0].sum(), y[:, w.ny - 1].sum()
+    assert abs(bottom / (area * beta * V * (2 * s * b + W)) - 1.0) < 1e-12
+    assert abs(top / (area * beta * V * (2 * s * b - W)) - 1.0) < 1e-12
+
+
 def test_pressure_neumann_viscous_part():
     """u = (0, sin(kx), 0): curl u = (0, 0, k cos kx), curl curl u = (0, k^2 sin kx, 0), the convective
     part vanishes; with q = y sin(kx), sum of q g over both walls = -2 beta nu k^2 (L_x/2) L_z. The
