@@ -1898,6 +1898,24 @@ def test_pressure_neumann_convective_part_with_enrichment():
     assert abs(top / (area * beta * V * (2 * s * b - W)) - 1.0) < 1e-12
 
 
+def test_pressure_neumann_on_the_sloped_bump_wall():
+    """u = (a x, 0, 0) cell by cell on the bump (the data are per wall face, so no continuity is needed):
+    div(u x u) = (2 a^2 x, 0, 0), and on the bump wall n dA = (y_w'(x), -1, 0) dx dz, so the bottom
+    wall's integral of q = 1 is -2 beta a^2 L_z int x y_w'(x) dx = 2 beta a^2 L_z int y_w dx (periodic,
+    y_w = 0 at the ends), with y_w the mesh's Q_k wall, whose bump area is 9 * 3.036 - V / L_z (V the
+    separately pinned volume; both integrals are exact for the polynomial map); the flat top wall gets
+    nothing."""
+    m = O.Mesh(12, 4, 1, 3, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
+    a, beta = 0.7, 1.5
+    u = _std_field(m, lambda x, y, z: a * x, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
+    y = m.pressure_neumann(u, np.zeros(m.n_u), beta).reshape(1, 4, 12, -1)
+    area = 9.0 * 3.036 - m.volume() / 4.5
+    assert abs(area / 0.3 - 1.0) < 1e-2
+    ref = 2 * beta * a * a * 4.5 * area
+    assert abs(y[:, 0].sum() / ref - 1.0) < 1e-11
+    assert abs(y[:, 3].sum()) < 1e-12 * ref
+
+
 def test_pressure_neumann_viscous_part():
     """u = (0, sin(kx), 0): curl u = (0, 0, k cos kx), curl curl u = (0, k^2 sin kx, 0), the convective
     part vanishes; with q = y sin(kx), sum of q g over both walls = -2 beta nu k^2 (L_x/2) L_z. The
