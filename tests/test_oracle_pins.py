@@ -1247,21 +1247,21 @@ def test_wall_shear_weights_nodes_with_the_hat_functions():
 
 
 def test_wall_shear_is_the_magnitude_of_the_hat_weighted_traction_vector():
-    """u = (1 - y^2) ((1 + a sin(2 pi z / L_z)) e_x + b e_z): the wall traction nu du/dn is a vector
-    with x and z components, varying along z. Each node gets the magnitude of its hat-weighted mean
-    traction, 2 nu sqrt((1 + a s sin(kappa z_k))^2 + b^2) with s = 2 (1 - cos kappa h) / (kappa h)^2
-    the hat's factor for the sine (uniform spacing h along z)."""
-    nu, a, b, nz = 1e-3, 0.5, 0.7, 16
+    """u = (1 - y^2) ((1 + a sin(2 pi z / L_z)) e_x + c e_y + b e_z): the wall traction nu du/dn is a
+    vector with three components, varying along z. Each node gets the magnitude of its hat-weighted
+    mean traction, 2 nu sqrt((1 + a s sin(kappa z_k))^2 + c^2 + b^2) with s = 2 (1 - cos kappa h) /
+    (kappa h)^2 the hat's factor for the sine (uniform spacing h along z)."""
+    nu, a, b, c, nz = 1e-3, 0.5, 0.7, 0.4, 16
     m = O.Mesh(2, 2, nz, 5, n_layers=0, nu=nu)
     lz = math.pi
     kap = 2 * math.pi / lz
-    u = _std_field(m, lambda x, y, z: (1 - y ** 2) * (1 + a * np.sin(kap * z)), lambda x, y, z: 0 * y,
+    u = _std_field(m, lambda x, y, z: (1 - y ** 2) * (1 + a * np.sin(kap * z)), lambda x, y, z: (1 - y ** 2) * c,
                    lambda x, y, z: (1 - y ** 2) * b + 0 * x)
     tn = m.wall_shear(u).reshape(2, nz, 2)            # [wall][k][i]
     h = lz / nz
     s = 2 * (1 - math.cos(kap * h)) / (kap * h) ** 2
     zk = np.arange(nz) * h
-    ref = 2 * nu * np.sqrt((1 + a * s * np.sin(kap * zk)) ** 2 + b ** 2)
+    ref = 2 * nu * np.sqrt((1 + a * s * np.sin(kap * zk)) ** 2 + c ** 2 + b ** 2)
     for wall in range(2):
         for i in range(2):
             assert np.abs(tn[wall, :, i] / ref - 1.0).max() < 1e-6
