@@ -1904,9 +1904,10 @@ def test_pressure_neumann_on_the_sloped_bump_wall():
     wall's integral of q = 1 is -2 beta a^2 L_z int x y_w'(x) dx = 2 beta a^2 L_z int y_w dx (periodic,
     y_w = 0 at the ends), with y_w the mesh's Q_k wall, whose bump area is 9 * 3.036 - V / L_z (V the
     separately pinned volume; both integrals are exact for the polynomial map); the flat top wall gets
-    nothing."""
+    nothing. A body force f = (0, f_y, 0) adds f . n: -f_y L_x L_z on the bump wall (n_y dA = -dx dz
+    there, whatever the slope) and +f_y L_x L_z on the top wall."""
     m = O.Mesh(12, 4, 1, 3, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
-    a, beta = 0.7, 1.5
+    a, beta, fy = 0.7, 1.5, 0.25
     u = _std_field(m, lambda x, y, z: a * x, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
     y = m.pressure_neumann(u, np.zeros(m.n_u), beta).reshape(1, 4, 12, -1)
     area = 9.0 * 3.036 - m.volume() / 4.5
@@ -1914,6 +1915,9 @@ def test_pressure_neumann_on_the_sloped_bump_wall():
     ref = 2 * beta * a * a * 4.5 * area
     assert abs(y[:, 0].sum() / ref - 1.0) < 1e-11
     assert abs(y[:, 3].sum()) < 1e-12 * ref
+    yf = m.pressure_neumann(u, np.zeros(m.n_u), beta, f=(0.0, fy, 0.0)).reshape(1, 4, 12, -1)
+    assert abs(yf[:, 0].sum() / (ref - fy * 9.0 * 4.5) - 1.0) < 1e-11
+    assert abs(yf[:, 3].sum() / (fy * 9.0 * 4.5) - 1.0) < 1e-11
 
 
 def test_pressure_neumann_viscous_part():
