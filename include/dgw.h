@@ -103,10 +103,12 @@ dgw_status dgw_mesh_create(const dgw_mesh_params *params, void *stream, dgw_mesh
 /* Free a mesh and everything the library holds for it (solver, Helmholtz and projection workspaces).
  * Waits for the device; NULL is accepted. Handles, not paper operations: no passage defines these. */
 dgw_status dgw_mesh_destroy(dgw_mesh_t mesh);
-/* n_p = nc (k+1)^3, n_u = 3 n_p + 24 n_enriched (enrich_l = 1) or 3 n_p + 3 n_enriched
- * (enrich_l = 0); hbm_bytes = device memory the mesh holds. */
+/* Sizes of the discrete spaces (Sec. 3.1 enrichment, Sec. 4.2 spaces): n_p = nc (k+1)^3,
+ * n_u = 3 n_p + 24 n_enriched (enrich_l = 1) or 3 n_p + 3 n_enriched (enrich_l = 0);
+ * hbm_bytes = device memory the mesh holds. */
 dgw_status dgw_mesh_info(dgw_mesh_t mesh, long *n_p, long *n_u, long *n_enriched, size_t *hbm_bytes);
-/* Physical positions of the pressure/velocity nodes, host buffer of 3*n_p doubles,
+/* Physical positions of the pressure/velocity nodes (the Gauss-Lobatto nodal points of the Q_k basis,
+ * Sec. 4.4; on curved cells the isoparametric map of Sec. 5.2), host buffer of 3*n_p doubles,
  * layout [c][(k+1)^3][xyz]. */
 dgw_status dgw_mesh_node_coords(dgw_mesh_t mesh, double *xyz_host);
 
@@ -186,8 +188,8 @@ dgw_status dgw_apply_inverse_mass(dgw_mesh_t mesh, const double *r, double *x, v
  * dgw_project_velocity (whose new space follows the threshold). Asynchronous. */
 dgw_status dgw_set_enrichment_switch(dgw_mesh_t mesh, double yplus_off, void *stream);
 
-/* Which enriched cells have the wall model switched on: active_host[e] (n_enriched ints, may be
- * NULL) and their count *n_active (may be NULL). Synchronises `stream`. */
+/* Which enriched cells have the wall model switched on (the switch-off of Sec. 3.2): active_host[e]
+ * (n_enriched ints, may be NULL) and their count *n_active (may be NULL). Synchronises `stream`. */
 dgw_status dgw_enrichment_active(dgw_mesh_t mesh, int *active_host, int *n_active, void *stream);
 
 /* y = -L(q, p) (Sec. 4.2, SIPG Laplace term with the flux of eq. ipflux on interior and
@@ -199,7 +201,8 @@ dgw_status dgw_apply_laplace(dgw_mesh_t mesh, int prec, const void *p, void *y, 
  * divergence; boundary rule below eq. poissonspat). u: n_u doubles, b: n_p doubles. */
 dgw_status dgw_apply_divergence(dgw_mesh_t mesh, const double *u, double *b, void *stream);
 
-/* The same divergence with a precision: DGW_FP64 (as dgw_apply_divergence) or DGW_DF64 (double
+/* The same divergence (Sec. 4.2, velocity divergence item) with a precision: DGW_FP64 (as
+ * dgw_apply_divergence) or DGW_DF64 (double
  * vectors, double-float arithmetic on the box rows whose cells and neighbours are standard cells;
  * the rows of and next to the enriched layers are computed in FP64; box cells only, DGW_EINVAL on
  * curved meshes). u: n_u doubles, b: n_p doubles. */
@@ -241,7 +244,8 @@ typedef struct {
 dgw_status dgw_pressure_solve(dgw_mesh_t mesh, const double *b, double *p, const dgw_solve_opts *opts,
                               dgw_solve_info *info, void *stream);
 
-/* Mixed-precision solves (mode 1 of dgw_pressure_solve) of ncols right-hand sides on one mesh, run
+/* Mixed-precision solves (mode 1 of dgw_pressure_solve; Sec. 4.1 eq. poisson) of ncols right-hand
+ * sides on one mesh, run
  * as one block: up to 8 columns share every launch (the FP32 operator, one captured V-cycle over the
  * block, the FP64 operator of the refinement), dot products are kept per column in a fixed order, so
  * each column's result does not depend on the other columns (the same bits alone or in any block).
@@ -345,7 +349,8 @@ typedef struct {
  * starting from the velocity u0 (n_u doubles, device, copied). The integrator owns its vectors;
  * the mesh must outlive it. Synchronises `stream`. */
 dgw_status dgw_ns_create(dgw_mesh_t mesh, const dgw_ns_params *params, const double *u0, void *stream, dgw_ns_t *out);
-/* Free the integrator's vectors (not the mesh); NULL is accepted. */
+/* Free the integrator's vectors (not the mesh); NULL is accepted. A handle of the Sec. 4.1 scheme,
+ * not an operation of the paper. */
 dgw_status dgw_ns_destroy(dgw_ns_t ns);
 /* One time step, BDF2 with second-order extrapolation (first order in the first step), constant dt
  * or (adaptive_dt) the CFL step of dgw_cfl_rate with the variable-step constants:
@@ -357,14 +362,16 @@ dgw_status dgw_ns_destroy(dgw_ns_t ns);
  * with tau_D and nu_t from u^n, CG with the exact inverse mass for the projection and GMRES for the
  * viscous step. Synchronises `stream`. DGW_ENOTCONV if a solve reaches max_iter. */
 dgw_status dgw_ns_step(dgw_ns_t ns, dgw_ns_step_info *info, void *stream);
-/* Device pointers of the current velocity u^n and pressure p^n (owned by the integrator, valid until
- * the next step) and the number of steps taken. */
+/* Device pointers of the current velocity u^n and pressure p^n of the Sec. 4.1 scheme (owned by the
+ * integrator, valid until the next step) and the number of steps taken. */
 dgw_status dgw_ns_state(dgw_ns_t ns, const double **u_dev, const double **p_dev, int *steps);
-/* Copy the current velocity (n_u doubles) and/or pressure (n_p doubles) into caller-owned device
- * buffers (either may be NULL). Asynchronous on `stream`. */
+/* Copy the current velocity (n_u doubles) and/or pressure (n_p doubles) of the Sec. 4.1 scheme into
+ * caller-owned device buffers (either may be NULL). Asynchronous on `stream`. */
 dgw_status dgw_ns_copy_state(dgw_ns_t ns, double *u_dev, double *p_dev, void *stream);
 
-/* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32): number of
+/* Describe (building it if needed) the multigrid hierarchy of `mode` (0 FP64, 1 FP32) that
+ * preconditions the pressure solve (Sec. 4.4 names a multigrid-preconditioned CG; the hierarchy is
+ * this library's own design): number of
  * levels, the estimated largest eigenvalue of D^-1 A per level (the Chebyshev smoother works on
  * [1.1 lmax / 45, 1.1 lmax]) and the cell count per level, finest first; at most max_levels
  * entries are written. Synchronises the library's solver stream. */
@@ -407,7 +414,8 @@ dgw_status dgw_submit(dgw_server_t server, const dgw_job *job, long *ticket);
  * otherwise DGW_OK with the job's own status (DGW_ENOMEM if it can never fit the budget), the solve
  * info (solves) and the submit-to-completion latency. A completed ticket is reported once. */
 dgw_status dgw_poll(dgw_server_t server, long ticket, dgw_status *job_status, dgw_solve_info *info, double *latency_ms);
-/* Queue depth, running jobs, resident meshes and reserved device bytes. */
+/* Queue depth, running jobs, resident meshes and reserved device bytes (request loop; no counterpart
+ * in the paper). */
 dgw_status dgw_server_stats(dgw_server_t server, int *queued, int *running, int *resident_meshes, size_t *reserved_bytes);
 /* Cancel queued jobs and wait up to timeout_ms for running ones; on DGW_ETIMEOUT the server stays
  * alive (running jobs still own their streams) and may be destroyed again later. */
@@ -416,8 +424,9 @@ dgw_status dgw_server_destroy(dgw_server_t server, int timeout_ms);
 /* Thread-local description of the last error. */
 const char *dgw_last_error(void);
 
-/* Process-wide counters since the library was loaded: kernels the library launched, and operator
- * DoF applications (the output DoFs of every operator apply, including those inside solves). */
+/* Process-wide counters since the library was loaded (no counterpart in the paper): kernels the
+ * library launched, and operator DoF applications (the output DoFs of every operator apply,
+ * including those inside solves). */
 void dgw_counters(unsigned long long *kernel_launches, unsigned long long *dof_applies);
 
 #ifdef __cplusplus
