@@ -31,10 +31,7 @@
  *     Hillewaert"); Spalding B = 5.17; Gauss-Lobatto nodal points; homogeneous Neumann data for
  *     the pressure on walls; enriched wall faces belong to the enriched-face class with the mirror
  *     state; nu_t frozen from a separately passed velocity field.
- *
- * Parity unpinned: in dgo_pressure_neumann, the enrichment of the vorticity input and the x and z
- * components of its curl, which reach the Neumann data only through the normal of a sloped (bump)
- * wall; no pin has an enriched vorticity there.
+
  */
 #include <math.h>
 #include <stdlib.h>

@@ -1905,7 +1905,8 @@ def test_pressure_neumann_on_the_sloped_bump_wall():
     y_w = 0 at the ends), with y_w the mesh's Q_k wall, whose bump area is 9 * 3.036 - V / L_z (V the
     separately pinned volume; both integrals are exact for the polynomial map); the flat top wall gets
     nothing. A body force f = (0, f_y, 0) adds f . n: -f_y L_x L_z on the bump wall (n_y dA = -dx dz
-    there, whatever the slope) and +f_y L_x L_z on the top wall."""
+    there, whatever the slope) and +f_y L_x L_z on the top wall. The viscous part nu curl(omega) . n
+    reaches the bump wall through n_x: with omega = (0, c x z, 0) it is -beta nu c L_z A_w."""
     m = O.Mesh(12, 4, 1, 3, lx=9.0, ly=3.036, lz=4.5, geometry=1, n_layers=0)
     a, beta, fy = 0.7, 1.5, 0.25
     u = _std_field(m, lambda x, y, z: a * x, lambda x, y, z: 0 * y, lambda x, y, z: 0 * y)
@@ -1918,6 +1919,14 @@ def test_pressure_neumann_on_the_sloped_bump_wall():
     yf = m.pressure_neumann(u, np.zeros(m.n_u), beta, f=(0.0, fy, 0.0)).reshape(1, 4, 12, -1)
     assert abs(yf[:, 0].sum() / (ref - fy * 9.0 * 4.5) - 1.0) < 1e-11
     assert abs(yf[:, 3].sum() / (fy * 9.0 * 4.5) - 1.0) < 1e-11
+    # viscous part: u = 0 and omega = (0, c x z, 0) cell by cell, curl omega = (-c x, 0, c z), so the
+    # bump wall gets -beta nu int (-c x) n_x dA = beta nu c L_z int x y_w' dx = -beta nu c L_z A_w
+    nu, c = m.params.nu, 0.9
+    om = _std_field(m, lambda x, y, z: 0 * y, lambda x, y, z: c * x * z, lambda x, y, z: 0 * y)
+    yv = m.pressure_neumann(np.zeros(m.n_u), om, beta).reshape(1, 4, 12, -1)
+    refv = -beta * nu * c * 4.5 * area
+    assert abs(yv[:, 0].sum() / refv - 1.0) < 1e-11
+    assert abs(yv[:, 3].sum()) < 1e-12 * abs(refv)
 
 
 def test_pressure_neumann_viscous_part():
