@@ -1065,6 +1065,35 @@ def test_oracle_operators_overwrite_their_output():
         assert np.abs(clean).max() > 0.0, name
 
 
+def test_active_cell_mask_restricts_outputs_to_those_cells():
+    """The sampling mask (used for sampled full-size parity and the CPU baseline) computes the outputs
+    of the masked cells exactly as the whole operator does and leaves the other cells' outputs zero;
+    clearing the mask restores the whole operator."""
+    w = I.WORKLOADS["channel_q2_8x8x8"]
+    m = O.Mesh(3, 4, 2, 2, lx=w.lx, lz=w.lz, nu=w.nu, tau_w=w.tau_w)
+    u = I.uniform(41, m.n_u, -1, 1)
+    p = I.uniform(42, m.n_p, -1, 1)
+    full = {"laplace": m.laplace(p), "divergence": m.divergence(u), "convective": m.convective(u),
+            "viscous": m.viscous(u, u)}
+    cells = [0, 5, 13, 23]
+    m.set_active(cells)
+    mask = np.zeros(m.nc, dtype=bool)
+    mask[cells] = True
+    n3 = (2 + 1) ** 3
+    part = {"laplace": m.laplace(p), "divergence": m.divergence(u), "convective": m.convective(u),
+            "viscous": m.viscous(u, u)}
+    m.set_active(None)
+    for name in full:
+        a, b = full[name], part[name]
+        std_n = m.n_p if name in ("laplace", "divergence") else 3 * m.n_p
+        per = 1 if name in ("laplace", "divergence") else 3
+        sa = a[:std_n].reshape(m.nc, per * n3)
+        sb = b[:std_n].reshape(m.nc, per * n3)
+        assert np.array_equal(sa[mask], sb[mask]), name
+        assert np.abs(sb[~mask]).max() == 0.0, name
+    assert np.array_equal(m.convective(u), full["convective"])
+
+
 def test_oracle_solve_reaches_tolerance_zero_mean():
     w = I.WORKLOADS["channel_q2_8x8x8"]
     m = O.Mesh(3, 4, 3, 2, n_layers=0, nu=w.nu)
