@@ -985,6 +985,7 @@ def test_enrichment_reproduces_wall_law_profile():
             yp = (1.0 - abs(yphys)) * w.u_tau / w.nu
             assert abs(r["yplus"] - yp) < 1e-10 * max(yp, 1)
             assert abs(r["u"][0] - w.u_tau * O.psi_spalding(yp)[0]) < 1e-14
+            assert abs(r["psi"] - O.psi_spalding(yp)[0]) < 1e-11 * max(1.0, abs(r["psi"]))
             assert abs(r["u"][1]) < 1e-300 and abs(r["u"][2]) < 1e-300
 
 
